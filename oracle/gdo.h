@@ -1,0 +1,151 @@
+/*
+ * gdo.h -- plain, serial, FP64 CPU oracle of the GameDev collision step
+ * (representative-particle Monte Carlo with frozen neighbourhoods).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load, call or run this code.
+ * It shares no code, header, table or constant with the CUDA library; it is
+ * written from the paper's definitions, step by step, with no blocking,
+ * fusion or reordering beyond what those definitions state.
+ *
+ * Units are cgs throughout.  Every function cites the paper passage it
+ * follows (section / equation names of "GameDev: GPU-accelerated model for
+ * dust evolution").  Where the paper is silent the reading taken is marked
+ * "reading:"; the same reading is implemented, independently, on the GPU.
+ *
+ * Compile with -ffp-contract=off: no fused multiply-adds, so every FP64
+ * expression is evaluated exactly as written (left to right).
+ */
+#ifndef GDO_H
+#define GDO_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { GDO_PATCH = 0, GDO_DISK = 1 };
+enum { GDO_PHYSICAL = 0, GDO_CONSTANT = 1, GDO_LINEAR = 2, GDO_PRODUCT = 3 };
+enum { GDO_NFINE = 96, GDO_TMIN = -72 };          /* fine controller bins */
+
+/* status bits (sticky) */
+enum {
+  GDO_ST_EVENT_CAP = 1 << 0,   /* a particle hit max_events in one interval */
+  GDO_ST_DT_FLOOR  = 1 << 1,   /* requested interval below dt_coll / 2^60 */
+  GDO_ST_NONFINITE = 1 << 2,   /* a rate was NaN or infinite */
+  GDO_ST_KNN       = 1 << 3    /* instance holds fewer than K particles */
+};
+
+typedef struct {
+  int32_t geometry;     /* GDO_PATCH: local periodic patch (x,y periodic), GDO_DISK: global disk */
+  int32_t kernel_mode;  /* GDO_PHYSICAL or one of the Appendix A test kernels */
+  int32_t K;            /* N_K, neighbours including the particle itself */
+  int32_t audit;        /* 1: adaptive safety factor C, 0: C fixed at 1 */
+  double r0;            /* reference radius R_0 [cm] (patch: its centre radius) */
+  double sigma0;        /* gas surface density at R_0 [g cm^-2] */
+  double p;             /* surface-density power-law index */
+  double T0;            /* gas temperature at R_0 [K] */
+  double q;             /* temperature power-law index */
+  double alpha;         /* viscosity parameter */
+  double M_star;        /* stellar mass [g] */
+  double rho_s;         /* grain internal density rho_o [g cm^-3] */
+  double s_min;         /* minimum fragment diameter [cm] */
+  double v_frag;        /* fragmentation speed [cm s^-1] */
+  double eps;           /* interval tolerance epsilon */
+  double dt_coll;       /* collision timestep Delta t_coll [s] */
+  double dt_fn_max;     /* maximum frozen-neighbour interval [s] */
+  double R_in, R_out;   /* global disk radial edges [cm] */
+  double box_x, box_y;  /* patch periodic extents [cm]; positions in [-box/2, box/2) */
+  double t0, m0;        /* test-kernel unit time [s] and unit mass [g] */
+  uint64_t seed;        /* Philox key */
+  int64_t max_events;   /* per particle and interval */
+} gdo_params;
+
+typedef struct {
+  double C;             /* adaptive safety factor, starts at 1 */
+  double dt_remain;     /* time left in the current collision timestep (derived from remain_ticks) */
+  double dt_exe;        /* executed interval of the last call */
+  double dt_req;        /* requested interval of the last call */
+  int64_t remain_ticks; /* time left, exactly, in units of dt_coll / 2^60 */
+  int64_t interval;     /* Philox interval counter of the next interval */
+  int64_t events;       /* events in the last interval */
+  int64_t near_draw;    /* near ties of draws against rate / time boundaries */
+  int64_t near_dt;      /* near ties of dt_req against a halving boundary */
+  int64_t near_audit;   /* near ties of the audit threshold */
+  int64_t status;       /* GDO_ST_* bits */
+  int32_t n_groups;     /* merged controller bins of the last call */
+  int32_t pad;
+} gdo_state;
+
+/* Gas and particle-independent quantities at one position (Sect. 2.2, 2.3.1). */
+typedef struct {
+  double R, Z, r, Om, T, cs, H, h, Sigma, rho_g, eta, Re, gst;
+} gdo_gas;
+
+/* Everything the rate model gives for one ordered pair (i, j) (Sect. 2.5.1-2.5.3). */
+typedef struct {
+  double dvR, dvZ, dvphi, dvB, dvt, dv, Kij, lam;
+  double psi, ncoll;
+  int32_t outcome;      /* 0 sticking, 1 erosion, 2 fragmentation */
+  int32_t pad;
+  double c[2];          /* effective channel rates lambda*_ij (second is 0 unless erosion) */
+  double J1[2], J2[2];  /* <J> and <J^2> of each channel */
+} gdo_pair_t;
+
+/* Optional per-particle outputs of one interval (any pointer may be NULL). */
+typedef struct {
+  int32_t* nbr;      /* [n*K] neighbour list: slot 0 the particle itself, then ascending index */
+  double*  d;        /* [n]   distance to the farthest retained neighbour */
+  double*  V;        /* [n]   sampling measure V_i */
+  double*  lam;      /* [n]   lambda*_i at the start of the interval */
+  double*  mA;       /* [n]   sum_o lambda*_io <J_io> */
+  double*  mB;       /* [n]   sum_o lambda*_io <J_io^2> */
+  double*  chan;     /* [n*K*2] channel rates lambda*_ij at the start of the interval */
+  int32_t* ev_count; /* [n]   events of the interval */
+  uint32_t* ev_hash; /* [n]   hash of the chosen (slot, channel) sequence */
+  int32_t* near;     /* [n]   near ties met while sampling the particle */
+  double*  jsum;     /* [n]   realised sum of |ln(s'/s)| over the interval's events */
+} gdo_outputs;
+
+void   gdo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+double gdo_u01(uint32_t a, uint32_t b);
+void   gdo_gas_at(const gdo_params* P, double x, double y, double z, gdo_gas* g);
+int    gdo_knn_one(const gdo_params* P, int64_t n, const double* x, const double* y,
+                   const double* z, int64_t i, int32_t* nbr, double* d);
+double gdo_volume(const gdo_params* P, double d, double R);
+double gdo_grain_mass(const gdo_params* P, double s);
+void   gdo_frag_moments(double s_i, double s_min, double* j1, double* j2);
+double gdo_turb_dv2(double St_a, double St_b, double Vg2, double Re);
+void   gdo_pair(const gdo_params* P, const gdo_gas* g, double s_i, double m_i,
+                double s_j, double m_j, double N_j, double V_i, gdo_pair_t* out);
+int    gdo_fine_bin(double s);
+void   gdo_choose_interval(const gdo_params* P, int64_t n, const double* s, const double* M,
+                           const double* mA, const double* mB, gdo_state* st, int32_t* group_of);
+void   gdo_audit(const gdo_params* P, int64_t n, const double* M, const double* jsum,
+                 const int32_t* group_of_particle, int32_t n_groups, gdo_state* st);
+int    gdo_sample_one(const gdo_params* P, const gdo_gas* g, int64_t i, const int32_t* nbr,
+                      double V_i, const double* s0, const double* m0, const double* N0,
+                      double M_i, double dt_exe, int64_t interval, double* s_io,
+                      int32_t* ev_count, uint32_t* ev_hash, int32_t* near, double* jsum,
+                      int64_t* status);
+int    gdo_interval_step(const gdo_params* P, int64_t n, const double* x, const double* y,
+                         const double* z, double* s, const double* M, gdo_state* st,
+                         gdo_outputs* out);
+int    gdo_rates_subset(const gdo_params* P, int64_t n, const double* x, const double* y,
+                        const double* z, const double* s, const double* M, int64_t nq,
+                        const int64_t* q, const int32_t* nbr, const double* d,
+                        double* lam, double* mA, double* mB, double* chan);
+int    gdo_sample_subset(const gdo_params* P, int64_t n, const double* x, const double* y,
+                         const double* z, const double* s0, const double* M, int64_t nq,
+                         const int64_t* q, const int32_t* nbr, const double* d, double dt_exe,
+                         int64_t interval, double* s_q, int32_t* ev_count, uint32_t* ev_hash,
+                         int32_t* near, double* jsum, int64_t* status);
+void   gdo_push_one(const gdo_params* P, int32_t drag, double dt, double* x, double* y,
+                    double* z, double* vr, double* lth, double* lph, double s);
+void   gdo_push(const gdo_params* P, int32_t drag, double dt, int64_t n, double* x, double* y,
+                double* z, double* vr, double* lth, double* lph, const double* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

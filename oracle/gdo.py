@@ -1,0 +1,290 @@
+"""ctypes wrapper of the plain FP64 CPU oracle (oracle/gdo.c).
+
+TEST INFRASTRUCTURE ONLY: only tests/, __graft_entry__.smoke() and the
+cpu_baseline / reference legs of bench.py may import this module.  It imports
+nothing from the CUDA package; inputs come from the seeded generators in
+paper_2609_35967_gb300.workloads (which hold none of the method's arithmetic).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gdo.c")
+_LIB = os.path.join(_HERE, "libgdo.so")
+_lock = threading.Lock()
+_lib = None
+
+PATCH, DISK = 0, 1
+PHYSICAL, CONSTANT, LINEAR, PRODUCT = 0, 1, 2, 3
+NFINE = 96
+
+
+def build(force: bool = False) -> str:
+    """Compile gdo.c with gcc (-O2, no FP contraction) into oracle/libgdo.so."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC),
+                                              os.path.getmtime(os.path.join(_HERE, "gdo.h")))):
+        return _LIB
+    tmp = _LIB + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+           "-shared", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Params(C.Structure):
+    _fields_ = [("geometry", C.c_int32), ("kernel_mode", C.c_int32), ("K", C.c_int32),
+                ("audit", C.c_int32),
+                ("r0", C.c_double), ("sigma0", C.c_double), ("p", C.c_double),
+                ("T0", C.c_double), ("q", C.c_double), ("alpha", C.c_double),
+                ("M_star", C.c_double), ("rho_s", C.c_double), ("s_min", C.c_double),
+                ("v_frag", C.c_double), ("eps", C.c_double), ("dt_coll", C.c_double),
+                ("dt_fn_max", C.c_double), ("R_in", C.c_double), ("R_out", C.c_double),
+                ("box_x", C.c_double), ("box_y", C.c_double), ("t0", C.c_double),
+                ("m0", C.c_double), ("seed", C.c_uint64), ("max_events", C.c_int64)]
+
+
+class State(C.Structure):
+    _fields_ = [("C", C.c_double), ("dt_remain", C.c_double), ("dt_exe", C.c_double),
+                ("dt_req", C.c_double), ("remain_ticks", C.c_int64), ("interval", C.c_int64), ("events", C.c_int64),
+                ("near_draw", C.c_int64), ("near_dt", C.c_int64), ("near_audit", C.c_int64),
+                ("status", C.c_int64), ("n_groups", C.c_int32), ("pad", C.c_int32)]
+
+
+class Gas(C.Structure):
+    _fields_ = [(k, C.c_double) for k in
+                ("R", "Z", "r", "Om", "T", "cs", "H", "h", "Sigma", "rho_g", "eta", "Re", "gst")]
+
+
+class Pair(C.Structure):
+    _fields_ = [("dvR", C.c_double), ("dvZ", C.c_double), ("dvphi", C.c_double),
+                ("dvB", C.c_double), ("dvt", C.c_double), ("dv", C.c_double),
+                ("Kij", C.c_double), ("lam", C.c_double), ("psi", C.c_double),
+                ("ncoll", C.c_double), ("outcome", C.c_int32), ("pad", C.c_int32),
+                ("c", C.c_double * 2), ("J1", C.c_double * 2), ("J2", C.c_double * 2)]
+
+
+class Outputs(C.Structure):
+    _fields_ = [("nbr", C.c_void_p), ("d", C.c_void_p), ("V", C.c_void_p),
+                ("lam", C.c_void_p), ("mA", C.c_void_p), ("mB", C.c_void_p),
+                ("chan", C.c_void_p), ("ev_count", C.c_void_p), ("ev_hash", C.c_void_p),
+                ("near", C.c_void_p), ("jsum", C.c_void_p)]
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_LIB)
+            vp, i64, dbl = C.c_void_p, C.c_int64, C.c_double
+            L.gdo_philox4x32_10.argtypes = [vp, vp, vp]
+            L.gdo_u01.argtypes = [C.c_uint32, C.c_uint32]
+            L.gdo_u01.restype = dbl
+            L.gdo_gas_at.argtypes = [vp, dbl, dbl, dbl, vp]
+            L.gdo_knn_one.argtypes = [vp, i64, vp, vp, vp, i64, vp, vp]
+            L.gdo_volume.argtypes = [vp, dbl, dbl]
+            L.gdo_volume.restype = dbl
+            L.gdo_grain_mass.argtypes = [vp, dbl]
+            L.gdo_grain_mass.restype = dbl
+            L.gdo_frag_moments.argtypes = [dbl, dbl, vp, vp]
+            L.gdo_turb_dv2.argtypes = [dbl, dbl, dbl, dbl]
+            L.gdo_turb_dv2.restype = dbl
+            L.gdo_pair.argtypes = [vp, vp, dbl, dbl, dbl, dbl, dbl, dbl, vp]
+            L.gdo_fine_bin.argtypes = [dbl]
+            L.gdo_fine_bin.restype = C.c_int
+            L.gdo_choose_interval.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
+            L.gdo_audit.argtypes = [vp, i64, vp, vp, vp, C.c_int32, vp]
+            L.gdo_interval_step.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp]
+            L.gdo_rates_subset.argtypes = [vp, i64, vp, vp, vp, vp, vp, i64, vp, vp, vp,
+                                           vp, vp, vp, vp]
+            L.gdo_sample_subset.argtypes = [vp, i64, vp, vp, vp, vp, vp, i64, vp, vp, vp,
+                                            dbl, i64, vp, vp, vp, vp, vp, vp]
+            L.gdo_push_one.argtypes = [vp, C.c_int32, dbl, vp, vp, vp, vp, vp, vp, dbl]
+            L.gdo_push.argtypes = [vp, C.c_int32, dbl, i64, vp, vp, vp, vp, vp, vp, vp]
+            _lib = L
+    return _lib
+
+
+_PARAM_KEYS = [f for f, _ in Params._fields_]
+
+
+def params(d: dict) -> Params:
+    """Oracle parameter struct from an instance dict (extra keys are ignored)."""
+    P = Params()
+    for k in _PARAM_KEYS:
+        if k in d:
+            setattr(P, k, d[k])
+    if "max_events" not in d:
+        P.max_events = 1 << 20
+    return P
+
+
+def new_state(P: Params) -> State:
+    st = State()
+    st.C = 1.0
+    st.dt_remain = P.dt_coll
+    st.remain_ticks = 1 << 60
+    st.interval = 0
+    return st
+
+
+def philox(ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().gdo_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def u01(a: int, b: int) -> float:
+    return lib().gdo_u01(a, b)
+
+
+def gas(P: Params, x: float, y: float, z: float) -> dict:
+    g = Gas()
+    lib().gdo_gas_at(C.byref(P), x, y, z, C.byref(g))
+    return {k: getattr(g, k) for k, _ in Gas._fields_}
+
+
+def gas_struct(P: Params, x: float, y: float, z: float) -> Gas:
+    g = Gas()
+    lib().gdo_gas_at(C.byref(P), x, y, z, C.byref(g))
+    return g
+
+
+def knn(P: Params, x, y, z, queries) -> tuple[np.ndarray, np.ndarray]:
+    """Brute-force lists for the given query indices: ([nq, K] int32, [nq] d)."""
+    x, y, z = (np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, z))
+    q = np.asarray(queries, dtype=np.int64)
+    nbr = np.zeros((len(q), P.K), dtype=np.int32)
+    d = np.zeros(len(q), dtype=np.float64)
+    L = lib()
+    dv = C.c_double()
+    for t, i in enumerate(q):
+        rc = L.gdo_knn_one(C.byref(P), len(x), _p(x), _p(y), _p(z), int(i),
+                           nbr[t].ctypes.data_as(C.c_void_p), C.byref(dv))
+        if rc != 0:
+            raise ValueError("instance holds fewer than K particles")
+        d[t] = dv.value
+    return nbr, d
+
+
+def volume(P: Params, d: float, R: float) -> float:
+    return lib().gdo_volume(C.byref(P), d, R)
+
+
+def grain_mass(P: Params, s: float) -> float:
+    return lib().gdo_grain_mass(C.byref(P), s)
+
+
+def frag_moments(s_i: float, s_min: float) -> tuple[float, float]:
+    a, b = C.c_double(), C.c_double()
+    lib().gdo_frag_moments(s_i, s_min, C.byref(a), C.byref(b))
+    return a.value, b.value
+
+
+def turb_dv2(sa, sb, vg2, re) -> float:
+    return lib().gdo_turb_dv2(sa, sb, vg2, re)
+
+
+def pair(P: Params, g: Gas, s_i, m_i, s_j, m_j, N_j, V_i) -> dict:
+    o = Pair()
+    lib().gdo_pair(C.byref(P), C.byref(g), s_i, m_i, s_j, m_j, N_j, V_i, C.byref(o))
+    r = {k: getattr(o, k) for k, _ in Pair._fields_ if k not in ("c", "J1", "J2", "pad")}
+    r["c"] = list(o.c)
+    r["J1"] = list(o.J1)
+    r["J2"] = list(o.J2)
+    return r
+
+
+def fine_bin(s: float) -> int:
+    return lib().gdo_fine_bin(s)
+
+
+def choose_interval(P: Params, st: State, s, M, mA, mB) -> np.ndarray:
+    s, M, mA, mB = (np.ascontiguousarray(a, dtype=np.float64) for a in (s, M, mA, mB))
+    grp = np.zeros(len(s), dtype=np.int32)
+    lib().gdo_choose_interval(C.byref(P), len(s), _p(s), _p(M), _p(mA), _p(mB),
+                              C.byref(st), _p(grp))
+    return grp
+
+
+def audit(P: Params, st: State, M, jsum, grp, n_groups):
+    M, jsum = (np.ascontiguousarray(a, dtype=np.float64) for a in (M, jsum))
+    grp = np.ascontiguousarray(grp, dtype=np.int32)
+    lib().gdo_audit(C.byref(P), len(M), _p(M), _p(jsum), _p(grp), n_groups, C.byref(st))
+
+
+def interval_step(P: Params, st: State, x, y, z, s, M, want=("nbr", "d", "V", "lam",
+                  "ev_count", "ev_hash", "near")) -> dict:
+    """One whole interval of one instance; s (float64 array) is updated in place."""
+    x, y, z, M = (np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, z, M))
+    assert s.dtype == np.float64 and s.flags.c_contiguous
+    n, K = len(x), P.K
+    shapes = {"nbr": ((n, K), np.int32), "d": (n, np.float64), "V": (n, np.float64),
+              "lam": (n, np.float64), "mA": (n, np.float64), "mB": (n, np.float64),
+              "chan": ((n, K, 2), np.float64), "ev_count": (n, np.int32),
+              "ev_hash": (n, np.uint32), "near": (n, np.int32), "jsum": (n, np.float64)}
+    res = {k: np.zeros(*shapes[k]) for k in want}
+    out = Outputs(**{k: _p(v) for k, v in res.items()})
+    rc = lib().gdo_interval_step(C.byref(P), n, _p(x), _p(y), _p(z), _p(s), _p(M),
+                                 C.byref(st), C.byref(out))
+    if rc != 0:
+        raise ValueError("oracle interval failed (instance smaller than K?)")
+    return res
+
+
+def rates_subset(P: Params, x, y, z, s, M, queries, nbr, d, chan=False) -> dict:
+    x, y, z, s, M = (np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, z, s, M))
+    q = np.ascontiguousarray(queries, dtype=np.int64)
+    nbr = np.ascontiguousarray(nbr, dtype=np.int32)
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    nq = len(q)
+    lam, mA, mB = np.zeros(nq), np.zeros(nq), np.zeros(nq)
+    ch = np.zeros((nq, P.K, 2)) if chan else None
+    lib().gdo_rates_subset(C.byref(P), len(x), _p(x), _p(y), _p(z), _p(s), _p(M), nq, _p(q),
+                           _p(nbr), _p(d), _p(lam), _p(mA), _p(mB), _p(ch))
+    r = {"lam": lam, "mA": mA, "mB": mB}
+    if chan:
+        r["chan"] = ch
+    return r
+
+
+def sample_subset(P: Params, x, y, z, s0, M, queries, nbr, d, dt_exe, interval) -> dict:
+    x, y, z, s0, M = (np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, z, s0, M))
+    q = np.ascontiguousarray(queries, dtype=np.int64)
+    nbr = np.ascontiguousarray(nbr, dtype=np.int32)
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    nq = len(q)
+    s_q = np.zeros(nq)
+    ec = np.zeros(nq, dtype=np.int32)
+    eh = np.zeros(nq, dtype=np.uint32)
+    nn = np.zeros(nq, dtype=np.int32)
+    js = np.zeros(nq)
+    status = C.c_int64(0)
+    lib().gdo_sample_subset(C.byref(P), len(x), _p(x), _p(y), _p(z), _p(s0), _p(M), nq, _p(q),
+                            _p(nbr), _p(d), dt_exe, interval, _p(s_q), _p(ec), _p(eh), _p(nn),
+                            _p(js), C.byref(status))
+    return {"s": s_q, "ev_count": ec, "ev_hash": eh, "near": nn, "jsum": js,
+            "status": status.value}
+
+
+def push(P: Params, x, y, z, vr, lth, lph, s, dt, drag=True):
+    """One staggered semi-analytic step of every particle, in place (float64 arrays)."""
+    for arr in (x, y, z, vr, lth, lph):
+        assert arr.dtype == np.float64 and arr.flags.c_contiguous
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    lib().gdo_push(C.byref(P), 1 if drag else 0, dt, len(x), _p(x), _p(y), _p(z), _p(vr),
+                   _p(lth), _p(lph), _p(s))
