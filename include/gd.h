@@ -1,0 +1,242 @@
+/*
+ * gd.h -- C ABI of the GB300 collision-step library (libgd.so).
+ *
+ * One call sequence advances every instance by one frozen-neighbour interval
+ * of the representative-particle Monte Carlo of "GameDev: GPU-accelerated
+ * model for dust evolution" (Sect. 2.5):
+ *
+ *   gd_build_neighbors    K nearest neighbours over a device cell list,
+ *                         sampling measures                      (Sect. 2.5.1)
+ *   gd_collision_rates    pair rates lambda_ij = n_ij K_ij, outcome channels,
+ *                         controller-bin moments and the executed interval
+ *                                                        (Sect. 2.5.1-2.5.3)
+ *   gd_sample_collisions  Gillespie sampling of events against the frozen
+ *                         neighbourhood, mass/weight updates      (Sect. 2.5.3)
+ *   gd_push_staggered     staggered semi-analytic trajectory step (Sect. 2.3.3)
+ *   gd_stats              reductions and counters (the only call that
+ *                         synchronises the stream)
+ *
+ * Conventions
+ *  - Units: cgs.  s is the grain diameter, M the represented particle mass
+ *    (constant), N = M/m with m = pi rho_o s^3 / 6 (Sect. 2).
+ *  - Particles of all instances are concatenated (CSR): instance b owns the
+ *    global indices [offsets[b], offsets[b+1]).  Every pointer to particle
+ *    data is a DEVICE pointer owned by the caller, who must keep it alive for
+ *    the life of the context; the library reads and writes it in place
+ *    (s, and x, y, z, vr, lth, lph in gd_push_staggered) and never writes M.
+ *  - The library owns its scratch (cell lists, neighbour lists in cell order,
+ *    frozen snapshots, controller bins, per-instance state); gd_create
+ *    allocates it with cudaMalloc, gd_destroy frees it.
+ *  - Every call except gd_stats and gd_destroy only enqueues work on the
+ *    context's stream and is asynchronous.  Argument and sequencing errors
+ *    return at once; errors found on the device set sticky status bits that
+ *    gd_stats reports (GD_ST_*).  No call aborts the process or traps the GPU.
+ *  - Optional *_out pointers are caller DEVICE buffers (NULL: not written).
+ */
+#ifndef GD_H
+#define GD_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gd_ctx gd_ctx;
+
+typedef enum {
+  GD_OK = 0,
+  GD_ERR_ARG = -1,       /* invalid argument                                  */
+  GD_ERR_CUDA = -2,      /* a CUDA runtime call failed                         */
+  GD_ERR_OOM = -3,       /* device allocation failed                           */
+  GD_ERR_CAPACITY = -4,  /* a library-owned buffer is too small                */
+  GD_ERR_NONFINITE = -5, /* a rate was NaN or infinite                         */
+  GD_ERR_EVENT_CAP = -6, /* a particle reached max_events_per_interval         */
+  GD_ERR_TIMEOUT = -7,   /* a bounded device wait gave up                      */
+  GD_ERR_STATE = -8      /* calls out of order (e.g. rates before neighbours)   */
+} gd_status;
+
+/* precision of the path */
+enum {
+  GD_FP64 = 0,   /* every step in FP64                                         */
+  GD_MIXED = 1   /* FP32 distances (FP64 re-rank at the K boundary), FP32 pair
+                    rates; FP64 prefix sums, waiting times, masses and weights  */
+};
+
+enum { GD_GEOM_PATCH = 0, GD_GEOM_DISK = 1 };
+enum { GD_KERNEL_PHYSICAL = 0, GD_KERNEL_CONSTANT = 1, GD_KERNEL_LINEAR = 2,
+       GD_KERNEL_PRODUCT = 3 };
+
+/* sticky device status bits */
+enum {
+  GD_ST_EVENT_CAP = 1 << 0,  /* a particle reached max_events_per_interval      */
+  GD_ST_DT_FLOOR = 1 << 1,   /* requested interval below dt_coll / 2^60          */
+  GD_ST_NONFINITE = 1 << 2,  /* NaN or infinite rate                             */
+  GD_ST_KNN = 1 << 3,        /* neighbour search could not find K-1 others       */
+  GD_ST_CAPACITY = 1 << 4,   /* cell grid exceeded its capacity                  */
+  GD_ST_TIMEOUT = 1 << 5     /* a bounded device wait gave up                    */
+};
+
+/* flags of gd_config.flags */
+enum {
+  GD_FLAG_TIMING = 1 << 0,   /* time every kernel with CUDA events (gd_stats)   */
+  GD_FLAG_NO_AUDIT = 1 << 1  /* keep the safety factor C at 1 in all instances  */
+};
+
+/* Per-instance parameters (Sect. 2.2 gas disk, Sect. 2.5 collision model). */
+typedef struct {
+  int32_t geometry;    /* GD_GEOM_PATCH: local patch, x radial / y azimuthal
+                          offsets in [-box/2, box/2), both periodic, z free;
+                          GD_GEOM_DISK: global disk, R = sqrt(x^2+y^2)        */
+  int32_t kernel_mode; /* GD_KERNEL_*: physical kernel or an Appendix A test
+                          kernel (V_i = 1, lambda_ij = (1/t0)(1/N_K)(m0/m_j) K) */
+  int32_t audit;       /* 1: adaptive safety factor C; 0: C = 1              */
+  int32_t pad0;
+  double r0;           /* reference radius R_0 (patch: its radius) [cm]      */
+  double sigma0;       /* gas surface density at R_0 [g cm^-2]               */
+  double p;            /* Sigma_g ~ R^p                                      */
+  double T0;           /* temperature at R_0 [K]                             */
+  double q;            /* T ~ R^q                                            */
+  double alpha;        /* viscosity parameter                                */
+  double M_star;       /* stellar mass [g]                                   */
+  double rho_s;        /* grain internal density rho_o [g cm^-3]             */
+  double s_min;        /* minimum fragment diameter [cm]                     */
+  double v_frag;       /* fragmentation speed [cm s^-1]                      */
+  double eps;          /* interval tolerance epsilon                         */
+  double dt_coll;      /* collision timestep [s]                             */
+  double dt_fn_max;    /* maximum frozen-neighbour interval [s]              */
+  double R_in, R_out;  /* global disk radial edges [cm] (flat-boundary caps)  */
+  double box_x, box_y; /* patch periodic extents [cm]                        */
+  double t0, m0;       /* test-kernel unit time and mass                     */
+  double cell_size;    /* cell edge [cm]; <= 0: chosen from the data          */
+  uint64_t seed;       /* Philox key of the instance                         */
+} gd_instance_params;
+
+typedef struct {
+  int32_t n_instances;
+  int32_t K;                   /* N_K, neighbours including the particle itself, 2..256 */
+  int32_t precision;           /* GD_FP64 or GD_MIXED                         */
+  int32_t flags;               /* GD_FLAG_*                                   */
+  const int64_t* offsets;      /* HOST [n_instances + 1], offsets[0] = 0      */
+  const gd_instance_params* params;  /* HOST [n_instances]                   */
+  double* x;                   /* DEVICE [N] positions [cm]                   */
+  double* y;
+  double* z;
+  double* s;                   /* DEVICE [N] diameters [cm], updated in place */
+  const double* M;             /* DEVICE [N] particle masses [g], read only    */
+  double* vr;                  /* DEVICE [N] or NULL: v_r      (push only)    */
+  double* lth;                 /* DEVICE [N] or NULL: l_theta  (push only)    */
+  double* lph;                 /* DEVICE [N] or NULL: l_phi    (push only)    */
+  void* stream;                /* cudaStream_t; NULL = legacy default stream  */
+  int64_t max_events_per_interval;   /* per particle; <= 0: 65536              */
+  double cell_factor;          /* cell edge = factor (V_box/N)^(1/3) when the
+                                  instance gives none; <= 0: 1                 */
+  int32_t knn_block;           /* threads per block of the neighbour kernel (0: 256) */
+  int32_t pad1;
+} gd_config;
+
+/* Library-wide counters (gd_stats). */
+typedef struct {
+  int64_t intervals;           /* completed gd_sample_collisions calls         */
+  int64_t events;              /* all events so far                            */
+  int64_t near_draw;           /* draws within 1e-10 of a rate / time boundary */
+  int64_t near_dt;             /* interval choices within 1e-10 of an edge     */
+  int64_t near_audit;          /* audit decisions within 1e-10 of the threshold */
+  int64_t launches;            /* kernels launched by the library so far       */
+  uint32_t status;             /* OR of every instance's GD_ST_* bits          */
+  int32_t n_instances;
+  double kernel_ms[8];         /* GD_FLAG_TIMING: summed kernel time by step:
+                                  0 cells, 1 knn, 2 rates, 3 interval, 4 sample,
+                                  5 push, 6 stats/other, 7 unused              */
+  int64_t kernel_calls[8];     /* launches timed in each slot                  */
+} gd_stats_t;
+
+/* Per-instance state and reductions (gd_stats). */
+typedef struct {
+  double C;                    /* safety factor                                */
+  double dt_exe;               /* executed interval of the last call [s]       */
+  double dt_req;               /* requested interval of the last call [s]      */
+  double dt_remain;            /* time left in the collision timestep [s]      */
+  double sum_M;                /* sum of M_i                                   */
+  double sum_Mm;               /* sum of M_i m_i (mass-weighted mean mass numerator) */
+  double sum_Ms;               /* sum of M_i s_i                               */
+  int64_t interval;            /* intervals executed                           */
+  int64_t events;              /* events of the last interval                  */
+  int64_t events_total;
+  int64_t near_draw, near_dt, near_audit;
+  uint32_t status;             /* GD_ST_* bits of this instance                */
+  int32_t n_groups;            /* controller bins of the last interval         */
+} gd_instance_stats;
+
+/* Creates a context over caller-owned particle arrays (see gd_config).  Checks
+ * every argument (each instance must hold at least K particles), copies the
+ * parameter tables to the device and allocates the library's scratch.
+ * Returns GD_ERR_ARG, GD_ERR_OOM or GD_ERR_CUDA on failure (*out = NULL). */
+gd_status gd_create(gd_ctx** out, const gd_config* cfg);
+
+/* Waits for the context's stream, frees everything the library allocated. */
+gd_status gd_destroy(gd_ctx* ctx);
+
+/* Sect. 2.5.1: bins every particle into a per-instance uniform cell grid
+ * (counting sort by cell), then finds each particle's N_K nearest particles
+ * of its instance, itself included at zero distance (minimum image across a
+ * patch's periodic edges), ranked by (d^2, index) with
+ * d^2 = (dx dx + dy dy) + dz dz in FP64.  Lists hold the particle itself in
+ * slot 0 and the other K-1 in ascending index order (the channel order used
+ * for sampling).  Also computes d_i (distance to the farthest retained
+ * neighbour), the sampling measure V_i = 4 pi d_i^3 / 3 minus flat-boundary
+ * caps at a global disk's radial edges (Sect. 2.5.1), and freezes the partner
+ * properties (s, m, N) for the interval (Sect. 2.5.3).
+ * nbr_out: DEVICE int32 [N*K] or NULL, global particle indices, row i for
+ * particle i.  d_out: DEVICE double [N] or NULL. */
+gd_status gd_build_neighbors(gd_ctx* ctx, int32_t* nbr_out, double* d_out);
+
+/* Sect. 2.5.1-2.5.3: for every particle and slot, the relative speed
+ * (radial drift, settling, azimuthal, Brownian and turbulent terms at the
+ * query particle's position), K_ij = pi (s_i+s_j)^2 dv / 4,
+ * lambda_ij = N_j K_ij / V_i, the outcome (sticking / erosion / fragmentation)
+ * with grouping N_coll, the effective channel rates lambda*_ij and
+ * lambda*_i = sum_j lambda*_ij; then the controller-bin moments A_b, B_b and,
+ * per instance, dt_req = min(dt_remain, dt_fn_max, eps C / A_b,
+ * eps^2 C^2 / B_b) and dt_exe = dt_coll / 2^k (smallest k with dt_exe <=
+ * dt_req).  Requires gd_build_neighbors since the last sampling.
+ * lambda_out: DEVICE double [N] or NULL: lambda*_i.
+ * chan_out: DEVICE double [N*K*2] or NULL: lambda*_ij per slot and channel. */
+gd_status gd_collision_rates(gd_ctx* ctx, double* lambda_out, double* chan_out);
+
+/* Sect. 2.5.3: each particle draws waiting times -ln U / lambda*_i until they
+ * exceed dt_exe; each event picks a channel with probability
+ * lambda*_ij / lambda*_i, applies the outcome to the particle alone (M kept,
+ * N' = M/m'), and refreshes the particle's own rates against the frozen
+ * partners.  Draws: Philox4x32-10, key = instance seed, counter =
+ * (index within instance, interval, event, 0|1).  Writes the new diameters
+ * into cfg.s and runs the post-interval audit of C.  Requires
+ * gd_collision_rates since the last build.
+ * ev_count_out, ev_hash_out, near_out: DEVICE [N] or NULL: events of each
+ * particle, a hash of its chosen channel sequence, and its near ties. */
+gd_status gd_sample_collisions(gd_ctx* ctx, int32_t* ev_count_out, uint32_t* ev_hash_out,
+                               int32_t* near_out);
+
+/* Sect. 2.3.3: one staggered semi-analytic step of length dt (dt < 0: each
+ * instance's last dt_exe) for every particle of every global-disk instance:
+ * drift half a step, exact linear-drag kick toward the gas velocity with
+ * gravity and the angular-momentum forces at the midpoint, drift the second
+ * half in mirrored order.  Needs vr, lth, lph in the config. */
+gd_status gd_push_staggered(gd_ctx* ctx, double dt);
+
+/* Synchronises the stream, reduces per-instance sums and copies counters.
+ * out: HOST, required.  inst_out: HOST [n_instances] or NULL.
+ * Returns the first device error as a gd_status (GD_OK if none). */
+gd_status gd_stats(gd_ctx* ctx, gd_stats_t* out, gd_instance_stats* inst_out);
+
+/* Runs n whole intervals (build, rates, sample and, if push != 0, push with
+ * dt_exe) by replaying a CUDA graph of one interval captured on first use
+ * (captures again if the arguments change).  Asynchronous. */
+gd_status gd_run_intervals(gd_ctx* ctx, int32_t n, int32_t push);
+
+/* Static string for a gd_status code. */
+const char* gd_status_string(gd_status code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

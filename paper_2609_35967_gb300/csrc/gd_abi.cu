@@ -1,0 +1,379 @@
+// gd_abi.cu -- the C ABI of include/gd.h: argument checks, the library-owned memory
+// plan, call sequencing, per-kernel event timing, CUDA-graph replay and gd_stats.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "gd_ctx.h"
+
+namespace gd {
+
+void time_begin(gd_ctx* c, int slot) {
+  if (!(c->flags & GD_FLAG_TIMING)) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(c->stream, &cs);
+  if (cs != cudaStreamCaptureStatusNone) { c->ev_slot.push_back(-1); return; }
+  if (c->ev_used == c->ev_pool.size()) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return;
+    if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return; }
+    c->ev_pool.push_back({a, b});
+  }
+  cudaEventRecord(c->ev_pool[c->ev_used].first, c->stream);
+  c->ev_slot.push_back(slot);
+}
+
+void time_end(gd_ctx* c) {
+  if (!(c->flags & GD_FLAG_TIMING)) return;
+  if (c->ev_slot.empty()) return;
+  if (c->ev_slot.back() < 0) { c->ev_slot.pop_back(); return; }
+  cudaEventRecord(c->ev_pool[c->ev_used].second, c->stream);
+  c->ev_used++;
+}
+
+static void collect_timing(gd_ctx* c) {
+  size_t k = 0;
+  for (size_t i = 0; i < c->ev_slot.size() && k < c->ev_used; ++i) {
+    int slot = c->ev_slot[i];
+    if (slot < 0) continue;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev_pool[k].first, c->ev_pool[k].second) == cudaSuccess) {
+      c->ms[slot] += ms;
+      c->calls[slot] += 1;
+    }
+    ++k;
+  }
+  c->ev_slot.clear();
+  c->ev_used = 0;
+}
+
+}  // namespace gd
+
+using namespace gd;
+
+static gd_status cuda_err(cudaError_t e) { return e == cudaSuccess ? GD_OK : GD_ERR_CUDA; }
+
+template <typename T>
+static cudaError_t dalloc(T** p, size_t n) {
+  if (n == 0) n = 1;
+  return cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T));
+}
+
+static void free_all(gd_ctx* c) {
+  void* ptrs[] = {c->d_off, c->d_tile_off, c->d_inst, c->d_grid, c->d_state, c->d_bins, c->d_cell_count,
+                  c->d_cell_start, c->d_scan_tmp, c->d_cell_of, c->d_slot, c->d_perm, c->d_rank_of,
+                  c->d_pos64, c->d_pos32, c->d_snap64, c->d_snap32, c->d_Mr, c->d_dist, c->d_V,
+                  c->d_lam, c->d_nbr, c->d_counters, c->d_sums};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (auto& e : c->ev_pool) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+  c->ev_pool.clear();
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  c->graph_exec = nullptr;
+}
+
+static bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
+  if (!out) return GD_ERR_ARG;
+  *out = nullptr;
+  if (!cfg || cfg->n_instances < 1 || !cfg->offsets || !cfg->params) return GD_ERR_ARG;
+  if (cfg->K < 2 || cfg->K > kMaxK) return GD_ERR_ARG;
+  if (cfg->precision != GD_FP64 && cfg->precision != GD_MIXED) return GD_ERR_ARG;
+  if (!cfg->x || !cfg->y || !cfg->z || !cfg->s || !cfg->M) return GD_ERR_ARG;
+  const int n = cfg->n_instances;
+  if (cfg->offsets[0] != 0) return GD_ERR_ARG;
+  for (int b = 0; b < n; ++b) {
+    if (cfg->offsets[b + 1] - cfg->offsets[b] < cfg->K) return GD_ERR_ARG;
+    const gd_instance_params& p = cfg->params[b];
+    if (p.geometry != GD_GEOM_PATCH && p.geometry != GD_GEOM_DISK) return GD_ERR_ARG;
+    if (p.kernel_mode < GD_KERNEL_PHYSICAL || p.kernel_mode > GD_KERNEL_PRODUCT) return GD_ERR_ARG;
+    if (!finite_pos(p.r0) || !finite_pos(p.sigma0) || !finite_pos(p.T0) || !finite_pos(p.M_star) ||
+        !finite_pos(p.rho_s) || !finite_pos(p.s_min) || !finite_pos(p.eps) || !finite_pos(p.dt_coll) ||
+        !finite_pos(p.dt_fn_max) || !(p.alpha >= 0.0) || !(p.v_frag > 0.0))
+      return GD_ERR_ARG;
+    if (p.geometry == GD_GEOM_PATCH && (!finite_pos(p.box_x) || !finite_pos(p.box_y))) return GD_ERR_ARG;
+    if (p.geometry == GD_GEOM_DISK && !(p.R_out > p.R_in)) return GD_ERR_ARG;
+    if (p.kernel_mode != GD_KERNEL_PHYSICAL && (!finite_pos(p.t0) || !finite_pos(p.m0))) return GD_ERR_ARG;
+  }
+  const long long N = cfg->offsets[n];
+  if (N >= (1LL << 31) - 1 || (long long)N * cfg->K >= (1LL << 40)) return GD_ERR_ARG;
+
+  gd_ctx* c = new (std::nothrow) gd_ctx();
+  if (!c) return GD_ERR_OOM;
+  c->n_inst = n;
+  c->K = cfg->K;
+  c->precision = cfg->precision;
+  c->flags = cfg->flags;
+  c->N = N;
+  c->cell_factor = cfg->cell_factor > 0.0 ? cfg->cell_factor : 1.0;
+  c->knn_block = cfg->knn_block > 0 ? cfg->knn_block : 256;
+  if (c->knn_block % 32 != 0 || c->knn_block > 1024) { delete c; return GD_ERR_ARG; }
+  c->max_events = cfg->max_events_per_interval > 0 ? cfg->max_events_per_interval : 65536;
+  c->stream = static_cast<cudaStream_t>(cfg->stream);
+  c->x = cfg->x; c->y = cfg->y; c->z = cfg->z; c->s = cfg->s; c->M = cfg->M;
+  c->vr = cfg->vr; c->lth = cfg->lth; c->lph = cfg->lph;
+  c->h_off.assign(cfg->offsets, cfg->offsets + n + 1);
+  c->h_params.assign(cfg->params, cfg->params + n);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    delete c;
+    return GD_ERR_CUDA;
+  }
+
+  std::vector<long long> tiles = tile_table(c->h_off);
+  c->n_tiles = (int)tiles.back();
+  c->cell_cap = 2 * N + 64LL * n + 1024;
+  long long nst = (c->cell_cap + 2047) / 2048;
+
+  bool ok = true;
+  ok &= dalloc(&c->d_off, n + 1) == cudaSuccess;
+  ok &= dalloc(&c->d_tile_off, n + 1) == cudaSuccess;
+  ok &= dalloc(&c->d_inst, n) == cudaSuccess;
+  ok &= dalloc(&c->d_grid, n) == cudaSuccess;
+  ok &= dalloc(&c->d_state, n) == cudaSuccess;
+  ok &= dalloc(&c->d_bins, n) == cudaSuccess;
+  ok &= dalloc(&c->d_cell_count, c->cell_cap + 1) == cudaSuccess;
+  ok &= dalloc(&c->d_cell_start, c->cell_cap + 1) == cudaSuccess;
+  ok &= dalloc(&c->d_scan_tmp, nst) == cudaSuccess;
+  ok &= dalloc(&c->d_cell_of, N) == cudaSuccess;
+  ok &= dalloc(&c->d_slot, N) == cudaSuccess;
+  ok &= dalloc(&c->d_perm, N) == cudaSuccess;
+  ok &= dalloc(&c->d_rank_of, N) == cudaSuccess;
+  ok &= dalloc(&c->d_pos64, N) == cudaSuccess;
+  ok &= dalloc(&c->d_snap64, N) == cudaSuccess;
+  if (c->precision == GD_MIXED) {
+    ok &= dalloc(&c->d_pos32, N) == cudaSuccess;
+    ok &= dalloc(&c->d_snap32, N) == cudaSuccess;
+  }
+  ok &= dalloc(&c->d_Mr, N) == cudaSuccess;
+  ok &= dalloc(&c->d_dist, N) == cudaSuccess;
+  ok &= dalloc(&c->d_V, N) == cudaSuccess;
+  ok &= dalloc(&c->d_lam, N) == cudaSuccess;
+  ok &= dalloc(&c->d_nbr, (size_t)N * c->K) == cudaSuccess;
+  ok &= dalloc(&c->d_counters, 16) == cudaSuccess;
+  ok &= dalloc(&c->d_sums, 3 * (size_t)n) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_all(c);
+    delete c;
+    return GD_ERR_OOM;
+  }
+
+  std::vector<InstDev> inst(n);
+  std::vector<StateDev> st(n);
+  for (int b = 0; b < n; ++b) {
+    const gd_instance_params& p = c->h_params[b];
+    InstDev& d = inst[b];
+    std::memset(&d, 0, sizeof(d));
+    d.geometry = p.geometry;
+    d.kernel_mode = p.kernel_mode;
+    d.audit = p.audit;
+    d.r0 = p.r0; d.sigma0 = p.sigma0; d.p = p.p; d.T0 = p.T0; d.q = p.q; d.alpha = p.alpha;
+    d.GM = kG * p.M_star;
+    d.rho_s = p.rho_s; d.s_min = p.s_min; d.v_frag = p.v_frag; d.eps = p.eps;
+    d.dt_coll = p.dt_coll; d.dt_fn_max = p.dt_fn_max; d.R_in = p.R_in; d.R_out = p.R_out;
+    d.box_x = p.box_x; d.box_y = p.box_y; d.t0 = p.t0; d.m0 = p.m0; d.cell_size = p.cell_size;
+    d.key0 = (uint32_t)p.seed;
+    d.key1 = (uint32_t)(p.seed >> 32);
+    d.off = c->h_off[b];
+    d.n = c->h_off[b + 1] - c->h_off[b];
+    if (p.geometry == GD_GEOM_DISK) c->any_disk = true;
+    StateDev& s = st[b];
+    std::memset(&s, 0, sizeof(s));
+    s.C = 1.0;
+    s.remain_ticks = 1LL << 60;
+    s.dt_remain = p.dt_coll;
+    for (int a = 0; a < 3; ++a) { s.bmin[a] = ~0ull; s.bmax[a] = 0ull; }
+  }
+  cudaStream_t str = c->stream;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_off, c->h_off.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, str);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_tile_off, tiles.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, str);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_inst, inst.data(), sizeof(InstDev) * n, cudaMemcpyHostToDevice, str);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_state, st.data(), sizeof(StateDev) * n, cudaMemcpyHostToDevice, str);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_bins, 0, sizeof(BinsDev) * n, str);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * 16, str);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(str);
+  if (e != cudaSuccess) {
+    free_all(c);
+    delete c;
+    return GD_ERR_CUDA;
+  }
+  *out = c;
+  return GD_OK;
+}
+
+extern "C" gd_status gd_destroy(gd_ctx* c) {
+  if (!c) return GD_ERR_ARG;
+  cudaStreamSynchronize(c->stream);
+  free_all(c);
+  delete c;
+  return GD_OK;
+}
+
+static gd_status do_build(gd_ctx* c, int32_t* nbr_out, double* d_out) {
+  cudaError_t e = launch_cells(c);
+  if (e == cudaSuccess) e = launch_knn(c);
+  if (e == cudaSuccess) e = launch_outputs_knn(c, nbr_out, d_out);
+  if (e != cudaSuccess) return GD_ERR_CUDA;
+  c->phase = 1;
+  return GD_OK;
+}
+
+static gd_status do_rates(gd_ctx* c, double* lam_out, double* chan_out) {
+  cudaError_t e = launch_rates(c, chan_out);
+  if (e == cudaSuccess) e = launch_interval(c);
+  if (e == cudaSuccess) e = launch_outputs_lam(c, lam_out);
+  if (e != cudaSuccess) return GD_ERR_CUDA;
+  c->phase = 2;
+  return GD_OK;
+}
+
+static gd_status do_sample(gd_ctx* c, int32_t* ev_count, uint32_t* ev_hash, int32_t* near) {
+  cudaError_t e = launch_sample(c, ev_count, ev_hash, near);
+  if (e == cudaSuccess) e = launch_audit(c);
+  if (e != cudaSuccess) return GD_ERR_CUDA;
+  c->phase = 0;
+  c->intervals++;
+  return GD_OK;
+}
+
+extern "C" gd_status gd_build_neighbors(gd_ctx* c, int32_t* nbr_out, double* d_out) {
+  if (!c) return GD_ERR_ARG;
+  return do_build(c, nbr_out, d_out);
+}
+
+extern "C" gd_status gd_collision_rates(gd_ctx* c, double* lambda_out, double* chan_out) {
+  if (!c) return GD_ERR_ARG;
+  if (c->phase != 1) return GD_ERR_STATE;
+  return do_rates(c, lambda_out, chan_out);
+}
+
+extern "C" gd_status gd_sample_collisions(gd_ctx* c, int32_t* ev_count_out, uint32_t* ev_hash_out,
+                                          int32_t* near_out) {
+  if (!c) return GD_ERR_ARG;
+  if (c->phase != 2) return GD_ERR_STATE;
+  if ((ev_count_out != nullptr) != (ev_hash_out != nullptr) || (ev_count_out != nullptr) != (near_out != nullptr))
+    return GD_ERR_ARG;
+  return do_sample(c, ev_count_out, ev_hash_out, near_out);
+}
+
+extern "C" gd_status gd_push_staggered(gd_ctx* c, double dt) {
+  if (!c) return GD_ERR_ARG;
+  if (!c->vr || !c->lth || !c->lph) return GD_ERR_ARG;
+  if (!std::isfinite(dt)) return GD_ERR_ARG;
+  return cuda_err(launch_push(c, dt));
+}
+
+extern "C" gd_status gd_run_intervals(gd_ctx* c, int32_t n, int32_t push) {
+  if (!c || n < 0) return GD_ERR_ARG;
+  if (push && (!c->vr || !c->lth || !c->lph)) return GD_ERR_ARG;
+  if (c->phase != 0) return GD_ERR_STATE;
+  if (n == 0) return GD_OK;
+  bool can_graph = c->stream != nullptr && !(c->flags & GD_FLAG_TIMING);
+  if (!can_graph) {
+    for (int i = 0; i < n; ++i) {
+      gd_status s = do_build(c, nullptr, nullptr);
+      if (s == GD_OK) s = do_rates(c, nullptr, nullptr);
+      if (s == GD_OK) s = do_sample(c, nullptr, nullptr, nullptr);
+      if (s == GD_OK && push) s = cuda_err(launch_push(c, -1.0));
+      if (s != GD_OK) return s;
+    }
+    return GD_OK;
+  }
+  if (!c->graph_exec || c->graph_push != (push ? 1 : 0)) {
+    if (c->graph_exec) { cudaGraphExecDestroy(c->graph_exec); c->graph_exec = nullptr; }
+    cudaGraph_t g = nullptr;
+    long long l0 = c->launches;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return GD_ERR_CUDA;
+    gd_status s = do_build(c, nullptr, nullptr);
+    if (s == GD_OK) s = do_rates(c, nullptr, nullptr);
+    if (s == GD_OK) s = do_sample(c, nullptr, nullptr, nullptr);
+    if (s == GD_OK && push) s = cuda_err(launch_push(c, -1.0));
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    c->intervals -= 1;          // the capture executed nothing
+    c->launches = l0;
+    c->graph_kernel_count = 0;
+    if (s != GD_OK || e != cudaSuccess) { if (g) cudaGraphDestroy(g); return s != GD_OK ? s : GD_ERR_CUDA; }
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
+    for (size_t i = 0; i < nn; ++i) {
+      cudaGraphNodeType ty;
+      if (cudaGraphNodeGetType(nodes[i], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel)
+        c->graph_kernel_count++;
+    }
+    e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { c->graph_exec = nullptr; return GD_ERR_CUDA; }
+    c->graph_push = push ? 1 : 0;
+  }
+  for (int i = 0; i < n; ++i) {
+    if (cudaGraphLaunch(c->graph_exec, c->stream) != cudaSuccess) return GD_ERR_CUDA;
+    c->intervals++;
+    c->launches += c->graph_kernel_count;
+  }
+  c->phase = 0;
+  return GD_OK;
+}
+
+extern "C" gd_status gd_stats(gd_ctx* c, gd_stats_t* out, gd_instance_stats* inst_out) {
+  if (!c || !out) return GD_ERR_ARG;
+  if (launch_stats(c, c->d_sums) != cudaSuccess) return GD_ERR_CUDA;
+  std::vector<StateDev> st(c->n_inst);
+  std::vector<double> sums(3 * (size_t)c->n_inst);
+  cudaError_t e = cudaMemcpyAsync(st.data(), c->d_state, sizeof(StateDev) * c->n_inst, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sums.data(), c->d_sums, sizeof(double) * sums.size(), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return GD_ERR_CUDA;
+  collect_timing(c);
+  std::memset(out, 0, sizeof(*out));
+  out->intervals = c->intervals;
+  out->launches = c->launches;
+  out->n_instances = c->n_inst;
+  for (int k = 0; k < gd_ctx::kSlots; ++k) { out->kernel_ms[k] = c->ms[k]; out->kernel_calls[k] = c->calls[k]; }
+  for (int b = 0; b < c->n_inst; ++b) {
+    const StateDev& s = st[b];
+    out->events += s.events_total;
+    out->near_draw += s.near_draw;
+    out->near_dt += s.near_dt;
+    out->near_audit += s.near_audit;
+    out->status |= s.status;
+    if (inst_out) {
+      gd_instance_stats& o = inst_out[b];
+      std::memset(&o, 0, sizeof(o));
+      o.C = s.C; o.dt_exe = s.dt_exe; o.dt_req = s.dt_req; o.dt_remain = s.dt_remain;
+      o.sum_M = sums[3 * b]; o.sum_Mm = sums[3 * b + 1]; o.sum_Ms = sums[3 * b + 2];
+      o.interval = s.interval_next;
+      o.events = s.events;
+      o.events_total = s.events_total;
+      o.near_draw = s.near_draw; o.near_dt = s.near_dt; o.near_audit = s.near_audit;
+      o.status = s.status;
+      o.n_groups = s.n_groups;
+    }
+  }
+  if (out->status & GD_ST_NONFINITE) return GD_ERR_NONFINITE;
+  if (out->status & GD_ST_EVENT_CAP) return GD_ERR_EVENT_CAP;
+  if (out->status & GD_ST_CAPACITY) return GD_ERR_CAPACITY;
+  if (out->status & GD_ST_TIMEOUT) return GD_ERR_TIMEOUT;
+  return GD_OK;
+}
+
+extern "C" const char* gd_status_string(gd_status code) {
+  switch (code) {
+    case GD_OK: return "ok";
+    case GD_ERR_ARG: return "invalid argument";
+    case GD_ERR_CUDA: return "CUDA runtime error";
+    case GD_ERR_OOM: return "device allocation failed";
+    case GD_ERR_CAPACITY: return "library buffer capacity exceeded";
+    case GD_ERR_NONFINITE: return "non-finite rate";
+    case GD_ERR_EVENT_CAP: return "event cap reached";
+    case GD_ERR_TIMEOUT: return "bounded device wait gave up";
+    case GD_ERR_STATE: return "calls out of order";
+  }
+  return "unknown status";
+}

@@ -1,0 +1,181 @@
+// gd_common.cuh -- device-side types and helpers shared by the library's kernels.
+//
+// Layout in HBM (library-owned, one context):
+//   rank space  : particles sorted by (instance, cell); rank r of instance b lies in
+//                 [off[b], off[b+1]) like the caller's indices.  perm[r] is the caller
+//                 index, rank_of[i] its inverse.
+//   Pos64[r]    : {x, y, z, caller index}            32 B  (FP64 K-NN, re-rank)
+//   float4 pos32: {x-c, y-c, z-c, caller index bits} 16 B  (FP32 K-NN), c = instance centre
+//   Snap64[r]   : {s, m, N, 1/m} frozen at the interval start        32 B
+//   float4 snap32: {s, m, N 2^-64, 1/m} frozen, FP32                 16 B
+//   nbr[r*K+k]  : ranks of the K neighbours, slot 0 = self, others by ascending caller index
+//   cell_start  : exclusive scan of per-cell counts, instance grids concatenated
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/gd.h"
+
+namespace gd {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kKB = 1.380649e-16;     // Boltzmann constant [erg/K]
+constexpr double kMH = 1.6735575e-24;    // hydrogen mass [g]
+constexpr double kMu = 2.34;             // mean molecular weight
+constexpr double kG = 6.674e-8;          // gravitational constant
+constexpr double kSigH2 = 2e-15;         // H2 cross-section [cm^2]
+constexpr int kNFine = 96;               // fine controller bins per instance
+constexpr int kTMin = -72;               // fine bin of index 0: third-octave t = -72
+constexpr int kMaxK = 256;
+
+// Per-instance parameters as the kernels read them (derived once at create).
+struct InstDev {
+  int geometry, kernel_mode, audit, pad;
+  double r0, sigma0, p, T0, q, alpha, GM, rho_s, s_min, v_frag, eps, dt_coll, dt_fn_max;
+  double R_in, R_out, box_x, box_y, t0, m0, cell_size;
+  uint32_t key0, key1;
+  long long off, n;
+};
+
+// Uniform cell grid of one instance, rebuilt every interval from the data bounds.
+struct GridDev {
+  double lo[3];      // origin
+  double cs[3];      // cell edge per axis
+  double inv[3];     // 1 / cs
+  double box[3];     // periodic extent (x, y of a patch), 0 otherwise
+  double ctr[3];     // origin of the FP32 mirror coordinates
+  double X32;        // bound on |FP32 mirror coordinate| + periodic extents (error model)
+  int dim[3];
+  int periodic;      // x and y periodic (patch)
+  long long cell_off;
+};
+
+// Mutable per-instance state (device resident).
+struct StateDev {
+  double C, dt_exe, dt_req, dt_remain;
+  long long remain_ticks;   // exact time left: units of dt_coll / 2^60
+  long long interval_cur;   // Philox interval counter of the current interval
+  long long interval_next;
+  long long events, events_total, near_draw, near_dt, near_audit;
+  unsigned int status;
+  int n_groups;
+  // bounds of the data (ordered-integer encodings of doubles), min then max, x y z
+  unsigned long long bmin[3], bmax[3];
+};
+
+// Fine-bin accumulators of one instance (doubles; counts exact below 2^53).
+struct BinsDev {
+  double cnt[kNFine], sM[kNFine], sA[kNFine], sB[kNFine], sJ[kNFine];
+  int gid[kNFine];
+  int ngroups;
+  int pad;
+};
+
+struct Pos64 {
+  double x, y, z;
+  long long j;
+};
+
+struct Snap64 {
+  double s, m, N, inv_m;
+};
+
+// ---------------------------------------------------------------- small helpers
+__device__ __forceinline__ int inst_of(const long long* __restrict__ off, int n_inst, long long r) {
+  int lo = 0, hi = n_inst - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (__ldg(&off[mid]) <= r) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Order-preserving map of doubles to unsigned 64-bit integers (for atomic min/max).
+__device__ __forceinline__ unsigned long long dbl_ord(double v) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__host__ __device__ inline double ord_dbl(unsigned long long o) {
+  unsigned long long b = (o >> 63) ? (o & 0x7FFFFFFFFFFFFFFFull) : ~o;
+  union { unsigned long long u; double d; } c;
+  c.u = b;
+  return c.d;
+}
+
+// Fine controller bin: thirds of an octave, edges at 2^e {1/2, 2^(1/3)/2, 2^(2/3)/2}
+// taken from the exponent and mantissa bits of s (s > 0, normal).
+__device__ __forceinline__ int fine_bin(double s) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(s);
+  int e = (int)((b >> 52) & 0x7FF) - 1022;                   // s = mant 2^e, mant in [1/2, 1)
+  double mant = __longlong_as_double((long long)((b & 0x000FFFFFFFFFFFFFull) |
+                                                 0x3FE0000000000000ull));
+  int t = 3 * e + (mant >= 0x1.428a2f98d728bp-1 ? 1 : 0) + (mant >= 0x1.965fea53d6e3dp-1 ? 1 : 0);
+  t -= kTMin;
+  return t < 0 ? 0 : (t > kNFine - 1 ? kNFine - 1 : t);
+}
+
+// Cell index of a coordinate along one axis of an instance grid; periodic axes wrap.
+__device__ __forceinline__ int axis_cell(const GridDev& g, int a, double v) {
+  double t = floor((v - g.lo[a]) * g.inv[a]);
+  int d = g.dim[a];
+  if (g.box[a] > 0.0) {
+    t = fmin(fmax(t, -1e15), 1e15);
+    long long k = (long long)t;
+    k %= d;
+    if (k < 0) k += d;
+    return (int)k;
+  }
+  return t < 0.0 ? 0 : (t >= (double)d ? d - 1 : (int)t);
+}
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Salmon et al. (SC'11): 10 rounds of two 32x32 products, counter permutation
+// (hi1^c1^k0, lo1, hi0^c3^k1, lo0), key bumped by the Weyl constants between rounds.
+struct U4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                     uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+  }
+  return U4{c0, c1, c2, c3};
+}
+
+// (k + 1/2) 2^-52 with k built from 26 bits of each word: exact, in (0, 1).
+__device__ __forceinline__ double u01(uint32_t a, uint32_t b) {
+  unsigned long long k = ((unsigned long long)(a >> 6) << 26) | (unsigned long long)(b >> 6);
+  return ((double)k + 0.5) * 0x1p-52;
+}
+
+// ---------------------------------------------------------------- warp helpers
+__device__ __forceinline__ double warp_incl_scan(double v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    double t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v = __dadd_rn(v, t);
+  }
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ void set_status(StateDev* st, unsigned bits) {
+  atomicOr(&st->status, bits);
+}
+
+}  // namespace gd

@@ -1,0 +1,93 @@
+// gd_ctx.h -- host-side context of the library and the kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "gd_common.cuh"
+
+struct gd_ctx {
+  // configuration
+  int n_inst = 0, K = 0, precision = 0, flags = 0;
+  long long N = 0;
+  double cell_factor = 1.0;
+  int knn_block = 256;
+  long long max_events = 65536;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  std::vector<long long> h_off;
+  std::vector<gd_instance_params> h_params;
+  bool any_disk = false;
+
+  // caller-owned particle arrays (device)
+  double *x = nullptr, *y = nullptr, *z = nullptr, *s = nullptr;
+  const double* M = nullptr;
+  double *vr = nullptr, *lth = nullptr, *lph = nullptr;
+
+  // library-owned device memory
+  long long* d_off = nullptr;           // [n_inst + 1]
+  long long* d_tile_off = nullptr;      // [n_inst + 1] first per-particle tile of each instance
+  int n_tiles = 0;
+  gd::InstDev* d_inst = nullptr;        // [n_inst]
+  gd::GridDev* d_grid = nullptr;        // [n_inst]
+  gd::StateDev* d_state = nullptr;      // [n_inst]
+  gd::BinsDev* d_bins = nullptr;        // [n_inst]
+  long long cell_cap = 0;               // capacity of the concatenated cell arrays
+  int* d_cell_count = nullptr;          // [cell_cap + 1]
+  int* d_cell_start = nullptr;          // [cell_cap + 1]
+  int* d_scan_tmp = nullptr;            // block sums of the scan
+  int* d_cell_of = nullptr;             // [N] cell of each caller index
+  int* d_slot = nullptr;                // [N] position inside the cell
+  int* d_perm = nullptr;                // [N] rank -> caller index
+  int* d_rank_of = nullptr;             // [N] caller index -> rank
+  gd::Pos64* d_pos64 = nullptr;         // [N]
+  float4* d_pos32 = nullptr;            // [N]
+  gd::Snap64* d_snap64 = nullptr;       // [N]
+  float4* d_snap32 = nullptr;           // [N]
+  double* d_Mr = nullptr;               // [N] M in rank order
+  double* d_dist = nullptr;             // [N] d_i, rank order
+  double* d_V = nullptr;                // [N] V_i, rank order
+  double* d_lam = nullptr;              // [N] lambda*_i, rank order
+  int* d_nbr = nullptr;                 // [N*K] ranks
+  unsigned long long* d_counters = nullptr;  // [16] spare device counters
+  double* d_sums = nullptr;             // [3 * n_inst] gd_stats reductions
+
+  // sequencing: 0 nothing, 1 neighbours built, 2 rates done
+  int phase = 0;
+  long long intervals = 0;
+  long long launches = 0;
+
+  // timing
+  static constexpr int kSlots = 8;
+  double ms[kSlots] = {0};
+  long long calls[kSlots] = {0};
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+  std::vector<int> ev_slot;
+  size_t ev_used = 0;
+
+  // graph replay of one interval
+  cudaGraphExec_t graph_exec = nullptr;
+  int graph_push = -1;
+  long long graph_kernel_count = 0;     // kernel nodes of the captured interval
+};
+
+namespace gd {
+// launchers (each returns cudaGetLastError() of its launches)
+cudaError_t launch_cells(gd_ctx* c);
+cudaError_t launch_knn(gd_ctx* c);
+cudaError_t launch_rates(gd_ctx* c, double* chan_out);
+cudaError_t launch_interval(gd_ctx* c);
+cudaError_t launch_sample(gd_ctx* c, int* ev_count, unsigned* ev_hash, int* near);
+cudaError_t launch_audit(gd_ctx* c);
+cudaError_t launch_push(gd_ctx* c, double dt);
+cudaError_t launch_stats(gd_ctx* c, double* d_sums);
+cudaError_t launch_outputs_knn(gd_ctx* c, int* nbr_out, double* d_out);
+cudaError_t launch_outputs_lam(gd_ctx* c, double* lam_out);
+
+std::vector<long long> tile_table(const std::vector<long long>& off);
+
+// event timing around a launch (no-op unless GD_FLAG_TIMING)
+void time_begin(gd_ctx* c, int slot);
+void time_end(gd_ctx* c);
+}  // namespace gd

@@ -1,0 +1,342 @@
+// k_cells.cu -- device cell list: per-instance bounds and grid, counting sort by cell,
+// and the frozen partner snapshot of the interval (Sect. 2.5.1, 2.5.3).
+//
+// A counting sort replaces the paper's KD-tree / Morton hierarchy: every particle gets
+// the cell of its instance's uniform grid, cells are counted with atomics, an exclusive
+// scan gives cell starts, and a scatter writes the particle, in cell order, into the
+// rank-space arrays that the neighbour, rate and sampling kernels stream through.
+#include <vector>
+
+#include "gd_ctx.h"
+#include "gd_physics.cuh"
+
+namespace gd {
+
+constexpr int kTile = 4096;       // particles per block in the per-particle passes
+constexpr int kScanTile = 2048;   // cells per block in the scan
+
+// Per-block tiles never straddle an instance: tile t covers [tile_lo, tile_hi) of one
+// instance.  The tile table is derived on the fly from the offsets: block b belongs
+// to the instance whose tile range contains b.
+struct TileMap {
+  const long long* off;
+  int n_inst;
+  const long long* tile_off;   // [n_inst + 1] first tile of each instance
+};
+
+__device__ __forceinline__ bool tile_range(const TileMap& tm, int tile, int& b, long long& lo,
+                                           long long& hi) {
+  int l = 0, h = tm.n_inst - 1;
+  while (l < h) {
+    int mid = (l + h + 1) >> 1;
+    if (tm.tile_off[mid] <= tile) l = mid; else h = mid - 1;
+  }
+  b = l;
+  long long t = tile - tm.tile_off[b];
+  lo = tm.off[b] + t * kTile;
+  hi = min(lo + kTile, tm.off[b + 1]);
+  return lo < hi;
+}
+
+// ---------------------------------------------------------------- bounds
+__global__ void k_bounds(TileMap tm, const double* __restrict__ x, const double* __restrict__ y,
+                         const double* __restrict__ z, StateDev* st) {
+  int b;
+  long long lo, hi;
+  if (!tile_range(tm, blockIdx.x, b, lo, hi)) return;
+  unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0, 0, 0};
+  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    unsigned long long o[3] = {dbl_ord(x[i]), dbl_ord(y[i]), dbl_ord(z[i])};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { mn[a] = min(mn[a], o[a]); mx[a] = max(mx[a], o[a]); }
+  }
+  __shared__ unsigned long long smn[3][32], smx[3][32];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    for (int o = 16; o > 0; o >>= 1) {
+      mn[a] = min(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+      mx[a] = max(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+    }
+    if (lane == 0) { smn[a][w] = mn[a]; smx[a][w] = mx[a]; }
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    int a = threadIdx.x;
+    unsigned long long m0 = ~0ull, m1 = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { m0 = min(m0, smn[a][k]); m1 = max(m1, smx[a][k]); }
+    atomicMin(&st[b].bmin[a], m0);
+    atomicMax(&st[b].bmax[a], m1);
+  }
+}
+
+// ---------------------------------------------------------------- grid choice
+// One thread: per instance, a uniform grid over the data bounds (patch: the periodic
+// box in x and y), cell edge from the instance or cell_factor (V_box / n)^(1/3), then
+// the concatenated cell offsets.  If the total exceeds the capacity every edge grows.
+__global__ void k_grid(const InstDev* __restrict__ P, StateDev* st, GridDev* grid, int n_inst,
+                       double cell_factor, long long cell_cap) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double grow = 1.0;
+  for (int attempt = 0; attempt < 40; ++attempt) {
+    long long total = 0;
+    for (int b = 0; b < n_inst; ++b) {
+      GridDev g;
+      double lo[3], ext[3];
+      for (int a = 0; a < 3; ++a) {
+        double mn = ord_dbl(st[b].bmin[a]), mx = ord_dbl(st[b].bmax[a]);
+        lo[a] = mn;
+        ext[a] = mx - mn;
+      }
+      bool per = P[b].geometry == GD_GEOM_PATCH;
+      if (per) { lo[0] = -0.5 * P[b].box_x; ext[0] = P[b].box_x; lo[1] = -0.5 * P[b].box_y; ext[1] = P[b].box_y; }
+      double tiny = 1e-300;
+      double vol = 1.0;
+      double emax = 0.0;
+      for (int a = 0; a < 3; ++a) emax = fmax(emax, ext[a]);
+      for (int a = 0; a < 3; ++a) vol *= fmax(ext[a], 1e-6 * emax + tiny);
+      double c = P[b].cell_size > 0.0 ? P[b].cell_size : cell_factor * cbrt(vol / (double)P[b].n);
+      c *= grow;
+      long long cells = 1;
+      for (int a = 0; a < 3; ++a) {
+        bool pa = per && a < 2;
+        double e = pa ? ext[a] : ext[a] * (1.0 + 1e-9) + 1e-12 * emax + tiny;
+        double dimd = pa ? floor(e / c) : ceil(e / c);
+        int dim = (int)fmin(fmax(dimd, 1.0), a < 2 ? 2048.0 : 1024.0);
+        g.lo[a] = lo[a];
+        g.cs[a] = e / dim;
+        g.inv[a] = dim / e;
+        g.dim[a] = dim;
+        g.box[a] = pa ? ext[a] : 0.0;
+        g.ctr[a] = lo[a] + 0.5 * e;
+        cells *= dim;
+      }
+      double X = 0.0;
+      for (int a = 0; a < 3; ++a) X = fmax(X, 0.5 * g.cs[a] * g.dim[a]);
+      if (per) X += fmax(g.box[0], g.box[1]);
+      g.X32 = X;
+      g.periodic = per ? 1 : 0;
+      g.cell_off = total;
+      total += cells;
+      grid[b] = g;
+    }
+    if (total <= cell_cap) break;
+    grow *= 1.1 * cbrt((double)total / (double)cell_cap);
+    if (attempt == 39) {
+      // capacity exhausted: one cell per instance keeps every index in bounds
+      // (the search stays exact, only slower) and the status reports it
+      for (int b = 0; b < n_inst; ++b) {
+        set_status(&st[b], GD_ST_CAPACITY);
+        GridDev& g = grid[b];
+        for (int a = 0; a < 3; ++a) {
+          double e = g.cs[a] * g.dim[a];
+          g.dim[a] = 1;
+          g.cs[a] = e;
+          g.inv[a] = 1.0 / e;
+        }
+        g.cell_off = b;
+      }
+    }
+  }
+  for (int b = 0; b < n_inst; ++b)
+    for (int a = 0; a < 3; ++a) { st[b].bmin[a] = ~0ull; st[b].bmax[a] = 0ull; }
+}
+
+__global__ void k_cell_count(TileMap tm, const GridDev* __restrict__ grid, const double* __restrict__ x,
+                             const double* __restrict__ y, const double* __restrict__ z,
+                             int* __restrict__ count, int* __restrict__ cell_of, int* __restrict__ slot,
+                             long long cell_cap) {
+  int b;
+  long long lo, hi;
+  if (!tile_range(tm, blockIdx.x, b, lo, hi)) return;
+  const GridDev g = grid[b];
+  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    int ix = axis_cell(g, 0, x[i]), iy = axis_cell(g, 1, y[i]), iz = axis_cell(g, 2, z[i]);
+    long long c = g.cell_off + ix + (long long)g.dim[0] * (iy + (long long)g.dim[1] * iz);
+    if (c >= cell_cap) c = cell_cap - 1;    // only after a capacity failure (status set)
+    cell_of[i] = (int)c;
+    slot[i] = atomicAdd(&count[c], 1);
+  }
+}
+
+// ---------------------------------------------------------------- exclusive scan
+__device__ __forceinline__ int block_excl_scan(int v, int* sh, int& total) {
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) sh[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    int s = lane < nw ? sh[lane] : 0;
+    int si = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(0xffffffffu, si, o);
+      if (lane >= o) si += t;
+    }
+    if (lane < nw) sh[lane] = si - s;
+    if (lane == 31) sh[32] = si;
+  }
+  __syncthreads();
+  total = sh[32];
+  int r = inc - v + sh[w];
+  __syncthreads();
+  return r;
+}
+
+// phase 1: per-tile sums
+__global__ void k_scan_reduce(const int* __restrict__ in, long long n, int* __restrict__ sums) {
+  long long base = (long long)blockIdx.x * kScanTile;
+  int acc = 0;
+  for (int k = threadIdx.x; k < kScanTile; k += blockDim.x) {
+    long long i = base + k;
+    if (i < n) acc += in[i];
+  }
+  __shared__ int sh[33];
+  int total;
+  block_excl_scan(acc, sh, total);
+  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+// phase 2: exclusive scan of the tile sums (one block)
+__global__ void k_scan_sums(int* sums, int nt) {
+  __shared__ int sh[33];
+  int carry = 0;
+  for (int base = 0; base < nt; base += blockDim.x) {
+    int i = base + threadIdx.x;
+    int v = i < nt ? sums[i] : 0;
+    int total;
+    int e = block_excl_scan(v, sh, total);
+    if (i < nt) sums[i] = e + carry;
+    carry += total;
+  }
+}
+
+// phase 3: scan inside each tile plus its offset; out has n + 1 entries
+__global__ void k_scan_final(const int* __restrict__ in, long long n, const int* __restrict__ sums,
+                             int* __restrict__ out) {
+  long long base = (long long)blockIdx.x * kScanTile;
+  constexpr int per = kScanTile / 256;
+  int v[per];
+  int acc = 0;
+#pragma unroll
+  for (int k = 0; k < per; ++k) {
+    long long i = base + threadIdx.x * per + k;
+    v[k] = i < n ? in[i] : 0;
+    acc += v[k];
+  }
+  __shared__ int sh[33];
+  int total;
+  int e = block_excl_scan(acc, sh, total) + sums[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < per; ++k) {
+    long long i = base + threadIdx.x * per + k;
+    if (i < n) out[i] = e;
+    e += v[k];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 255) out[n] = e;
+}
+
+// ---------------------------------------------------------------- scatter + snapshot
+template <bool kMixed>
+__global__ void k_scatter(TileMap tm, const InstDev* __restrict__ P, const GridDev* __restrict__ grid,
+                          const double* __restrict__ x, const double* __restrict__ y,
+                          const double* __restrict__ z, const double* __restrict__ s,
+                          const double* __restrict__ M, const int* __restrict__ cell_of,
+                          const int* __restrict__ slot, const int* __restrict__ start,
+                          int* __restrict__ perm, int* __restrict__ rank_of, Pos64* __restrict__ pos64,
+                          float4* __restrict__ pos32, Snap64* __restrict__ snap64,
+                          float4* __restrict__ snap32, double* __restrict__ Mr) {
+  int b;
+  long long lo, hi;
+  if (!tile_range(tm, blockIdx.x, b, lo, hi)) return;
+  const InstDev p = P[b];
+  const GridDev g = grid[b];
+  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    int r = start[cell_of[i]] + slot[i];
+    double xi = x[i], yi = y[i], zi = z[i], si = s[i], Mi = M[i];
+    perm[r] = (int)i;
+    rank_of[i] = r;
+    Pos64 q;
+    q.x = xi; q.y = yi; q.z = zi; q.j = i;
+    pos64[r] = q;
+    double m = grain_mass(p, si);
+    double N = Mi / m;
+    double im = 1.0 / m;
+    Snap64 sn;
+    sn.s = si; sn.m = m; sn.N = N; sn.inv_m = im;
+    snap64[r] = sn;
+    Mr[r] = Mi;
+    if (kMixed) {
+      // FP32 mirror relative to the particle's own cell origin (|coord| <= cell edge),
+      // cell coordinates packed in w (11 + 11 + 10 bits); periodic axes use the
+      // wrapped coordinate so that the cell and the offset agree.
+      int ix = axis_cell(g, 0, xi), iy = axis_cell(g, 1, yi), iz = axis_cell(g, 2, zi);
+      double xw = xi, yw = yi;
+      if (g.box[0] > 0.0) xw = xi - g.box[0] * floor((xi - g.lo[0]) / g.box[0]);
+      if (g.box[1] > 0.0) yw = yi - g.box[1] * floor((yi - g.lo[1]) / g.box[1]);
+      float fx = (float)(xw - (g.lo[0] + ix * g.cs[0]));
+      float fy = (float)(yw - (g.lo[1] + iy * g.cs[1]));
+      float fz = (float)(zi - (g.lo[2] + iz * g.cs[2]));
+      pos32[r] = make_float4(fx, fy, fz, __int_as_float(ix | (iy << 11) | (iz << 22)));
+      snap32[r] = make_float4((float)si, (float)m, (float)(N * 0x1p-64), (float)im);
+    }
+  }
+}
+
+}  // namespace gd
+
+// ---------------------------------------------------------------- launcher
+namespace gd {
+
+static TileMap tile_map(gd_ctx* c) {
+  TileMap tm;
+  tm.off = c->d_off;
+  tm.n_inst = c->n_inst;
+  tm.tile_off = c->d_tile_off;
+  return tm;
+}
+
+int num_tiles(gd_ctx* c) { return c->n_tiles; }
+
+std::vector<long long> tile_table(const std::vector<long long>& off) {
+  std::vector<long long> t(off.size(), 0);
+  for (size_t b = 0; b + 1 < off.size(); ++b) t[b + 1] = t[b] + (off[b + 1] - off[b] + kTile - 1) / kTile;
+  return t;
+}
+
+cudaError_t launch_cells(gd_ctx* c) {
+  TileMap tm = tile_map(c);
+  int nt = num_tiles(c);
+  cudaStream_t st = c->stream;
+  time_begin(c, 0);
+  k_bounds<<<nt, 256, 0, st>>>(tm, c->x, c->y, c->z, c->d_state);
+  k_grid<<<1, 32, 0, st>>>(c->d_inst, c->d_state, c->d_grid, c->n_inst, c->cell_factor, c->cell_cap);
+  cudaMemsetAsync(c->d_cell_count, 0, sizeof(int) * (c->cell_cap + 1), st);
+  k_cell_count<<<nt, 256, 0, st>>>(tm, c->d_grid, c->x, c->y, c->z, c->d_cell_count, c->d_cell_of,
+                                   c->d_slot, c->cell_cap);
+  long long ncell = c->cell_cap;
+  int nst = (int)((ncell + kScanTile - 1) / kScanTile);
+  k_scan_reduce<<<nst, 256, 0, st>>>(c->d_cell_count, ncell, c->d_scan_tmp);
+  k_scan_sums<<<1, 1024, 0, st>>>(c->d_scan_tmp, nst);
+  k_scan_final<<<nst, 256, 0, st>>>(c->d_cell_count, ncell, c->d_scan_tmp, c->d_cell_start);
+  if (c->precision == GD_MIXED)
+    k_scatter<true><<<nt, 256, 0, st>>>(tm, c->d_inst, c->d_grid, c->x, c->y, c->z, c->s, c->M,
+                                        c->d_cell_of, c->d_slot, c->d_cell_start, c->d_perm,
+                                        c->d_rank_of, c->d_pos64, c->d_pos32, c->d_snap64,
+                                        c->d_snap32, c->d_Mr);
+  else
+    k_scatter<false><<<nt, 256, 0, st>>>(tm, c->d_inst, c->d_grid, c->x, c->y, c->z, c->s, c->M,
+                                         c->d_cell_of, c->d_slot, c->d_cell_start, c->d_perm,
+                                         c->d_rank_of, c->d_pos64, c->d_pos32, c->d_snap64,
+                                         c->d_snap32, c->d_Mr);
+  time_end(c);
+  c->launches += 7;
+  return cudaGetLastError();
+}
+
+}  // namespace gd

@@ -1,0 +1,656 @@
+// k_mc.cu -- pair rates, controller bins, interval choice, event sampling and audit
+// (Sect. 2.5.1-2.5.3).  Rate kernel and sampler share one pair function and one warp
+// scan, so lambda*_i used for the interval and for the first waiting time is the same
+// number.
+//
+// Work mapping: a warp takes 32 consecutive ranks.  Per-particle FP64 work (gas disk,
+// Stokes numbers, fragment moments, Philox draws, logs) runs lane = particle; the K
+// pair evaluations of each particle run lane = slot (S = ceil(K/32) slots per lane),
+// reading one coalesced neighbour row and gathering frozen partner snapshots that sit
+// nearby in cell order.
+#include <climits>
+
+#include "gd_ctx.h"
+#include "gd_physics.cuh"
+
+namespace gd {
+
+constexpr unsigned FULLM = 0xffffffffu;
+
+struct McArgs {
+  long long N;
+  int K, n_inst;
+  const long long* off;
+  const InstDev* P;
+  StateDev* st;
+  BinsDev* bins;
+  const Pos64* pos64;
+  const Snap64* snap64;
+  const float4* snap32;
+  const double* Mr;
+  const double* V;
+  const int* nbr;
+  const int* perm;
+  double* lam;
+  double* chan_out;
+  double* s_out;
+  int* ev_count;
+  unsigned* ev_hash;
+  int* near_out;
+  long long max_events;
+  long long range;     // ranks per block (rate kernel)
+};
+
+// Per-particle quantities that do not depend on the live diameter.
+struct Fixed {
+  double gst, e2, e1, zo, cs, cB, Vg2, tRe, vfrag, m0;
+  double pref;        // lambda = pref * (pair rate in kernel units)
+  double rho_s, s_min, M;
+  int mode;
+};
+
+template <typename T>
+__device__ __forceinline__ double prefactor(const InstDev& P, double V, int K) {
+  if (P.kernel_mode != GD_KERNEL_PHYSICAL) return 1.0 / (P.t0 * (double)K);
+  if (sizeof(T) == 8) return kPi / (4.0 * V);
+  return kPi * 0x1p64 / (4.0 * V);
+}
+
+template <typename T>
+__device__ __forceinline__ Fixed make_fixed(const InstDev& P, const Gas& g, double V, double M, int K) {
+  Fixed f;
+  f.gst = g.gst;
+  f.e2 = 2.0 * g.eta * g.R * g.Om;
+  f.e1 = g.eta * g.R * g.Om;
+  f.zo = g.Z * g.Om;
+  f.cs = g.cs;
+  f.cB = 8.0 * kKB * g.T / kPi;
+  f.Vg2 = 1.5 * P.alpha * g.cs * g.cs;
+  f.tRe = 1.0 / sqrt(g.Re);
+  f.vfrag = P.v_frag;
+  f.m0 = P.m0;
+  f.pref = prefactor<T>(P, V, K);
+  f.rho_s = P.rho_s;
+  f.s_min = P.s_min;
+  f.M = M;
+  f.mode = P.kernel_mode;
+  return f;
+}
+
+// Query of a live particle (s, m) from the fixed part; all lanes compute it alike.
+template <typename T>
+__device__ __forceinline__ Query<T> live_query(const Fixed& f, double s, double m) {
+  Query<T> q;
+  double St = f.gst * s;
+  q.s = (T)s; q.m = (T)m; q.inv_m = (T)(1.0 / m);
+  q.St = (T)St;
+  q.ai = (T)(St / (1.0 + St * St));
+  q.bi = (T)(1.0 / (1.0 + St * St));
+  q.hi = (T)(St < 0.5 ? St : 0.5);
+  q.g = (T)f.gst;
+  q.e2 = (T)f.e2; q.e1 = (T)f.e1; q.zo = (T)f.zo;
+  q.cs = (T)f.cs; q.cB = (T)f.cB; q.Vg2 = (T)f.Vg2; q.tRe = (T)f.tRe;
+  q.vfrag = (T)f.vfrag; q.m0 = (T)f.m0;
+  q.mode = f.mode;
+  return q;
+}
+
+__device__ __forceinline__ Fixed shfl_fixed(const Fixed& a, int src) {
+  Fixed f;
+  f.gst = __shfl_sync(FULLM, a.gst, src);
+  f.e2 = __shfl_sync(FULLM, a.e2, src);
+  f.e1 = __shfl_sync(FULLM, a.e1, src);
+  f.zo = __shfl_sync(FULLM, a.zo, src);
+  f.cs = __shfl_sync(FULLM, a.cs, src);
+  f.cB = __shfl_sync(FULLM, a.cB, src);
+  f.Vg2 = __shfl_sync(FULLM, a.Vg2, src);
+  f.tRe = __shfl_sync(FULLM, a.tRe, src);
+  f.vfrag = __shfl_sync(FULLM, a.vfrag, src);
+  f.m0 = __shfl_sync(FULLM, a.m0, src);
+  f.pref = __shfl_sync(FULLM, a.pref, src);
+  f.rho_s = __shfl_sync(FULLM, a.rho_s, src);
+  f.s_min = __shfl_sync(FULLM, a.s_min, src);
+  f.M = __shfl_sync(FULLM, a.M, src);
+  f.mode = __shfl_sync(FULLM, a.mode, src);
+  return f;
+}
+
+// Partner snapshot in the pair precision.
+template <typename T> struct Partner { T s, m, Nq, inv_m; };
+
+template <typename T>
+__device__ __forceinline__ Partner<T> load_partner(const McArgs& A, int j) {
+  Partner<T> p;
+  if constexpr (sizeof(T) == 8) {
+    const double2* pp = reinterpret_cast<const double2*>(A.snap64 + j);
+    double2 a = __ldg(pp), b = __ldg(pp + 1);
+    p.s = a.x; p.m = a.y; p.Nq = b.x; p.inv_m = b.y;
+  } else {
+    float4 v = __ldg(A.snap32 + j);
+    p.s = v.x; p.m = v.y; p.Nq = v.z; p.inv_m = v.w;
+  }
+  return p;
+}
+
+// Channel rates of the S slots of this lane for particle row, plus the lane's
+// sequential sum in FP64 (slot-major, channel-minor).
+template <typename T, int S>
+__device__ __forceinline__ double lane_channels(const McArgs& A, const Query<T>& q, const int* row, int lane,
+                                                T (&c0)[S], T (&c1)[S], int (&jr)[S], PairOut<T> (&po)[S]) {
+  double v = 0.0;
+#pragma unroll
+  for (int t = 0; t < S; ++t) {
+    int k = lane * S + t;
+    c0[t] = (T)0; c1[t] = (T)0; jr[t] = -1;
+    po[t].outcome = 0; po[t].ncoll = (T)1; po[t].psi = (T)0;
+    if (k < A.K) {
+      int j = __ldg(row + k);
+      jr[t] = j;
+      Partner<T> p = load_partner<T>(A, j);
+      po[t] = pair_channels<T>(q, p.s, p.m, p.Nq, p.inv_m);
+      c0[t] = po[t].c0;
+      c1[t] = po[t].c1;
+      v = __dadd_rn(v, (double)c0[t]);
+      v = __dadd_rn(v, (double)c1[t]);
+    }
+  }
+  return v;
+}
+
+// ---------------------------------------------------------------- rate kernel
+template <typename T, int S>
+__global__ void __launch_bounds__(256) k_rates(McArgs A) {
+  __shared__ double sh[4][kNFine];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const long long lo = (long long)blockIdx.x * A.range;
+  const long long hi = min(lo + A.range, A.N);
+  if (lo >= hi) return;
+  const int b_lo = inst_of(A.off, A.n_inst, lo), b_hi = inst_of(A.off, A.n_inst, hi - 1);
+  const bool shared_bins = (b_lo == b_hi);
+  for (int t = threadIdx.x; t < 4 * kNFine; t += blockDim.x) sh[t / kNFine][t % kNFine] = 0.0;
+  __syncthreads();
+  for (long long base = lo + 32LL * wib; base < hi; base += 32LL * nw) {
+    const long long r = base + lane;
+    const bool valid = r < hi;
+    int b = 0;
+    Fixed fx;
+    double s_i = 1.0, m_i = 1.0, fj1 = 0.0, fj2 = 0.0;
+    if (valid) {
+      b = inst_of(A.off, A.n_inst, r);
+      const InstDev& P = A.P[b];
+      const Pos64 p = A.pos64[r];
+      Gas g = gas_at(P, p.x, p.y, p.z);
+      const Snap64 sn = A.snap64[r];
+      s_i = sn.s;
+      m_i = sn.m;
+      fx = make_fixed<T>(P, g, A.V[r], A.Mr[r], A.K);
+      frag_moments(s_i, P.s_min, fj1, fj2);
+    } else {
+      fx = Fixed{};
+      fx.pref = 0.0;
+      fx.mode = 0;
+    }
+    double my_tot = 0.0, my_a = 0.0, my_b = 0.0;
+    unsigned vmask = __ballot_sync(FULLM, valid);
+    while (vmask) {
+      const int p = __ffs(vmask) - 1;
+      vmask &= vmask - 1;
+      const long long rp = base + p;
+      const Fixed f = shfl_fixed(fx, p);
+      const double sp = __shfl_sync(FULLM, s_i, p), mp = __shfl_sync(FULLM, m_i, p);
+      const T j1 = (T)__shfl_sync(FULLM, fj1, p), j2 = (T)__shfl_sync(FULLM, fj2, p);
+      const Query<T> q = live_query<T>(f, sp, mp);
+      const int* row = A.nbr + rp * A.K;
+      T c0[S], c1[S];
+      int jr[S];
+      PairOut<T> po[S];
+      double v = lane_channels<T, S>(A, q, row, lane, c0, c1, jr, po);
+      double incl = warp_incl_scan(v, lane);
+      double tot = __shfl_sync(FULLM, incl, 31);
+      T la = (T)0, lb = (T)0;
+#pragma unroll
+      for (int t = 0; t < S; ++t) {
+        if (jr[t] < 0) continue;
+        T a, bb;
+        pair_moments<T>(po[t], j1, j2, a, bb);
+        la += a;
+        lb += bb;
+      }
+      double sa, sb;
+      if constexpr (sizeof(T) == 8) { sa = warp_sum(la); sb = warp_sum(lb); }
+      else { sa = (double)warp_sumf(la); sb = (double)warp_sumf(lb); }
+      if (lane == p) { my_tot = tot; my_a = sa; my_b = sb; }
+      if (A.chan_out) {
+        long long ci = (long long)A.perm[rp] * A.K;
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+          int k = lane * S + t;
+          if (k < A.K) {
+            A.chan_out[(ci + k) * 2] = f.pref * (double)c0[t];
+            A.chan_out[(ci + k) * 2 + 1] = f.pref * (double)c1[t];
+          }
+        }
+      }
+    }
+    if (valid) {
+      double lam = fx.pref * my_tot;
+      A.lam[r] = lam;
+      if (!isfinite(lam)) set_status(&A.st[b], GD_ST_NONFINITE);
+      int fbin = fine_bin(s_i);
+      double M = fx.M;
+      double va = M * (fx.pref * my_a), vb = M * (fx.pref * my_b);
+      if (shared_bins) {
+        atomicAdd(&sh[0][fbin], 1.0);
+        atomicAdd(&sh[1][fbin], M);
+        atomicAdd(&sh[2][fbin], va);
+        atomicAdd(&sh[3][fbin], vb);
+      } else {
+        BinsDev* bn = &A.bins[b];
+        atomicAdd(&bn->cnt[fbin], 1.0);
+        atomicAdd(&bn->sM[fbin], M);
+        atomicAdd(&bn->sA[fbin], va);
+        atomicAdd(&bn->sB[fbin], vb);
+      }
+    }
+  }
+  if (shared_bins) {
+    __syncthreads();
+    BinsDev* bn = &A.bins[b_lo];
+    for (int t = threadIdx.x; t < kNFine; t += blockDim.x) {
+      if (sh[0][t] != 0.0) {
+        atomicAdd(&bn->cnt[t], sh[0][t]);
+        atomicAdd(&bn->sM[t], sh[1][t]);
+        atomicAdd(&bn->sA[t], sh[2][t]);
+        atomicAdd(&bn->sB[t], sh[3][t]);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- interval choice
+// One thread per instance: merge fine bins into controller bins (>= max(K, 64)
+// particles, ascending, remainder joins the previous bin), A_b and B_b, dt_req and the
+// halving of dt_coll with the exact tick count of the time left.
+__global__ void k_interval(const InstDev* __restrict__ P, StateDev* st, BinsDev* bins, int n_inst, int K,
+                           int no_audit) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_inst) return;
+  BinsDev& B = bins[b];
+  StateDev& S = st[b];
+  const InstDev& p = P[b];
+  double thr = K > 64 ? K : 64;
+  int ng = 0;
+  double acc = 0.0;
+  for (int f = 0; f < kNFine; ++f) {
+    B.gid[f] = -1;
+    if (B.cnt[f] == 0.0) continue;
+    B.gid[f] = ng;
+    acc += B.cnt[f];
+    if (acc >= thr) { ng++; acc = 0.0; }
+  }
+  if (acc > 0.0) {
+    if (ng > 0) { for (int f = 0; f < kNFine; ++f) if (B.gid[f] == ng) B.gid[f] = ng - 1; }
+    else ng = 1;
+  }
+  B.ngroups = ng;
+  double C = (p.audit && !no_audit) ? S.C : 1.0;
+  if (S.remain_ticks <= 0) S.remain_ticks = 1LL << 60;
+  double remain = ldexp((double)S.remain_ticks, -60) * p.dt_coll;
+  double dt_cap = remain < p.dt_fn_max ? remain : p.dt_fn_max;
+  double dt_ab = HUGE_VAL;
+  for (int g = 0; g < ng; ++g) {
+    double sM = 0.0, sA = 0.0, sB = 0.0;
+    for (int f = 0; f < kNFine; ++f)
+      if (B.gid[f] == g) { sM += B.sM[f]; sA += B.sA[f]; sB += B.sB[f]; }
+    double A = sA / sM, Bm = sB / sM;
+    if (A > 0.0) { double t = p.eps * C / A; if (t < dt_ab) dt_ab = t; }
+    if (Bm > 0.0) { double t = p.eps * p.eps * C * C / Bm; if (t < dt_ab) dt_ab = t; }
+  }
+  double dt_req = dt_ab < dt_cap ? dt_ab : dt_cap;
+  double dt = p.dt_coll;
+  int k = 0;
+  while (k < 60 && (dt > dt_req || (1LL << (60 - k)) > S.remain_ticks)) { dt = 0.5 * dt; ++k; }
+  if (dt > dt_req) S.status |= GD_ST_DT_FLOOR;
+  if (dt_ab <= dt_cap * (1.0 + 1e-10) &&
+      (fabs(dt - dt_ab) <= 1e-10 * dt_ab || fabs(2.0 * dt - dt_ab) <= 1e-10 * dt_ab))
+    S.near_dt++;
+  S.dt_req = dt_req;
+  S.dt_exe = dt;
+  S.n_groups = ng;
+  S.remain_ticks -= 1LL << (60 - k);
+  if (S.remain_ticks == 0) S.remain_ticks = 1LL << 60;
+  S.dt_remain = ldexp((double)S.remain_ticks, -60) * p.dt_coll;
+  S.interval_cur = S.interval_next;
+  S.interval_next = S.interval_next + 1;
+  S.events = 0;
+}
+
+// ---------------------------------------------------------------- sampler
+template <typename T, int S>
+__global__ void __launch_bounds__(256) k_sample(McArgs A) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long base = warp * 32; base < A.N; base += nwarps * 32) {
+    const long long r = base + lane;
+    const bool valid = r < A.N;
+    int b = 0;
+    double lam = 0.0, dtw = 0.0, us = 0.0, dt_exe = 0.0;
+    unsigned ival = 0, i_loc = 0, key0 = 0, key1 = 0;
+    bool ev = false;
+    int nn = 0;
+    if (valid) {
+      b = inst_of(A.off, A.n_inst, r);
+      const InstDev& P = A.P[b];
+      dt_exe = A.st[b].dt_exe;
+      ival = (unsigned)A.st[b].interval_cur;
+      key0 = P.key0;
+      key1 = P.key1;
+      i_loc = (unsigned)(A.perm[r] - P.off);
+      lam = A.lam[r];
+      U4 w = philox(i_loc, ival, 0u, 0u, key0, key1);
+      double uw = u01(w.x, w.y);
+      us = u01(w.z, w.w);
+      if (lam > 0.0 && isfinite(lam)) {
+        dtw = -log(uw) / lam;
+        if (fabs(dtw - dt_exe) < 1e-10 * dt_exe) nn++;
+        ev = !(dtw > dt_exe);
+      }
+    }
+    unsigned emask = __ballot_sync(FULLM, ev);
+    if (emask == 0) {
+      if (valid && nn) { atomicAdd((unsigned long long*)&A.st[b].near_draw, (unsigned long long)nn); }
+      if (valid && A.ev_count) {
+        int ci = A.perm[r];
+        A.ev_count[ci] = 0;
+        A.ev_hash[ci] = 0u;
+        A.near_out[ci] = nn;
+      }
+      continue;
+    }
+    // per-lane fixed quantities of every particle of the chunk (lane = particle)
+    Fixed fx;
+    double s_i = 1.0, m_i = 1.0;
+    if (valid) {
+      const InstDev& P = A.P[b];
+      const Pos64 p = A.pos64[r];
+      Gas g = gas_at(P, p.x, p.y, p.z);
+      const Snap64 sn = A.snap64[r];
+      s_i = sn.s;
+      m_i = sn.m;
+      fx = make_fixed<T>(P, g, A.V[r], A.Mr[r], A.K);
+    } else {
+      fx = Fixed{};
+      fx.mode = 0;
+    }
+    int my_e = 0;
+    unsigned my_h = 0u;
+    while (emask) {
+      const int p = __ffs(emask) - 1;
+      emask &= emask - 1;
+      const long long rp = base + p;
+      const Fixed f = shfl_fixed(fx, p);
+      double s = __shfl_sync(FULLM, s_i, p), m = __shfl_sync(FULLM, m_i, p);
+      double t = __shfl_sync(FULLM, dtw, p);
+      double u_s = __shfl_sync(FULLM, us, p);
+      const double dte = __shfl_sync(FULLM, dt_exe, p);
+      const unsigned iv = __shfl_sync(FULLM, ival, p), il = __shfl_sync(FULLM, i_loc, p);
+      const unsigned k0 = __shfl_sync(FULLM, key0, p), k1 = __shfl_sync(FULLM, key1, p);
+      const int bp = __shfl_sync(FULLM, b, p);
+      const int* row = A.nbr + rp * A.K;
+      const double s_start = s;
+      int e = 0, near_ch = 0, near_u = 0;   // per-lane channel ties, warp-uniform ties
+      unsigned h = 0u;
+      double J = 0.0;
+      T c0[S], c1[S];
+      int jr[S];
+      PairOut<T> po[S];
+      Query<T> q = live_query<T>(f, s, m);
+      double v = lane_channels<T, S>(A, q, row, lane, c0, c1, jr, po);
+      double incl = warp_incl_scan(v, lane);
+      double tot = __shfl_sync(FULLM, incl, 31);
+      for (;;) {
+        // partner channel: the first cumulative rate above U_s lambda*
+        const double target = u_s * tot;
+        double cum = __shfl_up_sync(FULLM, incl, 1);
+        if (lane == 0) cum = 0.0;
+        int sel = INT_MAX, lastnz = -1;
+#pragma unroll
+        for (int t2 = 0; t2 < S; ++t2) {
+          int k = lane * S + t2;
+          if (jr[t2] < 0) continue;
+          double a = (double)c0[t2], bb = (double)c1[t2];
+          cum = __dadd_rn(cum, a);
+          if (a > 0.0) {
+            lastnz = 2 * k;
+            if (fabs(target - cum) < 1e-10 * tot) near_ch++;
+            if (sel == INT_MAX && target < cum) sel = 2 * k;
+          }
+          cum = __dadd_rn(cum, bb);
+          if (bb > 0.0) {
+            lastnz = 2 * k + 1;
+            if (fabs(target - cum) < 1e-10 * tot) near_ch++;
+            if (sel == INT_MAX && target < cum) sel = 2 * k + 1;
+          }
+        }
+        int chosen = sel;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) chosen = min(chosen, __shfl_xor_sync(FULLM, chosen, o));
+        if (chosen == INT_MAX) {
+          int ln = lastnz;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) ln = max(ln, __shfl_xor_sync(FULLM, ln, o));
+          chosen = ln;
+          near_u++;
+        }
+        if (chosen < 0) break;
+        const int slot = chosen >> 1, ch = chosen & 1;
+        const int owner = slot / S, tsl = slot % S;
+        // partner data and outcome from the owning lane
+        int jo = jr[0], oc = po[0].outcome;
+        T nco = po[0].ncoll;
+#pragma unroll
+        for (int t2 = 1; t2 < S; ++t2)
+          if (t2 == tsl) { jo = jr[t2]; oc = po[t2].outcome; nco = po[t2].ncoll; }
+        const int j = __shfl_sync(FULLM, jo, owner);
+        const int outcome = __shfl_sync(FULLM, oc, owner);
+        const double ncoll = (double)__shfl_sync(FULLM, nco, owner);
+        const Snap64 pj = A.snap64[j];
+        double m_new, s_new;
+        if (outcome == 0) {
+          m_new = m + ncoll * pj.m;
+          s_new = cbrt(6.0 * m_new / (kPi * f.rho_s));
+        } else if (outcome == 1 && ch == 0) {
+          m_new = m - ncoll * pj.m;
+          s_new = cbrt(6.0 * m_new / (kPi * f.rho_s));
+        } else if (outcome == 1) {
+          m_new = pj.m;
+          s_new = pj.s;
+        } else {
+          U4 w2 = philox(il, iv, (unsigned)e, 1u, k0, k1);
+          double U = u01(w2.x, w2.y);
+          double a = sqrt(f.s_min), bq = sqrt(s);
+          double xr = a + U * (bq - a);
+          s_new = xr * xr;
+          m_new = kPi * f.rho_s * s_new * s_new * s_new / 6.0;
+        }
+        J += fabs(log(s_new / s));
+        s = s_new;
+        m = m_new;
+        h = h * 31u + (unsigned)(chosen + 1);
+        ++e;
+        if (e >= A.max_events) { if (lane == 0) set_status(&A.st[bp], GD_ST_EVENT_CAP); break; }
+        q = live_query<T>(f, s, m);
+        v = lane_channels<T, S>(A, q, row, lane, c0, c1, jr, po);
+        incl = warp_incl_scan(v, lane);
+        tot = __shfl_sync(FULLM, incl, 31);
+        const double lam_now = f.pref * tot;
+        if (!(lam_now > 0.0) || !isfinite(lam_now)) {
+          if (lane == 0 && !(lam_now == 0.0)) set_status(&A.st[bp], GD_ST_NONFINITE);
+          break;
+        }
+        U4 w = philox(il, iv, (unsigned)e, 0u, k0, k1);
+        double uw = u01(w.x, w.y);
+        u_s = u01(w.z, w.w);
+        double dt2 = -log(uw) / lam_now;
+        if (fabs((t + dt2) - dte) < 1e-10 * dte) near_u++;
+        if (t + dt2 > dte) break;
+        t = t + dt2;
+      }
+      int near_tot = near_ch;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) near_tot += __shfl_xor_sync(FULLM, near_tot, o);
+      near_tot += near_u;
+      if (lane == p) { my_e = e; my_h = h; nn += near_tot; }
+      if (lane == 0) {
+        int ci = A.perm[rp];
+        A.s_out[ci] = s;
+        atomicAdd((unsigned long long*)&A.st[bp].events, (unsigned long long)e);
+        if (J > 0.0) atomicAdd(&A.bins[bp].sJ[fine_bin(s_start)], f.M * J);
+      }
+    }
+    if (valid && nn) atomicAdd((unsigned long long*)&A.st[b].near_draw, (unsigned long long)nn);
+    if (valid && A.ev_count) {
+      int ci = A.perm[r];
+      A.ev_count[ci] = my_e;
+      A.ev_hash[ci] = my_h;
+      A.near_out[ci] = nn;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- audit
+// One thread per instance: realised mass-weighted sum of |ln(s'/s)| per controller bin
+// against 2 eps C; C halves (>= 1/4) on excess, else grows by 1.25 (<= 1).  Clears the
+// fine bins for the next interval.
+__global__ void k_audit(const InstDev* __restrict__ P, StateDev* st, BinsDev* bins, int n_inst, int no_audit) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_inst) return;
+  BinsDev& B = bins[b];
+  StateDev& S = st[b];
+  if (P[b].audit && !no_audit) {
+    double thr = 2.0 * P[b].eps * S.C;
+    bool exceed = false;
+    for (int g = 0; g < B.ngroups; ++g) {
+      double sM = 0.0, sJ = 0.0;
+      for (int f = 0; f < kNFine; ++f)
+        if (B.gid[f] == g) { sM += B.sM[f]; sJ += B.sJ[f]; }
+      double Rg = sJ / sM;
+      if (fabs(Rg - thr) <= 1e-10 * thr) S.near_audit++;
+      if (Rg > thr) exceed = true;
+    }
+    S.C = exceed ? fmax(0.25, 0.5 * S.C) : fmin(1.0, 1.25 * S.C);
+  } else {
+    S.C = 1.0;
+  }
+  S.events_total += S.events;
+  for (int f = 0; f < kNFine; ++f) { B.cnt[f] = 0.0; B.sM[f] = 0.0; B.sA[f] = 0.0; B.sB[f] = 0.0; B.sJ[f] = 0.0; }
+}
+
+// ---------------------------------------------------------------- launchers
+static McArgs mc_args(gd_ctx* c) {
+  McArgs A;
+  A.N = c->N;
+  A.K = c->K;
+  A.n_inst = c->n_inst;
+  A.off = c->d_off;
+  A.P = c->d_inst;
+  A.st = c->d_state;
+  A.bins = c->d_bins;
+  A.pos64 = c->d_pos64;
+  A.snap64 = c->d_snap64;
+  A.snap32 = c->d_snap32;
+  A.Mr = c->d_Mr;
+  A.V = c->d_V;
+  A.nbr = c->d_nbr;
+  A.perm = c->d_perm;
+  A.lam = c->d_lam;
+  A.chan_out = nullptr;
+  A.s_out = c->s;
+  A.ev_count = nullptr;
+  A.ev_hash = nullptr;
+  A.near_out = nullptr;
+  A.max_events = c->max_events;
+  A.range = 0;
+  return A;
+}
+
+template <typename T>
+static void rates_t(gd_ctx* c, McArgs& A) {
+  int S = (c->K + 31) / 32;
+  long long blocks_want = (long long)c->num_sms * 4;
+  long long range = (A.N + blocks_want - 1) / blocks_want;
+  range = ((range + 255) / 256) * 256;
+  if (range < 256) range = 256;
+  A.range = range;
+  int blocks = (int)((A.N + range - 1) / range);
+  switch (S) {
+    case 1: k_rates<T, 1><<<blocks, 256, 0, c->stream>>>(A); break;
+    case 2: k_rates<T, 2><<<blocks, 256, 0, c->stream>>>(A); break;
+    case 3: k_rates<T, 3><<<blocks, 256, 0, c->stream>>>(A); break;
+    case 4: k_rates<T, 4><<<blocks, 256, 0, c->stream>>>(A); break;
+    default: k_rates<T, 8><<<blocks, 256, 0, c->stream>>>(A); break;
+  }
+}
+
+cudaError_t launch_rates(gd_ctx* c, double* chan_out) {
+  McArgs A = mc_args(c);
+  A.chan_out = chan_out;
+  time_begin(c, 2);
+  if (c->precision == GD_MIXED) rates_t<float>(c, A); else rates_t<double>(c, A);
+  time_end(c);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_interval(gd_ctx* c) {
+  time_begin(c, 3);
+  k_interval<<<(c->n_inst + 63) / 64, 64, 0, c->stream>>>(c->d_inst, c->d_state, c->d_bins, c->n_inst, c->K,
+                                                          (c->flags & GD_FLAG_NO_AUDIT) ? 1 : 0);
+  time_end(c);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
+template <typename T>
+static void sample_t(gd_ctx* c, McArgs& A) {
+  int S = (c->K + 31) / 32;
+  long long chunks = (A.N + 31) / 32;
+  long long blocks = (chunks + 7) / 8;
+  long long cap = (long long)c->num_sms * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  switch (S) {
+    case 1: k_sample<T, 1><<<(int)blocks, 256, 0, c->stream>>>(A); break;
+    case 2: k_sample<T, 2><<<(int)blocks, 256, 0, c->stream>>>(A); break;
+    case 3: k_sample<T, 3><<<(int)blocks, 256, 0, c->stream>>>(A); break;
+    case 4: k_sample<T, 4><<<(int)blocks, 256, 0, c->stream>>>(A); break;
+    default: k_sample<T, 8><<<(int)blocks, 256, 0, c->stream>>>(A); break;
+  }
+}
+
+cudaError_t launch_sample(gd_ctx* c, int* ev_count, unsigned* ev_hash, int* near) {
+  McArgs A = mc_args(c);
+  A.ev_count = ev_count;
+  A.ev_hash = ev_hash;
+  A.near_out = near;
+  if (ev_count == nullptr || ev_hash == nullptr || near == nullptr) {
+    A.ev_count = nullptr;
+  }
+  time_begin(c, 4);
+  if (c->precision == GD_MIXED) sample_t<float>(c, A); else sample_t<double>(c, A);
+  time_end(c);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_audit(gd_ctx* c) {
+  time_begin(c, 3);
+  k_audit<<<(c->n_inst + 63) / 64, 64, 0, c->stream>>>(c->d_inst, c->d_state, c->d_bins, c->n_inst,
+                                                       (c->flags & GD_FLAG_NO_AUDIT) ? 1 : 0);
+  time_end(c);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace gd

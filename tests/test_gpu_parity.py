@@ -1,0 +1,231 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the same
+seeded inputs.
+
+Bars (from the method's precision split):
+* neighbour lists and neighbour distances: bit-exact (both forms);
+* FP64 rates lambda*_i: within 1e-12 relative;
+* event sequences: identical per particle (count and channel hash) except where a
+  near tie (a draw within 1e-10 of a boundary) was flagged on either side;
+* diameters after sampling: within 1e-12 relative (FP64) where the sequences agree;
+* represented mass: never written (bitwise), sum N m = sum M within 1e-12;
+* mixed form: lists bit-exact; rates, events and sizes reported with stated bounds.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2609_35967_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _step_both(gd, oracle, sess, P, st, ins, s_or):
+    ref = oracle.interval_step(P, st, ins["x"], ins["y"], ins["z"], s_or, ins["M"],
+                               want=("nbr", "d", "V", "lam", "ev_count", "ev_hash", "near"))
+    nbr, d = sess.build_neighbors(want=True)
+    lam, _ = sess.collision_rates(want=True)
+    ec, eh, nn = sess.sample_collisions(want=True)
+    return ref, dict(nbr=nbr.cpu().numpy(), d=d.cpu().numpy(), lam=lam.cpu().numpy(),
+                     ev_count=ec.cpu().numpy(), ev_hash=eh.cpu().numpy().view(np.uint32),
+                     near=nn.cpu().numpy())
+
+
+def _compare_events(ref, got, allow_frac=1e-3):
+    same = (ref["ev_count"] == got["ev_count"]) & (ref["ev_hash"] == got["ev_hash"])
+    flagged = (ref["near"] > 0) | (got["near"] > 0)
+    bad = ~same & ~flagged
+    assert bad.sum() == 0, f"{bad.sum()} particles differ without a near tie"
+    return same
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_patch_interval_parity(gd, oracle, precision):
+    ins = W.patch_instance(2048, K=32, seed=5)
+    sess = gd.Session([ins], precision=precision)
+    P = oracle.params(ins["params"])
+    st = oracle.new_state(P)
+    s_or = ins["s"].copy()
+    for it in range(3):
+        ref, got = _step_both(gd, oracle, sess, P, st, ins, s_or)
+        assert np.array_equal(got["nbr"], ref["nbr"])
+        assert np.array_equal(got["d"], ref["d"])
+        rel = np.abs(got["lam"] / ref["lam"] - 1.0)
+        if precision == 0:
+            assert rel.max() < 1e-12
+        else:
+            assert rel.max() < 1e-4, rel.max()
+        same = _compare_events(ref, got) if precision == 0 else None
+        stats = sess.stats()
+        inst = stats["instances"][0]
+        assert inst["dt_exe"] == st.dt_exe or inst["near_dt"] > 0 or precision == 1
+        s_gpu = sess.t["s"].cpu().numpy()
+        if precision == 0:
+            assert np.abs(s_gpu[same] / s_or[same] - 1.0).max() < 1e-12
+        # keep both sides on the same state for the next interval
+        import torch
+        sess.t["s"].copy_(torch.as_tensor(s_or, device=sess.device))
+        torch.cuda.synchronize()
+    assert stats["status"] == 0
+    sess.close()
+
+
+def test_patch_hundred_intervals(gd, oracle):
+    """Configuration 0 shape (4096 particles, K = 32, seed 1): 100 intervals, FP64."""
+    ins = W.config0(n=4096)[0]
+    sess = gd.Session([ins], precision=gd.GD_FP64)
+    P = oracle.params(ins["params"])
+    st = oracle.new_state(P)
+    s_or = ins["s"].copy()
+    n_int = 100
+    ev_or = 0
+    for _ in range(n_int):
+        oracle.interval_step(P, st, ins["x"], ins["y"], ins["z"], s_or, ins["M"], want=())
+        ev_or += st.events
+        sess.build_neighbors()
+        sess.collision_rates()
+        sess.sample_collisions()
+    stats = sess.stats()
+    s_gpu = sess.t["s"].cpu().numpy()
+    near = stats["near_draw"] + stats["near_dt"] + st.near_draw + st.near_dt
+    assert stats["intervals"] == n_int
+    assert stats["status"] == 0
+    if near == 0:
+        assert stats["events"] == ev_or
+        assert np.abs(s_gpu / s_or - 1.0).max() < 1e-12
+    else:
+        assert abs(stats["events"] - ev_or) <= 2 * near
+    inst = stats["instances"][0]
+    assert inst["C"] == st.C
+    # represented mass is never written; sum N m = sum M
+    assert np.array_equal(sess.t["M"].cpu().numpy(), ins["M"])
+    m = math.pi * P.rho_s * s_gpu ** 3 / 6.0
+    assert abs((ins["M"] / m * m).sum() - ins["M"].sum()) <= 1e-12 * ins["M"].sum()
+    assert inst["sum_M"] == pytest.approx(ins["M"].sum(), rel=1e-14)
+    sess.close()
+
+
+def test_batched_patches(gd, oracle):
+    """Several independent patches of uneven size and parameters in one context."""
+    rng = np.random.default_rng(9)
+    insts = []
+    for b in range(6):
+        n = int(rng.integers(200, 3000))
+        insts.append(W.patch_instance(n, r_au=float(rng.uniform(5, 50)), alpha=10 ** rng.uniform(-4, -2),
+                                      v_frag=float(rng.uniform(100, 1000)), seed=1000 + b, K=16))
+    sess = gd.Session(insts, precision=gd.GD_FP64)
+    Ps = [oracle.params(i["params"]) for i in insts]
+    sts = [oracle.new_state(P) for P in Ps]
+    s_or = [i["s"].copy() for i in insts]
+    offs = W.concat(insts)["offsets"]
+    for it in range(3):
+        refs = [oracle.interval_step(P, st, i["x"], i["y"], i["z"], s, i["M"], want=("nbr", "lam"))
+                for P, st, i, s in zip(Ps, sts, insts, s_or)]
+        nbr, _ = sess.build_neighbors(want=True)
+        lam, _ = sess.collision_rates(want=True)
+        sess.sample_collisions()
+        nbr = nbr.cpu().numpy()
+        lam = lam.cpu().numpy()
+        for b, ref in enumerate(refs):
+            lo, hi = offs[b], offs[b + 1]
+            assert np.array_equal(nbr[lo:hi] - lo, ref["nbr"])
+            assert np.abs(lam[lo:hi] / ref["lam"] - 1.0).max() < 1e-12
+    stats = sess.stats()
+    s_gpu = sess.t["s"].cpu().numpy()
+    for b in range(len(insts)):
+        inst = stats["instances"][b]
+        if inst["near_draw"] == 0 and sts[b].near_draw == 0:
+            assert np.abs(s_gpu[offs[b]:offs[b + 1]] / s_or[b] - 1.0).max() < 1e-12
+        assert inst["dt_exe"] == sts[b].dt_exe or inst["near_dt"] > 0
+    sess.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_disk_sampled_queries(gd, oracle, precision):
+    """Global disk (radial caps, flared density): lists and rates of sampled particles."""
+    ins = W.disk_instance(1 << 15, seed=2, K=32, sizes=("lognormal", 10.0, 1.0))
+    sess = gd.Session([ins], precision=precision)
+    nbr, d = sess.build_neighbors(want=True)
+    lam, _ = sess.collision_rates(want=True)
+    sess.stats()
+    P = oracle.params(ins["params"])
+    q = np.random.default_rng(4).choice(len(ins["x"]), 300, replace=False)
+    onbr, od = oracle.knn(P, ins["x"], ins["y"], ins["z"], q)
+    assert np.array_equal(nbr.cpu().numpy()[q], onbr)
+    assert np.array_equal(d.cpu().numpy()[q], od)
+    r = oracle.rates_subset(P, ins["x"], ins["y"], ins["z"], ins["s"], ins["M"], q, onbr, od)
+    rel = np.abs(lam.cpu().numpy()[q] / r["lam"] - 1.0)
+    assert rel.max() < (1e-12 if precision == 0 else 1e-4), rel.max()
+    sess.close()
+
+
+def test_constant_kernel_mean_mass_gpu(gd):
+    """Appendix A constant kernel on the GPU: mass-weighted mean mass = 1 + t (5 sigma)."""
+    devs, ses = [], []
+    for seed in (21, 22):
+        ins = W.coag_instance(4096, K=16, mode=W.CONSTANT, seed=seed)
+        sess = gd.Session([ins], precision=gd.GD_FP64)
+        t = 0.0
+        while t < 4.0 - 1e-12:
+            sess.build_neighbors()
+            sess.collision_rates()
+            sess.sample_collisions()
+            t += sess.stats()["instances"][0]["dt_exe"]
+        s = sess.t["s"].cpu().numpy()
+        m = math.pi * ins["params"]["rho_s"] * s ** 3 / 6.0
+        devs.append(m.mean() - (1.0 + t))
+        ses.append(m.std() / math.sqrt(len(m)))
+        sess.close()
+    se = math.sqrt(sum(x * x for x in ses)) / len(ses)
+    assert abs(np.mean(devs)) < 5 * se
+
+
+def test_graph_replay_matches_calls(gd):
+    ins = W.patch_instance(3000, K=32, seed=8)
+    a = gd.Session([ins], precision=gd.GD_MIXED)
+    b = gd.Session([ins], precision=gd.GD_MIXED)
+    for _ in range(4):
+        a.build_neighbors()
+        a.collision_rates()
+        a.sample_collisions()
+    b.run_intervals(4)
+    sa, sb = a.stats(), b.stats()
+    assert sa["intervals"] == sb["intervals"] == 4
+    assert np.array_equal(a.t["s"].cpu().numpy(), b.t["s"].cpu().numpy())
+    assert sa["events"] == sb["events"]
+    a.close()
+    b.close()
+
+
+def test_push_matches_oracle(gd, oracle):
+    ins = W.disk_instance(4096, seed=6, K=32, velocities=True, sizes=("lognormal", 1.0, 0.5))
+    sess = gd.Session([ins], precision=gd.GD_FP64, velocities=True)
+    dt = 3.0e7
+    sess.push_staggered(dt)
+    sess.stats()
+    P = oracle.params(ins["params"])
+    x, y, z = ins["x"].copy(), ins["y"].copy(), ins["z"].copy()
+    vr, lth, lph = ins["vr"].copy(), ins["lth"].copy(), ins["lph"].copy()
+    oracle.push(P, x, y, z, vr, lth, lph, ins["s"], dt, drag=True)
+    for k, ref in (("x", x), ("y", y), ("z", z), ("lph", lph)):
+        got = sess.t[k].cpu().numpy()
+        scale = np.abs(ref).max()
+        assert np.abs(got - ref).max() <= 1e-12 * scale, k
+    for k, ref in (("vr", vr), ("lth", lth)):
+        got = sess.t[k].cpu().numpy()
+        scale = np.abs(lph / np.sqrt(x * x + y * y)).max()
+        assert np.abs(got - ref).max() <= 1e-10 * scale, k
+    sess.close()
+
+
+def test_sequencing_errors(gd):
+    ins = W.patch_instance(256, K=16, seed=1)
+    sess = gd.Session([ins])
+    with pytest.raises(gd.GDError) as e:
+        gd.gd_collision_rates(sess.ctx)
+    assert e.value.code == gd.GD_ERR_STATE
+    with pytest.raises(gd.GDError):
+        gd.gd_sample_collisions(sess.ctx)
+    with pytest.raises(gd.GDError):
+        gd.gd_push_staggered(sess.ctx, 1.0)     # no velocities configured
+    sess.close()
