@@ -1,0 +1,346 @@
+#!/usr/bin/env python3
+"""Benchmark of the collision step: particle-interval updates per second.
+
+A step is one frozen-neighbour interval of the whole hot path over every particle:
+gd_build_neighbors (cell list + K-NN), gd_collision_rates (pair rates, bin moments,
+interval choice) and gd_sample_collisions (events, mass/weight updates, audit).
+
+Default workload: the global disk of 2^22 particles with log-normal diameters
+(median 10 um, sigma_ln 1), K = 32, measured in the mixed form (value) and in the
+plain FP64 form (reported beside it).  Its working set (neighbour lists alone are
+512 MB) is larger than the 129 MB L2, so no L2 flush is added between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workload disk22|disk20|patches256|disk24|patch4096]
+
+Under torchrun (N > 1) every rank runs an independent replica (seed + rank) on its
+own GPU: the path does not shard without a halo exchange, so this is weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-collision updates/s (K-NN+rates+MC) mixed vs FP64 on 1 GB300; % HBM roofline"
+UNIT = "particle-interval updates/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def make_workload(name, rank=0):
+    from paper_2609_35967_gb300 import workloads as W
+    if name == "disk22":
+        return W.config2(seed=1 + rank), dict(workload="global disk 5-100 au, 2^22 particles, "
+                                               "log-normal a (median 10 um, sigma_ln 1), K=32")
+    if name == "disk20":
+        return W.config1(seed=1 + rank), dict(workload="global disk 5-100 au, 2^20 particles, "
+                                               "a = 1 um, K=32")
+    if name == "patches256":
+        return W.config3(seed0=1000 + 1000 * rank), dict(workload="256 local patches, N_b log-uniform "
+                                                          "2^10-2^16, K=32")
+    if name == "disk24":
+        return W.config4(seed=1 + rank), dict(workload="global disk, 2^24 particles, log-normal a "
+                                               "(median 1 um, sigma_ln 0.5), K=48, with push")
+    if name == "patch4096":
+        return W.config0(), dict(workload="local patch at 10 au, 4096 particles, K=32")
+    raise SystemExit(f"unknown workload {name}")
+
+
+# per-kernel algorithmic HBM bytes per particle
+def algo_bytes(kernel, K, mixed):
+    if kernel == "knn":
+        # own position (16 B FP32 or 32 B FP64), the list row (4K), d_i and V_i (16 B)
+        return (16 if mixed else 32) + 4 * K + 16
+    if kernel == "rates":
+        # list row (4K), one partner snapshot per particle (16 / 32 B), own position,
+        # snapshot, M and V (32 + 32 + 8 + 8), lambda* written (8)
+        return 4 * K + (16 if mixed else 32) + 88
+    if kernel == "sample":
+        return 8 + 8 + 4 + 8          # lambda*, state of the interval, perm, diameter
+    if kernel == "cells":
+        return 40 + 4 + 4 + 8 + 32 + 32 + (32 if mixed else 0) + 8
+    return 0
+
+
+class ClockSampler:
+    def __init__(self, index=0):
+        self.samples = []
+        self.proc = None
+        self.index = index
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([t.strip() for t in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        rows = [r for r in self.samples if len(r) >= 9]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        for r in rows:
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                "sw_power_cap"), r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def run_gpu(args, rank, world):
+    import torch
+
+    from paper_2609_35967_gb300 import binding as gd
+    from paper_2609_35967_gb300 import workloads as W
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    insts, cfg = make_workload(args.workload, rank)
+    K = insts[0]["params"]["K"]
+    push = args.workload == "disk24"
+    N = int(sum(len(i["x"]) for i in insts))
+    hbm, peak_kind = peaks()
+
+    def measure(precision, steps, warmup, timing):
+        sess = gd.Session(insts, precision=precision, device=str(dev), velocities=push,
+                          flags=gd.GD_FLAG_TIMING if timing else 0)
+        st = sess.stream
+
+        def step():
+            sess.build_neighbors()
+            sess.collision_rates()
+            sess.sample_collisions()
+            if push:
+                sess.push_staggered(-1.0)
+
+        for _ in range(warmup):
+            step()
+        pre = sess.stats()
+        clocks = ClockSampler(dev.index)
+        clocks.start()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(steps):
+            step()
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        ms = e0.elapsed_time(e1)
+        ck = clocks.stop()
+        post = sess.stats()
+        res = {"ms": ms, "clocks": ck, "launches": post["launches"] - pre["launches"],
+               "kernel_ms": {k: post["kernel_ms"][k] - pre["kernel_ms"][k] for k in post["kernel_ms"]},
+               "kernel_calls": {k: post["kernel_calls"][k] - pre["kernel_calls"][k]
+                                for k in post["kernel_calls"]},
+               "events": post["events"] - pre["events"], "status": post["status"]}
+        sess.close()
+        return res
+
+    mixed = measure(gd.GD_MIXED, args.steps, args.warmup, timing=True)
+    fp64 = None
+    if not args.skip_fp64:
+        fp64 = measure(gd.GD_FP64, max(1, args.steps // 3), max(1, args.warmup // 3), timing=True)
+
+    # end to end through the C ABI with host buffers: H2D of the step's inputs from
+    # pinned memory and D2H of the diameters inside the timed region, every step
+    cat = W.concat(insts)
+    sess = gd.Session(insts, precision=gd.GD_MIXED, device=str(dev), velocities=push)
+    host = {k: torch.as_tensor(cat[k]).pin_memory() for k in ("x", "y", "z", "s", "M")}
+    s_back = torch.empty(N, dtype=torch.float64).pin_memory()
+    st = sess.stream
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = s_back.numel() * s_back.element_size()
+
+    def e2e_step():
+        with torch.cuda.stream(st):
+            for k, v in host.items():
+                sess.t[k].copy_(v, non_blocking=True)
+        sess.build_neighbors()
+        sess.collision_rates()
+        sess.sample_collisions()
+        if push:
+            sess.push_staggered(-1.0)
+        with torch.cuda.stream(st):
+            s_back.copy_(sess.t["s"], non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    e2e_ms = max(e0.elapsed_time(e1), (time.perf_counter() - t0) * 1e3)
+    sess.close()
+
+    times = torch.tensor([mixed["ms"], fp64["ms"] if fp64 else 0.0, e2e_ms], dtype=torch.float64)
+    if world > 1:
+        t = times.to(dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        times = t.cpu()
+    return dict(N=N, K=K, cfg=cfg, mixed=mixed, fp64=fp64, times=times.tolist(), hbm=hbm,
+                peak_kind=peak_kind, h2d=h2d, d2h=d2h, push=push)
+
+
+def cpu_oracle_rate(insts, budget_s=12.0, max_q=4096):
+    """Oracle (serial, FP64, brute-force K-NN) on a bounded sample of query particles."""
+    import numpy as np
+
+    from oracle import gdo
+    ins = max(insts, key=lambda i: len(i["x"]))
+    P = gdo.params(ins["params"])
+    n = len(ins["x"])
+    rng = np.random.default_rng(0)
+    done = 0
+    t0 = time.perf_counter()
+    while done < max_q and time.perf_counter() - t0 < budget_s:
+        q = rng.choice(n, 8, replace=False)
+        nbr, d = gdo.knn(P, ins["x"], ins["y"], ins["z"], q)
+        gdo.rates_subset(P, ins["x"], ins["y"], ins["z"], ins["s"], ins["M"], q, nbr, d)
+        gdo.sample_subset(P, ins["x"], ins["y"], ins["z"], ins["s"], ins["M"], q, nbr, d,
+                          P.dt_fn_max / 64.0, 0)
+        done += len(q)
+    el = time.perf_counter() - t0
+    return done / el, done, el, n
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300")
+    ap.add_argument("--workload", default="disk22")
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        insts, cfg = make_workload(args.workload, 0)
+        vals = []
+        for _ in range(args.warmup):
+            cpu_oracle_rate(insts, budget_s=2.0, max_q=64)
+        total_q, total_t = 0, 0.0
+        for _ in range(args.steps):
+            v, q, el, n = cpu_oracle_rate(insts, budget_s=6.0, max_q=512)
+            vals.append(v)
+            total_q += q
+            total_t += el
+        value = total_q / total_t
+        sample = (f"{total_q} query particles of the {n}-particle instance over {args.steps} steps: "
+                  "brute-force K-NN, FP64 rates and Philox sampling of each")
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group(backend="nccl")
+    r = run_gpu(args, rank, world)
+    if rank != 0:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+        return
+    N, K = r["N"], r["K"]
+    ms_mixed, ms_fp64, ms_e2e = r["times"]
+    value = world * N * args.steps / (ms_mixed * 1e-3)
+    km = r["mixed"]["kernel_ms"]
+    kc = r["mixed"]["kernel_calls"]
+    dom = max(("knn", "rates", "sample", "cells"), key=lambda k: km.get(k, 0.0))
+    avg_s = km[dom] / max(1, kc[dom]) * 1e-3
+    ach = algo_bytes(dom, K, True) * N / avg_s / 1e9
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_mixed / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
+        "config": dict(r["cfg"], n_particles=N, K=K, precision="mixed",
+                       l2="no flush: working set > 129 MB L2 (lists alone 4K B/particle)",
+                       parallelism=f"{world} independent replicas" if world > 1 else "1 GPU"),
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": r["hbm"], "unit": "GB/s",
+                     "frac": ach / r["hbm"], "traffic": None,
+                     "peak_kind": r["peak_kind"],
+                     "algo_bytes_per_particle": algo_bytes(dom, K, True)},
+        "kernels_ms_per_step": {k: v / args.steps for k, v in km.items() if v > 0},
+        "gpu_launches": r["mixed"]["launches"],
+        "clocks": r["mixed"]["clocks"],
+        "e2e": {"value": world * N * args.steps / (ms_e2e * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
+    }
+    if r["fp64"]:
+        st = max(1, args.steps // 3)
+        out["fp64"] = {"value": world * N * st / (ms_fp64 * 1e-3), "ms_per_step": ms_fp64 / st,
+                       "kernels_ms_per_step": {k: v / st for k, v in r["fp64"]["kernel_ms"].items() if v > 0}}
+        out["mixed_over_fp64"] = out["value"] / out["fp64"]["value"]
+    if world == 1 and not args.skip_cpu:
+        insts, _ = make_workload(args.workload, 0)
+        v, q, el, n = cpu_oracle_rate(insts)
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"{q} query particles of the {n}-particle instance, {el:.1f} s: "
+                                         "brute-force K-NN, FP64 rates, sampling (serial C, -O2)"}
+    print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -211,10 +211,11 @@ def test_push_matches_oracle(gd, oracle):
         got = sess.t[k].cpu().numpy()
         scale = np.abs(ref).max()
         assert np.abs(got - ref).max() <= 1e-12 * scale, k
+    # velocities pass through acos/atan2/sin/cos/exp/expm1 (CUDA vs libm differ by a few
+    # ulp) and the 1 - R/r cancellation of the vertical gas factor: 1e-10 of their scale
     for k, ref in (("vr", vr), ("lth", lth)):
         got = sess.t[k].cpu().numpy()
-        scale = np.abs(lph / np.sqrt(x * x + y * y)).max()
-        assert np.abs(got - ref).max() <= 1e-10 * scale, k
+        assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max(), k
     sess.close()
 
 
