@@ -125,7 +125,7 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
 
   std::vector<long long> tiles = tile_table(c->h_off);
   c->n_tiles = (int)tiles.back();
-  c->cell_cap = 2 * N + 64LL * n + 1024;
+  c->cell_cap = 8 * N + 64LL * n + 1024;
   long long nst = (c->cell_cap + 2047) / 2048;
 
   bool ok = true;
@@ -144,10 +144,8 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
   ok &= dalloc(&c->d_rank_of, N) == cudaSuccess;
   ok &= dalloc(&c->d_pos64, N) == cudaSuccess;
   ok &= dalloc(&c->d_snap64, N) == cudaSuccess;
-  if (c->precision == GD_MIXED) {
-    ok &= dalloc(&c->d_pos32, N) == cudaSuccess;
-    ok &= dalloc(&c->d_snap32, N) == cudaSuccess;
-  }
+  ok &= dalloc(&c->d_pos32, N) == cudaSuccess;
+  if (c->precision == GD_MIXED) ok &= dalloc(&c->d_snap32, N) == cudaSuccess;
   ok &= dalloc(&c->d_Mr, N) == cudaSuccess;
   ok &= dalloc(&c->d_dist, N) == cudaSuccess;
   ok &= dalloc(&c->d_V, N) == cudaSuccess;

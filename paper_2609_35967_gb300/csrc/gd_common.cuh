@@ -5,7 +5,7 @@
 //                 [off[b], off[b+1]) like the caller's indices.  perm[r] is the caller
 //                 index, rank_of[i] its inverse.
 //   Pos64[r]    : {x, y, z, caller index}            32 B  (FP64 K-NN, re-rank)
-//   float4 pos32: {x-c, y-c, z-c, caller index bits} 16 B  (FP32 K-NN), c = instance centre
+//   float4 pos32: {x, y, z relative to the own cell origin, packed cell (11+11+10 bits)} 16 B
 //   Snap64[r]   : {s, m, N, 1/m} frozen at the interval start        32 B
 //   float4 snap32: {s, m, N 2^-64, 1/m} frozen, FP32                 16 B
 //   nbr[r*K+k]  : ranks of the K neighbours, slot 0 = self, others by ascending caller index
@@ -14,7 +14,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "../../include/gd.h"
+#include "gd.h"
 
 namespace gd {
 
@@ -44,7 +44,10 @@ struct GridDev {
   double inv[3];     // 1 / cs
   double box[3];     // periodic extent (x, y of a patch), 0 otherwise
   double ctr[3];     // origin of the FP32 mirror coordinates
-  double X32;        // bound on |FP32 mirror coordinate| + periodic extents (error model)
+  double X32;        // bound on |coordinate| + periodic extents (FP64 rounding of the mirror)
+  float cs32[3];     // cell edges and their inverses in FP32 (search bookkeeping)
+  float inv32[3];
+  float E32;         // absolute error bound of FP32 cell-relative distances [cm]
   int dim[3];
   int periodic;      // x and y periodic (patch)
   long long cell_off;

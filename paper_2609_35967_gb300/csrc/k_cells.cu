@@ -115,6 +115,15 @@ __global__ void k_grid(const InstDev* __restrict__ P, StateDev* st, GridDev* gri
       for (int a = 0; a < 3; ++a) X = fmax(X, 0.5 * g.cs[a] * g.dim[a]);
       if (per) X += fmax(g.box[0], g.box[1]);
       g.X32 = X;
+      double csmax = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        g.cs32[a] = (float)g.cs[a];
+        g.inv32[a] = (float)g.inv[a];
+        csmax = fmax(csmax, g.cs[a]);
+      }
+      // |sqrt(D32) - d| <= 10 u sqrt(D32) + E, u = 2^-24: cell-relative FP32 coordinates
+      // (<= u cell each), the FP32 cell offsets, and the FP64 rounding of the mirror
+      g.E32 = (float)((16.0 * 0x1p-24 * csmax + 32.0 * 0x1p-53 * X) * 1.0001);
       g.periodic = per ? 1 : 0;
       g.cell_off = total;
       total += cells;
@@ -271,7 +280,7 @@ __global__ void k_scatter(TileMap tm, const InstDev* __restrict__ P, const GridD
     sn.s = si; sn.m = m; sn.N = N; sn.inv_m = im;
     snap64[r] = sn;
     Mr[r] = Mi;
-    if (kMixed) {
+    {
       // FP32 mirror relative to the particle's own cell origin (|coord| <= cell edge),
       // cell coordinates packed in w (11 + 11 + 10 bits); periodic axes use the
       // wrapped coordinate so that the cell and the offset agree.
@@ -283,6 +292,8 @@ __global__ void k_scatter(TileMap tm, const InstDev* __restrict__ P, const GridD
       float fy = (float)(yw - (g.lo[1] + iy * g.cs[1]));
       float fz = (float)(zi - (g.lo[2] + iz * g.cs[2]));
       pos32[r] = make_float4(fx, fy, fz, __int_as_float(ix | (iy << 11) | (iz << 22)));
+    }
+    if (kMixed) {
       snap32[r] = make_float4((float)si, (float)m, (float)(N * 0x1p-64), (float)im);
     }
   }

@@ -1,21 +1,24 @@
 // k_knn.cu -- K nearest neighbours over the device cell list (Sect. 2.5.1).
 //
-// One warp per query particle.  The warp scans every cell row that intersects a ball
-// of radius rho around the query (rows are contiguous rank ranges, so loads are
-// coalesced), keeps a register top list distributed over the lanes (slot g lives in
-// lane g % 32, register g / 32) ordered by (key, index), and accepts rho once the ball
-// provably contains the K-1 nearest others; otherwise rho grows and the scan repeats.
-//
-//  FP64 form : key = bits of d^2 = (dx dx + dy dy) + dz dz (FP64, no FMA, minimum image),
-//              ties by caller index -- exactly the oracle's order.
-//  mixed form: key = FP32 d^2 from cell-relative FP32 coordinates.  An error bound
-//              |sqrt(D32) - d| <= rel sqrt(D32) + E (rel = 10 u, E = 16 u cell + FP64
-//              rounding, u = 2^-24) gives thresholds T_lo < T_hi around the (K-1)-th key:
-//              keys below T_lo are certain members, keys up to T_hi form the band whose
-//              members are re-ranked exactly in FP64.  Any doubt (band not held in the
-//              list, a periodic axis fully covered) falls back to the FP64 form.
-// Members are then sorted by caller index (bitonic over the lanes) and written as
-// ranks after the particle itself; d_i and the sampling measure V_i follow.
+// A warp owns a chunk of 32 consecutive query ranks (neighbouring cells) and works in
+// three phases:
+//  A  per query, warp-cooperative: scan every cell row that meets a ball of radius rho
+//     around the query (rows are contiguous rank ranges, so loads are coalesced), keep a
+//     register top list over the lanes (slot g in lane g % 32, register g / 32) ordered by
+//     (key, index), and accept rho once the ball provably holds the K-1 nearest others.
+//     All search bookkeeping (cell ranges, slab distances, radii) is FP32/INT in the
+//     query's cell-relative frame with conservative margins.
+//       FP64 form : key = bits of d^2 = (dx dx + dy dy) + dz dz in FP64 (no FMA, minimum
+//                   image), ties by caller index: the oracle's order exactly.
+//       mixed form: key = FP32 d^2 from cell-relative FP32 coordinates; with
+//                   |sqrt(D32) - d| <= 10u sqrt(D32) + E (u = 2^-24) keys below T_lo are
+//                   certain members and keys up to T_hi form a band that phase B ranks
+//                   exactly in FP64.  A band that overflows the list or the band buffer,
+//                   or a periodic axis covered whole, sends the query to the FP64 form.
+//  B  lane = query: the FP64 arithmetic (band re-rank, d_i = sqrt(d^2), V_i with the
+//     flat-boundary caps), so FP64 instructions carry 32 queries each.
+//  C  per query: members sorted by caller index (bitonic over the lanes), written as
+//     ranks after the particle itself.
 #include <climits>
 
 #include "gd_ctx.h"
@@ -24,6 +27,8 @@
 namespace gd {
 
 constexpr unsigned FULL = 0xffffffffu;
+constexpr int kBand = 8;          // band entries resolved in phase B per query
+constexpr int kWarps = 8;         // warps per block
 
 struct KnnArgs {
   long long N;
@@ -34,6 +39,7 @@ struct KnnArgs {
   const int* cstart;
   const Pos64* pos64;
   const float4* pos32;
+  const int* perm;
   int* nbr;
   double* dist;
   double* V;
@@ -49,7 +55,7 @@ __device__ __forceinline__ bool kless(KT ka, int ja, KT kb, int jb) {
   return ka < kb || (ka == kb && ja < jb);
 }
 
-// Sorted list of 32*KPL (key, index, rank) entries spread over the warp.
+// Sorted list of 32*KPL (key, tie index, rank) entries spread over the warp.
 template <int KPL, typename KT>
 struct TopList {
   KT k[KPL];
@@ -131,36 +137,48 @@ __device__ __forceinline__ void sort_by_index(int (&jj)[KPL], int (&rr)[KPL], in
   }
 }
 
-// ---------------------------------------------------------------- geometry
+// ---------------------------------------------------------------- geometry (FP32 / INT)
 struct QueryPos {
-  double x, y, z;     // raw position
-  double xw, yw;      // wrapped into the periodic box
+  double x, y, z;     // FP64 position (FP64 keys)
   int ix, iy, iz;     // own cell
-  float fx, fy, fz;   // FP32 cell-relative coordinates (mixed form)
+  float fx, fy, fz;   // position inside the own cell [cm]
 };
 
-__device__ __forceinline__ void axis_range(const GridDev& G, int a, double qa, double rs, int& lo,
-                                           int& hi, bool& full) {
-  double t0 = floor((qa - rs - G.lo[a]) * G.inv[a]);
-  double t1 = floor((qa + rs - G.lo[a]) * G.inv[a]);
-  int d = G.dim[a];
+struct Grid32 {
+  float cs[3], inv[3];
+  int dim[3];
+  bool per;           // x and y periodic
+  long long cell_off;
+};
+
+// Conservative cell range [lo, hi] (unwrapped on periodic axes) of the slab
+// |coordinate - query| <= rs along one axis; full = a periodic axis covered whole.
+__device__ __forceinline__ void axis_range32(const Grid32& G, int a, int ia, float fa, float rs, int& lo,
+                                             int& hi, bool& full) {
+  const float m = rs * 1.00001f + G.cs[a] * 1e-5f;
+  float t0 = floorf((fa - m) * G.inv[a]);
+  float t1 = floorf((fa + m) * G.inv[a]);
+  const int d = G.dim[a];
+  t0 = fmaxf(t0, -4.0e6f);
+  t1 = fminf(t1, 4.0e6f);
+  lo = ia + (int)t0;
+  hi = ia + (int)t1;
   full = false;
-  if (G.box[a] > 0.0) {
-    if (t1 - t0 + 1.0 >= (double)d) { lo = 0; hi = d - 1; full = true; return; }
-    lo = (int)t0;
-    hi = (int)t1;
+  if (G.per && a < 2) {
+    if (hi - lo + 1 >= d) { lo = 0; hi = d - 1; full = true; }
   } else {
-    t0 = fmax(t0, 0.0);
-    t1 = fmin(t1, (double)(d - 1));
-    lo = (int)t0;
-    hi = (int)t1;
+    lo = lo < 0 ? 0 : lo;
+    hi = hi > d - 1 ? d - 1 : hi;
   }
 }
 
-__device__ __forceinline__ double slab_dist(const GridDev& G, int a, double qa, int k) {
-  double l = G.lo[a] + k * G.cs[a];
-  double h = l + G.cs[a];
-  return fmax(0.0, fmax(l - qa, qa - h));
+// Lower bound of the distance from the query to the slab of (unwrapped) cell k.
+__device__ __forceinline__ float slab_dist32(const Grid32& G, int a, int ia, float fa, int k) {
+  float d;
+  if (k < ia) d = (float)(ia - k - 1) * G.cs[a] + fa;
+  else if (k > ia) d = (float)(k - ia) * G.cs[a] - fa;
+  else d = 0.0f;
+  return fmaxf(d * 0.99999f - G.cs[a] * 1e-5f, 0.0f);
 }
 
 __device__ __forceinline__ int floordiv(int a, int d) {
@@ -168,43 +186,43 @@ __device__ __forceinline__ int floordiv(int a, int d) {
   return (a % d != 0 && ((a < 0) != (d < 0))) ? q - 1 : q;
 }
 
-// Visits every stored rank range [ra, rb) of the cell rows within distance rs of the
-// query: visit(ra, rb, x_shift_cells, dy_cells, dz_cells).  Returns true when a periodic
-// axis had to be covered whole (FP32 offsets are then ambiguous).
+// Visits the stored rank ranges [ra, rb) of every cell row within rs of the query:
+// visit(ra, rb, x_shift_cells, dy_cells, dz_cells).  Returns true when a periodic axis
+// was covered whole (the FP32 cell offsets are then ambiguous).
 template <class F>
-__device__ __forceinline__ bool scan_ball(const GridDev& G, const int* __restrict__ cstart,
-                                          const QueryPos& Q, double rs, F&& visit) {
+__device__ __forceinline__ bool scan_ball(const Grid32& G, const int* __restrict__ cstart, const QueryPos& Q,
+                                          float rs, F&& visit) {
   bool amb = false;
   int lz, hz, ly, hy;
   bool fz, fy;
-  axis_range(G, 2, Q.z, rs, lz, hz, fz);
-  axis_range(G, 1, Q.yw, rs, ly, hy, fy);
-  if (fy && G.box[1] > 0.0) amb = true;
-  const double rs2 = rs * rs;
+  axis_range32(G, 2, Q.iz, Q.fz, rs, lz, hz, fz);
+  axis_range32(G, 1, Q.iy, Q.fy, rs, ly, hy, fy);
+  if (fy && G.per) amb = true;
+  const float rs2 = rs * rs * 1.00002f;
   const int dimx = G.dim[0], dimy = G.dim[1];
   for (int iz = lz; iz <= hz; ++iz) {
-    double dz = slab_dist(G, 2, Q.z, iz);
-    if (dz > rs) continue;
+    const float dz = slab_dist32(G, 2, Q.iz, Q.fz, iz);
+    if (dz * dz > rs2) continue;
     for (int iyu = ly; iyu <= hy; ++iyu) {
-      double dy = slab_dist(G, 1, Q.yw, iyu);
-      double dyz2 = dy * dy + dz * dz;
+      const float dy = fy ? 0.0f : slab_dist32(G, 1, Q.iy, Q.fy, iyu);
+      const float dyz2 = dy * dy + dz * dz;
       if (dyz2 > rs2) continue;
       int iy = iyu;
-      if (G.box[1] > 0.0) { iy %= dimy; if (iy < 0) iy += dimy; }
-      double xr = sqrt(fmax(rs2 - dyz2, 0.0));
+      if (G.per) { iy %= dimy; if (iy < 0) iy += dimy; }
+      const float xr = sqrtf(fmaxf(rs2 - dyz2, 0.0f));
       int lx, hx;
       bool fx;
-      axis_range(G, 0, Q.xw, xr, lx, hx, fx);
+      axis_range32(G, 0, Q.ix, Q.fx, xr, lx, hx, fx);
       if (lx > hx) continue;
-      if (fx && G.box[0] > 0.0) amb = true;
-      long long rowc = G.cell_off + (long long)dimx * (iy + (long long)dimy * iz);
+      if (fx && G.per) amb = true;
+      const long long rowc = G.cell_off + (long long)dimx * (iy + (long long)dimy * iz);
       int kx = 0, a0 = lx, e0 = hx;
-      if (G.box[0] > 0.0 && !fx) {
+      if (G.per && !fx) {
         kx = floordiv(lx, dimx);
         a0 = lx - kx * dimx;
         e0 = hx - kx * dimx;
       }
-      int e1 = e0 < dimx ? e0 : dimx - 1;
+      const int e1 = e0 < dimx ? e0 : dimx - 1;
       visit(__ldg(&cstart[rowc + a0]), __ldg(&cstart[rowc + e1 + 1]), kx * dimx, iyu - Q.iy, iz - Q.iz);
       if (e0 >= dimx)
         visit(__ldg(&cstart[rowc]), __ldg(&cstart[rowc + (e0 - dimx) + 1]), (kx + 1) * dimx,
@@ -215,19 +233,19 @@ __device__ __forceinline__ bool scan_ball(const GridDev& G, const int* __restric
 }
 
 // Offers one candidate per lane; lanes below the threshold are inserted in lane order.
-template <int KPL, typename KT>
+template <int KPL, typename KT, class R>
 __device__ __forceinline__ void offer(TopList<KPL, KT>& Lst, KT ck, int cj, int cr, KT& wk, int& wj,
-                                      int lane, int slot_thr) {
+                                      int lane, R&& refresh) {
   unsigned m = __ballot_sync(FULL, kless(ck, cj, wk, wj));
   while (m) {
-    int src = __ffs(m) - 1;
+    const int src = __ffs(m) - 1;
     m &= m - 1;
-    KT nk = __shfl_sync(FULL, ck, src);
-    int nj = __shfl_sync(FULL, cj, src);
-    int nr = __shfl_sync(FULL, cr, src);
+    const KT nk = __shfl_sync(FULL, ck, src);
+    const int nj = __shfl_sync(FULL, cj, src);
+    const int nr = __shfl_sync(FULL, cr, src);
     if (kless(nk, nj, wk, wj)) {
       Lst.insert(nk, nj, nr, lane);
-      Lst.get(slot_thr, wk, wj);
+      refresh();
     }
   }
 }
@@ -245,141 +263,137 @@ __device__ __forceinline__ double sample_volume(const InstDev& P, double d, doub
   return V;
 }
 
-template <int KPL>
-__device__ __forceinline__ void write_list(const KnnArgs& A, long long q, int L, int (&jj)[KPL],
-                                           int (&rr)[KPL], int lane, double d, const InstDev& P,
-                                           const QueryPos& Q) {
-  sort_by_index<KPL>(jj, rr, lane);
-  int* row = A.nbr + q * (long long)A.K;
-#pragma unroll
-  for (int t = 0; t < KPL; ++t) {
-    int e = t * 32 + lane;
-    if (e < L) row[1 + e] = rr[t];
-  }
-  if (lane == 0) {
-    row[0] = (int)q;
-    A.dist[q] = d;
-    A.V[q] = sample_volume(P, d, Q.x, Q.y);
-  }
-}
-
-__device__ __forceinline__ double rho_start(const GridDev& G, const int* __restrict__ cstart,
-                                            const QueryPos& Q, int L) {
+__device__ __forceinline__ float rho_start(const Grid32& G, const int* __restrict__ cstart, const QueryPos& Q,
+                                           int L) {
   int n = 0, nc = 0;
   for (int dz = -1; dz <= 1; ++dz) {
     int iz = Q.iz + dz;
     if (iz < 0 || iz >= G.dim[2]) continue;
     for (int dy = -1; dy <= 1; ++dy) {
       int iy = Q.iy + dy;
-      if (G.box[1] > 0.0) { iy %= G.dim[1]; if (iy < 0) iy += G.dim[1]; }
+      if (G.per) { iy %= G.dim[1]; if (iy < 0) iy += G.dim[1]; }
       else if (iy < 0 || iy >= G.dim[1]) continue;
-      for (int dx = -1; dx <= 1; ++dx) {
-        int ix = Q.ix + dx;
-        if (G.box[0] > 0.0) { ix %= G.dim[0]; if (ix < 0) ix += G.dim[0]; }
-        else if (ix < 0 || ix >= G.dim[0]) continue;
-        long long c = G.cell_off + ix + (long long)G.dim[0] * (iy + (long long)G.dim[1] * iz);
+      int x0 = Q.ix - 1, x1 = Q.ix + 1;
+      if (!G.per) { x0 = x0 < 0 ? 0 : x0; x1 = x1 >= G.dim[0] ? G.dim[0] - 1 : x1; }
+      for (int ix = x0; ix <= x1; ++ix) {
+        int xw = ix;
+        if (G.per) { xw %= G.dim[0]; if (xw < 0) xw += G.dim[0]; }
+        long long c = G.cell_off + xw + (long long)G.dim[0] * (iy + (long long)G.dim[1] * iz);
         n += __ldg(&cstart[c + 1]) - __ldg(&cstart[c]);
         ++nc;
       }
     }
   }
-  double csmax = fmax(G.cs[0], fmax(G.cs[1], G.cs[2]));
-  if (n <= 1) return 2.0 * csmax;
-  double nd = (double)(n - 1) / (nc * G.cs[0] * G.cs[1] * G.cs[2]);
-  return 1.2 * cbrt(3.0 * L / (4.0 * kPi * nd));
+  const float csmax = fmaxf(G.cs[0], fmaxf(G.cs[1], G.cs[2]));
+  if (n <= 1) return 2.0f * csmax;
+  // density in units of csmax^3 (a cell volume in cm^3 can exceed the FP32 range)
+  const float vcell = (G.cs[0] / csmax) * (G.cs[1] / csmax) * (G.cs[2] / csmax);
+  const float nd = (float)(n - 1) / ((float)nc * vcell);
+  const float r = 1.2f * csmax * cbrtf(3.0f * (float)L / (4.0f * 3.14159265f * nd));
+  return fminf(fmaxf(r, 1e-3f * csmax), 4.0f * csmax * (float)(G.dim[0] + G.dim[1] + G.dim[2]));
 }
 
-// ---------------------------------------------------------------- FP64 form
+__device__ __forceinline__ float grow(float rho, int found, int L) {
+  float g = cbrtf(1.3f * (float)L / (float)(found > 0 ? found : 1));
+  return rho * fminf(fmaxf(g, 1.25f), 3.0f);
+}
+
+// Minimum-image FP64 d^2 of rank r from the query: the oracle's expression.
+__device__ __forceinline__ double d2_fp64(const Pos64* __restrict__ pos64, int r, double qx, double qy,
+                                          double qz, double bx, double by, long long& j) {
+  const double2* pp = reinterpret_cast<const double2*>(pos64 + r);
+  double2 a = __ldg(pp), b = __ldg(pp + 1);
+  double dx = a.x - qx, dy = a.y - qy, dz = b.x - qz;
+  if (bx > 0.0) {
+    if (dx > 0.5 * bx) dx -= bx; else if (dx < -0.5 * bx) dx += bx;
+    if (dy > 0.5 * by) dy -= by; else if (dy < -0.5 * by) dy += by;
+  }
+  j = __double_as_longlong(b.y);
+  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// Phase-A result of one query, kept in shared memory for phases B and C.
+struct QInfo {
+  int state;          // 0 done (row, d, V written), 1 FP64 members written, 2 mixed band pending
+  int p_lo;           // certain members written to the row
+  int nb;             // band entries
+  int need;           // band entries to select
+  unsigned long long d2max;   // FP64 form: bits of the (K-1)-th d^2
+  int band[kBand];
+};
+
+// FP64-key search for one query (the plain form, and the fallback of the mixed form).
+// Writes the unsorted members to the row and the (K-1)-th d^2; returns false on failure.
 template <int KPL>
-__device__ void query_fp64(const KnnArgs& A, const GridDev& G, const InstDev& P, const QueryPos& Q,
-                           long long q, int lane, double rho, StateDev* st) {
+__device__ bool query_fp64(const KnnArgs& A, const Grid32& G, const GridDev& Gd, const QueryPos& Q, long long q,
+                           int lane, float rho, QInfo& qi) {
   const int L = A.K - 1;
   TopList<KPL, unsigned long long> Lst;
-  double diag = sqrt(G.cs[0] * G.cs[0] * G.dim[0] * G.dim[0] + G.cs[1] * G.cs[1] * G.dim[1] * G.dim[1] +
-                     G.cs[2] * G.cs[2] * G.dim[2] * G.dim[2]);
+  const double bx = Gd.box[0], by = Gd.box[1];
+  const float diag = sqrtf((float)G.dim[0] * G.dim[0] * G.cs[0] * G.cs[0] +
+                           (float)G.dim[1] * G.dim[1] * G.cs[1] * G.cs[1] +
+                           (float)G.dim[2] * G.dim[2] * G.cs[2] * G.cs[2]);
   for (int att = 0; att < 64; ++att) {
     Lst.reset();
     unsigned long long wk = ~0ull;
     int wj = INT_MAX;
-    const double rho2 = rho * rho;
-    const double rs = rho * (1.0 + 1e-9);
-    const double bx = G.box[0], by = G.box[1];
-    scan_ball(G, A.cstart, Q, rs, [&](int ra, int rb, int, int, int) {
+    const double rho2 = (double)rho * (double)rho;
+    auto refresh = [&]() { Lst.get(L - 1, wk, wj); };
+    scan_ball(G, A.cstart, Q, rho, [&](int ra, int rb, int, int, int) {
       for (int base = ra; base < rb; base += 32) {
-        int r = base + lane;
+        const int r = base + lane;
         unsigned long long ck = ~0ull;
         int cj = INT_MAX;
         if (r < rb && r != (int)q) {
-          const double2* pp = reinterpret_cast<const double2*>(A.pos64 + r);
-          double2 a = __ldg(pp), b = __ldg(pp + 1);
-          double dx = a.x - Q.x, dy = a.y - Q.y, dz = b.x - Q.z;
-          if (bx > 0.0) {
-            if (dx > 0.5 * bx) dx -= bx; else if (dx < -0.5 * bx) dx += bx;
-            if (dy > 0.5 * by) dy -= by; else if (dy < -0.5 * by) dy += by;
-          }
-          double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-          if (d2 <= rho2) {
-            ck = (unsigned long long)__double_as_longlong(d2);
-            cj = (int)__double_as_longlong(b.y);
-          }
+          long long jj;
+          const double d2 = d2_fp64(A.pos64, r, Q.x, Q.y, Q.z, bx, by, jj);
+          if (d2 <= rho2) { ck = (unsigned long long)__double_as_longlong(d2); cj = (int)jj; }
         }
-        offer(Lst, ck, cj, r, wk, wj, lane, L - 1);
+        offer(Lst, ck, cj, r, wk, wj, lane, refresh);
       }
     });
     unsigned long long kL;
     int jL;
     Lst.get(L - 1, kL, jL);
     if (kL != ~0ull) {
-      int jj[KPL], rr[KPL];
+      int* row = A.nbr + q * (long long)A.K;
 #pragma unroll
       for (int t = 0; t < KPL; ++t) {
-        bool in = t * 32 + lane < L;
-        jj[t] = in ? Lst.j[t] : INT_MAX;
-        rr[t] = in ? Lst.r[t] : -1;
+        int g = t * 32 + lane;
+        if (g < L) row[1 + g] = Lst.r[t];
       }
-      write_list<KPL>(A, q, L, jj, rr, lane, sqrt(__longlong_as_double((long long)kL)), P, Q);
-      return;
+      if (lane == 0) { qi.state = 1; qi.d2max = kL; }
+      return true;
     }
     int found = 0;
 #pragma unroll
     for (int t = 0; t < KPL; ++t) found += __popc(__ballot_sync(FULL, Lst.k[t] != ~0ull));
-    if (rho > 2.0 * diag) break;
-    double g = cbrt(1.3 * L / (double)(found > 0 ? found : 1));
-    rho *= fmin(fmax(g, 1.25), 3.0);
+    if (rho > 2.0f * diag) break;
+    rho = grow(rho, found, L);
   }
-  // no acceptable radius: keep the row valid (the particle against itself only), V = 1
-  int* row = A.nbr + q * (long long)A.K;
-  for (int k = lane; k < A.K; k += 32) row[k] = (int)q;
-  if (lane == 0) {
-    A.dist[q] = 0.0;
-    A.V[q] = 1.0;
-    set_status(st, GD_ST_KNN);
-  }
+  return false;
 }
 
-// ---------------------------------------------------------------- mixed form
+// FP32-key search with the FP64 band; returns false when the query needs the FP64 form.
 template <int KPL>
-__device__ bool query_mixed(const KnnArgs& A, const GridDev& G, const InstDev& P, const QueryPos& Q,
-                            long long q, int lane, double& rho) {
+__device__ bool query_mixed(const KnnArgs& A, const Grid32& G, const GridDev& Gd, const QueryPos& Q, long long q,
+                            int lane, float& rho, QInfo& qi) {
   const int L = A.K - 1;
   constexpr int S = 32 * KPL;
   if (S < L + 1) return false;
   TopList<KPL, unsigned> Lst;
-  const double u = 0x1p-24;
-  const double csmax = fmax(G.cs[0], fmax(G.cs[1], G.cs[2]));
-  const double E = 16.0 * u * csmax + 32.0 * 0x1p-53 * G.X32;
-  const double rel = 10.0 * u;
-  const float Ef = (float)(4.02 * E), E2f = (float)(4.02 * E * E);
-  const float csx = (float)G.cs[0], csy = (float)G.cs[1], csz = (float)G.cs[2];
-  double diag = sqrt(G.cs[0] * G.cs[0] * G.dim[0] * G.dim[0] + G.cs[1] * G.cs[1] * G.dim[1] * G.dim[1] +
-                     G.cs[2] * G.cs[2] * G.dim[2] * G.dim[2]);
+  const float E = Gd.E32;
+  const float rel = 10.0f * 5.9604645e-8f;
+  const float Ef = 4.02f * E, E2f = 4.02f * E * E;
+  const float diag = sqrtf((float)G.dim[0] * G.dim[0] * G.cs[0] * G.cs[0] +
+                           (float)G.dim[1] * G.dim[1] * G.cs[1] * G.cs[1] +
+                           (float)G.dim[2] * G.dim[2] * G.cs[2] * G.cs[2]);
   for (int att = 0; att < 64; ++att) {
     Lst.reset();
     unsigned wk = ~0u;
     int wj = INT_MAX;
-    const double rf = rho * (1.0 + rel) + E;
-    const float rhof2 = __double2float_ru(rf * rf * (1.0 + 1e-9));
-    const double rs = rho * (1.0 + 1e-9);
+    const float rf = (rho * (1.0f + rel) + E) * 1.000001f;
+    const float rhof2 = rf * rf * 1.000001f;
     // insertion threshold: the last list slot, or a bound above T_hi of the current
     // (K-1)-th key, whichever is lower
     auto refresh = [&]() {
@@ -390,38 +404,29 @@ __device__ bool query_mixed(const KnnArgs& A, const GridDev& G, const InstDev& P
       wk = kS;
       wj = jS;
       if (kL != ~0u) {
-        float tau = __uint_as_float(kL);
-        float tins = tau * (float)(1.0 + 12.0 * rel) + Ef * sqrtf(tau) + E2f;
-        unsigned tb = __float_as_uint(tins) + 4u;
+        const float tau = __uint_as_float(kL);
+        const float tins = (tau * (1.0f + 12.0f * rel) + Ef * sqrtf(tau) + E2f) * 1.00001f;
+        const unsigned tb = __float_as_uint(tins);
         if (tb < wk) { wk = tb; wj = INT_MAX; }
       }
     };
-    bool amb = scan_ball(G, A.cstart, Q, rs, [&](int ra, int rb, int xsh, int dyc, int dzc) {
+    const float csx = G.cs[0], csy = G.cs[1], csz = G.cs[2];
+    const bool amb = scan_ball(G, A.cstart, Q, rho, [&](int ra, int rb, int xsh, int dyc, int dzc) {
       const float offy = (float)dyc * csy, offz = (float)dzc * csz;
       for (int base = ra; base < rb; base += 32) {
-        int r = base + lane;
+        const int r = base + lane;
         unsigned ck = ~0u;
         int cj = INT_MAX;
         if (r < rb && r != (int)q) {
-          float4 p = __ldg(A.pos32 + r);
-          int ixj = __float_as_int(p.w) & 2047;
-          float dx = (p.x - Q.fx) + (float)(ixj + xsh - Q.ix) * csx;
-          float dy = (p.y - Q.fy) + offy;
-          float dz = (p.z - Q.fz) + offz;
-          float D = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+          const float4 p = __ldg(A.pos32 + r);
+          const int ixj = __float_as_int(p.w) & 2047;
+          const float dx = (p.x - Q.fx) + (float)(ixj + xsh - Q.ix) * csx;
+          const float dy = (p.y - Q.fy) + offy;
+          const float dz = (p.z - Q.fz) + offz;
+          const float D = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
           if (D <= rhof2) { ck = __float_as_uint(D); cj = r; }
         }
-        unsigned m = __ballot_sync(FULL, kless(ck, cj, wk, wj));
-        while (m) {
-          int src = __ffs(m) - 1;
-          m &= m - 1;
-          unsigned nk = __shfl_sync(FULL, ck, src);
-          int nj = __shfl_sync(FULL, cj, src);
-          if (kless(nk, nj, wk, wj)) {
-            Lst.insert(nk, nj, nj, lane);
-            refresh();
-          }
-        }
+        offer(Lst, ck, cj, cj, wk, wj, lane, refresh);
       }
     });
     if (amb) return false;
@@ -432,23 +437,23 @@ __device__ bool query_mixed(const KnnArgs& A, const GridDev& G, const InstDev& P
       int found = 0;
 #pragma unroll
       for (int t = 0; t < KPL; ++t) found += __popc(__ballot_sync(FULL, Lst.k[t] != ~0u));
-      if (rho > 2.0 * diag) return false;
-      double g = cbrt(1.3 * L / (double)(found > 0 ? found : 1));
-      rho *= fmin(fmax(g, 1.25), 3.0);
+      if (rho > 2.0f * diag) return false;
+      rho = grow(rho, found, L);
       continue;
     }
-    const double sq = sqrt((double)__uint_as_float(kL));
-    const double hi_tau = sq * (1.0 + rel) + E;
+    // FP32 bounds with relative margins far above their own rounding
+    const float sq = sqrtf(__uint_as_float(kL));
+    const float hi_tau = (sq * (1.0f + rel) * 1.000001f + E) * 1.00001f;
     if (hi_tau > rho) {
-      if (rho > 2.0 * diag) return false;
-      rho = fmax(rho * 1.25, hi_tau * 1.02);
+      if (rho > 2.0f * diag) return false;
+      rho = fmaxf(rho * 1.25f, hi_tau * 1.02f);
       continue;
     }
-    const double lo_tau = sq * (1.0 - rel) - E;
-    const double tlo = (lo_tau - E) / (1.0 + rel);
-    const double thi = (hi_tau + E) / (1.0 - rel);
-    const unsigned Tlo = tlo > 0.0 ? __float_as_uint(__double2float_rd(tlo * tlo * (1.0 - 1e-12))) : 0u;
-    const unsigned Thi = __float_as_uint(__double2float_ru(thi * thi * (1.0 + 1e-12)));
+    const float lo_tau = (sq * (1.0f - rel) * 0.999999f - E) * 0.99999f;
+    const float tlo = (lo_tau - E) / (1.0f + rel);
+    const float thi = (hi_tau + E) / (1.0f - rel);
+    const unsigned Tlo = tlo > 0.0f ? __float_as_uint(tlo * tlo * 0.9999f) : 0u;
+    const unsigned Thi = __float_as_uint(thi * thi * 1.0001f);
     unsigned kS;
     int jS;
     Lst.get(S - 1, kS, jS);
@@ -459,111 +464,145 @@ __device__ bool query_mixed(const KnnArgs& A, const GridDev& G, const InstDev& P
       p_lo += __popc(__ballot_sync(FULL, Lst.k[t] < Tlo));
       p_hi += __popc(__ballot_sync(FULL, Lst.k[t] <= Thi));
     }
-    const int need = L - p_lo;
-    // exact FP64 keys of the band entries
-    unsigned long long bk[KPL];
-    int bj[KPL];
-    double bd[KPL];
-    const double bx = G.box[0], by = G.box[1];
+    const int nb = p_hi - p_lo;
+    if (nb > kBand) return false;
+    int* row = A.nbr + q * (long long)A.K;
 #pragma unroll
     for (int t = 0; t < KPL; ++t) {
-      int g = t * 32 + lane;
-      bk[t] = ~0ull;
-      bj[t] = INT_MAX;
-      bd[t] = 0.0;
-      if (g >= p_lo && g < p_hi) {
-        const double2* pp = reinterpret_cast<const double2*>(A.pos64 + Lst.r[t]);
-        double2 a = __ldg(pp), b = __ldg(pp + 1);
-        double dx = a.x - Q.x, dy = a.y - Q.y, dz = b.x - Q.z;
-        if (bx > 0.0) {
-          if (dx > 0.5 * bx) dx -= bx; else if (dx < -0.5 * bx) dx += bx;
-          if (dy > 0.5 * by) dy -= by; else if (dy < -0.5 * by) dy += by;
-        }
-        double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-        bk[t] = (unsigned long long)__double_as_longlong(d2);
-        bj[t] = (int)__double_as_longlong(b.y);
-        bd[t] = d2;
-      }
+      const int g = t * 32 + lane;
+      if (g < p_lo) row[1 + g] = Lst.r[t];
+      else if (g < p_hi) qi.band[g - p_lo] = Lst.r[t];
     }
-    // rank of each band entry among the band by (d^2, index)
-    int rank[KPL];
-#pragma unroll
-    for (int t = 0; t < KPL; ++t) rank[t] = 0;
-    for (int g2 = p_lo; g2 < p_hi; ++g2) {
-      unsigned long long ok = bk[0];
-      int oj = bj[0];
-#pragma unroll
-      for (int t = 1; t < KPL; ++t)
-        if (t == (g2 >> 5)) { ok = bk[t]; oj = bj[t]; }
-      ok = __shfl_sync(FULL, ok, g2 & 31);
-      oj = __shfl_sync(FULL, oj, g2 & 31);
-#pragma unroll
-      for (int t = 0; t < KPL; ++t)
-        if (kless(ok, oj, bk[t], bj[t])) rank[t]++;
+    if (lane == 0) {
+      qi.state = 2;
+      qi.p_lo = p_lo;
+      qi.nb = nb;
+      qi.need = L - p_lo;
     }
-    double d2max = 0.0;
-    int jj[KPL], rr[KPL];
-#pragma unroll
-    for (int t = 0; t < KPL; ++t) {
-      int g = t * 32 + lane;
-      jj[t] = INT_MAX;
-      rr[t] = -1;
-      if (g < p_lo) {
-        rr[t] = Lst.r[t];
-        jj[t] = (int)__ldg(&A.pos64[rr[t]].j);
-      } else if (g < p_hi && rank[t] < need) {
-        rr[t] = Lst.r[t];
-        jj[t] = bj[t];
-        d2max = fmax(d2max, bd[t]);
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) d2max = fmax(d2max, __shfl_xor_sync(FULL, d2max, o));
-    write_list<KPL>(A, q, L, jj, rr, lane, sqrt(d2max), P, Q);
     return true;
   }
   return false;
 }
 
 template <int KPL, bool kMixed>
-__global__ void __launch_bounds__(256) k_knn(KnnArgs A) {
-  const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(kWarps * 32) k_knn(KnnArgs A) {
+  __shared__ QInfo info[kWarps][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long q = warp; q < A.N; q += nwarps) {
-    const int b = inst_of(A.off, A.n_inst, q);
-    const GridDev G = A.grid[b];
-    const InstDev P = A.P[b];
-    QueryPos Q;
-    const double2* pp = reinterpret_cast<const double2*>(A.pos64 + q);
-    double2 a = __ldg(pp), c = __ldg(pp + 1);
-    Q.x = a.x; Q.y = a.y; Q.z = c.x;
-    Q.xw = Q.x; Q.yw = Q.y;
-    if (G.box[0] > 0.0) Q.xw = Q.x - G.box[0] * floor((Q.x - G.lo[0]) / G.box[0]);
-    if (G.box[1] > 0.0) Q.yw = Q.y - G.box[1] * floor((Q.y - G.lo[1]) / G.box[1]);
-    Q.ix = axis_cell(G, 0, Q.x);
-    Q.iy = axis_cell(G, 1, Q.y);
-    Q.iz = axis_cell(G, 2, Q.z);
-    if (kMixed) {
-      float4 f = __ldg(A.pos32 + q);
+  const int L = A.K - 1;
+  for (long long base = warp * 32; base < A.N; base += nwarps * 32) {
+    // ---- phase A: per query, warp-cooperative FP32/INT search
+    for (int qi_ = 0; qi_ < 32; ++qi_) {
+      const long long q = base + qi_;
+      if (q >= A.N) break;
+      QInfo& qi = info[w][qi_];
+      const int b = inst_of(A.off, A.n_inst, q);
+      const GridDev& Gd = A.grid[b];
+      Grid32 G;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) { G.cs[a] = Gd.cs32[a]; G.inv[a] = Gd.inv32[a]; G.dim[a] = Gd.dim[a]; }
+      G.per = Gd.periodic != 0;
+      G.cell_off = Gd.cell_off;
+      QueryPos Q;
+      const float4 f = __ldg(A.pos32 + q);
+      const int pk = __float_as_int(f.w);
+      Q.ix = pk & 2047;
+      Q.iy = (pk >> 11) & 2047;
+      Q.iz = (pk >> 22) & 1023;
       Q.fx = f.x; Q.fy = f.y; Q.fz = f.z;
-    } else {
-      Q.fx = Q.fy = Q.fz = 0.f;
+      const double2* pp = reinterpret_cast<const double2*>(A.pos64 + q);
+      const double2 a0 = __ldg(pp), a1 = __ldg(pp + 1);
+      Q.x = a0.x; Q.y = a0.y; Q.z = a1.x;
+      float rho = rho_start(G, A.cstart, Q, L);
+      bool done = false;
+      if (kMixed) done = query_mixed<KPL>(A, G, Gd, Q, q, lane, rho, qi);
+      if (!done) done = query_fp64<KPL>(A, G, Gd, Q, q, lane, rho, qi);
+      if (!done) {
+        // no acceptable radius: keep the row valid (the particle against itself), V = 1
+        int* row = A.nbr + q * (long long)A.K;
+        for (int k = lane; k < A.K; k += 32) row[k] = (int)q;
+        if (lane == 0) {
+          qi.state = 0;
+          A.dist[q] = 0.0;
+          A.V[q] = 1.0;
+          set_status(&A.st[b], GD_ST_KNN);
+        }
+      }
     }
-    double rho = rho_start(G, A.cstart, Q, A.K - 1);
-    bool done = false;
-    if (kMixed) done = query_mixed<KPL>(A, G, P, Q, q, lane, rho);
-    if (!done) query_fp64<KPL>(A, G, P, Q, q, lane, rho, &A.st[b]);
+    __syncwarp();
+    // ---- phase B: lane = query, the FP64 arithmetic
+    {
+      const long long q = base + lane;
+      if (q < A.N) {
+        QInfo& qi = info[w][lane];
+        if (qi.state != 0) {
+          const int b = inst_of(A.off, A.n_inst, q);
+          const GridDev& Gd = A.grid[b];
+          const double2* pp = reinterpret_cast<const double2*>(A.pos64 + q);
+          const double2 a0 = __ldg(pp), a1 = __ldg(pp + 1);
+          double d2max;
+          if (qi.state == 1) {
+            d2max = __longlong_as_double((long long)qi.d2max);
+          } else {
+            // exact FP64 keys of the band, the `need` smallest by (d^2, index)
+            double bd[kBand];
+            long long bj[kBand];
+            for (int t = 0; t < qi.nb; ++t)
+              bd[t] = d2_fp64(A.pos64, qi.band[t], a0.x, a0.y, a1.x, Gd.box[0], Gd.box[1], bj[t]);
+            int* row = A.nbr + q * (long long)A.K;
+            int wr = 1 + qi.p_lo;
+            d2max = 0.0;
+            for (int t = 0; t < qi.nb; ++t) {
+              int rank = 0;
+              for (int u = 0; u < qi.nb; ++u)
+                if (bd[u] < bd[t] || (bd[u] == bd[t] && bj[u] < bj[t])) rank++;
+              if (rank < qi.need) {
+                row[wr++] = qi.band[t];
+                d2max = fmax(d2max, bd[t]);
+              }
+            }
+          }
+          const double d = sqrt(d2max);
+          A.dist[q] = d;
+          A.V[q] = sample_volume(A.P[b], d, a0.x, a0.y);
+        }
+      }
+    }
+    __syncwarp();
+    // ---- phase C: members by ascending caller index
+    for (int qi_ = 0; qi_ < 32; ++qi_) {
+      const long long q = base + qi_;
+      if (q >= A.N) break;
+      if (info[w][qi_].state == 0) continue;
+      int* row = A.nbr + q * (long long)A.K;
+      int jj[KPL], rr[KPL];
+#pragma unroll
+      for (int t = 0; t < KPL; ++t) {
+        const int g = t * 32 + lane;
+        if (g < L) { rr[t] = row[1 + g]; jj[t] = __ldg(&A.perm[rr[t]]); }
+        else { rr[t] = -1; jj[t] = INT_MAX; }
+      }
+      sort_by_index<KPL>(jj, rr, lane);
+#pragma unroll
+      for (int t = 0; t < KPL; ++t) {
+        const int g = t * 32 + lane;
+        if (g < L) row[1 + g] = rr[t];
+      }
+      if (lane == 0) row[0] = (int)q;
+    }
+    __syncwarp();
   }
 }
 
 template <int KPL, bool kMixed>
 static cudaError_t launch_knn_t(gd_ctx* c, const KnnArgs& A) {
-  int bs = c->knn_block;
+  const int bs = kWarps * 32;
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_knn<KPL, kMixed>, bs, 0);
   if (per_sm < 1) per_sm = 1;
-  long long want = (A.N * 32 + bs - 1) / bs;
+  long long chunks = (A.N + 31) / 32;
+  long long want = (chunks + kWarps - 1) / kWarps;
   long long blocks = (long long)c->num_sms * per_sm;
   if (blocks > want) blocks = want;
   if (blocks < 1) blocks = 1;
@@ -582,12 +621,13 @@ cudaError_t launch_knn(gd_ctx* c) {
   A.cstart = c->d_cell_start;
   A.pos64 = c->d_pos64;
   A.pos32 = c->d_pos32;
+  A.perm = c->d_perm;
   A.nbr = c->d_nbr;
   A.dist = c->d_dist;
   A.V = c->d_V;
   A.st = c->d_state;
-  bool mixed = c->precision == GD_MIXED;
-  int kpl = (c->K + 31) / 32;   // room for K-1 members and at least one band slot
+  const bool mixed = c->precision == GD_MIXED;
+  const int kpl = (c->K + 31) / 32;   // room for K-1 members and at least one band slot
   time_begin(c, 1);
   cudaError_t e;
   if (kpl <= 1) e = mixed ? launch_knn_t<1, true>(c, A) : launch_knn_t<1, false>(c, A);

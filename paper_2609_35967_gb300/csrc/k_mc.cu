@@ -77,21 +77,48 @@ __device__ __forceinline__ Fixed make_fixed(const InstDev& P, const Gas& g, doub
   return f;
 }
 
-// Query of a live particle (s, m) from the fixed part; all lanes compute it alike.
+// Query of a live particle (s, m) from the fixed part.  FP64 form: FP64 throughout; mixed
+// form: FP32 from the rounded s, m and gst (the rate kernel and the sampler build it with
+// this one function, so both see the same pair rates).
 template <typename T>
 __device__ __forceinline__ Query<T> live_query(const Fixed& f, double s, double m) {
   Query<T> q;
-  double St = f.gst * s;
-  q.s = (T)s; q.m = (T)m; q.inv_m = (T)(1.0 / m);
-  q.St = (T)St;
-  q.ai = (T)(St / (1.0 + St * St));
-  q.bi = (T)(1.0 / (1.0 + St * St));
-  q.hi = (T)(St < 0.5 ? St : 0.5);
+  if constexpr (sizeof(T) == 8) {
+    double St = f.gst * s;
+    q.s = s; q.m = m; q.inv_m = 1.0 / m;
+    q.St = St;
+    q.ai = St / (1.0 + St * St);
+    q.bi = 1.0 / (1.0 + St * St);
+    q.hi = St < 0.5 ? St : 0.5;
+  } else {
+    const float sf = (float)s, mf = (float)m, St = (float)f.gst * sf;
+    const float bi = 1.0f / (1.0f + St * St);
+    q.s = sf; q.m = mf; q.inv_m = 1.0f / mf;
+    q.St = St;
+    q.ai = St * bi;
+    q.bi = bi;
+    q.hi = St < 0.5f ? St : 0.5f;
+  }
   q.g = (T)f.gst;
   q.e2 = (T)f.e2; q.e1 = (T)f.e1; q.zo = (T)f.zo;
   q.cs = (T)f.cs; q.cB = (T)f.cB; q.Vg2 = (T)f.Vg2; q.tRe = (T)f.tRe;
   q.vfrag = (T)f.vfrag; q.m0 = (T)f.m0;
   q.mode = f.mode;
+  return q;
+}
+
+template <typename T>
+__device__ __forceinline__ Query<T> shfl_query(const Query<T>& a, int src) {
+  Query<T> q;
+  q.s = __shfl_sync(FULLM, a.s, src); q.m = __shfl_sync(FULLM, a.m, src);
+  q.inv_m = __shfl_sync(FULLM, a.inv_m, src); q.St = __shfl_sync(FULLM, a.St, src);
+  q.ai = __shfl_sync(FULLM, a.ai, src); q.bi = __shfl_sync(FULLM, a.bi, src);
+  q.hi = __shfl_sync(FULLM, a.hi, src); q.g = __shfl_sync(FULLM, a.g, src);
+  q.e2 = __shfl_sync(FULLM, a.e2, src); q.e1 = __shfl_sync(FULLM, a.e1, src);
+  q.zo = __shfl_sync(FULLM, a.zo, src); q.cs = __shfl_sync(FULLM, a.cs, src);
+  q.cB = __shfl_sync(FULLM, a.cB, src); q.Vg2 = __shfl_sync(FULLM, a.Vg2, src);
+  q.tRe = __shfl_sync(FULLM, a.tRe, src); q.vfrag = __shfl_sync(FULLM, a.vfrag, src);
+  q.m0 = __shfl_sync(FULLM, a.m0, src); q.mode = __shfl_sync(FULLM, a.mode, src);
   return q;
 }
 
@@ -191,15 +218,16 @@ __global__ void __launch_bounds__(256) k_rates(McArgs A) {
       fx.mode = 0;
     }
     double my_tot = 0.0, my_a = 0.0, my_b = 0.0;
+    const Query<T> myq = live_query<T>(fx, s_i, m_i);     // lane = particle
+    const T myj1 = (T)fj1, myj2 = (T)fj2;
+    const double mypref = fx.pref;
     unsigned vmask = __ballot_sync(FULLM, valid);
     while (vmask) {
       const int p = __ffs(vmask) - 1;
       vmask &= vmask - 1;
       const long long rp = base + p;
-      const Fixed f = shfl_fixed(fx, p);
-      const double sp = __shfl_sync(FULLM, s_i, p), mp = __shfl_sync(FULLM, m_i, p);
-      const T j1 = (T)__shfl_sync(FULLM, fj1, p), j2 = (T)__shfl_sync(FULLM, fj2, p);
-      const Query<T> q = live_query<T>(f, sp, mp);
+      const T j1 = __shfl_sync(FULLM, myj1, p), j2 = __shfl_sync(FULLM, myj2, p);
+      const Query<T> q = shfl_query<T>(myq, p);
       const int* row = A.nbr + rp * A.K;
       T c0[S], c1[S];
       int jr[S];
@@ -221,13 +249,14 @@ __global__ void __launch_bounds__(256) k_rates(McArgs A) {
       else { sa = (double)warp_sumf(la); sb = (double)warp_sumf(lb); }
       if (lane == p) { my_tot = tot; my_a = sa; my_b = sb; }
       if (A.chan_out) {
-        long long ci = (long long)A.perm[rp] * A.K;
+        const long long ci = (long long)A.perm[rp] * A.K;
+        const double pf = __shfl_sync(FULLM, mypref, p);
 #pragma unroll
         for (int t = 0; t < S; ++t) {
           int k = lane * S + t;
           if (k < A.K) {
-            A.chan_out[(ci + k) * 2] = f.pref * (double)c0[t];
-            A.chan_out[(ci + k) * 2 + 1] = f.pref * (double)c1[t];
+            A.chan_out[(ci + k) * 2] = pf * (double)c0[t];
+            A.chan_out[(ci + k) * 2 + 1] = pf * (double)c1[t];
           }
         }
       }
