@@ -236,6 +236,41 @@ gd_status gd_run_intervals(gd_ctx* ctx, int32_t n, int32_t push);
 /* Static string for a gd_status code. */
 const char* gd_status_string(gd_status code);
 
+/* ---------------------------------------------------------------------------
+ * No-allocation neighbour search (this entry point has no counterpart in the
+ * paper; it is a service to callers).
+ *
+ * For callers that cannot allocate device memory at run time: a host program
+ * that has already reserved the GPU's memory for its own pool, or a
+ * latency-bound loop that cannot take cudaMalloc's implicit synchronisation.
+ * gd_neighbors_fixed calls no cudaMalloc, cudaFree or allocating library
+ * routine.  Its scratch is one fixed device array of GD_FIXED_SCRATCH_BYTES
+ * bytes inside libgd.so, which every GPU that loads the library holds until
+ * the process exits.
+ *
+ * It computes, for ONE instance, the lists gd_build_neighbors would return
+ * (FP64 keys, minimum image in a patch): nbr_out row i = i, then the K-1
+ * nearest others by (d^2, index) in ascending index order; d_out[i] = distance
+ * to the farthest of them.  x, y, z: DEVICE [n]; nbr_out: DEVICE int32 [n*K];
+ * d_out: DEVICE [n] or NULL; params: HOST, only geometry, box_x, box_y and
+ * cell_size are read; stream: cudaStream_t (NULL = legacy default stream).
+ *
+ * Limits: n <= GD_FIXED_MAX_PARTICLES (else GD_ERR_CAPACITY, nothing runs),
+ * 2 <= K <= GD_FIXED_MAX_K and K <= n (else GD_ERR_ARG).
+ * The first call on a device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls share the one array, which keeps the last call's
+ * contents (each call clears what must start at zero): calls that overlap on
+ * the GPU -- on different streams, or from different threads -- race, so
+ * serialise them.  Asynchronous on the stream like the other calls.
+ * ------------------------------------------------------------------------- */
+#define GD_FIXED_MAX_PARTICLES 65536
+#define GD_FIXED_MAX_K 64
+#define GD_FIXED_SCRATCH_BYTES 4719360
+gd_status gd_neighbors_fixed(const double* x, const double* y, const double* z, int64_t n,
+                             int32_t K, const gd_instance_params* params, int32_t* nbr_out,
+                             double* d_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

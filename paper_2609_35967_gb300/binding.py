@@ -73,6 +73,8 @@ SIGNATURES = {
     "gd_stats": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "gd_run_intervals": ([C.c_void_p, C.c_int32, C.c_int32], C.c_int),
     "gd_status_string": ([C.c_int], C.c_char_p),
+    "gd_neighbors_fixed": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p,
+                            C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
 }
 
 _lib = None
@@ -152,6 +154,13 @@ def gd_run_intervals(ctx, n, push=False):
 
 def gd_status_string(code):
     return load().gd_status_string(int(code)).decode()
+
+
+def gd_neighbors_fixed(x, y, z, n, K, params: InstanceParams, nbr_out, d_out=0, stream=0):
+    """Neighbour lists of one instance without device allocation (see include/gd.h)."""
+    return _check("gd_neighbors_fixed",
+                  load().gd_neighbors_fixed(x, y, z, int(n), int(K), C.byref(params), nbr_out,
+                                            d_out or None, stream or None))
 
 
 # ------------------------------------------------------------------ convenience wrapper

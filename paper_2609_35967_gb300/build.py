@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libgd.so")
-SOURCES = ["gd_abi.cu", "k_cells.cu", "k_knn.cu", "k_mc.cu", "k_misc.cu"]
+SOURCES = ["gd_abi.cu", "k_cells.cu", "k_knn.cu", "k_mc.cu", "k_misc.cu", "gd_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC",
                 "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
