@@ -143,7 +143,8 @@ def run_gpu(args, rank, world):
 
     def measure(precision, steps, warmup, timing):
         sess = gd.Session(insts, precision=precision, device=str(dev), velocities=push,
-                          flags=gd.GD_FLAG_TIMING if timing else 0)
+                          flags=gd.GD_FLAG_TIMING if timing else 0, cell_factor=args.cell_factor)
+        cf = args.cell_factor if args.cell_factor > 0 else sess.autotune()
         st = sess.stream
 
         def step():
@@ -172,11 +173,11 @@ def run_gpu(args, rank, world):
         ms = e0.elapsed_time(e1)
         ck = clocks.stop()
         post = sess.stats()
-        res = {"ms": ms, "clocks": ck, "launches": post["launches"] - pre["launches"],
+        res = {"ms": ms, "clocks": ck, "launches": post["launches"] - pre["launches"] - 1,
                "kernel_ms": {k: post["kernel_ms"][k] - pre["kernel_ms"][k] for k in post["kernel_ms"]},
                "kernel_calls": {k: post["kernel_calls"][k] - pre["kernel_calls"][k]
                                 for k in post["kernel_calls"]},
-               "events": post["events"] - pre["events"], "status": post["status"]}
+               "events": post["events"] - pre["events"], "status": post["status"], "cell_factor": cf}
         sess.close()
         return res
 
@@ -188,7 +189,8 @@ def run_gpu(args, rank, world):
     # end to end through the C ABI with host buffers: H2D of the step's inputs from
     # pinned memory and D2H of the diameters inside the timed region, every step
     cat = W.concat(insts)
-    sess = gd.Session(insts, precision=gd.GD_MIXED, device=str(dev), velocities=push)
+    sess = gd.Session(insts, precision=gd.GD_MIXED, device=str(dev), velocities=push,
+                      cell_factor=mixed["cell_factor"])
     host = {k: torch.as_tensor(cat[k]).pin_memory() for k in ("x", "y", "z", "s", "M")}
     s_back = torch.empty(N, dtype=torch.float64).pin_memory()
     st = sess.stream
@@ -260,6 +262,8 @@ def main():
     ap.add_argument("--workload", default="disk22")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--cell-factor", type=float, default=0.0,
+                    help="cell edge factor; 0 = pick it with gd_autotune")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -314,12 +318,14 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
         "config": dict(r["cfg"], n_particles=N, K=K, precision="mixed",
                        l2="no flush: working set > 129 MB L2 (lists alone 4K B/particle)",
-                       parallelism=f"{world} independent replicas" if world > 1 else "1 GPU"),
+                       parallelism=f"{world} independent replicas" if world > 1 else "1 GPU",
+                       cell_factor=r["mixed"]["cell_factor"]),
+        "events_per_step": r["mixed"]["events"] / args.steps,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": r["hbm"], "unit": "GB/s",
                      "frac": ach / r["hbm"], "traffic": None,
                      "peak_kind": r["peak_kind"],
                      "algo_bytes_per_particle": algo_bytes(dom, K, True)},
-        "kernels_ms_per_step": {k: v / args.steps for k, v in km.items() if v > 0},
+        "kernels_ms_per_step": {k: v / args.steps for k, v in km.items() if v > 0 and k != "stats"},
         "gpu_launches": r["mixed"]["launches"],
         "clocks": r["mixed"]["clocks"],
         "e2e": {"value": world * N * args.steps / (ms_e2e * 1e-3), "unit": UNIT,
@@ -328,7 +334,9 @@ def main():
     if r["fp64"]:
         st = max(1, args.steps // 3)
         out["fp64"] = {"value": world * N * st / (ms_fp64 * 1e-3), "ms_per_step": ms_fp64 / st,
-                       "kernels_ms_per_step": {k: v / st for k, v in r["fp64"]["kernel_ms"].items() if v > 0}}
+                       "cell_factor": r["fp64"]["cell_factor"],
+                       "kernels_ms_per_step": {k: v / st for k, v in r["fp64"]["kernel_ms"].items()
+                                               if v > 0 and k != "stats"}}
         out["mixed_over_fp64"] = out["value"] / out["fp64"]["value"]
     if world == 1 and not args.skip_cpu:
         insts, _ = make_workload(args.workload, 0)

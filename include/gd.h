@@ -233,6 +233,16 @@ gd_status gd_stats(gd_ctx* ctx, gd_stats_t* out, gd_instance_stats* inst_out);
  * (captures again if the arguments change).  Asynchronous. */
 gd_status gd_run_intervals(gd_ctx* ctx, int32_t n, int32_t push);
 
+/* Autotuner: times the cell binning and neighbour search (gd_build_neighbors'
+ * kernels) on the current positions for a set of cell sizes -- the edge is
+ * factor * (V_box / N)^(1/3) for factor in {0.4, 0.5, ..., 1.4} -- with CUDA
+ * events, and keeps the fastest factor for the context (instances with an
+ * explicit cell_size keep it).  Results never depend on the choice: the lists
+ * are exact for any cell size.  Synchronises the stream; call it before
+ * gd_run_intervals captures its graph.  Leaves the context ready for
+ * gd_build_neighbors.  factor_out: HOST or NULL, receives the chosen factor. */
+gd_status gd_autotune(gd_ctx* ctx, double* factor_out);
+
 /* Static string for a gd_status code. */
 const char* gd_status_string(gd_status code);
 

@@ -73,6 +73,7 @@ SIGNATURES = {
     "gd_stats": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "gd_run_intervals": ([C.c_void_p, C.c_int32, C.c_int32], C.c_int),
     "gd_status_string": ([C.c_int], C.c_char_p),
+    "gd_autotune": ([C.c_void_p, C.c_void_p], C.c_int),
     "gd_neighbors_fixed": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p,
                             C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
 }
@@ -150,6 +151,12 @@ def gd_stats(ctx, n_instances):
 
 def gd_run_intervals(ctx, n, push=False):
     return _check("gd_run_intervals", load().gd_run_intervals(ctx, int(n), 1 if push else 0))
+
+
+def gd_autotune(ctx):
+    f = C.c_double(0.0)
+    _check("gd_autotune", load().gd_autotune(ctx, C.byref(f)))
+    return f.value
 
 
 def gd_status_string(code):
@@ -269,6 +276,9 @@ class Session:
 
     def run_intervals(self, n, push=False):
         gd_run_intervals(self.ctx, n, push)
+
+    def autotune(self):
+        return gd_autotune(self.ctx)
 
     def stats(self, check=True):
         code, st, inst = gd_stats(self.ctx, self.n_inst)

@@ -361,6 +361,42 @@ extern "C" gd_status gd_stats(gd_ctx* c, gd_stats_t* out, gd_instance_stats* ins
   return GD_OK;
 }
 
+extern "C" gd_status gd_autotune(gd_ctx* c, double* factor_out) {
+  if (!c) return GD_ERR_ARG;
+  if (c->phase != 0 && c->phase != 1) return GD_ERR_STATE;
+  static const double kFactors[] = {0.4, 0.5, 0.6, 0.7, 0.8, 0.9, 1.0, 1.2, 1.4};
+  const int saved_flags = c->flags;
+  c->flags &= ~GD_FLAG_TIMING;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) { c->flags = saved_flags; return GD_ERR_CUDA; }
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); c->flags = saved_flags; return GD_ERR_CUDA; }
+  double best = c->cell_factor;
+  float best_ms = 1e30f;
+  gd_status st = GD_OK;
+  for (double f : kFactors) {
+    c->cell_factor = f;
+    cudaError_t e = launch_cells(c);                  // warm-up: grid and lists for this size
+    if (e == cudaSuccess) e = launch_knn(c);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+    if (e == cudaSuccess) e = launch_cells(c);
+    if (e == cudaSuccess) e = launch_knn(c);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) { st = GD_ERR_CUDA; break; }
+    if (ms < best_ms) { best_ms = ms; best = f; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->flags = saved_flags;
+  c->cell_factor = best;
+  c->phase = 0;
+  if (c->graph_exec) { cudaGraphExecDestroy(c->graph_exec); c->graph_exec = nullptr; c->graph_push = -1; }
+  if (factor_out) *factor_out = best;
+  return st;
+}
+
 extern "C" const char* gd_status_string(gd_status code) {
   switch (code) {
     case GD_OK: return "ok";

@@ -28,7 +28,6 @@ namespace gd {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kBand = 8;          // band entries resolved in phase B per query
-constexpr int kWarps = 8;         // warps per block
 
 struct KnnArgs {
   long long N;
@@ -54,49 +53,6 @@ template <typename KT>
 __device__ __forceinline__ bool kless(KT ka, int ja, KT kb, int jb) {
   return ka < kb || (ka == kb && ja < jb);
 }
-
-// Sorted list of 32*KPL (key, tie index, rank) entries spread over the warp.
-template <int KPL, typename KT>
-struct TopList {
-  KT k[KPL];
-  int j[KPL];
-  int r[KPL];
-
-  __device__ __forceinline__ void reset() {
-#pragma unroll
-    for (int t = 0; t < KPL; ++t) { k[t] = kmax_<KT>(); j[t] = INT_MAX; r[t] = -1; }
-  }
-  __device__ __forceinline__ void get(int g, KT& kk, int& jj) const {
-    KT kv = k[0];
-    int jv = j[0];
-#pragma unroll
-    for (int t = 1; t < KPL; ++t)
-      if (t == (g >> 5)) { kv = k[t]; jv = j[t]; }
-    kk = __shfl_sync(FULL, kv, g & 31);
-    jj = __shfl_sync(FULL, jv, g & 31);
-  }
-  __device__ __forceinline__ void insert(KT nk, int nj, int nr, int lane) {
-    int p = 0;
-#pragma unroll
-    for (int t = 0; t < KPL; ++t) p += __popc(__ballot_sync(FULL, kless(k[t], j[t], nk, nj)));
-#pragma unroll
-    for (int t = KPL - 1; t >= 0; --t) {
-      KT uk = __shfl_up_sync(FULL, k[t], 1);
-      int uj = __shfl_up_sync(FULL, j[t], 1);
-      int ur = __shfl_up_sync(FULL, r[t], 1);
-      if (t > 0) {
-        const int tp = t > 0 ? t - 1 : 0;
-        KT ck = __shfl_sync(FULL, k[tp], 31);
-        int cj = __shfl_sync(FULL, j[tp], 31);
-        int cr = __shfl_sync(FULL, r[tp], 31);
-        if (lane == 0) { uk = ck; uj = cj; ur = cr; }
-      }
-      int g = t * 32 + lane;
-      if (g > p) { k[t] = uk; j[t] = uj; r[t] = ur; }
-      else if (g == p) { k[t] = nk; j[t] = nj; r[t] = nr; }
-    }
-  }
-};
 
 // Bitonic sort of 32*KPL (j, r) pairs by j, element e = t*32 + lane.
 template <int KPL>
@@ -186,12 +142,15 @@ __device__ __forceinline__ int floordiv(int a, int d) {
   return (a % d != 0 && ((a < 0) != (d < 0))) ? q - 1 : q;
 }
 
-// Visits the stored rank ranges [ra, rb) of every cell row within rs of the query:
-// visit(ra, rb, x_shift_cells, dy_cells, dz_cells).  Returns true when a periodic axis
-// was covered whole (the FP32 cell offsets are then ambiguous).
+// Candidate ranks of every cell row within rs of the query, in 32-wide batches flattened
+// across rows.  Rows are set up one per lane (their cell_start loads are in flight
+// together), a warp scan lays the rows' rank ranges end to end, and each lane of a batch
+// finds its row by a binary search over the lanes.  visit(valid, r, x_shift_cells,
+// dy_cells, dz_cells) sees every candidate once.  Returns true when a periodic axis was
+// covered whole (the FP32 cell offsets are then ambiguous).
 template <class F>
 __device__ __forceinline__ bool scan_ball(const Grid32& G, const int* __restrict__ cstart, const QueryPos& Q,
-                                          float rs, F&& visit) {
+                                          float rs, int lane, F&& visit) {
   bool amb = false;
   int lz, hz, ly, hy;
   bool fz, fy;
@@ -200,54 +159,76 @@ __device__ __forceinline__ bool scan_ball(const Grid32& G, const int* __restrict
   if (fy && G.per) amb = true;
   const float rs2 = rs * rs * 1.00002f;
   const int dimx = G.dim[0], dimy = G.dim[1];
-  for (int iz = lz; iz <= hz; ++iz) {
-    const float dz = slab_dist32(G, 2, Q.iz, Q.fz, iz);
-    if (dz * dz > rs2) continue;
-    for (int iyu = ly; iyu <= hy; ++iyu) {
+  const int ny = hy - ly + 1, nz = hz - lz + 1;
+  const int nrows = (ny > 0 && nz > 0) ? ny * nz : 0;
+  for (int r0 = 0; r0 < nrows; r0 += 32) {
+    const int row = r0 + lane;
+    int ra0 = 0, c0 = 0, ra1 = 0, c1 = 0, sh0 = 0, sh1 = 0, dyc = 0, dzc = 0;
+    bool rowamb = false;
+    if (row < nrows) {
+      const int iz = lz + row / ny, iyu = ly + row % ny;
+      const float dz = slab_dist32(G, 2, Q.iz, Q.fz, iz);
       const float dy = fy ? 0.0f : slab_dist32(G, 1, Q.iy, Q.fy, iyu);
       const float dyz2 = dy * dy + dz * dz;
-      if (dyz2 > rs2) continue;
-      int iy = iyu;
-      if (G.per) { iy %= dimy; if (iy < 0) iy += dimy; }
-      const float xr = sqrtf(fmaxf(rs2 - dyz2, 0.0f));
-      int lx, hx;
-      bool fx;
-      axis_range32(G, 0, Q.ix, Q.fx, xr, lx, hx, fx);
-      if (lx > hx) continue;
-      if (fx && G.per) amb = true;
-      const long long rowc = G.cell_off + (long long)dimx * (iy + (long long)dimy * iz);
-      int kx = 0, a0 = lx, e0 = hx;
-      if (G.per && !fx) {
-        kx = floordiv(lx, dimx);
-        a0 = lx - kx * dimx;
-        e0 = hx - kx * dimx;
+      if (dyz2 <= rs2) {
+        int iy = iyu;
+        if (G.per) { iy %= dimy; if (iy < 0) iy += dimy; }
+        const float xr = sqrtf(fmaxf(rs2 - dyz2, 0.0f));
+        int lx, hx;
+        bool fx;
+        axis_range32(G, 0, Q.ix, Q.fx, xr, lx, hx, fx);
+        if (lx <= hx) {
+          if (fx && G.per) rowamb = true;
+          const long long rowc = G.cell_off + (long long)dimx * (iy + (long long)dimy * iz);
+          int kx = 0, a0 = lx, e0 = hx;
+          if (G.per && !fx) {
+            kx = floordiv(lx, dimx);
+            a0 = lx - kx * dimx;
+            e0 = hx - kx * dimx;
+          }
+          const int e1 = e0 < dimx ? e0 : dimx - 1;
+          ra0 = __ldg(&cstart[rowc + a0]);
+          c0 = __ldg(&cstart[rowc + e1 + 1]) - ra0;
+          sh0 = kx * dimx;
+          if (e0 >= dimx) {
+            ra1 = __ldg(&cstart[rowc]);
+            c1 = __ldg(&cstart[rowc + (e0 - dimx) + 1]) - ra1;
+            sh1 = (kx + 1) * dimx;
+          }
+          dyc = iyu - Q.iy;
+          dzc = iz - Q.iz;
+        }
       }
-      const int e1 = e0 < dimx ? e0 : dimx - 1;
-      visit(__ldg(&cstart[rowc + a0]), __ldg(&cstart[rowc + e1 + 1]), kx * dimx, iyu - Q.iy, iz - Q.iz);
-      if (e0 >= dimx)
-        visit(__ldg(&cstart[rowc]), __ldg(&cstart[rowc + (e0 - dimx) + 1]), (kx + 1) * dimx,
-              iyu - Q.iy, iz - Q.iz);
+    }
+    if (__any_sync(FULL, rowamb)) amb = true;
+    const int cnt = c0 + c1;
+    int inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(FULL, inc, o);
+      if (lane >= o) inc += t;
+    }
+    const int excl = inc - cnt;
+    const int total = __shfl_sync(FULL, inc, 31);
+    for (int f0 = 0; f0 < total; f0 += 32) {
+      const int f = f0 + lane;
+      int o = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int c = o + step;
+        const int ex = __shfl_sync(FULL, excl, c & 31);
+        if (c < 32 && ex <= f) o = c;
+      }
+      const int oex = __shfl_sync(FULL, excl, o), oc0 = __shfl_sync(FULL, c0, o);
+      const int ora0 = __shfl_sync(FULL, ra0, o), ora1 = __shfl_sync(FULL, ra1, o);
+      const int osh0 = __shfl_sync(FULL, sh0, o), osh1 = __shfl_sync(FULL, sh1, o);
+      const int ody = __shfl_sync(FULL, dyc, o), odz = __shfl_sync(FULL, dzc, o);
+      const int loc = f - oex;
+      const bool first = loc < oc0;
+      visit(f < total, first ? ora0 + loc : ora1 + (loc - oc0), first ? osh0 : osh1, ody, odz);
     }
   }
   return amb;
-}
-
-// Offers one candidate per lane; lanes below the threshold are inserted in lane order.
-template <int KPL, typename KT, class R>
-__device__ __forceinline__ void offer(TopList<KPL, KT>& Lst, KT ck, int cj, int cr, KT& wk, int& wj,
-                                      int lane, R&& refresh) {
-  unsigned m = __ballot_sync(FULL, kless(ck, cj, wk, wj));
-  while (m) {
-    const int src = __ffs(m) - 1;
-    m &= m - 1;
-    const KT nk = __shfl_sync(FULL, ck, src);
-    const int nj = __shfl_sync(FULL, cj, src);
-    const int nr = __shfl_sync(FULL, cr, src);
-    if (kless(nk, nj, wk, wj)) {
-      Lst.insert(nk, nj, nr, lane);
-      refresh();
-    }
-  }
 }
 
 __device__ __forceinline__ double sample_volume(const InstDev& P, double d, double x, double y) {
@@ -263,26 +244,32 @@ __device__ __forceinline__ double sample_volume(const InstDev& P, double d, doub
   return V;
 }
 
+// Radius estimate from the particle count of the 27 cells around the query (lane c < 27
+// loads cell c, so the loads are in flight together).
 __device__ __forceinline__ float rho_start(const Grid32& G, const int* __restrict__ cstart, const QueryPos& Q,
-                                           int L) {
+                                           int L, int lane) {
   int n = 0, nc = 0;
-  for (int dz = -1; dz <= 1; ++dz) {
-    int iz = Q.iz + dz;
-    if (iz < 0 || iz >= G.dim[2]) continue;
-    for (int dy = -1; dy <= 1; ++dy) {
-      int iy = Q.iy + dy;
-      if (G.per) { iy %= G.dim[1]; if (iy < 0) iy += G.dim[1]; }
-      else if (iy < 0 || iy >= G.dim[1]) continue;
-      int x0 = Q.ix - 1, x1 = Q.ix + 1;
-      if (!G.per) { x0 = x0 < 0 ? 0 : x0; x1 = x1 >= G.dim[0] ? G.dim[0] - 1 : x1; }
-      for (int ix = x0; ix <= x1; ++ix) {
-        int xw = ix;
-        if (G.per) { xw %= G.dim[0]; if (xw < 0) xw += G.dim[0]; }
-        long long c = G.cell_off + xw + (long long)G.dim[0] * (iy + (long long)G.dim[1] * iz);
-        n += __ldg(&cstart[c + 1]) - __ldg(&cstart[c]);
-        ++nc;
-      }
+  if (lane < 27) {
+    const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+    int ix = Q.ix + dx, iy = Q.iy + dy;
+    const int iz = Q.iz + dz;
+    bool ok = iz >= 0 && iz < G.dim[2];
+    if (G.per) {
+      ix %= G.dim[0]; if (ix < 0) ix += G.dim[0];
+      iy %= G.dim[1]; if (iy < 0) iy += G.dim[1];
+    } else {
+      ok = ok && ix >= 0 && ix < G.dim[0] && iy >= 0 && iy < G.dim[1];
     }
+    if (ok) {
+      const long long c = G.cell_off + ix + (long long)G.dim[0] * (iy + (long long)G.dim[1] * iz);
+      n = __ldg(&cstart[c + 1]) - __ldg(&cstart[c]);
+      nc = 1;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    n += __shfl_xor_sync(FULL, n, o);
+    nc += __shfl_xor_sync(FULL, nc, o);
   }
   const float csmax = fmaxf(G.cs[0], fmaxf(G.cs[1], G.cs[2]));
   if (n <= 1) return 2.0f * csmax;
@@ -322,156 +309,202 @@ struct QInfo {
   int band[kBand];
 };
 
-// FP64-key search for one query (the plain form, and the fallback of the mixed form).
-// Writes the unsorted members to the row and the (K-1)-th d^2; returns false on failure.
-template <int KPL>
-__device__ bool query_fp64(const KnnArgs& A, const Grid32& G, const GridDev& Gd, const QueryPos& Q, long long q,
-                           int lane, float rho, QInfo& qi) {
-  const int L = A.K - 1;
-  TopList<KPL, unsigned long long> Lst;
-  const double bx = Gd.box[0], by = Gd.box[1];
-  const float diag = sqrtf((float)G.dim[0] * G.dim[0] * G.cs[0] * G.cs[0] +
-                           (float)G.dim[1] * G.dim[1] * G.cs[1] * G.cs[1] +
-                           (float)G.dim[2] * G.dim[2] * G.cs[2] * G.cs[2]);
-  for (int att = 0; att < 64; ++att) {
-    Lst.reset();
-    unsigned long long wk = ~0ull;
-    int wj = INT_MAX;
-    const double rho2 = (double)rho * (double)rho;
-    auto refresh = [&]() { Lst.get(L - 1, wk, wj); };
-    scan_ball(G, A.cstart, Q, rho, [&](int ra, int rb, int, int, int) {
-      for (int base = ra; base < rb; base += 32) {
-        const int r = base + lane;
-        unsigned long long ck = ~0ull;
-        int cj = INT_MAX;
-        if (r < rb && r != (int)q) {
-          long long jj;
-          const double d2 = d2_fp64(A.pos64, r, Q.x, Q.y, Q.z, bx, by, jj);
-          if (d2 <= rho2) { ck = (unsigned long long)__double_as_longlong(d2); cj = (int)jj; }
-        }
-        offer(Lst, ck, cj, r, wk, wj, lane, refresh);
-      }
-    });
-    unsigned long long kL;
-    int jL;
-    Lst.get(L - 1, kL, jL);
-    if (kL != ~0ull) {
-      int* row = A.nbr + q * (long long)A.K;
+// Candidates inside the search ball of one query, in shared memory (per warp).
+template <int KB>
+struct CandBuf {
+  unsigned long long key[32 * KB];   // FP64 form: bits of d^2; mixed: bits of the FP32 D
+  int j[32 * KB];                    // tie index: caller index (FP64) or rank (mixed)
+  int r[32 * KB];
+};
+
+// Compare-exchange of register pairs (t, t ^ RS) inside each lane, block direction from
+// the element index e = t*32 + lane.
+template <int RS, int KB>
+__device__ __forceinline__ void cas_regs(int nreg, int kk, unsigned long long (&k)[KB], int (&j)[KB],
+                                         int (&r)[KB], int lane) {
 #pragma unroll
-      for (int t = 0; t < KPL; ++t) {
-        int g = t * 32 + lane;
-        if (g < L) row[1 + g] = Lst.r[t];
+  for (int t = 0; t < KB; ++t) {
+    const int tp = t ^ RS;
+    if (tp > t && tp < KB && t < nreg && tp < nreg) {
+      const bool up = ((t * 32 + lane) & kk) == 0;
+      const bool gt = kless(k[tp], j[tp], k[t], j[t]);
+      if (up == gt) {
+        unsigned long long a = k[t]; k[t] = k[tp]; k[tp] = a;
+        int c = j[t]; j[t] = j[tp]; j[tp] = c;
+        c = r[t]; r[t] = r[tp]; r[tp] = c;
       }
-      if (lane == 0) { qi.state = 1; qi.d2max = kL; }
-      return true;
     }
-    int found = 0;
-#pragma unroll
-    for (int t = 0; t < KPL; ++t) found += __popc(__ballot_sync(FULL, Lst.k[t] != ~0ull));
-    if (rho > 2.0f * diag) break;
-    rho = grow(rho, found, L);
   }
-  return false;
 }
 
-// FP32-key search with the FP64 band; returns false when the query needs the FP64 form.
-template <int KPL>
-__device__ bool query_mixed(const KnnArgs& A, const Grid32& G, const GridDev& Gd, const QueryPos& Q, long long q,
-                            int lane, float& rho, QInfo& qi) {
+// Bitonic sort, ascending by (key, j), of the first 32*nreg register entries (nreg a power
+// of two <= KB).  The stage loops run at run time and only the per-register bodies are
+// unrolled, which keeps the code small (the search is otherwise instruction-cache bound).
+template <int KB>
+__device__ __forceinline__ void sort_cand(int nreg, unsigned long long (&k)[KB], int (&j)[KB], int (&r)[KB],
+                                          int lane) {
+  const int S = 32 * nreg;
+#pragma unroll 1
+  for (int kk = 2; kk <= S; kk <<= 1) {
+#pragma unroll 1
+    for (int s = kk >> 1; s > 0; s >>= 1) {
+      if (s >= 32) {
+        const int rs = s >> 5;
+        if (rs == 1) cas_regs<1, KB>(nreg, kk, k, j, r, lane);
+        else if (rs == 2) cas_regs<2, KB>(nreg, kk, k, j, r, lane);
+        else if (rs == 4) cas_regs<4, KB>(nreg, kk, k, j, r, lane);
+        else if (rs == 8) cas_regs<8, KB>(nreg, kk, k, j, r, lane);
+        else cas_regs<16, KB>(nreg, kk, k, j, r, lane);
+      } else {
+        const bool lower = (lane & s) == 0;
+#pragma unroll
+        for (int t = 0; t < KB; ++t) {
+          if (t < nreg) {
+            const unsigned long long pk = __shfl_xor_sync(FULL, k[t], s);
+            const int pj = __shfl_xor_sync(FULL, j[t], s);
+            const int pr = __shfl_xor_sync(FULL, r[t], s);
+            const bool up = ((t * 32 + lane) & kk) == 0;
+            const bool pless = kless(pk, pj, k[t], j[t]);
+            const bool pgreater = kless(k[t], j[t], pk, pj);
+            if ((lower == up) ? pless : pgreater) { k[t] = pk; j[t] = pj; r[t] = pr; }
+          }
+        }
+      }
+    }
+  }
+}
+
+template <int KB>
+__device__ __forceinline__ void sort_any(int n, unsigned long long (&k)[KB], int (&j)[KB], int (&r)[KB], int lane) {
+  int nreg = 1;
+  while (32 * nreg < n && nreg < KB) nreg <<= 1;
+  sort_cand<KB>(nreg, k, j, r, lane);
+}
+
+template <typename KT, int KB>
+__device__ __forceinline__ void get_entry(const unsigned long long (&k)[KB], int g, unsigned long long& out) {
+  unsigned long long v = k[0];
+#pragma unroll
+  for (int t = 1; t < KB; ++t)
+    if (t == (g >> 5)) v = k[t];
+  out = __shfl_sync(FULL, v, g & 31);
+}
+
+// Search of one query.  Candidates inside rho go to the warp's buffer, are sorted, and
+// the K-1 nearest taken; FP64 form: exact keys, the members and the (K-1)-th d^2 are
+// final; mixed form: certain members and the FP64 band are left to phase B.  Returns
+// false when the query must be redone (mixed: in the FP64 form; FP64: failed).
+template <int KB, bool kMixed>
+__device__ __forceinline__ bool query_buf(const KnnArgs& A, const Grid32& G, const GridDev& Gd, const QueryPos& Q, long long q,
+                          int lane, float& rho, QInfo& qi, CandBuf<KB>& buf, float& dk) {
+  constexpr int CAP = 32 * KB;
   const int L = A.K - 1;
-  constexpr int S = 32 * KPL;
-  if (S < L + 1) return false;
-  TopList<KPL, unsigned> Lst;
   const float E = Gd.E32;
   const float rel = 10.0f * 5.9604645e-8f;
-  const float Ef = 4.02f * E, E2f = 4.02f * E * E;
+  const double bx = Gd.box[0], by = Gd.box[1];
+  const float csx = G.cs[0], csy = G.cs[1], csz = G.cs[2];
   const float diag = sqrtf((float)G.dim[0] * G.dim[0] * G.cs[0] * G.cs[0] +
                            (float)G.dim[1] * G.dim[1] * G.cs[1] * G.cs[1] +
                            (float)G.dim[2] * G.dim[2] * G.cs[2] * G.cs[2]);
+  float r_lo = 0.0f, r_hi = 0.0f;    // radii known to hold too few / too many candidates
   for (int att = 0; att < 64; ++att) {
-    Lst.reset();
-    unsigned wk = ~0u;
-    int wj = INT_MAX;
-    const float rf = (rho * (1.0f + rel) + E) * 1.000001f;
+    int n_in = 0;
+    const double rho2 = (double)rho * (double)rho;
+    const float rf = (rho * (1.0f + 2.0f * rel) + 2.0f * E) * 1.000001f;
     const float rhof2 = rf * rf * 1.000001f;
-    // insertion threshold: the last list slot, or a bound above T_hi of the current
-    // (K-1)-th key, whichever is lower
-    auto refresh = [&]() {
-      unsigned kS, kL;
-      int jS, jL;
-      Lst.get(S - 1, kS, jS);
-      Lst.get(L - 1, kL, jL);
-      wk = kS;
-      wj = jS;
-      if (kL != ~0u) {
-        const float tau = __uint_as_float(kL);
-        const float tins = (tau * (1.0f + 12.0f * rel) + Ef * sqrtf(tau) + E2f) * 1.00001f;
-        const unsigned tb = __float_as_uint(tins);
-        if (tb < wk) { wk = tb; wj = INT_MAX; }
-      }
-    };
-    const float csx = G.cs[0], csy = G.cs[1], csz = G.cs[2];
-    const bool amb = scan_ball(G, A.cstart, Q, rho, [&](int ra, int rb, int xsh, int dyc, int dzc) {
-      const float offy = (float)dyc * csy, offz = (float)dzc * csz;
-      for (int base = ra; base < rb; base += 32) {
-        const int r = base + lane;
-        unsigned ck = ~0u;
-        int cj = INT_MAX;
-        if (r < rb && r != (int)q) {
+    const bool amb = scan_ball(G, A.cstart, Q, rho, lane, [&](bool valid, int r, int xsh, int dyc, int dzc) {
+      bool in = false;
+      unsigned long long key = 0;
+      int tj = 0;
+      if (valid && r != (int)q) {
+        if (kMixed) {
           const float4 p = __ldg(A.pos32 + r);
           const int ixj = __float_as_int(p.w) & 2047;
           const float dx = (p.x - Q.fx) + (float)(ixj + xsh - Q.ix) * csx;
-          const float dy = (p.y - Q.fy) + offy;
-          const float dz = (p.z - Q.fz) + offz;
+          const float dy = (p.y - Q.fy) + (float)dyc * csy;
+          const float dz = (p.z - Q.fz) + (float)dzc * csz;
           const float D = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-          if (D <= rhof2) { ck = __float_as_uint(D); cj = r; }
+          in = D <= rhof2;
+          key = __float_as_uint(D);
+          tj = r;
+        } else {
+          long long jj;
+          const double d2 = d2_fp64(A.pos64, r, Q.x, Q.y, Q.z, bx, by, jj);
+          in = d2 <= rho2;
+          key = (unsigned long long)__double_as_longlong(d2);
+          tj = (int)jj;
         }
-        offer(Lst, ck, cj, cj, wk, wj, lane, refresh);
       }
+      const unsigned m = __ballot_sync(FULL, in);
+      const int pos = n_in + __popc(m & ((1u << lane) - 1u));
+      if (in && pos < CAP) { buf.key[pos] = key; buf.j[pos] = tj; buf.r[pos] = r; }
+      n_in += __popc(m);
     });
-    if (amb) return false;
-    unsigned kL;
-    int jL;
-    Lst.get(L - 1, kL, jL);
-    if (kL == ~0u) {
-      int found = 0;
-#pragma unroll
-      for (int t = 0; t < KPL; ++t) found += __popc(__ballot_sync(FULL, Lst.k[t] != ~0u));
+    if (kMixed && amb) return false;
+    if (n_in < L) {
       if (rho > 2.0f * diag) return false;
-      rho = grow(rho, found, L);
+      r_lo = rho;
+      rho = r_hi > 0.0f ? sqrtf(r_lo * r_hi) : grow(rho, n_in, L);
       continue;
     }
+    if (n_in > CAP) {
+      r_hi = rho;
+      rho = r_lo > 0.0f ? sqrtf(r_lo * r_hi) : rho * fmaxf(cbrtf(0.7f * (float)CAP / (float)n_in), 0.3f);
+      continue;
+    }
+    __syncwarp();
+    unsigned long long k[KB];
+    int j[KB], r[KB];
+#pragma unroll
+    for (int t = 0; t < KB; ++t) {
+      const int e = t * 32 + lane;
+      if (e < n_in) { k[t] = buf.key[e]; j[t] = buf.j[e]; r[t] = buf.r[e]; }
+      else { k[t] = ~0ull; j[t] = INT_MAX; r[t] = -1; }
+    }
+    __syncwarp();
+    sort_any<KB>(n_in, k, j, r, lane);
+    unsigned long long kL;
+    get_entry<unsigned long long, KB>(k, L - 1, kL);
+    int* row = A.nbr + q * (long long)A.K;
+    if (!kMixed) {
+#pragma unroll
+      for (int t = 0; t < KB; ++t) {
+        const int e = t * 32 + lane;
+        if (e < L) row[1 + e] = r[t];
+      }
+      if (lane == 0) { qi.state = 1; qi.d2max = kL; }
+      dk = sqrtf((float)__longlong_as_double((long long)kL));   // radius hint only
+      return true;
+    }
     // FP32 bounds with relative margins far above their own rounding
-    const float sq = sqrtf(__uint_as_float(kL));
+    const float sq = sqrtf(__uint_as_float((unsigned)kL));
     const float hi_tau = (sq * (1.0f + rel) * 1.000001f + E) * 1.00001f;
     if (hi_tau > rho) {
       if (rho > 2.0f * diag) return false;
-      rho = fmaxf(rho * 1.25f, hi_tau * 1.02f);
+      r_lo = 0.0f;
+      r_hi = 0.0f;
+      rho = hi_tau * 1.02f;
       continue;
     }
     const float lo_tau = (sq * (1.0f - rel) * 0.999999f - E) * 0.99999f;
     const float tlo = (lo_tau - E) / (1.0f + rel);
     const float thi = (hi_tau + E) / (1.0f - rel);
-    const unsigned Tlo = tlo > 0.0f ? __float_as_uint(tlo * tlo * 0.9999f) : 0u;
-    const unsigned Thi = __float_as_uint(thi * thi * 1.0001f);
-    unsigned kS;
-    int jS;
-    Lst.get(S - 1, kS, jS);
-    if (!(kS > Thi)) return false;       // the band may extend past the list
+    const unsigned long long Tlo = tlo > 0.0f ? (unsigned long long)__float_as_uint(tlo * tlo * 0.99999f) : 0ull;
+    const unsigned long long Thi = (unsigned long long)__float_as_uint(thi * thi * 1.00001f);
+    if (Thi > (unsigned long long)__float_as_uint(rhof2)) return false;   // band reaches past the ball
     int p_lo = 0, p_hi = 0;
 #pragma unroll
-    for (int t = 0; t < KPL; ++t) {
-      p_lo += __popc(__ballot_sync(FULL, Lst.k[t] < Tlo));
-      p_hi += __popc(__ballot_sync(FULL, Lst.k[t] <= Thi));
+    for (int t = 0; t < KB; ++t) {
+      p_lo += __popc(__ballot_sync(FULL, k[t] < Tlo));
+      p_hi += __popc(__ballot_sync(FULL, k[t] <= Thi));
     }
     const int nb = p_hi - p_lo;
-    if (nb > kBand) return false;
-    int* row = A.nbr + q * (long long)A.K;
+    if (nb > kBand || p_lo > L - 1) return false;
 #pragma unroll
-    for (int t = 0; t < KPL; ++t) {
-      const int g = t * 32 + lane;
-      if (g < p_lo) row[1 + g] = Lst.r[t];
-      else if (g < p_hi) qi.band[g - p_lo] = Lst.r[t];
+    for (int t = 0; t < KB; ++t) {
+      const int e = t * 32 + lane;
+      if (e < p_lo) row[1 + e] = r[t];
+      else if (e < p_hi) qi.band[e - p_lo] = r[t];
     }
     if (lane == 0) {
       qi.state = 2;
@@ -479,20 +512,31 @@ __device__ bool query_mixed(const KnnArgs& A, const Grid32& G, const GridDev& Gd
       qi.nb = nb;
       qi.need = L - p_lo;
     }
+    dk = sq;
     return true;
   }
   return false;
 }
 
+template <int KPL> struct KnnShape {
+  static constexpr int KB = KPL <= 2 ? 4 : 2 * KPL;       // buffer of 32*KB candidates (>= 2K)
+  static constexpr int WPB = KPL <= 2 ? 8 : (KPL <= 4 ? 4 : 2);
+  static constexpr int MINB = KPL <= 1 ? 3 : 1;           // blocks per SM the registers allow
+};
+
 template <int KPL, bool kMixed>
-__global__ void __launch_bounds__(kWarps * 32) k_knn(KnnArgs A) {
-  __shared__ QInfo info[kWarps][32];
+__global__ void __launch_bounds__(KnnShape<KPL>::WPB * 32, KnnShape<KPL>::MINB) k_knn(KnnArgs A) {
+  constexpr int KB = KnnShape<KPL>::KB, WPB = KnnShape<KPL>::WPB;
+  __shared__ QInfo info[WPB][32];
+  __shared__ CandBuf<KB> buf[WPB];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   const int L = A.K - 1;
   for (long long base = warp * 32; base < A.N; base += nwarps * 32) {
     // ---- phase A: per query, warp-cooperative FP32/INT search
+    int prev_b = -1;
+    float prev_dk = 0.0f;
     for (int qi_ = 0; qi_ < 32; ++qi_) {
       const long long q = base + qi_;
       if (q >= A.N) break;
@@ -514,18 +558,24 @@ __global__ void __launch_bounds__(kWarps * 32) k_knn(KnnArgs A) {
       const double2* pp = reinterpret_cast<const double2*>(A.pos64 + q);
       const double2 a0 = __ldg(pp), a1 = __ldg(pp + 1);
       Q.x = a0.x; Q.y = a0.y; Q.z = a1.x;
-      float rho = rho_start(G, A.cstart, Q, L);
+      // the previous query of the chunk in the same cell gives a close radius
+      // the previous query of the chunk (a neighbour in cell order) gives a close radius
+      float rho = (prev_b == b && prev_dk > 0.0f) ? 1.15f * prev_dk : rho_start(G, A.cstart, Q, L, lane);
+      float dk = 0.0f;
       bool done = false;
-      if (kMixed) done = query_mixed<KPL>(A, G, Gd, Q, q, lane, rho, qi);
-      if (!done) done = query_fp64<KPL>(A, G, Gd, Q, q, lane, rho, qi);
+      if (kMixed) done = query_buf<KB, true>(A, G, Gd, Q, q, lane, rho, qi, buf[w], dk);
+      if (!done) done = query_buf<KB, false>(A, G, Gd, Q, q, lane, rho, qi, buf[w], dk);
+      prev_b = b;
+      prev_dk = done ? dk : 0.0f;
       if (!done) {
-        // no acceptable radius: keep the row valid (the particle against itself), V = 1
+        // no acceptable radius: keep the row valid (the particle against itself) with an
+        // infinite measure, so the particle gets no rate; the status reports it
         int* row = A.nbr + q * (long long)A.K;
         for (int k = lane; k < A.K; k += 32) row[k] = (int)q;
         if (lane == 0) {
           qi.state = 0;
           A.dist[q] = 0.0;
-          A.V[q] = 1.0;
+          A.V[q] = __longlong_as_double(0x7FF0000000000000ll);
           set_status(&A.st[b], GD_ST_KNN);
         }
       }
@@ -597,6 +647,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_knn(KnnArgs A) {
 
 template <int KPL, bool kMixed>
 static cudaError_t launch_knn_t(gd_ctx* c, const KnnArgs& A) {
+  constexpr int kWarps = KnnShape<KPL>::WPB;
   const int bs = kWarps * 32;
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_knn<KPL, kMixed>, bs, 0);

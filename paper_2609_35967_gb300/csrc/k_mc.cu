@@ -77,6 +77,60 @@ __device__ __forceinline__ Fixed make_fixed(const InstDev& P, const Gas& g, doub
   return f;
 }
 
+// Mixed form: the same quantities in FP32 (they only feed FP32 pair arithmetic).
+// Omega = sqrt(GM/R)/R keeps R^3 out of the FP32 range, and
+// 1 - R/r = Z^2/(r (r + R)) avoids the cancellation of the literal form.
+__device__ __forceinline__ Fixed make_fixed_f32(const InstDev& P, double x, double y, double z, double V,
+                                                double M, int K) {
+  const float R = P.geometry == GD_GEOM_PATCH ? (float)(P.r0 + x) : sqrtf((float)x * (float)x + (float)y * (float)y);
+  const float Z = (float)z;
+  const float r = sqrtf(R * R + Z * Z);
+  const float Om = sqrtf((float)P.GM / R) / R;
+  const float xr = R / (float)P.r0;
+  const float T = (float)P.T0 * powf(xr, (float)P.q);
+  const float cs = sqrtf((float)(kKB / (kMu * kMH)) * T);
+  const float H = cs / Om;
+  const float h = H / R;
+  const float Sigma = (float)P.sigma0 * powf(xr, (float)P.p);
+  const float omr = Z * Z / (r * (r + R));
+  const float vert = omr / (h * h);
+  const float rho = Sigma / (2.5066283f * H) * expf(-vert);
+  const float eta = -0.5f * (((float)P.p + 0.5f * (float)P.q - 1.5f) * h * h + (float)P.q * omr);
+  const float numol = 0.5f * 1.5957691f * cs * ((float)(kMu * kMH / kSigH2) / rho);
+  Fixed f;
+  f.gst = (double)(3.14159265f * (float)P.rho_s / (4.0f * Sigma) * expf(vert));
+  f.e2 = (double)(2.0f * eta * R * Om);
+  f.e1 = (double)(eta * R * Om);
+  f.zo = (double)(Z * Om);
+  f.cs = (double)cs;
+  f.cB = (double)((float)(8.0 * kKB / kPi) * T);
+  f.Vg2 = (double)(1.5f * (float)P.alpha * cs * cs);
+  f.tRe = (double)rsqrtf((float)P.alpha * cs * H / numol);
+  f.vfrag = P.v_frag;
+  f.m0 = P.m0;
+  f.pref = prefactor<float>(P, V, K);
+  f.rho_s = P.rho_s;
+  f.s_min = P.s_min;
+  f.M = M;
+  f.mode = P.kernel_mode;
+  return f;
+}
+
+// <J>, <J^2> of a fragmentation in FP32 (mixed form; they only feed the bin moments).
+__device__ __forceinline__ void frag_moments_f32(double s_i, double s_min, double& j1, double& j2) {
+  const float a = sqrtf((float)(s_min / s_i));
+  if (!(a < 1.0f)) { j1 = 0.0; j2 = 0.0; return; }
+  const float dd = 1.0f - a;
+  if (dd < 1e-2f) {
+    j1 = dd * (1.0f + dd * (1.0f / 3.0f + dd * (1.0f / 6.0f + dd * (1.0f / 10.0f))));
+    j2 = dd * dd * (4.0f / 3.0f + dd * (1.0f + dd * (11.0f / 15.0f + dd * (5.0f / 9.0f))));
+    return;
+  }
+  const float la = logf(a);
+  j1 = 2.0f * (1.0f - a + a * la) / (1.0f - a);
+  j2 = 4.0f * (2.0f - a * la * la + 2.0f * a * la - 2.0f * a) / (1.0f - a);
+}
+
 // Query of a live particle (s, m) from the fixed part.  FP64 form: FP64 throughout; mixed
 // form: FP32 from the rounded s, m and gst (the rate kernel and the sampler build it with
 // this one function, so both see the same pair rates).
@@ -184,6 +238,19 @@ __device__ __forceinline__ double lane_channels(const McArgs& A, const Query<T>&
   return v;
 }
 
+// Diameter from s^3 = 6 m/(pi rho_o).  FP64 form: cbrt.  Mixed form: the FP32 cube root
+// refined by one Newton step for y^3 = x in FP64, y <- y - (y^3 - x)/(3 y^2), which
+// brings the 2^-24 start to ~1e-14 relative at a fraction of the FP64 instructions.
+template <typename T>
+__device__ __forceinline__ double diameter_of(double x) {
+  if constexpr (sizeof(T) == 8) {
+    return cbrt(x);
+  } else {
+    const double y = (double)cbrtf((float)x);
+    return y - (y * y * y - x) / (3.0 * y * y);
+  }
+}
+
 // ---------------------------------------------------------------- rate kernel
 template <typename T, int S>
 __global__ void __launch_bounds__(256) k_rates(McArgs A) {
@@ -206,12 +273,17 @@ __global__ void __launch_bounds__(256) k_rates(McArgs A) {
       b = inst_of(A.off, A.n_inst, r);
       const InstDev& P = A.P[b];
       const Pos64 p = A.pos64[r];
-      Gas g = gas_at(P, p.x, p.y, p.z);
       const Snap64 sn = A.snap64[r];
       s_i = sn.s;
       m_i = sn.m;
-      fx = make_fixed<T>(P, g, A.V[r], A.Mr[r], A.K);
-      frag_moments(s_i, P.s_min, fj1, fj2);
+      if constexpr (sizeof(T) == 8) {
+        Gas g = gas_at(P, p.x, p.y, p.z);
+        fx = make_fixed<T>(P, g, A.V[r], A.Mr[r], A.K);
+        frag_moments(s_i, P.s_min, fj1, fj2);
+      } else {
+        fx = make_fixed_f32(P, p.x, p.y, p.z, A.V[r], A.Mr[r], A.K);
+        frag_moments_f32(s_i, P.s_min, fj1, fj2);
+      }
     } else {
       fx = Fixed{};
       fx.pref = 0.0;
@@ -232,9 +304,19 @@ __global__ void __launch_bounds__(256) k_rates(McArgs A) {
       T c0[S], c1[S];
       int jr[S];
       PairOut<T> po[S];
-      double v = lane_channels<T, S>(A, q, row, lane, c0, c1, jr, po);
-      double incl = warp_incl_scan(v, lane);
-      double tot = __shfl_sync(FULLM, incl, 31);
+      double tot;
+      if constexpr (sizeof(T) == 8) {
+        // FP64 form: the sampler's own scan, so lambda*_i is the same number there
+        const double v = lane_channels<T, S>(A, q, row, lane, c0, c1, jr, po);
+        tot = __shfl_sync(FULLM, warp_incl_scan(v, lane), 31);
+      } else {
+        // mixed form: rates accumulated in FP32 (only the sampler's prefix sums are FP64)
+        lane_channels<T, S>(A, q, row, lane, c0, c1, jr, po);
+        float vf = 0.0f;
+#pragma unroll
+        for (int t = 0; t < S; ++t) vf += c0[t] + c1[t];
+        tot = (double)warp_sumf(vf);
+      }
       T la = (T)0, lb = (T)0;
 #pragma unroll
       for (int t = 0; t < S; ++t) {
@@ -297,45 +379,58 @@ __global__ void __launch_bounds__(256) k_rates(McArgs A) {
 }
 
 // ---------------------------------------------------------------- interval choice
-// One thread per instance: merge fine bins into controller bins (>= max(K, 64)
-// particles, ascending, remainder joins the previous bin), A_b and B_b, dt_req and the
-// halving of dt_coll with the exact tick count of the time left.
+// One block per instance: the fine bins are read into shared memory by all threads, then
+// one thread merges them into controller bins (>= max(K, 64) particles, ascending, a
+// remainder joins the previous bin), forms A_b and B_b in one ascending pass, and halves
+// dt_coll with the exact tick count of the time left.
 __global__ void k_interval(const InstDev* __restrict__ P, StateDev* st, BinsDev* bins, int n_inst, int K,
                            int no_audit) {
-  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double cnt[kNFine], sM[kNFine], sA[kNFine], sB[kNFine];
+  __shared__ double gM[kNFine], gA[kNFine], gB[kNFine];
+  __shared__ int gid[kNFine];
+  const int b = blockIdx.x;
   if (b >= n_inst) return;
-  BinsDev& B = bins[b];
+  BinsDev& Bn = bins[b];
+  for (int f = threadIdx.x; f < kNFine; f += blockDim.x) {
+    cnt[f] = Bn.cnt[f]; sM[f] = Bn.sM[f]; sA[f] = Bn.sA[f]; sB[f] = Bn.sB[f];
+    gM[f] = 0.0; gA[f] = 0.0; gB[f] = 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   StateDev& S = st[b];
   const InstDev& p = P[b];
-  double thr = K > 64 ? K : 64;
+  const double thr = K > 64 ? K : 64;
   int ng = 0;
   double acc = 0.0;
   for (int f = 0; f < kNFine; ++f) {
-    B.gid[f] = -1;
-    if (B.cnt[f] == 0.0) continue;
-    B.gid[f] = ng;
-    acc += B.cnt[f];
+    gid[f] = -1;
+    if (cnt[f] == 0.0) continue;
+    gid[f] = ng;
+    acc += cnt[f];
     if (acc >= thr) { ng++; acc = 0.0; }
   }
   if (acc > 0.0) {
-    if (ng > 0) { for (int f = 0; f < kNFine; ++f) if (B.gid[f] == ng) B.gid[f] = ng - 1; }
+    if (ng > 0) { for (int f = 0; f < kNFine; ++f) if (gid[f] == ng) gid[f] = ng - 1; }
     else ng = 1;
   }
-  B.ngroups = ng;
-  double C = (p.audit && !no_audit) ? S.C : 1.0;
+  for (int f = 0; f < kNFine; ++f) {
+    const int g = gid[f];
+    if (g < 0) continue;
+    gM[g] += sM[f]; gA[g] += sA[f]; gB[g] += sB[f];
+  }
+  for (int f = 0; f < kNFine; ++f) Bn.gid[f] = gid[f];
+  Bn.ngroups = ng;
+  const double C = (p.audit && !no_audit) ? S.C : 1.0;
   if (S.remain_ticks <= 0) S.remain_ticks = 1LL << 60;
-  double remain = ldexp((double)S.remain_ticks, -60) * p.dt_coll;
-  double dt_cap = remain < p.dt_fn_max ? remain : p.dt_fn_max;
+  const double remain = ldexp((double)S.remain_ticks, -60) * p.dt_coll;
+  const double dt_cap = remain < p.dt_fn_max ? remain : p.dt_fn_max;
   double dt_ab = HUGE_VAL;
   for (int g = 0; g < ng; ++g) {
-    double sM = 0.0, sA = 0.0, sB = 0.0;
-    for (int f = 0; f < kNFine; ++f)
-      if (B.gid[f] == g) { sM += B.sM[f]; sA += B.sA[f]; sB += B.sB[f]; }
-    double A = sA / sM, Bm = sB / sM;
-    if (A > 0.0) { double t = p.eps * C / A; if (t < dt_ab) dt_ab = t; }
-    if (Bm > 0.0) { double t = p.eps * p.eps * C * C / Bm; if (t < dt_ab) dt_ab = t; }
+    const double A = gA[g] / gM[g], Bm = gB[g] / gM[g];
+    if (A > 0.0) { const double t = p.eps * C / A; if (t < dt_ab) dt_ab = t; }
+    if (Bm > 0.0) { const double t = p.eps * p.eps * C * C / Bm; if (t < dt_ab) dt_ab = t; }
   }
-  double dt_req = dt_ab < dt_cap ? dt_ab : dt_cap;
+  const double dt_req = dt_ab < dt_cap ? dt_ab : dt_cap;
   double dt = p.dt_coll;
   int k = 0;
   while (k < 60 && (dt > dt_req || (1LL << (60 - k)) > S.remain_ticks)) { dt = 0.5 * dt; ++k; }
@@ -403,11 +498,15 @@ __global__ void __launch_bounds__(256) k_sample(McArgs A) {
     if (valid) {
       const InstDev& P = A.P[b];
       const Pos64 p = A.pos64[r];
-      Gas g = gas_at(P, p.x, p.y, p.z);
       const Snap64 sn = A.snap64[r];
       s_i = sn.s;
       m_i = sn.m;
-      fx = make_fixed<T>(P, g, A.V[r], A.Mr[r], A.K);
+      if constexpr (sizeof(T) == 8) {
+        Gas g = gas_at(P, p.x, p.y, p.z);
+        fx = make_fixed<T>(P, g, A.V[r], A.Mr[r], A.K);
+      } else {
+        fx = make_fixed_f32(P, p.x, p.y, p.z, A.V[r], A.Mr[r], A.K);
+      }
     } else {
       fx = Fixed{};
       fx.mode = 0;
@@ -488,10 +587,10 @@ __global__ void __launch_bounds__(256) k_sample(McArgs A) {
         double m_new, s_new;
         if (outcome == 0) {
           m_new = m + ncoll * pj.m;
-          s_new = cbrt(6.0 * m_new / (kPi * f.rho_s));
+          s_new = diameter_of<T>(6.0 * m_new / (kPi * f.rho_s));
         } else if (outcome == 1 && ch == 0) {
           m_new = m - ncoll * pj.m;
-          s_new = cbrt(6.0 * m_new / (kPi * f.rho_s));
+          s_new = diameter_of<T>(6.0 * m_new / (kPi * f.rho_s));
         } else if (outcome == 1) {
           m_new = pj.m;
           s_new = pj.s;
@@ -503,7 +602,8 @@ __global__ void __launch_bounds__(256) k_sample(McArgs A) {
           s_new = xr * xr;
           m_new = kPi * f.rho_s * s_new * s_new * s_new / 6.0;
         }
-        J += fabs(log(s_new / s));
+        if constexpr (sizeof(T) == 8) J += fabs(log(s_new / s));
+        else J += (double)fabsf(logf((float)(s_new / s)));
         s = s_new;
         m = m_new;
         h = h * 31u + (unsigned)(chosen + 1);
@@ -549,31 +649,42 @@ __global__ void __launch_bounds__(256) k_sample(McArgs A) {
 }
 
 // ---------------------------------------------------------------- audit
-// One thread per instance: realised mass-weighted sum of |ln(s'/s)| per controller bin
+// One block per instance: realised mass-weighted sum of |ln(s'/s)| per controller bin
 // against 2 eps C; C halves (>= 1/4) on excess, else grows by 1.25 (<= 1).  Clears the
 // fine bins for the next interval.
 __global__ void k_audit(const InstDev* __restrict__ P, StateDev* st, BinsDev* bins, int n_inst, int no_audit) {
-  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double sM[kNFine], sJ[kNFine], gM[kNFine], gJ[kNFine];
+  __shared__ int gid[kNFine];
+  const int b = blockIdx.x;
   if (b >= n_inst) return;
-  BinsDev& B = bins[b];
-  StateDev& S = st[b];
-  if (P[b].audit && !no_audit) {
-    double thr = 2.0 * P[b].eps * S.C;
-    bool exceed = false;
-    for (int g = 0; g < B.ngroups; ++g) {
-      double sM = 0.0, sJ = 0.0;
-      for (int f = 0; f < kNFine; ++f)
-        if (B.gid[f] == g) { sM += B.sM[f]; sJ += B.sJ[f]; }
-      double Rg = sJ / sM;
-      if (fabs(Rg - thr) <= 1e-10 * thr) S.near_audit++;
-      if (Rg > thr) exceed = true;
-    }
-    S.C = exceed ? fmax(0.25, 0.5 * S.C) : fmin(1.0, 1.25 * S.C);
-  } else {
-    S.C = 1.0;
+  BinsDev& Bn = bins[b];
+  for (int f = threadIdx.x; f < kNFine; f += blockDim.x) {
+    sM[f] = Bn.sM[f]; sJ[f] = Bn.sJ[f]; gid[f] = Bn.gid[f];
+    gM[f] = 0.0; gJ[f] = 0.0;
   }
-  S.events_total += S.events;
-  for (int f = 0; f < kNFine; ++f) { B.cnt[f] = 0.0; B.sM[f] = 0.0; B.sA[f] = 0.0; B.sB[f] = 0.0; B.sJ[f] = 0.0; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    StateDev& S = st[b];
+    if (P[b].audit && !no_audit) {
+      for (int f = 0; f < kNFine; ++f)
+        if (gid[f] >= 0) { gM[gid[f]] += sM[f]; gJ[gid[f]] += sJ[f]; }
+      const double thr = 2.0 * P[b].eps * S.C;
+      bool exceed = false;
+      for (int g = 0; g < Bn.ngroups; ++g) {
+        const double Rg = gJ[g] / gM[g];
+        if (fabs(Rg - thr) <= 1e-10 * thr) S.near_audit++;
+        if (Rg > thr) exceed = true;
+      }
+      S.C = exceed ? fmax(0.25, 0.5 * S.C) : fmin(1.0, 1.25 * S.C);
+    } else {
+      S.C = 1.0;
+    }
+    S.events_total += S.events;
+  }
+  __syncthreads();
+  for (int f = threadIdx.x; f < kNFine; f += blockDim.x) {
+    Bn.cnt[f] = 0.0; Bn.sM[f] = 0.0; Bn.sA[f] = 0.0; Bn.sB[f] = 0.0; Bn.sJ[f] = 0.0;
+  }
 }
 
 // ---------------------------------------------------------------- launchers
@@ -634,8 +745,8 @@ cudaError_t launch_rates(gd_ctx* c, double* chan_out) {
 
 cudaError_t launch_interval(gd_ctx* c) {
   time_begin(c, 3);
-  k_interval<<<(c->n_inst + 63) / 64, 64, 0, c->stream>>>(c->d_inst, c->d_state, c->d_bins, c->n_inst, c->K,
-                                                          (c->flags & GD_FLAG_NO_AUDIT) ? 1 : 0);
+  k_interval<<<c->n_inst, 128, 0, c->stream>>>(c->d_inst, c->d_state, c->d_bins, c->n_inst, c->K,
+                                               (c->flags & GD_FLAG_NO_AUDIT) ? 1 : 0);
   time_end(c);
   c->launches += 1;
   return cudaGetLastError();
@@ -675,8 +786,8 @@ cudaError_t launch_sample(gd_ctx* c, int* ev_count, unsigned* ev_hash, int* near
 
 cudaError_t launch_audit(gd_ctx* c) {
   time_begin(c, 3);
-  k_audit<<<(c->n_inst + 63) / 64, 64, 0, c->stream>>>(c->d_inst, c->d_state, c->d_bins, c->n_inst,
-                                                       (c->flags & GD_FLAG_NO_AUDIT) ? 1 : 0);
+  k_audit<<<c->n_inst, 128, 0, c->stream>>>(c->d_inst, c->d_state, c->d_bins, c->n_inst,
+                                            (c->flags & GD_FLAG_NO_AUDIT) ? 1 : 0);
   time_end(c);
   c->launches += 1;
   return cudaGetLastError();

@@ -230,3 +230,48 @@ def test_sequencing_errors(gd):
     with pytest.raises(gd.GDError):
         gd.gd_push_staggered(sess.ctx, 1.0)     # no velocities configured
     sess.close()
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_full_size_disk_sampled(gd, oracle, precision):
+    """The benchmark workload at full size (2^22 particles, log-normal sizes, K = 32) in
+    the launch configuration bench.py times: lists, distances and rates of sampled
+    particles against the oracle's brute force, and two whole intervals without any
+    status bit (no failed search, no event cap, no non-finite rate)."""
+    ins = W.config2()[0]
+    sess = gd.Session([ins], precision=precision, flags=gd.GD_FLAG_TIMING)
+    nbr, d = sess.build_neighbors(want=True)
+    lam, _ = sess.collision_rates(want=True)
+    sess.sample_collisions()
+    sess.build_neighbors()
+    sess.collision_rates()
+    sess.sample_collisions()
+    st = sess.stats(check=False)
+    assert st["status"] == 0, st["status"]
+    P = oracle.params(ins["params"])
+    rng = np.random.default_rng(17)
+    q = rng.choice(len(ins["x"]), 48, replace=False)
+    # include the innermost and the highest particles (densest / sparsest regions)
+    R = np.hypot(ins["x"], ins["y"])
+    q = np.concatenate([q, [int(np.argmin(R)), int(np.argmax(np.abs(ins["z"])))]])
+    onbr, od = oracle.knn(P, ins["x"], ins["y"], ins["z"], q)
+    assert np.array_equal(nbr.cpu().numpy()[q], onbr)
+    assert np.array_equal(d.cpu().numpy()[q], od)
+    r = oracle.rates_subset(P, ins["x"], ins["y"], ins["z"], ins["s"], ins["M"], q, onbr, od)
+    rel = np.abs(lam.cpu().numpy()[q] / r["lam"] - 1.0)
+    assert rel.max() < (1e-12 if precision == 0 else 1e-4), rel.max()
+    sess.close()
+
+
+def test_autotune_keeps_lists_exact(gd, oracle):
+    ins = W.disk_instance(1 << 14, seed=31, K=32, sizes=("lognormal", 10.0, 1.0))
+    sess = gd.Session([ins], precision=gd.GD_MIXED)
+    f = sess.autotune()
+    assert 0.35 < f < 1.5
+    nbr, d = sess.build_neighbors(want=True)
+    P = oracle.params(ins["params"])
+    q = np.arange(0, len(ins["x"]), 97)
+    onbr, od = oracle.knn(P, ins["x"], ins["y"], ins["z"], q)
+    assert np.array_equal(nbr.cpu().numpy()[q], onbr)
+    assert np.array_equal(d.cpu().numpy()[q], od)
+    sess.close()
