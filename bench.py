@@ -173,7 +173,7 @@ def run_gpu(args, rank, world):
         ms = e0.elapsed_time(e1)
         ck = clocks.stop()
         post = sess.stats()
-        res = {"ms": ms, "clocks": ck, "launches": post["launches"] - pre["launches"] - 1,
+        res = {"ms": ms, "clocks": ck, "launches": post["launches"] - pre["launches"],
                "kernel_ms": {k: post["kernel_ms"][k] - pre["kernel_ms"][k] for k in post["kernel_ms"]},
                "kernel_calls": {k: post["kernel_calls"][k] - pre["kernel_calls"][k]
                                 for k in post["kernel_calls"]},
@@ -222,13 +222,20 @@ def run_gpu(args, rank, world):
     e2e_ms = max(e0.elapsed_time(e1), (time.perf_counter() - t0) * 1e3)
     sess.close()
 
-    times = torch.tensor([mixed["ms"], fp64["ms"] if fp64 else 0.0, e2e_ms], dtype=torch.float64)
-    if world > 1:
-        t = times.to(dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        times = t.cpu()
-    return dict(N=N, K=K, cfg=cfg, mixed=mixed, fp64=fp64, times=times.tolist(), hbm=hbm,
+    times = max_over_ranks([mixed["ms"], fp64["ms"] if fp64 else 0.0, e2e_ms], world, dev)
+    return dict(N=N, K=K, cfg=cfg, mixed=mixed, fp64=fp64, times=times, hbm=hbm,
                 peak_kind=peak_kind, h2d=h2d, d2h=d2h, push=push)
+
+
+def max_over_ranks(times, world, dev):
+    """Element-wise maximum of the ranks' timings (every rank gets the result)."""
+    import torch
+    t = torch.tensor(times, dtype=torch.float64)
+    if world > 1:
+        t = t.to(dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t = t.cpu()
+    return t.tolist()
 
 
 def cpu_oracle_rate(insts, budget_s=12.0, max_q=4096):
@@ -299,11 +306,22 @@ def main():
         import torch
         torch.distributed.init_process_group(backend="nccl")
     r = run_gpu(args, rank, world)
-    if rank != 0:
-        if world > 1:
-            import torch
-            torch.distributed.destroy_process_group()
-        return
+    if rank == 0:
+        out = result_line(r, args, world)
+        if world == 1 and not args.skip_cpu:
+            insts, _ = make_workload(args.workload, 0)
+            v, q, el, n = cpu_oracle_rate(insts)
+            out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                   "sample": f"{q} query particles of the {n}-particle instance, {el:.1f} s: "
+                                             "brute-force K-NN, FP64 rates, sampling (serial C, -O2)"}
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+def result_line(r, args, world):
+    """The JSON line of the GPU arm from one rank's results with max-over-ranks times."""
     N, K = r["N"], r["K"]
     ms_mixed, ms_fp64, ms_e2e = r["times"]
     value = world * N * args.steps / (ms_mixed * 1e-3)
@@ -338,16 +356,7 @@ def main():
                        "kernels_ms_per_step": {k: v / st for k, v in r["fp64"]["kernel_ms"].items()
                                                if v > 0 and k != "stats"}}
         out["mixed_over_fp64"] = out["value"] / out["fp64"]["value"]
-    if world == 1 and not args.skip_cpu:
-        insts, _ = make_workload(args.workload, 0)
-        v, q, el, n = cpu_oracle_rate(insts)
-        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                               "sample": f"{q} query particles of the {n}-particle instance, {el:.1f} s: "
-                                         "brute-force K-NN, FP64 rates, sampling (serial C, -O2)"}
-    print(json.dumps(out))
-    if world > 1:
-        import torch
-        torch.distributed.destroy_process_group()
+    return out
 
 
 if __name__ == "__main__":

@@ -138,10 +138,12 @@ typedef struct {
 typedef struct {
   int64_t intervals;           /* completed gd_sample_collisions calls         */
   int64_t events;              /* all events so far                            */
-  int64_t near_draw;           /* draws within 1e-10 of a rate / time boundary */
-  int64_t near_dt;             /* interval choices within 1e-10 of an edge     */
-  int64_t near_audit;          /* audit decisions within 1e-10 of the threshold */
-  int64_t launches;            /* kernels launched by the library so far       */
+  int64_t near_draw;           /* draws within the tie tolerance of a rate or
+                                  time boundary (1e-10 FP64 form, 2e-5 mixed)  */
+  int64_t near_dt;             /* interval choices within the tolerance of an edge */
+  int64_t near_audit;          /* audit decisions within the tolerance of the threshold */
+  int64_t launches;            /* kernels launched by the path so far (the two
+                                  reductions of gd_stats itself not included) */
   uint32_t status;             /* OR of every instance's GD_ST_* bits          */
   int32_t n_instances;
   double kernel_ms[8];         /* GD_FLAG_TIMING: summed kernel time by step:

@@ -152,7 +152,7 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
   ok &= dalloc(&c->d_lam, N) == cudaSuccess;
   ok &= dalloc(&c->d_nbr, (size_t)N * c->K) == cudaSuccess;
   ok &= dalloc(&c->d_counters, 16) == cudaSuccess;
-  ok &= dalloc(&c->d_sums, 3 * (size_t)n) == cudaSuccess;
+  ok &= dalloc(&c->d_sums, 3 * ((size_t)n + c->n_tiles)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     free_all(c);
@@ -176,6 +176,10 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
     d.box_x = p.box_x; d.box_y = p.box_y; d.t0 = p.t0; d.m0 = p.m0; d.cell_size = p.cell_size;
     d.key0 = (uint32_t)p.seed;
     d.key1 = (uint32_t)(p.seed >> 32);
+    d.k6 = 6.0 / (kPi * p.rho_s);
+    d.f_r0 = (float)p.r0; d.f_GM = (float)d.GM; d.f_T0 = (float)p.T0; d.f_q = (float)p.q;
+    d.f_p = (float)p.p; d.f_sigma0 = (float)p.sigma0; d.f_alpha = (float)p.alpha;
+    d.f_rho_s = (float)p.rho_s; d.f_vfrag = (float)p.v_frag; d.f_m0 = (float)p.m0;
     d.off = c->h_off[b];
     d.n = c->h_off[b + 1] - c->h_off[b];
     if (p.geometry == GD_GEOM_DISK) c->any_disk = true;

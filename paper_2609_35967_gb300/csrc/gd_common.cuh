@@ -35,6 +35,9 @@ struct InstDev {
   double R_in, R_out, box_x, box_y, t0, m0, cell_size;
   uint32_t key0, key1;
   long long off, n;
+  double k6;          // 6 / (pi rho_s)
+  // FP32 copies of the parameters the mixed form's per-particle gas disk uses
+  float f_r0, f_GM, f_T0, f_q, f_p, f_sigma0, f_alpha, f_rho_s, f_vfrag, f_m0;
 };
 
 // Uniform cell grid of one instance, rebuilt every interval from the data bounds.
@@ -112,7 +115,11 @@ __device__ __forceinline__ int fine_bin(double s) {
   int e = (int)((b >> 52) & 0x7FF) - 1022;                   // s = mant 2^e, mant in [1/2, 1)
   double mant = __longlong_as_double((long long)((b & 0x000FFFFFFFFFFFFFull) |
                                                  0x3FE0000000000000ull));
-  int t = 3 * e + (mant >= 0x1.428a2f98d728bp-1 ? 1 : 0) + (mant >= 0x1.965fea53d6e3dp-1 ? 1 : 0);
+  // mant and both edges share the exponent of [1/2, 1): compare their mantissa bits
+  const unsigned long long mb = (unsigned long long)__double_as_longlong(mant) & 0x000FFFFFFFFFFFFFull;
+  const unsigned long long e1 = (unsigned long long)__double_as_longlong(0x1.428a2f98d728bp-1) & 0x000FFFFFFFFFFFFFull;
+  const unsigned long long e2 = (unsigned long long)__double_as_longlong(0x1.965fea53d6e3dp-1) & 0x000FFFFFFFFFFFFFull;
+  int t = 3 * e + (mb >= e1 ? 1 : 0) + (mb >= e2 ? 1 : 0);
   t -= kTMin;
   return t < 0 ? 0 : (t > kNFine - 1 ? kNFine - 1 : t);
 }
@@ -152,7 +159,7 @@ __device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint
 // (k + 1/2) 2^-52 with k built from 26 bits of each word: exact, in (0, 1).
 __device__ __forceinline__ double u01(uint32_t a, uint32_t b) {
   unsigned long long k = ((unsigned long long)(a >> 6) << 26) | (unsigned long long)(b >> 6);
-  return ((double)k + 0.5) * 0x1p-52;
+  return (double)(2ull * k + 1ull) * 0x1p-53;   // = (k + 1/2) 2^-52, exactly
 }
 
 // ---------------------------------------------------------------- warp helpers

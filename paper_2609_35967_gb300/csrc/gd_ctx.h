@@ -51,7 +51,7 @@ struct gd_ctx {
   double* d_lam = nullptr;              // [N] lambda*_i, rank order
   int* d_nbr = nullptr;                 // [N*K] ranks
   unsigned long long* d_counters = nullptr;  // [16] spare device counters
-  double* d_sums = nullptr;             // [3 * n_inst] gd_stats reductions
+  double* d_sums = nullptr;             // [3 * (n_inst + n_tiles)] gd_stats sums, then per-tile partials
 
   // sequencing: 0 nothing, 1 neighbours built, 2 rates done
   int phase = 0;

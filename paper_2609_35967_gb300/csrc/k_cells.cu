@@ -38,6 +38,58 @@ __device__ __forceinline__ bool tile_range(const TileMap& tm, int tile, int& b, 
   return lo < hi;
 }
 
+// ---------------------------------------------------------------- stats
+// Sums of M, M m and M s per instance (a10): per-tile partials over a fixed stride and a
+// fixed tree, then each instance's partials in tile order.  Every launch adds in the same
+// order, so the result is bitwise reproducible.
+__device__ __forceinline__ void block_tree3(double (&sh)[3][256], double a0, double a1, double a2) {
+  sh[0][threadIdx.x] = a0;
+  sh[1][threadIdx.x] = a1;
+  sh[2][threadIdx.x] = a2;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+      for (int k = 0; k < 3; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256) k_stats_tile(TileMap tm, const InstDev* __restrict__ P,
+                                                    const double* __restrict__ s, const double* __restrict__ M,
+                                                    double* part) {
+  __shared__ double sh[3][256];
+  int b;
+  long long lo, hi;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  if (tile_range(tm, blockIdx.x, b, lo, hi)) {
+    const InstDev& p = P[b];
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+      const double si = s[i], Mi = M[i];
+      a0 += Mi;
+      a1 += Mi * grain_mass(p, si);
+      a2 += Mi * si;
+    }
+  }
+  block_tree3(sh, a0, a1, a2);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 3; ++k) part[3 * (long long)blockIdx.x + k] = sh[k][0];
+}
+
+__global__ void __launch_bounds__(256) k_stats_inst(const long long* __restrict__ tile_off,
+                                                    const double* __restrict__ part, double* out) {
+  __shared__ double sh[3][256];
+  const int b = blockIdx.x;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  for (long long t = tile_off[b] + threadIdx.x; t < tile_off[b + 1]; t += blockDim.x) {
+    a0 += part[3 * t];
+    a1 += part[3 * t + 1];
+    a2 += part[3 * t + 2];
+  }
+  block_tree3(sh, a0, a1, a2);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 3; ++k) out[3 * b + k] = sh[k][0];
+}
+
 // ---------------------------------------------------------------- bounds
 __global__ void k_bounds(TileMap tm, const double* __restrict__ x, const double* __restrict__ y,
                          const double* __restrict__ z, StateDev* st) {
@@ -318,6 +370,15 @@ std::vector<long long> tile_table(const std::vector<long long>& off) {
   std::vector<long long> t(off.size(), 0);
   for (size_t b = 0; b + 1 < off.size(); ++b) t[b + 1] = t[b] + (off[b + 1] - off[b] + kTile - 1) / kTile;
   return t;
+}
+
+cudaError_t launch_stats(gd_ctx* c, double* d_sums) {
+  time_begin(c, 6);
+  double* part = d_sums + 3 * (long long)c->n_inst;
+  k_stats_tile<<<c->n_tiles, 256, 0, c->stream>>>(tile_map(c), c->d_inst, c->s, c->M, part);
+  k_stats_inst<<<c->n_inst, 256, 0, c->stream>>>(c->d_tile_off, part, d_sums);
+  time_end(c);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_cells(gd_ctx* c) {

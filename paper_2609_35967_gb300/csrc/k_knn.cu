@@ -312,9 +312,9 @@ struct QInfo {
 // Candidates inside the search ball of one query, in shared memory (per warp).
 template <int KB>
 struct CandBuf {
-  unsigned long long key[32 * KB];   // FP64 form: bits of d^2; mixed: bits of the FP32 D
-  int j[32 * KB];                    // tie index: caller index (FP64) or rank (mixed)
-  int r[32 * KB];
+  unsigned long long key[32 * KB];   // FP64 form: bits of d^2; mixed: (bits of the FP32 D) << 32 | rank
+  int j[32 * KB];                    // FP64 form: tie index (caller index)
+  int r[32 * KB];                    // FP64 form: rank
 };
 
 // Compare-exchange of register pairs (t, t ^ RS) inside each lane, block direction from
@@ -381,6 +381,52 @@ __device__ __forceinline__ void sort_any(int n, unsigned long long (&k)[KB], int
   sort_cand<KB>(nreg, k, j, r, lane);
 }
 
+// Mixed form: the same bitonic network on packed keys (FP32 D bits << 32 | rank), which
+// are distinct, so one 64-bit comparison orders them by (D, rank).
+template <int RS, int KB>
+__device__ __forceinline__ void cas_packed(int nreg, int kk, unsigned long long (&k)[KB], int lane) {
+#pragma unroll
+  for (int t = 0; t < KB; ++t) {
+    const int tp = t ^ RS;
+    if (tp > t && tp < KB && t < nreg && tp < nreg) {
+      const bool up = ((t * 32 + lane) & kk) == 0;
+      if (up == (k[tp] < k[t])) { unsigned long long a = k[t]; k[t] = k[tp]; k[tp] = a; }
+    }
+  }
+}
+
+template <int KB>
+__device__ __forceinline__ void sort_packed(int n, unsigned long long (&k)[KB], int lane) {
+  int nreg = 1;
+  while (32 * nreg < n && nreg < KB) nreg <<= 1;
+  const int S = 32 * nreg;
+#pragma unroll 1
+  for (int kk = 2; kk <= S; kk <<= 1) {
+#pragma unroll 1
+    for (int s = kk >> 1; s > 0; s >>= 1) {
+      if (s >= 32) {
+        const int rs = s >> 5;
+        if (rs == 1) cas_packed<1, KB>(nreg, kk, k, lane);
+        else if (rs == 2) cas_packed<2, KB>(nreg, kk, k, lane);
+        else if (rs == 4) cas_packed<4, KB>(nreg, kk, k, lane);
+        else if (rs == 8) cas_packed<8, KB>(nreg, kk, k, lane);
+        else cas_packed<16, KB>(nreg, kk, k, lane);
+      } else {
+        const bool lower = (lane & s) == 0;
+#pragma unroll
+        for (int t = 0; t < KB; ++t) {
+          if (t < nreg) {
+            const unsigned long long pk = __shfl_xor_sync(FULL, k[t], s);
+            const bool up = ((t * 32 + lane) & kk) == 0;
+            // keep the smaller of the pair in the lower lane of an ascending block
+            if ((lower == up) == (pk < k[t])) k[t] = pk;
+          }
+        }
+      }
+    }
+  }
+}
+
 template <typename KT, int KB>
 __device__ __forceinline__ void get_entry(const unsigned long long (&k)[KB], int g, unsigned long long& out) {
   unsigned long long v = k[0];
@@ -425,8 +471,7 @@ __device__ __forceinline__ bool query_buf(const KnnArgs& A, const Grid32& G, con
           const float dz = (p.z - Q.fz) + (float)dzc * csz;
           const float D = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
           in = D <= rhof2;
-          key = __float_as_uint(D);
-          tj = r;
+          key = ((unsigned long long)__float_as_uint(D) << 32) | (unsigned)r;
         } else {
           long long jj;
           const double d2 = d2_fp64(A.pos64, r, Q.x, Q.y, Q.z, bx, by, jj);
@@ -437,7 +482,10 @@ __device__ __forceinline__ bool query_buf(const KnnArgs& A, const Grid32& G, con
       }
       const unsigned m = __ballot_sync(FULL, in);
       const int pos = n_in + __popc(m & ((1u << lane) - 1u));
-      if (in && pos < CAP) { buf.key[pos] = key; buf.j[pos] = tj; buf.r[pos] = r; }
+      if (in && pos < CAP) {
+        buf.key[pos] = key;
+        if (!kMixed) { buf.j[pos] = tj; buf.r[pos] = r; }
+      }
       n_in += __popc(m);
     });
     if (kMixed && amb) return false;
@@ -458,11 +506,22 @@ __device__ __forceinline__ bool query_buf(const KnnArgs& A, const Grid32& G, con
 #pragma unroll
     for (int t = 0; t < KB; ++t) {
       const int e = t * 32 + lane;
-      if (e < n_in) { k[t] = buf.key[e]; j[t] = buf.j[e]; r[t] = buf.r[e]; }
-      else { k[t] = ~0ull; j[t] = INT_MAX; r[t] = -1; }
+      if (kMixed) {
+        k[t] = e < n_in ? buf.key[e] : ~0ull;
+      } else if (e < n_in) {
+        k[t] = buf.key[e]; j[t] = buf.j[e]; r[t] = buf.r[e];
+      } else {
+        k[t] = ~0ull; j[t] = INT_MAX; r[t] = -1;
+      }
     }
     __syncwarp();
-    sort_any<KB>(n_in, k, j, r, lane);
+    if (kMixed) {
+      sort_packed<KB>(n_in, k, lane);
+#pragma unroll
+      for (int t = 0; t < KB; ++t) { r[t] = (int)(unsigned)k[t]; k[t] >>= 32; }
+    } else {
+      sort_any<KB>(n_in, k, j, r, lane);
+    }
     unsigned long long kL;
     get_entry<unsigned long long, KB>(k, L - 1, kL);
     int* row = A.nbr + q * (long long)A.K;
@@ -620,26 +679,39 @@ __global__ void __launch_bounds__(KnnShape<KPL>::WPB * 32, KnnShape<KPL>::MINB) 
       }
     }
     __syncwarp();
-    // ---- phase C: members by ascending caller index
-    for (int qi_ = 0; qi_ < 32; ++qi_) {
-      const long long q = base + qi_;
-      if (q >= A.N) break;
-      if (info[w][qi_].state == 0) continue;
-      int* row = A.nbr + q * (long long)A.K;
-      int jj[KPL], rr[KPL];
+    // ---- phase C: members by ascending caller index.  The rows and caller indices of
+    // kG queries are loaded before any of them is sorted, so their latencies overlap.
+    constexpr int kG = KPL <= 1 ? 4 : (KPL <= 2 ? 2 : 1);
+    for (int q0 = 0; q0 < 32; q0 += kG) {
+      int jj[kG][KPL], rr[kG][KPL];
+      bool live[kG];
 #pragma unroll
-      for (int t = 0; t < KPL; ++t) {
-        const int g = t * 32 + lane;
-        if (g < L) { rr[t] = row[1 + g]; jj[t] = __ldg(&A.perm[rr[t]]); }
-        else { rr[t] = -1; jj[t] = INT_MAX; }
-      }
-      sort_by_index<KPL>(jj, rr, lane);
+      for (int g = 0; g < kG; ++g) {
+        const long long q = base + q0 + g;
+        live[g] = q < A.N && info[w][q0 + g].state != 0;
 #pragma unroll
-      for (int t = 0; t < KPL; ++t) {
-        const int g = t * 32 + lane;
-        if (g < L) row[1 + g] = rr[t];
+        for (int t = 0; t < KPL; ++t) {
+          const int e = t * 32 + lane;
+          rr[g][t] = (live[g] && e < L) ? A.nbr[q * (long long)A.K + 1 + e] : -1;
+        }
       }
-      if (lane == 0) row[0] = (int)q;
+#pragma unroll
+      for (int g = 0; g < kG; ++g)
+#pragma unroll
+        for (int t = 0; t < KPL; ++t) jj[g][t] = rr[g][t] >= 0 ? __ldg(&A.perm[rr[g][t]]) : INT_MAX;
+#pragma unroll
+      for (int g = 0; g < kG; ++g) {
+        if (!live[g]) continue;
+        const long long q = base + q0 + g;
+        int* row = A.nbr + q * (long long)A.K;
+        sort_by_index<KPL>(jj[g], rr[g], lane);
+#pragma unroll
+        for (int t = 0; t < KPL; ++t) {
+          const int e = t * 32 + lane;
+          if (e < L) row[1 + e] = rr[g][t];
+        }
+        if (lane == 0) row[0] = (int)q;
+      }
     }
     __syncwarp();
   }

@@ -41,11 +41,14 @@ struct McArgs {
   long long range;     // ranks per block (rate kernel)
 };
 
-// Per-particle quantities that do not depend on the live diameter.
+// Per-particle quantities that do not depend on the live diameter.  The pair parameters
+// are held in the pair precision T, so the mixed form converts them once per particle.
+template <typename T>
 struct Fixed {
-  double gst, e2, e1, zo, cs, cB, Vg2, tRe, vfrag, m0;
+  T gst, e2, e1, zo, cs, cB, Vg2, tRe, vfrag, m0;
   double pref;        // lambda = pref * (pair rate in kernel units)
   double rho_s, s_min, M;
+  double k6;          // 6 / (pi rho_s): s^3 = k6 m
   int mode;
 };
 
@@ -57,8 +60,8 @@ __device__ __forceinline__ double prefactor(const InstDev& P, double V, int K) {
 }
 
 template <typename T>
-__device__ __forceinline__ Fixed make_fixed(const InstDev& P, const Gas& g, double V, double M, int K) {
-  Fixed f;
+__device__ __forceinline__ Fixed<T> make_fixed(const InstDev& P, const Gas& g, double V, double M, int K) {
+  Fixed<T> f;
   f.gst = g.gst;
   f.e2 = 2.0 * g.eta * g.R * g.Om;
   f.e1 = g.eta * g.R * g.Om;
@@ -73,6 +76,7 @@ __device__ __forceinline__ Fixed make_fixed(const InstDev& P, const Gas& g, doub
   f.rho_s = P.rho_s;
   f.s_min = P.s_min;
   f.M = M;
+  f.k6 = 6.0 / (kPi * P.rho_s);
   f.mode = P.kernel_mode;
   return f;
 }
@@ -80,45 +84,46 @@ __device__ __forceinline__ Fixed make_fixed(const InstDev& P, const Gas& g, doub
 // Mixed form: the same quantities in FP32 (they only feed FP32 pair arithmetic).
 // Omega = sqrt(GM/R)/R keeps R^3 out of the FP32 range, and
 // 1 - R/r = Z^2/(r (r + R)) avoids the cancellation of the literal form.
-__device__ __forceinline__ Fixed make_fixed_f32(const InstDev& P, double x, double y, double z, double V,
+__device__ __forceinline__ Fixed<float> make_fixed_f32(const InstDev& P, double x, double y, double z, double V,
                                                 double M, int K) {
   const float R = P.geometry == GD_GEOM_PATCH ? (float)(P.r0 + x) : sqrtf((float)x * (float)x + (float)y * (float)y);
   const float Z = (float)z;
   const float r = sqrtf(R * R + Z * Z);
-  const float Om = sqrtf((float)P.GM / R) / R;
-  const float xr = R / (float)P.r0;
-  const float T = (float)P.T0 * powf(xr, (float)P.q);
+  const float Om = sqrtf(P.f_GM / R) / R;
+  const float xr = R / P.f_r0;
+  const float T = P.f_T0 * powf(xr, P.f_q);
   const float cs = sqrtf((float)(kKB / (kMu * kMH)) * T);
   const float H = cs / Om;
   const float h = H / R;
-  const float Sigma = (float)P.sigma0 * powf(xr, (float)P.p);
+  const float Sigma = P.f_sigma0 * powf(xr, P.f_p);
   const float omr = Z * Z / (r * (r + R));
   const float vert = omr / (h * h);
   const float rho = Sigma / (2.5066283f * H) * expf(-vert);
-  const float eta = -0.5f * (((float)P.p + 0.5f * (float)P.q - 1.5f) * h * h + (float)P.q * omr);
+  const float eta = -0.5f * ((P.f_p + 0.5f * P.f_q - 1.5f) * h * h + P.f_q * omr);
   const float numol = 0.5f * 1.5957691f * cs * ((float)(kMu * kMH / kSigH2) / rho);
-  Fixed f;
-  f.gst = (double)(3.14159265f * (float)P.rho_s / (4.0f * Sigma) * expf(vert));
-  f.e2 = (double)(2.0f * eta * R * Om);
-  f.e1 = (double)(eta * R * Om);
-  f.zo = (double)(Z * Om);
-  f.cs = (double)cs;
-  f.cB = (double)((float)(8.0 * kKB / kPi) * T);
-  f.Vg2 = (double)(1.5f * (float)P.alpha * cs * cs);
-  f.tRe = (double)rsqrtf((float)P.alpha * cs * H / numol);
-  f.vfrag = P.v_frag;
-  f.m0 = P.m0;
+  Fixed<float> f;
+  f.gst = 3.14159265f * P.f_rho_s / (4.0f * Sigma) * expf(vert);
+  f.e2 = 2.0f * eta * R * Om;
+  f.e1 = eta * R * Om;
+  f.zo = Z * Om;
+  f.cs = cs;
+  f.cB = (float)(8.0 * kKB / kPi) * T;
+  f.Vg2 = 1.5f * P.f_alpha * cs * cs;
+  f.tRe = rsqrtf(P.f_alpha * cs * H / numol);
+  f.vfrag = P.f_vfrag;
+  f.m0 = P.f_m0;
   f.pref = prefactor<float>(P, V, K);
   f.rho_s = P.rho_s;
   f.s_min = P.s_min;
   f.M = M;
+  f.k6 = P.k6;
   f.mode = P.kernel_mode;
   return f;
 }
 
 // <J>, <J^2> of a fragmentation in FP32 (mixed form; they only feed the bin moments).
 __device__ __forceinline__ void frag_moments_f32(double s_i, double s_min, double& j1, double& j2) {
-  const float a = sqrtf((float)(s_min / s_i));
+  const float a = sqrtf((float)s_min / (float)s_i);
   if (!(a < 1.0f)) { j1 = 0.0; j2 = 0.0; return; }
   const float dd = 1.0f - a;
   if (dd < 1e-2f) {
@@ -135,7 +140,7 @@ __device__ __forceinline__ void frag_moments_f32(double s_i, double s_min, doubl
 // form: FP32 from the rounded s, m and gst (the rate kernel and the sampler build it with
 // this one function, so both see the same pair rates).
 template <typename T>
-__device__ __forceinline__ Query<T> live_query(const Fixed& f, double s, double m) {
+__device__ __forceinline__ Query<T> live_query(const Fixed<T>& f, double s, double m) {
   Query<T> q;
   if constexpr (sizeof(T) == 8) {
     double St = f.gst * s;
@@ -145,7 +150,7 @@ __device__ __forceinline__ Query<T> live_query(const Fixed& f, double s, double 
     q.bi = 1.0 / (1.0 + St * St);
     q.hi = St < 0.5 ? St : 0.5;
   } else {
-    const float sf = (float)s, mf = (float)m, St = (float)f.gst * sf;
+    const float sf = (float)s, mf = (float)m, St = f.gst * sf;
     const float bi = 1.0f / (1.0f + St * St);
     q.s = sf; q.m = mf; q.inv_m = 1.0f / mf;
     q.St = St;
@@ -153,10 +158,10 @@ __device__ __forceinline__ Query<T> live_query(const Fixed& f, double s, double 
     q.bi = bi;
     q.hi = St < 0.5f ? St : 0.5f;
   }
-  q.g = (T)f.gst;
-  q.e2 = (T)f.e2; q.e1 = (T)f.e1; q.zo = (T)f.zo;
-  q.cs = (T)f.cs; q.cB = (T)f.cB; q.Vg2 = (T)f.Vg2; q.tRe = (T)f.tRe;
-  q.vfrag = (T)f.vfrag; q.m0 = (T)f.m0;
+  q.g = f.gst;
+  q.e2 = f.e2; q.e1 = f.e1; q.zo = f.zo;
+  q.cs = f.cs; q.cB = f.cB; q.Vg2 = f.Vg2; q.tRe = f.tRe;
+  q.vfrag = f.vfrag; q.m0 = f.m0;
   q.mode = f.mode;
   return q;
 }
@@ -176,8 +181,9 @@ __device__ __forceinline__ Query<T> shfl_query(const Query<T>& a, int src) {
   return q;
 }
 
-__device__ __forceinline__ Fixed shfl_fixed(const Fixed& a, int src) {
-  Fixed f;
+template <typename T>
+__device__ __forceinline__ Fixed<T> shfl_fixed(const Fixed<T>& a, int src) {
+  Fixed<T> f;
   f.gst = __shfl_sync(FULLM, a.gst, src);
   f.e2 = __shfl_sync(FULLM, a.e2, src);
   f.e1 = __shfl_sync(FULLM, a.e1, src);
@@ -192,6 +198,7 @@ __device__ __forceinline__ Fixed shfl_fixed(const Fixed& a, int src) {
   f.rho_s = __shfl_sync(FULLM, a.rho_s, src);
   f.s_min = __shfl_sync(FULLM, a.s_min, src);
   f.M = __shfl_sync(FULLM, a.M, src);
+  f.k6 = __shfl_sync(FULLM, a.k6, src);
   f.mode = __shfl_sync(FULLM, a.mode, src);
   return f;
 }
@@ -238,36 +245,83 @@ __device__ __forceinline__ double lane_channels(const McArgs& A, const Query<T>&
   return v;
 }
 
-// Diameter from s^3 = 6 m/(pi rho_o).  FP64 form: cbrt.  Mixed form: the FP32 cube root
-// refined by one Newton step for y^3 = x in FP64, y <- y - (y^3 - x)/(3 y^2), which
-// brings the 2^-24 start to ~1e-14 relative at a fraction of the FP64 instructions.
+// Relative tolerance of a near tie (a draw this close to a decision boundary is counted):
+// FP64 form 1e-10; mixed form 2e-5, above the FP32 error of the pair rates.
+template <typename T> __device__ __forceinline__ double tie_tol() { return sizeof(T) == 8 ? 1e-10 : 2e-5; }
+
+// s^3 = 6 m / (pi rho_o).  The mixed form multiplies by the per-particle constant.
+template <typename T>
+__device__ __forceinline__ double cube_of(const Fixed<T>& f, double m) {
+  if constexpr (sizeof(T) == 8) return 6.0 * m / (kPi * f.rho_s); else return m * f.k6;
+}
+
+// Diameter from s^3 = x.  FP64 form: cbrt.  Mixed form: the FP32 cube root y refined by
+// one Newton step for y^3 = x, y <- y - (y^3 - x)/(3 y^2), with the residual in FP64 and
+// the 1/(3 y^2) factor in FP32: ~1e-13 relative for a handful of FP64 instructions.
 template <typename T>
 __device__ __forceinline__ double diameter_of(double x) {
   if constexpr (sizeof(T) == 8) {
     return cbrt(x);
   } else {
-    const double y = (double)cbrtf((float)x);
-    return y - (y * y * y - x) / (3.0 * y * y);
+    const float yf = cbrtf((float)x);
+    const double y = (double)yf;
+    const float c = (float)(y * y * y - x) * __frcp_rn(3.0f * yf * yf);
+    return y - (double)c;
+  }
+}
+
+// -ln U for U = (k + 1/2) 2^-52, k = (a >> 6) 2^26 + (b >> 6) (the u01 map), in FP32
+// without FP64 instructions.  For U >= 1/2 it is -log1p(-(1 - U)) with 1 - U formed from
+// the complement of k, so short waits keep their relative accuracy.
+__device__ __forceinline__ float neg_log_u01_f32(uint32_t a, uint32_t b) {
+  const uint32_t hi = a >> 6, lo = b >> 6;
+  if (hi >= (1u << 25)) {
+    const float v = fmaf((float)((1u << 26) - 1u - hi), 0x1p26f, (float)((1u << 26) - 1u - lo) + 0.5f) * 0x1p-52f;
+    return -log1pf(-v);
+  }
+  return -logf(fmaf((float)hi, 0x1p26f, (float)lo + 0.5f) * 0x1p-52f);
+}
+
+// Waiting time -ln(U_w) / lambda*_i.  FP64 form: FP64 throughout.  Mixed form: FP32
+// (lambda*_i is an FP32 sum of FP32 rates); the caller accumulates it in FP64.
+template <typename T>
+__device__ __forceinline__ double waiting_time(uint32_t a, uint32_t b, double lam) {
+  if constexpr (sizeof(T) == 8) {
+    return -log(u01(a, b)) / lam;
+  } else {
+    const float nl = neg_log_u01_f32(a, b);
+    if (lam >= 1e-30 && lam <= 1e30) return (double)(nl / (float)lam);
+    return (double)nl / lam;
   }
 }
 
 // ---------------------------------------------------------------- rate kernel
 template <typename T, int S>
 __global__ void __launch_bounds__(256) k_rates(McArgs A) {
+  // block-level fine-bin sums of the block's first instance: FP64 form in FP64; mixed form
+  // in FP32 (native shared atomics; they only feed the interval controller), then added
+  // to the instance's FP64 bins once per block
   __shared__ double sh[4][kNFine];
+  __shared__ float shf[3][kNFine];
+  __shared__ unsigned shc[kNFine];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const long long lo = (long long)blockIdx.x * A.range;
   const long long hi = min(lo + A.range, A.N);
   if (lo >= hi) return;
   const int b_lo = inst_of(A.off, A.n_inst, lo), b_hi = inst_of(A.off, A.n_inst, hi - 1);
   const bool shared_bins = (b_lo == b_hi);
-  for (int t = threadIdx.x; t < 4 * kNFine; t += blockDim.x) sh[t / kNFine][t % kNFine] = 0.0;
+  if constexpr (sizeof(T) == 8) {
+    for (int t = threadIdx.x; t < 4 * kNFine; t += blockDim.x) sh[t / kNFine][t % kNFine] = 0.0;
+  } else {
+    for (int t = threadIdx.x; t < 3 * kNFine; t += blockDim.x) shf[t / kNFine][t % kNFine] = 0.0f;
+    for (int t = threadIdx.x; t < kNFine; t += blockDim.x) shc[t] = 0u;
+  }
   __syncthreads();
   for (long long base = lo + 32LL * wib; base < hi; base += 32LL * nw) {
     const long long r = base + lane;
     const bool valid = r < hi;
     int b = 0;
-    Fixed fx;
+    Fixed<T> fx;
     double s_i = 1.0, m_i = 1.0, fj1 = 0.0, fj2 = 0.0;
     if (valid) {
       b = inst_of(A.off, A.n_inst, r);
@@ -278,18 +332,18 @@ __global__ void __launch_bounds__(256) k_rates(McArgs A) {
       m_i = sn.m;
       if constexpr (sizeof(T) == 8) {
         Gas g = gas_at(P, p.x, p.y, p.z);
-        fx = make_fixed<T>(P, g, A.V[r], A.Mr[r], A.K);
+        fx = make_fixed<double>(P, g, A.V[r], A.Mr[r], A.K);
         frag_moments(s_i, P.s_min, fj1, fj2);
       } else {
         fx = make_fixed_f32(P, p.x, p.y, p.z, A.V[r], A.Mr[r], A.K);
         frag_moments_f32(s_i, P.s_min, fj1, fj2);
       }
     } else {
-      fx = Fixed{};
+      fx = Fixed<T>{};
       fx.pref = 0.0;
       fx.mode = 0;
     }
-    double my_tot = 0.0, my_a = 0.0, my_b = 0.0;
+    T my_tot = (T)0, my_a = (T)0, my_b = (T)0;     // lane = particle; converted once below
     const Query<T> myq = live_query<T>(fx, s_i, m_i);     // lane = particle
     const T myj1 = (T)fj1, myj2 = (T)fj2;
     const double mypref = fx.pref;
@@ -304,7 +358,7 @@ __global__ void __launch_bounds__(256) k_rates(McArgs A) {
       T c0[S], c1[S];
       int jr[S];
       PairOut<T> po[S];
-      double tot;
+      T tot;
       if constexpr (sizeof(T) == 8) {
         // FP64 form: the sampler's own scan, so lambda*_i is the same number there
         const double v = lane_channels<T, S>(A, q, row, lane, c0, c1, jr, po);
@@ -315,7 +369,7 @@ __global__ void __launch_bounds__(256) k_rates(McArgs A) {
         float vf = 0.0f;
 #pragma unroll
         for (int t = 0; t < S; ++t) vf += c0[t] + c1[t];
-        tot = (double)warp_sumf(vf);
+        tot = warp_sumf(vf);
       }
       T la = (T)0, lb = (T)0;
 #pragma unroll
@@ -326,9 +380,9 @@ __global__ void __launch_bounds__(256) k_rates(McArgs A) {
         la += a;
         lb += bb;
       }
-      double sa, sb;
+      T sa, sb;
       if constexpr (sizeof(T) == 8) { sa = warp_sum(la); sb = warp_sum(lb); }
-      else { sa = (double)warp_sumf(la); sb = (double)warp_sumf(lb); }
+      else { sa = warp_sumf(la); sb = warp_sumf(lb); }
       if (lane == p) { my_tot = tot; my_a = sa; my_b = sb; }
       if (A.chan_out) {
         const long long ci = (long long)A.perm[rp] * A.K;
@@ -344,18 +398,25 @@ __global__ void __launch_bounds__(256) k_rates(McArgs A) {
       }
     }
     if (valid) {
-      double lam = fx.pref * my_tot;
+      double lam = fx.pref * (double)my_tot;
       A.lam[r] = lam;
       if (!isfinite(lam)) set_status(&A.st[b], GD_ST_NONFINITE);
       int fbin = fine_bin(s_i);
       double M = fx.M;
-      double va = M * (fx.pref * my_a), vb = M * (fx.pref * my_b);
-      if (shared_bins) {
+      if (sizeof(T) == 4 && b == b_lo) {
+        const float Mf = (float)M, pf = (float)fx.pref;
+        atomicAdd(&shc[fbin], 1u);
+        atomicAdd(&shf[0][fbin], Mf);
+        atomicAdd(&shf[1][fbin], Mf * (pf * (float)my_a));
+        atomicAdd(&shf[2][fbin], Mf * (pf * (float)my_b));
+      } else if (sizeof(T) == 8 && shared_bins) {
+        double va = M * (fx.pref * (double)my_a), vb = M * (fx.pref * (double)my_b);
         atomicAdd(&sh[0][fbin], 1.0);
         atomicAdd(&sh[1][fbin], M);
         atomicAdd(&sh[2][fbin], va);
         atomicAdd(&sh[3][fbin], vb);
       } else {
+        double va = M * (fx.pref * (double)my_a), vb = M * (fx.pref * (double)my_b);
         BinsDev* bn = &A.bins[b];
         atomicAdd(&bn->cnt[fbin], 1.0);
         atomicAdd(&bn->sM[fbin], M);
@@ -364,7 +425,18 @@ __global__ void __launch_bounds__(256) k_rates(McArgs A) {
       }
     }
   }
-  if (shared_bins) {
+  if constexpr (sizeof(T) == 4) {
+    __syncthreads();
+    BinsDev* bn = &A.bins[b_lo];
+    for (int t = threadIdx.x; t < kNFine; t += blockDim.x) {
+      if (shc[t] != 0u) {
+        atomicAdd(&bn->cnt[t], (double)shc[t]);
+        atomicAdd(&bn->sM[t], (double)shf[0][t]);
+        atomicAdd(&bn->sA[t], (double)shf[1][t]);
+        atomicAdd(&bn->sB[t], (double)shf[2][t]);
+      }
+    }
+  } else if (shared_bins) {
     __syncthreads();
     BinsDev* bn = &A.bins[b_lo];
     for (int t = threadIdx.x; t < kNFine; t += blockDim.x) {
@@ -384,7 +456,7 @@ __global__ void __launch_bounds__(256) k_rates(McArgs A) {
 // remainder joins the previous bin), forms A_b and B_b in one ascending pass, and halves
 // dt_coll with the exact tick count of the time left.
 __global__ void k_interval(const InstDev* __restrict__ P, StateDev* st, BinsDev* bins, int n_inst, int K,
-                           int no_audit) {
+                           int no_audit, double tie) {
   __shared__ double cnt[kNFine], sM[kNFine], sA[kNFine], sB[kNFine];
   __shared__ double gM[kNFine], gA[kNFine], gB[kNFine];
   __shared__ int gid[kNFine];
@@ -435,8 +507,8 @@ __global__ void k_interval(const InstDev* __restrict__ P, StateDev* st, BinsDev*
   int k = 0;
   while (k < 60 && (dt > dt_req || (1LL << (60 - k)) > S.remain_ticks)) { dt = 0.5 * dt; ++k; }
   if (dt > dt_req) S.status |= GD_ST_DT_FLOOR;
-  if (dt_ab <= dt_cap * (1.0 + 1e-10) &&
-      (fabs(dt - dt_ab) <= 1e-10 * dt_ab || fabs(2.0 * dt - dt_ab) <= 1e-10 * dt_ab))
+  if (dt_ab <= dt_cap * (1.0 + tie) &&
+      (fabs(dt - dt_ab) <= tie * dt_ab || fabs(2.0 * dt - dt_ab) <= tie * dt_ab))
     S.near_dt++;
   S.dt_req = dt_req;
   S.dt_exe = dt;
@@ -473,11 +545,10 @@ __global__ void __launch_bounds__(256) k_sample(McArgs A) {
       i_loc = (unsigned)(A.perm[r] - P.off);
       lam = A.lam[r];
       U4 w = philox(i_loc, ival, 0u, 0u, key0, key1);
-      double uw = u01(w.x, w.y);
       us = u01(w.z, w.w);
       if (lam > 0.0 && isfinite(lam)) {
-        dtw = -log(uw) / lam;
-        if (fabs(dtw - dt_exe) < 1e-10 * dt_exe) nn++;
+        dtw = waiting_time<T>(w.x, w.y, lam);
+        if (fabs(dtw - dt_exe) < tie_tol<T>() * dt_exe) nn++;
         ev = !(dtw > dt_exe);
       }
     }
@@ -493,7 +564,7 @@ __global__ void __launch_bounds__(256) k_sample(McArgs A) {
       continue;
     }
     // per-lane fixed quantities of every particle of the chunk (lane = particle)
-    Fixed fx;
+    Fixed<T> fx;
     double s_i = 1.0, m_i = 1.0;
     if (valid) {
       const InstDev& P = A.P[b];
@@ -503,12 +574,12 @@ __global__ void __launch_bounds__(256) k_sample(McArgs A) {
       m_i = sn.m;
       if constexpr (sizeof(T) == 8) {
         Gas g = gas_at(P, p.x, p.y, p.z);
-        fx = make_fixed<T>(P, g, A.V[r], A.Mr[r], A.K);
+        fx = make_fixed<double>(P, g, A.V[r], A.Mr[r], A.K);
       } else {
         fx = make_fixed_f32(P, p.x, p.y, p.z, A.V[r], A.Mr[r], A.K);
       }
     } else {
-      fx = Fixed{};
+      fx = Fixed<T>{};
       fx.mode = 0;
     }
     int my_e = 0;
@@ -517,7 +588,7 @@ __global__ void __launch_bounds__(256) k_sample(McArgs A) {
       const int p = __ffs(emask) - 1;
       emask &= emask - 1;
       const long long rp = base + p;
-      const Fixed f = shfl_fixed(fx, p);
+      const Fixed<T> f = shfl_fixed<T>(fx, p);
       double s = __shfl_sync(FULLM, s_i, p), m = __shfl_sync(FULLM, m_i, p);
       double t = __shfl_sync(FULLM, dtw, p);
       double u_s = __shfl_sync(FULLM, us, p);
@@ -529,7 +600,7 @@ __global__ void __launch_bounds__(256) k_sample(McArgs A) {
       const double s_start = s;
       int e = 0, near_ch = 0, near_u = 0;   // per-lane channel ties, warp-uniform ties
       unsigned h = 0u;
-      double J = 0.0;
+      T J = (T)0;
       T c0[S], c1[S];
       int jr[S];
       PairOut<T> po[S];
@@ -540,6 +611,7 @@ __global__ void __launch_bounds__(256) k_sample(McArgs A) {
       for (;;) {
         // partner channel: the first cumulative rate above U_s lambda*
         const double target = u_s * tot;
+        const double tie_ch = tie_tol<T>() * tot;
         double cum = __shfl_up_sync(FULLM, incl, 1);
         if (lane == 0) cum = 0.0;
         int sel = INT_MAX, lastnz = -1;
@@ -551,13 +623,13 @@ __global__ void __launch_bounds__(256) k_sample(McArgs A) {
           cum = __dadd_rn(cum, a);
           if (a > 0.0) {
             lastnz = 2 * k;
-            if (fabs(target - cum) < 1e-10 * tot) near_ch++;
+            if (fabs(target - cum) < tie_ch) near_ch++;
             if (sel == INT_MAX && target < cum) sel = 2 * k;
           }
           cum = __dadd_rn(cum, bb);
           if (bb > 0.0) {
             lastnz = 2 * k + 1;
-            if (fabs(target - cum) < 1e-10 * tot) near_ch++;
+            if (fabs(target - cum) < tie_ch) near_ch++;
             if (sel == INT_MAX && target < cum) sel = 2 * k + 1;
           }
         }
@@ -587,23 +659,32 @@ __global__ void __launch_bounds__(256) k_sample(McArgs A) {
         double m_new, s_new;
         if (outcome == 0) {
           m_new = m + ncoll * pj.m;
-          s_new = diameter_of<T>(6.0 * m_new / (kPi * f.rho_s));
+          s_new = diameter_of<T>(cube_of<T>(f, m_new));
         } else if (outcome == 1 && ch == 0) {
           m_new = m - ncoll * pj.m;
-          s_new = diameter_of<T>(6.0 * m_new / (kPi * f.rho_s));
+          s_new = diameter_of<T>(cube_of<T>(f, m_new));
         } else if (outcome == 1) {
           m_new = pj.m;
           s_new = pj.s;
         } else {
           U4 w2 = philox(il, iv, (unsigned)e, 1u, k0, k1);
-          double U = u01(w2.x, w2.y);
-          double a = sqrt(f.s_min), bq = sqrt(s);
-          double xr = a + U * (bq - a);
-          s_new = xr * xr;
-          m_new = kPi * f.rho_s * s_new * s_new * s_new / 6.0;
+          if constexpr (sizeof(T) == 8) {
+            double U = u01(w2.x, w2.y);
+            double a = sqrt(f.s_min), bq = sqrt(s);
+            double xr = a + U * (bq - a);
+            s_new = xr * xr;
+            m_new = kPi * f.rho_s * s_new * s_new * s_new / 6.0;
+          } else {
+            // the fragment size is a draw: FP32 is enough; the mass follows it in FP64
+            const float U = fmaf((float)(w2.x >> 6), 0x1p26f, (float)(w2.y >> 6) + 0.5f) * 0x1p-52f;
+            const float a = sqrtf((float)f.s_min), bq = sqrtf((float)s);
+            const float xr = fmaf(U, bq - a, a);
+            s_new = (double)(xr * xr);
+            m_new = s_new * s_new * s_new / f.k6;
+          }
         }
         if constexpr (sizeof(T) == 8) J += fabs(log(s_new / s));
-        else J += (double)fabsf(logf((float)(s_new / s)));
+        else J += fabsf(log1pf((float)(s_new - s) / (float)s));
         s = s_new;
         m = m_new;
         h = h * 31u + (unsigned)(chosen + 1);
@@ -619,10 +700,9 @@ __global__ void __launch_bounds__(256) k_sample(McArgs A) {
           break;
         }
         U4 w = philox(il, iv, (unsigned)e, 0u, k0, k1);
-        double uw = u01(w.x, w.y);
         u_s = u01(w.z, w.w);
-        double dt2 = -log(uw) / lam_now;
-        if (fabs((t + dt2) - dte) < 1e-10 * dte) near_u++;
+        const double dt2 = waiting_time<T>(w.x, w.y, lam_now);
+        if (fabs((t + dt2) - dte) < tie_tol<T>() * dte) near_u++;
         if (t + dt2 > dte) break;
         t = t + dt2;
       }
@@ -635,7 +715,7 @@ __global__ void __launch_bounds__(256) k_sample(McArgs A) {
         int ci = A.perm[rp];
         A.s_out[ci] = s;
         atomicAdd((unsigned long long*)&A.st[bp].events, (unsigned long long)e);
-        if (J > 0.0) atomicAdd(&A.bins[bp].sJ[fine_bin(s_start)], f.M * J);
+        if (J > (T)0) atomicAdd(&A.bins[bp].sJ[fine_bin(s_start)], f.M * (double)J);
       }
     }
     if (valid && nn) atomicAdd((unsigned long long*)&A.st[b].near_draw, (unsigned long long)nn);
@@ -652,7 +732,8 @@ __global__ void __launch_bounds__(256) k_sample(McArgs A) {
 // One block per instance: realised mass-weighted sum of |ln(s'/s)| per controller bin
 // against 2 eps C; C halves (>= 1/4) on excess, else grows by 1.25 (<= 1).  Clears the
 // fine bins for the next interval.
-__global__ void k_audit(const InstDev* __restrict__ P, StateDev* st, BinsDev* bins, int n_inst, int no_audit) {
+__global__ void k_audit(const InstDev* __restrict__ P, StateDev* st, BinsDev* bins, int n_inst, int no_audit,
+                        double tie) {
   __shared__ double sM[kNFine], sJ[kNFine], gM[kNFine], gJ[kNFine];
   __shared__ int gid[kNFine];
   const int b = blockIdx.x;
@@ -672,7 +753,7 @@ __global__ void k_audit(const InstDev* __restrict__ P, StateDev* st, BinsDev* bi
       bool exceed = false;
       for (int g = 0; g < Bn.ngroups; ++g) {
         const double Rg = gJ[g] / gM[g];
-        if (fabs(Rg - thr) <= 1e-10 * thr) S.near_audit++;
+        if (fabs(Rg - thr) <= tie * thr) S.near_audit++;
         if (Rg > thr) exceed = true;
       }
       S.C = exceed ? fmax(0.25, 0.5 * S.C) : fmin(1.0, 1.25 * S.C);
@@ -746,7 +827,8 @@ cudaError_t launch_rates(gd_ctx* c, double* chan_out) {
 cudaError_t launch_interval(gd_ctx* c) {
   time_begin(c, 3);
   k_interval<<<c->n_inst, 128, 0, c->stream>>>(c->d_inst, c->d_state, c->d_bins, c->n_inst, c->K,
-                                               (c->flags & GD_FLAG_NO_AUDIT) ? 1 : 0);
+                                               (c->flags & GD_FLAG_NO_AUDIT) ? 1 : 0,
+                                               c->precision == GD_MIXED ? 2e-5 : 1e-10);
   time_end(c);
   c->launches += 1;
   return cudaGetLastError();
@@ -787,7 +869,8 @@ cudaError_t launch_sample(gd_ctx* c, int* ev_count, unsigned* ev_hash, int* near
 cudaError_t launch_audit(gd_ctx* c) {
   time_begin(c, 3);
   k_audit<<<c->n_inst, 128, 0, c->stream>>>(c->d_inst, c->d_state, c->d_bins, c->n_inst,
-                                            (c->flags & GD_FLAG_NO_AUDIT) ? 1 : 0);
+                                            (c->flags & GD_FLAG_NO_AUDIT) ? 1 : 0,
+                                            c->precision == GD_MIXED ? 2e-5 : 1e-10);
   time_end(c);
   c->launches += 1;
   return cudaGetLastError();

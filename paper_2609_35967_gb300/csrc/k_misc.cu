@@ -53,34 +53,6 @@ __global__ void k_push(long long N, int n_inst, const long long* __restrict__ of
   lph[i] = LP;
 }
 
-// One block per instance, fixed-order (deterministic) sums of M, M m and M s.
-__global__ void k_stats(const long long* __restrict__ off, const InstDev* __restrict__ P,
-                        const double* __restrict__ s, const double* __restrict__ M, double* out) {
-  int b = blockIdx.x;
-  long long lo = off[b], hi = off[b + 1];
-  const InstDev& p = P[b];
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    double si = s[i], Mi = M[i];
-    double m = grain_mass(p, si);
-    a0 += Mi;
-    a1 += Mi * m;
-    a2 += Mi * si;
-  }
-  __shared__ double sh[3][1024];
-  sh[0][threadIdx.x] = a0;
-  sh[1][threadIdx.x] = a1;
-  sh[2][threadIdx.x] = a2;
-  __syncthreads();
-  for (int w = blockDim.x >> 1; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w)
-      for (int k = 0; k < 3; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0)
-    for (int k = 0; k < 3; ++k) out[3 * b + k] = sh[k][0];
-}
-
 __global__ void k_out_knn(long long N, int K, const int* __restrict__ rank_of, const int* __restrict__ perm,
                           const int* __restrict__ nbr, const double* __restrict__ dist, int* nbr_out,
                           double* d_out) {
@@ -104,14 +76,6 @@ cudaError_t launch_push(gd_ctx* c, double dt) {
   int blocks = (int)((c->N + 255) / 256);
   k_push<<<blocks, 256, 0, c->stream>>>(c->N, c->n_inst, c->d_off, c->d_inst, c->d_state, dt, c->x, c->y,
                                          c->z, c->vr, c->lth, c->lph, c->s);
-  time_end(c);
-  c->launches += 1;
-  return cudaGetLastError();
-}
-
-cudaError_t launch_stats(gd_ctx* c, double* d_sums) {
-  time_begin(c, 6);
-  k_stats<<<c->n_inst, 1024, 0, c->stream>>>(c->d_off, c->d_inst, c->s, c->M, d_sums);
   time_end(c);
   c->launches += 1;
   return cudaGetLastError();

@@ -8,7 +8,10 @@ Bars (from the method's precision split):
   near tie (a draw within 1e-10 of a boundary) was flagged on either side;
 * diameters after sampling: within 1e-12 relative (FP64) where the sequences agree;
 * represented mass: never written (bitwise), sum N m = sum M within 1e-12;
-* mixed form: lists bit-exact; rates, events and sizes reported with stated bounds.
+* mixed form: lists bit-exact; rates lambda*_i within 1e-4 relative; event sequences
+  identical except near ties at the mixed tolerance (2e-5 of a boundary, above the FP32
+  error of the rates) and at most a few grouping/outcome-threshold flips per thousand
+  event particles; diameters within 1e-5 relative where the sequences agree.
 """
 import math
 
@@ -55,13 +58,22 @@ def test_patch_interval_parity(gd, oracle, precision):
             assert rel.max() < 1e-12
         else:
             assert rel.max() < 1e-4, rel.max()
-        same = _compare_events(ref, got) if precision == 0 else None
         stats = sess.stats()
         inst = stats["instances"][0]
-        assert inst["dt_exe"] == st.dt_exe or inst["near_dt"] > 0 or precision == 1
         s_gpu = sess.t["s"].cpu().numpy()
-        if precision == 0:
+        if inst["dt_exe"] != st.dt_exe:
+            # only a flagged near tie of the interval or audit rule may change the interval
+            assert inst["near_dt"] + inst["near_audit"] + st.near_dt + st.near_audit > 0
+        elif precision == 0:
+            same = _compare_events(ref, got)
             assert np.abs(s_gpu[same] / s_or[same] - 1.0).max() < 1e-12
+        else:
+            same = (ref["ev_count"] == got["ev_count"]) & (ref["ev_hash"] == got["ev_hash"])
+            flagged = (ref["near"] > 0) | (got["near"] > 0)
+            n_ev = int((ref["ev_count"] > 0).sum())
+            bad = int((~same & ~flagged).sum())
+            assert bad <= max(2, 1e-3 * n_ev), (bad, n_ev)
+            assert np.abs(s_gpu[same] / s_or[same] - 1.0).max() < 1e-5
         # keep both sides on the same state for the next interval
         import torch
         sess.t["s"].copy_(torch.as_tensor(s_or, device=sess.device))
