@@ -39,6 +39,7 @@ struct McArgs {
   int* near_out;
   long long max_events;
   long long range;     // ranks per block (rate kernel)
+  unsigned long long* work;   // sampler: next chunk of 32 ranks (zeroed before the launch)
 };
 
 // Per-particle quantities that do not depend on the live diameter.  The pair parameters
@@ -220,22 +221,36 @@ __device__ __forceinline__ Partner<T> load_partner(const McArgs& A, int j) {
   return p;
 }
 
-// Channel rates of the S slots of this lane for particle row, plus the lane's
+// Neighbour ranks of the S slots of this lane in the row of rank rp (-1 past K).
+template <int S>
+__device__ __forceinline__ void load_row_slots(const McArgs& A, long long rp, int lane, int (&jr)[S]) {
+  const int* row = A.nbr + rp * A.K;
+#pragma unroll
+  for (int t = 0; t < S; ++t) {
+    const int k = lane * S + t;
+    jr[t] = k < A.K ? __ldg(row + k) : -1;
+  }
+}
+
+template <typename T, int S>
+__device__ __forceinline__ void load_partners(const McArgs& A, const int (&jr)[S], Partner<T> (&pt)[S]) {
+#pragma unroll
+  for (int t = 0; t < S; ++t)
+    if (jr[t] >= 0) pt[t] = load_partner<T>(A, jr[t]);
+}
+
+// Channel rates of the S slots of this lane from loaded partners, plus the lane's
 // sequential sum in FP64 (slot-major, channel-minor).
 template <typename T, int S>
-__device__ __forceinline__ double lane_channels(const McArgs& A, const Query<T>& q, const int* row, int lane,
-                                                T (&c0)[S], T (&c1)[S], int (&jr)[S], PairOut<T> (&po)[S]) {
+__device__ __forceinline__ double channels_of(const Query<T>& q, const int (&jr)[S], const Partner<T> (&pt)[S],
+                                              T (&c0)[S], T (&c1)[S], PairOut<T> (&po)[S]) {
   double v = 0.0;
 #pragma unroll
   for (int t = 0; t < S; ++t) {
-    int k = lane * S + t;
-    c0[t] = (T)0; c1[t] = (T)0; jr[t] = -1;
+    c0[t] = (T)0; c1[t] = (T)0;
     po[t].outcome = 0; po[t].ncoll = (T)1; po[t].psi = (T)0;
-    if (k < A.K) {
-      int j = __ldg(row + k);
-      jr[t] = j;
-      Partner<T> p = load_partner<T>(A, j);
-      po[t] = pair_channels<T>(q, p.s, p.m, p.Nq, p.inv_m);
+    if (jr[t] >= 0) {
+      po[t] = pair_channels<T>(q, pt[t].s, pt[t].m, pt[t].Nq, pt[t].inv_m);
       c0[t] = po[t].c0;
       c1[t] = po[t].c1;
       v = __dadd_rn(v, (double)c0[t]);
@@ -243,6 +258,15 @@ __device__ __forceinline__ double lane_channels(const McArgs& A, const Query<T>&
     }
   }
   return v;
+}
+
+template <typename T, int S>
+__device__ __forceinline__ double lane_channels(const McArgs& A, const Query<T>& q, long long rp, int lane,
+                                                T (&c0)[S], T (&c1)[S], int (&jr)[S], PairOut<T> (&po)[S]) {
+  Partner<T> pt[S];
+  load_row_slots<S>(A, rp, lane, jr);
+  load_partners<T, S>(A, jr, pt);
+  return channels_of<T, S>(q, jr, pt, c0, c1, po);
 }
 
 // Relative tolerance of a near tie (a draw this close to a decision boundary is counted):
@@ -297,7 +321,7 @@ __device__ __forceinline__ double waiting_time(uint32_t a, uint32_t b, double la
 
 // ---------------------------------------------------------------- rate kernel
 template <typename T, int S>
-__global__ void __launch_bounds__(256) k_rates(McArgs A) {
+__global__ void __launch_bounds__(128) k_rates(McArgs A) {
   // block-level fine-bin sums of the block's first instance: FP64 form in FP64; mixed form
   // in FP32 (native shared atomics; they only feed the interval controller), then added
   // to the instance's FP64 bins once per block
@@ -347,25 +371,38 @@ __global__ void __launch_bounds__(256) k_rates(McArgs A) {
     const Query<T> myq = live_query<T>(fx, s_i, m_i);     // lane = particle
     const T myj1 = (T)fj1, myj2 = (T)fj2;
     const double mypref = fx.pref;
-    unsigned vmask = __ballot_sync(FULLM, valid);
-    while (vmask) {
-      const int p = __ffs(vmask) - 1;
-      vmask &= vmask - 1;
+    // valid lanes are a prefix of the chunk; the loads are software-pipelined: the
+    // partners of the next particle and the row two ahead are in flight while the
+    // pairs of the current one are evaluated
+    const int nv = __popc(__ballot_sync(FULLM, valid));
+    int jA[S], jB[S];
+    Partner<T> ptA[S];
+    if (nv > 0) { load_row_slots<S>(A, base, lane, jA); load_partners<T, S>(A, jA, ptA); }
+    if (nv > 1) load_row_slots<S>(A, base + 1, lane, jB);
+    for (int p = 0; p < nv; ++p) {
       const long long rp = base + p;
+      int jr[S];
+      Partner<T> pt[S];
+#pragma unroll
+      for (int t = 0; t < S; ++t) { jr[t] = jA[t]; pt[t] = ptA[t]; }
+      if (p + 1 < nv) {
+#pragma unroll
+        for (int t = 0; t < S; ++t) jA[t] = jB[t];
+        load_partners<T, S>(A, jA, ptA);
+      }
+      if (p + 2 < nv) load_row_slots<S>(A, rp + 2, lane, jB);
       const T j1 = __shfl_sync(FULLM, myj1, p), j2 = __shfl_sync(FULLM, myj2, p);
       const Query<T> q = shfl_query<T>(myq, p);
-      const int* row = A.nbr + rp * A.K;
       T c0[S], c1[S];
-      int jr[S];
       PairOut<T> po[S];
       T tot;
       if constexpr (sizeof(T) == 8) {
         // FP64 form: the sampler's own scan, so lambda*_i is the same number there
-        const double v = lane_channels<T, S>(A, q, row, lane, c0, c1, jr, po);
+        const double v = channels_of<T, S>(q, jr, pt, c0, c1, po);
         tot = __shfl_sync(FULLM, warp_incl_scan(v, lane), 31);
       } else {
         // mixed form: rates accumulated in FP32 (only the sampler's prefix sums are FP64)
-        lane_channels<T, S>(A, q, row, lane, c0, c1, jr, po);
+        channels_of<T, S>(q, jr, pt, c0, c1, po);
         float vf = 0.0f;
 #pragma unroll
         for (int t = 0; t < S; ++t) vf += c0[t] + c1[t];
@@ -523,11 +560,16 @@ __global__ void k_interval(const InstDev* __restrict__ P, StateDev* st, BinsDev*
 
 // ---------------------------------------------------------------- sampler
 template <typename T, int S>
-__global__ void __launch_bounds__(256) k_sample(McArgs A) {
+__global__ void __launch_bounds__(64) k_sample(McArgs A) {
   const int lane = threadIdx.x & 31;
-  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long base = warp * 32; base < A.N; base += nwarps * 32) {
+  // chunks of 32 ranks are taken from a counter: event counts are heavy-tailed, so a
+  // static assignment would leave warps idle behind the busiest chunks
+  auto next_chunk = [&]() {
+    unsigned long long c = 0;
+    if (lane == 0) c = atomicAdd(A.work, 1ull);
+    return (long long)__shfl_sync(FULLM, c, 0) * 32;
+  };
+  for (long long base = next_chunk(); base < A.N; base = next_chunk()) {
     const long long r = base + lane;
     const bool valid = r < A.N;
     int b = 0;
@@ -596,7 +638,6 @@ __global__ void __launch_bounds__(256) k_sample(McArgs A) {
       const unsigned iv = __shfl_sync(FULLM, ival, p), il = __shfl_sync(FULLM, i_loc, p);
       const unsigned k0 = __shfl_sync(FULLM, key0, p), k1 = __shfl_sync(FULLM, key1, p);
       const int bp = __shfl_sync(FULLM, b, p);
-      const int* row = A.nbr + rp * A.K;
       const double s_start = s;
       int e = 0, near_ch = 0, near_u = 0;   // per-lane channel ties, warp-uniform ties
       unsigned h = 0u;
@@ -605,7 +646,7 @@ __global__ void __launch_bounds__(256) k_sample(McArgs A) {
       int jr[S];
       PairOut<T> po[S];
       Query<T> q = live_query<T>(f, s, m);
-      double v = lane_channels<T, S>(A, q, row, lane, c0, c1, jr, po);
+      double v = lane_channels<T, S>(A, q, rp, lane, c0, c1, jr, po);
       double incl = warp_incl_scan(v, lane);
       double tot = __shfl_sync(FULLM, incl, 31);
       for (;;) {
@@ -691,7 +732,7 @@ __global__ void __launch_bounds__(256) k_sample(McArgs A) {
         ++e;
         if (e >= A.max_events) { if (lane == 0) set_status(&A.st[bp], GD_ST_EVENT_CAP); break; }
         q = live_query<T>(f, s, m);
-        v = lane_channels<T, S>(A, q, row, lane, c0, c1, jr, po);
+        v = lane_channels<T, S>(A, q, rp, lane, c0, c1, jr, po);
         incl = warp_incl_scan(v, lane);
         tot = __shfl_sync(FULLM, incl, 31);
         const double lam_now = f.pref * tot;
@@ -792,6 +833,7 @@ static McArgs mc_args(gd_ctx* c) {
   A.ev_hash = nullptr;
   A.near_out = nullptr;
   A.max_events = c->max_events;
+  A.work = nullptr;
   A.range = 0;
   return A;
 }
@@ -799,18 +841,18 @@ static McArgs mc_args(gd_ctx* c) {
 template <typename T>
 static void rates_t(gd_ctx* c, McArgs& A) {
   int S = (c->K + 31) / 32;
-  long long blocks_want = (long long)c->num_sms * 4;
+  long long blocks_want = (long long)c->num_sms * 8;
   long long range = (A.N + blocks_want - 1) / blocks_want;
-  range = ((range + 255) / 256) * 256;
-  if (range < 256) range = 256;
+  range = ((range + 127) / 128) * 128;
+  if (range < 128) range = 128;
   A.range = range;
   int blocks = (int)((A.N + range - 1) / range);
   switch (S) {
-    case 1: k_rates<T, 1><<<blocks, 256, 0, c->stream>>>(A); break;
-    case 2: k_rates<T, 2><<<blocks, 256, 0, c->stream>>>(A); break;
-    case 3: k_rates<T, 3><<<blocks, 256, 0, c->stream>>>(A); break;
-    case 4: k_rates<T, 4><<<blocks, 256, 0, c->stream>>>(A); break;
-    default: k_rates<T, 8><<<blocks, 256, 0, c->stream>>>(A); break;
+    case 1: k_rates<T, 1><<<blocks, 128, 0, c->stream>>>(A); break;
+    case 2: k_rates<T, 2><<<blocks, 128, 0, c->stream>>>(A); break;
+    case 3: k_rates<T, 3><<<blocks, 128, 0, c->stream>>>(A); break;
+    case 4: k_rates<T, 4><<<blocks, 128, 0, c->stream>>>(A); break;
+    default: k_rates<T, 8><<<blocks, 128, 0, c->stream>>>(A); break;
   }
 }
 
@@ -834,20 +876,30 @@ cudaError_t launch_interval(gd_ctx* c) {
   return cudaGetLastError();
 }
 
+template <typename T, int S>
+static void sample_launch(gd_ctx* c, const McArgs& A) {
+  // 64-thread blocks: the register budget of this kernel then still fills the SM
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample<T, S>, 64, 0);
+  if (per_sm < 1) per_sm = 1;
+  long long chunks = (A.N + 31) / 32;
+  long long blocks = (long long)c->num_sms * per_sm;
+  if (blocks > (chunks + 1) / 2) blocks = (chunks + 1) / 2;
+  if (blocks < 1) blocks = 1;
+  k_sample<T, S><<<(int)blocks, 64, 0, c->stream>>>(A);
+}
+
 template <typename T>
 static void sample_t(gd_ctx* c, McArgs& A) {
   int S = (c->K + 31) / 32;
-  long long chunks = (A.N + 31) / 32;
-  long long blocks = (chunks + 7) / 8;
-  long long cap = (long long)c->num_sms * 8;
-  if (blocks > cap) blocks = cap;
-  if (blocks < 1) blocks = 1;
+  A.work = c->d_counters;
+  cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long), c->stream);
   switch (S) {
-    case 1: k_sample<T, 1><<<(int)blocks, 256, 0, c->stream>>>(A); break;
-    case 2: k_sample<T, 2><<<(int)blocks, 256, 0, c->stream>>>(A); break;
-    case 3: k_sample<T, 3><<<(int)blocks, 256, 0, c->stream>>>(A); break;
-    case 4: k_sample<T, 4><<<(int)blocks, 256, 0, c->stream>>>(A); break;
-    default: k_sample<T, 8><<<(int)blocks, 256, 0, c->stream>>>(A); break;
+    case 1: sample_launch<T, 1>(c, A); break;
+    case 2: sample_launch<T, 2>(c, A); break;
+    case 3: sample_launch<T, 3>(c, A); break;
+    case 4: sample_launch<T, 4>(c, A); break;
+    default: sample_launch<T, 8>(c, A); break;
   }
 }
 

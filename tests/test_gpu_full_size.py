@@ -1,0 +1,170 @@
+"""GPU parity at the full sizes of the five workload shapes, in the launch configuration
+bench.py times, on sampled outputs the oracle computes one by one.
+
+Sampled particles are checked against the oracle's brute force (lists and distances
+bit-exact, rates within the form's bound) and, for the first interval, their whole event
+sequence is replayed by the oracle with the GPU's interval length (particles are
+independent inside an interval, so this is an exact check of the sampled ones).
+"""
+import numpy as np
+import pytest
+
+from paper_2609_35967_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+RATE_TOL = {0: 1e-12, 1: 1e-4}
+
+
+def _sample(n, k, seed, extra=()):
+    q = np.random.default_rng(seed).choice(n, k, replace=False)
+    return np.unique(np.concatenate([q, np.asarray(extra, dtype=np.int64)]))
+
+
+def _check_subset(oracle, P, ins, q, nbr, d, lam, precision, events=None, interval=0):
+    onbr, od = oracle.knn(P, ins["x"], ins["y"], ins["z"], q)
+    assert np.array_equal(nbr[q], onbr)
+    assert np.array_equal(d[q], od)
+    r = oracle.rates_subset(P, ins["x"], ins["y"], ins["z"], ins["s"], ins["M"], q, onbr, od)
+    rel = np.abs(lam[q] / r["lam"] - 1.0)
+    assert rel.max() < RATE_TOL[precision], rel.max()
+    if events is None:
+        return 0
+    ec, eh, nn, dt_exe = events
+    o = oracle.sample_subset(P, ins["x"], ins["y"], ins["z"], ins["s"], ins["M"], q, onbr, od,
+                             dt_exe, interval)
+    same = (o["ev_count"] == ec[q]) & (o["ev_hash"] == eh[q])
+    flagged = (o["near"] > 0) | (nn[q] > 0)
+    bad = int((~same & ~flagged).sum())
+    if precision == 0:
+        assert bad == 0
+    else:
+        assert bad <= max(1, 2e-3 * len(q)), bad
+    return int(o["ev_count"].sum())
+
+
+def _extremes(ins):
+    R = np.hypot(ins["x"], ins["y"])
+    return [int(np.argmin(R)), int(np.argmax(R)), int(np.argmax(np.abs(ins["z"])))]
+
+
+def test_config1_disk_2p20_fp64(gd, oracle):
+    """Global disk of 2^20 equal 1 um grains, K = 32, plain FP64 form."""
+    ins = W.config1()[0]
+    sess = gd.Session([ins], precision=gd.GD_FP64)
+    nbr, d = sess.build_neighbors(want=True)
+    lam, _ = sess.collision_rates(want=True)
+    ec, eh, nn = sess.sample_collisions(want=True)
+    st = sess.stats()
+    P = oracle.params(ins["params"])
+    q = _sample(len(ins["x"]), 64, 21, _extremes(ins))
+    _check_subset(oracle, P, ins, q, nbr.cpu().numpy(), d.cpu().numpy(), lam.cpu().numpy(), 0,
+                  (ec.cpu().numpy(), eh.cpu().numpy().view(np.uint32), nn.cpu().numpy(),
+                   st["instances"][0]["dt_exe"]))
+    for _ in range(2):
+        sess.build_neighbors()
+        sess.collision_rates()
+        sess.sample_collisions()
+    st = sess.stats(check=False)
+    assert st["status"] == 0 and st["intervals"] == 3
+    sess.close()
+
+
+def test_config2_events_of_sampled_particles(gd, oracle):
+    """The bench workload (2^22, log-normal sizes, mixed form): first-interval events of
+    sampled particles replayed by the oracle."""
+    ins = W.config2()[0]
+    sess = gd.Session([ins], precision=gd.GD_MIXED)
+    sess.autotune()
+    nbr, d = sess.build_neighbors(want=True)
+    lam, _ = sess.collision_rates(want=True)
+    ec, eh, nn = sess.sample_collisions(want=True)
+    st = sess.stats()
+    P = oracle.params(ins["params"])
+    ecn = ec.cpu().numpy()
+    # half of the sample from particles that had events, so the replay is not vacuous
+    busy = np.flatnonzero(ecn > 0)
+    rng = np.random.default_rng(5)
+    q = np.unique(np.concatenate([_sample(len(ins["x"]), 32, 6, _extremes(ins)),
+                                  rng.choice(busy, min(32, len(busy)), replace=False)]))
+    n_ev = _check_subset(oracle, P, ins, q, nbr.cpu().numpy(), d.cpu().numpy(), lam.cpu().numpy(), 1,
+                         (ecn, eh.cpu().numpy().view(np.uint32), nn.cpu().numpy(),
+                          st["instances"][0]["dt_exe"]))
+    assert n_ev > 0
+    sess.close()
+
+
+def test_config3_batched_patches_graph(gd, oracle):
+    """256 independent patches of log-uniform sizes 2^10-2^16 and their own parameters in
+    one context (mixed form, autotuned cells): sampled queries of every patch, whole
+    first-interval events of the three smallest patches, then graph-replayed intervals."""
+    insts = W.config3()
+    offs = W.concat(insts)["offsets"]
+    sess = gd.Session(insts, precision=gd.GD_MIXED)
+    sess.autotune()
+    nbr, d = sess.build_neighbors(want=True)
+    lam, _ = sess.collision_rates(want=True)
+    ec, eh, nn = sess.sample_collisions(want=True)
+    st = sess.stats()
+    nbr, d, lam = nbr.cpu().numpy(), d.cpu().numpy(), lam.cpu().numpy()
+    ec, eh, nn = ec.cpu().numpy(), eh.cpu().numpy().view(np.uint32), nn.cpu().numpy()
+    sizes = np.diff(offs)
+    small = set(np.argsort(sizes)[:3].tolist())
+    rng = np.random.default_rng(33)
+    for b, ins in enumerate(insts):
+        lo, hi = offs[b], offs[b + 1]
+        P = oracle.params(ins["params"])
+        n = hi - lo
+        if b in small:
+            # the whole patch: lists, rates and events of every particle
+            q = np.arange(n)
+            ev = (ec[lo:hi], eh[lo:hi], nn[lo:hi], st["instances"][b]["dt_exe"])
+        else:
+            q = rng.choice(n, 3, replace=False)
+            ev = None
+        _check_subset(oracle, P, ins, q, nbr[lo:hi] - lo, d[lo:hi], lam[lo:hi], 1, ev)
+    M0 = [float(np.sum(i["M"])) for i in insts]
+    sess.run_intervals(3)
+    st = sess.stats(check=False)
+    assert st["status"] == 0 and st["intervals"] == 4
+    for b in range(len(insts)):
+        assert st["instances"][b]["sum_M"] == pytest.approx(M0[b], rel=1e-12)
+    assert np.array_equal(sess.t["M"].cpu().numpy(), W.concat(insts)["M"])
+    sess.close()
+
+
+def test_config4_disk_2p24_k48_push(gd, oracle):
+    """Global disk of 2^24 particles, K = 48, mixed form, staggered push after each
+    interval: sampled lists/rates/events, then the push of sampled particles against the
+    oracle's, then a further interval on the pushed positions."""
+    ins = W.config4()[0]
+    sess = gd.Session([ins], precision=gd.GD_MIXED, velocities=True)
+    nbr, d = sess.build_neighbors(want=True)
+    lam, _ = sess.collision_rates(want=True)
+    ec, eh, nn = sess.sample_collisions(want=True)
+    st = sess.stats()
+    dt = st["instances"][0]["dt_exe"]
+    P = oracle.params(ins["params"])
+    q = _sample(len(ins["x"]), 40, 44, _extremes(ins))
+    _check_subset(oracle, P, ins, q, nbr.cpu().numpy(), d.cpu().numpy(), lam.cpu().numpy(), 1,
+                  (ec.cpu().numpy(), eh.cpu().numpy().view(np.uint32), nn.cpu().numpy(), dt))
+    del nbr, d, lam, ec, eh, nn
+    s_now = sess.t["s"].cpu().numpy()[q]
+    sess.push_staggered(-1.0)
+    sess.stats()
+    arrs = {k: np.ascontiguousarray(ins[k][q]) for k in ("x", "y", "z", "vr", "lth", "lph")}
+    oracle.push(P, arrs["x"], arrs["y"], arrs["z"], arrs["vr"], arrs["lth"], arrs["lph"], s_now, dt,
+                drag=True)
+    for k in ("x", "y", "z", "lph"):
+        got = sess.t[k].cpu().numpy()[q]
+        assert np.abs(got - arrs[k]).max() <= 1e-12 * np.abs(arrs[k]).max(), k
+    for k in ("vr", "lth"):
+        got = sess.t[k].cpu().numpy()[q]
+        assert np.abs(got - arrs[k]).max() <= 1e-10 * np.abs(arrs[k]).max(), k
+    sess.build_neighbors()
+    sess.collision_rates()
+    sess.sample_collisions()
+    sess.push_staggered(-1.0)
+    st = sess.stats(check=False)
+    assert st["status"] == 0 and st["intervals"] == 2
+    sess.close()
