@@ -65,7 +65,7 @@ static void free_all(gd_ctx* c) {
   void* ptrs[] = {c->d_off, c->d_tile_off, c->d_inst, c->d_grid, c->d_state, c->d_bins, c->d_cell_count,
                   c->d_cell_start, c->d_scan_tmp, c->d_cell_of, c->d_slot, c->d_perm, c->d_rank_of,
                   c->d_pos64, c->d_pos32, c->d_snap64, c->d_snap32, c->d_Mr, c->d_dist, c->d_V,
-                  c->d_lam, c->d_nbr, c->d_counters, c->d_sums};
+                  c->d_lam, c->d_nbr, c->d_counters, c->d_sums, c->d_dprev, c->d_redo};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& e : c->ev_pool) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
@@ -148,6 +148,8 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
   if (c->precision == GD_MIXED) ok &= dalloc(&c->d_snap32, N) == cudaSuccess;
   ok &= dalloc(&c->d_Mr, N) == cudaSuccess;
   ok &= dalloc(&c->d_dist, N) == cudaSuccess;
+  ok &= dalloc(&c->d_dprev, N) == cudaSuccess;
+  ok &= dalloc(&c->d_redo, N) == cudaSuccess;
   ok &= dalloc(&c->d_V, N) == cudaSuccess;
   ok &= dalloc(&c->d_lam, N) == cudaSuccess;
   ok &= dalloc(&c->d_nbr, (size_t)N * c->K) == cudaSuccess;
@@ -198,6 +200,8 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_state, st.data(), sizeof(StateDev) * n, cudaMemcpyHostToDevice, str);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_bins, 0, sizeof(BinsDev) * n, str);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * 16, str);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_dprev, 0, sizeof(double) * N, str);
+  if (e == cudaSuccess) e = knn_prepare(c);
   if (e == cudaSuccess) e = cudaStreamSynchronize(str);
   if (e != cudaSuccess) {
     free_all(c);

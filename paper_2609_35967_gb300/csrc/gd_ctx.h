@@ -47,6 +47,8 @@ struct gd_ctx {
   float4* d_snap32 = nullptr;           // [N]
   double* d_Mr = nullptr;               // [N] M in rank order
   double* d_dist = nullptr;             // [N] d_i, rank order
+  double* d_dprev = nullptr;            // [N] d_i of the last build, caller order (0: none)
+  int* d_redo = nullptr;                // [N] mixed K-NN: queries the FP64 form redoes
   double* d_V = nullptr;                // [N] V_i, rank order
   double* d_lam = nullptr;              // [N] lambda*_i, rank order
   int* d_nbr = nullptr;                 // [N*K] ranks
@@ -76,6 +78,7 @@ namespace gd {
 // launchers (each returns cudaGetLastError() of its launches)
 cudaError_t launch_cells(gd_ctx* c);
 cudaError_t launch_knn(gd_ctx* c);
+cudaError_t knn_prepare(gd_ctx* c);
 cudaError_t launch_rates(gd_ctx* c, double* chan_out);
 cudaError_t launch_interval(gd_ctx* c);
 cudaError_t launch_sample(gd_ctx* c, int* ev_count, unsigned* ev_hash, int* near);

@@ -1,24 +1,27 @@
 // k_knn.cu -- K nearest neighbours over the device cell list (Sect. 2.5.1).
 //
-// A warp owns a chunk of 32 consecutive query ranks (neighbouring cells) and works in
-// three phases:
-//  A  per query, warp-cooperative: scan every cell row that meets a ball of radius rho
-//     around the query (rows are contiguous rank ranges, so loads are coalesced), keep a
-//     register top list over the lanes (slot g in lane g % 32, register g / 32) ordered by
-//     (key, index), and accept rho once the ball provably holds the K-1 nearest others.
-//     All search bookkeeping (cell ranges, slab distances, radii) is FP32/INT in the
-//     query's cell-relative frame with conservative margins.
-//       FP64 form : key = bits of d^2 = (dx dx + dy dy) + dz dz in FP64 (no FMA, minimum
-//                   image), ties by caller index: the oracle's order exactly.
-//       mixed form: key = FP32 d^2 from cell-relative FP32 coordinates; with
-//                   |sqrt(D32) - d| <= 10u sqrt(D32) + E (u = 2^-24) keys below T_lo are
-//                   certain members and keys up to T_hi form a band that phase B ranks
-//                   exactly in FP64.  A band that overflows the list or the band buffer,
-//                   or a periodic axis covered whole, sends the query to the FP64 form.
-//  B  lane = query: the FP64 arithmetic (band re-rank, d_i = sqrt(d^2), V_i with the
-//     flat-boundary caps), so FP64 instructions carry 32 queries each.
-//  C  per query: members sorted by caller index (bitonic over the lanes), written as
-//     ranks after the particle itself.
+// Lane = query.  Consecutive threads take consecutive query ranks (neighbouring cells),
+// and every thread runs the whole search of its own particle.  The only shared resource
+// is the warp's slice of shared memory, where lane l keeps its candidates: word w of
+// entry e at [(w * CAP + e) * 33 + l], so lanes touching the same entry, or one lane
+// walking its entries, never share a bank.
+//
+//  radius : 1.02 x the particle's d_i of the previous build when there is one, else an
+//           estimate from the particle count of the 27 cells around it;
+//  scan   : the cell rows that meet the ball are produced row by row and consumed
+//           candidate by candidate in one loop (the cell starts of the next row are
+//           loaded while the current row is scanned); keys inside the ball are kept;
+//  radius : grows or shrinks (bisection between radii known to hold too few / too many
+//           candidates) until the ball holds between K-1 and CAP other particles;
+//  keys   : FP64 form -- d^2 = (dx dx + dy dy) + dz dz in FP64 (no FMA, minimum image),
+//           ties by caller index: the oracle's order exactly.
+//           Mixed form -- FP32 D from cell-relative FP32 coordinates, ties by rank; with
+//           |sqrt(D) - d| <= 10u sqrt(D) + E (u = 2^-24) keys below T_lo are certain
+//           members and keys up to T_hi form a band ranked exactly in FP64.  A band wider
+//           than kBand, a periodic axis covered whole, or no acceptable radius puts the
+//           query on a list that the FP64 form then redoes.
+//  output : d_i = sqrt of the (K-1)-th d^2, V_i with the flat-boundary caps, and the row:
+//           the particle itself, then its members by ascending caller index.
 #include <climits>
 
 #include "gd_ctx.h"
@@ -26,8 +29,8 @@
 
 namespace gd {
 
-constexpr unsigned FULL = 0xffffffffu;
-constexpr int kBand = 8;          // band entries resolved in phase B per query
+constexpr int kBand = 8;          // band entries resolved in FP64 per mixed query
+constexpr int kPad = 33;          // words per entry row of a warp's buffer (32 lanes + 1)
 
 struct KnnArgs {
   long long N;
@@ -39,59 +42,17 @@ struct KnnArgs {
   const Pos64* pos64;
   const float4* pos32;
   const int* perm;
+  const int* rank_of;
   int* nbr;
   double* dist;
   double* V;
+  double* dprev;                  // caller order: d_i of the last build (0: unknown)
   StateDev* st;
+  int* redo;                      // mixed form: queries the FP64 form redoes
+  unsigned long long* redo_n;
+  const int* list;                // FP64 redo pass: the queries to process
+  const unsigned long long* list_n;
 };
-
-template <typename KT> __device__ __forceinline__ KT kmax_();
-template <> __device__ __forceinline__ unsigned long long kmax_<unsigned long long>() { return ~0ull; }
-template <> __device__ __forceinline__ unsigned kmax_<unsigned>() { return ~0u; }
-
-template <typename KT>
-__device__ __forceinline__ bool kless(KT ka, int ja, KT kb, int jb) {
-  return ka < kb || (ka == kb && ja < jb);
-}
-
-// Bitonic sort of 32*KPL (j, r) pairs by j, element e = t*32 + lane.
-template <int KPL>
-__device__ __forceinline__ void sort_by_index(int (&jj)[KPL], int (&rr)[KPL], int lane) {
-  constexpr int S = 32 * KPL;
-#pragma unroll
-  for (int k = 2; k <= S; k <<= 1) {
-#pragma unroll
-    for (int s = k >> 1; s > 0; s >>= 1) {
-      if (s >= 32) {
-        const int rs = s >> 5;
-#pragma unroll
-        for (int t = 0; t < KPL; ++t) {
-          const int tp = t ^ rs;
-          if (tp > t) {
-            int e = t * 32 + lane;
-            bool up = (e & k) == 0;
-            bool sw = up ? (jj[t] > jj[tp]) : (jj[t] < jj[tp]);
-            if (sw) {
-              int a = jj[t]; jj[t] = jj[tp]; jj[tp] = a;
-              a = rr[t]; rr[t] = rr[tp]; rr[tp] = a;
-            }
-          }
-        }
-      } else {
-#pragma unroll
-        for (int t = 0; t < KPL; ++t) {
-          int e = t * 32 + lane;
-          int pj = __shfl_xor_sync(FULL, jj[t], s);
-          int pr = __shfl_xor_sync(FULL, rr[t], s);
-          bool up = (e & k) == 0;
-          bool lower = (lane & s) == 0;
-          bool take = (lower == up) ? (pj < jj[t]) : (pj > jj[t]);
-          if (take) { jj[t] = pj; rr[t] = pr; }
-        }
-      }
-    }
-  }
-}
 
 // ---------------------------------------------------------------- geometry (FP32 / INT)
 struct QueryPos {
@@ -142,93 +103,87 @@ __device__ __forceinline__ int floordiv(int a, int d) {
   return (a % d != 0 && ((a < 0) != (d < 0))) ? q - 1 : q;
 }
 
-// Candidate ranks of every cell row within rs of the query, in 32-wide batches flattened
-// across rows.  Rows are set up one per lane (their cell_start loads are in flight
-// together), a warp scan lays the rows' rank ranges end to end, and each lane of a batch
-// finds its row by a binary search over the lanes.  visit(valid, r, x_shift_cells,
-// dy_cells, dz_cells) sees every candidate once.  Returns true when a periodic axis was
-// covered whole (the FP32 cell offsets are then ambiguous).
-template <class F>
-__device__ __forceinline__ bool scan_ball(const Grid32& G, const int* __restrict__ cstart, const QueryPos& Q,
-                                          float rs, int lane, F&& visit) {
-  bool amb = false;
+// One row segment: cells [ca, cb) of the concatenated cell arrays, the x shift of a
+// periodic wrap (cells) and the row's y and z offsets from the query cell.
+struct Seg {
+  long long ca, cb;
+  int xsh, dyc, dzc;
+};
+
+// Rows (z outer, y inner) of the ball of radius rs around the query, one segment per
+// call (a row wrapped across a periodic x edge gives two).
+struct RowIter {
   int lz, hz, ly, hy;
-  bool fz, fy;
-  axis_range32(G, 2, Q.iz, Q.fz, rs, lz, hz, fz);
-  axis_range32(G, 1, Q.iy, Q.fy, rs, ly, hy, fy);
-  if (fy && G.per) amb = true;
-  const float rs2 = rs * rs * 1.00002f;
+  int iz, iyu;
+  bool fy, pending;
+  float rs2;
+  Seg pend;
+};
+
+__device__ __forceinline__ void rows_begin(const Grid32& G, const QueryPos& Q, float rs, RowIter& it, bool& amb) {
+  bool fz;
+  axis_range32(G, 2, Q.iz, Q.fz, rs, it.lz, it.hz, fz);
+  axis_range32(G, 1, Q.iy, Q.fy, rs, it.ly, it.hy, it.fy);
+  if (it.fy && G.per) amb = true;
+  it.iz = it.lz;
+  it.iyu = it.ly;
+  it.pending = false;
+  it.rs2 = rs * rs * 1.00002f;
+  if (it.hy < it.ly) it.iz = it.hz + 1;   // empty
+}
+
+__device__ __forceinline__ bool rows_next(const Grid32& G, const QueryPos& Q, RowIter& it, Seg& s, bool& amb) {
+  if (it.pending) {
+    it.pending = false;
+    s = it.pend;
+    if (++it.iyu > it.hy) { it.iyu = it.ly; ++it.iz; }
+    return true;
+  }
   const int dimx = G.dim[0], dimy = G.dim[1];
-  const int ny = hy - ly + 1, nz = hz - lz + 1;
-  const int nrows = (ny > 0 && nz > 0) ? ny * nz : 0;
-  for (int r0 = 0; r0 < nrows; r0 += 32) {
-    const int row = r0 + lane;
-    int ra0 = 0, c0 = 0, ra1 = 0, c1 = 0, sh0 = 0, sh1 = 0, dyc = 0, dzc = 0;
-    bool rowamb = false;
-    if (row < nrows) {
-      const int iz = lz + row / ny, iyu = ly + row % ny;
-      const float dz = slab_dist32(G, 2, Q.iz, Q.fz, iz);
-      const float dy = fy ? 0.0f : slab_dist32(G, 1, Q.iy, Q.fy, iyu);
-      const float dyz2 = dy * dy + dz * dz;
-      if (dyz2 <= rs2) {
+  while (it.iz <= it.hz) {
+    const int iz = it.iz, iyu = it.iyu;
+    bool got = false;
+    const float dz = slab_dist32(G, 2, Q.iz, Q.fz, iz);
+    const float dy = it.fy ? 0.0f : slab_dist32(G, 1, Q.iy, Q.fy, iyu);
+    const float dyz2 = dy * dy + dz * dz;
+    if (dyz2 <= it.rs2) {
+      const float xr = sqrtf(fmaxf(it.rs2 - dyz2, 0.0f));
+      int lx, hx;
+      bool fx;
+      axis_range32(G, 0, Q.ix, Q.fx, xr, lx, hx, fx);
+      if (lx <= hx) {
+        if (fx && G.per) amb = true;
         int iy = iyu;
         if (G.per) { iy %= dimy; if (iy < 0) iy += dimy; }
-        const float xr = sqrtf(fmaxf(rs2 - dyz2, 0.0f));
-        int lx, hx;
-        bool fx;
-        axis_range32(G, 0, Q.ix, Q.fx, xr, lx, hx, fx);
-        if (lx <= hx) {
-          if (fx && G.per) rowamb = true;
-          const long long rowc = G.cell_off + (long long)dimx * (iy + (long long)dimy * iz);
-          int kx = 0, a0 = lx, e0 = hx;
-          if (G.per && !fx) {
-            kx = floordiv(lx, dimx);
-            a0 = lx - kx * dimx;
-            e0 = hx - kx * dimx;
-          }
-          const int e1 = e0 < dimx ? e0 : dimx - 1;
-          ra0 = __ldg(&cstart[rowc + a0]);
-          c0 = __ldg(&cstart[rowc + e1 + 1]) - ra0;
-          sh0 = kx * dimx;
-          if (e0 >= dimx) {
-            ra1 = __ldg(&cstart[rowc]);
-            c1 = __ldg(&cstart[rowc + (e0 - dimx) + 1]) - ra1;
-            sh1 = (kx + 1) * dimx;
-          }
-          dyc = iyu - Q.iy;
-          dzc = iz - Q.iz;
+        const long long rowc = G.cell_off + (long long)dimx * (iy + (long long)dimy * iz);
+        int kx = 0, a0 = lx, e0 = hx;
+        if (G.per && !fx) {
+          kx = floordiv(lx, dimx);
+          a0 = lx - kx * dimx;
+          e0 = hx - kx * dimx;
         }
+        const int e1 = e0 < dimx ? e0 : dimx - 1;
+        s.ca = rowc + a0;
+        s.cb = rowc + e1 + 1;
+        s.xsh = kx * dimx;
+        s.dyc = iyu - Q.iy;
+        s.dzc = iz - Q.iz;
+        if (e0 >= dimx) {
+          it.pending = true;
+          it.pend.ca = rowc;
+          it.pend.cb = rowc + (e0 - dimx) + 1;
+          it.pend.xsh = (kx + 1) * dimx;
+          it.pend.dyc = s.dyc;
+          it.pend.dzc = s.dzc;
+          return true;             // the row advances after its second segment
+        }
+        got = true;
       }
     }
-    if (__any_sync(FULL, rowamb)) amb = true;
-    const int cnt = c0 + c1;
-    int inc = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(FULL, inc, o);
-      if (lane >= o) inc += t;
-    }
-    const int excl = inc - cnt;
-    const int total = __shfl_sync(FULL, inc, 31);
-    for (int f0 = 0; f0 < total; f0 += 32) {
-      const int f = f0 + lane;
-      int o = 0;
-#pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const int c = o + step;
-        const int ex = __shfl_sync(FULL, excl, c & 31);
-        if (c < 32 && ex <= f) o = c;
-      }
-      const int oex = __shfl_sync(FULL, excl, o), oc0 = __shfl_sync(FULL, c0, o);
-      const int ora0 = __shfl_sync(FULL, ra0, o), ora1 = __shfl_sync(FULL, ra1, o);
-      const int osh0 = __shfl_sync(FULL, sh0, o), osh1 = __shfl_sync(FULL, sh1, o);
-      const int ody = __shfl_sync(FULL, dyc, o), odz = __shfl_sync(FULL, dzc, o);
-      const int loc = f - oex;
-      const bool first = loc < oc0;
-      visit(f < total, first ? ora0 + loc : ora1 + (loc - oc0), first ? osh0 : osh1, ody, odz);
-    }
+    if (++it.iyu > it.hy) { it.iyu = it.ly; ++it.iz; }
+    if (got) return true;
   }
-  return amb;
+  return false;
 }
 
 __device__ __forceinline__ double sample_volume(const InstDev& P, double d, double x, double y) {
@@ -244,13 +199,12 @@ __device__ __forceinline__ double sample_volume(const InstDev& P, double d, doub
   return V;
 }
 
-// Radius estimate from the particle count of the 27 cells around the query (lane c < 27
-// loads cell c, so the loads are in flight together).
+// Radius estimate from the particle count of the 27 cells around the query.
 __device__ __forceinline__ float rho_start(const Grid32& G, const int* __restrict__ cstart, const QueryPos& Q,
-                                           int L, int lane) {
+                                           int L) {
   int n = 0, nc = 0;
-  if (lane < 27) {
-    const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+  for (int c = 0; c < 27; ++c) {
+    const int dx = c % 3 - 1, dy = (c / 3) % 3 - 1, dz = c / 9 - 1;
     int ix = Q.ix + dx, iy = Q.iy + dy;
     const int iz = Q.iz + dz;
     bool ok = iz >= 0 && iz < G.dim[2];
@@ -261,15 +215,10 @@ __device__ __forceinline__ float rho_start(const Grid32& G, const int* __restric
       ok = ok && ix >= 0 && ix < G.dim[0] && iy >= 0 && iy < G.dim[1];
     }
     if (ok) {
-      const long long c = G.cell_off + ix + (long long)G.dim[0] * (iy + (long long)G.dim[1] * iz);
-      n = __ldg(&cstart[c + 1]) - __ldg(&cstart[c]);
-      nc = 1;
+      const long long cc = G.cell_off + ix + (long long)G.dim[0] * (iy + (long long)G.dim[1] * iz);
+      n += __ldg(&cstart[cc + 1]) - __ldg(&cstart[cc]);
+      nc += 1;
     }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    n += __shfl_xor_sync(FULL, n, o);
-    nc += __shfl_xor_sync(FULL, nc, o);
   }
   const float csmax = fmaxf(G.cs[0], fmaxf(G.cs[1], G.cs[2]));
   if (n <= 1) return 2.0f * csmax;
@@ -299,195 +248,140 @@ __device__ __forceinline__ double d2_fp64(const Pos64* __restrict__ pos64, int r
   return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
 
-// Phase-A result of one query, kept in shared memory for phases B and C.
-struct QInfo {
-  int state;          // 0 done (row, d, V written), 1 FP64 members written, 2 mixed band pending
-  int p_lo;           // certain members written to the row
-  int nb;             // band entries
-  int need;           // band entries to select
-  unsigned long long d2max;   // FP64 form: bits of the (K-1)-th d^2
-  int band[kBand];
-};
-
-// Candidates inside the search ball of one query, in shared memory (per warp).
-template <int KB>
-struct CandBuf {
-  unsigned long long key[32 * KB];   // FP64 form: bits of d^2; mixed: (bits of the FP32 D) << 32 | rank
-  int j[32 * KB];                    // FP64 form: tie index (caller index)
-  int r[32 * KB];                    // FP64 form: rank
-};
-
-// Compare-exchange of register pairs (t, t ^ RS) inside each lane, block direction from
-// the element index e = t*32 + lane.
-template <int RS, int KB>
-__device__ __forceinline__ void cas_regs(int nreg, int kk, unsigned long long (&k)[KB], int (&j)[KB],
-                                         int (&r)[KB], int lane) {
-#pragma unroll
-  for (int t = 0; t < KB; ++t) {
-    const int tp = t ^ RS;
-    if (tp > t && tp < KB && t < nreg && tp < nreg) {
-      const bool up = ((t * 32 + lane) & kk) == 0;
-      const bool gt = kless(k[tp], j[tp], k[t], j[t]);
-      if (up == gt) {
-        unsigned long long a = k[t]; k[t] = k[tp]; k[tp] = a;
-        int c = j[t]; j[t] = j[tp]; j[tp] = c;
-        c = r[t]; r[t] = r[tp]; r[tp] = c;
-      }
-    }
+// ---------------------------------------------------------------- the lane's buffer
+// kMixed: word 0 = bits of the FP32 D, word 1 = rank.  FP64: words 0/1 = low/high bits of
+// d^2, word 2 = caller index.  Entries compare as (key, tie) with unsigned integers
+// (non-negative floats order like their bit patterns).
+template <int CAP, bool kMixed>
+struct LaneBuf {
+  static constexpr int NW = kMixed ? 2 : 3;
+  uint32_t* b;
+  __device__ __forceinline__ uint32_t& w(int word, int e) const { return b[(word * CAP + e) * kPad]; }
+  __device__ __forceinline__ unsigned long long key(int e) const {
+    if (kMixed) return ((unsigned long long)w(0, e) << 32) | w(1, e);
+    return ((unsigned long long)w(1, e) << 32) | w(0, e);
   }
-}
-
-// Bitonic sort, ascending by (key, j), of the first 32*nreg register entries (nreg a power
-// of two <= KB).  The stage loops run at run time and only the per-register bodies are
-// unrolled, which keeps the code small (the search is otherwise instruction-cache bound).
-template <int KB>
-__device__ __forceinline__ void sort_cand(int nreg, unsigned long long (&k)[KB], int (&j)[KB], int (&r)[KB],
-                                          int lane) {
-  const int S = 32 * nreg;
-#pragma unroll 1
-  for (int kk = 2; kk <= S; kk <<= 1) {
-#pragma unroll 1
-    for (int s = kk >> 1; s > 0; s >>= 1) {
-      if (s >= 32) {
-        const int rs = s >> 5;
-        if (rs == 1) cas_regs<1, KB>(nreg, kk, k, j, r, lane);
-        else if (rs == 2) cas_regs<2, KB>(nreg, kk, k, j, r, lane);
-        else if (rs == 4) cas_regs<4, KB>(nreg, kk, k, j, r, lane);
-        else if (rs == 8) cas_regs<8, KB>(nreg, kk, k, j, r, lane);
-        else cas_regs<16, KB>(nreg, kk, k, j, r, lane);
-      } else {
-        const bool lower = (lane & s) == 0;
+  __device__ __forceinline__ bool greater(int a, int b2) const {   // entry a > entry b2
+    const unsigned long long ka = key(a), kb = key(b2);
+    if (kMixed) return ka > kb;
+    return ka > kb || (ka == kb && w(2, a) > w(2, b2));
+  }
+  __device__ __forceinline__ void swap(int a, int b2) const {
 #pragma unroll
-        for (int t = 0; t < KB; ++t) {
-          if (t < nreg) {
-            const unsigned long long pk = __shfl_xor_sync(FULL, k[t], s);
-            const int pj = __shfl_xor_sync(FULL, j[t], s);
-            const int pr = __shfl_xor_sync(FULL, r[t], s);
-            const bool up = ((t * 32 + lane) & kk) == 0;
-            const bool pless = kless(pk, pj, k[t], j[t]);
-            const bool pgreater = kless(k[t], j[t], pk, pj);
-            if ((lower == up) ? pless : pgreater) { k[t] = pk; j[t] = pj; r[t] = pr; }
+    for (int k = 0; k < NW; ++k) { const uint32_t t = w(k, a); w(k, a) = w(k, b2); w(k, b2) = t; }
+  }
+  // Leaves the L smallest of entries [0, n) in [0, L) (any order) by moving the largest
+  // remaining entry to the tail n - L times (the radius keeps n - L small); returns the
+  // index of the largest of them, the L-th smallest.
+  __device__ __forceinline__ int select(int n, int L) const {
+    for (int m = n; m > L; --m) {
+      int im = 0;
+      for (int e = 1; e < m; ++e)
+        if (greater(e, im)) im = e;
+      if (im != m - 1) swap(im, m - 1);
+    }
+    int im = 0;
+    for (int e = 1; e < L; ++e)
+      if (greater(e, im)) im = e;
+    return im;
+  }
+};
+
+// Candidates of the ball of radius rho; keys inside it go to the buffer (the first CAP of
+// them).  Returns how many were inside.
+template <int CAP, bool kMixed>
+__device__ __forceinline__ int scan_ball(const KnnArgs& A, const Grid32& G, const GridDev& Gd, const QueryPos& Q,
+                                         long long q, float rho, const LaneBuf<CAP, kMixed>& buf, bool& amb) {
+  const float rel = 10.0f * 5.9604645e-8f;
+  const float E = Gd.E32;
+  const float rf = (rho * (1.0f + 2.0f * rel) + 2.0f * E) * 1.000001f;
+  const float rhof2 = rf * rf * 1.000001f;
+  const double rho2 = (double)rho * (double)rho;
+  const double bx = Gd.box[0], by = Gd.box[1];
+  const int* __restrict__ cstart = A.cstart;
+  RowIter it;
+  rows_begin(G, Q, rho, it, amb);
+  // rows in order; the cell starts of the next row are loaded before the current row is
+  // scanned.  Neighbouring queries mostly share their rows, so the lanes of a warp walk
+  // the same candidates together.
+  Seg cur, nxt;
+  cur.xsh = cur.dyc = cur.dzc = 0;
+  bool has_cur = rows_next(G, Q, it, cur, amb);
+  int ca = 0, cb = 0;
+  if (has_cur) { ca = __ldg(cstart + cur.ca); cb = __ldg(cstart + cur.cb); }
+  int n_in = 0;
+  while (has_cur) {
+    nxt.xsh = nxt.dyc = nxt.dzc = 0;
+    const bool has_nxt = rows_next(G, Q, it, nxt, amb);
+    int na = 0, nb = 0;
+    if (has_nxt) { na = __ldg(cstart + nxt.ca); nb = __ldg(cstart + nxt.cb); }
+    const float dycf = (float)cur.dyc * G.cs[1], dzcf = (float)cur.dzc * G.cs[2];
+    const int xoff = cur.xsh - Q.ix;
+    if (kMixed) {
+      // four candidates per step, their loads issued together
+      for (int r0 = ca; r0 < cb; r0 += 4) {
+        float4 p[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) p[u] = r0 + u < cb ? __ldg(A.pos32 + r0 + u) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int r = r0 + u;
+          if (r >= cb || r == (int)q) continue;
+          const int ixj = __float_as_int(p[u].w) & 2047;
+          const float dx = (p[u].x - Q.fx) + (float)(ixj + xoff) * G.cs[0];
+          const float dy = (p[u].y - Q.fy) + dycf;
+          const float dz = (p[u].z - Q.fz) + dzcf;
+          const float D = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+          if (D <= rhof2) {
+            if (n_in < CAP) { buf.w(0, n_in) = __float_as_uint(D); buf.w(1, n_in) = (uint32_t)r; }
+            ++n_in;
           }
         }
       }
-    }
-  }
-}
-
-template <int KB>
-__device__ __forceinline__ void sort_any(int n, unsigned long long (&k)[KB], int (&j)[KB], int (&r)[KB], int lane) {
-  int nreg = 1;
-  while (32 * nreg < n && nreg < KB) nreg <<= 1;
-  sort_cand<KB>(nreg, k, j, r, lane);
-}
-
-// Mixed form: the same bitonic network on packed keys (FP32 D bits << 32 | rank), which
-// are distinct, so one 64-bit comparison orders them by (D, rank).
-template <int RS, int KB>
-__device__ __forceinline__ void cas_packed(int nreg, int kk, unsigned long long (&k)[KB], int lane) {
-#pragma unroll
-  for (int t = 0; t < KB; ++t) {
-    const int tp = t ^ RS;
-    if (tp > t && tp < KB && t < nreg && tp < nreg) {
-      const bool up = ((t * 32 + lane) & kk) == 0;
-      if (up == (k[tp] < k[t])) { unsigned long long a = k[t]; k[t] = k[tp]; k[tp] = a; }
-    }
-  }
-}
-
-template <int KB>
-__device__ __forceinline__ void sort_packed(int n, unsigned long long (&k)[KB], int lane) {
-  int nreg = 1;
-  while (32 * nreg < n && nreg < KB) nreg <<= 1;
-  const int S = 32 * nreg;
-#pragma unroll 1
-  for (int kk = 2; kk <= S; kk <<= 1) {
-#pragma unroll 1
-    for (int s = kk >> 1; s > 0; s >>= 1) {
-      if (s >= 32) {
-        const int rs = s >> 5;
-        if (rs == 1) cas_packed<1, KB>(nreg, kk, k, lane);
-        else if (rs == 2) cas_packed<2, KB>(nreg, kk, k, lane);
-        else if (rs == 4) cas_packed<4, KB>(nreg, kk, k, lane);
-        else if (rs == 8) cas_packed<8, KB>(nreg, kk, k, lane);
-        else cas_packed<16, KB>(nreg, kk, k, lane);
-      } else {
-        const bool lower = (lane & s) == 0;
-#pragma unroll
-        for (int t = 0; t < KB; ++t) {
-          if (t < nreg) {
-            const unsigned long long pk = __shfl_xor_sync(FULL, k[t], s);
-            const bool up = ((t * 32 + lane) & kk) == 0;
-            // keep the smaller of the pair in the lower lane of an ascending block
-            if ((lower == up) == (pk < k[t])) k[t] = pk;
+    } else {
+    for (int r = ca; r < cb; ++r) {
+      if (r == (int)q) continue;
+      {
+        long long jj;
+        const double d2 = d2_fp64(A.pos64, r, Q.x, Q.y, Q.z, bx, by, jj);
+        if (d2 <= rho2) {
+          if (n_in < CAP) {
+            const unsigned long long kb = (unsigned long long)__double_as_longlong(d2);
+            buf.w(0, n_in) = (uint32_t)kb;
+            buf.w(1, n_in) = (uint32_t)(kb >> 32);
+            if (LaneBuf<CAP, kMixed>::NW > 2) buf.w(2, n_in) = (uint32_t)jj;
           }
+          ++n_in;
         }
       }
     }
+    }
+    cur = nxt;
+    ca = na;
+    cb = nb;
+    has_cur = has_nxt;
   }
+  return n_in;
 }
 
-template <typename KT, int KB>
-__device__ __forceinline__ void get_entry(const unsigned long long (&k)[KB], int g, unsigned long long& out) {
-  unsigned long long v = k[0];
-#pragma unroll
-  for (int t = 1; t < KB; ++t)
-    if (t == (g >> 5)) v = k[t];
-  out = __shfl_sync(FULL, v, g & 31);
-}
-
-// Search of one query.  Candidates inside rho go to the warp's buffer, are sorted, and
-// the K-1 nearest taken; FP64 form: exact keys, the members and the (K-1)-th d^2 are
-// final; mixed form: certain members and the FP64 band are left to phase B.  Returns
-// false when the query must be redone (mixed: in the FP64 form; FP64: failed).
-template <int KB, bool kMixed>
-__device__ __forceinline__ bool query_buf(const KnnArgs& A, const Grid32& G, const GridDev& Gd, const QueryPos& Q, long long q,
-                          int lane, float& rho, QInfo& qi, CandBuf<KB>& buf, float& dk) {
-  constexpr int CAP = 32 * KB;
+// Search of one query.  On success the buffer holds the members: entries [0, L) with
+// word 0 = caller index and word 1 = rank (unsorted), and d2max is the (K-1)-th d^2.
+// Returns false when no acceptable radius was found (mixed: also when the FP32 keys
+// cannot decide the members).
+template <int CAP, bool kMixed>
+__device__ bool lane_query(const KnnArgs& A, const Grid32& G, const GridDev& Gd, const QueryPos& Q, long long q,
+                           float rho, const LaneBuf<CAP, kMixed>& buf, double& d2max) {
   const int L = A.K - 1;
   const float E = Gd.E32;
   const float rel = 10.0f * 5.9604645e-8f;
   const double bx = Gd.box[0], by = Gd.box[1];
-  const float csx = G.cs[0], csy = G.cs[1], csz = G.cs[2];
   const float diag = sqrtf((float)G.dim[0] * G.dim[0] * G.cs[0] * G.cs[0] +
                            (float)G.dim[1] * G.dim[1] * G.cs[1] * G.cs[1] +
                            (float)G.dim[2] * G.dim[2] * G.cs[2] * G.cs[2]);
   float r_lo = 0.0f, r_hi = 0.0f;    // radii known to hold too few / too many candidates
   for (int att = 0; att < 64; ++att) {
-    int n_in = 0;
-    const double rho2 = (double)rho * (double)rho;
-    const float rf = (rho * (1.0f + 2.0f * rel) + 2.0f * E) * 1.000001f;
-    const float rhof2 = rf * rf * 1.000001f;
-    const bool amb = scan_ball(G, A.cstart, Q, rho, lane, [&](bool valid, int r, int xsh, int dyc, int dzc) {
-      bool in = false;
-      unsigned long long key = 0;
-      int tj = 0;
-      if (valid && r != (int)q) {
-        if (kMixed) {
-          const float4 p = __ldg(A.pos32 + r);
-          const int ixj = __float_as_int(p.w) & 2047;
-          const float dx = (p.x - Q.fx) + (float)(ixj + xsh - Q.ix) * csx;
-          const float dy = (p.y - Q.fy) + (float)dyc * csy;
-          const float dz = (p.z - Q.fz) + (float)dzc * csz;
-          const float D = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-          in = D <= rhof2;
-          key = ((unsigned long long)__float_as_uint(D) << 32) | (unsigned)r;
-        } else {
-          long long jj;
-          const double d2 = d2_fp64(A.pos64, r, Q.x, Q.y, Q.z, bx, by, jj);
-          in = d2 <= rho2;
-          key = (unsigned long long)__double_as_longlong(d2);
-          tj = (int)jj;
-        }
-      }
-      const unsigned m = __ballot_sync(FULL, in);
-      const int pos = n_in + __popc(m & ((1u << lane) - 1u));
-      if (in && pos < CAP) {
-        buf.key[pos] = key;
-        if (!kMixed) { buf.j[pos] = tj; buf.r[pos] = r; }
-      }
-      n_in += __popc(m);
-    });
+    bool amb = false;
+    const int n_in = scan_ball<CAP, kMixed>(A, G, Gd, Q, q, rho, buf, amb);
     if (kMixed && amb) return false;
     if (n_in < L) {
       if (rho > 2.0f * diag) return false;
@@ -497,46 +391,22 @@ __device__ __forceinline__ bool query_buf(const KnnArgs& A, const Grid32& G, con
     }
     if (n_in > CAP) {
       r_hi = rho;
-      rho = r_lo > 0.0f ? sqrtf(r_lo * r_hi) : rho * fmaxf(cbrtf(0.7f * (float)CAP / (float)n_in), 0.3f);
+      rho = r_lo > 0.0f ? sqrtf(r_lo * r_hi) : rho * fmaxf(cbrtf(0.8f * (float)CAP / (float)n_in), 0.3f);
       continue;
     }
-    __syncwarp();
-    unsigned long long k[KB];
-    int j[KB], r[KB];
-#pragma unroll
-    for (int t = 0; t < KB; ++t) {
-      const int e = t * 32 + lane;
-      if (kMixed) {
-        k[t] = e < n_in ? buf.key[e] : ~0ull;
-      } else if (e < n_in) {
-        k[t] = buf.key[e]; j[t] = buf.j[e]; r[t] = buf.r[e];
-      } else {
-        k[t] = ~0ull; j[t] = INT_MAX; r[t] = -1;
-      }
-    }
-    __syncwarp();
-    if (kMixed) {
-      sort_packed<KB>(n_in, k, lane);
-#pragma unroll
-      for (int t = 0; t < KB; ++t) { r[t] = (int)(unsigned)k[t]; k[t] >>= 32; }
-    } else {
-      sort_any<KB>(n_in, k, j, r, lane);
-    }
-    unsigned long long kL;
-    get_entry<unsigned long long, KB>(k, L - 1, kL);
-    int* row = A.nbr + q * (long long)A.K;
+    const int iL = buf.select(n_in, L);
     if (!kMixed) {
-#pragma unroll
-      for (int t = 0; t < KB; ++t) {
-        const int e = t * 32 + lane;
-        if (e < L) row[1 + e] = r[t];
+      // exact keys: the L smallest are the members
+      d2max = __longlong_as_double((long long)(((unsigned long long)buf.w(1, iL) << 32) | buf.w(0, iL)));
+      for (int e = 0; e < L; ++e) {
+        const uint32_t j = buf.w(2, e);
+        buf.w(0, e) = j;
+        buf.w(1, e) = (uint32_t)__ldg(&A.rank_of[j]);
       }
-      if (lane == 0) { qi.state = 1; qi.d2max = kL; }
-      dk = sqrtf((float)__longlong_as_double((long long)kL));   // radius hint only
       return true;
     }
     // FP32 bounds with relative margins far above their own rounding
-    const float sq = sqrtf(__uint_as_float((unsigned)kL));
+    const float sq = sqrtf(__uint_as_float(buf.w(0, iL)));
     const float hi_tau = (sq * (1.0f + rel) * 1.000001f + E) * 1.00001f;
     if (hi_tau > rho) {
       if (rho > 2.0f * diag) return false;
@@ -545,192 +415,180 @@ __device__ __forceinline__ bool query_buf(const KnnArgs& A, const Grid32& G, con
       rho = hi_tau * 1.02f;
       continue;
     }
+    const float rf = (rho * (1.0f + 2.0f * rel) + 2.0f * E) * 1.000001f;
+    const float rhof2 = rf * rf * 1.000001f;
     const float lo_tau = (sq * (1.0f - rel) * 0.999999f - E) * 0.99999f;
     const float tlo = (lo_tau - E) / (1.0f + rel);
     const float thi = (hi_tau + E) / (1.0f - rel);
-    const unsigned long long Tlo = tlo > 0.0f ? (unsigned long long)__float_as_uint(tlo * tlo * 0.99999f) : 0ull;
-    const unsigned long long Thi = (unsigned long long)__float_as_uint(thi * thi * 1.00001f);
-    if (Thi > (unsigned long long)__float_as_uint(rhof2)) return false;   // band reaches past the ball
-    int p_lo = 0, p_hi = 0;
-#pragma unroll
-    for (int t = 0; t < KB; ++t) {
-      p_lo += __popc(__ballot_sync(FULL, k[t] < Tlo));
-      p_hi += __popc(__ballot_sync(FULL, k[t] <= Thi));
+    const uint32_t Tlo = tlo > 0.0f ? __float_as_uint(tlo * tlo * 0.99999f) : 0u;
+    const uint32_t Thi = __float_as_uint(thi * thi * 1.00001f);
+    if (Thi > __float_as_uint(rhof2)) return false;   // band reaches past the ball
+    // certain members (key < T_lo) compacted to the front; band ranks set aside
+    int p_lo = 0, nb = 0;
+    int br[kBand];
+    for (int e = 0; e < n_in; ++e) {
+      const uint32_t k = buf.w(0, e);
+      if (k < Tlo) {
+        buf.w(1, p_lo++) = buf.w(1, e);
+      } else if (k <= Thi) {
+        if (nb == kBand) return false;
+        br[nb++] = (int)buf.w(1, e);
+      }
     }
-    const int nb = p_hi - p_lo;
-    if (nb > kBand || p_lo > L - 1) return false;
-#pragma unroll
-    for (int t = 0; t < KB; ++t) {
-      const int e = t * 32 + lane;
-      if (e < p_lo) row[1 + e] = r[t];
-      else if (e < p_hi) qi.band[e - p_lo] = r[t];
+    const int need = L - p_lo;
+    if (need < 1 || need > nb) return false;
+    // exact FP64 keys of the band, the `need` smallest by (d^2, caller index)
+    double bd[kBand];
+    long long bj[kBand];
+    for (int t = 0; t < nb; ++t) bd[t] = d2_fp64(A.pos64, br[t], Q.x, Q.y, Q.z, bx, by, bj[t]);
+    d2max = 0.0;
+    int wr = p_lo;
+    for (int t = 0; t < nb; ++t) {
+      int rank = 0;
+      for (int u = 0; u < nb; ++u)
+        if (bd[u] < bd[t] || (bd[u] == bd[t] && bj[u] < bj[t])) rank++;
+      if (rank < need) {
+        buf.w(1, wr++) = (uint32_t)br[t];
+        d2max = fmax(d2max, bd[t]);
+      }
     }
-    if (lane == 0) {
-      qi.state = 2;
-      qi.p_lo = p_lo;
-      qi.nb = nb;
-      qi.need = L - p_lo;
-    }
-    dk = sq;
+    for (int e = 0; e < L; ++e) buf.w(0, e) = (uint32_t)__ldg(&A.perm[buf.w(1, e)]);
     return true;
   }
   return false;
 }
 
-template <int KPL> struct KnnShape {
-  static constexpr int KB = KPL <= 2 ? 4 : 2 * KPL;       // buffer of 32*KB candidates (>= 2K)
-  static constexpr int WPB = KPL <= 2 ? 8 : (KPL <= 4 ? 4 : 2);
-  static constexpr int MINB = KPL <= 1 ? 3 : 1;           // blocks per SM the registers allow
+template <int CAP> struct KnnShape {
+  // warps per block: buffers (2 words mixed, 3 FP64) of up to four warps within about
+  // 100 KB of shared memory per block
+  static constexpr int bytes(bool mixed) { return (mixed ? 2 : 3) * CAP * kPad * 4; }
+  static constexpr int wpb(bool mixed) {
+    return bytes(mixed) * 4 <= 104 * 1024 ? 4 : (bytes(mixed) * 2 <= 104 * 1024 ? 2 : 1);
+  }
 };
 
-template <int KPL, bool kMixed>
-__global__ void __launch_bounds__(KnnShape<KPL>::WPB * 32, KnnShape<KPL>::MINB) k_knn(KnnArgs A) {
-  constexpr int KB = KnnShape<KPL>::KB, WPB = KnnShape<KPL>::WPB;
-  __shared__ QInfo info[WPB][32];
-  __shared__ CandBuf<KB> buf[WPB];
+template <int CAP, bool kMixed>
+__global__ void __launch_bounds__(128, 5) k_knn(KnnArgs A) {
+  extern __shared__ uint32_t smem[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  LaneBuf<CAP, kMixed> buf;
+  buf.b = smem + (size_t)w * LaneBuf<CAP, kMixed>::NW * CAP * kPad + lane;
   const int L = A.K - 1;
-  for (long long base = warp * 32; base < A.N; base += nwarps * 32) {
-    // ---- phase A: per query, warp-cooperative FP32/INT search
-    int prev_b = -1;
-    float prev_dk = 0.0f;
-    for (int qi_ = 0; qi_ < 32; ++qi_) {
-      const long long q = base + qi_;
-      if (q >= A.N) break;
-      QInfo& qi = info[w][qi_];
-      const int b = inst_of(A.off, A.n_inst, q);
-      const GridDev& Gd = A.grid[b];
-      Grid32 G;
+  const long long total = A.list ? (long long)*A.list_n : A.N;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+    const long long q = A.list ? (long long)A.list[t] : t;
+    const int b = inst_of(A.off, A.n_inst, q);
+    const GridDev& Gd = A.grid[b];
+    Grid32 G;
 #pragma unroll
-      for (int a = 0; a < 3; ++a) { G.cs[a] = Gd.cs32[a]; G.inv[a] = Gd.inv32[a]; G.dim[a] = Gd.dim[a]; }
-      G.per = Gd.periodic != 0;
-      G.cell_off = Gd.cell_off;
-      QueryPos Q;
-      const float4 f = __ldg(A.pos32 + q);
-      const int pk = __float_as_int(f.w);
-      Q.ix = pk & 2047;
-      Q.iy = (pk >> 11) & 2047;
-      Q.iz = (pk >> 22) & 1023;
-      Q.fx = f.x; Q.fy = f.y; Q.fz = f.z;
-      const double2* pp = reinterpret_cast<const double2*>(A.pos64 + q);
-      const double2 a0 = __ldg(pp), a1 = __ldg(pp + 1);
-      Q.x = a0.x; Q.y = a0.y; Q.z = a1.x;
-      // the previous query of the chunk in the same cell gives a close radius
-      // the previous query of the chunk (a neighbour in cell order) gives a close radius
-      float rho = (prev_b == b && prev_dk > 0.0f) ? 1.15f * prev_dk : rho_start(G, A.cstart, Q, L, lane);
-      float dk = 0.0f;
-      bool done = false;
-      if (kMixed) done = query_buf<KB, true>(A, G, Gd, Q, q, lane, rho, qi, buf[w], dk);
-      if (!done) done = query_buf<KB, false>(A, G, Gd, Q, q, lane, rho, qi, buf[w], dk);
-      prev_b = b;
-      prev_dk = done ? dk : 0.0f;
-      if (!done) {
-        // no acceptable radius: keep the row valid (the particle against itself) with an
-        // infinite measure, so the particle gets no rate; the status reports it
-        int* row = A.nbr + q * (long long)A.K;
-        for (int k = lane; k < A.K; k += 32) row[k] = (int)q;
-        if (lane == 0) {
-          qi.state = 0;
-          A.dist[q] = 0.0;
-          A.V[q] = __longlong_as_double(0x7FF0000000000000ll);
-          set_status(&A.st[b], GD_ST_KNN);
+    for (int a = 0; a < 3; ++a) { G.cs[a] = Gd.cs32[a]; G.inv[a] = Gd.inv32[a]; G.dim[a] = Gd.dim[a]; }
+    G.per = Gd.periodic != 0;
+    G.cell_off = Gd.cell_off;
+    QueryPos Q;
+    const float4 f = __ldg(A.pos32 + q);
+    const int pk = __float_as_int(f.w);
+    Q.ix = pk & 2047;
+    Q.iy = (pk >> 11) & 2047;
+    Q.iz = (pk >> 22) & 1023;
+    Q.fx = f.x; Q.fy = f.y; Q.fz = f.z;
+    const double2* pp = reinterpret_cast<const double2*>(A.pos64 + q);
+    const double2 a0 = __ldg(pp), a1 = __ldg(pp + 1);
+    Q.x = a0.x; Q.y = a0.y; Q.z = a1.x;
+    const int ci = (int)__double_as_longlong(a1.y);   // caller index
+    // radius: the last build's d_i when known, else the neighbourhood's density
+    const double dp = A.dprev[ci];
+    const float csmax = fmaxf(G.cs[0], fmaxf(G.cs[1], G.cs[2]));
+    float rho = (dp > 0.0 && dp < 1e30) ? 1.02f * (float)dp : 0.0f;
+    if (!(rho > 1e-4f * csmax)) rho = rho_start(G, A.cstart, Q, L);
+    double d2max = 0.0;
+    const bool ok = lane_query<CAP, kMixed>(A, G, Gd, Q, q, rho, buf, d2max);
+    int* row = A.nbr + q * (long long)A.K;
+    if (ok) {
+      // members by ascending caller index (word 0), written as ranks (word 1)
+      for (int i = 1; i < L; ++i) {
+        const uint32_t j0 = buf.w(0, i), r0 = buf.w(1, i);
+        int k = i - 1;
+        while (k >= 0 && buf.w(0, k) > j0) {
+          buf.w(0, k + 1) = buf.w(0, k);
+          buf.w(1, k + 1) = buf.w(1, k);
+          --k;
         }
+        buf.w(0, k + 1) = j0;
+        buf.w(1, k + 1) = r0;
       }
+      row[0] = (int)q;
+      for (int e = 0; e < L; ++e) row[1 + e] = (int)buf.w(1, e);
+      const double d = sqrt(d2max);
+      A.dist[q] = d;
+      A.V[q] = sample_volume(A.P[b], d, Q.x, Q.y);
+      A.dprev[ci] = d;
+    } else if (kMixed) {
+      // the FP64 form redoes it
+      const unsigned long long slot = atomicAdd(A.redo_n, 1ull);
+      A.redo[slot] = (int)q;
+    } else {
+      // no acceptable radius: keep the row valid (the particle against itself) with an
+      // infinite measure, so the particle gets no rate; the status reports it
+      for (int k = 0; k < A.K; ++k) row[k] = (int)q;
+      A.dist[q] = 0.0;
+      A.V[q] = __longlong_as_double(0x7FF0000000000000ll);
+      A.dprev[ci] = 0.0;
+      set_status(&A.st[b], GD_ST_KNN);
     }
-    __syncwarp();
-    // ---- phase B: lane = query, the FP64 arithmetic
-    {
-      const long long q = base + lane;
-      if (q < A.N) {
-        QInfo& qi = info[w][lane];
-        if (qi.state != 0) {
-          const int b = inst_of(A.off, A.n_inst, q);
-          const GridDev& Gd = A.grid[b];
-          const double2* pp = reinterpret_cast<const double2*>(A.pos64 + q);
-          const double2 a0 = __ldg(pp), a1 = __ldg(pp + 1);
-          double d2max;
-          if (qi.state == 1) {
-            d2max = __longlong_as_double((long long)qi.d2max);
-          } else {
-            // exact FP64 keys of the band, the `need` smallest by (d^2, index)
-            double bd[kBand];
-            long long bj[kBand];
-            for (int t = 0; t < qi.nb; ++t)
-              bd[t] = d2_fp64(A.pos64, qi.band[t], a0.x, a0.y, a1.x, Gd.box[0], Gd.box[1], bj[t]);
-            int* row = A.nbr + q * (long long)A.K;
-            int wr = 1 + qi.p_lo;
-            d2max = 0.0;
-            for (int t = 0; t < qi.nb; ++t) {
-              int rank = 0;
-              for (int u = 0; u < qi.nb; ++u)
-                if (bd[u] < bd[t] || (bd[u] == bd[t] && bj[u] < bj[t])) rank++;
-              if (rank < qi.need) {
-                row[wr++] = qi.band[t];
-                d2max = fmax(d2max, bd[t]);
-              }
-            }
-          }
-          const double d = sqrt(d2max);
-          A.dist[q] = d;
-          A.V[q] = sample_volume(A.P[b], d, a0.x, a0.y);
-        }
-      }
-    }
-    __syncwarp();
-    // ---- phase C: members by ascending caller index.  The rows and caller indices of
-    // kG queries are loaded before any of them is sorted, so their latencies overlap.
-    constexpr int kG = KPL <= 1 ? 4 : (KPL <= 2 ? 2 : 1);
-    for (int q0 = 0; q0 < 32; q0 += kG) {
-      int jj[kG][KPL], rr[kG][KPL];
-      bool live[kG];
-#pragma unroll
-      for (int g = 0; g < kG; ++g) {
-        const long long q = base + q0 + g;
-        live[g] = q < A.N && info[w][q0 + g].state != 0;
-#pragma unroll
-        for (int t = 0; t < KPL; ++t) {
-          const int e = t * 32 + lane;
-          rr[g][t] = (live[g] && e < L) ? A.nbr[q * (long long)A.K + 1 + e] : -1;
-        }
-      }
-#pragma unroll
-      for (int g = 0; g < kG; ++g)
-#pragma unroll
-        for (int t = 0; t < KPL; ++t) jj[g][t] = rr[g][t] >= 0 ? __ldg(&A.perm[rr[g][t]]) : INT_MAX;
-#pragma unroll
-      for (int g = 0; g < kG; ++g) {
-        if (!live[g]) continue;
-        const long long q = base + q0 + g;
-        int* row = A.nbr + q * (long long)A.K;
-        sort_by_index<KPL>(jj[g], rr[g], lane);
-#pragma unroll
-        for (int t = 0; t < KPL; ++t) {
-          const int e = t * 32 + lane;
-          if (e < L) row[1 + e] = rr[g][t];
-        }
-        if (lane == 0) row[0] = (int)q;
-      }
-    }
-    __syncwarp();
   }
 }
 
-template <int KPL, bool kMixed>
+template <int CAP, bool kMixed>
 static cudaError_t launch_knn_t(gd_ctx* c, const KnnArgs& A) {
-  constexpr int kWarps = KnnShape<KPL>::WPB;
+  constexpr int kWarps = KnnShape<CAP>::wpb(kMixed);
   const int bs = kWarps * 32;
+  const int smem = kWarps * KnnShape<CAP>::bytes(kMixed);
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_knn<KPL, kMixed>, bs, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_knn<CAP, kMixed>, bs, smem);
   if (per_sm < 1) per_sm = 1;
-  long long chunks = (A.N + 31) / 32;
-  long long want = (chunks + kWarps - 1) / kWarps;
   long long blocks = (long long)c->num_sms * per_sm;
-  if (blocks > want) blocks = want;
+  if (!A.list) {
+    const long long want = (A.N + bs - 1) / bs;
+    if (blocks > want) blocks = want;
+  }
   if (blocks < 1) blocks = 1;
-  k_knn<KPL, kMixed><<<(int)blocks, bs, 0, c->stream>>>(A);
+  k_knn<CAP, kMixed><<<(int)blocks, bs, smem, c->stream>>>(A);
   return cudaGetLastError();
+}
+
+template <int CAP, bool kMixed>
+static cudaError_t prepare_t() {
+  constexpr int kWarps = KnnShape<CAP>::wpb(kMixed);
+  return cudaFuncSetAttribute(k_knn<CAP, kMixed>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              kWarps * KnnShape<CAP>::bytes(kMixed));
+}
+
+template <bool kMixed>
+static cudaError_t prepare_cap(int K) {
+  if (K <= 32) return prepare_t<40, kMixed>();
+  if (K <= 48) return prepare_t<64, kMixed>();
+  if (K <= 80) return prepare_t<96, kMixed>();
+  if (K <= 128) return prepare_t<144, kMixed>();
+  return prepare_t<272, kMixed>();
+}
+
+// Shared-memory opt-in of the neighbour kernels this context launches (once, before any
+// launch or graph capture).
+cudaError_t knn_prepare(gd_ctx* c) {
+  cudaError_t e = prepare_cap<false>(c->K);
+  if (e == cudaSuccess && c->precision == GD_MIXED) e = prepare_cap<true>(c->K);
+  return e;
+}
+
+template <bool kMixed>
+static cudaError_t launch_cap(gd_ctx* c, const KnnArgs& A) {
+  // buffer capacity: the K-1 members plus room for the radius margin
+  if (c->K <= 32) return launch_knn_t<40, kMixed>(c, A);
+  if (c->K <= 48) return launch_knn_t<64, kMixed>(c, A);
+  if (c->K <= 80) return launch_knn_t<96, kMixed>(c, A);
+  if (c->K <= 128) return launch_knn_t<144, kMixed>(c, A);
+  return launch_knn_t<272, kMixed>(c, A);
 }
 
 cudaError_t launch_knn(gd_ctx* c) {
@@ -745,20 +603,32 @@ cudaError_t launch_knn(gd_ctx* c) {
   A.pos64 = c->d_pos64;
   A.pos32 = c->d_pos32;
   A.perm = c->d_perm;
+  A.rank_of = c->d_rank_of;
   A.nbr = c->d_nbr;
   A.dist = c->d_dist;
   A.V = c->d_V;
+  A.dprev = c->d_dprev;
   A.st = c->d_state;
-  const bool mixed = c->precision == GD_MIXED;
-  const int kpl = (c->K + 31) / 32;   // room for K-1 members and at least one band slot
+  A.redo = c->d_redo;
+  A.redo_n = c->d_counters + 1;
+  A.list = nullptr;
+  A.list_n = nullptr;
   time_begin(c, 1);
-  cudaError_t e;
-  if (kpl <= 1) e = mixed ? launch_knn_t<1, true>(c, A) : launch_knn_t<1, false>(c, A);
-  else if (kpl <= 2) e = mixed ? launch_knn_t<2, true>(c, A) : launch_knn_t<2, false>(c, A);
-  else if (kpl <= 4) e = mixed ? launch_knn_t<4, true>(c, A) : launch_knn_t<4, false>(c, A);
-  else e = mixed ? launch_knn_t<8, true>(c, A) : launch_knn_t<8, false>(c, A);
+  cudaError_t e = cudaSuccess;
+  if (c->precision == GD_MIXED) {
+    e = cudaMemsetAsync(A.redo_n, 0, sizeof(unsigned long long), c->stream);
+    if (e == cudaSuccess) e = launch_cap<true>(c, A);
+    // the queries the FP32 keys could not decide, in the FP64 form
+    KnnArgs B = A;
+    B.list = c->d_redo;
+    B.list_n = A.redo_n;
+    if (e == cudaSuccess) e = launch_cap<false>(c, B);
+    c->launches += 2;
+  } else {
+    e = launch_cap<false>(c, A);
+    c->launches += 1;
+  }
   time_end(c);
-  c->launches += 1;
   return e;
 }
 
