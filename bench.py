@@ -79,6 +79,25 @@ def algo_bytes(kernel, K, mixed):
     return 0
 
 
+# DRAM bytes (read + write) of one launch at full size, from a one-pass ncu capture of the
+# bench command (dram__bytes_read.sum + dram__bytes_write.sum), per particle.  A record
+# holds only while the kernel's source file has the recorded content hash.
+KERNEL_SOURCE = {"knn": "k_knn.cu", "rates": "k_mc.cu", "sample": "k_mc.cu", "cells": "k_cells.cu"}
+TRAFFIC = {}
+
+
+def kernel_traffic(kernel, workload, n):
+    import hashlib
+    rec = TRAFFIC.get(kernel)
+    if not rec or rec["workload"] != workload:
+        return None
+    path = os.path.join(ROOT, "paper_2609_35967_gb300", "csrc", KERNEL_SOURCE[kernel])
+    with open(path, "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest() != rec["sha256"]:
+            return None
+    return rec["bytes_per_particle"] * n
+
+
 class ClockSampler:
     def __init__(self, index=0):
         self.samples = []
@@ -177,7 +196,8 @@ def run_gpu(args, rank, world):
                "kernel_ms": {k: post["kernel_ms"][k] - pre["kernel_ms"][k] for k in post["kernel_ms"]},
                "kernel_calls": {k: post["kernel_calls"][k] - pre["kernel_calls"][k]
                                 for k in post["kernel_calls"]},
-               "events": post["events"] - pre["events"], "status": post["status"], "cell_factor": cf}
+               "events": post["events"] - pre["events"], "status": post["status"], "cell_factor": cf,
+               "knn_redo": post["knn_redo"] - pre["knn_redo"]}
         sess.close()
         return res
 
@@ -339,8 +359,9 @@ def result_line(r, args, world):
                        parallelism=f"{world} independent replicas" if world > 1 else "1 GPU",
                        cell_factor=r["mixed"]["cell_factor"]),
         "events_per_step": r["mixed"]["events"] / args.steps,
+        "knn_fp64_redo_per_step": r["mixed"].get("knn_redo", 0) / args.steps,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": r["hbm"], "unit": "GB/s",
-                     "frac": ach / r["hbm"], "traffic": None,
+                     "frac": ach / r["hbm"], "traffic": kernel_traffic(dom, args.workload, N),
                      "peak_kind": r["peak_kind"],
                      "algo_bytes_per_particle": algo_bytes(dom, K, True)},
         "kernels_ms_per_step": {k: v / args.steps for k, v in km.items() if v > 0 and k != "stats"},

@@ -150,6 +150,8 @@ typedef struct {
                                   0 cells, 1 knn, 2 rates, 3 interval, 4 sample,
                                   5 push, 6 stats/other, 7 unused              */
   int64_t kernel_calls[8];     /* launches timed in each slot                  */
+  int64_t knn_redo;            /* mixed form: neighbour searches the FP32 keys
+                                  could not decide, redone in FP64 (all builds) */
 } gd_stats_t;
 
 /* Per-instance state and reductions (gd_stats). */

@@ -348,6 +348,7 @@ extern "C" gd_status gd_stats(gd_ctx* c, gd_stats_t* out, gd_instance_stats* ins
     out->near_draw += s.near_draw;
     out->near_dt += s.near_dt;
     out->near_audit += s.near_audit;
+    out->knn_redo += s.knn_redo;
     out->status |= s.status;
     if (inst_out) {
       gd_instance_stats& o = inst_out[b];

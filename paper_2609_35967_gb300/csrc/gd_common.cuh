@@ -63,6 +63,7 @@ struct StateDev {
   long long interval_cur;   // Philox interval counter of the current interval
   long long interval_next;
   long long events, events_total, near_draw, near_dt, near_audit;
+  long long knn_redo;       // mixed K-NN queries redone in FP64
   unsigned int status;
   int n_groups;
   // bounds of the data (ordered-integer encodings of doubles), min then max, x y z

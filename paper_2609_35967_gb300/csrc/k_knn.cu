@@ -6,8 +6,9 @@
 // entry e at [(w * CAP + e) * 33 + l], so lanes touching the same entry, or one lane
 // walking its entries, never share a bank.
 //
-//  radius : 1.02 x the particle's d_i of the previous build when there is one, else an
-//           estimate from the particle count of the 27 cells around it;
+//  radius : 1.02 x the particle's d_i of the previous build when there is one (exact
+//           when the particles did not move; after a push the radius search corrects it),
+//           else an estimate from the particle count of the 27 cells around it;
 //  scan   : the cell rows that meet the ball are produced row by row and consumed
 //           candidate by candidate in one loop (the cell starts of the next row are
 //           loaded while the current row is scanned); keys inside the ball are kept;
@@ -527,6 +528,7 @@ __global__ void __launch_bounds__(128, 5) k_knn(KnnArgs A) {
       // the FP64 form redoes it
       const unsigned long long slot = atomicAdd(A.redo_n, 1ull);
       A.redo[slot] = (int)q;
+      atomicAdd((unsigned long long*)&A.st[b].knn_redo, 1ull);
     } else {
       // no acceptable radius: keep the row valid (the particle against itself) with an
       // infinite measure, so the particle gets no rate; the status reports it

@@ -314,7 +314,8 @@ __device__ __forceinline__ double waiting_time(uint32_t a, uint32_t b, double la
     return -log(u01(a, b)) / lam;
   } else {
     const float nl = neg_log_u01_f32(a, b);
-    if (lam >= 1e-30 && lam <= 1e30) return (double)(nl / (float)lam);
+    const float lf = (float)lam;
+    if (lf > 1e-30f && lf < 1e30f) return (double)(nl / lf);
     return (double)nl / lam;
   }
 }
@@ -639,6 +640,7 @@ __global__ void __launch_bounds__(64) k_sample(McArgs A) {
       const unsigned k0 = __shfl_sync(FULLM, key0, p), k1 = __shfl_sync(FULLM, key1, p);
       const int bp = __shfl_sync(FULLM, b, p);
       const double s_start = s;
+      const double tie_dte = tie_tol<T>() * dte;
       int e = 0, near_ch = 0, near_u = 0;   // per-lane channel ties, warp-uniform ties
       unsigned h = 0u;
       T J = (T)0;
@@ -660,15 +662,15 @@ __global__ void __launch_bounds__(64) k_sample(McArgs A) {
         for (int t2 = 0; t2 < S; ++t2) {
           int k = lane * S + t2;
           if (jr[t2] < 0) continue;
-          double a = (double)c0[t2], bb = (double)c1[t2];
+          const double a = (double)c0[t2], bb = (double)c1[t2];
           cum = __dadd_rn(cum, a);
-          if (a > 0.0) {
+          if (c0[t2] > (T)0) {
             lastnz = 2 * k;
             if (fabs(target - cum) < tie_ch) near_ch++;
             if (sel == INT_MAX && target < cum) sel = 2 * k;
           }
           cum = __dadd_rn(cum, bb);
-          if (bb > 0.0) {
+          if (c1[t2] > (T)0) {
             lastnz = 2 * k + 1;
             if (fabs(target - cum) < tie_ch) near_ch++;
             if (sel == INT_MAX && target < cum) sel = 2 * k + 1;
@@ -689,24 +691,30 @@ __global__ void __launch_bounds__(64) k_sample(McArgs A) {
         const int owner = slot / S, tsl = slot % S;
         // partner data and outcome from the owning lane
         int jo = jr[0], oc = po[0].outcome;
-        T nco = po[0].ncoll;
+        T nco = po[0].ncoll, pso = po[0].psi;
 #pragma unroll
         for (int t2 = 1; t2 < S; ++t2)
-          if (t2 == tsl) { jo = jr[t2]; oc = po[t2].outcome; nco = po[t2].ncoll; }
+          if (t2 == tsl) { jo = jr[t2]; oc = po[t2].outcome; nco = po[t2].ncoll; pso = po[t2].psi; }
         const int j = __shfl_sync(FULLM, jo, owner);
         const int outcome = __shfl_sync(FULLM, oc, owner);
-        const double ncoll = (double)__shfl_sync(FULLM, nco, owner);
+        const T ncoll_t = __shfl_sync(FULLM, nco, owner);
+        const T psi_t = __shfl_sync(FULLM, pso, owner);
+        const double ncoll = (double)ncoll_t;
         const Snap64 pj = A.snap64[j];
         double m_new, s_new;
+        float Jf = 0.0f;   // mixed form: |ln s'/s| of the event from the pair's FP32 psi
         if (outcome == 0) {
-          m_new = m + ncoll * pj.m;
+          if constexpr (sizeof(T) == 8) m_new = m + ncoll * pj.m; else m_new = fma(ncoll, pj.m, m);
           s_new = diameter_of<T>(cube_of<T>(f, m_new));
+          if constexpr (sizeof(T) == 4) Jf = log1pf((float)ncoll_t * (float)psi_t) * (1.0f / 3.0f);
         } else if (outcome == 1 && ch == 0) {
-          m_new = m - ncoll * pj.m;
+          if constexpr (sizeof(T) == 8) m_new = m - ncoll * pj.m; else m_new = fma(-ncoll, pj.m, m);
           s_new = diameter_of<T>(cube_of<T>(f, m_new));
+          if constexpr (sizeof(T) == 4) Jf = fabsf(log1pf(-(float)ncoll_t * (float)psi_t)) * (1.0f / 3.0f);
         } else if (outcome == 1) {
           m_new = pj.m;
           s_new = pj.s;
+          if constexpr (sizeof(T) == 4) Jf = fabsf(logf((float)psi_t)) * (1.0f / 3.0f);
         } else {
           U4 w2 = philox(il, iv, (unsigned)e, 1u, k0, k1);
           if constexpr (sizeof(T) == 8) {
@@ -722,10 +730,11 @@ __global__ void __launch_bounds__(64) k_sample(McArgs A) {
             const float xr = fmaf(U, bq - a, a);
             s_new = (double)(xr * xr);
             m_new = s_new * s_new * s_new / f.k6;
+            Jf = 2.0f * fabsf(logf(xr / bq));
           }
         }
         if constexpr (sizeof(T) == 8) J += fabs(log(s_new / s));
-        else J += fabsf(log1pf((float)(s_new - s) / (float)s));
+        else J += Jf;
         s = s_new;
         m = m_new;
         h = h * 31u + (unsigned)(chosen + 1);
@@ -743,7 +752,7 @@ __global__ void __launch_bounds__(64) k_sample(McArgs A) {
         U4 w = philox(il, iv, (unsigned)e, 0u, k0, k1);
         u_s = u01(w.z, w.w);
         const double dt2 = waiting_time<T>(w.x, w.y, lam_now);
-        if (fabs((t + dt2) - dte) < tie_tol<T>() * dte) near_u++;
+        if (fabs((t + dt2) - dte) < tie_dte) near_u++;
         if (t + dt2 > dte) break;
         t = t + dt2;
       }

@@ -59,7 +59,7 @@ def _fake_rank_result(N=1000, K=32, ms=(20.0, 60.0, 25.0)):
 
 
 def test_result_line_whole_job_value():
-    args = types.SimpleNamespace(steps=10, warmup=3)
+    args = types.SimpleNamespace(steps=10, warmup=3, workload="disk22")
     for world in (1, 2, 4):
         r = _fake_rank_result()
         out = bench.result_line(r, args, world)
