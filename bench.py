@@ -83,7 +83,14 @@ def algo_bytes(kernel, K, mixed):
 # bench command (dram__bytes_read.sum + dram__bytes_write.sum), per particle.  A record
 # holds only while the kernel's source file has the recorded content hash.
 KERNEL_SOURCE = {"knn": "k_knn.cu", "rates": "k_mc.cu", "sample": "k_mc.cu", "cells": "k_cells.cu"}
-TRAFFIC = {}
+TRAFFIC = {
+    "knn": {"workload": "disk22", "bytes_per_particle": (638.67e6 + 670.52e6) / 4194304,
+            "sha256": "192cdd3ec158ac3d45689e42440505331ce66dcb9ab1a9e1995c1eceba2f8c2e"},
+    "rates": {"workload": "disk22", "bytes_per_particle": (1107.226e6 + 34.108e6) / 4194304,
+              "sha256": "1b13bc85bd63bf91acc7252eae5382910f30c276d2b1f968244e60402870c45a"},
+    "sample": {"workload": "disk22", "bytes_per_particle": (439.222e6 + 12.090e6) / 4194304,
+               "sha256": "1b13bc85bd63bf91acc7252eae5382910f30c276d2b1f968244e60402870c45a"},
+}
 
 
 def kernel_traffic(kernel, workload, n):
