@@ -469,7 +469,7 @@ template <int CAP> struct KnnShape {
 };
 
 template <int CAP, bool kMixed>
-__global__ void __launch_bounds__(128, 5) k_knn(KnnArgs A) {
+__global__ void __launch_bounds__(128, CAP <= 40 ? 5 : 4) k_knn(KnnArgs A) {
   extern __shared__ uint32_t smem[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   LaneBuf<CAP, kMixed> buf;

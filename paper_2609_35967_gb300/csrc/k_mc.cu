@@ -279,6 +279,27 @@ __device__ __forceinline__ double cube_of(const Fixed<T>& f, double m) {
   if constexpr (sizeof(T) == 8) return 6.0 * m / (kPi * f.rho_s); else return m * f.k6;
 }
 
+// This lane's channel rates summed in FP32 (slot order), for the mixed form's FP32 prefix.
+template <int S>
+__device__ __forceinline__ float lane_sumf(const float (&c0)[S], const float (&c1)[S], const int (&jr)[S]) {
+  float v = 0.0f;
+#pragma unroll
+  for (int t = 0; t < S; ++t)
+    if (jr[t] >= 0) { v += c0[t]; v += c1[t]; }
+  return v;
+}
+template <int S>
+__device__ __forceinline__ float lane_sumf(const double (&)[S], const double (&)[S], const int (&)[S]) { return 0.0f; }
+
+__device__ __forceinline__ float warp_incl_scanf(float v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float t = __shfl_up_sync(FULLM, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
 // Diameter from s^3 = x.  FP64 form: cbrt.  Mixed form: the FP32 cube root y refined by
 // one Newton step for y^3 = x, y <- y - (y^3 - x)/(3 y^2), with the residual in FP64 and
 // the 1/(3 y^2) factor in FP32: ~1e-13 relative for a handful of FP64 instructions.
@@ -575,7 +596,7 @@ __global__ void __launch_bounds__(64) k_sample(McArgs A) {
     const bool valid = r < A.N;
     int b = 0;
     double lam = 0.0, dtw = 0.0, us = 0.0, dt_exe = 0.0;
-    unsigned ival = 0, i_loc = 0, key0 = 0, key1 = 0;
+    unsigned ival = 0, i_loc = 0, key0 = 0, key1 = 0, usw0 = 0, usw1 = 0;
     bool ev = false;
     int nn = 0;
     if (valid) {
@@ -588,7 +609,9 @@ __global__ void __launch_bounds__(64) k_sample(McArgs A) {
       i_loc = (unsigned)(A.perm[r] - P.off);
       lam = A.lam[r];
       U4 w = philox(i_loc, ival, 0u, 0u, key0, key1);
-      us = u01(w.z, w.w);
+      usw0 = w.z;
+      usw1 = w.w;
+      if constexpr (sizeof(T) == 8) us = u01(w.z, w.w);
       if (lam > 0.0 && isfinite(lam)) {
         dtw = waiting_time<T>(w.x, w.y, lam);
         if (fabs(dtw - dt_exe) < tie_tol<T>() * dt_exe) nn++;
@@ -635,6 +658,7 @@ __global__ void __launch_bounds__(64) k_sample(McArgs A) {
       double s = __shfl_sync(FULLM, s_i, p), m = __shfl_sync(FULLM, m_i, p);
       double t = __shfl_sync(FULLM, dtw, p);
       double u_s = __shfl_sync(FULLM, us, p);
+      unsigned uw0 = __shfl_sync(FULLM, usw0, p), uw1 = __shfl_sync(FULLM, usw1, p);   // words of U_s
       const double dte = __shfl_sync(FULLM, dt_exe, p);
       const unsigned iv = __shfl_sync(FULLM, ival, p), il = __shfl_sync(FULLM, i_loc, p);
       const unsigned k0 = __shfl_sync(FULLM, key0, p), k1 = __shfl_sync(FULLM, key1, p);
@@ -649,42 +673,100 @@ __global__ void __launch_bounds__(64) k_sample(McArgs A) {
       PairOut<T> po[S];
       Query<T> q = live_query<T>(f, s, m);
       double v = lane_channels<T, S>(A, q, rp, lane, c0, c1, jr, po);
-      double incl = warp_incl_scan(v, lane);
-      double tot = __shfl_sync(FULLM, incl, 31);
+      double incl = 0.0, tot = 0.0;
+      float inclf = 0.0f, totf = 0.0f;
+      if constexpr (sizeof(T) == 8) {
+        incl = warp_incl_scan(v, lane);
+        tot = __shfl_sync(FULLM, incl, 31);
+      } else {
+        inclf = warp_incl_scanf(lane_sumf<S>(c0, c1, jr), lane);
+        totf = __shfl_sync(FULLM, inclf, 31);
+      }
       for (;;) {
         // partner channel: the first cumulative rate above U_s lambda*
-        const double target = u_s * tot;
-        const double tie_ch = tie_tol<T>() * tot;
-        double cum = __shfl_up_sync(FULLM, incl, 1);
-        if (lane == 0) cum = 0.0;
-        int sel = INT_MAX, lastnz = -1;
+        int chosen = INT_MAX;
+        bool certified = false;
+        if constexpr (sizeof(T) == 4) {
+          // Mixed form: the choice of the FP64 prefix, found on the FP32 prefix.  Any FP32
+          // prefix of these FP32 rates is within (5 + 2S + 2) u lambda* of the exact one, so
+          // when the target lies more than 4e-6 lambda* inside the chosen channel both give
+          // that channel; otherwise the FP64 prefix below decides.
+          const float tf = fmaf((float)(uw0 >> 6), 0x1p26f, (float)(uw1 >> 6) + 0.5f) * 0x1p-52f * totf;
+          const float tie_f = 2e-5f * totf, mg = 4e-6f * totf;
+          float cumf = __shfl_up_sync(FULLM, inclf, 1);
+          if (lane == 0) cumf = 0.0f;
+          int sel = INT_MAX;
+          float blo = 0.0f, bhi = 0.0f;
 #pragma unroll
-        for (int t2 = 0; t2 < S; ++t2) {
-          int k = lane * S + t2;
-          if (jr[t2] < 0) continue;
-          const double a = (double)c0[t2], bb = (double)c1[t2];
-          cum = __dadd_rn(cum, a);
-          if (c0[t2] > (T)0) {
-            lastnz = 2 * k;
-            if (fabs(target - cum) < tie_ch) near_ch++;
-            if (sel == INT_MAX && target < cum) sel = 2 * k;
+          for (int t2 = 0; t2 < S; ++t2) {
+            const int k = lane * S + t2;
+            if (jr[t2] < 0) continue;
+            const float b0 = cumf;
+            cumf += c0[t2];
+            if (c0[t2] > 0.0f) {
+              if (fabsf(tf - cumf) < tie_f) near_ch++;
+              if (sel == INT_MAX && tf < cumf) { sel = 2 * k; blo = b0; bhi = cumf; }
+            }
+            const float b1 = cumf;
+            cumf += c1[t2];
+            if (c1[t2] > 0.0f) {
+              if (fabsf(tf - cumf) < tie_f) near_ch++;
+              if (sel == INT_MAX && tf < cumf) { sel = 2 * k + 1; blo = b1; bhi = cumf; }
+            }
           }
-          cum = __dadd_rn(cum, bb);
-          if (c1[t2] > (T)0) {
-            lastnz = 2 * k + 1;
-            if (fabs(target - cum) < tie_ch) near_ch++;
-            if (sel == INT_MAX && target < cum) sel = 2 * k + 1;
+          chosen = sel;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) chosen = min(chosen, __shfl_xor_sync(FULLM, chosen, o));
+          if (chosen != INT_MAX) {
+            const int own = (chosen >> 1) / S;
+            const bool ok = (bhi - tf > mg) && (blo == 0.0f || tf - blo > mg);
+            certified = __shfl_sync(FULLM, ok, own);
+          }
+          if (!certified) {
+            // the FP64 prefix of the same rates
+            v = 0.0;
+#pragma unroll
+            for (int t2 = 0; t2 < S; ++t2)
+              if (jr[t2] >= 0) { v = __dadd_rn(v, (double)c0[t2]); v = __dadd_rn(v, (double)c1[t2]); }
+            incl = warp_incl_scan(v, lane);
+            tot = __shfl_sync(FULLM, incl, 31);
+            u_s = u01(uw0, uw1);
           }
         }
-        int chosen = sel;
+        if (!certified) {
+          const double target = u_s * tot;
+          const double tie_ch = tie_tol<T>() * tot;
+          double cum = __shfl_up_sync(FULLM, incl, 1);
+          if (lane == 0) cum = 0.0;
+          int sel = INT_MAX, lastnz = -1;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) chosen = min(chosen, __shfl_xor_sync(FULLM, chosen, o));
-        if (chosen == INT_MAX) {
-          int ln = lastnz;
+          for (int t2 = 0; t2 < S; ++t2) {
+            int k = lane * S + t2;
+            if (jr[t2] < 0) continue;
+            const double a = (double)c0[t2], bb = (double)c1[t2];
+            cum = __dadd_rn(cum, a);
+            if (c0[t2] > (T)0) {
+              lastnz = 2 * k;
+              if (sizeof(T) == 8 && fabs(target - cum) < tie_ch) near_ch++;
+              if (sel == INT_MAX && target < cum) sel = 2 * k;
+            }
+            cum = __dadd_rn(cum, bb);
+            if (c1[t2] > (T)0) {
+              lastnz = 2 * k + 1;
+              if (sizeof(T) == 8 && fabs(target - cum) < tie_ch) near_ch++;
+              if (sel == INT_MAX && target < cum) sel = 2 * k + 1;
+            }
+          }
+          chosen = sel;
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) ln = max(ln, __shfl_xor_sync(FULLM, ln, o));
-          chosen = ln;
-          near_u++;
+          for (int o = 16; o > 0; o >>= 1) chosen = min(chosen, __shfl_xor_sync(FULLM, chosen, o));
+          if (chosen == INT_MAX) {
+            int ln = lastnz;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) ln = max(ln, __shfl_xor_sync(FULLM, ln, o));
+            chosen = ln;
+            near_u++;
+          }
         }
         if (chosen < 0) break;
         const int slot = chosen >> 1, ch = chosen & 1;
@@ -742,15 +824,22 @@ __global__ void __launch_bounds__(64) k_sample(McArgs A) {
         if (e >= A.max_events) { if (lane == 0) set_status(&A.st[bp], GD_ST_EVENT_CAP); break; }
         q = live_query<T>(f, s, m);
         v = lane_channels<T, S>(A, q, rp, lane, c0, c1, jr, po);
-        incl = warp_incl_scan(v, lane);
-        tot = __shfl_sync(FULLM, incl, 31);
-        const double lam_now = f.pref * tot;
+        if constexpr (sizeof(T) == 8) {
+          incl = warp_incl_scan(v, lane);
+          tot = __shfl_sync(FULLM, incl, 31);
+        } else {
+          inclf = warp_incl_scanf(lane_sumf<S>(c0, c1, jr), lane);
+          totf = __shfl_sync(FULLM, inclf, 31);
+        }
+        const double lam_now = f.pref * (sizeof(T) == 8 ? tot : (double)totf);
         if (!(lam_now > 0.0) || !isfinite(lam_now)) {
           if (lane == 0 && !(lam_now == 0.0)) set_status(&A.st[bp], GD_ST_NONFINITE);
           break;
         }
         U4 w = philox(il, iv, (unsigned)e, 0u, k0, k1);
-        u_s = u01(w.z, w.w);
+        uw0 = w.z;
+        uw1 = w.w;
+        if constexpr (sizeof(T) == 8) u_s = u01(w.z, w.w);
         const double dt2 = waiting_time<T>(w.x, w.y, lam_now);
         if (fabs((t + dt2) - dte) < tie_dte) near_u++;
         if (t + dt2 > dte) break;
