@@ -238,10 +238,10 @@ gd_status gd_stats(gd_ctx* ctx, gd_stats_t* out, gd_instance_stats* inst_out);
 gd_status gd_run_intervals(gd_ctx* ctx, int32_t n, int32_t push);
 
 /* Autotuner: times the cell binning and neighbour search (gd_build_neighbors'
- * kernels) on the current positions for a set of cell sizes -- the edge is
- * factor * (V_box / N)^(1/3) for factor in {0.4, 0.5, ..., 1.4} -- with CUDA
- * events, and keeps the fastest factor for the context (instances with an
- * explicit cell_size keep it).  Results never depend on the choice: the lists
+ * kernels) on the current positions for a set of cell shapes -- the y and z edge
+ * is factor * (V_box / N)^(1/3) for factor in {0.5, 0.6, 0.7, 0.8, 1.0, 1.2, 1.4},
+ * the x edge that divided by 1, 2 or 4 -- with CUDA events, and keeps the fastest
+ * for the context (instances with an explicit cell_size keep their edge).  Results never depend on the choice: the lists
  * are exact for any cell size.  Synchronises the stream; call it before
  * gd_run_intervals captures its graph.  Leaves the context ready for
  * gd_build_neighbors.  factor_out: HOST or NULL, receives the chosen factor. */

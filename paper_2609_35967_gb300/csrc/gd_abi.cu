@@ -125,7 +125,7 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
 
   std::vector<long long> tiles = tile_table(c->h_off);
   c->n_tiles = (int)tiles.back();
-  c->cell_cap = 8 * N + 64LL * n + 1024;
+  c->cell_cap = 16 * N + 64LL * n + 1024;
   long long nst = (c->cell_cap + 2047) / 2048;
 
   bool ok = true;
@@ -373,17 +373,21 @@ extern "C" gd_status gd_stats(gd_ctx* c, gd_stats_t* out, gd_instance_stats* ins
 extern "C" gd_status gd_autotune(gd_ctx* c, double* factor_out) {
   if (!c) return GD_ERR_ARG;
   if (c->phase != 0 && c->phase != 1) return GD_ERR_STATE;
-  static const double kFactors[] = {0.4, 0.5, 0.6, 0.7, 0.8, 0.9, 1.0, 1.2, 1.4};
+  static const double kFactors[] = {0.5, 0.6, 0.7, 0.8, 1.0, 1.2, 1.4};
+  static const int kSplits[] = {1, 2, 4};
   const int saved_flags = c->flags;
   c->flags &= ~GD_FLAG_TIMING;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) { c->flags = saved_flags; return GD_ERR_CUDA; }
   if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); c->flags = saved_flags; return GD_ERR_CUDA; }
   double best = c->cell_factor;
+  int best_split = c->cell_xsplit;
   float best_ms = 1e30f;
   gd_status st = GD_OK;
-  for (double f : kFactors) {
+  for (int k = 0; k < 21 && st == GD_OK; ++k) {
+    const double f = kFactors[k / 3];
     c->cell_factor = f;
+    c->cell_xsplit = kSplits[k % 3];
     cudaError_t e = launch_cells(c);                  // warm-up: grid and lists for this size
     if (e == cudaSuccess) e = launch_knn(c);
     if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
@@ -394,12 +398,13 @@ extern "C" gd_status gd_autotune(gd_ctx* c, double* factor_out) {
     float ms = 0.0f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
     if (e != cudaSuccess) { st = GD_ERR_CUDA; break; }
-    if (ms < best_ms) { best_ms = ms; best = f; }
+    if (ms < best_ms) { best_ms = ms; best = f; best_split = c->cell_xsplit; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   c->flags = saved_flags;
   c->cell_factor = best;
+  c->cell_xsplit = best_split;
   c->phase = 0;
   if (c->graph_exec) { cudaGraphExecDestroy(c->graph_exec); c->graph_exec = nullptr; c->graph_push = -1; }
   if (factor_out) *factor_out = best;

@@ -127,7 +127,7 @@ __global__ void k_bounds(TileMap tm, const double* __restrict__ x, const double*
 // box in x and y), cell edge from the instance or cell_factor (V_box / n)^(1/3), then
 // the concatenated cell offsets.  If the total exceeds the capacity every edge grows.
 __global__ void k_grid(const InstDev* __restrict__ P, StateDev* st, GridDev* grid, int n_inst,
-                       double cell_factor, long long cell_cap) {
+                       double cell_factor, int xsplit, long long cell_cap) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double grow = 1.0;
   for (int attempt = 0; attempt < 40; ++attempt) {
@@ -153,7 +153,8 @@ __global__ void k_grid(const InstDev* __restrict__ P, StateDev* st, GridDev* gri
       for (int a = 0; a < 3; ++a) {
         bool pa = per && a < 2;
         double e = pa ? ext[a] : ext[a] * (1.0 + 1e-9) + 1e-12 * emax + tiny;
-        double dimd = pa ? floor(e / c) : ceil(e / c);
+        const double ca = a == 0 ? c / xsplit : c;
+        double dimd = pa ? floor(e / ca) : ceil(e / ca);
         int dim = (int)fmin(fmax(dimd, 1.0), a < 2 ? 2048.0 : 1024.0);
         g.lo[a] = lo[a];
         g.cs[a] = e / dim;
@@ -387,7 +388,8 @@ cudaError_t launch_cells(gd_ctx* c) {
   cudaStream_t st = c->stream;
   time_begin(c, 0);
   k_bounds<<<nt, 256, 0, st>>>(tm, c->x, c->y, c->z, c->d_state);
-  k_grid<<<1, 32, 0, st>>>(c->d_inst, c->d_state, c->d_grid, c->n_inst, c->cell_factor, c->cell_cap);
+  k_grid<<<1, 32, 0, st>>>(c->d_inst, c->d_state, c->d_grid, c->n_inst, c->cell_factor, c->cell_xsplit,
+                           c->cell_cap);
   cudaMemsetAsync(c->d_cell_count, 0, sizeof(int) * (c->cell_cap + 1), st);
   k_cell_count<<<nt, 256, 0, st>>>(tm, c->d_grid, c->x, c->y, c->z, c->d_cell_count, c->d_cell_of,
                                    c->d_slot, c->cell_cap);
