@@ -342,15 +342,17 @@ __device__ __forceinline__ double waiting_time(uint32_t a, uint32_t b, double la
 }
 
 // ---------------------------------------------------------------- rate kernel
+// Lane = particle: each thread walks its own neighbour row (the 128-byte row stays in
+// L1 across the walk), evaluates the K pairs in slot order and sums lambda*_i and the bin
+// moments in registers.  FP64 form: the channel rates are added in the oracle's order
+// (slot by slot, remnant before debris).  Block-level fine-bin sums of the block's first
+// instance: FP64 form in FP64; mixed form in FP32 (native shared atomics; they only feed
+// the interval controller), added to the instance's FP64 bins once per block.
 template <typename T, int S>
 __global__ void __launch_bounds__(128) k_rates(McArgs A) {
-  // block-level fine-bin sums of the block's first instance: FP64 form in FP64; mixed form
-  // in FP32 (native shared atomics; they only feed the interval controller), then added
-  // to the instance's FP64 bins once per block
   __shared__ double sh[4][kNFine];
   __shared__ float shf[3][kNFine];
   __shared__ unsigned shc[kNFine];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const long long lo = (long long)blockIdx.x * A.range;
   const long long hi = min(lo + A.range, A.N);
   if (lo >= hi) return;
@@ -363,125 +365,67 @@ __global__ void __launch_bounds__(128) k_rates(McArgs A) {
     for (int t = threadIdx.x; t < kNFine; t += blockDim.x) shc[t] = 0u;
   }
   __syncthreads();
-  for (long long base = lo + 32LL * wib; base < hi; base += 32LL * nw) {
-    const long long r = base + lane;
-    const bool valid = r < hi;
-    int b = 0;
+  for (long long r = lo + threadIdx.x; r < hi; r += blockDim.x) {
+    const int b = inst_of(A.off, A.n_inst, r);
+    const InstDev& P = A.P[b];
+    const Pos64 p = A.pos64[r];
+    const Snap64 sn = A.snap64[r];
+    const double s_i = sn.s, m_i = sn.m;
     Fixed<T> fx;
-    double s_i = 1.0, m_i = 1.0, fj1 = 0.0, fj2 = 0.0;
-    if (valid) {
-      b = inst_of(A.off, A.n_inst, r);
-      const InstDev& P = A.P[b];
-      const Pos64 p = A.pos64[r];
-      const Snap64 sn = A.snap64[r];
-      s_i = sn.s;
-      m_i = sn.m;
-      if constexpr (sizeof(T) == 8) {
-        Gas g = gas_at(P, p.x, p.y, p.z);
-        fx = make_fixed<double>(P, g, A.V[r], A.Mr[r], A.K);
-        frag_moments(s_i, P.s_min, fj1, fj2);
-      } else {
-        fx = make_fixed_f32(P, p.x, p.y, p.z, A.V[r], A.Mr[r], A.K);
-        frag_moments_f32(s_i, P.s_min, fj1, fj2);
-      }
+    double fj1, fj2;
+    if constexpr (sizeof(T) == 8) {
+      Gas g = gas_at(P, p.x, p.y, p.z);
+      fx = make_fixed<double>(P, g, A.V[r], A.Mr[r], A.K);
+      frag_moments(s_i, P.s_min, fj1, fj2);
     } else {
-      fx = Fixed<T>{};
-      fx.pref = 0.0;
-      fx.mode = 0;
+      fx = make_fixed_f32(P, p.x, p.y, p.z, A.V[r], A.Mr[r], A.K);
+      frag_moments_f32(s_i, P.s_min, fj1, fj2);
     }
-    T my_tot = (T)0, my_a = (T)0, my_b = (T)0;     // lane = particle; converted once below
-    const Query<T> myq = live_query<T>(fx, s_i, m_i);     // lane = particle
-    const T myj1 = (T)fj1, myj2 = (T)fj2;
-    const double mypref = fx.pref;
-    // valid lanes are a prefix of the chunk; the loads are software-pipelined: the
-    // partners of the next particle and the row two ahead are in flight while the
-    // pairs of the current one are evaluated
-    const int nv = __popc(__ballot_sync(FULLM, valid));
-    int jA[S], jB[S];
-    Partner<T> ptA[S];
-    if (nv > 0) { load_row_slots<S>(A, base, lane, jA); load_partners<T, S>(A, jA, ptA); }
-    if (nv > 1) load_row_slots<S>(A, base + 1, lane, jB);
-    for (int p = 0; p < nv; ++p) {
-      const long long rp = base + p;
-      int jr[S];
-      Partner<T> pt[S];
-#pragma unroll
-      for (int t = 0; t < S; ++t) { jr[t] = jA[t]; pt[t] = ptA[t]; }
-      if (p + 1 < nv) {
-#pragma unroll
-        for (int t = 0; t < S; ++t) jA[t] = jB[t];
-        load_partners<T, S>(A, jA, ptA);
-      }
-      if (p + 2 < nv) load_row_slots<S>(A, rp + 2, lane, jB);
-      const T j1 = __shfl_sync(FULLM, myj1, p), j2 = __shfl_sync(FULLM, myj2, p);
-      const Query<T> q = shfl_query<T>(myq, p);
-      T c0[S], c1[S];
-      PairOut<T> po[S];
-      T tot;
-      if constexpr (sizeof(T) == 8) {
-        // FP64 form: the sampler's own scan, so lambda*_i is the same number there
-        const double v = channels_of<T, S>(q, jr, pt, c0, c1, po);
-        tot = __shfl_sync(FULLM, warp_incl_scan(v, lane), 31);
-      } else {
-        // mixed form: rates accumulated in FP32 (only the sampler's prefix sums are FP64)
-        channels_of<T, S>(q, jr, pt, c0, c1, po);
-        float vf = 0.0f;
-#pragma unroll
-        for (int t = 0; t < S; ++t) vf += c0[t] + c1[t];
-        tot = warp_sumf(vf);
-      }
-      T la = (T)0, lb = (T)0;
-#pragma unroll
-      for (int t = 0; t < S; ++t) {
-        if (jr[t] < 0) continue;
-        T a, bb;
-        pair_moments<T>(po[t], j1, j2, a, bb);
-        la += a;
-        lb += bb;
-      }
-      T sa, sb;
-      if constexpr (sizeof(T) == 8) { sa = warp_sum(la); sb = warp_sum(lb); }
-      else { sa = warp_sumf(la); sb = warp_sumf(lb); }
-      if (lane == p) { my_tot = tot; my_a = sa; my_b = sb; }
+    const Query<T> q = live_query<T>(fx, s_i, m_i);
+    const T j1 = (T)fj1, j2 = (T)fj2;
+    const int* row = A.nbr + r * A.K;
+    const long long ci = A.chan_out ? (long long)A.perm[r] * A.K : 0;
+    T tot = (T)0, la = (T)0, lb = (T)0;
+    // partners loaded one slot ahead of the pair being evaluated
+    int jn = __ldg(row);
+    Partner<T> pn = load_partner<T>(A, jn);
+    for (int k = 0; k < A.K; ++k) {
+      const Partner<T> pt = pn;
+      if (k + 1 < A.K) { jn = __ldg(row + k + 1); pn = load_partner<T>(A, jn); }
+      const PairOut<T> po = pair_channels<T>(q, pt.s, pt.m, pt.Nq, pt.inv_m);
+      if constexpr (sizeof(T) == 8) { tot = __dadd_rn(tot, po.c0); tot = __dadd_rn(tot, po.c1); }
+      else { tot += po.c0; tot += po.c1; }
+      T a, bb;
+      pair_moments<T>(po, j1, j2, a, bb);
+      la += a;
+      lb += bb;
       if (A.chan_out) {
-        const long long ci = (long long)A.perm[rp] * A.K;
-        const double pf = __shfl_sync(FULLM, mypref, p);
-#pragma unroll
-        for (int t = 0; t < S; ++t) {
-          int k = lane * S + t;
-          if (k < A.K) {
-            A.chan_out[(ci + k) * 2] = pf * (double)c0[t];
-            A.chan_out[(ci + k) * 2 + 1] = pf * (double)c1[t];
-          }
-        }
+        A.chan_out[(ci + k) * 2] = fx.pref * (double)po.c0;
+        A.chan_out[(ci + k) * 2 + 1] = fx.pref * (double)po.c1;
       }
     }
-    if (valid) {
-      double lam = fx.pref * (double)my_tot;
-      A.lam[r] = lam;
-      if (!isfinite(lam)) set_status(&A.st[b], GD_ST_NONFINITE);
-      int fbin = fine_bin(s_i);
-      double M = fx.M;
-      if (sizeof(T) == 4 && b == b_lo) {
-        const float Mf = (float)M, pf = (float)fx.pref;
-        atomicAdd(&shc[fbin], 1u);
-        atomicAdd(&shf[0][fbin], Mf);
-        atomicAdd(&shf[1][fbin], Mf * (pf * (float)my_a));
-        atomicAdd(&shf[2][fbin], Mf * (pf * (float)my_b));
-      } else if (sizeof(T) == 8 && shared_bins) {
-        double va = M * (fx.pref * (double)my_a), vb = M * (fx.pref * (double)my_b);
-        atomicAdd(&sh[0][fbin], 1.0);
-        atomicAdd(&sh[1][fbin], M);
-        atomicAdd(&sh[2][fbin], va);
-        atomicAdd(&sh[3][fbin], vb);
-      } else {
-        double va = M * (fx.pref * (double)my_a), vb = M * (fx.pref * (double)my_b);
-        BinsDev* bn = &A.bins[b];
-        atomicAdd(&bn->cnt[fbin], 1.0);
-        atomicAdd(&bn->sM[fbin], M);
-        atomicAdd(&bn->sA[fbin], va);
-        atomicAdd(&bn->sB[fbin], vb);
-      }
+    const double lam = fx.pref * (double)tot;
+    A.lam[r] = lam;
+    if (!isfinite(lam)) set_status(&A.st[b], GD_ST_NONFINITE);
+    const int fbin = fine_bin(s_i);
+    const double M = fx.M;
+    if (sizeof(T) == 4 && b == b_lo) {
+      const float Mf = (float)M, pf = (float)fx.pref;
+      atomicAdd(&shc[fbin], 1u);
+      atomicAdd(&shf[0][fbin], Mf);
+      atomicAdd(&shf[1][fbin], Mf * (pf * (float)la));
+      atomicAdd(&shf[2][fbin], Mf * (pf * (float)lb));
+    } else if (sizeof(T) == 8 && shared_bins) {
+      atomicAdd(&sh[0][fbin], 1.0);
+      atomicAdd(&sh[1][fbin], M);
+      atomicAdd(&sh[2][fbin], M * (fx.pref * (double)la));
+      atomicAdd(&sh[3][fbin], M * (fx.pref * (double)lb));
+    } else {
+      BinsDev* bn = &A.bins[b];
+      atomicAdd(&bn->cnt[fbin], 1.0);
+      atomicAdd(&bn->sM[fbin], M);
+      atomicAdd(&bn->sA[fbin], M * (fx.pref * (double)la));
+      atomicAdd(&bn->sB[fbin], M * (fx.pref * (double)lb));
     }
   }
   if constexpr (sizeof(T) == 4) {
@@ -938,20 +882,13 @@ static McArgs mc_args(gd_ctx* c) {
 
 template <typename T>
 static void rates_t(gd_ctx* c, McArgs& A) {
-  int S = (c->K + 31) / 32;
   long long blocks_want = (long long)c->num_sms * 8;
   long long range = (A.N + blocks_want - 1) / blocks_want;
   range = ((range + 127) / 128) * 128;
   if (range < 128) range = 128;
   A.range = range;
   int blocks = (int)((A.N + range - 1) / range);
-  switch (S) {
-    case 1: k_rates<T, 1><<<blocks, 128, 0, c->stream>>>(A); break;
-    case 2: k_rates<T, 2><<<blocks, 128, 0, c->stream>>>(A); break;
-    case 3: k_rates<T, 3><<<blocks, 128, 0, c->stream>>>(A); break;
-    case 4: k_rates<T, 4><<<blocks, 128, 0, c->stream>>>(A); break;
-    default: k_rates<T, 8><<<blocks, 128, 0, c->stream>>>(A); break;
-  }
+  k_rates<T, 1><<<blocks, 128, 0, c->stream>>>(A);   // lane = particle: any K
 }
 
 cudaError_t launch_rates(gd_ctx* c, double* chan_out) {
