@@ -126,7 +126,7 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
   std::vector<long long> tiles = tile_table(c->h_off);
   c->n_tiles = (int)tiles.back();
   c->cell_cap = 16 * N + 64LL * n + 1024;
-  long long nst = (c->cell_cap + 2047) / 2048;
+  long long nst = (c->cell_cap + 2048) / 2048 + 1;   // scan tiles of cells [0, cell_cap]
 
   bool ok = true;
   ok &= dalloc(&c->d_off, n + 1) == cudaSuccess;

@@ -127,7 +127,7 @@ __global__ void k_bounds(TileMap tm, const double* __restrict__ x, const double*
 // box in x and y), cell edge from the instance or cell_factor (V_box / n)^(1/3), then
 // the concatenated cell offsets.  If the total exceeds the capacity every edge grows.
 __global__ void k_grid(const InstDev* __restrict__ P, StateDev* st, GridDev* grid, int n_inst,
-                       double cell_factor, int xsplit, long long cell_cap) {
+                       double cell_factor, int xsplit, long long cell_cap, unsigned long long* used) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double grow = 1.0;
   for (int attempt = 0; attempt < 40; ++attempt) {
@@ -182,7 +182,7 @@ __global__ void k_grid(const InstDev* __restrict__ P, StateDev* st, GridDev* gri
       total += cells;
       grid[b] = g;
     }
-    if (total <= cell_cap) break;
+    if (total <= cell_cap) { *used = (unsigned long long)total; break; }
     grow *= 1.1 * cbrt((double)total / (double)cell_cap);
     if (attempt == 39) {
       // capacity exhausted: one cell per instance keeps every index in bounds
@@ -198,6 +198,7 @@ __global__ void k_grid(const InstDev* __restrict__ P, StateDev* st, GridDev* gri
         }
         g.cell_off = b;
       }
+      *used = (unsigned long long)n_inst;
     }
   }
   for (int b = 0; b < n_inst; ++b)
@@ -251,8 +252,13 @@ __device__ __forceinline__ int block_excl_scan(int v, int* sh, int& total) {
 }
 
 // phase 1: per-tile sums
-__global__ void k_scan_reduce(const int* __restrict__ in, long long n, int* __restrict__ sums) {
+// The scan covers the cells the grid uses (k_grid writes their number to *used); tiles
+// past it only report a zero sum.
+__global__ void k_scan_reduce(const int* __restrict__ in, const unsigned long long* __restrict__ used,
+                              int* __restrict__ sums) {
+  const long long n = (long long)*used;
   long long base = (long long)blockIdx.x * kScanTile;
+  if (base > n) { if (threadIdx.x == 0) sums[blockIdx.x] = 0; return; }
   int acc = 0;
   for (int k = threadIdx.x; k < kScanTile; k += blockDim.x) {
     long long i = base + k;
@@ -278,10 +284,12 @@ __global__ void k_scan_sums(int* sums, int nt) {
   }
 }
 
-// phase 3: scan inside each tile plus its offset; out has n + 1 entries
-__global__ void k_scan_final(const int* __restrict__ in, long long n, const int* __restrict__ sums,
-                             int* __restrict__ out) {
+// phase 3: scan inside each tile plus its offset; out[0..n] (out[n] = the total)
+__global__ void k_scan_final(const int* __restrict__ in, const unsigned long long* __restrict__ used,
+                             const int* __restrict__ sums, int* __restrict__ out) {
+  const long long n = (long long)*used;
   long long base = (long long)blockIdx.x * kScanTile;
+  if (base > n) return;
   constexpr int per = kScanTile / 256;
   int v[per];
   int acc = 0;
@@ -297,10 +305,16 @@ __global__ void k_scan_final(const int* __restrict__ in, long long n, const int*
 #pragma unroll
   for (int k = 0; k < per; ++k) {
     long long i = base + threadIdx.x * per + k;
-    if (i < n) out[i] = e;
+    if (i <= n) out[i] = e;
     e += v[k];
   }
-  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 255) out[n] = e;
+}
+
+// Zeroes the counts of the cells the grid uses (and the end entry).
+__global__ void k_zero_counts(int* __restrict__ count, const unsigned long long* __restrict__ used) {
+  const long long n = (long long)*used;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += (long long)gridDim.x * blockDim.x)
+    count[i] = 0;
 }
 
 // ---------------------------------------------------------------- scatter + snapshot
@@ -326,9 +340,9 @@ __global__ void k_scatter(TileMap tm, const InstDev* __restrict__ P, const GridD
     Pos64 q;
     q.x = xi; q.y = yi; q.z = zi; q.j = i;
     pos64[r] = q;
-    double m = grain_mass(p, si);
-    double N = Mi / m;
-    double im = 1.0 / m;
+    const double m = grain_mass(p, si);
+    const double im = 1.0 / m;
+    const double N = Mi * im;
     Snap64 sn;
     sn.s = si; sn.m = m; sn.N = N; sn.inv_m = im;
     snap64[r] = sn;
@@ -337,7 +351,9 @@ __global__ void k_scatter(TileMap tm, const InstDev* __restrict__ P, const GridD
       // FP32 mirror relative to the particle's own cell origin (|coord| <= cell edge),
       // cell coordinates packed in w (11 + 11 + 10 bits); periodic axes use the
       // wrapped coordinate so that the cell and the offset agree.
-      int ix = axis_cell(g, 0, xi), iy = axis_cell(g, 1, yi), iz = axis_cell(g, 2, zi);
+      // the cell from its index (integer work instead of three FP64 floors)
+      const int rem = cell_of[i] - (int)g.cell_off;
+      const int ix = rem % g.dim[0], iy = (rem / g.dim[0]) % g.dim[1], iz = rem / (g.dim[0] * g.dim[1]);
       double xw = xi, yw = yi;
       if (g.box[0] > 0.0) xw = xi - g.box[0] * floor((xi - g.lo[0]) / g.box[0]);
       if (g.box[1] > 0.0) yw = yi - g.box[1] * floor((yi - g.lo[1]) / g.box[1]);
@@ -388,16 +404,18 @@ cudaError_t launch_cells(gd_ctx* c) {
   cudaStream_t st = c->stream;
   time_begin(c, 0);
   k_bounds<<<nt, 256, 0, st>>>(tm, c->x, c->y, c->z, c->d_state);
+  // cells in use (written by k_grid): the zeroing and the scan stop there
+  unsigned long long* used = c->d_counters + 2;
   k_grid<<<1, 32, 0, st>>>(c->d_inst, c->d_state, c->d_grid, c->n_inst, c->cell_factor, c->cell_xsplit,
-                           c->cell_cap);
-  cudaMemsetAsync(c->d_cell_count, 0, sizeof(int) * (c->cell_cap + 1), st);
+                           c->cell_cap, used);
+  const long long ncell = c->cell_cap;
+  k_zero_counts<<<c->num_sms * 8, 256, 0, st>>>(c->d_cell_count, used);
   k_cell_count<<<nt, 256, 0, st>>>(tm, c->d_grid, c->x, c->y, c->z, c->d_cell_count, c->d_cell_of,
                                    c->d_slot, c->cell_cap);
-  long long ncell = c->cell_cap;
-  int nst = (int)((ncell + kScanTile - 1) / kScanTile);
-  k_scan_reduce<<<nst, 256, 0, st>>>(c->d_cell_count, ncell, c->d_scan_tmp);
+  int nst = (int)((ncell + kScanTile) / kScanTile);   // tiles of cells [0, ncell] (end entry included)
+  k_scan_reduce<<<nst, 256, 0, st>>>(c->d_cell_count, used, c->d_scan_tmp);
   k_scan_sums<<<1, 1024, 0, st>>>(c->d_scan_tmp, nst);
-  k_scan_final<<<nst, 256, 0, st>>>(c->d_cell_count, ncell, c->d_scan_tmp, c->d_cell_start);
+  k_scan_final<<<nst, 256, 0, st>>>(c->d_cell_count, used, c->d_scan_tmp, c->d_cell_start);
   if (c->precision == GD_MIXED)
     k_scatter<true><<<nt, 256, 0, st>>>(tm, c->d_inst, c->d_grid, c->x, c->y, c->z, c->s, c->M,
                                         c->d_cell_of, c->d_slot, c->d_cell_start, c->d_perm,
@@ -409,7 +427,7 @@ cudaError_t launch_cells(gd_ctx* c) {
                                          c->d_rank_of, c->d_pos64, c->d_pos32, c->d_snap64,
                                          c->d_snap32, c->d_Mr);
   time_end(c);
-  c->launches += 7;
+  c->launches += 8;
   return cudaGetLastError();
 }
 

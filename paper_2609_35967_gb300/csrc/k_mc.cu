@@ -167,6 +167,24 @@ __device__ __forceinline__ Query<T> live_query(const Fixed<T>& f, double s, doub
   return q;
 }
 
+// Mixed-form query from the FP32 diameter and mass.
+__device__ __forceinline__ Query<float> live_query_f(const Fixed<float>& f, float sf, float mf) {
+  Query<float> q;
+  const float St = f.gst * sf;
+  const float bi = 1.0f / (1.0f + St * St);
+  q.s = sf; q.m = mf; q.inv_m = 1.0f / mf;
+  q.St = St;
+  q.ai = St * bi;
+  q.bi = bi;
+  q.hi = St < 0.5f ? St : 0.5f;
+  q.g = f.gst;
+  q.e2 = f.e2; q.e1 = f.e1; q.zo = f.zo;
+  q.cs = f.cs; q.cB = f.cB; q.Vg2 = f.Vg2; q.tRe = f.tRe;
+  q.vfrag = f.vfrag; q.m0 = f.m0;
+  q.mode = f.mode;
+  return q;
+}
+
 template <typename T>
 __device__ __forceinline__ Query<T> shfl_query(const Query<T>& a, int src) {
   Query<T> q;
@@ -609,6 +627,8 @@ __global__ void __launch_bounds__(64) k_sample(McArgs A) {
       const int bp = __shfl_sync(FULLM, b, p);
       const double s_start = s;
       const double tie_dte = tie_tol<T>() * dte;
+      float sf = (float)s;      // mixed form: the FP32 diameter the pair rates use
+      bool s_stale = false;     // mixed form: s lags m after a sticking or erosion event
       int e = 0, near_ch = 0, near_u = 0;   // per-lane channel ties, warp-uniform ties
       unsigned h = 0u;
       T J = (T)0;
@@ -727,20 +747,34 @@ __global__ void __launch_bounds__(64) k_sample(McArgs A) {
         const T psi_t = __shfl_sync(FULLM, pso, owner);
         const double ncoll = (double)ncoll_t;
         const Snap64 pj = A.snap64[j];
-        double m_new, s_new;
+        double m_new, s_new = s;
         float Jf = 0.0f;   // mixed form: |ln s'/s| of the event from the pair's FP32 psi
         if (outcome == 0) {
-          if constexpr (sizeof(T) == 8) m_new = m + ncoll * pj.m; else m_new = fma(ncoll, pj.m, m);
-          s_new = diameter_of<T>(cube_of<T>(f, m_new));
-          if constexpr (sizeof(T) == 4) Jf = log1pf((float)ncoll_t * (float)psi_t) * (1.0f / 3.0f);
+          if constexpr (sizeof(T) == 8) {
+            m_new = m + ncoll * pj.m;
+            s_new = diameter_of<T>(cube_of<T>(f, m_new));
+          } else {
+            // mixed form: the mass in FP64; the pair rates only need the FP32 diameter, the
+            // FP64-accurate one is formed once when the particle's events are done
+            m_new = fma(ncoll, pj.m, m);
+            sf = cbrtf((float)cube_of<T>(f, m_new));
+            s_stale = true;
+            Jf = log1pf((float)ncoll_t * (float)psi_t) * (1.0f / 3.0f);
+          }
         } else if (outcome == 1 && ch == 0) {
-          if constexpr (sizeof(T) == 8) m_new = m - ncoll * pj.m; else m_new = fma(-ncoll, pj.m, m);
-          s_new = diameter_of<T>(cube_of<T>(f, m_new));
-          if constexpr (sizeof(T) == 4) Jf = fabsf(log1pf(-(float)ncoll_t * (float)psi_t)) * (1.0f / 3.0f);
+          if constexpr (sizeof(T) == 8) {
+            m_new = m - ncoll * pj.m;
+            s_new = diameter_of<T>(cube_of<T>(f, m_new));
+          } else {
+            m_new = fma(-ncoll, pj.m, m);
+            sf = cbrtf((float)cube_of<T>(f, m_new));
+            s_stale = true;
+            Jf = fabsf(log1pf(-(float)ncoll_t * (float)psi_t)) * (1.0f / 3.0f);
+          }
         } else if (outcome == 1) {
           m_new = pj.m;
           s_new = pj.s;
-          if constexpr (sizeof(T) == 4) Jf = fabsf(logf((float)psi_t)) * (1.0f / 3.0f);
+          if constexpr (sizeof(T) == 4) { sf = (float)s_new; s_stale = false; Jf = fabsf(logf((float)psi_t)) * (1.0f / 3.0f); }
         } else {
           U4 w2 = philox(il, iv, (unsigned)e, 1u, k0, k1);
           if constexpr (sizeof(T) == 8) {
@@ -752,9 +786,11 @@ __global__ void __launch_bounds__(64) k_sample(McArgs A) {
           } else {
             // the fragment size is a draw: FP32 is enough; the mass follows it in FP64
             const float U = fmaf((float)(w2.x >> 6), 0x1p26f, (float)(w2.y >> 6) + 0.5f) * 0x1p-52f;
-            const float a = sqrtf((float)f.s_min), bq = sqrtf((float)s);
+            const float a = sqrtf((float)f.s_min), bq = sqrtf(sf);
             const float xr = fmaf(U, bq - a, a);
-            s_new = (double)(xr * xr);
+            sf = xr * xr;
+            s_new = (double)sf;
+            s_stale = false;
             m_new = s_new * s_new * s_new / f.k6;
             Jf = 2.0f * fabsf(logf(xr / bq));
           }
@@ -766,7 +802,8 @@ __global__ void __launch_bounds__(64) k_sample(McArgs A) {
         h = h * 31u + (unsigned)(chosen + 1);
         ++e;
         if (e >= A.max_events) { if (lane == 0) set_status(&A.st[bp], GD_ST_EVENT_CAP); break; }
-        q = live_query<T>(f, s, m);
+        if constexpr (sizeof(T) == 8) q = live_query<T>(f, s, m);
+        else q = live_query_f(f, sf, (float)m);
         v = lane_channels<T, S>(A, q, rp, lane, c0, c1, jr, po);
         if constexpr (sizeof(T) == 8) {
           incl = warp_incl_scan(v, lane);
@@ -775,10 +812,19 @@ __global__ void __launch_bounds__(64) k_sample(McArgs A) {
           inclf = warp_incl_scanf(lane_sumf<S>(c0, c1, jr), lane);
           totf = __shfl_sync(FULLM, inclf, 31);
         }
-        const double lam_now = f.pref * (sizeof(T) == 8 ? tot : (double)totf);
-        if (!(lam_now > 0.0) || !isfinite(lam_now)) {
-          if (lane == 0 && !(lam_now == 0.0)) set_status(&A.st[bp], GD_ST_NONFINITE);
-          break;
+        double lam_now;
+        if constexpr (sizeof(T) == 8) {
+          lam_now = f.pref * tot;
+          if (!(lam_now > 0.0) || !isfinite(lam_now)) {
+            if (lane == 0 && !(lam_now == 0.0)) set_status(&A.st[bp], GD_ST_NONFINITE);
+            break;
+          }
+        } else {
+          if (!(totf > 0.0f) || !isfinite(totf)) {
+            if (lane == 0 && !(totf == 0.0f)) set_status(&A.st[bp], GD_ST_NONFINITE);
+            break;
+          }
+          lam_now = f.pref * (double)totf;
         }
         U4 w = philox(il, iv, (unsigned)e, 0u, k0, k1);
         uw0 = w.z;
@@ -788,6 +834,9 @@ __global__ void __launch_bounds__(64) k_sample(McArgs A) {
         if (fabs((t + dt2) - dte) < tie_dte) near_u++;
         if (t + dt2 > dte) break;
         t = t + dt2;
+      }
+      if constexpr (sizeof(T) == 4) {
+        if (s_stale) s = diameter_of<T>(cube_of<T>(f, m));
       }
       int near_tot = near_ch;
 #pragma unroll
