@@ -169,8 +169,9 @@ def run_gpu(args, rank, world):
 
     def measure(precision, steps, warmup, timing):
         sess = gd.Session(insts, precision=precision, device=str(dev), velocities=push,
-                          flags=gd.GD_FLAG_TIMING if timing else 0, cell_factor=args.cell_factor)
-        cf = args.cell_factor if args.cell_factor > 0 else sess.autotune()
+                          flags=gd.GD_FLAG_TIMING if timing else 0, cell_factor=args.cell_factor,
+                          cell_xsplit=args.cell_xsplit)
+        cf, xs = (args.cell_factor, max(1, args.cell_xsplit)) if args.cell_factor > 0 else sess.autotune()
         st = sess.stream
 
         def step():
@@ -204,6 +205,7 @@ def run_gpu(args, rank, world):
                "kernel_calls": {k: post["kernel_calls"][k] - pre["kernel_calls"][k]
                                 for k in post["kernel_calls"]},
                "events": post["events"] - pre["events"], "status": post["status"], "cell_factor": cf,
+               "cell_xsplit": xs,
                "knn_redo": post["knn_redo"] - pre["knn_redo"]}
         sess.close()
         return res
@@ -217,7 +219,7 @@ def run_gpu(args, rank, world):
     # pinned memory and D2H of the diameters inside the timed region, every step
     cat = W.concat(insts)
     sess = gd.Session(insts, precision=gd.GD_MIXED, device=str(dev), velocities=push,
-                      cell_factor=mixed["cell_factor"])
+                      cell_factor=mixed["cell_factor"], cell_xsplit=mixed["cell_xsplit"])
     host = {k: torch.as_tensor(cat[k]).pin_memory() for k in ("x", "y", "z", "s", "M")}
     s_back = torch.empty(N, dtype=torch.float64).pin_memory()
     st = sess.stream
@@ -297,7 +299,9 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cell-factor", type=float, default=0.0,
-                    help="cell edge factor; 0 = pick it with gd_autotune")
+                    help="cell edge factor; 0 = pick it and the x division with gd_autotune")
+    ap.add_argument("--cell-xsplit", type=int, default=0, choices=(0, 1, 2, 4),
+                    help="x division of the cell edge when --cell-factor is given (0: 1)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -364,7 +368,8 @@ def result_line(r, args, world):
         "config": dict(r["cfg"], n_particles=N, K=K, precision="mixed",
                        l2="no flush: working set > 129 MB L2 (lists alone 4K B/particle)",
                        parallelism=f"{world} independent replicas" if world > 1 else "1 GPU",
-                       cell_factor=r["mixed"]["cell_factor"]),
+                       cell_factor=r["mixed"]["cell_factor"],
+                       cell_xsplit=r["mixed"].get("cell_xsplit", 1)),
         "events_per_step": r["mixed"]["events"] / args.steps,
         "knn_fp64_redo_per_step": r["mixed"].get("knn_redo", 0) / args.steps,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": r["hbm"], "unit": "GB/s",

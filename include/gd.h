@@ -130,7 +130,8 @@ typedef struct {
   int64_t max_events_per_interval;   /* per particle; <= 0: 65536              */
   double cell_factor;          /* cell edge = factor (V_box/N)^(1/3) when the
                                   instance gives none; <= 0: 1                 */
-  int32_t knn_block;           /* threads per block of the neighbour kernel (0: 256) */
+  int32_t cell_xsplit;         /* cell x edge = the y/z edge divided by 1, 2 or 4;
+                                  0: 1                                         */
   int32_t pad1;
 } gd_config;
 
@@ -244,8 +245,9 @@ gd_status gd_run_intervals(gd_ctx* ctx, int32_t n, int32_t push);
  * for the context (instances with an explicit cell_size keep their edge).  Results never depend on the choice: the lists
  * are exact for any cell size.  Synchronises the stream; call it before
  * gd_run_intervals captures its graph.  Leaves the context ready for
- * gd_build_neighbors.  factor_out: HOST or NULL, receives the chosen factor. */
-gd_status gd_autotune(gd_ctx* ctx, double* factor_out);
+ * gd_build_neighbors.  factor_out, xsplit_out: HOST or NULL, receive the chosen
+ * factor and x division. */
+gd_status gd_autotune(gd_ctx* ctx, double* factor_out, int32_t* xsplit_out);
 
 /* Static string for a gd_status code. */
 const char* gd_status_string(gd_status code);

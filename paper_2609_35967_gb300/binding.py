@@ -44,7 +44,7 @@ class Config(C.Structure):
                 ("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p), ("s", C.c_void_p),
                 ("M", C.c_void_p), ("vr", C.c_void_p), ("lth", C.c_void_p), ("lph", C.c_void_p),
                 ("stream", C.c_void_p), ("max_events_per_interval", C.c_int64),
-                ("cell_factor", C.c_double), ("knn_block", C.c_int32), ("pad1", C.c_int32)]
+                ("cell_factor", C.c_double), ("cell_xsplit", C.c_int32), ("pad1", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -73,7 +73,7 @@ SIGNATURES = {
     "gd_stats": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "gd_run_intervals": ([C.c_void_p, C.c_int32, C.c_int32], C.c_int),
     "gd_status_string": ([C.c_int], C.c_char_p),
-    "gd_autotune": ([C.c_void_p, C.c_void_p], C.c_int),
+    "gd_autotune": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "gd_neighbors_fixed": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p,
                             C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
 }
@@ -154,9 +154,10 @@ def gd_run_intervals(ctx, n, push=False):
 
 
 def gd_autotune(ctx):
-    f = C.c_double(0.0)
-    _check("gd_autotune", load().gd_autotune(ctx, C.byref(f)))
-    return f.value
+    """Returns (cell edge factor, x division) chosen by the library."""
+    f, xs = C.c_double(0.0), C.c_int32(0)
+    _check("gd_autotune", load().gd_autotune(ctx, C.byref(f), C.byref(xs)))
+    return f.value, xs.value
 
 
 def gd_status_string(code):
@@ -186,7 +187,7 @@ class Session:
     """Owns torch device copies of a workload and one library context."""
 
     def __init__(self, instances, K=None, precision=GD_FP64, flags=0, device="cuda:0",
-                 stream=None, max_events=0, cell_factor=0.0, knn_block=0, velocities=False):
+                 stream=None, max_events=0, cell_factor=0.0, cell_xsplit=0, velocities=False):
         import numpy as np
         import torch
 
@@ -221,7 +222,7 @@ class Session:
         cfg.stream = self.stream.cuda_stream
         cfg.max_events_per_interval = max_events
         cfg.cell_factor = cell_factor
-        cfg.knn_block = knn_block
+        cfg.cell_xsplit = cell_xsplit
         torch.cuda.synchronize(dev)
         self.cfg = cfg
         self.ctx = gd_create(cfg)

@@ -109,8 +109,8 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
   c->flags = cfg->flags;
   c->N = N;
   c->cell_factor = cfg->cell_factor > 0.0 ? cfg->cell_factor : 1.0;
-  c->knn_block = cfg->knn_block > 0 ? cfg->knn_block : 256;
-  if (c->knn_block % 32 != 0 || c->knn_block > 1024) { delete c; return GD_ERR_ARG; }
+  c->cell_xsplit = cfg->cell_xsplit > 0 ? cfg->cell_xsplit : 1;
+  if (c->cell_xsplit != 1 && c->cell_xsplit != 2 && c->cell_xsplit != 4) { delete c; return GD_ERR_ARG; }
   c->max_events = cfg->max_events_per_interval > 0 ? cfg->max_events_per_interval : 65536;
   c->stream = static_cast<cudaStream_t>(cfg->stream);
   c->x = cfg->x; c->y = cfg->y; c->z = cfg->z; c->s = cfg->s; c->M = cfg->M;
@@ -370,7 +370,7 @@ extern "C" gd_status gd_stats(gd_ctx* c, gd_stats_t* out, gd_instance_stats* ins
   return GD_OK;
 }
 
-extern "C" gd_status gd_autotune(gd_ctx* c, double* factor_out) {
+extern "C" gd_status gd_autotune(gd_ctx* c, double* factor_out, int32_t* xsplit_out) {
   if (!c) return GD_ERR_ARG;
   if (c->phase != 0 && c->phase != 1) return GD_ERR_STATE;
   static const double kFactors[] = {0.5, 0.6, 0.7, 0.8, 1.0, 1.2, 1.4};
@@ -408,6 +408,7 @@ extern "C" gd_status gd_autotune(gd_ctx* c, double* factor_out) {
   c->phase = 0;
   if (c->graph_exec) { cudaGraphExecDestroy(c->graph_exec); c->graph_exec = nullptr; c->graph_push = -1; }
   if (factor_out) *factor_out = best;
+  if (xsplit_out) *xsplit_out = best_split;
   return st;
 }
 

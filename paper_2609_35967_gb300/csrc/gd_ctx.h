@@ -14,7 +14,6 @@ struct gd_ctx {
   double cell_factor = 1.0;
   int cell_xsplit = 1;                  // x cells per cell edge (rows are y-z lines; finer x
                                         // cells trim each row's x range at no extra row cost)
-  int knn_block = 256;
   long long max_events = 65536;
   cudaStream_t stream = nullptr;
   int num_sms = 0;

@@ -1,0 +1,95 @@
+"""GPU parity at the edges: the smallest and largest K (every buffer size of the neighbour
+search), an instance of exactly K particles, exact distance ties on a lattice, duplicate
+positions, a ragged batch, and one particle far from all others."""
+import numpy as np
+import pytest
+
+from paper_2609_35967_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _lists_rates(gd, oracle, insts, precision, check_events=True):
+    sess = gd.Session(insts, precision=precision)
+    nbr, d = sess.build_neighbors(want=True)
+    lam, _ = sess.collision_rates(want=True)
+    ec, eh, nn = sess.sample_collisions(want=True)
+    st = sess.stats(check=False)
+    nbr, d, lam = nbr.cpu().numpy(), d.cpu().numpy(), lam.cpu().numpy()
+    ec, eh, nn = ec.cpu().numpy(), eh.cpu().numpy().view(np.uint32), nn.cpu().numpy()
+    offs = W.concat(insts)["offsets"]
+    status = 0
+    for b, ins in enumerate(insts):
+        lo, hi = offs[b], offs[b + 1]
+        P = oracle.params(ins["params"])
+        q = np.arange(hi - lo)
+        onbr, od = oracle.knn(P, ins["x"], ins["y"], ins["z"], q)
+        assert np.array_equal(nbr[lo:hi] - lo, onbr), b
+        assert np.array_equal(d[lo:hi], od), b
+        r = oracle.rates_subset(P, ins["x"], ins["y"], ins["z"], ins["s"], ins["M"], q, onbr, od)
+        rel = np.abs(lam[lo:hi] / r["lam"] - 1.0)
+        assert rel.max() < (1e-12 if precision == 0 else 1e-4), (b, rel.max())
+        if check_events:
+            o = oracle.sample_subset(P, ins["x"], ins["y"], ins["z"], ins["s"], ins["M"], q, onbr, od,
+                                     st["instances"][b]["dt_exe"], 0)
+            same = (o["ev_count"] == ec[lo:hi]) & (o["ev_hash"] == eh[lo:hi])
+            flagged = (o["near"] > 0) | (nn[lo:hi] > 0)
+            bad = int((~same & ~flagged).sum())
+            assert bad <= (0 if precision == 0 else max(1, 2e-3 * len(q))), (b, bad)
+            # a particle that reaches the per-interval event cap does so on both sides
+            assert st["instances"][b]["status"] == o["status"], (b, st["instances"][b]["status"])
+            status |= o["status"]
+    assert st["status"] == status, st["status"]
+    sess.close()
+
+
+@pytest.mark.parametrize("K", [2, 33, 64, 100, 200])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_K_range(gd, oracle, K, precision):
+    """Every buffer size of the search: K = 2 (one neighbour), 33 / 64 / 100 / 200. At K = 2
+    a mutually nearest pair sticks until it reaches the per-interval event cap; the oracle
+    reaches it too, so the status bit is compared rather than required to be clear."""
+    n = max(600, 3 * K)
+    ins = W.patch_instance(n, K=K, seed=40 + K)
+    _lists_rates(gd, oracle, [ins], precision)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_instance_of_exactly_K(gd, oracle, precision):
+    """n = K: every list holds the whole instance."""
+    ins = W.patch_instance(32, K=32, seed=3)
+    _lists_rates(gd, oracle, [ins], precision)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_lattice_ties(gd, oracle, precision):
+    """A cubic lattice inside a periodic patch: many exactly equal distances, decided by
+    the lower caller index (the order is shuffled so that it is not the rank order)."""
+    ins = W.patch_instance(512, K=20, seed=4)
+    L = ins["params"]["box_x"]
+    g = (np.arange(8) + 0.5) / 8 * L - 0.5 * L
+    X, Y, Z = np.meshgrid(g, g, (np.arange(8) - 3.5) * 0.05 * L, indexing="ij")
+    perm = np.random.default_rng(7).permutation(512)
+    ins["x"], ins["y"], ins["z"] = X.ravel()[perm].copy(), Y.ravel()[perm].copy(), Z.ravel()[perm].copy()
+    _lists_rates(gd, oracle, [ins], precision, check_events=False)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_duplicate_positions(gd, oracle, precision):
+    """Pairs of particles at identical positions (zero distances, ties by index)."""
+    ins = W.patch_instance(400, K=16, seed=5)
+    for k in ("x", "y", "z"):
+        ins[k][200:] = ins[k][:200]
+    _lists_rates(gd, oracle, [ins], precision, check_events=False)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_ragged_batch_and_outlier(gd, oracle, precision):
+    """Instances of K, K+1, 37, 1000 and 5000 particles in one context, and a disk with one
+    particle far above the midplane."""
+    K = 24
+    insts = [W.patch_instance(n, K=K, seed=60 + i) for i, n in enumerate((K, K + 1, 37, 1000, 5000))]
+    disk = W.disk_instance(3000, seed=9, K=K, sizes=("lognormal", 10.0, 1.0))
+    disk["z"][17] = 40.0 * W.AU
+    insts.append(disk)
+    _lists_rates(gd, oracle, insts, precision)

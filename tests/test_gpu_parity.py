@@ -278,8 +278,8 @@ def test_full_size_disk_sampled(gd, oracle, precision):
 def test_autotune_keeps_lists_exact(gd, oracle):
     ins = W.disk_instance(1 << 14, seed=31, K=32, sizes=("lognormal", 10.0, 1.0))
     sess = gd.Session([ins], precision=gd.GD_MIXED)
-    f = sess.autotune()
-    assert 0.35 < f < 1.5
+    f, xs = sess.autotune()
+    assert 0.35 < f < 1.5 and xs in (1, 2, 4)
     nbr, d = sess.build_neighbors(want=True)
     P = oracle.params(ins["params"])
     q = np.arange(0, len(ins["x"]), 97)
