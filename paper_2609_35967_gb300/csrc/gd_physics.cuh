@@ -115,6 +115,17 @@ __device__ __forceinline__ T turb_dv2(T sa, T sb, T vg2, T tre) {
   T s1 = sa > sb ? sa : sb;
   T s2 = sa > sb ? sb : sa;
   const T one = (T)1;
+  // mixed form: the fast FP32 quotient (about 2 ulp; every denominator here is far inside
+  // its range), which costs a fraction of the IEEE division's instruction sequence
+  if constexpr (sizeof(T) == 4) {
+    if (s1 < tre) return vg2 * __fdividef(s1 - s2, s1 + s2) * (__fdividef(s1 * s1, s1 + tre) - __fdividef(s2 * s2, s2 + tre));
+    if (s1 < one) {
+      T e = __fdividef(s2, s1);
+      const T ya = (T)1.6;
+      return vg2 * s1 * ((T)2 * ya - (one + e) + __fdividef((T)2, one + e) * ((T)(1.0 / 2.6) + __fdividef(e * e * e, ya + e)));
+    }
+    return vg2 * (__fdividef(one, one + s1) + __fdividef(one, one + s2));
+  }
   if (s1 < tre) return vg2 * (s1 - s2) / (s1 + s2) * (s1 * s1 / (s1 + tre) - s2 * s2 / (s2 + tre));
   if (s1 < one) {
     T e = s2 / s1;
@@ -141,7 +152,8 @@ __device__ __forceinline__ PairOut<T> pair_channels(const Query<T>& q, T s_j, T 
   const T one = (T)1;
   T psi;
   if constexpr (sizeof(T) == 8) psi = m_j / q.m; else psi = m_j * q.inv_m;
-  T ncoll = (psi <= (T)1e-6) ? floor((T)1e-4 / psi) : one;
+  T ncoll = one;
+  if (psi <= (T)1e-6) { if constexpr (sizeof(T) == 4) ncoll = floorf(__fdividef(1e-4f, psi)); else ncoll = floor((T)1e-4 / psi); }
   T rate;
   int outcome;
   if (q.mode == GD_KERNEL_PHYSICAL) {
@@ -158,12 +170,17 @@ __device__ __forceinline__ PairOut<T> pair_channels(const Query<T>& q, T s_j, T 
     T dvR = q.e2 * (q.ai - aj);
     T dvZ = q.zo * (q.hi - hj);
     T dvP = q.e1 * (q.bi - bj);
-    T vb = sqrt(q.cB * (q.inv_m + inv_m_j));
+    T vb;
+    // mixed form: x rsqrt(x) for the FP32 roots (x > 0 here: masses and c_s are positive)
+    if constexpr (sizeof(T) == 4) { const float xb = q.cB * (q.inv_m + inv_m_j); vb = xb * rsqrtf(xb); }
+    else vb = sqrt(q.cB * (q.inv_m + inv_m_j));
     T dvB = q.cs < vb ? q.cs : vb;
     T t2 = turb_dv2<T>(q.St, St_j, q.Vg2, q.tRe);
     T dvt2;
     if constexpr (sizeof(T) == 8) { T dvt = sqrt(t2); dvt2 = dvt * dvt; } else { dvt2 = t2; }
-    T dv = sqrt(dvR * dvR + dvZ * dvZ + dvP * dvP + dvB * dvB + dvt2);
+    T dv;
+    if constexpr (sizeof(T) == 4) { const float xd = dvR * dvR + dvZ * dvZ + dvP * dvP + dvB * dvB + dvt2; dv = xd * rsqrtf(xd); }
+    else dv = sqrt(dvR * dvR + dvZ * dvZ + dvP * dvP + dvB * dvB + dvt2);
     T ss = q.s + s_j;
     rate = Nq_j * (ss * ss * dv);
     outcome = (dv < q.vfrag) ? 0 : ((psi <= (T)0.1) ? 1 : 2);

@@ -191,7 +191,12 @@ __device__ __forceinline__ double sample_volume(const InstDev& P, double d, doub
   if (P.kernel_mode != GD_KERNEL_PHYSICAL) return 1.0;
   double V = 4.0 * kPi * d * d * d / 3.0;
   if (P.geometry == GD_GEOM_DISK) {
-    double R = sqrt(x * x + y * y);
+    const double R2 = x * x + y * y;
+    const double a = P.R_in + d, bo = P.R_out - d;
+    // clear of both edges by a relative 1e-12, far above the rounding of R2 and of the
+    // squares: no cap applies and R is not needed
+    if (R2 > a * a * (1.0 + 1e-12) && bo > 0.0 && R2 < bo * bo * (1.0 - 1e-12)) return V;
+    double R = sqrt(R2);
     double h = R - P.R_in;
     if (h > 0.0 && h < d) V -= kPi * (d - h) * (d - h) * (2.0 * d + h) / 3.0;
     h = P.R_out - R;
@@ -438,11 +443,14 @@ __device__ bool lane_query(const KnnArgs& A, const Grid32& G, const GridDev& Gd,
     }
     const int need = L - p_lo;
     if (need < 1 || need > nb) return false;
-    // exact FP64 keys of the band, the `need` smallest by (d^2, caller index)
-    double bd[kBand];
+    // exact FP64 keys of the band, the `need` smallest by (d^2, caller index); the keys
+    // are compared as bit patterns (non-negative doubles order like them), on the integer
+    // units rather than the FP64 pipe
+    unsigned long long bd[kBand];
     long long bj[kBand];
-    for (int t = 0; t < nb; ++t) bd[t] = d2_fp64(A.pos64, br[t], Q.x, Q.y, Q.z, bx, by, bj[t]);
-    d2max = 0.0;
+    for (int t = 0; t < nb; ++t)
+      bd[t] = (unsigned long long)__double_as_longlong(d2_fp64(A.pos64, br[t], Q.x, Q.y, Q.z, bx, by, bj[t]));
+    unsigned long long kmax = 0;
     int wr = p_lo;
     for (int t = 0; t < nb; ++t) {
       int rank = 0;
@@ -450,9 +458,10 @@ __device__ bool lane_query(const KnnArgs& A, const Grid32& G, const GridDev& Gd,
         if (bd[u] < bd[t] || (bd[u] == bd[t] && bj[u] < bj[t])) rank++;
       if (rank < need) {
         buf.w(1, wr++) = (uint32_t)br[t];
-        d2max = fmax(d2max, bd[t]);
+        kmax = kmax > bd[t] ? kmax : bd[t];
       }
     }
+    d2max = __longlong_as_double((long long)kmax);
     for (int e = 0; e < L; ++e) buf.w(0, e) = (uint32_t)__ldg(&A.perm[buf.w(1, e)]);
     return true;
   }
