@@ -80,28 +80,29 @@ def algo_bytes(kernel, K, mixed):
 
 
 # DRAM bytes (read + write) of one launch at full size, from a one-pass ncu capture of the
-# bench command (dram__bytes_read.sum + dram__bytes_write.sum), per particle.  A record
-# holds only while the kernel's source file has the recorded content hash.
-KERNEL_SOURCE = {"knn": "k_knn.cu", "rates": "k_mc.cu", "sample": "k_mc.cu", "cells": "k_cells.cu"}
-TRAFFIC = {
-    "knn": {"workload": "disk22", "bytes_per_particle": (638.67e6 + 670.52e6) / 4194304,
-            "sha256": "192cdd3ec158ac3d45689e42440505331ce66dcb9ab1a9e1995c1eceba2f8c2e"},
-    "rates": {"workload": "disk22", "bytes_per_particle": (1107.226e6 + 34.108e6) / 4194304,
-              "sha256": "1b13bc85bd63bf91acc7252eae5382910f30c276d2b1f968244e60402870c45a"},
-    "sample": {"workload": "disk22", "bytes_per_particle": (439.222e6 + 12.090e6) / 4194304,
-               "sha256": "1b13bc85bd63bf91acc7252eae5382910f30c276d2b1f968244e60402870c45a"},
-}
+# bench command (dram__bytes_read.sum + dram__bytes_write.sum), per particle.  The records
+# hold only while every CUDA source of the library has the content it had at the capture
+# (a kernel's code spans its own file and the shared headers).
+TRAFFIC_CSRC_SHA256 = None
+TRAFFIC = {}
+
+
+def csrc_digest():
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2609_35967_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(name.encode())
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()
 
 
 def kernel_traffic(kernel, workload, n):
-    import hashlib
     rec = TRAFFIC.get(kernel)
-    if not rec or rec["workload"] != workload:
+    if not rec or rec["workload"] != workload or csrc_digest() != TRAFFIC_CSRC_SHA256:
         return None
-    path = os.path.join(ROOT, "paper_2609_35967_gb300", "csrc", KERNEL_SOURCE[kernel])
-    with open(path, "rb") as f:
-        if hashlib.sha256(f.read()).hexdigest() != rec["sha256"]:
-            return None
     return rec["bytes_per_particle"] * n
 
 

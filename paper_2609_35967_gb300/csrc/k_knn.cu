@@ -468,6 +468,25 @@ __device__ bool lane_query(const KnnArgs& A, const Grid32& G, const GridDev& Gd,
   return false;
 }
 
+// Ascending sort of 32 keys held in registers (bitonic network, fully unrolled).
+__device__ __forceinline__ void bitonic32(uint32_t (&c)[32]) {
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int l = i ^ j;
+        if (l > i) {
+          const uint32_t a = c[i], b = c[l];
+          const uint32_t lo = a < b ? a : b, hi = a < b ? b : a;
+          if ((i & k) == 0) { c[i] = lo; c[l] = hi; } else { c[i] = hi; c[l] = lo; }
+        }
+      }
+    }
+  }
+}
+
 template <int CAP> struct KnnShape {
   // warps per block: buffers (2 words mixed, 3 FP64) of up to four warps within about
   // 100 KB of shared memory per block
@@ -515,20 +534,31 @@ __global__ void __launch_bounds__(128, CAP <= 40 ? 5 : 4) k_knn(KnnArgs A) {
     const bool ok = lane_query<CAP, kMixed>(A, G, Gd, Q, q, rho, buf, d2max);
     int* row = A.nbr + q * (long long)A.K;
     if (ok) {
-      // members by ascending caller index (word 0), written as ranks (word 1)
-      for (int i = 1; i < L; ++i) {
-        const uint32_t j0 = buf.w(0, i), r0 = buf.w(1, i);
-        int k = i - 1;
-        while (k >= 0 && buf.w(0, k) > j0) {
-          buf.w(0, k + 1) = buf.w(0, k);
-          buf.w(1, k + 1) = buf.w(1, k);
-          --k;
-        }
-        buf.w(0, k + 1) = j0;
-        buf.w(1, k + 1) = r0;
-      }
       row[0] = (int)q;
-      for (int e = 0; e < L; ++e) row[1 + e] = (int)buf.w(1, e);
+      if constexpr (CAP <= 40) {
+        // K <= 32: the members' caller indices sorted in registers, their ranks read back
+        uint32_t cs[32];
+#pragma unroll
+        for (int e = 0; e < 32; ++e) cs[e] = e < L ? buf.w(0, e) : 0xFFFFFFFFu;
+        bitonic32(cs);
+#pragma unroll
+        for (int e = 0; e < 31; ++e)
+          if (e < L) row[1 + e] = __ldg(&A.rank_of[cs[e]]);
+      } else {
+        // members by ascending caller index (word 0), written as ranks (word 1)
+        for (int i = 1; i < L; ++i) {
+          const uint32_t j0 = buf.w(0, i), r0 = buf.w(1, i);
+          int k = i - 1;
+          while (k >= 0 && buf.w(0, k) > j0) {
+            buf.w(0, k + 1) = buf.w(0, k);
+            buf.w(1, k + 1) = buf.w(1, k);
+            --k;
+          }
+          buf.w(0, k + 1) = j0;
+          buf.w(1, k + 1) = r0;
+        }
+        for (int e = 0; e < L; ++e) row[1 + e] = (int)buf.w(1, e);
+      }
       const double d = sqrt(d2max);
       A.dist[q] = d;
       A.V[q] = sample_volume(A.P[b], d, Q.x, Q.y);

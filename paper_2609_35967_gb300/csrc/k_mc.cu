@@ -171,8 +171,8 @@ __device__ __forceinline__ Query<T> live_query(const Fixed<T>& f, double s, doub
 __device__ __forceinline__ Query<float> live_query_f(const Fixed<float>& f, float sf, float mf) {
   Query<float> q;
   const float St = f.gst * sf;
-  const float bi = 1.0f / (1.0f + St * St);
-  q.s = sf; q.m = mf; q.inv_m = 1.0f / mf;
+  const float bi = __fdividef(1.0f, 1.0f + St * St);
+  q.s = sf; q.m = mf; q.inv_m = __fdividef(1.0f, mf);
   q.St = St;
   q.ai = St * bi;
   q.bi = bi;
@@ -354,7 +354,7 @@ __device__ __forceinline__ double waiting_time(uint32_t a, uint32_t b, double la
   } else {
     const float nl = neg_log_u01_f32(a, b);
     const float lf = (float)lam;
-    if (lf > 1e-30f && lf < 1e30f) return (double)(nl / lf);
+    if (lf > 1e-30f && lf < 1e30f) return (double)__fdividef(nl, lf);
     return (double)nl / lam;
   }
 }
