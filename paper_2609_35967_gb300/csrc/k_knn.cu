@@ -267,11 +267,6 @@ struct LaneBuf {
     if (kMixed) return ((unsigned long long)w(0, e) << 32) | w(1, e);
     return ((unsigned long long)w(1, e) << 32) | w(0, e);
   }
-  __device__ __forceinline__ bool greater(int a, int b2) const {   // entry a > entry b2
-    const unsigned long long ka = key(a), kb = key(b2);
-    if (kMixed) return ka > kb;
-    return ka > kb || (ka == kb && w(2, a) > w(2, b2));
-  }
   __device__ __forceinline__ void swap(int a, int b2) const {
 #pragma unroll
     for (int k = 0; k < NW; ++k) { const uint32_t t = w(k, a); w(k, a) = w(k, b2); w(k, b2) = t; }
@@ -281,14 +276,25 @@ struct LaneBuf {
   // index of the largest of them, the L-th smallest.
   __device__ __forceinline__ int select(int n, int L) const {
     for (int m = n; m > L; --m) {
-      int im = 0;
-      for (int e = 1; e < m; ++e)
-        if (greater(e, im)) im = e;
+      const int im = argmax(m);
       if (im != m - 1) swap(im, m - 1);
     }
+    return argmax(L);
+  }
+  // index of the largest of entries [0, m), the running maximum kept in registers
+  __device__ __forceinline__ int argmax(int m) const {
     int im = 0;
-    for (int e = 1; e < L; ++e)
-      if (greater(e, im)) im = e;
+    unsigned long long km = key(0);
+    uint32_t jm = kMixed ? 0u : w(2, 0);
+    for (int e = 1; e < m; ++e) {
+      const unsigned long long ke = key(e);
+      if (kMixed) {
+        if (ke > km) { km = ke; im = e; }
+      } else {
+        const uint32_t je = w(2, e);
+        if (ke > km || (ke == km && je > jm)) { km = ke; jm = je; im = e; }
+      }
+    }
     return im;
   }
 };
@@ -371,7 +377,9 @@ __device__ __forceinline__ int scan_ball(const KnnArgs& A, const Grid32& G, cons
 }
 
 // Search of one query.  On success the buffer holds the members: entries [0, L) with
-// word 0 = caller index and word 1 = rank (unsorted), and d2max is the (K-1)-th d^2.
+// word 0 = caller index and word 1 = rank (unsorted), and d2max is the (K-1)-th d^2.  For
+// K <= 32 (CAP = 40) the output gathers what it needs itself: the mixed form leaves only
+// the ranks (word 1), the FP64 form only the caller indices (word 0).
 // Returns false when no acceptable radius was found (mixed: also when the FP32 keys
 // cannot decide the members).
 template <int CAP, bool kMixed>
@@ -404,10 +412,15 @@ __device__ bool lane_query(const KnnArgs& A, const Grid32& G, const GridDev& Gd,
     if (!kMixed) {
       // exact keys: the L smallest are the members
       d2max = __longlong_as_double((long long)(((unsigned long long)buf.w(1, iL) << 32) | buf.w(0, iL)));
-      for (int e = 0; e < L; ++e) {
-        const uint32_t j = buf.w(2, e);
-        buf.w(0, e) = j;
-        buf.w(1, e) = (uint32_t)__ldg(&A.rank_of[j]);
+      if constexpr (CAP <= 40) {
+        for (int e = 0; e < L; ++e) buf.w(0, e) = buf.w(2, e);
+      } else {
+#pragma unroll 4
+        for (int e = 0; e < L; ++e) {
+          const uint32_t j = buf.w(2, e);
+          buf.w(0, e) = j;
+          buf.w(1, e) = (uint32_t)__ldg(&A.rank_of[j]);
+        }
       }
       return true;
     }
@@ -462,7 +475,10 @@ __device__ bool lane_query(const KnnArgs& A, const Grid32& G, const GridDev& Gd,
       }
     }
     d2max = __longlong_as_double((long long)kmax);
-    for (int e = 0; e < L; ++e) buf.w(0, e) = (uint32_t)__ldg(&A.perm[buf.w(1, e)]);
+    if constexpr (CAP > 40) {
+#pragma unroll 4
+      for (int e = 0; e < L; ++e) buf.w(0, e) = (uint32_t)__ldg(&A.perm[buf.w(1, e)]);
+    }
     return true;
   }
   return false;
@@ -539,7 +555,10 @@ __global__ void __launch_bounds__(128, CAP <= 40 ? 5 : 4) k_knn(KnnArgs A) {
         // K <= 32: the members' caller indices sorted in registers, their ranks read back
         uint32_t cs[32];
 #pragma unroll
-        for (int e = 0; e < 32; ++e) cs[e] = e < L ? buf.w(0, e) : 0xFFFFFFFFu;
+        for (int e = 0; e < 32; ++e) {
+          if (e < L) cs[e] = kMixed ? (uint32_t)__ldg(&A.perm[buf.w(1, e)]) : buf.w(0, e);
+          else cs[e] = 0xFFFFFFFFu;
+        }
         bitonic32(cs);
 #pragma unroll
         for (int e = 0; e < 31; ++e)
