@@ -378,7 +378,7 @@ __device__ __forceinline__ int scan_ball(const KnnArgs& A, const Grid32& G, cons
 
 // Search of one query.  On success the buffer holds the members: entries [0, L) with
 // word 0 = caller index and word 1 = rank (unsorted), and d2max is the (K-1)-th d^2.  For
-// K <= 32 (CAP = 40) the output gathers what it needs itself: the mixed form leaves only
+// K <= 48 (CAP <= 64) the output gathers what it needs itself: the mixed form leaves only
 // the ranks (word 1), the FP64 form only the caller indices (word 0).
 // Returns false when no acceptable radius was found (mixed: also when the FP32 keys
 // cannot decide the members).
@@ -412,7 +412,7 @@ __device__ bool lane_query(const KnnArgs& A, const Grid32& G, const GridDev& Gd,
     if (!kMixed) {
       // exact keys: the L smallest are the members
       d2max = __longlong_as_double((long long)(((unsigned long long)buf.w(1, iL) << 32) | buf.w(0, iL)));
-      if constexpr (CAP <= 40) {
+      if constexpr (CAP <= 64) {
         for (int e = 0; e < L; ++e) buf.w(0, e) = buf.w(2, e);
       } else {
 #pragma unroll 4
@@ -475,7 +475,7 @@ __device__ bool lane_query(const KnnArgs& A, const Grid32& G, const GridDev& Gd,
       }
     }
     d2max = __longlong_as_double((long long)kmax);
-    if constexpr (CAP > 40) {
+    if constexpr (CAP > 64) {
 #pragma unroll 4
       for (int e = 0; e < L; ++e) buf.w(0, e) = (uint32_t)__ldg(&A.perm[buf.w(1, e)]);
     }
@@ -563,6 +563,38 @@ __global__ void __launch_bounds__(128, CAP <= 40 ? 5 : 4) k_knn(KnnArgs A) {
 #pragma unroll
         for (int e = 0; e < 31; ++e)
           if (e < L) row[1 + e] = __ldg(&A.rank_of[cs[e]]);
+      } else if constexpr (CAP == 64) {
+        // K <= 48: each half of the members sorted in registers and put back in word 0,
+        // the halves merged into word 1, the ranks read back
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+          uint32_t cs[32];
+#pragma unroll
+          for (int e = 0; e < 32; ++e) {
+            const int i = 32 * h + e;
+            if (i < L) cs[e] = kMixed ? (uint32_t)__ldg(&A.perm[buf.w(1, i)]) : buf.w(0, i);
+            else cs[e] = 0xFFFFFFFFu;
+          }
+          bitonic32(cs);
+#pragma unroll
+          for (int e = 0; e < 32; ++e) buf.w(0, 32 * h + e) = cs[e];
+        }
+        const int n1 = L < 32 ? L : 32;
+        int i = 0, j = 32;
+        uint32_t a = buf.w(0, 0), bq = buf.w(0, 32);   // past a half's members: 0xFFFFFFFF
+        for (int k = 0; k < L; ++k) {
+          if (a < bq) {
+            buf.w(1, k) = a;
+            ++i;
+            a = i < n1 ? buf.w(0, i) : 0xFFFFFFFFu;
+          } else {
+            buf.w(1, k) = bq;
+            ++j;
+            bq = j < L ? buf.w(0, j) : 0xFFFFFFFFu;
+          }
+        }
+#pragma unroll 4
+        for (int k = 0; k < L; ++k) row[1 + k] = __ldg(&A.rank_of[buf.w(1, k)]);
       } else {
         // members by ascending caller index (word 0), written as ranks (word 1)
         for (int i = 1; i < L; ++i) {

@@ -544,7 +544,7 @@ __global__ void k_interval(const InstDev* __restrict__ P, StateDev* st, BinsDev*
 
 // ---------------------------------------------------------------- sampler
 template <typename T, int S>
-__global__ void __launch_bounds__(64) k_sample(McArgs A) {
+__global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
   const int lane = threadIdx.x & 31;
   // chunks of 32 ranks are taken from a counter: event counts are heavy-tailed, so a
   // static assignment would leave warps idle behind the busiest chunks
