@@ -195,10 +195,12 @@ __device__ __forceinline__ PairOut<T> pair_channels(const Query<T>& q, T s_j, T 
   o.ncoll = ncoll;
   o.outcome = outcome;
   if (outcome == 0) {
-    o.c0 = (ncoll == one) ? rate : rate / ncoll;
+    if constexpr (sizeof(T) == 4) o.c0 = (ncoll == one) ? rate : __fdividef(rate, ncoll);
+    else o.c0 = (ncoll == one) ? rate : rate / ncoll;
     o.c1 = (T)0;
   } else if (outcome == 1) {
-    o.c0 = (ncoll == one) ? (one - psi) * rate : (one - psi) * rate / ncoll;
+    if constexpr (sizeof(T) == 4) o.c0 = (ncoll == one) ? (one - psi) * rate : __fdividef((one - psi) * rate, ncoll);
+    else o.c0 = (ncoll == one) ? (one - psi) * rate : (one - psi) * rate / ncoll;
     o.c1 = psi * rate;
   } else {
     o.c0 = rate;

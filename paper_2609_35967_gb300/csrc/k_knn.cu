@@ -551,29 +551,38 @@ __global__ void __launch_bounds__(128, CAP <= 40 ? 5 : 4) k_knn(KnnArgs A) {
     int* row = A.nbr + q * (long long)A.K;
     if (ok) {
       row[0] = (int)q;
+      // Sort keys: the caller index.  For K <= 48 in the mixed form with caller indices
+      // below 2^26 it carries the member's buffer entry in its low 6 bits, so that the rank
+      // is read back from shared memory instead of gathered from rank_of (for K <= 32 the
+      // unrolled gathers measured slightly faster).
+      const bool packed = kMixed && CAP == 64 && A.N <= (1LL << 26);
+      auto sort_key = [&](int e) -> uint32_t {
+        if (!kMixed) return buf.w(0, e);
+        const uint32_t c = (uint32_t)__ldg(&A.perm[buf.w(1, e)]);
+        return packed ? (c << 6) | (uint32_t)e : c;
+      };
+      auto rank_of_key = [&](uint32_t k) -> int {
+        return packed ? (int)buf.w(1, (int)(k & 63u)) : __ldg(&A.rank_of[k]);
+      };
       if constexpr (CAP <= 40) {
-        // K <= 32: the members' caller indices sorted in registers, their ranks read back
+        // K <= 32: the members' sort keys ordered in registers
         uint32_t cs[32];
 #pragma unroll
-        for (int e = 0; e < 32; ++e) {
-          if (e < L) cs[e] = kMixed ? (uint32_t)__ldg(&A.perm[buf.w(1, e)]) : buf.w(0, e);
-          else cs[e] = 0xFFFFFFFFu;
-        }
+        for (int e = 0; e < 32; ++e) cs[e] = e < L ? sort_key(e) : 0xFFFFFFFFu;
         bitonic32(cs);
 #pragma unroll
         for (int e = 0; e < 31; ++e)
-          if (e < L) row[1 + e] = __ldg(&A.rank_of[cs[e]]);
+          if (e < L) row[1 + e] = rank_of_key(cs[e]);
       } else if constexpr (CAP == 64) {
-        // K <= 48: each half of the members sorted in registers and put back in word 0,
-        // the halves merged into word 1, the ranks read back
+        // K <= 48: each half of the members' sort keys ordered in registers and put back
+        // in word 0 (word 1 keeps the mixed form's ranks), then the halves merged
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) {
           uint32_t cs[32];
 #pragma unroll
           for (int e = 0; e < 32; ++e) {
             const int i = 32 * h + e;
-            if (i < L) cs[e] = kMixed ? (uint32_t)__ldg(&A.perm[buf.w(1, i)]) : buf.w(0, i);
-            else cs[e] = 0xFFFFFFFFu;
+            cs[e] = i < L ? sort_key(i) : 0xFFFFFFFFu;
           }
           bitonic32(cs);
 #pragma unroll
@@ -583,18 +592,17 @@ __global__ void __launch_bounds__(128, CAP <= 40 ? 5 : 4) k_knn(KnnArgs A) {
         int i = 0, j = 32;
         uint32_t a = buf.w(0, 0), bq = buf.w(0, 32);   // past a half's members: 0xFFFFFFFF
         for (int k = 0; k < L; ++k) {
-          if (a < bq) {
-            buf.w(1, k) = a;
-            ++i;
-            a = i < n1 ? buf.w(0, i) : 0xFFFFFFFFu;
-          } else {
-            buf.w(1, k) = bq;
-            ++j;
-            bq = j < L ? buf.w(0, j) : 0xFFFFFFFFu;
-          }
+          const bool first = a < bq;
+          const uint32_t key = first ? a : bq;
+          if (first) { ++i; a = i < n1 ? buf.w(0, i) : 0xFFFFFFFFu; }
+          else { ++j; bq = j < L ? buf.w(0, j) : 0xFFFFFFFFu; }
+          if (packed) row[1 + k] = rank_of_key(key);
+          else buf.w(1, k) = key;
         }
+        if (!packed) {
 #pragma unroll 4
-        for (int k = 0; k < L; ++k) row[1 + k] = __ldg(&A.rank_of[buf.w(1, k)]);
+          for (int k = 0; k < L; ++k) row[1 + k] = __ldg(&A.rank_of[buf.w(1, k)]);
+        }
       } else {
         // members by ascending caller index (word 0), written as ranks (word 1)
         for (int i = 1; i < L; ++i) {

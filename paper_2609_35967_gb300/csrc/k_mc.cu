@@ -627,6 +627,8 @@ __global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
       const int bp = __shfl_sync(FULLM, b, p);
       const double s_start = s;
       const double tie_dte = tie_tol<T>() * dte;
+      // mixed form: FP32 copies of per-particle constants for the per-event FP32 steps
+      const float k6f = (float)f.k6, preff = (float)f.pref;
       float sf = (float)s;      // mixed form: the FP32 diameter the pair rates use
       bool s_stale = false;     // mixed form: s lags m after a sticking or erosion event
       int e = 0, near_ch = 0, near_u = 0;   // per-lane channel ties, warp-uniform ties
@@ -757,7 +759,7 @@ __global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
             // mixed form: the mass in FP64; the pair rates only need the FP32 diameter, the
             // FP64-accurate one is formed once when the particle's events are done
             m_new = fma(ncoll, pj.m, m);
-            sf = cbrtf((float)cube_of<T>(f, m_new));
+            sf = cbrtf((float)m_new * k6f);
             s_stale = true;
             Jf = log1pf((float)ncoll_t * (float)psi_t) * (1.0f / 3.0f);
           }
@@ -767,7 +769,7 @@ __global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
             s_new = diameter_of<T>(cube_of<T>(f, m_new));
           } else {
             m_new = fma(-ncoll, pj.m, m);
-            sf = cbrtf((float)cube_of<T>(f, m_new));
+            sf = cbrtf((float)m_new * k6f);
             s_stale = true;
             Jf = fabsf(log1pf(-(float)ncoll_t * (float)psi_t)) * (1.0f / 3.0f);
           }
@@ -812,7 +814,7 @@ __global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
           inclf = warp_incl_scanf(lane_sumf<S>(c0, c1, jr), lane);
           totf = __shfl_sync(FULLM, inclf, 31);
         }
-        double lam_now;
+        double lam_now = 0.0;   // FP64 form only
         if constexpr (sizeof(T) == 8) {
           lam_now = f.pref * tot;
           if (!(lam_now > 0.0) || !isfinite(lam_now)) {
@@ -824,13 +826,21 @@ __global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
             if (lane == 0 && !(totf == 0.0f)) set_status(&A.st[bp], GD_ST_NONFINITE);
             break;
           }
-          lam_now = f.pref * (double)totf;
         }
         U4 w = philox(il, iv, (unsigned)e, 0u, k0, k1);
         uw0 = w.z;
         uw1 = w.w;
         if constexpr (sizeof(T) == 8) u_s = u01(w.z, w.w);
-        const double dt2 = waiting_time<T>(w.x, w.y, lam_now);
+        double dt2;
+        if constexpr (sizeof(T) == 8) {
+          dt2 = waiting_time<T>(w.x, w.y, lam_now);
+        } else {
+          // lambda* = pref * totf in FP32 when it is in range (the FP32 wait is formed from
+          // it anyway), else in FP64
+          const float lf = preff * totf;
+          const float nl = neg_log_u01_f32(w.x, w.y);
+          dt2 = (lf > 1e-30f && lf < 1e30f) ? (double)__fdividef(nl, lf) : (double)nl / (f.pref * (double)totf);
+        }
         if (fabs((t + dt2) - dte) < tie_dte) near_u++;
         if (t + dt2 > dte) break;
         t = t + dt2;
