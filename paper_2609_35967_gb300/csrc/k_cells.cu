@@ -123,85 +123,144 @@ __global__ void k_bounds(TileMap tm, const double* __restrict__ x, const double*
 }
 
 // ---------------------------------------------------------------- grid choice
-// One thread: per instance, a uniform grid over the data bounds (patch: the periodic
-// box in x and y), cell edge from the instance or cell_factor (V_box / n)^(1/3), then
-// the concatenated cell offsets.  If the total exceeds the capacity every edge grows.
+// Derived fields of a grid from its origin, edges, dimensions and periodic box: the FP32
+// copies and the bound E32 of the FP32 distance error.
+__device__ __forceinline__ void grid_finish(GridDev& g, bool per) {
+  double X = 0.0;
+  for (int a = 0; a < 3; ++a) X = fmax(X, 0.5 * g.cs[a] * g.dim[a]);
+  if (per) X += fmax(g.box[0], g.box[1]);
+  g.X32 = X;
+  double csmax = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    g.cs32[a] = (float)g.cs[a];
+    g.inv32[a] = (float)g.inv[a];
+    csmax = fmax(csmax, g.cs[a]);
+  }
+  // |sqrt(D32) - d| <= 10 u sqrt(D32) + E, u = 2^-24: cell-relative FP32 coordinates
+  // (<= u cell each), the FP32 cell offsets, and the FP64 rounding of the mirror
+  g.E32 = (float)((16.0 * 0x1p-24 * csmax + 32.0 * 0x1p-53 * X) * 1.0001);
+  g.periodic = per ? 1 : 0;
+}
+
+// Uniform grid of one instance over its data bounds (patch: the periodic box in x and
+// y): cell edge from the instance or cell_factor (V_box / n)^(1/3), times grow, the x edge
+// divided by xsplit.  Returns the number of cells (cell_off is left to the caller).
+__device__ long long grid_of(const InstDev& P, const StateDev& S, double cell_factor, int xsplit, double grow,
+                             GridDev& g) {
+  double lo[3], ext[3];
+  for (int a = 0; a < 3; ++a) {
+    const double mn = ord_dbl(S.bmin[a]), mx = ord_dbl(S.bmax[a]);
+    lo[a] = mn;
+    ext[a] = mx - mn;
+  }
+  const bool per = P.geometry == GD_GEOM_PATCH;
+  if (per) { lo[0] = -0.5 * P.box_x; ext[0] = P.box_x; lo[1] = -0.5 * P.box_y; ext[1] = P.box_y; }
+  const double tiny = 1e-300;
+  double vol = 1.0, emax = 0.0;
+  for (int a = 0; a < 3; ++a) emax = fmax(emax, ext[a]);
+  for (int a = 0; a < 3; ++a) vol *= fmax(ext[a], 1e-6 * emax + tiny);
+  double c = P.cell_size > 0.0 ? P.cell_size : cell_factor * cbrt(vol / (double)P.n);
+  c *= grow;
+  long long cells = 1;
+  for (int a = 0; a < 3; ++a) {
+    const bool pa = per && a < 2;
+    const double e = pa ? ext[a] : ext[a] * (1.0 + 1e-9) + 1e-12 * emax + tiny;
+    const double ca = a == 0 ? c / xsplit : c;
+    const double dimd = pa ? floor(e / ca) : ceil(e / ca);
+    const int dim = (int)fmin(fmax(dimd, 1.0), a < 2 ? 2048.0 : 1024.0);
+    g.lo[a] = lo[a];
+    g.cs[a] = e / dim;
+    g.inv[a] = dim / e;
+    g.dim[a] = dim;
+    g.box[a] = pa ? ext[a] : 0.0;
+    g.ctr[a] = lo[a] + 0.5 * e;
+    cells *= dim;
+  }
+  grid_finish(g, per);
+  return cells;
+}
+
+__device__ __forceinline__ long long block_sum64(long long v, long long* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  long long t = 0;
+  for (int k = 0; k < nw; ++k) t += sh[k];
+  __syncthreads();
+  return t;
+}
+
+// One block: every thread takes instances b = tid, tid + blockDim, ...  The grids of all
+// instances for a common growth factor; while the total exceeds the capacity every edge
+// grows.  Then the concatenated cell offsets (a block scan in chunks of blockDim
+// instances) and the bounds reset for the next build.
 __global__ void k_grid(const InstDev* __restrict__ P, StateDev* st, GridDev* grid, int n_inst,
                        double cell_factor, int xsplit, long long cell_cap, unsigned long long* used) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  __shared__ long long sh[33];
+  const int tid = threadIdx.x, nthr = blockDim.x;
   double grow = 1.0;
+  bool fits = false;
   for (int attempt = 0; attempt < 40; ++attempt) {
-    long long total = 0;
-    for (int b = 0; b < n_inst; ++b) {
+    long long mine = 0;
+    for (int b = tid; b < n_inst; b += nthr) {
       GridDev g;
-      double lo[3], ext[3];
-      for (int a = 0; a < 3; ++a) {
-        double mn = ord_dbl(st[b].bmin[a]), mx = ord_dbl(st[b].bmax[a]);
-        lo[a] = mn;
-        ext[a] = mx - mn;
-      }
-      bool per = P[b].geometry == GD_GEOM_PATCH;
-      if (per) { lo[0] = -0.5 * P[b].box_x; ext[0] = P[b].box_x; lo[1] = -0.5 * P[b].box_y; ext[1] = P[b].box_y; }
-      double tiny = 1e-300;
-      double vol = 1.0;
-      double emax = 0.0;
-      for (int a = 0; a < 3; ++a) emax = fmax(emax, ext[a]);
-      for (int a = 0; a < 3; ++a) vol *= fmax(ext[a], 1e-6 * emax + tiny);
-      double c = P[b].cell_size > 0.0 ? P[b].cell_size : cell_factor * cbrt(vol / (double)P[b].n);
-      c *= grow;
-      long long cells = 1;
-      for (int a = 0; a < 3; ++a) {
-        bool pa = per && a < 2;
-        double e = pa ? ext[a] : ext[a] * (1.0 + 1e-9) + 1e-12 * emax + tiny;
-        const double ca = a == 0 ? c / xsplit : c;
-        double dimd = pa ? floor(e / ca) : ceil(e / ca);
-        int dim = (int)fmin(fmax(dimd, 1.0), a < 2 ? 2048.0 : 1024.0);
-        g.lo[a] = lo[a];
-        g.cs[a] = e / dim;
-        g.inv[a] = dim / e;
-        g.dim[a] = dim;
-        g.box[a] = pa ? ext[a] : 0.0;
-        g.ctr[a] = lo[a] + 0.5 * e;
-        cells *= dim;
-      }
-      double X = 0.0;
-      for (int a = 0; a < 3; ++a) X = fmax(X, 0.5 * g.cs[a] * g.dim[a]);
-      if (per) X += fmax(g.box[0], g.box[1]);
-      g.X32 = X;
-      double csmax = 0.0;
-      for (int a = 0; a < 3; ++a) {
-        g.cs32[a] = (float)g.cs[a];
-        g.inv32[a] = (float)g.inv[a];
-        csmax = fmax(csmax, g.cs[a]);
-      }
-      // |sqrt(D32) - d| <= 10 u sqrt(D32) + E, u = 2^-24: cell-relative FP32 coordinates
-      // (<= u cell each), the FP32 cell offsets, and the FP64 rounding of the mirror
-      g.E32 = (float)((16.0 * 0x1p-24 * csmax + 32.0 * 0x1p-53 * X) * 1.0001);
-      g.periodic = per ? 1 : 0;
-      g.cell_off = total;
-      total += cells;
-      grid[b] = g;
+      mine += grid_of(P[b], st[b], cell_factor, xsplit, grow, g);
     }
-    if (total <= cell_cap) { *used = (unsigned long long)total; break; }
+    const long long total = block_sum64(mine, sh);
+    if (total <= cell_cap) { fits = true; break; }
     grow *= 1.1 * cbrt((double)total / (double)cell_cap);
-    if (attempt == 39) {
-      // capacity exhausted: one cell per instance keeps every index in bounds
-      // (the search stays exact, only slower) and the status reports it
-      for (int b = 0; b < n_inst; ++b) {
-        set_status(&st[b], GD_ST_CAPACITY);
-        GridDev& g = grid[b];
-        for (int a = 0; a < 3; ++a) {
-          double e = g.cs[a] * g.dim[a];
-          g.dim[a] = 1;
-          g.cs[a] = e;
-          g.inv[a] = 1.0 / e;
-        }
-        g.cell_off = b;
-      }
-      *used = (unsigned long long)n_inst;
-    }
   }
-  for (int b = 0; b < n_inst; ++b)
+  if (fits) {
+    long long carry = 0;
+    for (int base = 0; base < n_inst; base += nthr) {
+      const int b = base + tid;
+      GridDev g;
+      const long long cells = b < n_inst ? grid_of(P[b], st[b], cell_factor, xsplit, grow, g) : 0;
+      // exclusive scan of the chunk's cell counts
+      long long inc = cells;
+      const int lane = tid & 31, w = tid >> 5, nw = nthr >> 5;
+      for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+      }
+      __syncthreads();
+      if (lane == 31) sh[w] = inc;
+      __syncthreads();
+      long long before = 0, chunk = 0;
+      for (int k = 0; k < nw; ++k) {
+        if (k < w) before += sh[k];
+        chunk += sh[k];
+      }
+      if (b < n_inst) {
+        g.cell_off = carry + before + inc - cells;
+        grid[b] = g;
+      }
+      carry += chunk;
+    }
+    if (tid == 0) *used = (unsigned long long)carry;
+  } else {
+    // capacity exhausted: one cell per instance keeps every index in bounds (the search
+    // stays exact, only slower) and the status reports it
+    for (int b = tid; b < n_inst; b += nthr) {
+      GridDev g;
+      grid_of(P[b], st[b], cell_factor, xsplit, grow, g);
+      for (int a = 0; a < 3; ++a) {
+        const double e = g.cs[a] * g.dim[a];
+        g.dim[a] = 1;
+        g.cs[a] = e;
+        g.inv[a] = 1.0 / e;
+      }
+      grid_finish(g, P[b].geometry == GD_GEOM_PATCH);
+      g.cell_off = b;
+      grid[b] = g;
+      set_status(&st[b], GD_ST_CAPACITY);
+    }
+    if (tid == 0) *used = (unsigned long long)n_inst;
+  }
+  __syncthreads();
+  for (int b = tid; b < n_inst; b += nthr)
     for (int a = 0; a < 3; ++a) { st[b].bmin[a] = ~0ull; st[b].bmax[a] = 0ull; }
 }
 
@@ -406,7 +465,7 @@ cudaError_t launch_cells(gd_ctx* c) {
   k_bounds<<<nt, 256, 0, st>>>(tm, c->x, c->y, c->z, c->d_state);
   // cells in use (written by k_grid): the zeroing and the scan stop there
   unsigned long long* used = c->d_counters + 2;
-  k_grid<<<1, 32, 0, st>>>(c->d_inst, c->d_state, c->d_grid, c->n_inst, c->cell_factor, c->cell_xsplit,
+  k_grid<<<1, 256, 0, st>>>(c->d_inst, c->d_state, c->d_grid, c->n_inst, c->cell_factor, c->cell_xsplit,
                            c->cell_cap, used);
   const long long ncell = c->cell_cap;
   k_zero_counts<<<c->num_sms * 8, 256, 0, st>>>(c->d_cell_count, used);
