@@ -1,0 +1,96 @@
+"""GPU path on the coagulation-test kernels (Appendix A): linear K = (m_i + m_j)/m0 and
+product K = m_i m_j / m0^2, with V_i = 1.
+
+* Parity with the oracle interval by interval on the same inputs: lists bit-exact, rates
+  within 1e-12 (FP64 form) or 1e-4 (mixed form), event sequences identical except flagged
+  near ties, diameters within 1e-12 where the sequences agree (FP64 form).
+* The Smoluchowski solutions through the W1 distance of Appendix B, at the thresholds the
+  oracle's pins use, run through the CUDA path alone at 4096 particles.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2609_35967_gb300 import workloads as W
+
+import coag_exact as X
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("mode", [W.LINEAR, W.PRODUCT])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_coag_interval_parity(gd, oracle, mode, precision):
+    ins = W.coag_instance(2048, K=16, mode=mode, seed=31)
+    sess = gd.Session([ins], precision=precision)
+    P = oracle.params(ins["params"])
+    st = oracle.new_state(P)
+    s_or = ins["s"].copy()
+    import torch
+    for _ in range(4):
+        ref = oracle.interval_step(P, st, ins["x"], ins["y"], ins["z"], s_or, ins["M"],
+                                   want=("nbr", "d", "lam", "ev_count", "ev_hash", "near"))
+        nbr, d = sess.build_neighbors(want=True)
+        lam, _ = sess.collision_rates(want=True)
+        ec, eh, nn = sess.sample_collisions(want=True)
+        assert np.array_equal(nbr.cpu().numpy(), ref["nbr"])
+        assert np.array_equal(d.cpu().numpy(), ref["d"])
+        rel = np.abs(lam.cpu().numpy() / ref["lam"] - 1.0)
+        assert rel.max() < (1e-12 if precision == 0 else 1e-4), rel.max()
+        inst = sess.stats()["instances"][0]
+        if inst["dt_exe"] != st.dt_exe:
+            assert inst["near_dt"] + inst["near_audit"] + st.near_dt + st.near_audit > 0
+        else:
+            ec, eh, nn = ec.cpu().numpy(), eh.cpu().numpy().view(np.uint32), nn.cpu().numpy()
+            same = (ref["ev_count"] == ec) & (ref["ev_hash"] == eh)
+            flagged = (ref["near"] > 0) | (nn > 0)
+            bad = int((~same & ~flagged).sum())
+            n_ev = int((ref["ev_count"] > 0).sum())
+            assert bad <= (0 if precision == 0 else max(2, 1e-3 * n_ev)), (bad, n_ev)
+            s_gpu = sess.t["s"].cpu().numpy()
+            tol = 1e-12 if precision == 0 else 1e-5
+            assert np.abs(s_gpu[same] / s_or[same] - 1.0).max() < tol
+        # both sides continue from the oracle's state
+        sess.t["s"].copy_(torch.as_tensor(s_or, device=sess.device))
+        torch.cuda.synchronize()
+    sess.close()
+
+
+def _run_gpu(gd, mode, seed, t_end, precision, shuffle=False, n=4096, K=16):
+    import torch
+    ins = W.coag_instance(n, K=K, mode=mode, seed=seed)
+    sess = gd.Session([ins], precision=precision)
+    rng = np.random.default_rng(2000 + seed)
+    t = 0.0
+    while t < t_end - 1e-12:
+        if shuffle:
+            p = torch.as_tensor(rng.permutation(n), device=sess.device)
+            for k in ("x", "y", "z"):
+                sess.t[k].copy_(sess.t[k][p].clone())
+            torch.cuda.synchronize()     # the library's stream reads the permuted positions
+        sess.build_neighbors()
+        sess.collision_rates()
+        sess.sample_collisions()
+        t += sess.stats()["instances"][0]["dt_exe"]
+    st = sess.stats()
+    assert st["status"] == 0
+    s = sess.t["s"].cpu().numpy()
+    sess.close()
+    m = math.pi * ins["params"]["rho_s"] * s ** 3 / 6.0
+    return m, ins["M"], t
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_linear_kernel_solution_gpu(gd, precision):
+    m, M, t = _run_gpu(gd, W.LINEAR, 41, 1.0, precision)
+    assert X.w1(m, M, X.cdf_linear(t), -3.0, 3.0) < 0.06
+    assert abs(m.mean() / X.mean_linear(t) - 1.0) < 0.2
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_product_kernel_solution_gpu(gd, precision):
+    m, M, t = _run_gpu(gd, W.PRODUCT, 41, 0.5, precision, shuffle=True)
+    assert np.abs(m - np.rint(m)).max() < 1e-6
+    assert X.w1(m, M, X.cdf_product(t), 0.0, 3.0) < 0.035
+    assert abs(m.mean() / X.mean_product(t) - 1.0) < 0.15
