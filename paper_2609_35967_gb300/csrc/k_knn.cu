@@ -376,10 +376,9 @@ __device__ __forceinline__ int scan_ball(const KnnArgs& A, const Grid32& G, cons
   return n_in;
 }
 
-// Search of one query.  On success the buffer holds the members: entries [0, L) with
-// word 0 = caller index and word 1 = rank (unsorted), and d2max is the (K-1)-th d^2.  For
-// K <= 48 (CAP <= 64) the output gathers what it needs itself: the mixed form leaves only
-// the ranks (word 1), the FP64 form only the caller indices (word 0).
+// Search of one query.  On success the buffer holds the members in entries [0, L)
+// (unsorted) -- the mixed form their ranks (word 1), the FP64 form their caller indices
+// (word 0) -- and d2max is the (K-1)-th d^2.  The output gathers the rest itself.
 // Returns false when no acceptable radius was found (mixed: also when the FP32 keys
 // cannot decide the members).
 template <int CAP, bool kMixed>
@@ -412,16 +411,7 @@ __device__ bool lane_query(const KnnArgs& A, const Grid32& G, const GridDev& Gd,
     if (!kMixed) {
       // exact keys: the L smallest are the members
       d2max = __longlong_as_double((long long)(((unsigned long long)buf.w(1, iL) << 32) | buf.w(0, iL)));
-      if constexpr (CAP <= 64) {
-        for (int e = 0; e < L; ++e) buf.w(0, e) = buf.w(2, e);
-      } else {
-#pragma unroll 4
-        for (int e = 0; e < L; ++e) {
-          const uint32_t j = buf.w(2, e);
-          buf.w(0, e) = j;
-          buf.w(1, e) = (uint32_t)__ldg(&A.rank_of[j]);
-        }
-      }
+      for (int e = 0; e < L; ++e) buf.w(0, e) = buf.w(2, e);
       return true;
     }
     // FP32 bounds with relative margins far above their own rounding
@@ -475,10 +465,6 @@ __device__ bool lane_query(const KnnArgs& A, const Grid32& G, const GridDev& Gd,
       }
     }
     d2max = __longlong_as_double((long long)kmax);
-    if constexpr (CAP > 64) {
-#pragma unroll 4
-      for (int e = 0; e < L; ++e) buf.w(0, e) = (uint32_t)__ldg(&A.perm[buf.w(1, e)]);
-    }
     return true;
   }
   return false;
@@ -551,18 +537,19 @@ __global__ void __launch_bounds__(128, CAP <= 40 ? 5 : 4) k_knn(KnnArgs A) {
     int* row = A.nbr + q * (long long)A.K;
     if (ok) {
       row[0] = (int)q;
-      // Sort keys: the caller index.  For K <= 48 in the mixed form with caller indices
-      // below 2^26 it carries the member's buffer entry in its low 6 bits, so that the rank
-      // is read back from shared memory instead of gathered from rank_of (for K <= 32 the
-      // unrolled gathers measured slightly faster).
-      const bool packed = kMixed && CAP == 64 && A.N <= (1LL << 26);
+      // Sort keys: the caller index.  For K > 32 in the mixed form, when the caller
+      // indices leave room, it carries the member's buffer entry in its low kEB bits, so
+      // that the rank is read back from shared memory instead of gathered from rank_of
+      // (for K <= 32 the unrolled gathers measured slightly faster).
+      constexpr int kEB = CAP <= 64 ? 6 : CAP <= 128 ? 7 : CAP <= 256 ? 8 : 9;
+      const bool packed = kMixed && CAP >= 64 && A.N <= (1LL << (32 - kEB));
       auto sort_key = [&](int e) -> uint32_t {
         if (!kMixed) return buf.w(0, e);
         const uint32_t c = (uint32_t)__ldg(&A.perm[buf.w(1, e)]);
-        return packed ? (c << 6) | (uint32_t)e : c;
+        return packed ? (c << kEB) | (uint32_t)e : c;
       };
       auto rank_of_key = [&](uint32_t k) -> int {
-        return packed ? (int)buf.w(1, (int)(k & 63u)) : __ldg(&A.rank_of[k]);
+        return packed ? (int)buf.w(1, (int)(k & ((1u << kEB) - 1u))) : __ldg(&A.rank_of[k]);
       };
       if constexpr (CAP <= 40) {
         // K <= 32: the members' sort keys ordered in registers
@@ -604,19 +591,50 @@ __global__ void __launch_bounds__(128, CAP <= 40 ? 5 : 4) k_knn(KnnArgs A) {
           for (int k = 0; k < L; ++k) row[1 + k] = __ldg(&A.rank_of[buf.w(1, k)]);
         }
       } else {
-        // members by ascending caller index (word 0), written as ranks (word 1)
-        for (int i = 1; i < L; ++i) {
-          const uint32_t j0 = buf.w(0, i), r0 = buf.w(1, i);
-          int k = i - 1;
-          while (k >= 0 && buf.w(0, k) > j0) {
-            buf.w(0, k + 1) = buf.w(0, k);
-            buf.w(1, k + 1) = buf.w(1, k);
-            --k;
+        // K > 48: runs of 32 members' sort keys ordered in registers and put back in word
+        // 0 (word 1 keeps the mixed form's ranks), then the runs merged
+        constexpr int NR = (CAP + 31) / 32;
+#pragma unroll 1
+        for (int h = 0; h < NR && 32 * h < L; ++h) {
+          uint32_t cs[32];
+#pragma unroll
+          for (int e = 0; e < 32; ++e) {
+            const int i = 32 * h + e;
+            cs[e] = i < L ? sort_key(i) : 0xFFFFFFFFu;
           }
-          buf.w(0, k + 1) = j0;
-          buf.w(1, k + 1) = r0;
+          bitonic32(cs);
+#pragma unroll
+          for (int e = 0; e < 32; ++e)
+            if (32 * h + e < L) buf.w(0, 32 * h + e) = cs[e];
         }
-        for (int e = 0; e < L; ++e) row[1 + e] = (int)buf.w(1, e);
+        uint32_t hd[NR];      // each run's next key (0xFFFFFFFF when it is used up)
+        int ps[NR];
+#pragma unroll
+        for (int c = 0; c < NR; ++c) {
+          ps[c] = 32 * c;
+          hd[c] = ps[c] < L ? buf.w(0, ps[c]) : 0xFFFFFFFFu;
+        }
+        for (int k = 0; k < L; ++k) {
+          uint32_t key = hd[0];
+          int bi = 0;
+#pragma unroll
+          for (int c = 1; c < NR; ++c)
+            if (hd[c] < key) { key = hd[c]; bi = c; }
+#pragma unroll
+          for (int c = 0; c < NR; ++c) {
+            if (c == bi) {
+              ++ps[c];
+              const int end = 32 * c + 32 < L ? 32 * c + 32 : L;
+              hd[c] = ps[c] < end ? buf.w(0, ps[c]) : 0xFFFFFFFFu;
+            }
+          }
+          if (packed) row[1 + k] = rank_of_key(key);
+          else buf.w(1, k) = key;
+        }
+        if (!packed) {
+#pragma unroll 4
+          for (int k = 0; k < L; ++k) row[1 + k] = __ldg(&A.rank_of[buf.w(1, k)]);
+        }
       }
       const double d = sqrt(d2max);
       A.dist[q] = d;
