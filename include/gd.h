@@ -63,6 +63,7 @@ enum {
 };
 
 enum { GD_GEOM_PATCH = 0, GD_GEOM_DISK = 1 };
+enum { GD_DIFF_PHYSICAL = 0, GD_DIFF_RING = 1 };   /* gd_diffuse models */
 enum { GD_KERNEL_PHYSICAL = 0, GD_KERNEL_CONSTANT = 1, GD_KERNEL_LINEAR = 2,
        GD_KERNEL_PRODUCT = 3 };
 
@@ -109,6 +110,14 @@ typedef struct {
   double t0, m0;       /* test-kernel unit time and mass                     */
   double cell_size;    /* cell edge [cm]; <= 0: chosen from the data          */
   uint64_t seed;       /* Philox key of the instance                         */
+  int32_t diff_mode;   /* gd_diffuse: GD_DIFF_PHYSICAL, D = nu/(Sc (1+St^2))
+                          with nu = alpha c_s H_g (Sect. 2.4); GD_DIFF_RING, the
+                          ring test of Sect. 3.2: radial only, D = D0 (R/R_0)^2 */
+  int32_t diff_chi;    /* 1: concentration diffusion (drift along ln rho_g);
+                          0: density diffusion                                */
+  double Sc_R, Sc_Z, Sc_phi;  /* Schmidt numbers of the three directions
+                                 (<= 0: 1)                                    */
+  double D0;           /* ring test: D at R_0 [cm^2 s^-1]                     */
 } gd_instance_params;
 
 typedef struct {
@@ -149,7 +158,7 @@ typedef struct {
   int32_t n_instances;
   double kernel_ms[8];         /* GD_FLAG_TIMING: summed kernel time by step:
                                   0 cells, 1 knn, 2 rates, 3 interval, 4 sample,
-                                  5 push, 6 stats/other, 7 unused              */
+                                  5 push, 6 stats/other, 7 diffusion           */
   int64_t kernel_calls[8];     /* launches timed in each slot                  */
   int64_t knn_redo;            /* mixed form: neighbour searches the FP32 keys
                                   could not decide, redone in FP64 (all builds) */
@@ -227,6 +236,22 @@ gd_status gd_sample_collisions(gd_ctx* ctx, int32_t* ev_count_out, uint32_t* ev_
  * gravity and the angular-momentum forces at the midpoint, drift the second
  * half in mirrored order.  Needs vr, lth, lph in the config. */
 gd_status gd_push_staggered(gd_ctx* ctx, double dt);
+
+/* Sect. 2.4: one Euler-Maruyama dust diffusion step of length dt (dt < 0: each
+ * instance's last dt_exe) for every particle.  The tensor is diagonal in the
+ * local cylindrical basis, D_a = nu/(Sc_a (1 + St^2)); the step is
+ *   dR = sqrt(2 D_R dt) zeta_R + (D_R/R + dD_R/dR + chi D_R dln rho_g/dR) dt,
+ *   dZ = sqrt(2 D_Z dt) zeta_Z + (dD_Z/dZ + chi D_Z dln rho_g/dZ) dt,
+ *   dphi = sqrt(2 D_phi dt) zeta_phi / R,
+ * with the derivatives of the analytic gas disk and zeta from Philox4x32-10
+ * (key = instance seed, counter = (index in the instance, call number,
+ * 0xFFFFFFFE, 0 or 1), Box-Muller).  Global disk: applied in (R, phi, Z); with
+ * velocities in the config their Cartesian vector is kept and (v_r, l_theta,
+ * l_phi) are recomputed at the new position.  Local patch: x += dR,
+ * y += R dphi, z += dZ, wrapped.  GD_DIFF_RING: radial only with D = D0 (R/R_0)^2.
+ * Positions are written in place (x, y, z; vr, lth, lph when given).
+ * Returns GD_ERR_ARG for a non-finite dt.  Asynchronous. */
+gd_status gd_diffuse(gd_ctx* ctx, double dt);
 
 /* Synchronises the stream, reduces per-instance sums and copies counters.
  * out: HOST, required.  inst_out: HOST [n_instances] or NULL.

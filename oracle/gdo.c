@@ -723,3 +723,127 @@ void gdo_push(const gdo_params* P, int32_t drag, double dt, int64_t n, double* x
   for (int64_t i = 0; i < n; ++i)
     gdo_push_one(P, drag, dt, &x[i], &y[i], &z[i], &vr[i], &lth[i], &lph[i], s[i]);
 }
+
+/* ------------------------------------------------------------------ */
+/* Dust diffusion, Sect. 2.4.  The diffusion tensor is diagonal in the local
+ * cylindrical basis, D_a = nu / (Sc_a (1 + St^2)) with nu = alpha c_s H_g at R
+ * (Sect. 2.2), and one Euler-Maruyama step displaces a particle by
+ *   dR   = sqrt(2 D_R dt) zeta_R + (D_R/R + dD_R/dR + chi D_R dln rho_g/dR) dt
+ *   dZ   = sqrt(2 D_Z dt) zeta_Z + (dD_Z/dZ + chi D_Z dln rho_g/dZ) dt
+ *   dphi = sqrt(2 D_phi dt) zeta_phi / R     (the phi derivatives vanish: the
+ *          disk is axisymmetric).
+ * Reading: with the analytic disk of gas_RZ, ln nu = (q + 3/2) ln R + const,
+ * ln St = const + ln s - ln Sigma_g + v with v = (1 - R/r)/h_g^2, h_g^2 ~ R^(q+1),
+ * ln rho_g = ln Sigma_g - ln H_g - v + const, so
+ *   dv/dR = -Z^2/(r^3 h^2) - (q+1) v / R,   dv/dZ = R Z/(r^3 h^2),
+ *   dln D/dR = (q + 3/2)/R - f (-p/R + dv/dR),   dln D/dZ = -f dv/dZ,
+ *   dln rho_g/dR = (p - q/2 - 3/2)/R - dv/dR,    dln rho_g/dZ = -dv/dZ,
+ * with f = 2 St^2/(1 + St^2).
+ * out: D_R, D_Z, D_phi, drift_R, drift_Z (the dt coefficients above), and
+ * dln rho_g/dR, dln rho_g/dZ. */
+void gdo_diff_coeffs(const gdo_params* P, double R, double Z, double s, double out[7]) {
+  gdo_gas g;
+  gas_RZ(P, R, Z, &g);
+  double St = g.gst * s;
+  double nu = P->alpha * g.cs * g.H;
+  double D = nu / (1.0 + St * St);
+  double v = (1.0 - R / g.r) / (g.h * g.h);
+  double r3h2 = g.r * g.r * g.r * g.h * g.h;
+  double dvdR = -Z * Z / r3h2 - (P->q + 1.0) * v / R;
+  double dvdZ = R * Z / r3h2;
+  double f = 2.0 * St * St / (1.0 + St * St);
+  double dlnD_dR = (P->q + 1.5) / R - f * (-P->p / R + dvdR);
+  double dlnD_dZ = -f * dvdZ;
+  double dlnrho_dR = (P->p - 0.5 * P->q - 1.5) / R - dvdR;
+  double dlnrho_dZ = -dvdZ;
+  double chi = (double)P->diff_chi;
+  double DR = D / P->Sc_R, DZ = D / P->Sc_Z, Dp = D / P->Sc_phi;
+  out[0] = DR;
+  out[1] = DZ;
+  out[2] = Dp;
+  out[3] = DR * (1.0 / R + dlnD_dR + chi * dlnrho_dR);
+  out[4] = DZ * (dlnD_dZ + chi * dlnrho_dZ);
+  out[5] = dlnrho_dR;
+  out[6] = dlnrho_dZ;
+}
+
+/* Two standard normals from one Philox draw (Box-Muller on the (0,1) map). */
+static void normals(const gdo_params* P, uint32_t i_loc, int64_t step, uint32_t word, double* n0,
+                    double* n1) {
+  uint32_t ctr[4] = {i_loc, (uint32_t)step, 0xFFFFFFFEu, word};
+  uint32_t key[2] = {(uint32_t)P->seed, (uint32_t)(P->seed >> 32)};
+  uint32_t w[4];
+  gdo_philox4x32_10(ctr, key, w);
+  double u1 = gdo_u01(w[0], w[1]), u2 = gdo_u01(w[2], w[3]);
+  double rad = sqrt(-2.0 * log(u1));
+  *n0 = rad * cos(2.0 * GDO_PI * u2);
+  *n1 = rad * sin(2.0 * GDO_PI * u2);
+}
+
+/* One Euler-Maruyama diffusion step of length dt for particles 0..n-1 of one
+ * instance (Sect. 2.4).  Draws: Philox4x32-10 with the instance key and counter
+ * (i, step, 0xFFFFFFFE, 0) for zeta_R, zeta_Z and (i, step, 0xFFFFFFFE, 1) for
+ * zeta_phi (reading: a counter space of its own, apart from the sampler's and
+ * the initial conditions').
+ * Global disk: the displacement is applied in (R, phi, Z) and the position
+ * rewritten in Cartesian; when velocities are given, their Cartesian vector is
+ * kept and (v_r, l_theta, l_phi) recomputed in the basis at the new position
+ * (reading of "recalculate the stored velocity components").  Local patch:
+ * x += dR, y += R dphi, z += dZ with the periodic wrap.  Ring test (Sect. 3.2):
+ * radial only, D = D0 (R/R_0)^2, drift D/R + dD/dR + chi D p / R, phi and Z
+ * unchanged. */
+void gdo_diffuse(const gdo_params* P, double dt, int64_t step, int64_t n, double* x, double* y,
+                 double* z, double* vr, double* lth, double* lph, const double* s) {
+  for (int64_t i = 0; i < n; ++i) {
+    double zR, zZ, zP, unused;
+    normals(P, (uint32_t)i, step, 0u, &zR, &zZ);
+    normals(P, (uint32_t)i, step, 1u, &zP, &unused);
+    if (P->geometry == GDO_PATCH) {
+      double R = P->r0 + x[i];
+      double c[7];
+      gdo_diff_coeffs(P, R, z[i], s[i], c);
+      double dR = sqrt(2.0 * c[0] * dt) * zR + c[3] * dt;
+      double dZ = sqrt(2.0 * c[1] * dt) * zZ + c[4] * dt;
+      double dy = sqrt(2.0 * c[2] * dt) * zP;
+      double xn = x[i] + dR, yn = y[i] + dy;
+      xn -= P->box_x * floor((xn + 0.5 * P->box_x) / P->box_x);
+      yn -= P->box_y * floor((yn + 0.5 * P->box_y) / P->box_y);
+      x[i] = xn;
+      y[i] = yn;
+      z[i] = z[i] + dZ;
+      continue;
+    }
+    double R = sqrt(x[i] * x[i] + y[i] * y[i]);
+    double ph = atan2(y[i], x[i]);
+    double Z = z[i];
+    double dR, dZ = 0.0, dph = 0.0;
+    if (P->diff_mode == GDO_DIFF_RING) {
+      double D = P->D0 * (R / P->r0) * (R / P->r0);
+      dR = sqrt(2.0 * D * dt) * zR + D / R * (3.0 + (double)P->diff_chi * P->p) * dt;
+    } else {
+      double c[7];
+      gdo_diff_coeffs(P, R, Z, s[i], c);
+      dR = sqrt(2.0 * c[0] * dt) * zR + c[3] * dt;
+      dZ = sqrt(2.0 * c[1] * dt) * zZ + c[4] * dt;
+      dph = sqrt(2.0 * c[2] * dt) * zP / R;
+    }
+    double Rn = R + dR, phn = ph + dph, Zn = Z + dZ;
+    if (Rn < 0.0) { Rn = -Rn; phn += GDO_PI; }
+    double xn = Rn * cos(phn), yn = Rn * sin(phn);
+    if (vr && lth && lph) {
+      /* Cartesian velocity from (v_r, l_theta = r^2 dtheta/dt, l_phi = r^2 sin^2 theta dphi/dt) */
+      double r = sqrt(R * R + Z * Z), st = R / r, ct = Z / r, cp = cos(ph), sp = sin(ph);
+      double vth = lth[i] / r, vph = lph[i] / (r * st);
+      double vx = vr[i] * st * cp + vth * ct * cp - vph * sp;
+      double vy = vr[i] * st * sp + vth * ct * sp + vph * cp;
+      double vz = vr[i] * ct - vth * st;
+      double rn = sqrt(Rn * Rn + Zn * Zn), stn = Rn / rn, ctn = Zn / rn, cpn = cos(phn), spn = sin(phn);
+      vr[i] = vx * stn * cpn + vy * stn * spn + vz * ctn;
+      lth[i] = rn * (vx * ctn * cpn + vy * ctn * spn - vz * stn);
+      lph[i] = rn * stn * (-vx * spn + vy * cpn);
+    }
+    x[i] = xn;
+    y[i] = yn;
+    z[i] = Zn;
+  }
+}

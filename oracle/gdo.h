@@ -26,6 +26,7 @@ extern "C" {
 
 enum { GDO_PATCH = 0, GDO_DISK = 1 };
 enum { GDO_PHYSICAL = 0, GDO_CONSTANT = 1, GDO_LINEAR = 2, GDO_PRODUCT = 3 };
+enum { GDO_DIFF_PHYSICAL = 0, GDO_DIFF_RING = 1 };  /* dust diffusion models (Sect. 2.4, 3.2) */
 enum { GDO_NFINE = 96, GDO_TMIN = -72 };          /* fine controller bins */
 
 /* status bits (sticky) */
@@ -59,6 +60,11 @@ typedef struct {
   double t0, m0;        /* test-kernel unit time [s] and unit mass [g] */
   uint64_t seed;        /* Philox key */
   int64_t max_events;   /* per particle and interval */
+  int32_t diff_mode;    /* GDO_DIFF_PHYSICAL: D = nu/(Sc (1+St^2)) from the gas disk;
+                           GDO_DIFF_RING: the ring test, radial only, D = D0 (R/R_0)^2 */
+  int32_t diff_chi;     /* 1: concentration diffusion (drift along ln rho_g), 0: density */
+  double Sc_R, Sc_Z, Sc_phi;  /* Schmidt numbers of the three directions */
+  double D0;            /* ring test: D at R_0 [cm^2 s^-1] */
 } gdo_params;
 
 typedef struct {
@@ -144,6 +150,9 @@ void   gdo_push_one(const gdo_params* P, int32_t drag, double dt, double* x, dou
                     double* z, double* vr, double* lth, double* lph, double s);
 void   gdo_push(const gdo_params* P, int32_t drag, double dt, int64_t n, double* x, double* y,
                 double* z, double* vr, double* lth, double* lph, const double* s);
+void   gdo_diff_coeffs(const gdo_params* P, double R, double Z, double s, double out[7]);
+void   gdo_diffuse(const gdo_params* P, double dt, int64_t step, int64_t n, double* x, double* y,
+                   double* z, double* vr, double* lth, double* lph, const double* s);
 
 #ifdef __cplusplus
 }

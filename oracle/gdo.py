@@ -48,7 +48,9 @@ class Params(C.Structure):
                 ("v_frag", C.c_double), ("eps", C.c_double), ("dt_coll", C.c_double),
                 ("dt_fn_max", C.c_double), ("R_in", C.c_double), ("R_out", C.c_double),
                 ("box_x", C.c_double), ("box_y", C.c_double), ("t0", C.c_double),
-                ("m0", C.c_double), ("seed", C.c_uint64), ("max_events", C.c_int64)]
+                ("m0", C.c_double), ("seed", C.c_uint64), ("max_events", C.c_int64),
+                ("diff_mode", C.c_int32), ("diff_chi", C.c_int32), ("Sc_R", C.c_double),
+                ("Sc_Z", C.c_double), ("Sc_phi", C.c_double), ("D0", C.c_double)]
 
 
 class State(C.Structure):
@@ -113,6 +115,8 @@ def lib():
                                             dbl, i64, vp, vp, vp, vp, vp, vp]
             L.gdo_push_one.argtypes = [vp, C.c_int32, dbl, vp, vp, vp, vp, vp, vp, dbl]
             L.gdo_push.argtypes = [vp, C.c_int32, dbl, i64, vp, vp, vp, vp, vp, vp, vp]
+            L.gdo_diff_coeffs.argtypes = [vp, dbl, dbl, dbl, vp]
+            L.gdo_diffuse.argtypes = [vp, dbl, i64, i64, vp, vp, vp, vp, vp, vp, vp]
             _lib = L
     return _lib
 
@@ -128,6 +132,11 @@ def params(d: dict) -> Params:
             setattr(P, k, d[k])
     if "max_events" not in d:
         P.max_events = 1 << 20
+    for k in ("Sc_R", "Sc_Z", "Sc_phi"):
+        if k not in d:
+            setattr(P, k, 1.0)
+    if "diff_chi" not in d:
+        P.diff_chi = 1
     return P
 
 
@@ -288,3 +297,20 @@ def push(P: Params, x, y, z, vr, lth, lph, s, dt, drag=True):
     s = np.ascontiguousarray(s, dtype=np.float64)
     lib().gdo_push(C.byref(P), 1 if drag else 0, dt, len(x), _p(x), _p(y), _p(z), _p(vr),
                    _p(lth), _p(lph), _p(s))
+
+
+def diff_coeffs(P: Params, R: float, Z: float, s: float) -> np.ndarray:
+    """D_R, D_Z, D_phi, the R and Z drift coefficients, dln rho_g/dR, dln rho_g/dZ."""
+    out = np.zeros(7)
+    lib().gdo_diff_coeffs(C.byref(P), R, Z, s, _p(out))
+    return out
+
+
+def diffuse(P: Params, dt, step, x, y, z, s, vr=None, lth=None, lph=None):
+    """One Euler-Maruyama diffusion step of every particle of one instance, in place."""
+    for arr in (x, y, z):
+        assert arr.dtype == np.float64 and arr.flags.c_contiguous
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    v = (vr, lth, lph)
+    ptrs = [_p(a) if a is not None else None for a in v]
+    lib().gdo_diffuse(C.byref(P), dt, step, len(x), _p(x), _p(y), _p(z), *ptrs, _p(s))

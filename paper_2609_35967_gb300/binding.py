@@ -24,7 +24,7 @@ GD_FP64, GD_MIXED = 0, 1
 GD_GEOM_PATCH, GD_GEOM_DISK = 0, 1
 GD_FLAG_TIMING, GD_FLAG_NO_AUDIT = 1, 2
 ST_EVENT_CAP, ST_DT_FLOOR, ST_NONFINITE, ST_KNN, ST_CAPACITY, ST_TIMEOUT = 1, 2, 4, 8, 16, 32
-TIMING_SLOTS = ("cells", "knn", "rates", "interval", "sample", "push", "stats", "spare")
+TIMING_SLOTS = ("cells", "knn", "rates", "interval", "sample", "push", "stats", "diffuse")
 
 
 class InstanceParams(C.Structure):
@@ -35,7 +35,9 @@ class InstanceParams(C.Structure):
                 ("v_frag", C.c_double), ("eps", C.c_double), ("dt_coll", C.c_double),
                 ("dt_fn_max", C.c_double), ("R_in", C.c_double), ("R_out", C.c_double),
                 ("box_x", C.c_double), ("box_y", C.c_double), ("t0", C.c_double),
-                ("m0", C.c_double), ("cell_size", C.c_double), ("seed", C.c_uint64)]
+                ("m0", C.c_double), ("cell_size", C.c_double), ("seed", C.c_uint64),
+                ("diff_mode", C.c_int32), ("diff_chi", C.c_int32), ("Sc_R", C.c_double),
+                ("Sc_Z", C.c_double), ("Sc_phi", C.c_double), ("D0", C.c_double)]
 
 
 class Config(C.Structure):
@@ -70,6 +72,7 @@ SIGNATURES = {
     "gd_collision_rates": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "gd_sample_collisions": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "gd_push_staggered": ([C.c_void_p, C.c_double], C.c_int),
+    "gd_diffuse": ([C.c_void_p, C.c_double], C.c_int),
     "gd_stats": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "gd_run_intervals": ([C.c_void_p, C.c_int32, C.c_int32], C.c_int),
     "gd_status_string": ([C.c_int], C.c_char_p),
@@ -140,6 +143,10 @@ def gd_sample_collisions(ctx, ev_count_out=0, ev_hash_out=0, near_out=0):
 
 def gd_push_staggered(ctx, dt):
     return _check("gd_push_staggered", load().gd_push_staggered(ctx, float(dt)))
+
+
+def gd_diffuse(ctx, dt):
+    return _check("gd_diffuse", load().gd_diffuse(ctx, float(dt)))
 
 
 def gd_stats(ctx, n_instances):
@@ -274,6 +281,9 @@ class Session:
 
     def push_staggered(self, dt=-1.0):
         gd_push_staggered(self.ctx, dt)
+
+    def diffuse(self, dt=-1.0):
+        gd_diffuse(self.ctx, dt)
 
     def run_intervals(self, n, push=False):
         gd_run_intervals(self.ctx, n, push)

@@ -96,6 +96,9 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
       return GD_ERR_ARG;
     if (p.geometry == GD_GEOM_PATCH && (!finite_pos(p.box_x) || !finite_pos(p.box_y))) return GD_ERR_ARG;
     if (p.geometry == GD_GEOM_DISK && !(p.R_out > p.R_in)) return GD_ERR_ARG;
+    if (p.diff_mode != GD_DIFF_PHYSICAL && p.diff_mode != GD_DIFF_RING) return GD_ERR_ARG;
+    if (p.diff_chi != 0 && p.diff_chi != 1) return GD_ERR_ARG;
+    if (p.diff_mode == GD_DIFF_RING && !(p.D0 >= 0.0 && std::isfinite(p.D0) && p.r0 > 0.0)) return GD_ERR_ARG;
     if (p.kernel_mode != GD_KERNEL_PHYSICAL && (!finite_pos(p.t0) || !finite_pos(p.m0))) return GD_ERR_ARG;
   }
   const long long N = cfg->offsets[n];
@@ -182,6 +185,12 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
     d.f_r0 = (float)p.r0; d.f_GM = (float)d.GM; d.f_T0 = (float)p.T0; d.f_q = (float)p.q;
     d.f_p = (float)p.p; d.f_sigma0 = (float)p.sigma0; d.f_alpha = (float)p.alpha;
     d.f_rho_s = (float)p.rho_s; d.f_vfrag = (float)p.v_frag; d.f_m0 = (float)p.m0;
+    d.diff_mode = p.diff_mode;
+    d.diff_chi = p.diff_chi;
+    d.Sc_R = p.Sc_R > 0.0 ? p.Sc_R : 1.0;
+    d.Sc_Z = p.Sc_Z > 0.0 ? p.Sc_Z : 1.0;
+    d.Sc_phi = p.Sc_phi > 0.0 ? p.Sc_phi : 1.0;
+    d.D0 = p.D0;
     d.off = c->h_off[b];
     d.n = c->h_off[b + 1] - c->h_off[b];
     if (p.geometry == GD_GEOM_DISK) c->any_disk = true;
@@ -272,6 +281,12 @@ extern "C" gd_status gd_push_staggered(gd_ctx* c, double dt) {
   if (!c->vr || !c->lth || !c->lph) return GD_ERR_ARG;
   if (!std::isfinite(dt)) return GD_ERR_ARG;
   return cuda_err(launch_push(c, dt));
+}
+
+extern "C" gd_status gd_diffuse(gd_ctx* c, double dt) {
+  if (!c) return GD_ERR_ARG;
+  if (!std::isfinite(dt)) return GD_ERR_ARG;
+  return cuda_err(launch_diffuse(c, dt));
 }
 
 extern "C" gd_status gd_run_intervals(gd_ctx* c, int32_t n, int32_t push) {

@@ -38,6 +38,9 @@ struct InstDev {
   double k6;          // 6 / (pi rho_s)
   // FP32 copies of the parameters the mixed form's per-particle gas disk uses
   float f_r0, f_GM, f_T0, f_q, f_p, f_sigma0, f_alpha, f_rho_s, f_vfrag, f_m0;
+  // dust diffusion (Sect. 2.4)
+  int diff_mode, diff_chi;
+  double Sc_R, Sc_Z, Sc_phi, D0;
 };
 
 // Uniform cell grid of one instance, rebuilt every interval from the data bounds.

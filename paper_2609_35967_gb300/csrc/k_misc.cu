@@ -1,5 +1,6 @@
-// k_misc.cu -- staggered semi-analytic push (Sect. 2.3.3), per-instance reductions for
-// gd_stats, and conversion of rank-space results to the caller's order.
+// k_misc.cu -- staggered semi-analytic push (Sect. 2.3.3), dust diffusion (Sect. 2.4),
+// per-instance reductions for gd_stats, and conversion of rank-space results to the
+// caller's order.
 #include "gd_ctx.h"
 #include "gd_physics.cuh"
 
@@ -53,6 +54,110 @@ __global__ void k_push(long long N, int n_inst, const long long* __restrict__ of
   lph[i] = LP;
 }
 
+// ---------------------------------------------------------------- dust diffusion
+// Sect. 2.4.  Coefficients at (R, Z) for a grain of diameter s: D_a = nu/(Sc_a (1+St^2)),
+// nu = alpha c_s H_g at R, and the dt coefficients of the R and Z steps.  With
+// v = (1 - R/r)/h^2 (the gas disk's vertical exponent; h^2 ~ R^(q+1)):
+//   dv/dR = -Z^2/(r^3 h^2) - (q+1) v/R,  dv/dZ = R Z/(r^3 h^2),
+//   dln D/dR = (q + 3/2)/R - f (dv/dR - p/R),  dln D/dZ = -f dv/dZ,  f = 2 St^2/(1+St^2),
+//   dln rho_g/dR = (p - q/2 - 3/2)/R - dv/dR,  dln rho_g/dZ = -dv/dZ.
+struct DiffCoef {
+  double DR, DZ, Dp, aR, aZ;
+};
+
+__device__ __forceinline__ DiffCoef diff_coef(const InstDev& p, double R, double Z, double s) {
+  const Gas g = gas_RZ(p, R, Z);
+  const double St = g.gst * s;
+  const double D = p.alpha * g.cs * g.H / (1.0 + St * St);
+  const double v = (1.0 - R / g.r) / (g.h * g.h);
+  const double r3h2 = g.r * g.r * g.r * (g.h * g.h);
+  const double dvdR = -Z * Z / r3h2 - (p.q + 1.0) * v / R;
+  const double dvdZ = R * Z / r3h2;
+  const double f = 2.0 * St * St / (1.0 + St * St);
+  const double chi = (double)p.diff_chi;
+  DiffCoef c;
+  c.DR = D / p.Sc_R;
+  c.DZ = D / p.Sc_Z;
+  c.Dp = D / p.Sc_phi;
+  c.aR = c.DR * (1.0 / R + ((p.q + 1.5) / R - f * (dvdR - p.p / R)) + chi * ((p.p - 0.5 * p.q - 1.5) / R - dvdR));
+  c.aZ = c.DZ * (-f * dvdZ - chi * dvdZ);
+  return c;
+}
+
+// Two standard normals from one Philox draw (Box-Muller on the (0,1) map).
+__device__ __forceinline__ void normal_pair(const InstDev& p, uint32_t i_loc, uint32_t step, uint32_t word,
+                                            double& n0, double& n1) {
+  const U4 w = philox(i_loc, step, 0xFFFFFFFEu, word, p.key0, p.key1);
+  const double u1 = u01(w.x, w.y), u2 = u01(w.z, w.w);
+  const double rad = sqrt(-2.0 * log(u1));
+  double sn, cn;
+  sincospi(2.0 * u2, &sn, &cn);
+  n0 = rad * cn;
+  n1 = rad * sn;
+}
+
+// One Euler-Maruyama step per particle (caller order), every instance.
+__global__ void k_diffuse(long long N, int n_inst, const long long* __restrict__ off,
+                          const InstDev* __restrict__ P, const StateDev* __restrict__ st, double dt_in,
+                          long long step, double* x, double* y, double* z, double* vr, double* lth,
+                          double* lph, const double* __restrict__ s) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int b = inst_of(off, n_inst, i);
+  const InstDev& p = P[b];
+  const double dt = dt_in < 0.0 ? st[b].dt_exe : dt_in;
+  const uint32_t il = (uint32_t)(i - p.off);
+  double zR, zZ, zP, unused;
+  normal_pair(p, il, (uint32_t)step, 0u, zR, zZ);
+  normal_pair(p, il, (uint32_t)step, 1u, zP, unused);
+  if (p.geometry == GD_GEOM_PATCH) {
+    const DiffCoef c = diff_coef(p, p.r0 + x[i], z[i], s[i]);
+    double xn = x[i] + (sqrt(2.0 * c.DR * dt) * zR + c.aR * dt);
+    double yn = y[i] + sqrt(2.0 * c.Dp * dt) * zP;
+    xn -= p.box_x * floor((xn + 0.5 * p.box_x) / p.box_x);
+    yn -= p.box_y * floor((yn + 0.5 * p.box_y) / p.box_y);
+    x[i] = xn;
+    y[i] = yn;
+    z[i] = z[i] + (sqrt(2.0 * c.DZ * dt) * zZ + c.aZ * dt);
+    return;
+  }
+  const double X = x[i], Y = y[i], Z = z[i];
+  const double R = sqrt(X * X + Y * Y);
+  const double ph = atan2(Y, X);
+  double dR, dZ = 0.0, dph = 0.0;
+  if (p.diff_mode == GD_DIFF_RING) {
+    const double D = p.D0 * (R / p.r0) * (R / p.r0);
+    dR = sqrt(2.0 * D * dt) * zR + D / R * (3.0 + (double)p.diff_chi * p.p) * dt;
+  } else {
+    const DiffCoef c = diff_coef(p, R, Z, s[i]);
+    dR = sqrt(2.0 * c.DR * dt) * zR + c.aR * dt;
+    dZ = sqrt(2.0 * c.DZ * dt) * zZ + c.aZ * dt;
+    dph = sqrt(2.0 * c.Dp * dt) * zP / R;
+  }
+  double Rn = R + dR, phn = ph + dph;
+  const double Zn = Z + dZ;
+  if (Rn < 0.0) { Rn = -Rn; phn += kPi; }
+  double spn, cpn;
+  sincos(phn, &spn, &cpn);
+  if (vr && lth && lph) {
+    // keep the Cartesian velocity; its spherical components in the new basis
+    const double r = sqrt(R * R + Z * Z), sth = R / r, cth = Z / r;
+    double sp, cp;
+    sincos(ph, &sp, &cp);
+    const double vth = lth[i] / r, vph = lph[i] / (r * sth);
+    const double vx = vr[i] * sth * cp + vth * cth * cp - vph * sp;
+    const double vy = vr[i] * sth * sp + vth * cth * sp + vph * cp;
+    const double vz = vr[i] * cth - vth * sth;
+    const double rn = sqrt(Rn * Rn + Zn * Zn), sthn = Rn / rn, cthn = Zn / rn;
+    vr[i] = vx * sthn * cpn + vy * sthn * spn + vz * cthn;
+    lth[i] = rn * (vx * cthn * cpn + vy * cthn * spn - vz * sthn);
+    lph[i] = rn * sthn * (-vx * spn + vy * cpn);
+  }
+  x[i] = Rn * cpn;
+  y[i] = Rn * spn;
+  z[i] = Zn;
+}
+
 __global__ void k_out_knn(long long N, int K, const int* __restrict__ rank_of, const int* __restrict__ perm,
                           const int* __restrict__ nbr, const double* __restrict__ dist, int* nbr_out,
                           double* d_out) {
@@ -78,6 +183,17 @@ cudaError_t launch_push(gd_ctx* c, double dt) {
                                          c->z, c->vr, c->lth, c->lph, c->s);
   time_end(c);
   c->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diffuse(gd_ctx* c, double dt) {
+  time_begin(c, 7);
+  const int blocks = (int)((c->N + 255) / 256);
+  k_diffuse<<<blocks, 256, 0, c->stream>>>(c->N, c->n_inst, c->d_off, c->d_inst, c->d_state, dt, c->diff_step,
+                                           c->x, c->y, c->z, c->vr, c->lth, c->lph, c->s);
+  time_end(c);
+  c->launches += 1;
+  c->diff_step += 1;
   return cudaGetLastError();
 }
 

@@ -18,7 +18,9 @@ Units: cgs.  Diameters s = 2a.  Recipes (stated again in the design doc):
   phi uniform, z ~ N(0, H_d^2) with the settling equilibrium
   H_d = H_g sqrt(alpha/(alpha + St));
 * coagulation test (Appendix A): uniform positions in a periodic unit box,
-  unit masses (constant / product kernel) or Gamma(2) masses (linear kernel).
+  unit masses (constant / product kernel) or Gamma(2) masses (linear kernel);
+* diffusion ring test (Sect. 3.2): code units R_0 = 1, D_0 = 1e-4, p = -1,
+  ln(R/R_0) ~ N(0, 0.05^2), phi uniform, z = 0.
 """
 from __future__ import annotations
 
@@ -36,6 +38,7 @@ _MU = 2.34
 
 PATCH, DISK = 0, 1
 PHYSICAL, CONSTANT, LINEAR, PRODUCT = 0, 1, 2, 3
+DIFF_PHYSICAL, DIFF_RING = 0, 1
 S_MIN = 2e-5          # minimum fragment diameter: a = 0.1 um
 
 
@@ -50,7 +53,8 @@ def _base_params(**kw):
              p=-1.0, q=-0.5, T0=50.0, alpha=1e-3, M_star=MSUN, rho_s=1.67, s_min=S_MIN,
              v_frag=100.0, eps=0.08, dt_coll=0.0, dt_fn_max=0.0, R_in=0.0, R_out=0.0,
              box_x=0.0, box_y=0.0, t0=1.0, m0=1.0, seed=1, max_events=1 << 16,
-             cell_size=0.0)
+             cell_size=0.0, diff_mode=DIFF_PHYSICAL, diff_chi=1, Sc_R=1.0, Sc_Z=1.0, Sc_phi=1.0,
+             D0=0.0)
     d.update(kw)
     return d
 
@@ -140,6 +144,24 @@ def coag_instance(n, K=32, mode=CONSTANT, seed=1, eps=0.08, dt_coll=1.0, **extra
                      dt_fn_max=dt_coll, box_x=1.0, box_y=1.0, t0=1.0, m0=1.0, seed=seed,
                      **extra)
     return dict(params=P, x=x, y=y, z=z, s=s, M=M)
+
+
+def ring_params(chi=1, seed=1):
+    """Parameters of the diffusion ring test (Sect. 3.2), code units."""
+    return _base_params(geometry=DISK, r0=1.0, p=-1.0, diff_mode=DIFF_RING, diff_chi=chi, D0=1e-4,
+                        R_in=0.0, R_out=1e3, seed=seed, dt_coll=1.0, dt_fn_max=1.0)
+
+
+def ring_instance(n, chi=1, seed=1, K=16):
+    """Diffusion ring test: ln(R/R_0) ~ N(0, 0.05^2), phi uniform, z = 0."""
+    rng = np.random.default_rng(seed)
+    lnR = rng.normal(0.0, 0.05, n)
+    ph = rng.uniform(0.0, 2 * math.pi, n)
+    R = np.exp(lnR)
+    P = ring_params(chi=chi, seed=seed)
+    P["K"] = K
+    return dict(params=P, x=R * np.cos(ph), y=R * np.sin(ph), z=np.zeros(n), s=np.full(n, 1e-4),
+                M=np.full(n, 1.0 / n))
 
 
 # ---------------------------------------------------------------- configurations
