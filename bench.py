@@ -290,6 +290,43 @@ def cpu_oracle_rate(insts, budget_s=12.0, max_q=4096):
     return done / el, done, el, n
 
 
+def diffusion_line(args):
+    """The dust diffusion step (Sect. 2.4) alone: gd_diffuse on the 2^22 disk with
+    velocities, CUDA events on the library stream over the timed steps."""
+    import torch
+    from paper_2609_35967_gb300 import binding as gd
+    from paper_2609_35967_gb300 import workloads as W
+    ins = W.disk_instance(1 << 22, seed=1, K=32, sizes=("lognormal", 10.0, 1.0), velocities=True)
+    N = len(ins["x"])
+    sess = gd.Session([ins], precision=gd.GD_MIXED, velocities=True, flags=gd.GD_FLAG_TIMING)
+    dt = 0.05 * ins["params"]["dt_coll"]
+    for _ in range(args.warmup):
+        sess.diffuse(dt)
+    pre = sess.stats()["kernel_ms"]["diffuse"]
+    st = sess.stream
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        sess.diffuse(dt)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    kms = (sess.stats()["kernel_ms"]["diffuse"] - pre) / args.steps
+    sess.close()
+    hbm, peak_kind = peaks()
+    bytes_pp = 7 * 8 + 6 * 8     # reads x y z s vr lth lph, writes x y z vr lth lph (FP64)
+    ach = bytes_pp * N / (kms * 1e-3) / 1e9
+    return {"metric": "particle diffusion steps/s (Sect. 2.4 Euler-Maruyama, with velocities)",
+            "value": N * args.steps / (ms * 1e-3), "unit": "particle-steps/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "global disk 5-100 au, 2^22 particles with velocities, dt = dt_coll/20",
+                       "n_particles": N},
+            "roofline": {"bound": "hbm", "kernel": "diffuse", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                         "frac": ach / hbm, "peak_kind": peak_kind, "algo_bytes_per_particle": bytes_pp}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -303,6 +340,8 @@ def main():
                     help="cell edge factor; 0 = pick it and the x division with gd_autotune")
     ap.add_argument("--cell-xsplit", type=int, default=0, choices=(0, 1, 2, 4),
                     help="x division of the cell edge when --cell-factor is given (0: 1)")
+    ap.add_argument("--diffusion", action="store_true",
+                    help="time the dust diffusion step alone (one JSON line, 1 GPU)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -332,6 +371,11 @@ def main():
             "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return
+
+    if args.diffusion:
+        if rank == 0:
+            print(json.dumps(diffusion_line(args)))
         return
 
     if world > 1:

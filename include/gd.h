@@ -253,6 +253,30 @@ gd_status gd_push_staggered(gd_ctx* ctx, double dt);
  * Returns GD_ERR_ARG for a non-finite dt.  Asynchronous. */
 gd_status gd_diffuse(gd_ctx* ctx, double dt);
 
+/* Sect. 2.5.3 with a bounded collision step: every instance runs frozen-neighbour
+ * intervals (build or reuse the lists, rates, interval choice, sampling, audit)
+ * over a collision step of length tau (in place of dt_coll), the intervals
+ * halving tau exactly, and idles once its step is used up; the call returns
+ * when every instance has finished.  Positions are frozen during the step, so
+ * the neighbour lists are built once: by the first interval, or not at all
+ * when reuse_lists != 0 and the particles have not moved since the last build
+ * (the caller's promise).  Later intervals refresh only the partner snapshot.
+ * Synchronises the stream after every interval (the number of intervals is
+ * data dependent).  max_intervals bounds the loop: GD_ERR_TIMEOUT when it is
+ * reached first.  n_intervals_out: HOST or NULL.  Afterwards the instances are
+ * back to collision steps of dt_coll.  GD_ERR_ARG for tau <= 0 or non-finite,
+ * GD_ERR_STATE between a build and its sampling. */
+gd_status gd_collide(gd_ctx* ctx, double tau, int32_t reuse_lists, int32_t max_intervals,
+                     int32_t* n_intervals_out);
+
+/* Sect. 2.6: one numerical timestep of length dt in the symmetric split
+ * C(dt/2) D(dt/2) T(dt) D(dt/2) C(dt/2): collisions (gd_collide), diffusion
+ * (gd_diffuse), transport (gd_push_staggered, when the config has velocities;
+ * patch instances do not move).  The first C reuses the lists of the previous
+ * call's last C when reuse_lists != 0 (nothing moves between the two); the last
+ * C rebuilds them.  n_intervals_out: HOST or NULL, the intervals of both C. */
+gd_status gd_step(gd_ctx* ctx, double dt, int32_t reuse_lists, int32_t* n_intervals_out);
+
 /* Synchronises the stream, reduces per-instance sums and copies counters.
  * out: HOST, required.  inst_out: HOST [n_instances] or NULL.
  * Returns the first device error as a gd_status (GD_OK if none). */

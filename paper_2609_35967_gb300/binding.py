@@ -73,6 +73,8 @@ SIGNATURES = {
     "gd_sample_collisions": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "gd_push_staggered": ([C.c_void_p, C.c_double], C.c_int),
     "gd_diffuse": ([C.c_void_p, C.c_double], C.c_int),
+    "gd_collide": ([C.c_void_p, C.c_double, C.c_int32, C.c_int32, C.c_void_p], C.c_int),
+    "gd_step": ([C.c_void_p, C.c_double, C.c_int32, C.c_void_p], C.c_int),
     "gd_stats": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "gd_run_intervals": ([C.c_void_p, C.c_int32, C.c_int32], C.c_int),
     "gd_status_string": ([C.c_int], C.c_char_p),
@@ -147,6 +149,21 @@ def gd_push_staggered(ctx, dt):
 
 def gd_diffuse(ctx, dt):
     return _check("gd_diffuse", load().gd_diffuse(ctx, float(dt)))
+
+
+def gd_collide(ctx, tau, reuse_lists=False, max_intervals=1 << 20):
+    """Returns the number of intervals the bounded collision step took."""
+    n = C.c_int32(0)
+    _check("gd_collide", load().gd_collide(ctx, float(tau), 1 if reuse_lists else 0, int(max_intervals),
+                                           C.byref(n)))
+    return n.value
+
+
+def gd_step(ctx, dt, reuse_lists=False):
+    """Returns the number of collision intervals of the split timestep."""
+    n = C.c_int32(0)
+    _check("gd_step", load().gd_step(ctx, float(dt), 1 if reuse_lists else 0, C.byref(n)))
+    return n.value
 
 
 def gd_stats(ctx, n_instances):
@@ -284,6 +301,12 @@ class Session:
 
     def diffuse(self, dt=-1.0):
         gd_diffuse(self.ctx, dt)
+
+    def collide(self, tau, reuse_lists=False, max_intervals=1 << 20):
+        return gd_collide(self.ctx, tau, reuse_lists, max_intervals)
+
+    def step(self, dt, reuse_lists=False):
+        return gd_step(self.ctx, dt, reuse_lists)
 
     def run_intervals(self, n, push=False):
         gd_run_intervals(self.ctx, n, push)

@@ -235,6 +235,7 @@ static gd_status do_build(gd_ctx* c, int32_t* nbr_out, double* d_out) {
   if (e == cudaSuccess) e = launch_outputs_knn(c, nbr_out, d_out);
   if (e != cudaSuccess) return GD_ERR_CUDA;
   c->phase = 1;
+  c->lists_valid = true;
   return GD_OK;
 }
 
@@ -287,6 +288,56 @@ extern "C" gd_status gd_diffuse(gd_ctx* c, double dt) {
   if (!c) return GD_ERR_ARG;
   if (!std::isfinite(dt)) return GD_ERR_ARG;
   return cuda_err(launch_diffuse(c, dt));
+}
+
+extern "C" gd_status gd_collide(gd_ctx* c, double tau, int32_t reuse_lists, int32_t max_intervals,
+                                int32_t* n_intervals_out) {
+  if (n_intervals_out) *n_intervals_out = 0;
+  if (!c || !(tau > 0.0) || !std::isfinite(tau) || max_intervals < 1) return GD_ERR_ARG;
+  if (c->phase != 0) return GD_ERR_STATE;
+  int* d_flag = reinterpret_cast<int*>(c->d_counters + 4);
+  gd_status s = cuda_err(launch_step_begin(c, tau, 1));
+  int n = 0, done = 0;
+  while (s == GD_OK && n < max_intervals) {
+    // positions are frozen within the step: the lists are built once (or kept from the
+    // last step), later intervals only refresh the partner snapshot
+    if (n == 0 && !(reuse_lists && c->lists_valid)) {
+      s = do_build(c, nullptr, nullptr);
+    } else {
+      s = cuda_err(launch_snapshot(c));
+      c->phase = 1;
+    }
+    if (s == GD_OK) s = do_rates(c, nullptr, nullptr);
+    if (s == GD_OK) s = do_sample(c, nullptr, nullptr, nullptr);
+    if (s != GD_OK) break;
+    ++n;
+    cudaError_t e = launch_step_done(c, d_flag);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&done, d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) { s = GD_ERR_CUDA; break; }
+    if (done) break;
+  }
+  // back to open-ended collision steps of dt_coll
+  const gd_status r = cuda_err(launch_step_begin(c, 0.0, 0));
+  if (s == GD_OK) s = r;
+  if (n_intervals_out) *n_intervals_out = n;
+  if (s == GD_OK && !done) s = GD_ERR_TIMEOUT;
+  return s;
+}
+
+extern "C" gd_status gd_step(gd_ctx* c, double dt, int32_t reuse_lists, int32_t* n_intervals_out) {
+  if (n_intervals_out) *n_intervals_out = 0;
+  if (!c || !(dt > 0.0) || !std::isfinite(dt)) return GD_ERR_ARG;
+  if (c->phase != 0) return GD_ERR_STATE;
+  const int32_t kMaxIntervals = 1 << 20;
+  int32_t n1 = 0, n2 = 0;
+  gd_status s = gd_collide(c, 0.5 * dt, reuse_lists, kMaxIntervals, &n1);
+  if (s == GD_OK) s = cuda_err(launch_diffuse(c, 0.5 * dt));
+  if (s == GD_OK && c->vr && c->lth && c->lph) s = cuda_err(launch_push(c, dt));
+  if (s == GD_OK) s = cuda_err(launch_diffuse(c, 0.5 * dt));
+  if (s == GD_OK) s = gd_collide(c, 0.5 * dt, 0, kMaxIntervals, &n2);
+  if (n_intervals_out) *n_intervals_out = n1 + n2;
+  return s;
 }
 
 extern "C" gd_status gd_run_intervals(gd_ctx* c, int32_t n, int32_t push) {

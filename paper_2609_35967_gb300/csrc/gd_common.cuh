@@ -67,6 +67,9 @@ struct StateDev {
   long long interval_next;
   long long events, events_total, near_draw, near_dt, near_audit;
   long long knn_redo;       // mixed K-NN queries redone in FP64
+  double tau;               // length of the current collision step (0: dt_coll)
+  int hold;                 // 1: idle once the current collision step is used up (gd_collide)
+  int pad_hold;
   unsigned int status;
   int n_groups;
   // bounds of the data (ordered-integer encodings of doubles), min then max, x y z

@@ -61,6 +61,7 @@ struct gd_ctx {
   long long intervals = 0;
   long long launches = 0;
   long long diff_step = 0;              // gd_diffuse calls so far (Philox counter word 1)
+  bool lists_valid = false;             // neighbour lists built (gd_collide may reuse them)
 
   // timing
   static constexpr int kSlots = 8;
@@ -87,6 +88,9 @@ cudaError_t launch_sample(gd_ctx* c, int* ev_count, unsigned* ev_hash, int* near
 cudaError_t launch_audit(gd_ctx* c);
 cudaError_t launch_push(gd_ctx* c, double dt);
 cudaError_t launch_diffuse(gd_ctx* c, double dt);
+cudaError_t launch_snapshot(gd_ctx* c);
+cudaError_t launch_step_begin(gd_ctx* c, double tau, int hold);
+cudaError_t launch_step_done(gd_ctx* c, int* d_flag);
 cudaError_t launch_stats(gd_ctx* c, double* d_sums);
 cudaError_t launch_outputs_knn(gd_ctx* c, int* nbr_out, double* d_out);
 cudaError_t launch_outputs_lam(gd_ctx* c, double* lam_out);

@@ -377,6 +377,35 @@ __global__ void k_zero_counts(int* __restrict__ count, const unsigned long long*
 }
 
 // ---------------------------------------------------------------- scatter + snapshot
+// Frozen partner properties of one particle at rank r (Sect. 2.5.3): s, m, N = M/m, 1/m,
+// the represented mass, and the mixed form's FP32 copy (N scaled by 2^-64).
+template <bool kMixed>
+__device__ __forceinline__ void put_snapshot(const InstDev& p, long long r, double si, double Mi,
+                                             Snap64* __restrict__ snap64, float4* __restrict__ snap32,
+                                             double* __restrict__ Mr) {
+  const double m = grain_mass(p, si);
+  const double im = 1.0 / m;
+  const double N = Mi * im;
+  Snap64 sn;
+  sn.s = si; sn.m = m; sn.N = N; sn.inv_m = im;
+  snap64[r] = sn;
+  Mr[r] = Mi;
+  if (kMixed) snap32[r] = make_float4((float)si, (float)m, (float)(N * 0x1p-64), (float)im);
+}
+
+// The snapshot alone, at unchanged ranks (positions did not move since the last build).
+template <bool kMixed>
+__global__ void k_snapshot(TileMap tm, const InstDev* __restrict__ P, const double* __restrict__ s,
+                           const double* __restrict__ M, const int* __restrict__ rank_of,
+                           Snap64* __restrict__ snap64, float4* __restrict__ snap32, double* __restrict__ Mr) {
+  int b;
+  long long lo, hi;
+  if (!tile_range(tm, blockIdx.x, b, lo, hi)) return;
+  const InstDev p = P[b];
+  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x)
+    put_snapshot<kMixed>(p, rank_of[i], s[i], M[i], snap64, snap32, Mr);
+}
+
 template <bool kMixed>
 __global__ void k_scatter(TileMap tm, const InstDev* __restrict__ P, const GridDev* __restrict__ grid,
                           const double* __restrict__ x, const double* __restrict__ y,
@@ -399,13 +428,7 @@ __global__ void k_scatter(TileMap tm, const InstDev* __restrict__ P, const GridD
     Pos64 q;
     q.x = xi; q.y = yi; q.z = zi; q.j = i;
     pos64[r] = q;
-    const double m = grain_mass(p, si);
-    const double im = 1.0 / m;
-    const double N = Mi * im;
-    Snap64 sn;
-    sn.s = si; sn.m = m; sn.N = N; sn.inv_m = im;
-    snap64[r] = sn;
-    Mr[r] = Mi;
+    put_snapshot<kMixed>(p, r, si, Mi, snap64, snap32, Mr);
     {
       // FP32 mirror relative to the particle's own cell origin (|coord| <= cell edge),
       // cell coordinates packed in w (11 + 11 + 10 bits); periodic axes use the
@@ -420,9 +443,6 @@ __global__ void k_scatter(TileMap tm, const InstDev* __restrict__ P, const GridD
       float fy = (float)(yw - (g.lo[1] + iy * g.cs[1]));
       float fz = (float)(zi - (g.lo[2] + iz * g.cs[2]));
       pos32[r] = make_float4(fx, fy, fz, __int_as_float(ix | (iy << 11) | (iz << 22)));
-    }
-    if (kMixed) {
-      snap32[r] = make_float4((float)si, (float)m, (float)(N * 0x1p-64), (float)im);
     }
   }
 }
@@ -446,6 +466,21 @@ std::vector<long long> tile_table(const std::vector<long long>& off) {
   std::vector<long long> t(off.size(), 0);
   for (size_t b = 0; b + 1 < off.size(); ++b) t[b + 1] = t[b] + (off[b + 1] - off[b] + kTile - 1) / kTile;
   return t;
+}
+
+// Partner snapshot refresh at unchanged ranks (gd_collide's later intervals).
+cudaError_t launch_snapshot(gd_ctx* c) {
+  time_begin(c, 0);
+  const int nt = num_tiles(c);
+  if (c->precision == GD_MIXED)
+    k_snapshot<true><<<nt, 256, 0, c->stream>>>(tile_map(c), c->d_inst, c->s, c->M, c->d_rank_of, c->d_snap64,
+                                                c->d_snap32, c->d_Mr);
+  else
+    k_snapshot<false><<<nt, 256, 0, c->stream>>>(tile_map(c), c->d_inst, c->s, c->M, c->d_rank_of, c->d_snap64,
+                                                 c->d_snap32, c->d_Mr);
+  time_end(c);
+  c->launches += 1;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_stats(gd_ctx* c, double* d_sums) {

@@ -514,8 +514,15 @@ __global__ void k_interval(const InstDev* __restrict__ P, StateDev* st, BinsDev*
   for (int f = 0; f < kNFine; ++f) Bn.gid[f] = gid[f];
   Bn.ngroups = ng;
   const double C = (p.audit && !no_audit) ? S.C : 1.0;
+  const double dtc = S.tau > 0.0 ? S.tau : p.dt_coll;
+  if (S.hold && S.remain_ticks <= 0) {
+    // a bounded collision step (gd_collide) that is used up: idle until the next one
+    S.dt_exe = 0.0;
+    S.events = 0;
+    return;
+  }
   if (S.remain_ticks <= 0) S.remain_ticks = 1LL << 60;
-  const double remain = ldexp((double)S.remain_ticks, -60) * p.dt_coll;
+  const double remain = ldexp((double)S.remain_ticks, -60) * dtc;
   const double dt_cap = remain < p.dt_fn_max ? remain : p.dt_fn_max;
   double dt_ab = HUGE_VAL;
   for (int g = 0; g < ng; ++g) {
@@ -524,7 +531,7 @@ __global__ void k_interval(const InstDev* __restrict__ P, StateDev* st, BinsDev*
     if (Bm > 0.0) { const double t = p.eps * p.eps * C * C / Bm; if (t < dt_ab) dt_ab = t; }
   }
   const double dt_req = dt_ab < dt_cap ? dt_ab : dt_cap;
-  double dt = p.dt_coll;
+  double dt = dtc;
   int k = 0;
   while (k < 60 && (dt > dt_req || (1LL << (60 - k)) > S.remain_ticks)) { dt = 0.5 * dt; ++k; }
   if (dt > dt_req) S.status |= GD_ST_DT_FLOOR;
@@ -535,8 +542,8 @@ __global__ void k_interval(const InstDev* __restrict__ P, StateDev* st, BinsDev*
   S.dt_exe = dt;
   S.n_groups = ng;
   S.remain_ticks -= 1LL << (60 - k);
-  if (S.remain_ticks == 0) S.remain_ticks = 1LL << 60;
-  S.dt_remain = ldexp((double)S.remain_ticks, -60) * p.dt_coll;
+  if (S.remain_ticks == 0 && !S.hold) S.remain_ticks = 1LL << 60;
+  S.dt_remain = ldexp((double)S.remain_ticks, -60) * dtc;
   S.interval_cur = S.interval_next;
   S.interval_next = S.interval_next + 1;
   S.events = 0;
@@ -870,6 +877,30 @@ __global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
   }
 }
 
+// ---------------------------------------------------------------- bounded collision steps
+// gd_collide: every instance starts a collision step of length tau and idles once it is
+// used up, until the next call.
+// hold = 0 with tau = 0 returns the instances to collision steps of dt_coll.
+__global__ void k_step_begin(const InstDev* __restrict__ P, StateDev* st, int n_inst, double tau, int hold) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_inst) return;
+  st[b].tau = tau;
+  st[b].hold = hold;
+  st[b].remain_ticks = 1LL << 60;
+  st[b].dt_remain = tau > 0.0 ? tau : P[b].dt_coll;
+}
+
+// *flag = 1 when every instance has used up its collision step.
+__global__ void k_step_done(const StateDev* st, int n_inst, int* flag) {
+  __shared__ int open;
+  if (threadIdx.x == 0) open = 0;
+  __syncthreads();
+  for (int b = threadIdx.x; b < n_inst; b += blockDim.x)
+    if (st[b].remain_ticks > 0) open = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) *flag = open ? 0 : 1;
+}
+
 // ---------------------------------------------------------------- audit
 // One block per instance: realised mass-weighted sum of |ln(s'/s)| per controller bin
 // against 2 eps C; C halves (>= 1/4) on excess, else grows by 1.25 (<= 1).  Clears the
@@ -886,7 +917,7 @@ __global__ void k_audit(const InstDev* __restrict__ P, StateDev* st, BinsDev* bi
     gM[f] = 0.0; gJ[f] = 0.0;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && st[b].dt_exe > 0.0) {   // an idle (held) interval leaves C alone
     StateDev& S = st[b];
     if (P[b].audit && !no_audit) {
       for (int f = 0; f < kNFine; ++f)
@@ -911,6 +942,18 @@ __global__ void k_audit(const InstDev* __restrict__ P, StateDev* st, BinsDev* bi
 }
 
 // ---------------------------------------------------------------- launchers
+cudaError_t launch_step_begin(gd_ctx* c, double tau, int hold) {
+  k_step_begin<<<(c->n_inst + 127) / 128, 128, 0, c->stream>>>(c->d_inst, c->d_state, c->n_inst, tau, hold);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_done(gd_ctx* c, int* d_flag) {
+  k_step_done<<<1, 256, 0, c->stream>>>(c->d_state, c->n_inst, d_flag);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
 static McArgs mc_args(gd_ctx* c) {
   McArgs A;
   A.N = c->N;
