@@ -296,40 +296,53 @@ def cpu_oracle_rate(insts, budget_s=12.0, max_q=4096):
 
 
 def diffusion_line(args):
-    """The dust diffusion step (Sect. 2.4) alone: gd_diffuse on the 2^22 disk with
-    velocities, CUDA events on the library stream over the timed steps."""
+    """The dust diffusion step (Sect. 2.4) alone on the 2^22 disk: positions only in the
+    mixed form (FP32 draws and coefficients, FP64 positions), and with velocities (the
+    FP64 step with the velocity basis change); CUDA events on the library stream."""
     import torch
     from paper_2609_35967_gb300 import binding as gd
     from paper_2609_35967_gb300 import workloads as W
     ins = W.disk_instance(1 << 22, seed=1, K=32, sizes=("lognormal", 10.0, 1.0), velocities=True)
     N = len(ins["x"])
-    sess = gd.Session([ins], precision=gd.GD_MIXED, velocities=True, flags=gd.GD_FLAG_TIMING)
     dt = 0.05 * ins["params"]["dt_coll"]
-    for _ in range(args.warmup):
-        sess.diffuse(dt)
-    pre = sess.stats()["kernel_ms"]["diffuse"]
-    st = sess.stream
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    for _ in range(args.steps):
-        sess.diffuse(dt)
-    e1.record(st)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    kms = (sess.stats()["kernel_ms"]["diffuse"] - pre) / args.steps
-    sess.close()
     hbm, peak_kind = peaks()
-    bytes_pp = 7 * 8 + 6 * 8     # reads x y z s vr lth lph, writes x y z vr lth lph (FP64)
+
+    def timed(velocities):
+        sess = gd.Session([ins], precision=gd.GD_MIXED, velocities=velocities, flags=gd.GD_FLAG_TIMING)
+        for _ in range(args.warmup):
+            sess.diffuse(dt)
+        pre = sess.stats()["kernel_ms"]["diffuse"]
+        st = sess.stream
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.steps):
+            sess.diffuse(dt)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        kms = (sess.stats()["kernel_ms"]["diffuse"] - pre) / args.steps
+        sess.close()
+        return ms, kms
+
+    ms, kms = timed(False)
+    bytes_pp = 4 * 8 + 3 * 8     # reads x y z s, writes x y z (FP64)
     ach = bytes_pp * N / (kms * 1e-3) / 1e9
-    return {"metric": "particle diffusion steps/s (Sect. 2.4 Euler-Maruyama, with velocities)",
+    ms_v, kms_v = timed(True)
+    bytes_v = 7 * 8 + 6 * 8
+    ach_v = bytes_v * N / (kms_v * 1e-3) / 1e9
+    return {"metric": "particle diffusion steps/s (Sect. 2.4 Euler-Maruyama)",
             "value": N * args.steps / (ms * 1e-3), "unit": "particle-steps/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "global disk 5-100 au, 2^22 particles with velocities, dt = dt_coll/20",
+            "higher_is_better": True, "dtype": "f32 coefficients, f64 positions", "data": "synthetic",
+            "config": {"workload": "global disk 5-100 au, 2^22 particles, dt = dt_coll/20, positions only",
                        "n_particles": N},
-            "roofline": {"bound": "hbm", "kernel": "diffuse", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                         "frac": ach / hbm, "peak_kind": peak_kind, "algo_bytes_per_particle": bytes_pp}}
+            "roofline": {"bound": "hbm", "kernel": "diffuse (mixed)", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                         "frac": ach / hbm, "peak_kind": peak_kind, "algo_bytes_per_particle": bytes_pp},
+            "with_velocities": {"value": N * args.steps / (ms_v * 1e-3), "ms_per_step": ms_v / args.steps,
+                                "dtype": "f64", "roofline": {"bound": "hbm", "achieved": ach_v, "peak": hbm,
+                                                             "frac": ach_v / hbm,
+                                                             "algo_bytes_per_particle": bytes_v}}}
 
 
 def main():

@@ -96,6 +96,104 @@ __device__ __forceinline__ void normal_pair(const InstDev& p, uint32_t i_loc, ui
   n1 = rad * sn;
 }
 
+// Mixed form: the same coefficients in FP32, written in units of R so that no
+// intermediate leaves the FP32 range (zeta = Z/R, rho = r/R; 1 - R/r = zeta^2/(rho(rho+1))).
+// aR and aZ are the dt coefficients of the R and Z steps, as in diff_coef.
+struct DiffCoefF {
+  float DR, DZ, Dp, aR, aZ;
+};
+
+__device__ __forceinline__ DiffCoefF diff_coef_f(const InstDev& p, float R, float Z, float s) {
+  const float zeta = Z / R;
+  const float rho = sqrtf(1.0f + zeta * zeta);
+  const float Om = sqrtf(p.f_GM / R) / R;
+  const float xr = R / p.f_r0;
+  const float T = p.f_T0 * powf(xr, p.f_q);
+  const float cs = sqrtf((float)(kKB / (kMu * kMH)) * T);
+  const float H = cs / Om;
+  const float h2 = (H / R) * (H / R);
+  const float Sigma = p.f_sigma0 * powf(xr, p.f_p);
+  const float v = zeta * zeta / (rho * (rho + 1.0f)) / h2;
+  const float St = 3.14159265f * p.f_rho_s / (4.0f * Sigma) * expf(v) * s;
+  const float D = p.f_alpha * cs * H / (1.0f + St * St);
+  const float rho3h2 = rho * rho * rho * h2;
+  const float q = p.f_q, pp = p.f_p, chi = (float)p.diff_chi;
+  const float R_dvdR = -(zeta * zeta / rho3h2 + (q + 1.0f) * v);
+  const float R_dvdZ = zeta / rho3h2;
+  const float f = 2.0f * St * St / (1.0f + St * St);
+  DiffCoefF c;
+  c.DR = D / (float)p.Sc_R;
+  c.DZ = D / (float)p.Sc_Z;
+  c.Dp = D / (float)p.Sc_phi;
+  c.aR = c.DR / R * (1.0f + (q + 1.5f) - f * (R_dvdR - pp) + chi * ((pp - 0.5f * q - 1.5f) - R_dvdR));
+  c.aZ = c.DZ / R * (-(f + chi) * R_dvdZ);
+  return c;
+}
+
+// Mixed form: two standard normals in FP32 from the same uniforms as the FP64 form
+// ((k + 1/2) 2^-52 with k = (a >> 6) 2^26 + (b >> 6)), rounded once to FP32.
+__device__ __forceinline__ void normal_pair_f(const InstDev& p, uint32_t i_loc, uint32_t step, uint32_t word,
+                                              float& n0, float& n1) {
+  const U4 w = philox(i_loc, step, 0xFFFFFFFEu, word, p.key0, p.key1);
+  const float u1 = fmaf((float)(w.x >> 6), 0x1p-26f, ((float)(w.y >> 6) + 0.5f) * 0x1p-52f);
+  const float u2 = fmaf((float)(w.z >> 6), 0x1p-26f, ((float)(w.w >> 6) + 0.5f) * 0x1p-52f);
+  const float rad = sqrtf(-2.0f * logf(u1));
+  float sn, cn;
+  sincospif(2.0f * u2, &sn, &cn);
+  n0 = rad * cn;
+  n1 = rad * sn;
+}
+
+// Mixed form without velocities: FP32 draws and coefficients, the displacement applied to
+// the FP64 position without FP64 transcendentals -- the rotation by dphi through
+// cos dphi - 1 = -2 sin^2(dphi/2) and sin dphi, the radial step as the factor 1 + dR/R.
+__global__ void k_diffuse_f(long long N, int n_inst, const long long* __restrict__ off,
+                            const InstDev* __restrict__ P, const StateDev* __restrict__ st, double dt_in,
+                            long long step, double* x, double* y, double* z, const double* __restrict__ s) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int b = inst_of(off, n_inst, i);
+  const InstDev& p = P[b];
+  const float dt = (float)(dt_in < 0.0 ? st[b].dt_exe : dt_in);
+  const uint32_t il = (uint32_t)(i - p.off);
+  float zR, zZ, zP, unused;
+  normal_pair_f(p, il, (uint32_t)step, 0u, zR, zZ);
+  normal_pair_f(p, il, (uint32_t)step, 1u, zP, unused);
+  const double X = x[i], Y = y[i], Z = z[i];
+  const float sf = (float)s[i];
+  if (p.geometry == GD_GEOM_PATCH) {
+    const DiffCoefF c = diff_coef_f(p, (float)(p.r0 + X), (float)Z, sf);
+    double xn = X + (double)(sqrtf(2.0f * c.DR * dt) * zR + c.aR * dt);
+    double yn = Y + (double)(sqrtf(2.0f * c.Dp * dt) * zP);
+    xn -= p.box_x * floor((xn + 0.5 * p.box_x) / p.box_x);
+    yn -= p.box_y * floor((yn + 0.5 * p.box_y) / p.box_y);
+    x[i] = xn;
+    y[i] = yn;
+    z[i] = Z + (double)(sqrtf(2.0f * c.DZ * dt) * zZ + c.aZ * dt);
+    return;
+  }
+  const float Xf = (float)X, Yf = (float)Y;
+  const float Rf = sqrtf(Xf * Xf + Yf * Yf);
+  float dR, dZ = 0.0f, dph = 0.0f;
+  if (p.diff_mode == GD_DIFF_RING) {
+    const float g = Rf / (float)p.r0;
+    const float D = (float)p.D0 * g * g;
+    dR = sqrtf(2.0f * D * dt) * zR + D / Rf * (3.0f + (float)p.diff_chi * (float)p.p) * dt;
+  } else {
+    const DiffCoefF c = diff_coef_f(p, Rf, (float)Z, sf);
+    dR = sqrtf(2.0f * c.DR * dt) * zR + c.aR * dt;
+    dZ = sqrtf(2.0f * c.DZ * dt) * zZ + c.aZ * dt;
+    dph = sqrtf(2.0f * c.Dp * dt) * zP / Rf;
+  }
+  const float sh = sinf(0.5f * dph);
+  const double cm1 = (double)(-2.0f * sh * sh), s1 = (double)sinf(dph);
+  const double xr = X + (cm1 * X - s1 * Y), yr = Y + (cm1 * Y + s1 * X);
+  const double k = (double)(dR / Rf);
+  x[i] = xr + k * xr;
+  y[i] = yr + k * yr;
+  z[i] = Z + (double)dZ;
+}
+
 // One Euler-Maruyama step per particle (caller order), every instance.
 __global__ void k_diffuse(long long N, int n_inst, const long long* __restrict__ off,
                           const InstDev* __restrict__ P, const StateDev* __restrict__ st, double dt_in,
@@ -189,8 +287,12 @@ cudaError_t launch_push(gd_ctx* c, double dt) {
 cudaError_t launch_diffuse(gd_ctx* c, double dt) {
   time_begin(c, 7);
   const int blocks = (int)((c->N + 255) / 256);
-  k_diffuse<<<blocks, 256, 0, c->stream>>>(c->N, c->n_inst, c->d_off, c->d_inst, c->d_state, dt, c->diff_step,
-                                           c->x, c->y, c->z, c->vr, c->lth, c->lph, c->s);
+  if (c->precision == GD_MIXED && !(c->vr && c->lth && c->lph))
+    k_diffuse_f<<<blocks, 256, 0, c->stream>>>(c->N, c->n_inst, c->d_off, c->d_inst, c->d_state, dt,
+                                               c->diff_step, c->x, c->y, c->z, c->s);
+  else
+    k_diffuse<<<blocks, 256, 0, c->stream>>>(c->N, c->n_inst, c->d_off, c->d_inst, c->d_state, dt,
+                                             c->diff_step, c->x, c->y, c->z, c->vr, c->lth, c->lph, c->s);
   time_end(c);
   c->launches += 1;
   c->diff_step += 1;

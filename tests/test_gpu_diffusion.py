@@ -102,3 +102,27 @@ def test_neighbours_after_diffusion(gd, oracle):
     assert np.array_equal(nbr.cpu().numpy()[q], onbr)
     assert np.array_equal(d.cpu().numpy()[q], od)
     sess.close()
+
+
+@pytest.mark.parametrize("geometry", ["disk", "patch"])
+def test_mixed_diffusion_close_to_oracle(gd, oracle, geometry):
+    """Mixed form without velocities: FP32 draws (the FP64 form's uniforms rounded to FP32)
+    and FP32 coefficients, the step applied to the FP64 positions.  The displacements agree
+    with the FP64 oracle's to 1e-4 of their size."""
+    if geometry == "disk":
+        ins = W.disk_instance(5000, seed=17, sizes=("lognormal", 10.0, 1.0))
+        om = math.sqrt(6.674e-8 * W.MSUN / (5 * W.AU) ** 3)
+    else:
+        ins = W.patch_instance(4000, seed=18, alpha=1e-2)
+        om = math.sqrt(6.674e-8 * W.MSUN / ins["params"]["r0"] ** 3)
+    st, (x, y, z), _, got = _steps_both(gd, oracle, ins, 1, False, 1, 20.0 / om)
+    L = ins["params"]["box_x"] if geometry == "patch" else 0.0
+
+    def diff(a, b):
+        # minimum image across the patch's periodic edges
+        return a - b - (L * np.round((a - b) / L) if L > 0.0 else 0.0)
+
+    d = np.sqrt(diff(x, ins["x"]) ** 2 + diff(y, ins["y"]) ** 2 + (z - ins["z"]) ** 2)
+    err = np.sqrt(diff(got["x"], x) ** 2 + diff(got["y"], y) ** 2 + (got["z"] - z) ** 2)
+    assert np.median(d) > 0.0
+    assert (err <= 1e-4 * np.median(d) + 1e-4 * d).all(), (err / np.median(d)).max()
