@@ -260,7 +260,8 @@ gd_status gd_diffuse(gd_ctx* ctx, double dt);
  * when every instance has finished.  Positions are frozen during the step, so
  * the neighbour lists are built once: by the first interval, or not at all
  * when reuse_lists != 0 and the particles have not moved since the last build
- * (the caller's promise).  Later intervals refresh only the partner snapshot.
+ * (the caller's promise for its own changes; a gd_diffuse or gd_push_staggered
+ * call since the last build makes the step build anyway).  Later intervals refresh only the partner snapshot.
  * Synchronises the stream after every interval (the number of intervals is
  * data dependent).  max_intervals bounds the loop: GD_ERR_TIMEOUT when it is
  * reached first.  n_intervals_out: HOST or NULL.  Afterwards the instances are

@@ -281,12 +281,14 @@ extern "C" gd_status gd_push_staggered(gd_ctx* c, double dt) {
   if (!c) return GD_ERR_ARG;
   if (!c->vr || !c->lth || !c->lph) return GD_ERR_ARG;
   if (!std::isfinite(dt)) return GD_ERR_ARG;
+  c->lists_valid = false;           // positions move: gd_collide must build again
   return cuda_err(launch_push(c, dt));
 }
 
 extern "C" gd_status gd_diffuse(gd_ctx* c, double dt) {
   if (!c) return GD_ERR_ARG;
   if (!std::isfinite(dt)) return GD_ERR_ARG;
+  c->lists_valid = false;           // positions move: gd_collide must build again
   return cuda_err(launch_diffuse(c, dt));
 }
 
