@@ -63,7 +63,7 @@ def make_workload(name, rank=0):
     raise SystemExit(f"unknown workload {name}")
 
 
-# per-kernel algorithmic HBM bytes per particle
+# per-kernel algorithmic HBM bytes per particle (what a launch must read and write)
 def algo_bytes(kernel, K, mixed):
     if kernel == "knn":
         # own position (16 B FP32 or 32 B FP64), the list row (4K), d_i and V_i (16 B)

@@ -7,7 +7,7 @@ place particles (scale heights, column masses), and both the CUDA library and
 the CPU oracle read the same arrays.  Every generator is deterministic in its
 seed (numpy PCG64).
 
-Units: cgs.  Diameters s = 2a.  Recipes (stated again in the design doc):
+Units: cgs.  Diameters s = 2a.  Recipes:
 
 * local patch (Sect. 2.1, periodic sector): centred at radius r, x (radial)
   and y (azimuthal) uniform over one gas scale height, z ~ N(0, (0.1 H_g)^2);
