@@ -43,10 +43,11 @@ def _lists_rates(gd, oracle, insts, precision, check_events=True):
     sess.close()
 
 
-@pytest.mark.parametrize("K", [2, 33, 64, 100, 200])
+@pytest.mark.parametrize("K", [2, 33, 64, 100, 200, 256])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_K_range(gd, oracle, K, precision):
-    """Every buffer size of the search: K = 2 (one neighbour), 33 / 64 / 100 / 200. At K = 2
+    """Every buffer size of the search: K = 2 (one neighbour), 33 / 64 / 100 / 200, and the
+    largest K the library takes (256, the neighbourhood of the coagulation survey).  At K = 2
     a mutually nearest pair sticks until it reaches the per-interval event cap; the oracle
     reaches it too, so the status bit is compared rather than required to be clear."""
     n = max(600, 3 * K)
