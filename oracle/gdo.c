@@ -847,3 +847,82 @@ void gdo_diffuse(const gdo_params* P, double dt, int64_t step, int64_t n, double
     z[i] = Zn;
   }
 }
+
+/* Sect. 2.6: the local timestep Delta t_i of particle i, the most restrictive of
+ * the limits set by orbital motion and by the deterministic and diffusive
+ * displacements against the local grid spacing.  Reading (the paper names the
+ * limits, not their form or constants):
+ *   orbital:        f_orb * 2 pi / Omega_K(R_i)
+ *   deterministic:  c_adv * dx_i / |u_i|, u_i the velocity relative to the local
+ *                   circular Keplerian motion, (v_r, l_theta / r, l_phi / R - Omega_K R);
+ *                   global-disk particles with velocities only (patches do not move)
+ *   diffusive:      (c_diff * dx_i)^2 / (2 D_i), D_i the largest of the directional
+ *                   coefficients of Sect. 2.4 (ring test: D0 (R/R_0)^2)
+ * with dx_i = dx_H * H_g(R_i): the analytic gas disk has no grid, so the caller
+ * states its resolution in local gas scale heights.  A limit whose coefficient is
+ * <= 0, or whose rate is zero, is off; a particle with no limit gives +infinity.
+ * v: NULL or {v_r, l_theta, l_phi}. */
+double gdo_local_dt(const gdo_params* P, const gdo_dt_rule* rule, double x, double y, double z,
+                    double s, const double* v) {
+  double R = P->geometry == GDO_PATCH ? P->r0 + x : sqrt(x * x + y * y);
+  double Z = z;
+  gdo_gas g;
+  gas_RZ(P, R, Z, &g);
+  double dt = INFINITY;
+  if (rule->f_orb > 0.0) {
+    double t_orb = rule->f_orb * 2.0 * GDO_PI / g.Om;
+    if (t_orb < dt) dt = t_orb;
+  }
+  double dx = rule->dx_H * g.H;
+  if (rule->c_adv > 0.0 && v != NULL && P->geometry == GDO_DISK) {
+    double r = sqrt(R * R + Z * Z);
+    double u_r = v[0];
+    double u_th = v[1] / r;
+    double u_ph = v[2] / R - g.Om * R;
+    double u = sqrt(u_r * u_r + u_th * u_th + u_ph * u_ph);
+    if (u > 0.0) {
+      double t_adv = rule->c_adv * dx / u;
+      if (t_adv < dt) dt = t_adv;
+    }
+  }
+  if (rule->c_diff > 0.0) {
+    double D;
+    if (P->diff_mode == GDO_DIFF_RING) {
+      D = P->D0 * (R / P->r0) * (R / P->r0);
+    } else {
+      double c[7];
+      gdo_diff_coeffs(P, R, Z, s, c);
+      D = c[0];
+      if (c[1] > D) D = c[1];
+      if (c[2] > D) D = c[2];
+    }
+    if (D > 0.0) {
+      double t_diff = (rule->c_diff * dx) * (rule->c_diff * dx) / (2.0 * D);
+      if (t_diff < dt) dt = t_diff;
+    }
+  }
+  return dt;
+}
+
+/* Sect. 2.6: Delta t = min(Delta t_max, Delta t_out, min_i Delta t_i) over the
+ * particles 0..n-1 of one instance (a context of several instances takes the
+ * minimum over them).  dti: NULL or [n], each particle's Delta t_i. */
+double gdo_timestep(const gdo_params* P, const gdo_dt_rule* rule, int64_t n, const double* x,
+                    const double* y, const double* z, const double* s, const double* vr,
+                    const double* lth, const double* lph, double* dti) {
+  double dt = rule->dt_max < rule->dt_out ? rule->dt_max : rule->dt_out;
+  for (int64_t i = 0; i < n; ++i) {
+    double v[3];
+    const double* vp = NULL;
+    if (vr != NULL && lth != NULL && lph != NULL) {
+      v[0] = vr[i];
+      v[1] = lth[i];
+      v[2] = lph[i];
+      vp = v;
+    }
+    double t = gdo_local_dt(P, rule, x[i], y[i], z[i], s[i], vp);
+    if (dti != NULL) dti[i] = t;
+    if (t < dt) dt = t;
+  }
+  return dt;
+}

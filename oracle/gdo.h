@@ -150,9 +150,24 @@ void   gdo_push_one(const gdo_params* P, int32_t drag, double dt, double* x, dou
                     double* z, double* vr, double* lth, double* lph, double s);
 void   gdo_push(const gdo_params* P, int32_t drag, double dt, int64_t n, double* x, double* y,
                 double* z, double* vr, double* lth, double* lph, const double* s);
+/* The common transport timestep of Sect. 2.6 (reading; see gdo_local_dt). */
+typedef struct {
+  double dt_max;        /* prescribed maximum timestep Delta t_max [s] */
+  double dt_out;        /* time left before the next output Delta t_out [s] */
+  double f_orb;         /* orbital limit: Delta t_i <= f_orb * 2 pi / Omega_K(R_i); <= 0: off */
+  double dx_H;          /* local grid spacing Delta x_i = dx_H * H_g(R_i) */
+  double c_adv;         /* deterministic displacement |u_i| dt <= c_adv Delta x_i; <= 0: off */
+  double c_diff;        /* diffusive displacement sqrt(2 D_i dt) <= c_diff Delta x_i; <= 0: off */
+} gdo_dt_rule;
+
 void   gdo_diff_coeffs(const gdo_params* P, double R, double Z, double s, double out[7]);
 void   gdo_diffuse(const gdo_params* P, double dt, int64_t step, int64_t n, double* x, double* y,
                    double* z, double* vr, double* lth, double* lph, const double* s);
+double gdo_local_dt(const gdo_params* P, const gdo_dt_rule* rule, double x, double y, double z,
+                    double s, const double* v);
+double gdo_timestep(const gdo_params* P, const gdo_dt_rule* rule, int64_t n, const double* x,
+                    const double* y, const double* z, const double* s, const double* vr,
+                    const double* lth, const double* lph, double* dti);
 
 #ifdef __cplusplus
 }

@@ -8,6 +8,7 @@ paper_2609_35967_gb300.workloads (which hold none of the method's arithmetic).
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -117,6 +118,10 @@ def lib():
             L.gdo_push.argtypes = [vp, C.c_int32, dbl, i64, vp, vp, vp, vp, vp, vp, vp]
             L.gdo_diff_coeffs.argtypes = [vp, dbl, dbl, dbl, vp]
             L.gdo_diffuse.argtypes = [vp, dbl, i64, i64, vp, vp, vp, vp, vp, vp, vp]
+            L.gdo_local_dt.argtypes = [vp, vp, dbl, dbl, dbl, dbl, vp]
+            L.gdo_local_dt.restype = dbl
+            L.gdo_timestep.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
+            L.gdo_timestep.restype = dbl
             _lib = L
     return _lib
 
@@ -314,3 +319,28 @@ def diffuse(P: Params, dt, step, x, y, z, s, vr=None, lth=None, lph=None):
     v = (vr, lth, lph)
     ptrs = [_p(a) if a is not None else None for a in v]
     lib().gdo_diffuse(C.byref(P), dt, step, len(x), _p(x), _p(y), _p(z), *ptrs, _p(s))
+
+
+class DtRule(C.Structure):
+    _fields_ = [("dt_max", C.c_double), ("dt_out", C.c_double), ("f_orb", C.c_double),
+                ("dx_H", C.c_double), ("c_adv", C.c_double), ("c_diff", C.c_double)]
+
+
+def dt_rule(dt_max, dt_out=math.inf, f_orb=0.0, dx_H=0.0, c_adv=0.0, c_diff=0.0) -> DtRule:
+    return DtRule(dt_max, dt_out, f_orb, dx_H, c_adv, c_diff)
+
+
+def local_dt(P: Params, rule: DtRule, x, y, z, s, v=None) -> float:
+    """Delta t_i of one particle (Sect. 2.6); v = (v_r, l_theta, l_phi) or None."""
+    vv = None if v is None else np.ascontiguousarray(v, dtype=np.float64)
+    return lib().gdo_local_dt(C.byref(P), C.byref(rule), x, y, z, s, None if vv is None else _p(vv))
+
+
+def timestep(P: Params, rule: DtRule, x, y, z, s, vr=None, lth=None, lph=None):
+    """Delta t = min(dt_max, dt_out, min_i Delta t_i) over one instance, and every Delta t_i."""
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, z, s)]
+    vs = [None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in (vr, lth, lph)]
+    dti = np.zeros(len(arrs[0]))
+    dt = lib().gdo_timestep(C.byref(P), C.byref(rule), len(dti), *[_p(a) for a in arrs],
+                            *[None if a is None else _p(a) for a in vs], _p(dti))
+    return dt, dti
