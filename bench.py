@@ -83,12 +83,12 @@ def algo_bytes(kernel, K, mixed):
 # bench command (dram__bytes_read.sum + dram__bytes_write.sum), per particle.  The records
 # hold only while the sources the measured kernels compile from (their files and the shared
 # headers) have the content they had at the capture.
-TRAFFIC_CSRC_SHA256 = "c18edfc8541ed1f128837b500b987840951bdeb0881d57ed008ee92a49c47c79"
+TRAFFIC_CSRC_SHA256 = "c4262a3392280fb99c122581e12898f6a52773d8b1c23b56e2722663ba07d53a"
 TRAFFIC = {
-    "knn": {"workload": "disk22", "bytes_per_particle": 428.956},
-    "rates": {"workload": "disk22", "bytes_per_particle": 295.973},
-    "sample": {"workload": "disk22", "bytes_per_particle": 108.428},
-    "cells": {"workload": "disk22", "bytes_per_particle": 390.821},
+    "knn": {"workload": "disk22", "bytes_per_particle": 429.566},
+    "rates": {"workload": "disk22", "bytes_per_particle": 296.584},
+    "sample": {"workload": "disk22", "bytes_per_particle": 108.363},
+    "cells": {"workload": "disk22", "bytes_per_particle": 390.146},
 }
 
 
@@ -327,7 +327,27 @@ def diffusion_line(args):
         sess.close()
         return ms, kms
 
+    def timed_timestep():
+        # Sect. 2.6: the common transport timestep with every limit on (one kernel, a
+        # 16-byte copy back and a synchronisation per call)
+        sess = gd.Session([ins], precision=gd.GD_MIXED, velocities=True)
+        rule = dict(dt_max=ins["params"]["dt_coll"], f_orb=0.05, dx_H=0.1, c_adv=0.5, c_diff=0.5)
+        for _ in range(args.warmup):
+            sess.timestep(**rule)
+        st = sess.stream
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.steps):
+            dt_g = sess.timestep(**rule)
+        e1.record(st)
+        torch.cuda.synchronize()
+        sess.close()
+        return e0.elapsed_time(e1) / args.steps, dt_g
+
     ms, kms = timed(False)
+    ms_t, dt_g = timed_timestep()
+    bytes_t = 7 * 8              # reads x y z s vr lth lph (FP64)
     bytes_pp = 4 * 8 + 3 * 8     # reads x y z s, writes x y z (FP64)
     ach = bytes_pp * N / (kms * 1e-3) / 1e9
     ms_v, kms_v = timed(True)
@@ -344,7 +364,12 @@ def diffusion_line(args):
             "with_velocities": {"value": N * args.steps / (ms_v * 1e-3), "ms_per_step": ms_v / args.steps,
                                 "dtype": "f64", "roofline": {"bound": "hbm", "achieved": ach_v, "peak": hbm,
                                                              "frac": ach_v / hbm,
-                                                             "algo_bytes_per_particle": bytes_v}}}
+                                                             "algo_bytes_per_particle": bytes_v}},
+            "timestep": {"what": "gd_timestep, every limit on, with velocities (kernel + copy back + sync)",
+                         "ms_per_call": ms_t, "dt_over_dt_coll": dt_g / ins["params"]["dt_coll"],
+                         "roofline": {"bound": "hbm", "achieved": bytes_t * N / (ms_t * 1e-3) / 1e9, "peak": hbm,
+                                      "frac": bytes_t * N / (ms_t * 1e-3) / 1e9 / hbm,
+                                      "algo_bytes_per_particle": bytes_t}}}
 
 
 def main():

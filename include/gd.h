@@ -278,6 +278,35 @@ gd_status gd_collide(gd_ctx* ctx, double tau, int32_t reuse_lists, int32_t max_i
  * C rebuilds them.  n_intervals_out: HOST or NULL, the intervals of both C. */
 gd_status gd_step(gd_ctx* ctx, double dt, int32_t reuse_lists, int32_t* n_intervals_out);
 
+/* Sect. 2.6: the common transport timestep of every particle of the context,
+ *   dt = min(dt_max, dt_out, min_i dt_i),
+ * dt_i the most restrictive local limit of particle i (the paper names the
+ * limits, orbital motion and the deterministic and diffusive displacements
+ * against the local grid spacing, not their form; this is the form taken):
+ *   orbital        f_orb * 2 pi / Omega_K(R_i)
+ *   deterministic  c_adv * dx_i / |u_i|, u_i = (v_r, l_theta / r, l_phi / R -
+ *                  Omega_K R) the velocity relative to the local circular Keplerian
+ *                  motion; global-disk particles of a config with velocities only
+ *   diffusive      (c_diff * dx_i)^2 / (2 D_i), D_i the largest directional
+ *                  coefficient of gd_diffuse's model at the particle
+ * with dx_i = dx_H * H_g(R_i) (the analytic disk has no grid: the caller states
+ * its resolution in local gas scale heights).  A limit whose coefficient is <= 0
+ * is off.  FP64 in both precision forms.  dt_out_host: HOST, required, receives
+ * dt.  dti_out: DEVICE [N] caller order, or NULL, receives every dt_i (+infinity
+ * where no limit applies).  Synchronises the stream.  GD_ERR_ARG for a missing
+ * rule, dt_max or dt_out not > 0, a non-finite coefficient, or dx_H not > 0 and
+ * finite with c_adv or c_diff on; GD_ERR_NONFINITE when some dt_i is NaN or not
+ * > 0 (dt is still written, from the other particles). */
+typedef struct {
+  double dt_max;       /* prescribed maximum timestep [s]                      */
+  double dt_out;       /* time left before the next output [s] (HUGE_VAL: none) */
+  double f_orb;        /* orbital limit, fraction of the local Keplerian period */
+  double dx_H;         /* local grid spacing in local gas scale heights        */
+  double c_adv;        /* deterministic displacement per step, in spacings     */
+  double c_diff;       /* diffusive displacement sqrt(2 D dt), in spacings     */
+} gd_dt_rule;
+gd_status gd_timestep(gd_ctx* ctx, const gd_dt_rule* rule, double* dt_out_host, double* dti_out);
+
 /* Synchronises the stream, reduces per-instance sums and copies counters.
  * out: HOST, required.  inst_out: HOST [n_instances] or NULL.
  * Returns the first device error as a gd_status (GD_OK if none). */

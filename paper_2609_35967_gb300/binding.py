@@ -12,6 +12,7 @@ torch stream, and forwards each call.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import threading
 
@@ -64,6 +65,12 @@ class InstanceStats(C.Structure):
                 ("near_audit", C.c_int64), ("status", C.c_uint32), ("n_groups", C.c_int32)]
 
 
+class DtRule(C.Structure):
+    """gd_dt_rule: the common transport timestep's bounds and local limits."""
+    _fields_ = [("dt_max", C.c_double), ("dt_out", C.c_double), ("f_orb", C.c_double),
+                ("dx_H", C.c_double), ("c_adv", C.c_double), ("c_diff", C.c_double)]
+
+
 # every function declared in include/gd.h, with ctypes signatures
 SIGNATURES = {
     "gd_create": ([C.c_void_p, C.c_void_p], C.c_int),
@@ -75,6 +82,7 @@ SIGNATURES = {
     "gd_diffuse": ([C.c_void_p, C.c_double], C.c_int),
     "gd_collide": ([C.c_void_p, C.c_double, C.c_int32, C.c_int32, C.c_void_p], C.c_int),
     "gd_step": ([C.c_void_p, C.c_double, C.c_int32, C.c_void_p], C.c_int),
+    "gd_timestep": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "gd_stats": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "gd_run_intervals": ([C.c_void_p, C.c_int32, C.c_int32], C.c_int),
     "gd_status_string": ([C.c_int], C.c_char_p),
@@ -164,6 +172,13 @@ def gd_step(ctx, dt, reuse_lists=False):
     n = C.c_int32(0)
     _check("gd_step", load().gd_step(ctx, float(dt), 1 if reuse_lists else 0, C.byref(n)))
     return n.value
+
+
+def gd_timestep(ctx, rule: DtRule, dti_out=0):
+    """Returns the common transport timestep dt (Sect. 2.6)."""
+    dt = C.c_double(0.0)
+    _check("gd_timestep", load().gd_timestep(ctx, C.byref(rule), C.byref(dt), dti_out or None))
+    return dt.value
 
 
 def gd_stats(ctx, n_instances):
@@ -307,6 +322,14 @@ class Session:
 
     def step(self, dt, reuse_lists=False):
         return gd_step(self.ctx, dt, reuse_lists)
+
+    def timestep(self, dt_max, dt_out=math.inf, f_orb=0.0, dx_H=0.0, c_adv=0.0, c_diff=0.0, want=False):
+        """The common transport timestep; with want=True also every particle's dt_i."""
+        import torch
+        rule = DtRule(dt_max, dt_out, f_orb, dx_H, c_adv, c_diff)
+        dti = torch.empty(self.N, dtype=torch.float64, device=self.device) if want else None
+        dt = gd_timestep(self.ctx, rule, dti.data_ptr() if dti is not None else 0)
+        return (dt, dti) if want else dt
 
     def run_intervals(self, n, push=False):
         gd_run_intervals(self.ctx, n, push)

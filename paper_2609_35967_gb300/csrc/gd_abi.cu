@@ -342,6 +342,31 @@ extern "C" gd_status gd_step(gd_ctx* c, double dt, int32_t reuse_lists, int32_t*
   return s;
 }
 
+extern "C" gd_status gd_timestep(gd_ctx* c, const gd_dt_rule* r, double* dt_out_host, double* dti_out) {
+  if (dt_out_host) *dt_out_host = 0.0;
+  if (!c || !r || !dt_out_host) return GD_ERR_ARG;
+  if (!(r->dt_max > 0.0) || !(r->dt_out > 0.0)) return GD_ERR_ARG;
+  if (!std::isfinite(r->f_orb) || !std::isfinite(r->c_adv) || !std::isfinite(r->c_diff)) return GD_ERR_ARG;
+  if ((r->c_adv > 0.0 || r->c_diff > 0.0) && !(r->dx_H > 0.0 && std::isfinite(r->dx_H))) return GD_ERR_ARG;
+  unsigned long long* d_min = c->d_counters + 8;
+  unsigned long long* d_bad = c->d_counters + 9;
+  unsigned long long h[2] = {0, 0};
+  cudaError_t e = cudaMemsetAsync(d_min, 0xFF, sizeof(unsigned long long), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), c->stream);
+  if (e == cudaSuccess && c->N > 0) e = launch_timestep(c, *r, dti_out, d_min, d_bad);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, d_min, sizeof h, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return GD_ERR_CUDA;
+  double dt = r->dt_max < r->dt_out ? r->dt_max : r->dt_out;
+  if (h[0] != ~0ull) {
+    double m;
+    std::memcpy(&m, &h[0], sizeof m);
+    if (m < dt) dt = m;
+  }
+  *dt_out_host = dt;
+  return h[1] ? GD_ERR_NONFINITE : GD_OK;
+}
+
 extern "C" gd_status gd_run_intervals(gd_ctx* c, int32_t n, int32_t push) {
   if (!c || n < 0) return GD_ERR_ARG;
   if (push && (!c->vr || !c->lth || !c->lph)) return GD_ERR_ARG;

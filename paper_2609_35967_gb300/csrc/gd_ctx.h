@@ -88,6 +88,8 @@ cudaError_t launch_sample(gd_ctx* c, int* ev_count, unsigned* ev_hash, int* near
 cudaError_t launch_audit(gd_ctx* c);
 cudaError_t launch_push(gd_ctx* c, double dt);
 cudaError_t launch_diffuse(gd_ctx* c, double dt);
+cudaError_t launch_timestep(gd_ctx* c, const gd_dt_rule& r, double* dti_out, unsigned long long* d_min,
+                            unsigned long long* d_bad);
 cudaError_t launch_snapshot(gd_ctx* c);
 cudaError_t launch_step_begin(gd_ctx* c, double tau, int hold);
 cudaError_t launch_step_done(gd_ctx* c, int* d_flag);

@@ -1,5 +1,5 @@
 // k_misc.cu -- staggered semi-analytic push (Sect. 2.3.3), dust diffusion (Sect. 2.4),
-// per-instance reductions for gd_stats, and conversion of rank-space results to the
+// the common transport timestep (Sect. 2.6) and conversion of rank-space results to the
 // caller's order.
 #include "gd_ctx.h"
 #include "gd_physics.cuh"
@@ -254,6 +254,83 @@ __global__ void k_diffuse(long long N, int n_inst, const long long* __restrict__
   x[i] = Rn * cpn;
   y[i] = Rn * spn;
   z[i] = Zn;
+}
+
+// ---------------------------------------------------------------- transport timestep
+// Sect. 2.6: the local limit dt_i of one particle; +infinity when no limit applies.
+__device__ __forceinline__ double local_dt(const InstDev& p, const gd_dt_rule& r, double x, double y,
+                                           double z, double s, bool has_v, double vr, double lth,
+                                           double lph) {
+  const double R = p.geometry == GD_GEOM_PATCH ? p.r0 + x : sqrt(x * x + y * y);
+  const Gas g = gas_RZ(p, R, z);
+  double dt = __longlong_as_double(0x7FF0000000000000ll);
+  if (r.f_orb > 0.0) dt = fmin(dt, r.f_orb * 2.0 * kPi / g.Om);
+  const double dx = r.dx_H * g.H;
+  if (r.c_adv > 0.0 && has_v && p.geometry == GD_GEOM_DISK) {
+    const double rr = sqrt(R * R + z * z);
+    const double ur = vr, uth = lth / rr, uph = lph / R - g.Om * R;
+    const double u = sqrt(ur * ur + uth * uth + uph * uph);
+    if (u > 0.0) dt = fmin(dt, r.c_adv * dx / u);
+  }
+  if (r.c_diff > 0.0) {
+    double D;
+    if (p.diff_mode == GD_DIFF_RING) {
+      D = p.D0 * (R / p.r0) * (R / p.r0);
+    } else {
+      const DiffCoef c = diff_coef(p, R, z, s);
+      D = fmax(c.DR, fmax(c.DZ, c.Dp));
+    }
+    if (D > 0.0) dt = fmin(dt, (r.c_diff * dx) * (r.c_diff * dx) / (2.0 * D));
+  }
+  return dt;
+}
+
+// Grid-stride over the particles (caller order); each block's minimum joins the
+// context's with one atomicMin on the bit pattern (positive doubles and +infinity
+// order as their bits).  A dt_i that is NaN or not > 0 sets *bad instead.
+__global__ void __launch_bounds__(256) k_timestep(long long N, int n_inst, const long long* __restrict__ off,
+                                                  const InstDev* __restrict__ P, gd_dt_rule r,
+                                                  const double* __restrict__ x, const double* __restrict__ y,
+                                                  const double* __restrict__ z, const double* __restrict__ s,
+                                                  const double* __restrict__ vr, const double* __restrict__ lth,
+                                                  const double* __restrict__ lph, double* dti_out,
+                                                  unsigned long long* d_min, unsigned long long* d_bad) {
+  const bool has_v = vr && lth && lph;
+  double m = __longlong_as_double(0x7FF0000000000000ll);
+  bool bad = false;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int b = inst_of(off, n_inst, i);
+    const double t = local_dt(P[b], r, x[i], y[i], z[i], s[i], has_v, has_v ? vr[i] : 0.0,
+                              has_v ? lth[i] : 0.0, has_v ? lph[i] : 0.0);
+    if (dti_out) dti_out[i] = t;
+    if (t > 0.0) m = fmin(m, t);
+    else bad = true;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+  __shared__ double wm[8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) wm[w] = m;
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(d_bad, 1ull);
+  if (threadIdx.x == 0) {
+    double bm = wm[0];
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) bm = fmin(bm, wm[k]);
+    atomicMin(d_min, (unsigned long long)__double_as_longlong(bm));
+  }
+}
+
+cudaError_t launch_timestep(gd_ctx* c, const gd_dt_rule& r, double* dti_out, unsigned long long* d_min,
+                            unsigned long long* d_bad) {
+  time_begin(c, 6);
+  long long blocks = (c->N + 255) / 256;
+  if (blocks > 8LL * c->num_sms) blocks = 8LL * c->num_sms;
+  if (blocks < 1) blocks = 1;
+  k_timestep<<<(int)blocks, 256, 0, c->stream>>>(c->N, c->n_inst, c->d_off, c->d_inst, r, c->x, c->y, c->z,
+                                                 c->s, c->vr, c->lth, c->lph, dti_out, d_min, d_bad);
+  time_end(c);
+  c->launches += 1;
+  return cudaGetLastError();
 }
 
 __global__ void k_out_knn(long long N, int K, const int* __restrict__ rank_of, const int* __restrict__ perm,
