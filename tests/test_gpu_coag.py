@@ -94,3 +94,29 @@ def test_product_kernel_solution_gpu(gd, precision):
     assert np.abs(m - np.rint(m)).max() < 1e-6
     assert X.w1(m, M, X.cdf_product(t), 0.0, 3.0) < 0.035
     assert abs(m.mean() / X.mean_product(t) - 1.0) < 0.15
+
+
+def test_survey_trends(gd):
+    """Appendix B's survey trends through the same runs as tests/coag_survey.py.
+    Linear kernel at t~ = 4, 2^17 particles: W1 falls with N_K (about as 1/N_K; the
+    10^6-particle survey gives 0.070 and 0.018 dex at N_K = 16 and 64).  Constant kernel:
+    the interval count, and with it the wall time, scales as eps^-2 (second-moment
+    constraint).  Product kernel at t~ = 0.9: W1 rises steeply with eps and the high-mass
+    end lags; this runs at the survey's 10^6 particles, N_K = 256 and first seed, because
+    smaller reshuffled systems run away before t~ = 0.9 (2^17 particles, N_K = 64, eps =
+    0.02 gel at t~ = 0.83 in both forms)."""
+    import coag_survey as S
+    n = 1 << 17
+    w16 = S.run(gd, "linear", n, 16, 0.08, 7)
+    w64 = S.run(gd, "linear", n, 64, 0.08, 7)
+    assert w16[3] == 0 and w64[3] == 0
+    assert w16[0] > 2.5 * w64[0], (w16[0], w64[0])
+    assert abs(w64[4] - 1.0) < 0.03                   # mean mass against 2 exp(2 t~)
+    c08 = S.run(gd, "constant", n, 16, 0.08, 7)
+    c16 = S.run(gd, "constant", n, 16, 0.16, 7)
+    assert 3.0 < c08[2] / c16[2] < 5.0, (c08[2], c16[2])
+    p04 = S.run(gd, "product", 1000000, 256, 0.04, 100)
+    p16 = S.run(gd, "product", 1000000, 256, 0.16, 100)
+    assert p04[3] == 0 and p16[3] == 0
+    assert p16[0] > 5.0 * p04[0], (p04[0], p16[0])   # survey: 0.0046 and 0.103 dex
+    assert p16[4] < 0.8 < p04[4]                      # the high-mass end lags at large eps
