@@ -327,10 +327,10 @@ def diffusion_line(args):
         sess.close()
         return ms, kms
 
-    def timed_timestep():
+    def timed_timestep(precision):
         # Sect. 2.6: the common transport timestep with every limit on (one kernel, a
         # 16-byte copy back and a synchronisation per call)
-        sess = gd.Session([ins], precision=gd.GD_MIXED, velocities=True)
+        sess = gd.Session([ins], precision=precision, velocities=True)
         rule = dict(dt_max=ins["params"]["dt_coll"], f_orb=0.05, dx_H=0.1, c_adv=0.5, c_diff=0.5)
         for _ in range(args.warmup):
             sess.timestep(**rule)
@@ -346,7 +346,8 @@ def diffusion_line(args):
         return e0.elapsed_time(e1) / args.steps, dt_g
 
     ms, kms = timed(False)
-    ms_t, dt_g = timed_timestep()
+    ms_t, dt_g = timed_timestep(gd.GD_MIXED)
+    ms_t64, dt_g64 = timed_timestep(gd.GD_FP64)
     bytes_t = 7 * 8              # reads x y z s vr lth lph (FP64)
     bytes_pp = 4 * 8 + 3 * 8     # reads x y z s, writes x y z (FP64)
     ach = bytes_pp * N / (kms * 1e-3) / 1e9
@@ -365,8 +366,10 @@ def diffusion_line(args):
                                 "dtype": "f64", "roofline": {"bound": "hbm", "achieved": ach_v, "peak": hbm,
                                                              "frac": ach_v / hbm,
                                                              "algo_bytes_per_particle": bytes_v}},
-            "timestep": {"what": "gd_timestep, every limit on, with velocities (kernel + copy back + sync)",
+            "timestep": {"what": "gd_timestep, every limit on, with velocities (kernel + copy back + sync), "
+                                 "mixed form (FP32 limits)",
                          "ms_per_call": ms_t, "dt_over_dt_coll": dt_g / ins["params"]["dt_coll"],
+                         "fp64": {"ms_per_call": ms_t64, "dt_rel_diff": dt_g / dt_g64 - 1.0},
                          "roofline": {"bound": "hbm", "achieved": bytes_t * N / (ms_t * 1e-3) / 1e9, "peak": hbm,
                                       "frac": bytes_t * N / (ms_t * 1e-3) / 1e9 / hbm,
                                       "algo_bytes_per_particle": bytes_t}}}

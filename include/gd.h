@@ -291,7 +291,10 @@ gd_status gd_step(gd_ctx* ctx, double dt, int32_t reuse_lists, int32_t* n_interv
  *                  coefficient of gd_diffuse's model at the particle
  * with dx_i = dx_H * H_g(R_i) (the analytic disk has no grid: the caller states
  * its resolution in local gas scale heights).  A limit whose coefficient is <= 0
- * is off.  FP64 in both precision forms.  dt_out_host: HOST, required, receives
+ * is off.  GD_FP64: FP64 throughout; GD_MIXED: each dt_i in FP32 (a few ulps of
+ * the gas disk's powers and exponential; the deterministic limit's azimuthal
+ * speed l_phi / R - sqrt(GM / R) from an FP64 difference of squares, so that
+ * it does not cancel), the minimum exact over the FP32 values.  dt_out_host: HOST, required, receives
  * dt.  dti_out: DEVICE [N] caller order, or NULL, receives every dt_i (+infinity
  * where no limit applies).  Synchronises the stream.  GD_ERR_ARG for a missing
  * rule, dt_max or dt_out not > 0, a non-finite coefficient, or dx_H not > 0 and

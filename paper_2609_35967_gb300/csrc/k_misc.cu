@@ -285,9 +285,59 @@ __device__ __forceinline__ double local_dt(const InstDev& p, const gd_dt_rule& r
   return dt;
 }
 
+// Mixed form: the same limits in FP32 (the gas disk as in diff_coef_f), fast FP32
+// quotients.  The azimuthal speed relative to the Keplerian one, l_phi / R - v_K,
+// cancels for prograde orbits: it is formed as ((l_phi^2 - GM R) / R^2) / (l_phi / R + v_K)
+// with l_phi^2 - GM R in FP64 (scaled by 1/R^2 into the FP32 range), so that it keeps
+// its relative accuracy down to the rounding of l_phi itself.
+__device__ __forceinline__ float local_dt_f(const InstDev& p, const gd_dt_rule& r, double x, double y,
+                                            double z, float s, bool has_v, double vr, double lth,
+                                            double lph) {
+  const float R = p.geometry == GD_GEOM_PATCH ? (float)(p.r0 + x)
+                                              : sqrtf((float)x * (float)x + (float)y * (float)y);
+  const float Z = (float)z;
+  const float vK = sqrtf(__fdividef(p.f_GM, R));
+  const float Om = __fdividef(vK, R);
+  const float T = p.f_T0 * powf(__fdividef(R, p.f_r0), p.f_q);
+  const float cs = sqrtf((float)(kKB / (kMu * kMH)) * T);
+  const float H = __fdividef(cs, Om);
+  float dt = __int_as_float(0x7F800000);
+  if (r.f_orb > 0.0) dt = fminf(dt, __fdividef((float)(r.f_orb * 2.0 * kPi), Om));
+  const float dx = (float)r.dx_H * H;
+  if (r.c_adv > 0.0 && has_v && p.geometry == GD_GEOM_DISK) {
+    const float rr = sqrtf(R * R + Z * Z);
+    const float lR = __fdividef((float)lph, R);
+    float uph;
+    if (lph > 0.0) {
+      const double Rd = sqrt(x * x + y * y);
+      const float dl2 = (float)((lph * lph - p.GM * Rd) * (double)__fdividef(1.0f, R * R));
+      uph = __fdividef(dl2, lR + vK);
+    } else {
+      uph = lR - vK;
+    }
+    const float ur = (float)vr, uth = __fdividef((float)lth, rr);
+    const float u = sqrtf(ur * ur + uth * uth + uph * uph);
+    if (u > 0.0f) dt = fminf(dt, __fdividef((float)r.c_adv * dx, u));
+  }
+  if (r.c_diff > 0.0) {
+    float D;
+    if (p.diff_mode == GD_DIFF_RING) {
+      const float g = __fdividef(R, p.f_r0);
+      D = (float)p.D0 * g * g;
+    } else {
+      const DiffCoefF c = diff_coef_f(p, R, Z, s);
+      D = fmaxf(c.DR, fmaxf(c.DZ, c.Dp));
+    }
+    const float cdx = (float)r.c_diff * dx;
+    if (D > 0.0f) dt = fminf(dt, __fdividef(cdx * cdx, 2.0f * D));
+  }
+  return dt;
+}
+
 // Grid-stride over the particles (caller order); each block's minimum joins the
 // context's with one atomicMin on the bit pattern (positive doubles and +infinity
 // order as their bits).  A dt_i that is NaN or not > 0 sets *bad instead.
+template <bool kMixed>
 __global__ void __launch_bounds__(256) k_timestep(long long N, int n_inst, const long long* __restrict__ off,
                                                   const InstDev* __restrict__ P, gd_dt_rule r,
                                                   const double* __restrict__ x, const double* __restrict__ y,
@@ -301,8 +351,13 @@ __global__ void __launch_bounds__(256) k_timestep(long long N, int n_inst, const
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x) {
     const int b = inst_of(off, n_inst, i);
-    const double t = local_dt(P[b], r, x[i], y[i], z[i], s[i], has_v, has_v ? vr[i] : 0.0,
-                              has_v ? lth[i] : 0.0, has_v ? lph[i] : 0.0);
+    double t;
+    if constexpr (kMixed)
+      t = (double)local_dt_f(P[b], r, x[i], y[i], z[i], (float)s[i], has_v, has_v ? vr[i] : 0.0,
+                             has_v ? lth[i] : 0.0, has_v ? lph[i] : 0.0);
+    else
+      t = local_dt(P[b], r, x[i], y[i], z[i], s[i], has_v, has_v ? vr[i] : 0.0, has_v ? lth[i] : 0.0,
+                   has_v ? lph[i] : 0.0);
     if (dti_out) dti_out[i] = t;
     if (t > 0.0) m = fmin(m, t);
     else bad = true;
@@ -326,8 +381,12 @@ cudaError_t launch_timestep(gd_ctx* c, const gd_dt_rule& r, double* dti_out, uns
   long long blocks = (c->N + 255) / 256;
   if (blocks > 8LL * c->num_sms) blocks = 8LL * c->num_sms;
   if (blocks < 1) blocks = 1;
-  k_timestep<<<(int)blocks, 256, 0, c->stream>>>(c->N, c->n_inst, c->d_off, c->d_inst, r, c->x, c->y, c->z,
-                                                 c->s, c->vr, c->lth, c->lph, dti_out, d_min, d_bad);
+  if (c->precision == GD_MIXED)
+    k_timestep<true><<<(int)blocks, 256, 0, c->stream>>>(c->N, c->n_inst, c->d_off, c->d_inst, r, c->x, c->y,
+                                                         c->z, c->s, c->vr, c->lth, c->lph, dti_out, d_min, d_bad);
+  else
+    k_timestep<false><<<(int)blocks, 256, 0, c->stream>>>(c->N, c->n_inst, c->d_off, c->d_inst, r, c->x, c->y,
+                                                          c->z, c->s, c->vr, c->lth, c->lph, dti_out, d_min, d_bad);
   time_end(c);
   c->launches += 1;
   return cudaGetLastError();
