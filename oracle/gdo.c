@@ -103,7 +103,22 @@ static void gas_RZ(const gdo_params* P, double R, double Z, gdo_gas* g) {
  * R = sqrt(x^2 + y^2) (Sect. 2.1). */
 void gdo_gas_at(const gdo_params* P, double x, double y, double z, gdo_gas* g) {
   double R = (P->geometry == GDO_PATCH) ? P->r0 + x : sqrt(x * x + y * y);
+  /* vertically integrated models (radial-azimuthal, radial) see the midplane */
+  if (P->model == GDO_MODEL_RPHI || P->model == GDO_MODEL_R) z = 0.0;
   gas_RZ(P, R, z, g);
+}
+
+/* Coordinates of the neighbour search, Sect. 2.5.1: 3D positions; the
+ * meridional plane (R, Z) of a 2D radial-polar model; the midplane (x, y) of a
+ * vertically integrated model; R alone in a 1D radial model. */
+static void model_coords(const gdo_params* P, double x, double y, double z, double* X, double* Y,
+                         double* Z) {
+  switch (P->model) {
+    case GDO_MODEL_RZ: *X = sqrt(x * x + y * y); *Y = z; *Z = 0.0; break;
+    case GDO_MODEL_RPHI: *X = x; *Y = y; *Z = 0.0; break;
+    case GDO_MODEL_R: *X = sqrt(x * x + y * y); *Y = 0.0; *Z = 0.0; break;
+    default: *X = x; *Y = y; *Z = z; break;
+  }
 }
 
 /* m = pi rho_o s^3 / 6, Sect. 2 (s is the diameter). */
@@ -113,8 +128,9 @@ double gdo_grain_mass(const gdo_params* P, double s) {
 
 /* ------------------------------------------------------------------ */
 /* K nearest neighbours of particle i by brute force (Sect. 2.5.1): every
- * other particle j is ranked by (d^2, j) with d^2 = (dx dx + dy dy) + dz dz,
- * minimum image in the periodic x and y of a patch.  Reading: the particle
+ * other particle j is ranked by (d^2, j) with d^2 = (dx dx + dy dy) + dz dz in
+ * the model's coordinates (model_coords), minimum image in the periodic x and y
+ * of a patch.  Reading: the particle
  * itself always takes slot 0 (it is included at zero distance), the K-1
  * nearest others follow in ascending index order, and no maximum search
  * scale applies.  *d receives the distance to the farthest retained
@@ -126,11 +142,15 @@ int gdo_knn_one(const gdo_params* P, int64_t n, const double* x, const double* y
   double* bd = (double*)malloc(sizeof(double) * (L > 0 ? L : 1));
   int64_t* bj = (int64_t*)malloc(sizeof(int64_t) * (L > 0 ? L : 1));
   int cnt = 0;
+  double xi, yi, zi;
+  model_coords(P, x[i], y[i], z[i], &xi, &yi, &zi);
   for (int64_t j = 0; j < n; ++j) {
     if (j == i) continue;
-    double dx = x[j] - x[i];
-    double dy = y[j] - y[i];
-    double dz = z[j] - z[i];
+    double xj, yj, zj;
+    model_coords(P, x[j], y[j], z[j], &xj, &yj, &zj);
+    double dx = xj - xi;
+    double dy = yj - yi;
+    double dz = zj - zi;
     if (P->geometry == GDO_PATCH) {
       if (dx > 0.5 * P->box_x) dx -= P->box_x;
       else if (dx < -0.5 * P->box_x) dx += P->box_x;
@@ -169,16 +189,47 @@ int gdo_knn_one(const gdo_params* P, int64_t n, const double* x, const double* y
  * the part outside is removed treating the boundary as locally flat.
  * Reading: for the global disk each radial edge at distance 0 < h < d
  * removes the spherical cap pi (d-h)^2 (2d+h) / 3; patches are periodic in
- * x, y and unbounded in z, so they need no correction. */
+ * x, y and unbounded in z, so they need no correction.  Reduced models: the
+ * sampled area (a disk of radius d in the meridional plane or the midplane, an
+ * annulus in 1D) times 2 pi R (2D radial-polar: a toroidal volume) or times
+ * the vertical length sqrt(2 pi (H_i^2 + H_j^2)) of the Gaussian average
+ * (vertically integrated models), so that lambda_ij = N_j K_ij / V_i keeps
+ * its form.  R: the particle's cylindrical radius. */
 double gdo_volume(const gdo_params* P, double d, double R) {
-  double V = 4.0 * GDO_PI * d * d * d / 3.0;
-  if (P->geometry == GDO_DISK) {
-    double h = R - P->R_in;
-    if (h > 0.0 && h < d) V -= GDO_PI * (d - h) * (d - h) * (2.0 * d + h) / 3.0;
-    h = P->R_out - R;
-    if (h > 0.0 && h < d) V -= GDO_PI * (d - h) * (d - h) * (2.0 * d + h) / 3.0;
+  if (P->model == GDO_MODEL_3D) {
+    double V = 4.0 * GDO_PI * d * d * d / 3.0;
+    if (P->geometry == GDO_DISK) {
+      double h = R - P->R_in;
+      if (h > 0.0 && h < d) V -= GDO_PI * (d - h) * (d - h) * (2.0 * d + h) / 3.0;
+      h = P->R_out - R;
+      if (h > 0.0 && h < d) V -= GDO_PI * (d - h) * (d - h) * (2.0 * d + h) / 3.0;
+    }
+    return V;
   }
-  return V;
+  /* reduced models (Sect. 2.5.1) */
+  double A;
+  if (P->model == GDO_MODEL_R) {
+    /* the annulus [R - d, R + d], clipped at the disk's edges */
+    double lo = R - d > P->R_in ? R - d : P->R_in;
+    double hi = R + d < P->R_out ? R + d : P->R_out;
+    A = GDO_PI * (hi * hi - lo * lo);
+  } else {
+    /* the disk of radius d; a radial edge at distance 0 < h < d, taken as a
+     * straight line, removes the circular segment d^2 acos(h/d) - h sqrt(d^2 - h^2) */
+    A = GDO_PI * d * d;
+    if (P->geometry == GDO_DISK) {
+      double h = R - P->R_in;
+      if (h > 0.0 && h < d) A -= d * d * acos(h / d) - h * sqrt(d * d - h * h);
+      h = P->R_out - R;
+      if (h > 0.0 && h < d) A -= d * d * acos(h / d) - h * sqrt(d * d - h * h);
+    }
+  }
+  if (P->model == GDO_MODEL_RZ) return A * 2.0 * GDO_PI * R;   /* toroidal volume */
+  /* vertically integrated: lambda_ij = N_j K_ij / (A sqrt(2 pi (H_i^2 + H_j^2)));
+   * reading: H_i = H_j = H_g(R_i), at i's position like every pair quantity */
+  gdo_gas g;
+  gas_RZ(P, R, 0.0, &g);
+  return A * sqrt(2.0 * GDO_PI * (g.H * g.H + g.H * g.H));
 }
 
 /* ------------------------------------------------------------------ */

@@ -27,6 +27,9 @@ extern "C" {
 enum { GDO_PATCH = 0, GDO_DISK = 1 };
 enum { GDO_PHYSICAL = 0, GDO_CONSTANT = 1, GDO_LINEAR = 2, GDO_PRODUCT = 3 };
 enum { GDO_DIFF_PHYSICAL = 0, GDO_DIFF_RING = 1 };  /* dust diffusion models (Sect. 2.4, 3.2) */
+/* resolved dimensions of the collision model (Sect. 2.5.1): 3D; 2D radial-polar
+ * (meridional plane); 2D radial-azimuthal, vertically integrated; 1D radial */
+enum { GDO_MODEL_3D = 0, GDO_MODEL_RZ = 1, GDO_MODEL_RPHI = 2, GDO_MODEL_R = 3 };
 enum { GDO_NFINE = 96, GDO_TMIN = -72 };          /* fine controller bins */
 
 /* status bits (sticky) */
@@ -65,6 +68,9 @@ typedef struct {
   int32_t diff_chi;     /* 1: concentration diffusion (drift along ln rho_g), 0: density */
   double Sc_R, Sc_Z, Sc_phi;  /* Schmidt numbers of the three directions */
   double D0;            /* ring test: D at R_0 [cm^2 s^-1] */
+  int32_t model;        /* GDO_MODEL_*: which dimensions the neighbour search and the
+                           sampling measure resolve (RZ and R: global disks only) */
+  int32_t pad_model;
 } gdo_params;
 
 typedef struct {

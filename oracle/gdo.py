@@ -51,7 +51,8 @@ class Params(C.Structure):
                 ("box_x", C.c_double), ("box_y", C.c_double), ("t0", C.c_double),
                 ("m0", C.c_double), ("seed", C.c_uint64), ("max_events", C.c_int64),
                 ("diff_mode", C.c_int32), ("diff_chi", C.c_int32), ("Sc_R", C.c_double),
-                ("Sc_Z", C.c_double), ("Sc_phi", C.c_double), ("D0", C.c_double)]
+                ("Sc_Z", C.c_double), ("Sc_phi", C.c_double), ("D0", C.c_double),
+                ("model", C.c_int32), ("pad_model", C.c_int32)]
 
 
 class State(C.Structure):
