@@ -11,7 +11,7 @@ plain FP64 form (reported beside it).  Its working set (neighbour lists alone ar
 512 MB) is larger than the 129 MB L2, so no L2 flush is added between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload disk22|disk20|patches256|disk24|patch4096]
+                  [--workload disk22|disk20|patches256|disk24|patch4096|disk22_rz|disk22_rphi|disk22_r]
 
 Under torchrun (N > 1) every rank runs an independent replica (seed + rank) on its
 own GPU: the path does not shard without a halo exchange, so this is weak scaling.
@@ -60,6 +60,16 @@ def make_workload(name, rank=0):
                                                "(median 1 um, sigma_ln 0.5), K=48, with push")
     if name == "patch4096":
         return W.config0(), dict(workload="local patch at 10 au, 4096 particles, K=32")
+    models = {"disk22_rz": (W.MODEL_RZ, "2D radial-polar model (meridional plane)"),
+              "disk22_rphi": (W.MODEL_RPHI, "vertically integrated radial-azimuthal model (midplane)"),
+              "disk22_r": (W.MODEL_R, "1D radial model")}
+    if name in models:
+        model, what = models[name]
+        insts = W.config2(seed=1 + rank)
+        for ins in insts:
+            ins["params"] = dict(ins["params"], model=model)
+        return insts, dict(workload="global disk 5-100 au, 2^22 particles, log-normal a (median 10 um, "
+                                    f"sigma_ln 1), K=32, {what}")
     raise SystemExit(f"unknown workload {name}")
 
 

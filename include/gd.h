@@ -64,6 +64,19 @@ enum {
 
 enum { GD_GEOM_PATCH = 0, GD_GEOM_DISK = 1 };
 enum { GD_DIFF_PHYSICAL = 0, GD_DIFF_RING = 1 };   /* gd_diffuse models */
+/* Collision models of Sect. 2.5.1 by the dimensions they resolve.  The neighbour
+ * search runs in the model's coordinates and V_i is the model's measure:
+ *   GD_MODEL_3D   (x, y, z); V = 4 pi d^3 / 3 (spherical caps at disk edges)
+ *   GD_MODEL_RZ   2D radial-polar, the meridional plane (R, Z); V = A 2 pi R,
+ *                 A = pi d^2 minus the circular segments beyond a radial edge
+ *   GD_MODEL_RPHI 2D radial-azimuthal, vertically integrated, the midplane (x, y);
+ *                 V = A sqrt(2 pi (H_i^2 + H_j^2)) with H_i = H_j = H_g(R_i)
+ *   GD_MODEL_R    1D radial, R; V = pi (R_hi^2 - R_lo^2) over [R - d, R + d]
+ *                 clipped at the edges, times the same vertical length
+ * The vertically integrated models (RPHI, R) evaluate the gas and the pair
+ * speeds in the midplane.  gd_push_staggered, gd_diffuse and gd_timestep move
+ * and limit the 3D positions whatever the model. */
+enum { GD_MODEL_3D = 0, GD_MODEL_RZ = 1, GD_MODEL_RPHI = 2, GD_MODEL_R = 3 };
 enum { GD_KERNEL_PHYSICAL = 0, GD_KERNEL_CONSTANT = 1, GD_KERNEL_LINEAR = 2,
        GD_KERNEL_PRODUCT = 3 };
 
@@ -91,7 +104,8 @@ typedef struct {
   int32_t kernel_mode; /* GD_KERNEL_*: physical kernel or an Appendix A test
                           kernel (V_i = 1, lambda_ij = (1/t0)(1/N_K)(m0/m_j) K) */
   int32_t audit;       /* 1: adaptive safety factor C; 0: C = 1              */
-  int32_t pad0;
+  int32_t model;       /* GD_MODEL_*: dimensions the collision model resolves
+                          (Sect. 2.5.1); RZ and R need GD_GEOM_DISK          */
   double r0;           /* reference radius R_0 (patch: its radius) [cm]      */
   double sigma0;       /* gas surface density at R_0 [g cm^-2]               */
   double p;            /* Sigma_g ~ R^p                                      */
@@ -354,7 +368,8 @@ const char* gd_status_string(gd_status code);
  * cell_size are read; stream: cudaStream_t (NULL = legacy default stream).
  *
  * Limits: n <= GD_FIXED_MAX_PARTICLES (else GD_ERR_CAPACITY, nothing runs),
- * 2 <= K <= GD_FIXED_MAX_K and K <= n (else GD_ERR_ARG).
+ * 2 <= K <= GD_FIXED_MAX_K and K <= n, params->model == GD_MODEL_3D (else
+ * GD_ERR_ARG).
  * The first call on a device looks up the array's device address with that
  * device current (cudaGetSymbolAddress); make that first call before any
  * stream capture.  All calls share the one array, which keeps the last call's

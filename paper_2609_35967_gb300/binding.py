@@ -30,7 +30,7 @@ TIMING_SLOTS = ("cells", "knn", "rates", "interval", "sample", "push", "stats", 
 
 class InstanceParams(C.Structure):
     _fields_ = [("geometry", C.c_int32), ("kernel_mode", C.c_int32), ("audit", C.c_int32),
-                ("pad0", C.c_int32), ("r0", C.c_double), ("sigma0", C.c_double),
+                ("model", C.c_int32), ("r0", C.c_double), ("sigma0", C.c_double),
                 ("p", C.c_double), ("T0", C.c_double), ("q", C.c_double), ("alpha", C.c_double),
                 ("M_star", C.c_double), ("rho_s", C.c_double), ("s_min", C.c_double),
                 ("v_frag", C.c_double), ("eps", C.c_double), ("dt_coll", C.c_double),

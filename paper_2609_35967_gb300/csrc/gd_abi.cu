@@ -97,6 +97,8 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
     if (p.geometry == GD_GEOM_PATCH && (!finite_pos(p.box_x) || !finite_pos(p.box_y))) return GD_ERR_ARG;
     if (p.geometry == GD_GEOM_DISK && !(p.R_out > p.R_in)) return GD_ERR_ARG;
     if (p.diff_mode != GD_DIFF_PHYSICAL && p.diff_mode != GD_DIFF_RING) return GD_ERR_ARG;
+    if (p.model < GD_MODEL_3D || p.model > GD_MODEL_R) return GD_ERR_ARG;
+    if ((p.model == GD_MODEL_RZ || p.model == GD_MODEL_R) && p.geometry != GD_GEOM_DISK) return GD_ERR_ARG;
     if (p.diff_chi != 0 && p.diff_chi != 1) return GD_ERR_ARG;
     if (p.diff_mode == GD_DIFF_RING && !(p.D0 >= 0.0 && std::isfinite(p.D0) && p.r0 > 0.0)) return GD_ERR_ARG;
     if (p.kernel_mode != GD_KERNEL_PHYSICAL && (!finite_pos(p.t0) || !finite_pos(p.m0))) return GD_ERR_ARG;
@@ -174,6 +176,7 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
     d.geometry = p.geometry;
     d.kernel_mode = p.kernel_mode;
     d.audit = p.audit;
+    d.model = p.model;
     d.r0 = p.r0; d.sigma0 = p.sigma0; d.p = p.p; d.T0 = p.T0; d.q = p.q; d.alpha = p.alpha;
     d.GM = kG * p.M_star;
     d.rho_s = p.rho_s; d.s_min = p.s_min; d.v_frag = p.v_frag; d.eps = p.eps;

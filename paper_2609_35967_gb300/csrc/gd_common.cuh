@@ -30,7 +30,7 @@ constexpr int kMaxK = 256;
 
 // Per-instance parameters as the kernels read them (derived once at create).
 struct InstDev {
-  int geometry, kernel_mode, audit, pad;
+  int geometry, kernel_mode, audit, model;
   double r0, sigma0, p, T0, q, alpha, GM, rho_s, s_min, v_frag, eps, dt_coll, dt_fn_max;
   double R_in, R_out, box_x, box_y, t0, m0, cell_size;
   uint32_t key0, key1;
@@ -42,6 +42,18 @@ struct InstDev {
   int diff_mode, diff_chi;
   double Sc_R, Sc_Z, Sc_phi, D0;
 };
+
+// Coordinates of the neighbour search in the instance's collision model (Sect. 2.5.1):
+// 3D positions, the meridional plane (R, Z, 0), the midplane (x, y, 0) or (R, 0, 0).  R is
+// the correctly rounded sqrt(x*x + y*y) without contraction, as the oracle forms it.
+__device__ __forceinline__ void model_pos(int model, double x, double y, double z, double& X, double& Y,
+                                          double& Z) {
+  if (model == GD_MODEL_3D) { X = x; Y = y; Z = z; return; }
+  if (model == GD_MODEL_RPHI) { X = x; Y = y; Z = 0.0; return; }
+  X = __dsqrt_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)));
+  Y = model == GD_MODEL_RZ ? z : 0.0;
+  Z = 0.0;
+}
 
 // Uniform cell grid of one instance, rebuilt every interval from the data bounds.
 struct GridDev {

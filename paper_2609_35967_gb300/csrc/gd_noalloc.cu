@@ -380,6 +380,7 @@ extern "C" gd_status gd_neighbors_fixed(const double* x, const double* y, const 
   if (n > kMaxN) return GD_ERR_CAPACITY;
   if (params->geometry != GD_GEOM_PATCH && params->geometry != GD_GEOM_DISK) return GD_ERR_ARG;
   if (params->geometry == GD_GEOM_PATCH && !(params->box_x > 0.0 && params->box_y > 0.0)) return GD_ERR_ARG;
+  if (params->model != GD_MODEL_3D) return GD_ERR_ARG;   // 3D positions only
   unsigned char* base = nullptr;
   gd_status st = scratch_address(&base);
   if (st != GD_OK) return st;

@@ -91,14 +91,17 @@ __global__ void __launch_bounds__(256) k_stats_inst(const long long* __restrict_
 }
 
 // ---------------------------------------------------------------- bounds
-__global__ void k_bounds(TileMap tm, const double* __restrict__ x, const double* __restrict__ y,
-                         const double* __restrict__ z, StateDev* st) {
+__global__ void k_bounds(TileMap tm, const InstDev* __restrict__ P, const double* __restrict__ x,
+                         const double* __restrict__ y, const double* __restrict__ z, StateDev* st) {
   int b;
   long long lo, hi;
   if (!tile_range(tm, blockIdx.x, b, lo, hi)) return;
+  const int model = P[b].model;
   unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0, 0, 0};
   for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    unsigned long long o[3] = {dbl_ord(x[i]), dbl_ord(y[i]), dbl_ord(z[i])};
+    double X, Y, Z;
+    model_pos(model, x[i], y[i], z[i], X, Y, Z);
+    unsigned long long o[3] = {dbl_ord(X), dbl_ord(Y), dbl_ord(Z)};
 #pragma unroll
     for (int a = 0; a < 3; ++a) { mn[a] = min(mn[a], o[a]); mx[a] = max(mx[a], o[a]); }
   }
@@ -159,7 +162,21 @@ __device__ long long grid_of(const InstDev& P, const StateDev& S, double cell_fa
   double vol = 1.0, emax = 0.0;
   for (int a = 0; a < 3; ++a) emax = fmax(emax, ext[a]);
   for (int a = 0; a < 3; ++a) vol *= fmax(ext[a], 1e-6 * emax + tiny);
-  double c = P.cell_size > 0.0 ? P.cell_size : cell_factor * cbrt(vol / (double)P.n);
+  double c;
+  if (P.cell_size > 0.0) {
+    c = P.cell_size;
+  } else if (P.model == GD_MODEL_3D) {
+    c = cell_factor * cbrt(vol / (double)P.n);
+  } else {
+    // reduced models: the points span 2 (RZ, RPHI) or 1 (R) axes
+    double span = 1.0;
+    int D = 0;
+    for (int a = 0; a < 3; ++a)
+      if (ext[a] > 1e-9 * emax) { span *= ext[a]; ++D; }
+    const double per = span / (double)P.n;
+    c = cell_factor * (D >= 3 ? cbrt(per) : D == 2 ? sqrt(per) : D == 1 ? per : 1.0);
+    if (!(c > 0.0)) c = emax + tiny;
+  }
   c *= grow;
   long long cells = 1;
   for (int a = 0; a < 3; ++a) {
@@ -264,16 +281,19 @@ __global__ void k_grid(const InstDev* __restrict__ P, StateDev* st, GridDev* gri
     for (int a = 0; a < 3; ++a) { st[b].bmin[a] = ~0ull; st[b].bmax[a] = 0ull; }
 }
 
-__global__ void k_cell_count(TileMap tm, const GridDev* __restrict__ grid, const double* __restrict__ x,
-                             const double* __restrict__ y, const double* __restrict__ z,
-                             int* __restrict__ count, int* __restrict__ cell_of, int* __restrict__ slot,
-                             long long cell_cap) {
+__global__ void k_cell_count(TileMap tm, const InstDev* __restrict__ P, const GridDev* __restrict__ grid,
+                             const double* __restrict__ x, const double* __restrict__ y,
+                             const double* __restrict__ z, int* __restrict__ count, int* __restrict__ cell_of,
+                             int* __restrict__ slot, long long cell_cap) {
   int b;
   long long lo, hi;
   if (!tile_range(tm, blockIdx.x, b, lo, hi)) return;
   const GridDev g = grid[b];
+  const int model = P[b].model;
   for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    int ix = axis_cell(g, 0, x[i]), iy = axis_cell(g, 1, y[i]), iz = axis_cell(g, 2, z[i]);
+    double X, Y, Z;
+    model_pos(model, x[i], y[i], z[i], X, Y, Z);
+    int ix = axis_cell(g, 0, X), iy = axis_cell(g, 1, Y), iz = axis_cell(g, 2, Z);
     long long c = g.cell_off + ix + (long long)g.dim[0] * (iy + (long long)g.dim[1] * iz);
     if (c >= cell_cap) c = cell_cap - 1;    // only after a capacity failure (status set)
     cell_of[i] = (int)c;
@@ -422,7 +442,9 @@ __global__ void k_scatter(TileMap tm, const InstDev* __restrict__ P, const GridD
   const GridDev g = grid[b];
   for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
     int r = start[cell_of[i]] + slot[i];
-    double xi = x[i], yi = y[i], zi = z[i], si = s[i], Mi = M[i];
+    double xi, yi, zi;
+    model_pos(p.model, x[i], y[i], z[i], xi, yi, zi);
+    const double si = s[i], Mi = M[i];
     perm[r] = (int)i;
     rank_of[i] = r;
     Pos64 q;
@@ -497,14 +519,14 @@ cudaError_t launch_cells(gd_ctx* c) {
   int nt = num_tiles(c);
   cudaStream_t st = c->stream;
   time_begin(c, 0);
-  k_bounds<<<nt, 256, 0, st>>>(tm, c->x, c->y, c->z, c->d_state);
+  k_bounds<<<nt, 256, 0, st>>>(tm, c->d_inst, c->x, c->y, c->z, c->d_state);
   // cells in use (written by k_grid): the zeroing and the scan stop there
   unsigned long long* used = c->d_counters + 2;
   k_grid<<<1, 256, 0, st>>>(c->d_inst, c->d_state, c->d_grid, c->n_inst, c->cell_factor, c->cell_xsplit,
                            c->cell_cap, used);
   const long long ncell = c->cell_cap;
   k_zero_counts<<<c->num_sms * 8, 256, 0, st>>>(c->d_cell_count, used);
-  k_cell_count<<<nt, 256, 0, st>>>(tm, c->d_grid, c->x, c->y, c->z, c->d_cell_count, c->d_cell_of,
+  k_cell_count<<<nt, 256, 0, st>>>(tm, c->d_inst, c->d_grid, c->x, c->y, c->z, c->d_cell_count, c->d_cell_of,
                                    c->d_slot, c->cell_cap);
   int nst = (int)((ncell + kScanTile) / kScanTile);   // tiles of cells [0, ncell] (end entry included)
   k_scan_reduce<<<nst, 256, 0, st>>>(c->d_cell_count, used, c->d_scan_tmp);

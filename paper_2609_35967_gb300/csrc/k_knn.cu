@@ -187,8 +187,11 @@ __device__ __forceinline__ bool rows_next(const Grid32& G, const QueryPos& Q, Ro
   return false;
 }
 
+__device__ __forceinline__ double sample_volume_reduced(const InstDev& P, double d, double x, double y);
+
 __device__ __forceinline__ double sample_volume(const InstDev& P, double d, double x, double y) {
   if (P.kernel_mode != GD_KERNEL_PHYSICAL) return 1.0;
+  if (P.model != GD_MODEL_3D) return sample_volume_reduced(P, d, x, y);
   double V = 4.0 * kPi * d * d * d / 3.0;
   if (P.geometry == GD_GEOM_DISK) {
     const double R2 = x * x + y * y;
@@ -203,6 +206,35 @@ __device__ __forceinline__ double sample_volume(const InstDev& P, double d, doub
     if (h > 0.0 && h < d) V -= kPi * (d - h) * (d - h) * (2.0 * d + h) / 3.0;
   }
   return V;
+}
+
+// Reduced models (Sect. 2.5.1), (x, y) the query's coordinates in its model: the sampled
+// area (a disk of radius d less the circular segments beyond a radial edge taken as a
+// straight line; the 1D annulus [R - d, R + d] clipped at the edges) times 2 pi R (2D
+// radial-polar: a toroidal volume) or times the vertical length sqrt(2 pi (H_i^2 + H_j^2))
+// of the Gaussian average with H_i = H_j = H_g(R_i) (vertically integrated models).
+__device__ __forceinline__ double sample_volume_reduced(const InstDev& P, double d, double x, double y) {
+  double R;
+  if (P.geometry == GD_GEOM_PATCH) R = P.r0 + x;
+  else if (P.model == GD_MODEL_RPHI) R = __dsqrt_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)));
+  else R = x;
+  double A;
+  if (P.model == GD_MODEL_R) {
+    const double lo = R - d > P.R_in ? R - d : P.R_in;
+    const double hi = R + d < P.R_out ? R + d : P.R_out;
+    A = kPi * (hi * hi - lo * lo);
+  } else {
+    A = kPi * d * d;
+    if (P.geometry == GD_GEOM_DISK) {
+      double h = R - P.R_in;
+      if (h > 0.0 && h < d) A -= d * d * acos(h / d) - h * sqrt(d * d - h * h);
+      h = P.R_out - R;
+      if (h > 0.0 && h < d) A -= d * d * acos(h / d) - h * sqrt(d * d - h * h);
+    }
+  }
+  if (P.model == GD_MODEL_RZ) return A * 2.0 * kPi * R;
+  const Gas g = gas_RZ(P, R, 0.0);
+  return A * sqrt(2.0 * kPi * (g.H * g.H + g.H * g.H));
 }
 
 // Radius estimate from the particle count of the 27 cells around the query.

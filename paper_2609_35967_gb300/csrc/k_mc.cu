@@ -122,6 +122,19 @@ __device__ __forceinline__ Fixed<float> make_fixed_f32(const InstDev& P, double 
   return f;
 }
 
+// The gas at a particle from its search coordinates (Pos64): the 2D radial-polar model
+// holds (R, Z, 0); the others hold positions whose R and Z the gas disk reads directly
+// (the vertically integrated models have Z = 0, the midplane).
+__device__ __forceinline__ Gas gas_of(const InstDev& P, const Pos64& p) {
+  return P.model == GD_MODEL_RZ ? gas_RZ(P, p.x, p.y) : gas_at(P, p.x, p.y, p.z);
+}
+
+__device__ __forceinline__ Fixed<float> make_fixed_f32_at(const InstDev& P, const Pos64& p, double V, double M,
+                                                          int K) {
+  if (P.model == GD_MODEL_RZ) return make_fixed_f32(P, p.x, 0.0, p.y, V, M, K);
+  return make_fixed_f32(P, p.x, p.y, p.z, V, M, K);
+}
+
 // <J>, <J^2> of a fragmentation in FP32 (mixed form; they only feed the bin moments).
 __device__ __forceinline__ void frag_moments_f32(double s_i, double s_min, double& j1, double& j2) {
   const float a = sqrtf((float)s_min / (float)s_i);
@@ -392,11 +405,11 @@ __global__ void __launch_bounds__(128) k_rates(McArgs A) {
     Fixed<T> fx;
     double fj1, fj2;
     if constexpr (sizeof(T) == 8) {
-      Gas g = gas_at(P, p.x, p.y, p.z);
+      Gas g = gas_of(P, p);
       fx = make_fixed<double>(P, g, A.V[r], A.Mr[r], A.K);
       frag_moments(s_i, P.s_min, fj1, fj2);
     } else {
-      fx = make_fixed_f32(P, p.x, p.y, p.z, A.V[r], A.Mr[r], A.K);
+      fx = make_fixed_f32_at(P, p, A.V[r], A.Mr[r], A.K);
       frag_moments_f32(s_i, P.s_min, fj1, fj2);
     }
     const Query<T> q = live_query<T>(fx, s_i, m_i);
@@ -608,10 +621,10 @@ __global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
       s_i = sn.s;
       m_i = sn.m;
       if constexpr (sizeof(T) == 8) {
-        Gas g = gas_at(P, p.x, p.y, p.z);
+        Gas g = gas_of(P, p);
         fx = make_fixed<double>(P, g, A.V[r], A.Mr[r], A.K);
       } else {
-        fx = make_fixed_f32(P, p.x, p.y, p.z, A.V[r], A.Mr[r], A.K);
+        fx = make_fixed_f32_at(P, p, A.V[r], A.Mr[r], A.K);
       }
     } else {
       fx = Fixed<T>{};

@@ -39,6 +39,7 @@ _MU = 2.34
 PATCH, DISK = 0, 1
 PHYSICAL, CONSTANT, LINEAR, PRODUCT = 0, 1, 2, 3
 DIFF_PHYSICAL, DIFF_RING = 0, 1
+MODEL_3D, MODEL_RZ, MODEL_RPHI, MODEL_R = 0, 1, 2, 3
 S_MIN = 2e-5          # minimum fragment diameter: a = 0.1 um
 
 
