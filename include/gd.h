@@ -72,7 +72,8 @@ enum { GD_DIFF_PHYSICAL = 0, GD_DIFF_RING = 1 };   /* gd_diffuse models */
  *   GD_MODEL_RPHI 2D radial-azimuthal, vertically integrated, the midplane (x, y);
  *                 V = A sqrt(2 pi (H_i^2 + H_j^2)) with H_i = H_j = H_g(R_i)
  *   GD_MODEL_R    1D radial, R; V = pi (R_hi^2 - R_lo^2) over [R - d, R + d]
- *                 clipped at the edges, times the same vertical length
+ *                 clipped at the edges, times the same vertical length; a
+ *                 context holds 1D instances only or none (GD_ERR_ARG)
  * The vertically integrated models (RPHI, R) evaluate the gas and the pair
  * speeds in the midplane.  gd_push_staggered, gd_diffuse and gd_timestep move
  * and limit the 3D positions whatever the model. */

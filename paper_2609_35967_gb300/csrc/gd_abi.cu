@@ -99,6 +99,8 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
     if (p.diff_mode != GD_DIFF_PHYSICAL && p.diff_mode != GD_DIFF_RING) return GD_ERR_ARG;
     if (p.model < GD_MODEL_3D || p.model > GD_MODEL_R) return GD_ERR_ARG;
     if ((p.model == GD_MODEL_RZ || p.model == GD_MODEL_R) && p.geometry != GD_GEOM_DISK) return GD_ERR_ARG;
+    // the 1D model's one-row grids take their own neighbour kernel: all or none
+    if ((p.model == GD_MODEL_R) != (cfg->params[0].model == GD_MODEL_R)) return GD_ERR_ARG;
     if (p.diff_chi != 0 && p.diff_chi != 1) return GD_ERR_ARG;
     if (p.diff_mode == GD_DIFF_RING && !(p.D0 >= 0.0 && std::isfinite(p.D0) && p.r0 > 0.0)) return GD_ERR_ARG;
     if (p.kernel_mode != GD_KERNEL_PHYSICAL && (!finite_pos(p.t0) || !finite_pos(p.m0))) return GD_ERR_ARG;
@@ -197,6 +199,7 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
     d.off = c->h_off[b];
     d.n = c->h_off[b + 1] - c->h_off[b];
     if (p.geometry == GD_GEOM_DISK) c->any_disk = true;
+    if (p.model == GD_MODEL_R) c->any_model_r = true;
     StateDev& s = st[b];
     std::memset(&s, 0, sizeof(s));
     s.C = 1.0;

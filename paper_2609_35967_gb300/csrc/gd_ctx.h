@@ -20,6 +20,7 @@ struct gd_ctx {
   std::vector<long long> h_off;
   std::vector<gd_instance_params> h_params;
   bool any_disk = false;
+  bool any_model_r = false;             // the instances use the 1D radial model (all of them)
 
   // caller-owned particle arrays (device)
   double *x = nullptr, *y = nullptr, *z = nullptr, *s = nullptr;

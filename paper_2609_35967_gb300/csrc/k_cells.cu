@@ -184,7 +184,10 @@ __device__ long long grid_of(const InstDev& P, const StateDev& S, double cell_fa
     const double e = pa ? ext[a] : ext[a] * (1.0 + 1e-9) + 1e-12 * emax + tiny;
     const double ca = a == 0 ? c / xsplit : c;
     const double dimd = pa ? floor(e / ca) : ceil(e / ca);
-    const int dim = (int)fmin(fmax(dimd, 1.0), a < 2 ? 2048.0 : 1024.0);
+    // per-axis cell limits: the FP32 mirror packs the cell coordinates as 11 + 11 + 10
+    // bits; the 1D radial model has y = z = 0 and gives x all the bits
+    const double cap = P.model == GD_MODEL_R ? (a == 0 ? 16777216.0 : 1.0) : (a < 2 ? 2048.0 : 1024.0);
+    const int dim = (int)fmin(fmax(dimd, 1.0), cap);
     g.lo[a] = lo[a];
     g.cs[a] = e / dim;
     g.inv[a] = dim / e;

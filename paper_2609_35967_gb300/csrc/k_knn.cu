@@ -333,7 +333,8 @@ struct LaneBuf {
 
 // Candidates of the ball of radius rho; keys inside it go to the buffer (the first CAP of
 // them).  Returns how many were inside.
-template <int CAP, bool kMixed>
+// kRow1: a one-row grid (the 1D radial model) packs the x cell in all the bits of w.
+template <int CAP, bool kMixed, bool kRow1>
 __device__ __forceinline__ int scan_ball(const KnnArgs& A, const Grid32& G, const GridDev& Gd, const QueryPos& Q,
                                          long long q, float rho, const LaneBuf<CAP, kMixed>& buf, bool& amb) {
   const float rel = 10.0f * 5.9604645e-8f;
@@ -371,7 +372,7 @@ __device__ __forceinline__ int scan_ball(const KnnArgs& A, const Grid32& G, cons
         for (int u = 0; u < 4; ++u) {
           const int r = r0 + u;
           if (r >= cb || r == (int)q) continue;
-          const int ixj = __float_as_int(p[u].w) & 2047;
+          const int ixj = __float_as_int(p[u].w) & (kRow1 ? 0x7FFFFFFF : 2047);
           const float dx = (p[u].x - Q.fx) + (float)(ixj + xoff) * G.cs[0];
           const float dy = (p[u].y - Q.fy) + dycf;
           const float dz = (p[u].z - Q.fz) + dzcf;
@@ -413,7 +414,7 @@ __device__ __forceinline__ int scan_ball(const KnnArgs& A, const Grid32& G, cons
 // (word 0) -- and d2max is the (K-1)-th d^2.  The output gathers the rest itself.
 // Returns false when no acceptable radius was found (mixed: also when the FP32 keys
 // cannot decide the members).
-template <int CAP, bool kMixed>
+template <int CAP, bool kMixed, bool kRow1>
 __device__ bool lane_query(const KnnArgs& A, const Grid32& G, const GridDev& Gd, const QueryPos& Q, long long q,
                            float rho, const LaneBuf<CAP, kMixed>& buf, double& d2max) {
   const int L = A.K - 1;
@@ -426,7 +427,7 @@ __device__ bool lane_query(const KnnArgs& A, const Grid32& G, const GridDev& Gd,
   float r_lo = 0.0f, r_hi = 0.0f;    // radii known to hold too few / too many candidates
   for (int att = 0; att < 64; ++att) {
     bool amb = false;
-    const int n_in = scan_ball<CAP, kMixed>(A, G, Gd, Q, q, rho, buf, amb);
+    const int n_in = scan_ball<CAP, kMixed, kRow1>(A, G, Gd, Q, q, rho, buf, amb);
     if (kMixed && amb) return false;
     if (n_in < L) {
       if (rho > 2.0f * diag) return false;
@@ -530,7 +531,9 @@ template <int CAP> struct KnnShape {
   }
 };
 
-template <int CAP, bool kMixed>
+// kRow1: a context of 1D radial instances (their one-row grids pack the x cell in all the
+// bits of w; the 1D model cannot share a context with the others).
+template <int CAP, bool kMixed, bool kRow1>
 __global__ void __launch_bounds__(128, CAP <= 40 ? 5 : 4) k_knn(KnnArgs A) {
   extern __shared__ uint32_t smem[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -551,9 +554,9 @@ __global__ void __launch_bounds__(128, CAP <= 40 ? 5 : 4) k_knn(KnnArgs A) {
     QueryPos Q;
     const float4 f = __ldg(A.pos32 + q);
     const int pk = __float_as_int(f.w);
-    Q.ix = pk & 2047;
-    Q.iy = (pk >> 11) & 2047;
-    Q.iz = (pk >> 22) & 1023;
+    Q.ix = kRow1 ? pk : pk & 2047;
+    Q.iy = kRow1 ? 0 : (pk >> 11) & 2047;
+    Q.iz = kRow1 ? 0 : (pk >> 22) & 1023;
     Q.fx = f.x; Q.fy = f.y; Q.fz = f.z;
     const double2* pp = reinterpret_cast<const double2*>(A.pos64 + q);
     const double2 a0 = __ldg(pp), a1 = __ldg(pp + 1);
@@ -565,7 +568,7 @@ __global__ void __launch_bounds__(128, CAP <= 40 ? 5 : 4) k_knn(KnnArgs A) {
     float rho = (dp > 0.0 && dp < 1e30) ? 1.02f * (float)dp : 0.0f;
     if (!(rho > 1e-4f * csmax)) rho = rho_start(G, A.cstart, Q, L);
     double d2max = 0.0;
-    const bool ok = lane_query<CAP, kMixed>(A, G, Gd, Q, q, rho, buf, d2max);
+    const bool ok = lane_query<CAP, kMixed, kRow1>(A, G, Gd, Q, q, rho, buf, d2max);
     int* row = A.nbr + q * (long long)A.K;
     if (ok) {
       row[0] = (int)q;
@@ -689,13 +692,13 @@ __global__ void __launch_bounds__(128, CAP <= 40 ? 5 : 4) k_knn(KnnArgs A) {
   }
 }
 
-template <int CAP, bool kMixed>
+template <int CAP, bool kMixed, bool kRow1>
 static cudaError_t launch_knn_t(gd_ctx* c, const KnnArgs& A) {
   constexpr int kWarps = KnnShape<CAP>::wpb(kMixed);
   const int bs = kWarps * 32;
   const int smem = kWarps * KnnShape<CAP>::bytes(kMixed);
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_knn<CAP, kMixed>, bs, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_knn<CAP, kMixed, kRow1>, bs, smem);
   if (per_sm < 1) per_sm = 1;
   long long blocks = (long long)c->num_sms * per_sm;
   if (!A.list) {
@@ -703,15 +706,18 @@ static cudaError_t launch_knn_t(gd_ctx* c, const KnnArgs& A) {
     if (blocks > want) blocks = want;
   }
   if (blocks < 1) blocks = 1;
-  k_knn<CAP, kMixed><<<(int)blocks, bs, smem, c->stream>>>(A);
+  k_knn<CAP, kMixed, kRow1><<<(int)blocks, bs, smem, c->stream>>>(A);
   return cudaGetLastError();
 }
 
 template <int CAP, bool kMixed>
 static cudaError_t prepare_t() {
   constexpr int kWarps = KnnShape<CAP>::wpb(kMixed);
-  return cudaFuncSetAttribute(k_knn<CAP, kMixed>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              kWarps * KnnShape<CAP>::bytes(kMixed));
+  const int smem = kWarps * KnnShape<CAP>::bytes(kMixed);
+  cudaError_t e = cudaFuncSetAttribute(k_knn<CAP, kMixed, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_knn<CAP, kMixed, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return e;
 }
 
 template <bool kMixed>
@@ -731,14 +737,19 @@ cudaError_t knn_prepare(gd_ctx* c) {
   return e;
 }
 
+template <int CAP, bool kMixed>
+static cudaError_t launch_both(gd_ctx* c, const KnnArgs& A) {
+  return c->any_model_r ? launch_knn_t<CAP, kMixed, true>(c, A) : launch_knn_t<CAP, kMixed, false>(c, A);
+}
+
 template <bool kMixed>
 static cudaError_t launch_cap(gd_ctx* c, const KnnArgs& A) {
   // buffer capacity: the K-1 members plus room for the radius margin
-  if (c->K <= 32) return launch_knn_t<40, kMixed>(c, A);
-  if (c->K <= 48) return launch_knn_t<64, kMixed>(c, A);
-  if (c->K <= 80) return launch_knn_t<96, kMixed>(c, A);
-  if (c->K <= 128) return launch_knn_t<144, kMixed>(c, A);
-  return launch_knn_t<272, kMixed>(c, A);
+  if (c->K <= 32) return launch_both<40, kMixed>(c, A);
+  if (c->K <= 48) return launch_both<64, kMixed>(c, A);
+  if (c->K <= 80) return launch_both<96, kMixed>(c, A);
+  if (c->K <= 128) return launch_both<144, kMixed>(c, A);
+  return launch_both<272, kMixed>(c, A);
 }
 
 cudaError_t launch_knn(gd_ctx* c) {

@@ -3,11 +3,12 @@
 The 2D radial-polar model (neighbours in the meridional plane, V = A 2 pi R), the
 vertically integrated radial-azimuthal model (neighbours in the midplane, V = A times the
 Gaussian vertical length) on a disk and on a periodic patch, and the 1D radial model
-(the clipped annulus), each in one context with a 3D disk: lists and d_i bit-exact,
+(the clipped annulus, in a context of its own), the 2D models in one context with a 3D
+disk: lists and d_i bit-exact,
 lambda*_i within 1e-12 (FP64 form) or 1e-4 (mixed form), first-interval event sequences
 identical except flagged near ties, in both forms; then a few whole intervals of each
 model against the oracle's interval step.  The argument checks refuse the radial models
-on a patch.
+on a patch and a 1D instance beside others.
 """
 import numpy as np
 import pytest
@@ -19,22 +20,24 @@ from test_gpu_edge import _lists_rates
 pytestmark = pytest.mark.gpu
 
 
-def _model_insts():
+def _model_insts(models):
     insts = []
-    for b, model in enumerate((1, 2, 3)):
-        ins = W.disk_instance(1500 + 300 * b, seed=90 + b, sizes=("lognormal", 10.0, 1.0), alpha=1e-2)
+    for b, model in enumerate(models):
+        ins = W.disk_instance(1500 + 300 * b, seed=90 + b + 5 * model, sizes=("lognormal", 10.0, 1.0), alpha=1e-2)
         ins["params"] = dict(ins["params"], model=model)
         insts.append(ins)
-    pat = W.patch_instance(1200, seed=94, alpha=3e-3)
-    pat["params"] = dict(pat["params"], model=2)
-    insts.append(pat)
-    insts.append(W.disk_instance(1000, seed=95, sizes=("lognormal", 10.0, 1.0)))   # 3D
     return insts
 
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_models_lists_rates_events(gd, oracle, precision):
-    _lists_rates(gd, oracle, _model_insts(), precision)
+    # the 2D models and a 3D disk in one context, with a vertically integrated patch
+    insts = _model_insts((1, 2, 0))
+    pat = W.patch_instance(1200, seed=94, alpha=3e-3)
+    pat["params"] = dict(pat["params"], model=2)
+    _lists_rates(gd, oracle, insts + [pat], precision)
+    # the 1D model takes a context of its own
+    _lists_rates(gd, oracle, _model_insts((3, 3)), precision)
 
 
 @pytest.mark.parametrize("model", [1, 2, 3])
@@ -73,3 +76,7 @@ def test_radial_models_need_a_disk(gd):
     ins["params"] = dict(ins["params"], model=4)
     with pytest.raises(gd.GDError):
         gd.Session([ins], precision=1)
+    # 1D instances cannot share a context with the others
+    with pytest.raises(gd.GDError) as e:
+        gd.Session(_model_insts((3, 0)), precision=1)
+    assert e.value.code == gd.GD_ERR_ARG
