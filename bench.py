@@ -93,12 +93,12 @@ def algo_bytes(kernel, K, mixed):
 # bench command (dram__bytes_read.sum + dram__bytes_write.sum), per particle.  The records
 # hold only while the sources the measured kernels compile from (their files and the shared
 # headers) have the content they had at the capture.
-TRAFFIC_CSRC_SHA256 = "c4262a3392280fb99c122581e12898f6a52773d8b1c23b56e2722663ba07d53a"
+TRAFFIC_CSRC_SHA256 = "bb50c548188a2b947ebd160ed5000aad1d766cf10acda74c078952067457c344"
 TRAFFIC = {
-    "knn": {"workload": "disk22", "bytes_per_particle": 429.566},
-    "rates": {"workload": "disk22", "bytes_per_particle": 296.584},
-    "sample": {"workload": "disk22", "bytes_per_particle": 108.363},
-    "cells": {"workload": "disk22", "bytes_per_particle": 390.146},
+    "knn": {"workload": "disk22", "bytes_per_particle": 428.921},
+    "rates": {"workload": "disk22", "bytes_per_particle": 296.718},
+    "sample": {"workload": "disk22", "bytes_per_particle": 108.729},
+    "cells": {"workload": "disk22", "bytes_per_particle": 399.304},
 }
 
 
