@@ -307,6 +307,54 @@ def cpu_oracle_rate(insts, budget_s=12.0, max_q=4096):
     return done / el, done, el, n
 
 
+def split_step_line(args):
+    """Whole numerical timesteps of Sect. 2.6 on the 2^22 disk with velocities, mixed form:
+    each step takes dt from gd_timestep and runs C(dt/2) D(dt/2) T(dt) D(dt/2) C(dt/2)
+    (gd_step), the first C reusing the previous step's lists.  CUDA events on the library
+    stream around the whole loop (gd_collide and gd_timestep synchronise inside it)."""
+    import torch
+    from paper_2609_35967_gb300 import binding as gd
+    from paper_2609_35967_gb300 import workloads as W
+    ins = W.disk_instance(1 << 22, seed=1, K=32, sizes=("lognormal", 10.0, 1.0), velocities=True)
+    N = len(ins["x"])
+    rule = dict(dt_max=ins["params"]["dt_coll"], f_orb=0.05, dx_H=0.1, c_adv=0.5, c_diff=0.5)
+
+    def run(timing):
+        sess = gd.Session([ins], precision=gd.GD_MIXED, velocities=True,
+                          flags=gd.GD_FLAG_TIMING if timing else 0)
+        for k in range(args.warmup):
+            sess.step(sess.timestep(**rule), reuse_lists=k > 0)
+        pre = sess.stats()
+        st = sess.stream
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        n_iv, t_sim = 0, 0.0
+        for _ in range(args.steps):
+            dt = sess.timestep(**rule)
+            n_iv += sess.step(dt, reuse_lists=True)
+            t_sim += dt
+        e1.record(st)
+        torch.cuda.synchronize()
+        post = sess.stats()
+        sess.close()
+        split = {k: (post["kernel_ms"][k] - pre["kernel_ms"][k]) / args.steps for k in post["kernel_ms"]}
+        return e0.elapsed_time(e1), n_iv, t_sim, split, post["status"]
+
+    ms, n_iv, t_sim, _, status = run(False)
+    _, _, _, split, _ = run(True)
+    return {"metric": "particle timesteps/s (Sect. 2.6 split step C D T D C with gd_timestep)",
+            "value": N * args.steps / (ms * 1e-3), "unit": "particle-steps/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "dtype": "f32+f64 (mixed)", "data": "synthetic",
+            "config": {"workload": "global disk 5-100 au, 2^22 particles, log-normal a (median 10 um, "
+                                   "sigma_ln 1), K=32, with velocities; dt from gd_timestep (f_orb 0.05, "
+                                   "dx_H 0.1, c_adv 0.5, c_diff 0.5, dt_max one orbit at 5 au)",
+                       "n_particles": N},
+            "collision_intervals_per_step": n_iv / args.steps, "dt_mean_s": t_sim / args.steps,
+            "kernels_ms_per_step": {k: v for k, v in split.items() if v > 0.0}, "status": status}
+
+
 def diffusion_line(args):
     """The dust diffusion step (Sect. 2.4) alone on the 2^22 disk: positions only in the
     mixed form (FP32 draws and coefficients, FP64 positions), and with velocities (the
@@ -400,6 +448,8 @@ def main():
                     help="x division of the cell edge when --cell-factor is given (0: 1)")
     ap.add_argument("--diffusion", action="store_true",
                     help="time the dust diffusion step alone (one JSON line, 1 GPU)")
+    ap.add_argument("--split-step", action="store_true",
+                    help="time whole split timesteps with gd_timestep (one JSON line, 1 GPU)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -434,6 +484,10 @@ def main():
     if args.diffusion:
         if rank == 0:
             print(json.dumps(diffusion_line(args)))
+        return
+    if args.split_step:
+        if rank == 0:
+            print(json.dumps(split_step_line(args)))
         return
 
     if world > 1:
