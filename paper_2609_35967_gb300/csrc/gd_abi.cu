@@ -393,6 +393,8 @@ extern "C" gd_status gd_run_intervals(gd_ctx* c, int32_t n, int32_t push) {
     if (c->graph_exec) { cudaGraphExecDestroy(c->graph_exec); c->graph_exec = nullptr; }
     cudaGraph_t g = nullptr;
     long long l0 = c->launches;
+    // the captured build is replayed after the previous interval's push
+    c->moved = push != 0;
     if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return GD_ERR_CUDA;
     gd_status s = do_build(c, nullptr, nullptr);
     if (s == GD_OK) s = do_rates(c, nullptr, nullptr);

@@ -63,6 +63,7 @@ struct gd_ctx {
   long long launches = 0;
   long long diff_step = 0;              // gd_diffuse calls so far (Philox counter word 1)
   bool lists_valid = false;             // neighbour lists built (gd_collide may reuse them)
+  bool moved = false;                   // particles moved since the last neighbour build
 
   // timing
   static constexpr int kSlots = 8;

@@ -53,6 +53,7 @@ struct KnnArgs {
   unsigned long long* redo_n;
   const int* list;                // FP64 redo pass: the queries to process
   const unsigned long long* list_n;
+  float rfac;                     // first radius = rfac d_i of the last build
 };
 
 // ---------------------------------------------------------------- geometry (FP32 / INT)
@@ -267,9 +268,10 @@ __device__ __forceinline__ float rho_start(const Grid32& G, const int* __restric
   return fminf(fmaxf(r, 1e-3f * csmax), 4.0f * csmax * (float)(G.dim[0] + G.dim[1] + G.dim[2]));
 }
 
-__device__ __forceinline__ float grow(float rho, int found, int L) {
-  float g = cbrtf(1.3f * (float)L / (float)(found > 0 ? found : 1));
-  return rho * fminf(fmaxf(g, 1.25f), 3.0f);
+__device__ __forceinline__ float grow(float rho, int found, int L, int cap) {
+  // few found: the count says little, so grow by at least a quarter
+  const float g = cbrtf(0.5f * (float)(L + cap) / (float)(found > 0 ? found : 1));
+  return rho * fminf(fmaxf(g, 4 * found >= L ? 1.01f : 1.25f), 3.0f);
 }
 
 // Minimum-image FP64 d^2 of rank r from the query: the oracle's expression.
@@ -429,15 +431,17 @@ __device__ bool lane_query(const KnnArgs& A, const Grid32& G, const GridDev& Gd,
     bool amb = false;
     const int n_in = scan_ball<CAP, kMixed, kRow1>(A, G, Gd, Q, q, rho, buf, amb);
     if (kMixed && amb) return false;
+    // a radius that held too few or too many is rescaled by the count towards the middle
+    // of the acceptable range [L, CAP] (count ~ rho^3), then bisected once both are known
     if (n_in < L) {
       if (rho > 2.0f * diag) return false;
       r_lo = rho;
-      rho = r_hi > 0.0f ? sqrtf(r_lo * r_hi) : grow(rho, n_in, L);
+      rho = r_hi > 0.0f ? sqrtf(r_lo * r_hi) : grow(rho, n_in, L, CAP);
       continue;
     }
     if (n_in > CAP) {
       r_hi = rho;
-      rho = r_lo > 0.0f ? sqrtf(r_lo * r_hi) : rho * fmaxf(cbrtf(0.8f * (float)CAP / (float)n_in), 0.3f);
+      rho = r_lo > 0.0f ? sqrtf(r_lo * r_hi) : rho * fmaxf(cbrtf(0.5f * (float)(L + CAP) / (float)n_in), 0.3f);
       continue;
     }
     const int iL = buf.select(n_in, L);
@@ -565,7 +569,7 @@ __global__ void __launch_bounds__(128, CAP <= 40 ? 5 : 4) k_knn(KnnArgs A) {
     // radius: the last build's d_i when known, else the neighbourhood's density
     const double dp = A.dprev[ci];
     const float csmax = fmaxf(G.cs[0], fmaxf(G.cs[1], G.cs[2]));
-    float rho = (dp > 0.0 && dp < 1e30) ? 1.02f * (float)dp : 0.0f;
+    float rho = (dp > 0.0 && dp < 1e30) ? A.rfac * (float)dp : 0.0f;
     if (!(rho > 1e-4f * csmax)) rho = rho_start(G, A.cstart, Q, L);
     double d2max = 0.0;
     const bool ok = lane_query<CAP, kMixed, kRow1>(A, G, Gd, Q, q, rho, buf, d2max);
@@ -774,6 +778,11 @@ cudaError_t launch_knn(gd_ctx* c) {
   A.redo_n = c->d_counters + 1;
   A.list = nullptr;
   A.list_n = nullptr;
+  // static particles: d_i of the last build is exact and 1.02 d_i holds the K-1 others; after
+  // a move the K-th distance scatters around it, so the first radius aims at the middle of
+  // the buffer's range instead
+  A.rfac = c->moved ? 1.045f : 1.02f;
+  c->moved = false;
   time_begin(c, 1);
   cudaError_t e = cudaSuccess;
   if (c->precision == GD_MIXED) {

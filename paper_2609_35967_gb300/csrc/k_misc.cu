@@ -417,6 +417,7 @@ cudaError_t launch_push(gd_ctx* c, double dt) {
                                          c->z, c->vr, c->lth, c->lph, c->s);
   time_end(c);
   c->launches += 1;
+  c->moved = true;
   return cudaGetLastError();
 }
 
@@ -432,6 +433,7 @@ cudaError_t launch_diffuse(gd_ctx* c, double dt) {
   time_end(c);
   c->launches += 1;
   c->diff_step += 1;
+  c->moved = true;
   return cudaGetLastError();
 }
 
