@@ -358,7 +358,7 @@ def split_step_line(args):
 def diffusion_line(args):
     """The dust diffusion step (Sect. 2.4) alone on the 2^22 disk: positions only in the
     mixed form (FP32 draws and coefficients, FP64 positions), and with velocities (the
-    FP64 step with the velocity basis change); CUDA events on the library stream."""
+    velocity basis change in FP64 from direction cosines); CUDA events on the library stream."""
     import torch
     from paper_2609_35967_gb300 import binding as gd
     from paper_2609_35967_gb300 import workloads as W
@@ -421,7 +421,8 @@ def diffusion_line(args):
             "roofline": {"bound": "hbm", "kernel": "diffuse (mixed)", "achieved": ach, "peak": hbm, "unit": "GB/s",
                          "frac": ach / hbm, "peak_kind": peak_kind, "algo_bytes_per_particle": bytes_pp},
             "with_velocities": {"value": N * args.steps / (ms_v * 1e-3), "ms_per_step": ms_v / args.steps,
-                                "dtype": "f64", "roofline": {"bound": "hbm", "achieved": ach_v, "peak": hbm,
+                                "dtype": "f32 coefficients, f64 positions and velocity basis change",
+                                "roofline": {"bound": "hbm", "achieved": ach_v, "peak": hbm,
                                                              "frac": ach_v / hbm,
                                                              "algo_bytes_per_particle": bytes_v}},
             "timestep": {"what": "gd_timestep, every limit on, with velocities (kernel + copy back + sync), "

@@ -264,6 +264,9 @@ gd_status gd_push_staggered(gd_ctx* ctx, double dt);
  * velocities in the config their Cartesian vector is kept and (v_r, l_theta,
  * l_phi) are recomputed at the new position.  Local patch: x += dR,
  * y += R dphi, z += dZ, wrapped.  GD_DIFF_RING: radial only with D = D0 (R/R_0)^2.
+ * GD_MIXED: FP32 draws and coefficients, the displacement applied to the FP64
+ * position (a rotation by dphi and the factor 1 + dR/R), the velocities
+ * re-projected in FP64 from the direction cosines of the two positions.
  * Positions are written in place (x, y, z; vr, lth, lph when given).
  * Returns GD_ERR_ARG for a non-finite dt.  Asynchronous. */
 gd_status gd_diffuse(gd_ctx* ctx, double dt);

@@ -147,9 +147,13 @@ __device__ __forceinline__ void normal_pair_f(const InstDev& p, uint32_t i_loc, 
 // Mixed form without velocities: FP32 draws and coefficients, the displacement applied to
 // the FP64 position without FP64 transcendentals -- the rotation by dphi through
 // cos dphi - 1 = -2 sin^2(dphi/2) and sin dphi, the radial step as the factor 1 + dR/R.
+// With velocities, their Cartesian vector is kept and (v_r, l_theta, l_phi) re-projected at
+// the new position in FP64 from the direction cosines of the two positions (cos phi = x/R,
+// sin theta = R/r, ...), with no transcendental function.
 __global__ void k_diffuse_f(long long N, int n_inst, const long long* __restrict__ off,
                             const InstDev* __restrict__ P, const StateDev* __restrict__ st, double dt_in,
-                            long long step, double* x, double* y, double* z, const double* __restrict__ s) {
+                            long long step, double* x, double* y, double* z, double* vr, double* lth,
+                            double* lph, const double* __restrict__ s) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const int b = inst_of(off, n_inst, i);
@@ -189,9 +193,25 @@ __global__ void k_diffuse_f(long long N, int n_inst, const long long* __restrict
   const double cm1 = (double)(-2.0f * sh * sh), s1 = (double)sinf(dph);
   const double xr = X + (cm1 * X - s1 * Y), yr = Y + (cm1 * Y + s1 * X);
   const double k = (double)(dR / Rf);
-  x[i] = xr + k * xr;
-  y[i] = yr + k * yr;
-  z[i] = Z + (double)dZ;
+  const double xn = xr + k * xr, yn = yr + k * yr, zn = Z + (double)dZ;
+  x[i] = xn;
+  y[i] = yn;
+  z[i] = zn;
+  if (vr && lth && lph) {
+    const double R2 = X * X + Y * Y, R = sqrt(R2), r = sqrt(R2 + Z * Z);
+    const double iR = 1.0 / R, ir = 1.0 / r;
+    const double sth = R * ir, cth = Z * ir, cp = X * iR, sp = Y * iR;
+    const double vth = lth[i] * ir, vph = lph[i] * iR, v_r = vr[i];
+    const double vx = v_r * sth * cp + vth * cth * cp - vph * sp;
+    const double vy = v_r * sth * sp + vth * cth * sp + vph * cp;
+    const double vz = v_r * cth - vth * sth;
+    const double Rn2 = xn * xn + yn * yn, Rn = sqrt(Rn2), rn = sqrt(Rn2 + zn * zn);
+    const double iRn = 1.0 / Rn, irn = 1.0 / rn;
+    const double sthn = Rn * irn, cthn = zn * irn, cpn = xn * iRn, spn = yn * iRn;
+    vr[i] = vx * sthn * cpn + vy * sthn * spn + vz * cthn;
+    lth[i] = rn * (vx * cthn * cpn + vy * cthn * spn - vz * sthn);
+    lph[i] = Rn * (-vx * spn + vy * cpn);
+  }
 }
 
 // One Euler-Maruyama step per particle (caller order), every instance.
@@ -424,9 +444,9 @@ cudaError_t launch_push(gd_ctx* c, double dt) {
 cudaError_t launch_diffuse(gd_ctx* c, double dt) {
   time_begin(c, 7);
   const int blocks = (int)((c->N + 255) / 256);
-  if (c->precision == GD_MIXED && !(c->vr && c->lth && c->lph))
+  if (c->precision == GD_MIXED)
     k_diffuse_f<<<blocks, 256, 0, c->stream>>>(c->N, c->n_inst, c->d_off, c->d_inst, c->d_state, dt,
-                                               c->diff_step, c->x, c->y, c->z, c->s);
+                                               c->diff_step, c->x, c->y, c->z, c->vr, c->lth, c->lph, c->s);
   else
     k_diffuse<<<blocks, 256, 0, c->stream>>>(c->N, c->n_inst, c->d_off, c->d_inst, c->d_state, dt,
                                              c->diff_step, c->x, c->y, c->z, c->vr, c->lth, c->lph, c->s);

@@ -37,7 +37,7 @@ def test_disk_diffusion_parity(gd, oracle, chi):
     ins = W.disk_instance(5000, seed=12, sizes=("lognormal", 10.0, 1.0), velocities=True)
     ins["params"] = dict(ins["params"], diff_chi=chi, Sc_Z=2.0)
     om5 = math.sqrt(6.674e-8 * W.MSUN / (5 * W.AU) ** 3)
-    st, (x, y, z), v, got = _steps_both(gd, oracle, ins, 1, True, 3, 20.0 / om5)
+    st, (x, y, z), v, got = _steps_both(gd, oracle, ins, 0, True, 3, 20.0 / om5)
     assert st["status"] == 0
     R = np.sqrt(x * x + y * y)
     for a, g in ((x, got["x"]), (y, got["y"]), (z, got["z"])):
@@ -104,18 +104,29 @@ def test_neighbours_after_diffusion(gd, oracle):
     sess.close()
 
 
-@pytest.mark.parametrize("geometry", ["disk", "patch"])
+@pytest.mark.parametrize("geometry", ["disk", "patch", "disk_v"])
 def test_mixed_diffusion_close_to_oracle(gd, oracle, geometry):
-    """Mixed form without velocities: FP32 draws (the FP64 form's uniforms rounded to FP32)
-    and FP32 coefficients, the step applied to the FP64 positions.  The displacements agree
-    with the FP64 oracle's to 1e-4 of their size."""
-    if geometry == "disk":
-        ins = W.disk_instance(5000, seed=17, sizes=("lognormal", 10.0, 1.0))
+    """Mixed form: FP32 draws (the FP64 form's uniforms rounded to FP32) and FP32
+    coefficients, the step applied to the FP64 positions.  The displacements agree with the
+    FP64 oracle's to 1e-4 of their size.  With velocities (disk_v) the FP64 basis change
+    from direction cosines gives the oracle's components to 1e-6 of their scale (the two
+    sides re-project at positions that differ by the displacement error)."""
+    vel = geometry == "disk_v"
+    if geometry.startswith("disk"):
+        ins = W.disk_instance(5000, seed=17, sizes=("lognormal", 10.0, 1.0), velocities=vel)
         om = math.sqrt(6.674e-8 * W.MSUN / (5 * W.AU) ** 3)
     else:
         ins = W.patch_instance(4000, seed=18, alpha=1e-2)
         om = math.sqrt(6.674e-8 * W.MSUN / ins["params"]["r0"] ** 3)
-    st, (x, y, z), _, got = _steps_both(gd, oracle, ins, 1, False, 1, 20.0 / om)
+    st, (x, y, z), v, got = _steps_both(gd, oracle, ins, 1, vel, 1, 20.0 / om)
+    if vel:
+        # scales: the speed for v_r, r times it for l_theta, R times it for l_phi (the
+        # components start at the gas motion, so v_r and l_theta are small themselves)
+        Rn = np.hypot(x, y)
+        speed = np.abs(v[2] / Rn)
+        for a, k, sc in zip(v, ("vr", "lth", "lph"), (speed, speed * np.hypot(Rn, z), speed * Rn)):
+            err = np.abs(got[k] - a).max() / sc.max()
+            assert err < 1e-6, (k, err)
     L = ins["params"]["box_x"] if geometry == "patch" else 0.0
 
     def diff(a, b):
