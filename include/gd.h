@@ -249,7 +249,10 @@ gd_status gd_sample_collisions(gd_ctx* ctx, int32_t* ev_count_out, uint32_t* ev_
  * instance's last dt_exe) for every particle of every global-disk instance:
  * drift half a step, exact linear-drag kick toward the gas velocity with
  * gravity and the angular-momentum forces at the midpoint, drift the second
- * half in mirrored order.  Needs vr, lth, lph in the config. */
+ * half in mirrored order.  Needs vr, lth, lph in the config.  GD_MIXED: the
+ * drifts rotate the FP64 position by FP32 angle increments (about z by
+ * h l_phi / R^2, in the meridional plane by h l_theta / r^2) and scale it by
+ * 1 + h v_r / r; the forces are FP64, the gas disk and the drag factor FP32. */
 gd_status gd_push_staggered(gd_ctx* ctx, double dt);
 
 /* Sect. 2.4: one Euler-Maruyama dust diffusion step of length dt (dt < 0: each

@@ -54,6 +54,93 @@ __global__ void k_push(long long N, int n_inst, const long long* __restrict__ of
   lph[i] = LP;
 }
 
+// Mixed form of the same step without FP64 transcendentals.  The position stays FP64 and
+// each drift applies its angle increments as rotations: dphi = h l_phi / R^2 about the z
+// axis and dtheta = h l_theta / r^2 in the meridional plane, through cos a - 1 =
+// -2 sin^2(a/2) and sin a in FP32, then the radial step as the factor 1 + h v_r / r.  The
+// kick takes the forces in FP64 from direction cosines (algebraic), the gas disk, t_s and
+// the relaxation factor k in FP32, and the gas angular momentum sqrt(1 - 2 eta) sqrt(GM R)
+// in FP64 so that l_phi,g - l_phi keeps its accuracy.
+__device__ __forceinline__ void drift_f(double h, double& X, double& Y, double& Z, double VR, double LT,
+                                        double LP, bool first_half) {
+  auto phi = [&]() {
+    const double R2 = X * X + Y * Y;
+    const float dph = (float)(h * LP) / (float)R2;
+    const float s2 = sinf(0.5f * dph);
+    const double c1 = (double)(-2.0f * s2 * s2), s1 = (double)sinf(dph);
+    const double Xr = X + (c1 * X - s1 * Y), Yr = Y + (c1 * Y + s1 * X);
+    X = Xr;
+    Y = Yr;
+  };
+  auto theta = [&]() {
+    const double R = sqrt(X * X + Y * Y), r2 = R * R + Z * Z;
+    const float dth = (float)(h * LT) / (float)r2;
+    const float t2 = sinf(0.5f * dth);
+    const double ct = (double)(-2.0f * t2 * t2), st = (double)sinf(dth);
+    // theta from +z: R' = R cos + Z sin, Z' = Z cos - R sin
+    const double dR = ct * R + st * Z, dZ = ct * Z - st * R;
+    const double f = 1.0 + dR / R;
+    X *= f;
+    Y *= f;
+    Z += dZ;
+  };
+  auto radius = [&]() {
+    const double r = sqrt(X * X + Y * Y + Z * Z);
+    const double f = 1.0 + h * VR / r;
+    X *= f;
+    Y *= f;
+    Z *= f;
+  };
+  // first half: phi, theta (both at the old radius), radius; second half mirrored
+  if (first_half) { phi(); theta(); radius(); }
+  else { radius(); theta(); phi(); }
+}
+
+__global__ void k_push_f(long long N, int n_inst, const long long* __restrict__ off,
+                         const InstDev* __restrict__ P, const StateDev* __restrict__ st, double dt_in,
+                         double* x, double* y, double* z, double* vr, double* lth, double* lph,
+                         const double* __restrict__ s) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int b = inst_of(off, n_inst, i);
+  const InstDev& p = P[b];
+  if (p.geometry != GD_GEOM_DISK) return;
+  const double dt = dt_in < 0.0 ? st[b].dt_exe : dt_in;
+  const double h = 0.5 * dt;
+  double X = x[i], Y = y[i], Zc = z[i], VR = vr[i], LT = lth[i], LP = lph[i];
+  drift_f(h, X, Y, Zc, VR, LT, LP, true);
+  // kick at the midpoint
+  const double R2 = X * X + Y * Y, R = sqrt(R2), r = sqrt(R2 + Zc * Zc);
+  const double ir = 1.0 / r, sth = R * ir, cth = Zc * ir, ir2 = ir * ir;
+  // f_r = -GM/r^2 + l_theta^2/r^3 + l_phi^2/(r^3 sin^2 theta), r^3 sin^2 theta = r R^2
+  const double fr = (-p.GM + LT * LT * ir + LP * LP * r / R2) * ir2;
+  const double fth = LP * LP * cth * ir2 / (sth * sth * sth);
+  // the gas disk at the midpoint in FP32 (the forms of the FP32 diffusion coefficients)
+  const float Rf = (float)R, Zf = (float)Zc;
+  const float Om = sqrtf(p.f_GM / Rf) / Rf;
+  const float xr = Rf / p.f_r0;
+  const float cs = sqrtf((float)(kKB / (kMu * kMH)) * (p.f_T0 * powf(xr, p.f_q)));
+  const float hg = cs / Om / Rf;
+  const float rf = sqrtf(Rf * Rf + Zf * Zf);
+  const float omr = Zf * Zf / (rf * (rf + Rf));
+  const float eta = -0.5f * ((p.f_p + 0.5f * p.f_q - 1.5f) * hg * hg + p.f_q * omr);
+  const float gst = 3.14159265f * p.f_rho_s / (4.0f * p.f_sigma0 * powf(xr, p.f_p)) * expf(omr / (hg * hg));
+  const float gam = Om / (gst * (float)s[i]);
+  const float kf = gam > 0.0f ? -expm1f(-(float)dt * gam) / gam : (float)dt;
+  const double k = (double)kf, kg = (double)(kf * gam);
+  const double ygph = sqrt(1.0 - 2.0 * (double)eta) * sqrt(p.GM * R);
+  VR = VR - kg * VR + k * fr;
+  LT = LT - kg * LT + k * fth;
+  LP = LP + kg * (ygph - LP);
+  drift_f(h, X, Y, Zc, VR, LT, LP, false);
+  x[i] = X;
+  y[i] = Y;
+  z[i] = Zc;
+  vr[i] = VR;
+  lth[i] = LT;
+  lph[i] = LP;
+}
+
 // ---------------------------------------------------------------- dust diffusion
 // Sect. 2.4.  Coefficients at (R, Z) for a grain of diameter s: D_a = nu/(Sc_a (1+St^2)),
 // nu = alpha c_s H_g at R, and the dt coefficients of the R and Z steps.  With
@@ -433,8 +520,12 @@ __global__ void k_out_lam(long long N, const int* __restrict__ rank_of, const do
 cudaError_t launch_push(gd_ctx* c, double dt) {
   time_begin(c, 5);
   int blocks = (int)((c->N + 255) / 256);
-  k_push<<<blocks, 256, 0, c->stream>>>(c->N, c->n_inst, c->d_off, c->d_inst, c->d_state, dt, c->x, c->y,
-                                         c->z, c->vr, c->lth, c->lph, c->s);
+  if (c->precision == GD_MIXED)
+    k_push_f<<<blocks, 256, 0, c->stream>>>(c->N, c->n_inst, c->d_off, c->d_inst, c->d_state, dt, c->x, c->y,
+                                            c->z, c->vr, c->lth, c->lph, c->s);
+  else
+    k_push<<<blocks, 256, 0, c->stream>>>(c->N, c->n_inst, c->d_off, c->d_inst, c->d_state, dt, c->x, c->y,
+                                          c->z, c->vr, c->lth, c->lph, c->s);
   time_end(c);
   c->launches += 1;
   c->moved = true;

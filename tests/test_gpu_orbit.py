@@ -20,18 +20,18 @@ pytestmark = pytest.mark.gpu
 G = 6.674e-8
 
 
-def _orbit_session(gd, n=4):
+def _orbit_session(gd, n=4, precision=0):
     # a cold disk (T0 = 1e-12 K: c_s ~ 6e-3 v_K, so eta ~ 5e-5 and the gas velocity is
     # defined everywhere on the orbit)
     P = W._base_params(geometry=W.DISK, K=2, r0=1.0, M_star=1.0 / G, sigma0=1.0, T0=1e-12, rho_s=1.0,
                        R_in=0.05, R_out=20.0, dt_coll=1.0, dt_fn_max=1.0)
     ins = dict(params=P, x=np.full(n, 0.5), y=np.zeros(n), z=np.zeros(n), s=np.full(n, 1e20),
                M=np.full(n, 1.0 / n), vr=np.zeros(n), lth=np.zeros(n), lph=np.full(n, math.sqrt(3.0) / 2.0))
-    return gd.Session([ins], precision=gd.GD_FP64, velocities=True)
+    return gd.Session([ins], precision=precision, velocities=True)
 
 
-def _max_energy_error(gd, steps_per_orbit, orbits, samples_per_orbit=16):
-    sess = _orbit_session(gd)
+def _max_energy_error(gd, steps_per_orbit, orbits, precision=0, samples_per_orbit=16):
+    sess = _orbit_session(gd, precision=precision)
     dt = 2 * math.pi / steps_per_orbit
     every = steps_per_orbit // samples_per_orbit
     worst = 0.0
@@ -50,10 +50,12 @@ def _max_energy_error(gd, steps_per_orbit, orbits, samples_per_orbit=16):
     return worst
 
 
-def test_eccentric_orbit_energy(gd):
-    e160 = _max_energy_error(gd, 160, 20)
-    e320 = _max_energy_error(gd, 320, 20)
+@pytest.mark.parametrize("precision", [0, 1])
+def test_eccentric_orbit_energy(gd, precision):
+    """Both forms; the mixed form drifts by rotations with FP32 angle increments."""
+    e160 = _max_energy_error(gd, 160, 20, precision)
+    e320 = _max_energy_error(gd, 320, 20, precision)
     # second order: halving dt divides the error by about 4
     assert 3.0 < e160 / e320 < 5.0, (e160, e320)
-    e640 = _max_energy_error(gd, 640, 100)
+    e640 = _max_energy_error(gd, 640, 100, precision)
     assert e640 < 1e-4, e640

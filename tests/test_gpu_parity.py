@@ -209,6 +209,38 @@ def test_graph_replay_matches_calls(gd):
     b.close()
 
 
+def test_mixed_push_close_to_oracle(gd, oracle):
+    """Mixed form of the push: the drifts as rotations by FP32 angle increments applied to
+    the FP64 position, the forces in FP64, the gas disk and the drag factor in FP32.  The
+    positions agree with the oracle's to 1e-7 of the radius, the velocities to 1e-6 of the
+    speed scale (v_r), r times it (l_theta) and R times it (l_phi)."""
+    ins = W.disk_instance(4096, seed=6, K=32, velocities=True, sizes=("lognormal", 1.0, 0.5))
+    rng = np.random.default_rng(3)
+    R0 = np.hypot(ins["x"], ins["y"])
+    ins["vr"] = rng.normal(0.0, 3e3, 4096)
+    ins["lth"] = rng.normal(0.0, 3e3, 4096) * R0
+    sess = gd.Session([ins], precision=gd.GD_MIXED, velocities=True)
+    dt = 3.0e7
+    sess.push_staggered(dt)
+    sess.stats()
+    P = oracle.params(ins["params"])
+    x, y, z = ins["x"].copy(), ins["y"].copy(), ins["z"].copy()
+    vr, lth, lph = ins["vr"].copy(), ins["lth"].copy(), ins["lph"].copy()
+    oracle.push(P, x, y, z, vr, lth, lph, ins["s"], dt, drag=True)
+    got = {k: sess.t[k].cpu().numpy() for k in ("x", "y", "z", "vr", "lth", "lph")}
+    sess.close()
+    R = np.hypot(x, y)
+    for k, ref in (("x", x), ("y", y), ("z", z)):
+        assert np.abs(got[k] - ref).max() <= 1e-7 * R.max(), k
+    speed = np.abs(lph / R)
+    for k, ref, sc in (("vr", vr, speed), ("lth", lth, speed * np.hypot(R, z)), ("lph", lph, speed * R)):
+        err = (np.abs(got[k] - ref) / sc).max()
+        assert err < 1e-6, (k, err)
+    # the particles did move and the velocities changed
+    assert np.abs(got["x"] - ins["x"]).max() > 1e3 * 1e-7 * R.max()
+    assert np.abs(got["vr"] - ins["vr"]).max() > 1e-3 * np.abs(ins["vr"]).max()
+
+
 def test_push_matches_oracle(gd, oracle):
     ins = W.disk_instance(4096, seed=6, K=32, velocities=True, sizes=("lognormal", 1.0, 0.5))
     sess = gd.Session([ins], precision=gd.GD_FP64, velocities=True)
