@@ -738,6 +738,9 @@ static cudaError_t prepare_cap(int K) {
 cudaError_t knn_prepare(gd_ctx* c) {
   cudaError_t e = prepare_cap<false>(c->K);
   if (e == cudaSuccess && c->precision == GD_MIXED) e = prepare_cap<true>(c->K);
+  // the wider buffer of a build after particles moved (K <= 32)
+  if (e == cudaSuccess && c->K <= 32) e = prepare_cap<false>(48);
+  if (e == cudaSuccess && c->K <= 32 && c->precision == GD_MIXED) e = prepare_cap<true>(48);
   return e;
 }
 
@@ -747,9 +750,10 @@ static cudaError_t launch_both(gd_ctx* c, const KnnArgs& A) {
 }
 
 template <bool kMixed>
-static cudaError_t launch_cap(gd_ctx* c, const KnnArgs& A) {
-  // buffer capacity: the K-1 members plus room for the radius margin
-  if (c->K <= 32) return launch_both<40, kMixed>(c, A);
+static cudaError_t launch_cap(gd_ctx* c, const KnnArgs& A, bool wide) {
+  // buffer capacity: the K-1 members plus room for the radius margin; after particles
+  // moved, the K-th distance is uncertain and K <= 32 takes the 64-entry buffer
+  if (c->K <= 32) return wide ? launch_both<64, kMixed>(c, A) : launch_both<40, kMixed>(c, A);
   if (c->K <= 48) return launch_both<64, kMixed>(c, A);
   if (c->K <= 80) return launch_both<96, kMixed>(c, A);
   if (c->K <= 128) return launch_both<144, kMixed>(c, A);
@@ -781,21 +785,22 @@ cudaError_t launch_knn(gd_ctx* c) {
   // static particles: d_i of the last build is exact and 1.02 d_i holds the K-1 others; after
   // a move the K-th distance scatters around it, so the first radius aims at the middle of
   // the buffer's range instead
+  const bool wide = c->moved;
   A.rfac = c->moved ? 1.045f : 1.02f;
   c->moved = false;
   time_begin(c, 1);
   cudaError_t e = cudaSuccess;
   if (c->precision == GD_MIXED) {
     e = cudaMemsetAsync(A.redo_n, 0, sizeof(unsigned long long), c->stream);
-    if (e == cudaSuccess) e = launch_cap<true>(c, A);
+    if (e == cudaSuccess) e = launch_cap<true>(c, A, wide);
     // the queries the FP32 keys could not decide, in the FP64 form
     KnnArgs B = A;
     B.list = c->d_redo;
     B.list_n = A.redo_n;
-    if (e == cudaSuccess) e = launch_cap<false>(c, B);
+    if (e == cudaSuccess) e = launch_cap<false>(c, B, wide);
     c->launches += 2;
   } else {
-    e = launch_cap<false>(c, A);
+    e = launch_cap<false>(c, A, wide);
     c->launches += 1;
   }
   time_end(c);
