@@ -93,12 +93,12 @@ def algo_bytes(kernel, K, mixed):
 # bench command (dram__bytes_read.sum + dram__bytes_write.sum), per particle.  The records
 # hold only while the sources the measured kernels compile from (their files and the shared
 # headers) have the content they had at the capture.
-TRAFFIC_CSRC_SHA256 = "0ac13823c8139b6baa27140c4c9053c7eb29e7e9e04e749f5277041ff62dc828"
+TRAFFIC_CSRC_SHA256 = "4fcd75968df81bea2d8c6b7a641da2c66715ed9e07873d5bb6d5912d07416acc"
 TRAFFIC = {
-    "knn": {"workload": "disk22", "bytes_per_particle": 427.020},
-    "rates": {"workload": "disk22", "bytes_per_particle": 296.903},
-    "sample": {"workload": "disk22", "bytes_per_particle": 108.518},
-    "cells": {"workload": "disk22", "bytes_per_particle": 398.431},
+    "knn": {"workload": "disk22", "bytes_per_particle": 427.318},
+    "rates": {"workload": "disk22", "bytes_per_particle": 297.257},
+    "sample": {"workload": "disk22", "bytes_per_particle": 108.494},
+    "cells": {"workload": "disk22", "bytes_per_particle": 399.111},
 }
 
 
