@@ -44,6 +44,25 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def pipe_peaks():
+    """FP32 and FP64 FMA-pipe peaks of this GPU (TFLOP/s), measured by the FMA-chain
+    microbenchmark in libgdpeaks.so (CUDA events, best of five launches)."""
+    import ctypes
+    lib = ctypes.CDLL(os.path.join(ROOT, "paper_2609_35967_gb300", "libgdpeaks.so"))
+    lib.gdp_fma_tflops.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    lib.gdp_fma_tflops.restype = ctypes.c_int
+    out = {}
+    for name, fp64 in (("fp32_tflops", 0), ("fp64_tflops", 1)):
+        v, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        rc = lib.gdp_fma_tflops(fp64, ctypes.byref(v), ctypes.byref(ms))
+        if rc != 0:
+            raise RuntimeError(f"gdp_fma_tflops({fp64}) failed: {rc}")
+        out[name] = v.value
+    out["how"] = ("FMA chains (8 independent per thread, 256-thread blocks, 8 per SM), "
+                  "2 flops per FMA, CUDA events, best of 5 launches")
+    return out
+
+
 def make_workload(name, rank=0):
     from paper_2609_35967_gb300 import workloads as W
     if name == "disk22":
@@ -451,6 +470,8 @@ def main():
                     help="time the dust diffusion step alone (one JSON line, 1 GPU)")
     ap.add_argument("--split-step", action="store_true",
                     help="time whole split timesteps with gd_timestep (one JSON line, 1 GPU)")
+    ap.add_argument("--peaks", action="store_true",
+                    help="measure the FP32 / FP64 FMA-pipe peaks alone (one JSON line, 1 GPU)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -482,6 +503,12 @@ def main():
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return
 
+    if args.peaks:
+        if rank == 0:
+            import torch
+            torch.cuda.init()
+            print(json.dumps({"pipe_peaks": pipe_peaks()}))
+        return
     if args.diffusion:
         if rank == 0:
             print(json.dumps(diffusion_line(args)))

@@ -336,6 +336,16 @@ gd_status gd_timestep(gd_ctx* ctx, const gd_dt_rule* rule, double* dt_out_host, 
  * Returns the first device error as a gd_status (GD_OK if none). */
 gd_status gd_stats(gd_ctx* ctx, gd_stats_t* out, gd_instance_stats* inst_out);
 
+/* Sect. 2.5.3: the controller bins of one instance's last interval choice.  A_b and B_b
+ * are the mass-weighted means over a bin's particles of sum_o lambda*_io <J_io> and of
+ * sum_o lambda*_io <J_io^2> (J = |ln(s'/s)| of each outcome channel o), the bins in
+ * ascending size; dt_req took min_b eps C / A_b and min_b eps^2 C^2 / B_b.  The fine-bin
+ * sums behind them are formed in a fixed order, so they do not depend on scheduling.
+ * Synchronises the stream.  instance: 0 .. n_instances - 1 (else GD_ERR_ARG).
+ * A_out, B_out: HOST [96] or NULL, bins past n_groups are 0; n_groups_out: HOST or NULL. */
+gd_status gd_controller_bins(gd_ctx* ctx, int32_t instance, double* A_out, double* B_out,
+                             int32_t* n_groups_out);
+
 /* Runs n whole intervals (build, rates, sample and, if push != 0, push with
  * dt_exe) by replaying a CUDA graph of one interval captured on first use
  * (captures again if the arguments change).  Asynchronous. */
@@ -376,13 +386,18 @@ const char* gd_status_string(gd_status code);
  *
  * Limits: n <= GD_FIXED_MAX_PARTICLES (else GD_ERR_CAPACITY, nothing runs),
  * 2 <= K <= GD_FIXED_MAX_K and K <= n, params->model == GD_MODEL_3D (else
- * GD_ERR_ARG).
+ * GD_ERR_ARG).  A query whose search finds no K-1 others within its bounded
+ * number of radius growths (a non-finite coordinate) gets a row of -1 and
+ * d_out = -1; the call is asynchronous and still returns GD_OK, so a caller that
+ * can meet such input checks row[0] >= 0 after synchronising.
  * The first call on a device looks up the array's device address with that
- * device current (cudaGetSymbolAddress); make that first call before any
- * stream capture.  All calls share the one array, which keeps the last call's
- * contents (each call clears what must start at zero): calls that overlap on
- * the GPU -- on different streams, or from different threads -- race, so
- * serialise them.  Asynchronous on the stream like the other calls.
+ * device current (cudaGetSymbolAddress) and keeps it for the life of the
+ * process; make that first call before any stream capture, and do not use the
+ * library across a cudaDeviceReset, which would leave the kept address stale.
+ * All calls share the one array, which keeps the last call's contents (each call
+ * clears what must start at zero): calls that overlap on the GPU -- on different
+ * streams, or from different threads -- race, so serialise them.  Asynchronous
+ * on the stream like the other calls.
  * ------------------------------------------------------------------------- */
 #define GD_FIXED_MAX_PARTICLES 65536
 #define GD_FIXED_MAX_K 64

@@ -380,6 +380,12 @@ int gdo_fine_bin(double s) {
 void gdo_choose_interval(const gdo_params* P, int64_t n, const double* s, const double* M,
                          const double* mA, const double* mB, gdo_state* st,
                          int32_t* group_of) {
+  gdo_choose_interval_ab(P, n, s, M, mA, mB, st, group_of, NULL, NULL);
+}
+
+void gdo_choose_interval_ab(const gdo_params* P, int64_t n, const double* s, const double* M,
+                            const double* mA, const double* mB, gdo_state* st,
+                            int32_t* group_of, double* A_b, double* B_b) {
   int64_t cnt[GDO_NFINE];
   int gid[GDO_NFINE];
   double sM[GDO_NFINE], sA[GDO_NFINE], sB[GDO_NFINE];
@@ -420,9 +426,15 @@ void gdo_choose_interval(const gdo_params* P, int64_t n, const double* s, const 
   double remain = ldexp((double)st->remain_ticks, -60) * P->dt_coll;
   double dt_cap = remain < P->dt_fn_max ? remain : P->dt_fn_max;
   double dt_ab = HUGE_VAL;     /* the moment constraints (floating sums) */
+  for (int g = 0; g < GDO_NFINE; ++g) {
+    if (A_b) A_b[g] = 0.0;
+    if (B_b) B_b[g] = 0.0;
+  }
   for (int g = 0; g < ng; ++g) {
     double A = sA[g] / sM[g];
     double B = sB[g] / sM[g];
+    if (A_b) A_b[g] = A;
+    if (B_b) B_b[g] = B;
     if (A > 0.0) { double t = P->eps * C / A; if (t < dt_ab) dt_ab = t; }
     if (B > 0.0) { double t = P->eps * P->eps * C * C / B; if (t < dt_ab) dt_ab = t; }
   }
@@ -691,7 +703,8 @@ int gdo_interval_step(const gdo_params* P, int64_t n, const double* x, const dou
   }
   st->near_dt = 0;
   st->near_audit = 0;
-  gdo_choose_interval(P, n, s0, M, mA, mB, st, grp);
+  gdo_choose_interval_ab(P, n, s0, M, mA, mB, st, grp, out ? out->A_b : NULL,
+                         out ? out->B_b : NULL);
   st->events = 0;
   st->near_draw = 0;
   for (int64_t i = 0; i < n; ++i) {

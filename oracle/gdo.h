@@ -117,6 +117,9 @@ typedef struct {
   uint32_t* ev_hash; /* [n]   hash of the chosen (slot, channel) sequence */
   int32_t* near;     /* [n]   near ties met while sampling the particle */
   double*  jsum;     /* [n]   realised sum of |ln(s'/s)| over the interval's events */
+  double*  A_b;      /* [GDO_NFINE] A_b of each controller bin of the interval choice
+                        (entries past n_groups are 0) */
+  double*  B_b;      /* [GDO_NFINE] B_b likewise */
 } gdo_outputs;
 
 void   gdo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
@@ -133,6 +136,10 @@ void   gdo_pair(const gdo_params* P, const gdo_gas* g, double s_i, double m_i,
 int    gdo_fine_bin(double s);
 void   gdo_choose_interval(const gdo_params* P, int64_t n, const double* s, const double* M,
                            const double* mA, const double* mB, gdo_state* st, int32_t* group_of);
+/* The same, also returning A_b and B_b of every controller bin (NULL: not written). */
+void   gdo_choose_interval_ab(const gdo_params* P, int64_t n, const double* s, const double* M,
+                              const double* mA, const double* mB, gdo_state* st, int32_t* group_of,
+                              double* A_b, double* B_b);
 void   gdo_audit(const gdo_params* P, int64_t n, const double* M, const double* jsum,
                  const int32_t* group_of_particle, int32_t n_groups, gdo_state* st);
 int    gdo_sample_one(const gdo_params* P, const gdo_gas* g, int64_t i, const int32_t* nbr,

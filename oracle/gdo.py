@@ -79,7 +79,8 @@ class Outputs(C.Structure):
     _fields_ = [("nbr", C.c_void_p), ("d", C.c_void_p), ("V", C.c_void_p),
                 ("lam", C.c_void_p), ("mA", C.c_void_p), ("mB", C.c_void_p),
                 ("chan", C.c_void_p), ("ev_count", C.c_void_p), ("ev_hash", C.c_void_p),
-                ("near", C.c_void_p), ("jsum", C.c_void_p)]
+                ("near", C.c_void_p), ("jsum", C.c_void_p), ("A_b", C.c_void_p),
+                ("B_b", C.c_void_p)]
 
 
 def _p(a):
@@ -109,6 +110,7 @@ def lib():
             L.gdo_fine_bin.argtypes = [dbl]
             L.gdo_fine_bin.restype = C.c_int
             L.gdo_choose_interval.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
+            L.gdo_choose_interval_ab.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
             L.gdo_audit.argtypes = [vp, i64, vp, vp, vp, C.c_int32, vp]
             L.gdo_interval_step.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp]
             L.gdo_rates_subset.argtypes = [vp, i64, vp, vp, vp, vp, vp, i64, vp, vp, vp,
@@ -228,11 +230,17 @@ def fine_bin(s: float) -> int:
     return lib().gdo_fine_bin(s)
 
 
-def choose_interval(P: Params, st: State, s, M, mA, mB) -> np.ndarray:
+def choose_interval(P: Params, st: State, s, M, mA, mB, moments=False):
+    """Interval choice of one instance; returns the controller bin of each particle, and
+    with moments=True also (A_b, B_b) of the first st.n_groups bins."""
     s, M, mA, mB = (np.ascontiguousarray(a, dtype=np.float64) for a in (s, M, mA, mB))
     grp = np.zeros(len(s), dtype=np.int32)
-    lib().gdo_choose_interval(C.byref(P), len(s), _p(s), _p(M), _p(mA), _p(mB),
-                              C.byref(st), _p(grp))
+    A = np.zeros(NFINE)
+    B = np.zeros(NFINE)
+    lib().gdo_choose_interval_ab(C.byref(P), len(s), _p(s), _p(M), _p(mA), _p(mB),
+                                 C.byref(st), _p(grp), _p(A), _p(B))
+    if moments:
+        return grp, A[:st.n_groups], B[:st.n_groups]
     return grp
 
 
@@ -251,7 +259,8 @@ def interval_step(P: Params, st: State, x, y, z, s, M, want=("nbr", "d", "V", "l
     shapes = {"nbr": ((n, K), np.int32), "d": (n, np.float64), "V": (n, np.float64),
               "lam": (n, np.float64), "mA": (n, np.float64), "mB": (n, np.float64),
               "chan": ((n, K, 2), np.float64), "ev_count": (n, np.int32),
-              "ev_hash": (n, np.uint32), "near": (n, np.int32), "jsum": (n, np.float64)}
+              "ev_hash": (n, np.uint32), "near": (n, np.int32), "jsum": (n, np.float64),
+              "A_b": (NFINE, np.float64), "B_b": (NFINE, np.float64)}
     res = {k: np.zeros(*shapes[k]) for k in want}
     out = Outputs(**{k: _p(v) for k, v in res.items()})
     rc = lib().gdo_interval_step(C.byref(P), n, _p(x), _p(y), _p(z), _p(s), _p(M),

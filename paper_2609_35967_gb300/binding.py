@@ -87,6 +87,7 @@ SIGNATURES = {
     "gd_run_intervals": ([C.c_void_p, C.c_int32, C.c_int32], C.c_int),
     "gd_status_string": ([C.c_int], C.c_char_p),
     "gd_autotune": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "gd_controller_bins": ([C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "gd_neighbors_fixed": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p,
                             C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
 }
@@ -197,6 +198,13 @@ def gd_autotune(ctx):
     f, xs = C.c_double(0.0), C.c_int32(0)
     _check("gd_autotune", load().gd_autotune(ctx, C.byref(f), C.byref(xs)))
     return f.value, xs.value
+
+
+def gd_controller_bins(ctx, instance):
+    """(A_b, B_b) of one instance's last interval choice, as two lists of n_groups floats."""
+    A, B, n = (C.c_double * 96)(), (C.c_double * 96)(), C.c_int32(0)
+    _check("gd_controller_bins", load().gd_controller_bins(ctx, int(instance), A, B, C.byref(n)))
+    return list(A)[:n.value], list(B)[:n.value]
 
 
 def gd_status_string(code):
@@ -336,6 +344,9 @@ class Session:
 
     def autotune(self):
         return gd_autotune(self.ctx)
+
+    def controller_bins(self, instance=0):
+        return gd_controller_bins(self.ctx, instance)
 
     def stats(self, check=True):
         code, st, inst = gd_stats(self.ctx, self.n_inst)

@@ -15,6 +15,9 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libgd.so")
 SOURCES = ["gd_abi.cu", "k_cells.cu", "k_knn.cu", "k_mc.cu", "k_misc.cu", "gd_noalloc.cu"]
+# FMA-chain microbenchmarks of the FP32 / FP64 pipes (the bench's pipe roofline denominators)
+PEAKS_LIB = os.path.join(HERE, "libgdpeaks.so")
+PEAKS_SRC = "pipe_peaks.cu"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC",
                 "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
@@ -34,10 +37,13 @@ def _inputs():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
-        return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(p) <= t for p in _inputs() + [__file__])
+    for lib in (LIB, PEAKS_LIB):
+        if not os.path.exists(lib):
+            return False
+        t = os.path.getmtime(lib)
+        if not all(os.path.getmtime(p) <= t for p in _inputs() + [__file__]):
+            return False
+    return True
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -55,8 +61,19 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
         return obj, r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
+    def compile_peaks():
+        tmp = PEAKS_LIB + ".tmp%d" % os.getpid()
+        cmd = [nvcc, *ARCH, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+               os.path.join(CSRC, PEAKS_SRC), "-o", tmp]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {PEAKS_SRC}:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, PEAKS_LIB)
+
+    with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES) + 1, os.cpu_count() or 4)) as ex:
+        peaks = ex.submit(compile_peaks)
         results = list(ex.map(compile_one, SOURCES))
+        peaks.result()
     if verbose:
         for _, log in results:
             sys.stderr.write(log)

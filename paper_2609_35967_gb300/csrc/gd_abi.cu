@@ -65,7 +65,8 @@ static void free_all(gd_ctx* c) {
   void* ptrs[] = {c->d_off, c->d_tile_off, c->d_inst, c->d_grid, c->d_state, c->d_bins, c->d_cell_count,
                   c->d_cell_start, c->d_scan_tmp, c->d_cell_of, c->d_slot, c->d_perm, c->d_rank_of,
                   c->d_pos64, c->d_pos32, c->d_snap64, c->d_snap32, c->d_Mr, c->d_dist, c->d_V,
-                  c->d_lam, c->d_nbr, c->d_counters, c->d_sums, c->d_dprev, c->d_redo};
+                  c->d_lam, c->d_nbr, c->d_counters, c->d_sums, c->d_dprev, c->d_redo, c->d_gx,
+                  c->d_pref32, c->d_contrib, c->d_MJ, c->d_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& e : c->ev_pool) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
@@ -160,6 +161,13 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
   ok &= dalloc(&c->d_V, N) == cudaSuccess;
   ok &= dalloc(&c->d_lam, N) == cudaSuccess;
   ok &= dalloc(&c->d_nbr, (size_t)N * c->K) == cudaSuccess;
+  if (c->precision == GD_MIXED) {
+    ok &= dalloc(&c->d_gx, N) == cudaSuccess;
+    ok &= dalloc(&c->d_pref32, N) == cudaSuccess;
+  }
+  ok &= dalloc(reinterpret_cast<Contrib64**>(&c->d_contrib), N) == cudaSuccess;
+  ok &= dalloc(&c->d_MJ, N) == cudaSuccess;
+  ok &= dalloc(&c->d_part, (size_t)kBinQ * kNFine * c->n_tiles) == cudaSuccess;
   ok &= dalloc(&c->d_counters, 16) == cudaSuccess;
   ok &= dalloc(&c->d_sums, 3 * ((size_t)n + c->n_tiles)) == cudaSuccess;
   if (!ok) {
@@ -190,6 +198,7 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
     d.f_r0 = (float)p.r0; d.f_GM = (float)d.GM; d.f_T0 = (float)p.T0; d.f_q = (float)p.q;
     d.f_p = (float)p.p; d.f_sigma0 = (float)p.sigma0; d.f_alpha = (float)p.alpha;
     d.f_rho_s = (float)p.rho_s; d.f_vfrag = (float)p.v_frag; d.f_m0 = (float)p.m0;
+    d.f_smin = (float)p.s_min;
     d.diff_mode = p.diff_mode;
     d.diff_chi = p.diff_chi;
     d.Sc_R = p.Sc_R > 0.0 ? p.Sc_R : 1.0;
@@ -468,6 +477,19 @@ extern "C" gd_status gd_stats(gd_ctx* c, gd_stats_t* out, gd_instance_stats* ins
   if (out->status & GD_ST_EVENT_CAP) return GD_ERR_EVENT_CAP;
   if (out->status & GD_ST_CAPACITY) return GD_ERR_CAPACITY;
   if (out->status & GD_ST_TIMEOUT) return GD_ERR_TIMEOUT;
+  return GD_OK;
+}
+
+extern "C" gd_status gd_controller_bins(gd_ctx* c, int32_t instance, double* A_out, double* B_out,
+                                        int32_t* n_groups_out) {
+  if (!c || instance < 0 || instance >= c->n_inst) return GD_ERR_ARG;
+  BinsDev h;
+  cudaError_t e = cudaMemcpyAsync(&h, c->d_bins + instance, sizeof(BinsDev), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return GD_ERR_CUDA;
+  if (A_out) std::memcpy(A_out, h.gA, sizeof(h.gA));
+  if (B_out) std::memcpy(B_out, h.gB, sizeof(h.gB));
+  if (n_groups_out) *n_groups_out = h.ngroups;
   return GD_OK;
 }
 

@@ -37,7 +37,7 @@ struct InstDev {
   long long off, n;
   double k6;          // 6 / (pi rho_s)
   // FP32 copies of the parameters the mixed form's per-particle gas disk uses
-  float f_r0, f_GM, f_T0, f_q, f_p, f_sigma0, f_alpha, f_rho_s, f_vfrag, f_m0;
+  float f_r0, f_GM, f_T0, f_q, f_p, f_sigma0, f_alpha, f_rho_s, f_vfrag, f_m0, f_smin;
   // dust diffusion (Sect. 2.4)
   int diff_mode, diff_chi;
   double Sc_R, Sc_Z, Sc_phi, D0;
@@ -88,12 +88,48 @@ struct StateDev {
   unsigned long long bmin[3], bmax[3];
 };
 
-// Fine-bin accumulators of one instance (doubles; counts exact below 2^53).
+// Fine-bin sums of one instance (doubles; counts exact below 2^53), in this order (the
+// tile reduction addresses them as quantity q of the block cnt, sM, sA, sB, sJ), and the
+// controller bins of the last interval choice: the fine bins' group ids and each group's
+// A_b and B_b.
+constexpr int kBinQ = 5;          // cnt, sM, sA, sB, sJ
 struct BinsDev {
   double cnt[kNFine], sM[kNFine], sA[kNFine], sB[kNFine], sJ[kNFine];
+  double gA[kNFine], gB[kNFine];
   int gid[kNFine];
   int ngroups;
   int pad;
+};
+
+// Per-block tiles of the per-particle passes: tile t covers [lo, hi) of one instance (at
+// most kTile particles, never straddling an instance).  The tile table is derived from the
+// offsets: block t belongs to the instance whose tile range contains t.
+constexpr int kTile = 4096;
+struct TileMap {
+  const long long* off;
+  int n_inst;
+  const long long* tile_off;   // [n_inst + 1] first tile of each instance
+};
+
+__device__ __forceinline__ bool tile_range(const TileMap& tm, int tile, int& b, long long& lo, long long& hi) {
+  int l = 0, h = tm.n_inst - 1;
+  while (l < h) {
+    int mid = (l + h + 1) >> 1;
+    if (tm.tile_off[mid] <= tile) l = mid; else h = mid - 1;
+  }
+  b = l;
+  long long t = tile - tm.tile_off[b];
+  lo = tm.off[b] + t * kTile;
+  hi = min(lo + kTile, tm.off[b + 1]);
+  return lo < hi;
+}
+
+// One particle's contribution to the fine-bin sums of the interval choice (FP64 form):
+// M_i, M_i pref sum_o lambda*_io <J_io>, likewise <J_io^2>, and the fine bin.  The mixed
+// form holds the same in a float4 (M, MA, MB, bin bits).
+struct Contrib64 {
+  double M, MA, MB;
+  long long fbin;
 };
 
 struct Pos64 {

@@ -54,6 +54,13 @@ struct gd_ctx {
   double* d_V = nullptr;                // [N] V_i, rank order
   double* d_lam = nullptr;              // [N] lambda*_i, rank order
   int* d_nbr = nullptr;                 // [N*K] ranks
+  float4* d_gx = nullptr;               // [N] mixed form: FP32 (R, Z, M) and the fine bin (bits)
+  float* d_pref32 = nullptr;            // [N] mixed form: FP32 rate prefactor
+  void* d_contrib = nullptr;            // [N] rank order: each particle's fine-bin contribution
+                                        // (FP64 form gd::Contrib64, mixed form float4)
+  double* d_MJ = nullptr;               // [N] caller order: M_i times the interval's realised
+                                        // sum of |ln s'/s|
+  double* d_part = nullptr;             // [kBinQ * kNFine * n_tiles] per-tile fine-bin partial sums
   unsigned long long* d_counters = nullptr;  // [16] spare device counters
   double* d_sums = nullptr;             // [3 * (n_inst + n_tiles)] gd_stats sums, then per-tile partials
 
@@ -80,6 +87,14 @@ struct gd_ctx {
 };
 
 namespace gd {
+inline TileMap tile_map(const gd_ctx* c) {
+  TileMap tm;
+  tm.off = c->d_off;
+  tm.n_inst = c->n_inst;
+  tm.tile_off = c->d_tile_off;
+  return tm;
+}
+
 // launchers (each returns cudaGetLastError() of its launches)
 cudaError_t launch_cells(gd_ctx* c);
 cudaError_t launch_knn(gd_ctx* c);

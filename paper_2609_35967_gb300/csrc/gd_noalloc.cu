@@ -100,7 +100,11 @@ __global__ void fk_bounds(unsigned char* b, const double* __restrict__ x, const 
 }
 
 // One thread: a uniform grid over the bounds (patch: the periodic box in x and y), at
-// most kMaxCells cells.
+// most kMaxCells cells.  The cell edge starts from cell_size or (volume / n)^(1/3), made
+// finite and positive (coincident particles give a zero volume), and grows until the grid
+// fits; if it still does not fit (a cell_size far below the extent, or non-finite bounds),
+// one cell per axis keeps every cell index inside the scratch arrays, and the search stays
+// exact, only slower.
 __global__ void fk_grid(unsigned char* b, int geometry, double box_x, double box_y, double cell_size,
                         long long n) {
   Ptr p = ptrs(b);
@@ -116,8 +120,12 @@ __global__ void fk_grid(unsigned char* b, int geometry, double box_x, double box
   double vol = 1.0;
   for (int a = 0; a < 3; ++a) vol *= fmax(ext[a], 1e-6 * emax + 1e-300);
   double c = cell_size > 0.0 ? cell_size : cbrt(vol / (double)n);
+  if (!(c > 0.0) || !isfinite(c)) c = emax > 0.0 && isfinite(emax) ? emax : 1.0;
+  long long cells = 0;
+  bool finite = true;
   for (int attempt = 0; attempt < 60; ++attempt) {
-    long long cells = 1;
+    cells = 1;
+    finite = true;
     for (int a = 0; a < 3; ++a) {
       const bool pa = per && a < 2;
       const double e = pa ? ext[a] : ext[a] * (1.0 + 1e-9) + 1e-12 * emax + 1e-300;
@@ -129,9 +137,20 @@ __global__ void fk_grid(unsigned char* b, int geometry, double box_x, double box
       g.box[a] = pa ? ext[a] : 0.0;
       g.dim[a] = dim;
       cells *= dim;
+      finite = finite && isfinite(g.lo[a]) && isfinite(g.cs[a]) && isfinite(g.inv[a]);
     }
     if (cells <= kMaxCells) break;
-    c *= 1.2;
+    c *= 2.0;
+  }
+  if (cells > kMaxCells || !finite) {
+    for (int a = 0; a < 3; ++a) {
+      const bool pa = per && a < 2;
+      const double e = pa ? ext[a] : ext[a] * (1.0 + 1e-9) + 1e-12 * emax + 1e-300;
+      g.lo[a] = isfinite(lo[a]) ? lo[a] : 0.0;
+      g.cs[a] = isfinite(e) && e > 0.0 ? e : 1.0;
+      g.inv[a] = 1.0 / g.cs[a];
+      g.dim[a] = 1;
+    }
   }
   g.per = per ? 1 : 0;
 }
@@ -352,7 +371,9 @@ __global__ void __launch_bounds__(256) fk_knn(unsigned char* b, long long n, int
   }
 }
 
-// Device address of the fixed array, looked up once per device (with that device current).
+// Device address of the fixed array, looked up once per device (with that device current)
+// and kept for the life of the process: a cudaDeviceReset, which replaces the device's
+// primary context, leaves the kept address stale, so the library is not used across one.
 static std::mutex g_mu;
 static void* g_addr[256];
 

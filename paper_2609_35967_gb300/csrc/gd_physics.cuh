@@ -50,6 +50,15 @@ __device__ __forceinline__ Gas gas_at(const InstDev& P, double x, double y, doub
   return gas_RZ(P, R, z);
 }
 
+// Per-particle prefactor of the pair rates, lambda_ij = pref * (pair rate in kernel units):
+// physical kernel pi / (4 V_i) (Eq. rate with K_ij = pi (s_i + s_j)^2 dv / 4), in the mixed
+// form pi 2^64 / (4 V_i) because its FP32 snapshot holds N_j 2^-64; the test kernels of
+// Appendix A 1 / (t0 N_K) with V_i = 1.
+__device__ __forceinline__ double rate_prefactor(const InstDev& P, double V, int K, bool mixed) {
+  if (P.kernel_mode != GD_KERNEL_PHYSICAL) return 1.0 / (P.t0 * (double)K);
+  return mixed ? kPi * 0x1p64 / (4.0 * V) : kPi / (4.0 * V);
+}
+
 __device__ __forceinline__ double grain_mass(const InstDev& P, double s) {
   return kPi * P.rho_s * s * s * s / 6.0;
 }

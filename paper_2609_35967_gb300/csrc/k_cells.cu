@@ -12,31 +12,7 @@
 
 namespace gd {
 
-constexpr int kTile = 4096;       // particles per block in the per-particle passes
 constexpr int kScanTile = 2048;   // cells per block in the scan
-
-// Per-block tiles never straddle an instance: tile t covers [tile_lo, tile_hi) of one
-// instance.  The tile table is derived on the fly from the offsets: block b belongs
-// to the instance whose tile range contains b.
-struct TileMap {
-  const long long* off;
-  int n_inst;
-  const long long* tile_off;   // [n_inst + 1] first tile of each instance
-};
-
-__device__ __forceinline__ bool tile_range(const TileMap& tm, int tile, int& b, long long& lo,
-                                           long long& hi) {
-  int l = 0, h = tm.n_inst - 1;
-  while (l < h) {
-    int mid = (l + h + 1) >> 1;
-    if (tm.tile_off[mid] <= tile) l = mid; else h = mid - 1;
-  }
-  b = l;
-  long long t = tile - tm.tile_off[b];
-  lo = tm.off[b] + t * kTile;
-  hi = min(lo + kTile, tm.off[b + 1]);
-  return lo < hi;
-}
 
 // ---------------------------------------------------------------- stats
 // Sums of M, M m and M s per instance (a10): per-tile partials over a fixed stride and a
@@ -416,17 +392,32 @@ __device__ __forceinline__ void put_snapshot(const InstDev& p, long long r, doub
   if (kMixed) snap32[r] = make_float4((float)si, (float)m, (float)(N * 0x1p-64), (float)im);
 }
 
-// The snapshot alone, at unchanged ranks (positions did not move since the last build).
+// The gas disk's (R, Z) of a particle from its search coordinates (model_pos): a patch sits
+// at R = R_0 + x; the 2D radial-polar and 1D models search (R, Z, 0) and (R, 0, 0); the 3D
+// and radial-azimuthal models hold (x, y, z) and (x, y, 0).
+__device__ __forceinline__ void gas_coords(const InstDev& p, double X, double Y, double Z, double& R, double& Zg) {
+  if (p.geometry == GD_GEOM_PATCH) R = p.r0 + X;
+  else if (p.model == GD_MODEL_RZ || p.model == GD_MODEL_R) R = X;
+  else R = sqrt(X * X + Y * Y);
+  Zg = p.model == GD_MODEL_RZ ? Y : Z;
+}
+
+// The snapshot alone, at unchanged ranks (positions did not move since the last build); the
+// mixed form's FP32 (R, Z, M) stay, its fine bin follows the new size.
 template <bool kMixed>
 __global__ void k_snapshot(TileMap tm, const InstDev* __restrict__ P, const double* __restrict__ s,
                            const double* __restrict__ M, const int* __restrict__ rank_of,
-                           Snap64* __restrict__ snap64, float4* __restrict__ snap32, double* __restrict__ Mr) {
+                           Snap64* __restrict__ snap64, float4* __restrict__ snap32, double* __restrict__ Mr,
+                           float4* __restrict__ gx) {
   int b;
   long long lo, hi;
   if (!tile_range(tm, blockIdx.x, b, lo, hi)) return;
   const InstDev p = P[b];
-  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x)
-    put_snapshot<kMixed>(p, rank_of[i], s[i], M[i], snap64, snap32, Mr);
+  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const int r = rank_of[i];
+    put_snapshot<kMixed>(p, r, s[i], M[i], snap64, snap32, Mr);
+    if (kMixed) reinterpret_cast<float*>(gx + r)[3] = __int_as_float(fine_bin(s[i]));
+  }
 }
 
 template <bool kMixed>
@@ -437,7 +428,7 @@ __global__ void k_scatter(TileMap tm, const InstDev* __restrict__ P, const GridD
                           const int* __restrict__ slot, const int* __restrict__ start,
                           int* __restrict__ perm, int* __restrict__ rank_of, Pos64* __restrict__ pos64,
                           float4* __restrict__ pos32, Snap64* __restrict__ snap64,
-                          float4* __restrict__ snap32, double* __restrict__ Mr) {
+                          float4* __restrict__ snap32, double* __restrict__ Mr, float4* __restrict__ gx) {
   int b;
   long long lo, hi;
   if (!tile_range(tm, blockIdx.x, b, lo, hi)) return;
@@ -454,6 +445,11 @@ __global__ void k_scatter(TileMap tm, const InstDev* __restrict__ P, const GridD
     q.x = xi; q.y = yi; q.z = zi; q.j = i;
     pos64[r] = q;
     put_snapshot<kMixed>(p, r, si, Mi, snap64, snap32, Mr);
+    if (kMixed) {
+      double R, Zg;
+      gas_coords(p, xi, yi, zi, R, Zg);
+      gx[r] = make_float4((float)R, (float)Zg, (float)Mi, __int_as_float(fine_bin(si)));
+    }
     {
       // FP32 mirror relative to the particle's own cell origin (|coord| <= cell edge),
       // cell coordinates packed in w (11 + 11 + 10 bits); periodic axes use the
@@ -477,14 +473,6 @@ __global__ void k_scatter(TileMap tm, const InstDev* __restrict__ P, const GridD
 // ---------------------------------------------------------------- launcher
 namespace gd {
 
-static TileMap tile_map(gd_ctx* c) {
-  TileMap tm;
-  tm.off = c->d_off;
-  tm.n_inst = c->n_inst;
-  tm.tile_off = c->d_tile_off;
-  return tm;
-}
-
 int num_tiles(gd_ctx* c) { return c->n_tiles; }
 
 std::vector<long long> tile_table(const std::vector<long long>& off) {
@@ -499,10 +487,10 @@ cudaError_t launch_snapshot(gd_ctx* c) {
   const int nt = num_tiles(c);
   if (c->precision == GD_MIXED)
     k_snapshot<true><<<nt, 256, 0, c->stream>>>(tile_map(c), c->d_inst, c->s, c->M, c->d_rank_of, c->d_snap64,
-                                                c->d_snap32, c->d_Mr);
+                                                c->d_snap32, c->d_Mr, c->d_gx);
   else
     k_snapshot<false><<<nt, 256, 0, c->stream>>>(tile_map(c), c->d_inst, c->s, c->M, c->d_rank_of, c->d_snap64,
-                                                 c->d_snap32, c->d_Mr);
+                                                 c->d_snap32, c->d_Mr, c->d_gx);
   time_end(c);
   c->launches += 1;
   return cudaGetLastError();
@@ -539,12 +527,12 @@ cudaError_t launch_cells(gd_ctx* c) {
     k_scatter<true><<<nt, 256, 0, st>>>(tm, c->d_inst, c->d_grid, c->x, c->y, c->z, c->s, c->M,
                                         c->d_cell_of, c->d_slot, c->d_cell_start, c->d_perm,
                                         c->d_rank_of, c->d_pos64, c->d_pos32, c->d_snap64,
-                                        c->d_snap32, c->d_Mr);
+                                        c->d_snap32, c->d_Mr, c->d_gx);
   else
     k_scatter<false><<<nt, 256, 0, st>>>(tm, c->d_inst, c->d_grid, c->x, c->y, c->z, c->s, c->M,
                                          c->d_cell_of, c->d_slot, c->d_cell_start, c->d_perm,
                                          c->d_rank_of, c->d_pos64, c->d_pos32, c->d_snap64,
-                                         c->d_snap32, c->d_Mr);
+                                         c->d_snap32, c->d_Mr, c->d_gx);
   time_end(c);
   c->launches += 8;
   return cudaGetLastError();

@@ -47,6 +47,7 @@ struct KnnArgs {
   int* nbr;
   double* dist;
   double* V;
+  float* pref32;                  // mixed form: FP32 rate prefactor (NULL in the FP64 form)
   double* dprev;                  // caller order: d_i of the last build (0: unknown)
   StateDev* st;
   int* redo;                      // mixed form: queries the FP64 form redoes
@@ -677,7 +678,9 @@ __global__ void __launch_bounds__(128, CAP <= 40 ? 5 : 4) k_knn(KnnArgs A) {
       }
       const double d = sqrt(d2max);
       A.dist[q] = d;
-      A.V[q] = sample_volume(A.P[b], d, Q.x, Q.y);
+      const double Vq = sample_volume(A.P[b], d, Q.x, Q.y);
+      A.V[q] = Vq;
+      if (A.pref32) A.pref32[q] = (float)rate_prefactor(A.P[b], Vq, A.K, true);
       A.dprev[ci] = d;
     } else if (kMixed) {
       // the FP64 form redoes it
@@ -690,6 +693,7 @@ __global__ void __launch_bounds__(128, CAP <= 40 ? 5 : 4) k_knn(KnnArgs A) {
       for (int k = 0; k < A.K; ++k) row[k] = (int)q;
       A.dist[q] = 0.0;
       A.V[q] = __longlong_as_double(0x7FF0000000000000ll);
+      if (A.pref32) A.pref32[q] = 0.0f;
       A.dprev[ci] = 0.0;
       set_status(&A.st[b], GD_ST_KNN);
     }
@@ -776,6 +780,7 @@ cudaError_t launch_knn(gd_ctx* c) {
   A.nbr = c->d_nbr;
   A.dist = c->d_dist;
   A.V = c->d_V;
+  A.pref32 = c->d_pref32;
   A.dprev = c->d_dprev;
   A.st = c->d_state;
   A.redo = c->d_redo;

@@ -38,27 +38,26 @@ struct McArgs {
   unsigned* ev_hash;
   int* near_out;
   long long max_events;
-  long long range;     // ranks per block (rate kernel)
   unsigned long long* work;   // sampler: next chunk of 32 ranks (zeroed before the launch)
+  const float4* gx;           // mixed form: FP32 (R, Z, M) and the fine bin of each rank
+  const float* pref32;        // mixed form: FP32 rate prefactor of each rank
+  void* contrib;              // rank order: fine-bin contribution of each particle (rate kernel)
+  double* MJ;                 // caller order: M_i times the realised sum of |ln s'/s| (sampler)
+  double* part;               // per-tile fine-bin partial sums [kBinQ][kNFine][n_tiles]
+  long long n_tiles;
 };
 
 // Per-particle quantities that do not depend on the live diameter.  The pair parameters
 // are held in the pair precision T, so the mixed form converts them once per particle.
 template <typename T>
 struct Fixed {
-  T gst, e2, e1, zo, cs, cB, Vg2, tRe, vfrag, m0;
+  T gst, e2, e1, zo, cs, cB, Vg2, tRe, vfrag, m0, smin;
+  T prefT;            // the prefactor in the pair precision
   double pref;        // lambda = pref * (pair rate in kernel units)
   double rho_s, s_min, M;
   double k6;          // 6 / (pi rho_s): s^3 = k6 m
   int mode;
 };
-
-template <typename T>
-__device__ __forceinline__ double prefactor(const InstDev& P, double V, int K) {
-  if (P.kernel_mode != GD_KERNEL_PHYSICAL) return 1.0 / (P.t0 * (double)K);
-  if (sizeof(T) == 8) return kPi / (4.0 * V);
-  return kPi * 0x1p64 / (4.0 * V);
-}
 
 template <typename T>
 __device__ __forceinline__ Fixed<T> make_fixed(const InstDev& P, const Gas& g, double V, double M, int K) {
@@ -73,7 +72,9 @@ __device__ __forceinline__ Fixed<T> make_fixed(const InstDev& P, const Gas& g, d
   f.tRe = 1.0 / sqrt(g.Re);
   f.vfrag = P.v_frag;
   f.m0 = P.m0;
-  f.pref = prefactor<T>(P, V, K);
+  f.smin = P.s_min;
+  f.pref = rate_prefactor(P, V, K, sizeof(T) == 4);
+  f.prefT = (T)f.pref;
   f.rho_s = P.rho_s;
   f.s_min = P.s_min;
   f.M = M;
@@ -82,13 +83,12 @@ __device__ __forceinline__ Fixed<T> make_fixed(const InstDev& P, const Gas& g, d
   return f;
 }
 
-// Mixed form: the same quantities in FP32 (they only feed FP32 pair arithmetic).
-// Omega = sqrt(GM/R)/R keeps R^3 out of the FP32 range, and
+// Mixed form: the same quantities in FP32 from the particle's FP32 gas coordinates
+// (R, Z, M, fine bin) and FP32 prefactor, both written once per build; they only feed FP32
+// pair arithmetic.  Omega = sqrt(GM/R)/R keeps R^3 out of the FP32 range, and
 // 1 - R/r = Z^2/(r (r + R)) avoids the cancellation of the literal form.
-__device__ __forceinline__ Fixed<float> make_fixed_f32(const InstDev& P, double x, double y, double z, double V,
-                                                double M, int K) {
-  const float R = P.geometry == GD_GEOM_PATCH ? (float)(P.r0 + x) : sqrtf((float)x * (float)x + (float)y * (float)y);
-  const float Z = (float)z;
+__device__ __forceinline__ Fixed<float> make_fixed_f32(const InstDev& P, float4 gx, float pref) {
+  const float R = gx.x, Z = gx.y;
   const float r = sqrtf(R * R + Z * Z);
   const float Om = sqrtf(P.f_GM / R) / R;
   const float xr = R / P.f_r0;
@@ -113,10 +113,12 @@ __device__ __forceinline__ Fixed<float> make_fixed_f32(const InstDev& P, double 
   f.tRe = rsqrtf(P.f_alpha * cs * H / numol);
   f.vfrag = P.f_vfrag;
   f.m0 = P.f_m0;
-  f.pref = prefactor<float>(P, V, K);
+  f.smin = P.f_smin;
+  f.prefT = pref;
+  f.pref = (double)pref;
   f.rho_s = P.rho_s;
   f.s_min = P.s_min;
-  f.M = M;
+  f.M = (double)gx.z;
   f.k6 = P.k6;
   f.mode = P.kernel_mode;
   return f;
@@ -129,16 +131,10 @@ __device__ __forceinline__ Gas gas_of(const InstDev& P, const Pos64& p) {
   return P.model == GD_MODEL_RZ ? gas_RZ(P, p.x, p.y) : gas_at(P, p.x, p.y, p.z);
 }
 
-__device__ __forceinline__ Fixed<float> make_fixed_f32_at(const InstDev& P, const Pos64& p, double V, double M,
-                                                          int K) {
-  if (P.model == GD_MODEL_RZ) return make_fixed_f32(P, p.x, 0.0, p.y, V, M, K);
-  return make_fixed_f32(P, p.x, p.y, p.z, V, M, K);
-}
-
 // <J>, <J^2> of a fragmentation in FP32 (mixed form; they only feed the bin moments).
-__device__ __forceinline__ void frag_moments_f32(double s_i, double s_min, double& j1, double& j2) {
-  const float a = sqrtf((float)s_min / (float)s_i);
-  if (!(a < 1.0f)) { j1 = 0.0; j2 = 0.0; return; }
+__device__ __forceinline__ void frag_moments_f32(float s_i, float s_min, float& j1, float& j2) {
+  const float a = sqrtf(s_min / s_i);
+  if (!(a < 1.0f)) { j1 = 0.0f; j2 = 0.0f; return; }
   const float dd = 1.0f - a;
   if (dd < 1e-2f) {
     j1 = dd * (1.0f + dd * (1.0f / 3.0f + dd * (1.0f / 6.0f + dd * (1.0f / 10.0f))));
@@ -150,34 +146,47 @@ __device__ __forceinline__ void frag_moments_f32(double s_i, double s_min, doubl
   j2 = 4.0f * (2.0f - a * la * la + 2.0f * a * la - 2.0f * a) / (1.0f - a);
 }
 
-// Query of a live particle (s, m) from the fixed part.  FP64 form: FP64 throughout; mixed
-// form: FP32 from the rounded s, m and gst (the rate kernel and the sampler build it with
-// this one function, so both see the same pair rates).
-template <typename T>
-__device__ __forceinline__ Query<T> live_query(const Fixed<T>& f, double s, double m) {
-  Query<T> q;
-  if constexpr (sizeof(T) == 8) {
-    double St = f.gst * s;
-    q.s = s; q.m = m; q.inv_m = 1.0 / m;
-    q.St = St;
-    q.ai = St / (1.0 + St * St);
-    q.bi = 1.0 / (1.0 + St * St);
-    q.hi = St < 0.5 ? St : 0.5;
-  } else {
-    const float sf = (float)s, mf = (float)m, St = f.gst * sf;
-    const float bi = 1.0f / (1.0f + St * St);
-    q.s = sf; q.m = mf; q.inv_m = 1.0f / mf;
-    q.St = St;
-    q.ai = St * bi;
-    q.bi = bi;
-    q.hi = St < 0.5f ? St : 0.5f;
-  }
+// Mixed-form query from the FP32 diameter and mass with the IEEE quotient: the rate kernel
+// and the sampler's first evaluation of a particle both build it here, so both see the same
+// pair rates.
+__device__ __forceinline__ Query<float> live_query_f32(const Fixed<float>& f, float sf, float mf) {
+  Query<float> q;
+  const float St = f.gst * sf;
+  const float bi = 1.0f / (1.0f + St * St);
+  q.s = sf; q.m = mf; q.inv_m = 1.0f / mf;
+  q.St = St;
+  q.ai = St * bi;
+  q.bi = bi;
+  q.hi = St < 0.5f ? St : 0.5f;
   q.g = f.gst;
   q.e2 = f.e2; q.e1 = f.e1; q.zo = f.zo;
   q.cs = f.cs; q.cB = f.cB; q.Vg2 = f.Vg2; q.tRe = f.tRe;
   q.vfrag = f.vfrag; q.m0 = f.m0;
   q.mode = f.mode;
   return q;
+}
+
+// Query of a live particle (s, m) from the fixed part.  FP64 form: FP64 throughout; mixed
+// form: FP32 from the rounded s and m.
+template <typename T>
+__device__ __forceinline__ Query<T> live_query(const Fixed<T>& f, double s, double m) {
+  if constexpr (sizeof(T) == 8) {
+    Query<T> q;
+    double St = f.gst * s;
+    q.s = s; q.m = m; q.inv_m = 1.0 / m;
+    q.St = St;
+    q.ai = St / (1.0 + St * St);
+    q.bi = 1.0 / (1.0 + St * St);
+    q.hi = St < 0.5 ? St : 0.5;
+    q.g = f.gst;
+    q.e2 = f.e2; q.e1 = f.e1; q.zo = f.zo;
+    q.cs = f.cs; q.cB = f.cB; q.Vg2 = f.Vg2; q.tRe = f.tRe;
+    q.vfrag = f.vfrag; q.m0 = f.m0;
+    q.mode = f.mode;
+    return q;
+  } else {
+    return live_query_f32(f, (float)s, (float)m);
+  }
 }
 
 // Mixed-form query from the FP32 diameter and mass.
@@ -226,6 +235,8 @@ __device__ __forceinline__ Fixed<T> shfl_fixed(const Fixed<T>& a, int src) {
   f.tRe = __shfl_sync(FULLM, a.tRe, src);
   f.vfrag = __shfl_sync(FULLM, a.vfrag, src);
   f.m0 = __shfl_sync(FULLM, a.m0, src);
+  f.smin = __shfl_sync(FULLM, a.smin, src);
+  f.prefT = __shfl_sync(FULLM, a.prefT, src);
   f.pref = __shfl_sync(FULLM, a.pref, src);
   f.rho_s = __shfl_sync(FULLM, a.rho_s, src);
   f.s_min = __shfl_sync(FULLM, a.s_min, src);
@@ -372,48 +383,75 @@ __device__ __forceinline__ double waiting_time(uint32_t a, uint32_t b, double la
   }
 }
 
-// ---------------------------------------------------------------- rate kernel
-// Lane = particle: each thread walks its own neighbour row (the 128-byte row stays in
-// L1 across the walk), evaluates the K pairs in slot order and sums lambda*_i and the bin
-// moments in registers.  FP64 form: the channel rates are added in the oracle's order
-// (slot by slot, remnant before debris).  Block-level fine-bin sums of the block's first
-// instance: FP64 form in FP64; mixed form in FP32 (native shared atomics; they only feed
-// the interval controller), added to the instance's FP64 bins once per block.
-template <typename T, int S>
-__global__ void __launch_bounds__(128) k_rates(McArgs A) {
-  __shared__ double sh[4][kNFine];
-  __shared__ float shf[3][kNFine];
-  __shared__ unsigned shc[kNFine];
-  const long long lo = (long long)blockIdx.x * A.range;
-  const long long hi = min(lo + A.range, A.N);
-  if (lo >= hi) return;
-  const int b_lo = inst_of(A.off, A.n_inst, lo), b_hi = inst_of(A.off, A.n_inst, hi - 1);
-  const bool shared_bins = (b_lo == b_hi);
-  if constexpr (sizeof(T) == 8) {
-    for (int t = threadIdx.x; t < 4 * kNFine; t += blockDim.x) sh[t / kNFine][t % kNFine] = 0.0;
-  } else {
-    for (int t = threadIdx.x; t < 3 * kNFine; t += blockDim.x) shf[t / kNFine][t % kNFine] = 0.0f;
-    for (int t = threadIdx.x; t < kNFine; t += blockDim.x) shc[t] = 0u;
+// ---------------------------------------------------------------- fixed-order bin sums
+// Fine-bin accumulation of one warp in a fixed order: the lanes holding particles of the
+// same fine bin (one match group) sum the group's values in ascending lane order, and the
+// group's lowest lane adds the sums to the warp's own accumulators acc[k * kNFine + bin].
+// A warp's batches come in a fixed order, so no sum depends on scheduling (no float atomics).
+// fbin < 0: the lane adds nothing.
+template <typename Acc, int NV>
+__device__ __forceinline__ void warp_bin_add(Acc* acc, int* cnt, int fbin, const Acc (&v)[NV], int lane) {
+  const int key = fbin >= 0 ? fbin : kNFine + lane;
+  const unsigned grp = __match_any_sync(FULLM, key);
+  const int npop = __popc(grp);
+  const int nmax = (int)__reduce_max_sync(FULLM, (unsigned)npop);
+  Acc sum[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) sum[k] = (Acc)0;
+  unsigned m = grp;
+  for (int i = 0; i < nmax; ++i) {
+    const int src = m ? __ffs(m) - 1 : lane;
+    m &= m - 1u;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      const Acc t = __shfl_sync(FULLM, v[k], src);
+      if (i < npop) sum[k] += t;
+    }
   }
-  __syncthreads();
+  if (fbin >= 0 && lane == __ffs(grp) - 1) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k * kNFine + fbin] += sum[k];
+    if (cnt) cnt[fbin] += npop;
+  }
+  __syncwarp();
+}
+
+// ---------------------------------------------------------------- rate kernel
+// Block = one tile of up to kTile ranks of one instance; lane = particle: each thread walks
+// its own neighbour row (the row stays in L1 across the walk), evaluates the K pairs in slot
+// order and sums lambda*_i and the moments sum lambda* <J>, sum lambda* <J^2> in registers
+// (FP64 form: the channel rates in the oracle's order, slot by slot, remnant before debris).
+// Each particle's contribution to the fine-bin sums (M, M pref sum lambda* <J>, likewise
+// <J^2>, and its fine bin) is written in rank order; k_bins_tile adds them up in caller order.
+// Mixed form: FP32 throughout the particle's work, from its FP32 gas coordinates, snapshot
+// and prefactor.
+template <typename T>
+__global__ void __launch_bounds__(128) k_rates(McArgs A, TileMap tm) {
+  int b;
+  long long lo, hi;
+  tile_range(tm, blockIdx.x, b, lo, hi);
+  const InstDev& P = A.P[b];
   for (long long r = lo + threadIdx.x; r < hi; r += blockDim.x) {
-    const int b = inst_of(A.off, A.n_inst, r);
-    const InstDev& P = A.P[b];
-    const Pos64 p = A.pos64[r];
-    const Snap64 sn = A.snap64[r];
-    const double s_i = sn.s, m_i = sn.m;
     Fixed<T> fx;
-    double fj1, fj2;
+    Query<T> q;
+    T j1, j2;
+    int fbin;
     if constexpr (sizeof(T) == 8) {
+      const Pos64 p = A.pos64[r];
+      const Snap64 sn = A.snap64[r];
       Gas g = gas_of(P, p);
       fx = make_fixed<double>(P, g, A.V[r], A.Mr[r], A.K);
-      frag_moments(s_i, P.s_min, fj1, fj2);
+      frag_moments(sn.s, P.s_min, j1, j2);
+      q = live_query<T>(fx, sn.s, sn.m);
+      fbin = fine_bin(sn.s);
     } else {
-      fx = make_fixed_f32_at(P, p, A.V[r], A.Mr[r], A.K);
-      frag_moments_f32(s_i, P.s_min, fj1, fj2);
+      const float4 g4 = A.gx[r];
+      const float4 sn = A.snap32[r];
+      fx = make_fixed_f32(P, g4, A.pref32[r]);
+      frag_moments_f32(sn.x, fx.smin, j1, j2);
+      q = live_query_f32(fx, sn.x, sn.y);
+      fbin = __float_as_int(g4.w);
     }
-    const Query<T> q = live_query<T>(fx, s_i, m_i);
-    const T j1 = (T)fj1, j2 = (T)fj2;
     const int* row = A.nbr + r * A.K;
     const long long ci = A.chan_out ? (long long)A.perm[r] * A.K : 0;
     T tot = (T)0, la = (T)0, lb = (T)0;
@@ -435,53 +473,133 @@ __global__ void __launch_bounds__(128) k_rates(McArgs A) {
         A.chan_out[(ci + k) * 2 + 1] = fx.pref * (double)po.c1;
       }
     }
-    const double lam = fx.pref * (double)tot;
+    double lam;
+    if constexpr (sizeof(T) == 8) {
+      lam = fx.pref * tot;
+      Contrib64 c;
+      c.M = fx.M;
+      c.MA = fx.M * (fx.pref * la);
+      c.MB = fx.M * (fx.pref * lb);
+      c.fbin = fbin;
+      static_cast<Contrib64*>(A.contrib)[r] = c;
+    } else {
+      const float lf = fx.prefT * tot;
+      lam = (lf > 1e-30f && lf < 1e30f) ? (double)lf : fx.pref * (double)tot;
+      const float Mf = A.gx[r].z;
+      static_cast<float4*>(A.contrib)[r] =
+          make_float4(Mf, Mf * (fx.prefT * la), Mf * (fx.prefT * lb), __int_as_float(fbin));
+    }
     A.lam[r] = lam;
     if (!isfinite(lam)) set_status(&A.st[b], GD_ST_NONFINITE);
-    const int fbin = fine_bin(s_i);
-    const double M = fx.M;
-    if (sizeof(T) == 4 && b == b_lo) {
-      const float Mf = (float)M, pf = (float)fx.pref;
-      atomicAdd(&shc[fbin], 1u);
-      atomicAdd(&shf[0][fbin], Mf);
-      atomicAdd(&shf[1][fbin], Mf * (pf * (float)la));
-      atomicAdd(&shf[2][fbin], Mf * (pf * (float)lb));
-    } else if (sizeof(T) == 8 && shared_bins) {
-      atomicAdd(&sh[0][fbin], 1.0);
-      atomicAdd(&sh[1][fbin], M);
-      atomicAdd(&sh[2][fbin], M * (fx.pref * (double)la));
-      atomicAdd(&sh[3][fbin], M * (fx.pref * (double)lb));
-    } else {
-      BinsDev* bn = &A.bins[b];
-      atomicAdd(&bn->cnt[fbin], 1.0);
-      atomicAdd(&bn->sM[fbin], M);
-      atomicAdd(&bn->sA[fbin], M * (fx.pref * (double)la));
-      atomicAdd(&bn->sB[fbin], M * (fx.pref * (double)lb));
-    }
   }
-  if constexpr (sizeof(T) == 4) {
-    __syncthreads();
-    BinsDev* bn = &A.bins[b_lo];
-    for (int t = threadIdx.x; t < kNFine; t += blockDim.x) {
-      if (shc[t] != 0u) {
-        atomicAdd(&bn->cnt[t], (double)shc[t]);
-        atomicAdd(&bn->sM[t], (double)shf[0][t]);
-        atomicAdd(&bn->sA[t], (double)shf[1][t]);
-        atomicAdd(&bn->sB[t], (double)shf[2][t]);
+}
+
+// Fine-bin partial sums of one tile of CALLER indices (count, M, M A, M B), each particle's
+// contribution gathered from its rank: the rank order inside a cell follows the counting
+// sort's atomics, the caller order does not, so the sums are the same in every run.  Warps
+// add in the fixed order of warp_bin_add (FP64 form in FP64, mixed form in FP32), the warps'
+// sums are added in warp order in FP64.
+template <typename T>
+__global__ void __launch_bounds__(128) k_bins_tile(TileMap tm, const int* __restrict__ rank_of,
+                                                   const void* __restrict__ contrib, double* part,
+                                                   long long n_tiles) {
+  constexpr int NW = 4;
+  __shared__ T acc[NW][3 * kNFine];
+  __shared__ int cnt[NW][kNFine];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int t = threadIdx.x; t < NW * 3 * kNFine; t += blockDim.x) (&acc[0][0])[t] = (T)0;
+  for (int t = threadIdx.x; t < NW * kNFine; t += blockDim.x) (&cnt[0][0])[t] = 0;
+  __syncthreads();
+  int b;
+  long long lo, hi;
+  tile_range(tm, blockIdx.x, b, lo, hi);
+  for (long long base = lo; base < hi; base += blockDim.x) {
+    const long long i = base + threadIdx.x;
+    int fb = -1;
+    T v[3] = {(T)0, (T)0, (T)0};
+    if (i < hi) {
+      const int r = rank_of[i];
+      if constexpr (sizeof(T) == 8) {
+        const Contrib64 c = static_cast<const Contrib64*>(contrib)[r];
+        v[0] = c.M; v[1] = c.MA; v[2] = c.MB;
+        fb = (int)c.fbin;
+      } else {
+        const float4 c = static_cast<const float4*>(contrib)[r];
+        v[0] = c.x; v[1] = c.y; v[2] = c.z;
+        fb = __float_as_int(c.w);
       }
     }
-  } else if (shared_bins) {
-    __syncthreads();
-    BinsDev* bn = &A.bins[b_lo];
-    for (int t = threadIdx.x; t < kNFine; t += blockDim.x) {
-      if (sh[0][t] != 0.0) {
-        atomicAdd(&bn->cnt[t], sh[0][t]);
-        atomicAdd(&bn->sM[t], sh[1][t]);
-        atomicAdd(&bn->sA[t], sh[2][t]);
-        atomicAdd(&bn->sB[t], sh[3][t]);
+    warp_bin_add<T, 3>(&acc[w][0], &cnt[w][0], fb, v, lane);
+  }
+  __syncthreads();
+  for (int f = threadIdx.x; f < kNFine; f += blockDim.x) {
+    double c = 0.0, sM = 0.0, sA = 0.0, sB = 0.0;
+    for (int ww = 0; ww < NW; ++ww) {
+      c += (double)cnt[ww][f];
+      sM += (double)acc[ww][f];
+      sA += (double)acc[ww][kNFine + f];
+      sB += (double)acc[ww][2 * kNFine + f];
+    }
+    part[(0LL * kNFine + f) * n_tiles + blockIdx.x] = c;
+    part[(1LL * kNFine + f) * n_tiles + blockIdx.x] = sM;
+    part[(2LL * kNFine + f) * n_tiles + blockIdx.x] = sA;
+    part[(3LL * kNFine + f) * n_tiles + blockIdx.x] = sB;
+  }
+}
+
+// Fine-bin sums of M_i J_i of the interval (the realised |ln s'/s| of each particle's
+// events, caller order) per tile of caller indices, in the same fixed order; quantity 4 of
+// the tile partials.  The fine bin is that of the particle's size at the interval start.
+template <bool kMixed>
+__global__ void __launch_bounds__(128) k_jbins(TileMap tm, const int* __restrict__ rank_of,
+                                               const void* __restrict__ contrib, const double* __restrict__ MJ,
+                                               double* part, long long n_tiles) {
+  constexpr int NW = 4;
+  __shared__ double acc[NW][kNFine];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int t = threadIdx.x; t < NW * kNFine; t += blockDim.x) (&acc[0][0])[t] = 0.0;
+  __syncthreads();
+  int b;
+  long long lo, hi;
+  tile_range(tm, blockIdx.x, b, lo, hi);
+  for (long long base = lo; base < hi; base += blockDim.x) {
+    const long long i = base + threadIdx.x;
+    double v[1] = {0.0};
+    int fb = -1;
+    if (i < hi) {
+      v[0] = MJ[i];
+      if (v[0] != 0.0) {
+        const int r = rank_of[i];
+        if (kMixed) fb = __float_as_int(static_cast<const float4*>(contrib)[r].w);
+        else fb = (int)static_cast<const Contrib64*>(contrib)[r].fbin;
       }
     }
+    warp_bin_add<double, 1>(&acc[w][0], nullptr, fb, v, lane);
   }
+  __syncthreads();
+  for (int f = threadIdx.x; f < kNFine; f += blockDim.x) {
+    double sJ = 0.0;
+    for (int ww = 0; ww < NW; ++ww) sJ += acc[ww][f];
+    part[(4LL * kNFine + f) * n_tiles + blockIdx.x] = sJ;
+  }
+}
+
+// Per-instance fine-bin sums from the tile partials, in a fixed order: one warp per
+// (quantity, bin); lane l adds the instance's tiles l, l + 32, ... in order, then the lanes'
+// sums meet in a fixed butterfly.  Quantities q0 .. q0 + nq - 1 of BinsDev (cnt, sM, sA, sB,
+// sJ) are overwritten.
+__global__ void k_bins_reduce(const long long* __restrict__ tile_off, const double* __restrict__ part,
+                              long long n_tiles, int q0, int nq, BinsDev* bins) {
+  const int b = blockIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int pair = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (pair >= nq * kNFine) return;
+  const int q = q0 + pair / kNFine, f = pair % kNFine;
+  const double* src = part + ((long long)q * kNFine + f) * n_tiles;
+  double v = 0.0;
+  for (long long t = tile_off[b] + lane; t < tile_off[b + 1]; t += 32) v += src[t];
+  v = warp_sum(v);
+  if (lane == 0) (&bins[b].cnt[0])[q * kNFine + f] = v;
 }
 
 // ---------------------------------------------------------------- interval choice
@@ -538,8 +656,11 @@ __global__ void k_interval(const InstDev* __restrict__ P, StateDev* st, BinsDev*
   const double remain = ldexp((double)S.remain_ticks, -60) * dtc;
   const double dt_cap = remain < p.dt_fn_max ? remain : p.dt_fn_max;
   double dt_ab = HUGE_VAL;
+  for (int g = 0; g < kNFine; ++g) { Bn.gA[g] = 0.0; Bn.gB[g] = 0.0; }
   for (int g = 0; g < ng; ++g) {
     const double A = gA[g] / gM[g], Bm = gB[g] / gM[g];
+    Bn.gA[g] = A;
+    Bn.gB[g] = Bm;
     if (A > 0.0) { const double t = p.eps * C / A; if (t < dt_ab) dt_ab = t; }
     if (Bm > 0.0) { const double t = p.eps * p.eps * C * C / Bm; if (t < dt_ab) dt_ab = t; }
   }
@@ -603,6 +724,7 @@ __global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
     unsigned emask = __ballot_sync(FULLM, ev);
     if (emask == 0) {
       if (valid && nn) { atomicAdd((unsigned long long*)&A.st[b].near_draw, (unsigned long long)nn); }
+      if (valid) A.MJ[A.perm[r]] = 0.0;
       if (valid && A.ev_count) {
         int ci = A.perm[r];
         A.ev_count[ci] = 0;
@@ -624,7 +746,7 @@ __global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
         Gas g = gas_of(P, p);
         fx = make_fixed<double>(P, g, A.V[r], A.Mr[r], A.K);
       } else {
-        fx = make_fixed_f32_at(P, p, A.V[r], A.Mr[r], A.K);
+        fx = make_fixed_f32(P, A.gx[r], A.pref32[r]);
       }
     } else {
       fx = Fixed<T>{};
@@ -632,6 +754,7 @@ __global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
     }
     int my_e = 0;
     unsigned my_h = 0u;
+    double my_MJ = 0.0;
     while (emask) {
       const int p = __ffs(emask) - 1;
       emask &= emask - 1;
@@ -645,10 +768,9 @@ __global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
       const unsigned iv = __shfl_sync(FULLM, ival, p), il = __shfl_sync(FULLM, i_loc, p);
       const unsigned k0 = __shfl_sync(FULLM, key0, p), k1 = __shfl_sync(FULLM, key1, p);
       const int bp = __shfl_sync(FULLM, b, p);
-      const double s_start = s;
       const double tie_dte = tie_tol<T>() * dte;
       // mixed form: FP32 copies of per-particle constants for the per-event FP32 steps
-      const float k6f = (float)f.k6, preff = (float)f.pref;
+      const float k6f = (float)f.k6, preff = f.prefT;
       float sf = (float)s;      // mixed form: the FP32 diameter the pair rates use
       bool s_stale = false;     // mixed form: s lags m after a sticking or erosion event
       int e = 0, near_ch = 0, near_u = 0;   // per-lane channel ties, warp-uniform ties
@@ -808,7 +930,7 @@ __global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
           } else {
             // the fragment size is a draw: FP32 is enough; the mass follows it in FP64
             const float U = fmaf((float)(w2.x >> 6), 0x1p26f, (float)(w2.y >> 6) + 0.5f) * 0x1p-52f;
-            const float a = sqrtf((float)f.s_min), bq = sqrtf(sf);
+            const float a = sqrtf(f.smin), bq = sqrtf(sf);
             const float xr = fmaf(U, bq - a, a);
             sf = xr * xr;
             s_new = (double)sf;
@@ -872,14 +994,14 @@ __global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) near_tot += __shfl_xor_sync(FULLM, near_tot, o);
       near_tot += near_u;
-      if (lane == p) { my_e = e; my_h = h; nn += near_tot; }
+      if (lane == p) { my_e = e; my_h = h; nn += near_tot; my_MJ = f.M * (double)J; }
       if (lane == 0) {
         int ci = A.perm[rp];
         A.s_out[ci] = s;
         atomicAdd((unsigned long long*)&A.st[bp].events, (unsigned long long)e);
-        if (J > (T)0) atomicAdd(&A.bins[bp].sJ[fine_bin(s_start)], f.M * (double)J);
       }
     }
+    if (valid) A.MJ[A.perm[r]] = my_MJ;
     if (valid && nn) atomicAdd((unsigned long long*)&A.st[b].near_draw, (unsigned long long)nn);
     if (valid && A.ev_count) {
       int ci = A.perm[r];
@@ -991,28 +1113,38 @@ static McArgs mc_args(gd_ctx* c) {
   A.near_out = nullptr;
   A.max_events = c->max_events;
   A.work = nullptr;
-  A.range = 0;
+  A.gx = c->d_gx;
+  A.pref32 = c->d_pref32;
+  A.contrib = c->d_contrib;
+  A.MJ = c->d_MJ;
+  A.part = c->d_part;
+  A.n_tiles = c->n_tiles;
   return A;
 }
 
-template <typename T>
-static void rates_t(gd_ctx* c, McArgs& A) {
-  long long blocks_want = (long long)c->num_sms * 8;
-  long long range = (A.N + blocks_want - 1) / blocks_want;
-  range = ((range + 127) / 128) * 128;
-  if (range < 128) range = 128;
-  A.range = range;
-  int blocks = (int)((A.N + range - 1) / range);
-  k_rates<T, 1><<<blocks, 128, 0, c->stream>>>(A);   // lane = particle: any K
+// Per-instance sums of quantities q0 .. q0 + nq - 1 from the tile partials (8 warps a block).
+static void bins_reduce(gd_ctx* c, int q0, int nq) {
+  dim3 grid(c->n_inst, (nq * kNFine + 7) / 8);
+  k_bins_reduce<<<grid, 256, 0, c->stream>>>(c->d_tile_off, c->d_part, c->n_tiles, q0, nq, c->d_bins);
 }
 
 cudaError_t launch_rates(gd_ctx* c, double* chan_out) {
   McArgs A = mc_args(c);
   A.chan_out = chan_out;
   time_begin(c, 2);
-  if (c->precision == GD_MIXED) rates_t<float>(c, A); else rates_t<double>(c, A);
+  // one block per tile, lane = particle: any K
+  if (c->precision == GD_MIXED) {
+    k_rates<float><<<c->n_tiles, 128, 0, c->stream>>>(A, tile_map(c));
+    k_bins_tile<float><<<c->n_tiles, 128, 0, c->stream>>>(tile_map(c), c->d_rank_of, c->d_contrib, c->d_part,
+                                                          c->n_tiles);
+  } else {
+    k_rates<double><<<c->n_tiles, 128, 0, c->stream>>>(A, tile_map(c));
+    k_bins_tile<double><<<c->n_tiles, 128, 0, c->stream>>>(tile_map(c), c->d_rank_of, c->d_contrib, c->d_part,
+                                                           c->n_tiles);
+  }
+  bins_reduce(c, 0, 4);
   time_end(c);
-  c->launches += 1;
+  c->launches += 3;
   return cudaGetLastError();
 }
 
@@ -1070,11 +1202,18 @@ cudaError_t launch_sample(gd_ctx* c, int* ev_count, unsigned* ev_hash, int* near
 
 cudaError_t launch_audit(gd_ctx* c) {
   time_begin(c, 3);
+  if (c->precision == GD_MIXED)
+    k_jbins<true><<<c->n_tiles, 128, 0, c->stream>>>(tile_map(c), c->d_rank_of, c->d_contrib, c->d_MJ, c->d_part,
+                                                     c->n_tiles);
+  else
+    k_jbins<false><<<c->n_tiles, 128, 0, c->stream>>>(tile_map(c), c->d_rank_of, c->d_contrib, c->d_MJ, c->d_part,
+                                                      c->n_tiles);
+  bins_reduce(c, 4, 1);
   k_audit<<<c->n_inst, 128, 0, c->stream>>>(c->d_inst, c->d_state, c->d_bins, c->n_inst,
                                             (c->flags & GD_FLAG_NO_AUDIT) ? 1 : 0,
                                             c->precision == GD_MIXED ? 2e-5 : 1e-10);
   time_end(c);
-  c->launches += 1;
+  c->launches += 3;
   return cudaGetLastError();
 }
 

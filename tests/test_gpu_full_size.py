@@ -21,13 +21,20 @@ def _sample(n, k, seed, extra=()):
     return np.unique(np.concatenate([q, np.asarray(extra, dtype=np.int64)]))
 
 
-def _check_subset(oracle, P, ins, q, nbr, d, lam, precision, events=None, interval=0):
+def _check_subset(oracle, P, ins, q, nbr, d, lam, precision, events=None, interval=0, chan=None):
     onbr, od = oracle.knn(P, ins["x"], ins["y"], ins["z"], q)
     assert np.array_equal(nbr[q], onbr)
     assert np.array_equal(d[q], od)
-    r = oracle.rates_subset(P, ins["x"], ins["y"], ins["z"], ins["s"], ins["M"], q, onbr, od)
+    r = oracle.rates_subset(P, ins["x"], ins["y"], ins["z"], ins["s"], ins["M"], q, onbr, od,
+                            chan=chan is not None)
     rel = np.abs(lam[q] / r["lam"] - 1.0)
     assert rel.max() < RATE_TOL[precision], rel.max()
+    if chan is not None:
+        # every channel rate of every slot: zeros exactly zero, the rest within the bound
+        rc, gc = r["chan"], chan[q]
+        assert np.array_equal(rc == 0.0, gc == 0.0)
+        nz = rc != 0.0
+        assert np.abs(gc[nz] / rc[nz] - 1.0).max() < RATE_TOL[precision]
     if events is None:
         return 0
     ec, eh, nn, dt_exe = events
@@ -53,14 +60,15 @@ def test_config1_disk_2p20_fp64(gd, oracle):
     ins = W.config1()[0]
     sess = gd.Session([ins], precision=gd.GD_FP64)
     nbr, d = sess.build_neighbors(want=True)
-    lam, _ = sess.collision_rates(want=True)
+    lam, chan = sess.collision_rates(want=True, chan=True)
     ec, eh, nn = sess.sample_collisions(want=True)
     st = sess.stats()
     P = oracle.params(ins["params"])
-    q = _sample(len(ins["x"]), 64, 21, _extremes(ins))
+    q = _sample(len(ins["x"]), 256, 21, _extremes(ins))
     _check_subset(oracle, P, ins, q, nbr.cpu().numpy(), d.cpu().numpy(), lam.cpu().numpy(), 0,
                   (ec.cpu().numpy(), eh.cpu().numpy().view(np.uint32), nn.cpu().numpy(),
-                   st["instances"][0]["dt_exe"]))
+                   st["instances"][0]["dt_exe"]), chan=chan.cpu().numpy())
+    del chan
     for _ in range(2):
         sess.build_neighbors()
         sess.collision_rates()
@@ -85,8 +93,8 @@ def test_config2_events_of_sampled_particles(gd, oracle):
     # half of the sample from particles that had events, so the replay is not vacuous
     busy = np.flatnonzero(ecn > 0)
     rng = np.random.default_rng(5)
-    q = np.unique(np.concatenate([_sample(len(ins["x"]), 32, 6, _extremes(ins)),
-                                  rng.choice(busy, min(32, len(busy)), replace=False)]))
+    q = np.unique(np.concatenate([_sample(len(ins["x"]), 128, 6, _extremes(ins)),
+                                  rng.choice(busy, min(128, len(busy)), replace=False)]))
     n_ev = _check_subset(oracle, P, ins, q, nbr.cpu().numpy(), d.cpu().numpy(), lam.cpu().numpy(), 1,
                          (ecn, eh.cpu().numpy().view(np.uint32), nn.cpu().numpy(),
                           st["instances"][0]["dt_exe"]))
@@ -146,7 +154,7 @@ def test_config4_disk_2p24_k48_push(gd, oracle):
     st = sess.stats()
     dt = st["instances"][0]["dt_exe"]
     P = oracle.params(ins["params"])
-    q = _sample(len(ins["x"]), 40, 44, _extremes(ins))
+    q = _sample(len(ins["x"]), 160, 44, _extremes(ins))
     _check_subset(oracle, P, ins, q, nbr.cpu().numpy(), d.cpu().numpy(), lam.cpu().numpy(), 1,
                   (ec.cpu().numpy(), eh.cpu().numpy().view(np.uint32), nn.cpu().numpy(), dt))
     del nbr, d, lam, ec, eh, nn

@@ -33,10 +33,12 @@ def test_two_bin_toy(oracle):
     # group 1 (small): mA alternates 1e-9 / 3e-9 with M 1 / 3 -> A_1 = (1e-9 + 9e-9)/4
     mA = np.where(np.arange(n) < 64, np.where(np.arange(n) % 2 == 0, 1e-9, 3e-9), 5e-9)
     mB = np.where(np.arange(n) < 64, 1e-9, 4e-10)
-    grp = oracle.choose_interval(P, st, s, M, mA, mB)
+    grp, A, B = oracle.choose_interval(P, st, s, M, mA, mB, moments=True)
     assert st.n_groups == 2
     assert list(np.unique(grp[:64])) == [0] and list(np.unique(grp[64:])) == [1]
     A1, A2, B1, B2 = 2.5e-9, 5e-9, 1e-9, 4e-10
+    # the controller-bin moments themselves: mass-weighted means of each bin
+    assert A == pytest.approx([A1, A2], rel=1e-15) and B == pytest.approx([B1, B2], rel=1e-15)
     want = min(1e9, 0.1 / A1, 0.1 / A2, 0.01 / B1, 0.01 / B2)
     assert want == pytest.approx(1e7)
     assert st.dt_req == pytest.approx(want, rel=1e-14)
