@@ -177,6 +177,10 @@ typedef struct {
   int64_t kernel_calls[8];     /* launches timed in each slot                  */
   int64_t knn_redo;            /* mixed form: neighbour searches the FP32 keys
                                   could not decide, redone in FP64 (all builds) */
+  int64_t rate_redo;           /* mixed form: particles whose pair rates the FP32
+                                  error bounds could not certify, redone in FP64 */
+  int64_t sample_redo;         /* mixed form: particles with an uncertified sampling
+                                  decision, replayed in FP64 (all intervals) */
 } gd_stats_t;
 
 /* Per-instance state and reductions (gd_stats). */

@@ -195,6 +195,7 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
     d.key0 = (uint32_t)p.seed;
     d.key1 = (uint32_t)(p.seed >> 32);
     d.k6 = 6.0 / (kPi * p.rho_s);
+    d.mk = kPi * p.rho_s / 6.0;
     d.f_r0 = (float)p.r0; d.f_GM = (float)d.GM; d.f_T0 = (float)p.T0; d.f_q = (float)p.q;
     d.f_p = (float)p.p; d.f_sigma0 = (float)p.sigma0; d.f_alpha = (float)p.alpha;
     d.f_rho_s = (float)p.rho_s; d.f_vfrag = (float)p.v_frag; d.f_m0 = (float)p.m0;
@@ -459,6 +460,8 @@ extern "C" gd_status gd_stats(gd_ctx* c, gd_stats_t* out, gd_instance_stats* ins
     out->near_dt += s.near_dt;
     out->near_audit += s.near_audit;
     out->knn_redo += s.knn_redo;
+    out->rate_redo += s.rate_redo;
+    out->sample_redo += s.sample_redo;
     out->status |= s.status;
     if (inst_out) {
       gd_instance_stats& o = inst_out[b];

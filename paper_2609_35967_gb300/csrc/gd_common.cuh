@@ -36,6 +36,7 @@ struct InstDev {
   uint32_t key0, key1;
   long long off, n;
   double k6;          // 6 / (pi rho_s)
+  double mk;          // pi rho_s / 6
   // FP32 copies of the parameters the mixed form's per-particle gas disk uses
   float f_r0, f_GM, f_T0, f_q, f_p, f_sigma0, f_alpha, f_rho_s, f_vfrag, f_m0, f_smin;
   // dust diffusion (Sect. 2.4)
@@ -79,6 +80,8 @@ struct StateDev {
   long long interval_next;
   long long events, events_total, near_draw, near_dt, near_audit;
   long long knn_redo;       // mixed K-NN queries redone in FP64
+  long long rate_redo;      // mixed rates redone in FP64
+  long long sample_redo;    // mixed sampling replayed in FP64
   double tau;               // length of the current collision step (0: dt_coll)
   int hold;                 // 1: idle once the current collision step is used up (gd_collide)
   int pad_hold;
@@ -89,12 +92,13 @@ struct StateDev {
 };
 
 // Fine-bin sums of one instance (doubles; counts exact below 2^53), in this order (the
-// tile reduction addresses them as quantity q of the block cnt, sM, sA, sB, sJ), and the
+// tile reduction addresses them as quantity q of the block cnt, sM, sA, sB, sJ, sE), and the
 // controller bins of the last interval choice: the fine bins' group ids and each group's
-// A_b and B_b.
-constexpr int kBinQ = 5;          // cnt, sM, sA, sB, sJ
+// A_b and B_b.  sE is not a sum: the largest relative error bound of the mixed form's FP32
+// moment contributions in the bin (0 in the FP64 form).
+constexpr int kBinQ = 6;          // cnt, sM, sA, sB, sJ, sE
 struct BinsDev {
-  double cnt[kNFine], sM[kNFine], sA[kNFine], sB[kNFine], sJ[kNFine];
+  double cnt[kNFine], sM[kNFine], sA[kNFine], sB[kNFine], sJ[kNFine], sE[kNFine];
   double gA[kNFine], gB[kNFine];
   int gid[kNFine];
   int ngroups;
@@ -126,11 +130,21 @@ __device__ __forceinline__ bool tile_range(const TileMap& tm, int tile, int& b, 
 
 // One particle's contribution to the fine-bin sums of the interval choice (FP64 form):
 // M_i, M_i pref sum_o lambda*_io <J_io>, likewise <J_io^2>, and the fine bin.  The mixed
-// form holds the same in a float4 (M, MA, MB, bin bits).
+// form holds the same in a float4 (M, MA, MB, w) whose w packs the fine bin in its low 7
+// bits and, above them, the particle's relative error bound of its FP32 rates and moments
+// rounded up (pack_ebin / ebin_bin / ebin_err).
 struct Contrib64 {
   double M, MA, MB;
   long long fbin;
 };
+
+__device__ __forceinline__ float pack_ebin(float err, int bin) {
+  const float e = fminf(fmaxf(err, 0.0f), 1.0f);
+  const unsigned up = (__float_as_uint(e) + 127u) & ~127u;     // rounded up to 2^-16 relative
+  return __uint_as_float(up | (unsigned)bin);
+}
+__device__ __forceinline__ int ebin_bin(float w) { return (int)(__float_as_uint(w) & 127u); }
+__device__ __forceinline__ float ebin_err(float w) { return __uint_as_float(__float_as_uint(w) & ~127u); }
 
 struct Pos64 {
   double x, y, z;

@@ -91,6 +91,8 @@ struct Query {
   T e2, e1, zo;       // 2 eta R Omega, eta R Omega, Z Omega
   T cs, cB, Vg2, tRe; // c_s, 8 k_B T / pi, V_g^2 = 3/2 alpha c_s^2, Re^-1/2
   T vfrag, m0;
+  T ferr;             // mixed form: bound on the relative error common to the particle's FP32
+                      // gas constants (St factor, drift speeds, c_s, V_g^2, Re^-1/2); 0 in FP64
   int mode;
 };
 
@@ -113,34 +115,46 @@ __device__ __forceinline__ Query<T> make_query(const InstDev& P, const Gas& g, d
   q.tRe = (T)(1.0 / sqrt(g.Re));
   q.vfrag = (T)P.v_frag;
   q.m0 = (T)P.m0;
+  q.ferr = (T)0;
   q.mode = P.kernel_mode;
   return q;
 }
 
 // Ormel & Cuzzi (2007) closed-form regimes (the paper cites them without printing):
-// St1 >= St2, eps = St2/St1, t_eta = Re^-1/2, y_a = 1.6.
+// St1 >= St2, eps = St2/St1, t_eta = Re^-1/2, y_a = 1.6.  regime: 0 tiny (St1 < t_eta),
+// 1 intermediate (St1 < 1), 2 heavy; s1, s2 receive St1, St2.
 template <typename T>
-__device__ __forceinline__ T turb_dv2(T sa, T sb, T vg2, T tre) {
-  T s1 = sa > sb ? sa : sb;
-  T s2 = sa > sb ? sb : sa;
+__device__ __forceinline__ T turb_dv2(T sa, T sb, T vg2, T tre, int& regime, T& s1, T& s2) {
+  s1 = sa > sb ? sa : sb;
+  s2 = sa > sb ? sb : sa;
   const T one = (T)1;
   // mixed form: the fast FP32 quotient (about 2 ulp; every denominator here is far inside
   // its range), which costs a fraction of the IEEE division's instruction sequence
   if constexpr (sizeof(T) == 4) {
-    if (s1 < tre) return vg2 * __fdividef(s1 - s2, s1 + s2) * (__fdividef(s1 * s1, s1 + tre) - __fdividef(s2 * s2, s2 + tre));
+    if (s1 < tre) {
+      regime = 0;
+      return vg2 * __fdividef(s1 - s2, s1 + s2) * (__fdividef(s1 * s1, s1 + tre) - __fdividef(s2 * s2, s2 + tre));
+    }
     if (s1 < one) {
+      regime = 1;
       T e = __fdividef(s2, s1);
       const T ya = (T)1.6;
       return vg2 * s1 * ((T)2 * ya - (one + e) + __fdividef((T)2, one + e) * ((T)(1.0 / 2.6) + __fdividef(e * e * e, ya + e)));
     }
+    regime = 2;
     return vg2 * (__fdividef(one, one + s1) + __fdividef(one, one + s2));
   }
-  if (s1 < tre) return vg2 * (s1 - s2) / (s1 + s2) * (s1 * s1 / (s1 + tre) - s2 * s2 / (s2 + tre));
+  if (s1 < tre) {
+    regime = 0;
+    return vg2 * (s1 - s2) / (s1 + s2) * (s1 * s1 / (s1 + tre) - s2 * s2 / (s2 + tre));
+  }
   if (s1 < one) {
+    regime = 1;
     T e = s2 / s1;
     const T ya = (T)1.6;
     return vg2 * s1 * ((T)2 * ya - (one + e) + (T)2 / (one + e) * (one / (one + ya) + e * e * e / (ya + e)));
   }
+  regime = 2;
   return vg2 * (one / (one + s1) + one / (one + s2));
 }
 
@@ -149,12 +163,39 @@ struct PairOut {
   T c0, c1;       // effective channel rates in units of the per-particle prefactor
   T ncoll, psi;
   int outcome;    // 0 sticking, 1 erosion (c0 remnant, c1 debris), 2 fragmentation
+  int cert;       // mixed form: 1 when every threshold decision of the pair (outcome,
+                  // grouping, turbulence regime) is certified to be the FP64 one; FP64 form: 0
+                  // when a decision lies within 1e-10 of its threshold (a near tie)
+  T derr;         // mixed form: bound on the relative error of c0 and c1
+  T rate;         // the pair rate before the outcome split and grouping
+  int group64;    // mixed form: N_coll = floor(1e-4/psi) is beyond what the FP32 values
+                  // certify (1e-4/psi above 2^23 or near an integer): regroup64 forms it in FP64
 };
+
+constexpr float kU32 = 5.9604645e-8f;     // unit roundoff of FP32, 2^-24
 
 // One ordered pair (i, j) at i's position (Sect. 2.5.2).  Rates come out in units of
 // a per-particle prefactor: physical mode q = Nq_j (s_i+s_j)^2 dv with
 // lambda = q pi/(4 V_i) (Nq_j = N_j, or N_j 2^-64 in FP32); test modes
 // q = (m0/m_j) K_ij with lambda = q / (t0 N_K).
+//
+// Mixed form: every threshold the FP32 values decide is certified against an error bound.
+// St_i and St_j share the query's FP32 Stokes factor, so its relative error eps (q.ferr,
+// like that of the other gas constants) scales the differences St_i - St_j, a_i - a_j, ...
+// rather than cancelling; the rounding of each term (a few u of its magnitude) is what
+// cancels.  With dSt = |St_i - St_j| the absolute errors are bounded by
+//   dv_R: |2 eta R Omega| (3 eps dSt + 4u (a_i + a_j)) + eps |dv_R|   (a = St/(1+St^2), 1-Lipschitz)
+//   dv_Z: |Z Omega| (eps dSt + 2u (h_i + h_j)) + eps |dv_Z|           (h = min(St, 1/2))
+//   dv_phi: |eta R Omega| (2 eps dSt + 4u (b_i + b_j)) + eps |dv_phi| (b = 1/(1+St^2))
+//   dv_B: (eps + 4u) dv_B;  dv_t^2: (9 eps + 8u) |dv_t^2| + 6u V_g^2 |St1 - St2| in the tiny
+//   regime, (2 eps + 30u) |dv_t^2| in the intermediate one, (2 eps + 6u) |dv_t^2| above
+// and dv^2 by E2 = 2 (2 sum |dv_k| err_k + err_t + 5u dv^2) (a factor 2 of margin).  The
+// decision dv < v_frag is certified when |dv^2 - v_frag^2| > E2 + 4u v_frag^2; psi = m_j/m_i
+// (relative error <= 6u) against 0.1 and 1e-6 with a margin of 16u; N_coll = floor(1e-4/psi)
+// when 1e-4/psi (8.5u) lies more than 20u of itself from an integer below 2^23, else the
+// caller forms it from the FP64 masses (group64, regroup64); the regime of St1 against
+// Re^-1/2 and 1 with a margin of 2 (eps + 2u).  The channel rates are then within
+// derr = E2 / (2 dv^2) + 8u of the FP64 ones.
 template <typename T>
 __device__ __forceinline__ PairOut<T> pair_channels(const Query<T>& q, T s_j, T m_j, T Nq_j, T inv_m_j) {
   PairOut<T> o;
@@ -162,9 +203,15 @@ __device__ __forceinline__ PairOut<T> pair_channels(const Query<T>& q, T s_j, T 
   T psi;
   if constexpr (sizeof(T) == 8) psi = m_j / q.m; else psi = m_j * q.inv_m;
   T ncoll = one;
-  if (psi <= (T)1e-6) { if constexpr (sizeof(T) == 4) ncoll = floorf(__fdividef(1e-4f, psi)); else ncoll = floor((T)1e-4 / psi); }
+  T vg = (T)0;      // 1e-4 / psi when grouped
+  if (psi <= (T)1e-6) {
+    if constexpr (sizeof(T) == 4) vg = __fdividef(1e-4f, psi); else vg = (T)1e-4 / psi;
+    ncoll = floor(vg);
+  }
   T rate;
   int outcome;
+  bool cert = true;
+  T derr = (T)0;
   if (q.mode == GD_KERNEL_PHYSICAL) {
     T St_j = q.g * s_j;
     T aj, bj;
@@ -184,25 +231,68 @@ __device__ __forceinline__ PairOut<T> pair_channels(const Query<T>& q, T s_j, T 
     if constexpr (sizeof(T) == 4) { const float xb = q.cB * (q.inv_m + inv_m_j); vb = xb * rsqrtf(xb); }
     else vb = sqrt(q.cB * (q.inv_m + inv_m_j));
     T dvB = q.cs < vb ? q.cs : vb;
-    T t2 = turb_dv2<T>(q.St, St_j, q.Vg2, q.tRe);
+    int regime;
+    T s1, s2;
+    T t2 = turb_dv2<T>(q.St, St_j, q.Vg2, q.tRe, regime, s1, s2);
     T dvt2;
     if constexpr (sizeof(T) == 8) { T dvt = sqrt(t2); dvt2 = dvt * dvt; } else { dvt2 = t2; }
-    T dv;
-    if constexpr (sizeof(T) == 4) { const float xd = dvR * dvR + dvZ * dvZ + dvP * dvP + dvB * dvB + dvt2; dv = xd * rsqrtf(xd); }
-    else dv = sqrt(dvR * dvR + dvZ * dvZ + dvP * dvP + dvB * dvB + dvt2);
+    T dv, xd;
+    if constexpr (sizeof(T) == 4) { xd = dvR * dvR + dvZ * dvZ + dvP * dvP + dvB * dvB + dvt2; dv = xd * rsqrtf(xd); }
+    else { xd = dvR * dvR + dvZ * dvZ + dvP * dvP + dvB * dvB + dvt2; dv = sqrt(xd); }
     T ss = q.s + s_j;
     rate = Nq_j * (ss * ss * dv);
     outcome = (dv < q.vfrag) ? 0 : ((psi <= (T)0.1) ? 1 : 2);
+    if constexpr (sizeof(T) == 4) {
+      const float u = kU32, eps = q.ferr;
+      const float dSt = fabsf(q.St - St_j);
+      const float eR = fabsf(q.e2) * (3.f * eps * dSt + 4.f * u * (q.ai + aj)) + eps * fabsf(dvR);
+      const float eZ = fabsf(q.zo) * (eps * dSt + 2.f * u * (q.hi + hj)) + eps * fabsf(dvZ);
+      const float eP = fabsf(q.e1) * (2.f * eps * dSt + 4.f * u * (q.bi + bj)) + eps * fabsf(dvP);
+      const float eB = (eps + 4.f * u) * dvB;
+      float eT;
+      if (regime == 0) eT = (9.f * eps + 8.f * u) * fabsf(t2) + 6.f * u * q.Vg2 * (s1 - s2);
+      else if (regime == 1) eT = (2.f * eps + 30.f * u) * fabsf(t2);
+      else eT = (2.f * eps + 6.f * u) * fabsf(t2);
+      const float E2 =
+          2.f * (2.f * (fabsf(dvR) * eR + fabsf(dvZ) * eZ + fabsf(dvP) * eP + dvB * eB) + eT + 5.f * u * xd);
+      const float vf2 = q.vfrag * q.vfrag;
+      const float mr = 2.f * (eps + 2.f * u);
+      cert = fabsf(xd - vf2) > E2 + 4.f * u * vf2 && fabsf(s1 - q.tRe) > mr * (s1 + q.tRe) &&
+             fabsf(s1 - one) > mr * s1;
+      if (outcome != 0) cert = cert && fabsf(psi - 0.1f) > 16.f * u * 0.1f;
+      derr = __fdividef(E2, 2.f * xd) + 8.f * u;
+    } else {
+      const double tie = 1e-10;
+      cert = !(fabs(dv - q.vfrag) <= tie * q.vfrag || fabs(s1 - q.tRe) <= tie * (s1 + q.tRe) ||
+               fabs(s1 - one) <= tie || (outcome != 0 && fabs(psi - 0.1) <= tie * 0.1));
+    }
   } else {
     T Kk = one;
     if (q.mode == GD_KERNEL_LINEAR) Kk = (q.m + m_j) / q.m0;
     if (q.mode == GD_KERNEL_PRODUCT) Kk = q.m * m_j / (q.m0 * q.m0);
     rate = q.m0 * inv_m_j * Kk;
     outcome = 0;
+    if constexpr (sizeof(T) == 4) derr = 12.f * kU32;
+  }
+  // grouping: psi against 1e-6 and N_coll = floor(1e-4 / psi)
+  int group64 = 0;
+  if constexpr (sizeof(T) == 4) {
+    const float u = kU32;
+    cert = cert && fabsf(psi - 1e-6f) > 16.f * u * 1e-6f;
+    if (psi <= 1e-6f && !(vg < 8388608.f && vg - ncoll > 20.f * u * vg && ncoll + 1.f - vg > 20.f * u * vg))
+      group64 = 1;
+  } else {
+    const double tie = 1e-10;
+    if (fabs(psi - 1e-6) <= tie * 1e-6) cert = false;
+    if (psi <= 1e-6 && (vg - ncoll <= tie * vg || ncoll + 1.0 - vg <= tie * vg)) cert = false;
   }
   o.psi = psi;
   o.ncoll = ncoll;
   o.outcome = outcome;
+  o.cert = cert ? 1 : 0;
+  o.derr = derr;
+  o.rate = rate;
+  o.group64 = group64;
   if (outcome == 0) {
     if constexpr (sizeof(T) == 4) o.c0 = (ncoll == one) ? rate : __fdividef(rate, ncoll);
     else o.c0 = (ncoll == one) ? rate : rate / ncoll;
@@ -216,6 +306,23 @@ __device__ __forceinline__ PairOut<T> pair_channels(const Query<T>& q, T s_j, T 
     o.c1 = (T)0;
   }
   return o;
+}
+
+// Mixed form: N_coll of a grouped pair from the FP64 masses m_i and m_j with the FP64 form's
+// operations (psi = m_j / m_i, floor(1e-4 / psi)), the channel rates recomputed with it in
+// FP32 (N_coll rounded to FP32, half a unit more of error).  A count within 1e-10 of an
+// integer boundary stays uncertified.
+__device__ __forceinline__ void regroup64(PairOut<float>& o, double m_i, double m_j) {
+  const double psi = m_j / m_i;
+  const double vg = 1e-4 / psi;
+  const double n = floor(vg);
+  if (vg - n <= 1e-10 * vg || n + 1.0 - vg <= 1e-10 * vg) o.cert = 0;
+  const float nf = (float)n;
+  o.ncoll = nf;
+  if (o.outcome == 0) o.c0 = __fdividef(o.rate, nf);
+  else if (o.outcome == 1) o.c0 = __fdividef((1.0f - o.psi) * o.rate, nf);
+  o.derr += 3.f * kU32;
+  o.group64 = 0;
 }
 
 // J = |ln(s'/s_i)| of the deterministic channels (Sect. 2.5.3): ln(1 + N psi)/3 for

@@ -42,6 +42,10 @@ struct McArgs {
   const float4* gx;           // mixed form: FP32 (R, Z, M) and the fine bin of each rank
   const float* pref32;        // mixed form: FP32 rate prefactor of each rank
   void* contrib;              // rank order: fine-bin contribution of each particle (rate kernel)
+  int* redo;                  // mixed form: ranks whose rates or sampling are redone in FP64
+  unsigned long long* redo_n; //   (their number; zeroed before the launch)
+  const int* list;            // FP64 list mode: the ranks to process
+  const unsigned long long* list_n;
   double* MJ;                 // caller order: M_i times the realised sum of |ln s'/s| (sampler)
   double* part;               // per-tile fine-bin partial sums [kBinQ][kNFine][n_tiles]
   long long n_tiles;
@@ -52,10 +56,12 @@ struct McArgs {
 template <typename T>
 struct Fixed {
   T gst, e2, e1, zo, cs, cB, Vg2, tRe, vfrag, m0, smin;
+  T ferr;             // mixed form: common relative error bound of the FP32 gas constants
   T prefT;            // the prefactor in the pair precision
   double pref;        // lambda = pref * (pair rate in kernel units)
   double rho_s, s_min, M;
   double k6;          // 6 / (pi rho_s): s^3 = k6 m
+  double mk;          // pi rho_s / 6: m = mk s^3
   int mode;
 };
 
@@ -73,12 +79,14 @@ __device__ __forceinline__ Fixed<T> make_fixed(const InstDev& P, const Gas& g, d
   f.vfrag = P.v_frag;
   f.m0 = P.m0;
   f.smin = P.s_min;
+  f.ferr = (T)0;
   f.pref = rate_prefactor(P, V, K, sizeof(T) == 4);
   f.prefT = (T)f.pref;
   f.rho_s = P.rho_s;
   f.s_min = P.s_min;
   f.M = M;
   f.k6 = 6.0 / (kPi * P.rho_s);
+  f.mk = kPi * P.rho_s / 6.0;
   f.mode = P.kernel_mode;
   return f;
 }
@@ -87,6 +95,12 @@ __device__ __forceinline__ Fixed<T> make_fixed(const InstDev& P, const Gas& g, d
 // (R, Z, M, fine bin) and FP32 prefactor, both written once per build; they only feed FP32
 // pair arithmetic.  Omega = sqrt(GM/R)/R keeps R^3 out of the FP32 range, and
 // 1 - R/r = Z^2/(r (r + R)) avoids the cancellation of the literal form.
+// ferr bounds the relative error these constants share, counted operation by operation
+// from R and Z rounded once (u each) with the documented ulp bounds of expf (2) and rsqrtf
+// (2) and 8 ulp taken for powf: the Stokes factor (15 + 27.5 v) u with v the vertical
+// exponent (its own error 27.5 u amplified v times by exp), Re^-1/2 (27 + 14 v) u, c_s 6 u,
+// V_g^2 14.5 u, the drift speeds 5 u plus eta's (21 |A| + 7 |B|) / |A + B| u, A and B its two
+// terms, and 1.5 u per unit of |p|, |q| from the radius ratio; the largest, doubled.
 __device__ __forceinline__ Fixed<float> make_fixed_f32(const InstDev& P, float4 gx, float pref) {
   const float R = gx.x, Z = gx.y;
   const float r = sqrtf(R * R + Z * Z);
@@ -100,7 +114,8 @@ __device__ __forceinline__ Fixed<float> make_fixed_f32(const InstDev& P, float4 
   const float omr = Z * Z / (r * (r + R));
   const float vert = omr / (h * h);
   const float rho = Sigma / (2.5066283f * H) * expf(-vert);
-  const float eta = -0.5f * ((P.f_p + 0.5f * P.f_q - 1.5f) * h * h + P.f_q * omr);
+  const float eA = (P.f_p + 0.5f * P.f_q - 1.5f) * h * h, eB = P.f_q * omr;
+  const float eta = -0.5f * (eA + eB);
   const float numol = 0.5f * 1.5957691f * cs * ((float)(kMu * kMH / kSigH2) / rho);
   Fixed<float> f;
   f.gst = 3.14159265f * P.f_rho_s / (4.0f * Sigma) * expf(vert);
@@ -114,13 +129,37 @@ __device__ __forceinline__ Fixed<float> make_fixed_f32(const InstDev& P, float4 
   f.vfrag = P.f_vfrag;
   f.m0 = P.f_m0;
   f.smin = P.f_smin;
+  {
+    const float pw = 1.5f * fmaxf(fabsf(P.f_p), fabsf(P.f_q));
+    const float fe_eta = __fdividef(21.f * fabsf(eA) + 7.f * fabsf(eB), fmaxf(fabsf(eA + eB), 1e-30f)) + 6.f;
+    const float fe = fmaxf(fe_eta, 27.f + 28.f * vert) + pw;
+    f.ferr = 2.f * fe * kU32;
+  }
   f.prefT = pref;
   f.pref = (double)pref;
   f.rho_s = P.rho_s;
   f.s_min = P.s_min;
   f.M = (double)gx.z;
   f.k6 = P.k6;
+  f.mk = P.mk;
   f.mode = P.kernel_mode;
+  return f;
+}
+
+// Mixed form from FP64-accurate constants: the FP64 fixed part rounded once to FP32, so the
+// common relative error of the gas constants is their rounding (u/2 each; 2u is taken).
+// The sampler uses it for particles that expect many events, whose many decisions it makes
+// far easier to certify.
+__device__ __forceinline__ Fixed<float> fixed_f32_of(const Fixed<double>& d, float pref32) {
+  Fixed<float> f;
+  f.gst = (float)d.gst; f.e2 = (float)d.e2; f.e1 = (float)d.e1; f.zo = (float)d.zo;
+  f.cs = (float)d.cs; f.cB = (float)d.cB; f.Vg2 = (float)d.Vg2; f.tRe = (float)d.tRe;
+  f.vfrag = (float)d.vfrag; f.m0 = (float)d.m0; f.smin = (float)d.smin;
+  f.ferr = 2.f * kU32;
+  f.prefT = pref32;
+  f.pref = (double)pref32;
+  f.rho_s = d.rho_s; f.s_min = d.s_min; f.M = d.M; f.k6 = d.k6; f.mk = d.mk;
+  f.mode = d.mode;
   return f;
 }
 
@@ -162,6 +201,7 @@ __device__ __forceinline__ Query<float> live_query_f32(const Fixed<float>& f, fl
   q.e2 = f.e2; q.e1 = f.e1; q.zo = f.zo;
   q.cs = f.cs; q.cB = f.cB; q.Vg2 = f.Vg2; q.tRe = f.tRe;
   q.vfrag = f.vfrag; q.m0 = f.m0;
+  q.ferr = f.ferr;
   q.mode = f.mode;
   return q;
 }
@@ -182,6 +222,7 @@ __device__ __forceinline__ Query<T> live_query(const Fixed<T>& f, double s, doub
     q.e2 = f.e2; q.e1 = f.e1; q.zo = f.zo;
     q.cs = f.cs; q.cB = f.cB; q.Vg2 = f.Vg2; q.tRe = f.tRe;
     q.vfrag = f.vfrag; q.m0 = f.m0;
+    q.ferr = 0.0;
     q.mode = f.mode;
     return q;
   } else {
@@ -203,6 +244,7 @@ __device__ __forceinline__ Query<float> live_query_f(const Fixed<float>& f, floa
   q.e2 = f.e2; q.e1 = f.e1; q.zo = f.zo;
   q.cs = f.cs; q.cB = f.cB; q.Vg2 = f.Vg2; q.tRe = f.tRe;
   q.vfrag = f.vfrag; q.m0 = f.m0;
+  q.ferr = f.ferr;
   q.mode = f.mode;
   return q;
 }
@@ -219,6 +261,7 @@ __device__ __forceinline__ Query<T> shfl_query(const Query<T>& a, int src) {
   q.cB = __shfl_sync(FULLM, a.cB, src); q.Vg2 = __shfl_sync(FULLM, a.Vg2, src);
   q.tRe = __shfl_sync(FULLM, a.tRe, src); q.vfrag = __shfl_sync(FULLM, a.vfrag, src);
   q.m0 = __shfl_sync(FULLM, a.m0, src); q.mode = __shfl_sync(FULLM, a.mode, src);
+  q.ferr = __shfl_sync(FULLM, a.ferr, src);
   return q;
 }
 
@@ -236,12 +279,14 @@ __device__ __forceinline__ Fixed<T> shfl_fixed(const Fixed<T>& a, int src) {
   f.vfrag = __shfl_sync(FULLM, a.vfrag, src);
   f.m0 = __shfl_sync(FULLM, a.m0, src);
   f.smin = __shfl_sync(FULLM, a.smin, src);
+  f.ferr = __shfl_sync(FULLM, a.ferr, src);
   f.prefT = __shfl_sync(FULLM, a.prefT, src);
   f.pref = __shfl_sync(FULLM, a.pref, src);
   f.rho_s = __shfl_sync(FULLM, a.rho_s, src);
   f.s_min = __shfl_sync(FULLM, a.s_min, src);
   f.M = __shfl_sync(FULLM, a.M, src);
   f.k6 = __shfl_sync(FULLM, a.k6, src);
+  f.mk = __shfl_sync(FULLM, a.mk, src);
   f.mode = __shfl_sync(FULLM, a.mode, src);
   return f;
 }
@@ -282,10 +327,12 @@ __device__ __forceinline__ void load_partners(const McArgs& A, const int (&jr)[S
 }
 
 // Channel rates of the S slots of this lane from loaded partners, plus the lane's
-// sequential sum in FP64 (slot-major, channel-minor).
+// sequential sum in FP64 (slot-major, channel-minor).  Mixed form: a grouped pair whose
+// N_coll the FP32 values cannot certify takes it from the FP64 masses (m64: the query's).
 template <typename T, int S>
-__device__ __forceinline__ double channels_of(const Query<T>& q, const int (&jr)[S], const Partner<T> (&pt)[S],
-                                              T (&c0)[S], T (&c1)[S], PairOut<T> (&po)[S]) {
+__device__ __forceinline__ double channels_of(const McArgs& A, const Query<T>& q, double m64, const int (&jr)[S],
+                                              const Partner<T> (&pt)[S], T (&c0)[S], T (&c1)[S],
+                                              PairOut<T> (&po)[S]) {
   double v = 0.0;
 #pragma unroll
   for (int t = 0; t < S; ++t) {
@@ -293,6 +340,9 @@ __device__ __forceinline__ double channels_of(const Query<T>& q, const int (&jr)
     po[t].outcome = 0; po[t].ncoll = (T)1; po[t].psi = (T)0;
     if (jr[t] >= 0) {
       po[t] = pair_channels<T>(q, pt[t].s, pt[t].m, pt[t].Nq, pt[t].inv_m);
+      if constexpr (sizeof(T) == 4) {
+        if (po[t].group64) regroup64(po[t], m64, A.snap64[jr[t]].m);
+      }
       c0[t] = po[t].c0;
       c1[t] = po[t].c1;
       v = __dadd_rn(v, (double)c0[t]);
@@ -303,17 +353,13 @@ __device__ __forceinline__ double channels_of(const Query<T>& q, const int (&jr)
 }
 
 template <typename T, int S>
-__device__ __forceinline__ double lane_channels(const McArgs& A, const Query<T>& q, long long rp, int lane,
-                                                T (&c0)[S], T (&c1)[S], int (&jr)[S], PairOut<T> (&po)[S]) {
+__device__ __forceinline__ double lane_channels(const McArgs& A, const Query<T>& q, double m64, long long rp,
+                                                int lane, T (&c0)[S], T (&c1)[S], int (&jr)[S], PairOut<T> (&po)[S]) {
   Partner<T> pt[S];
   load_row_slots<S>(A, rp, lane, jr);
   load_partners<T, S>(A, jr, pt);
-  return channels_of<T, S>(q, jr, pt, c0, c1, po);
+  return channels_of<T, S>(A, q, m64, jr, pt, c0, c1, po);
 }
-
-// Relative tolerance of a near tie (a draw this close to a decision boundary is counted):
-// FP64 form 1e-10; mixed form 2e-5, above the FP32 error of the pair rates.
-template <typename T> __device__ __forceinline__ double tie_tol() { return sizeof(T) == 8 ? 1e-10 : 2e-5; }
 
 // s^3 = 6 m / (pi rho_o).  The mixed form multiplies by the per-particle constant.
 template <typename T>
@@ -425,6 +471,87 @@ __device__ __forceinline__ void warp_bin_add(Acc* acc, int* cnt, int fbin, const
 // <J^2>, and its fine bin) is written in rank order; k_bins_tile adds them up in caller order.
 // Mixed form: FP32 throughout the particle's work, from its FP32 gas coordinates, snapshot
 // and prefactor.
+// One particle's lambda*_i and fine-bin contribution; returns false when a pair's threshold
+// decision is uncertified (mixed form).  err: mixed form, bound on the relative error of the
+// FP32 lambda*_i and moments -- the pairs' absolute error bounds derr_k c_k summed and divided
+// by the sums they bound (lambda*_i and both moments; the largest of the three), plus the
+// FP32 sums' and the moments' roundings; 0 in the FP64 form.  A pair of nearly equal grains
+// can have a large relative bound (St_i - St_j cancels in FP32) but then has a tiny rate.
+template <typename T>
+__device__ __forceinline__ bool rate_particle(const McArgs& A, const InstDev& P, long long r, double& lam,
+                                              T (&v)[3], int& fbin, float& err) {
+  Fixed<T> fx;
+  Query<T> q;
+  T j1, j2;
+  if constexpr (sizeof(T) == 8) {
+    const Pos64 p = A.pos64[r];
+    const Snap64 sn = A.snap64[r];
+    Gas g = gas_of(P, p);
+    fx = make_fixed<double>(P, g, A.V[r], A.Mr[r], A.K);
+    frag_moments(sn.s, P.s_min, j1, j2);
+    q = live_query<T>(fx, sn.s, sn.m);
+    fbin = fine_bin(sn.s);
+  } else {
+    const float4 g4 = A.gx[r];
+    const float4 sn = A.snap32[r];
+    fx = make_fixed_f32(P, g4, A.pref32[r]);
+    frag_moments_f32(sn.x, fx.smin, j1, j2);
+    q = live_query_f32(fx, sn.x, sn.y);
+    fbin = __float_as_int(g4.w);
+  }
+  const int* row = A.nbr + r * A.K;
+  const long long ci = A.chan_out ? (long long)A.perm[r] * A.K : 0;
+  T tot = (T)0, la = (T)0, lb = (T)0;
+  bool cert = true;
+  float et = 0.0f, ea = 0.0f, eb = 0.0f;   // mixed form: absolute error bounds of the sums
+  // partners loaded one slot ahead of the pair being evaluated
+  int jn = __ldg(row);
+  Partner<T> pn = load_partner<T>(A, jn);
+  for (int k = 0; k < A.K; ++k) {
+    const Partner<T> pt = pn;
+    const int jn_cur = jn;
+    if (k + 1 < A.K) { jn = __ldg(row + k + 1); pn = load_partner<T>(A, jn); }
+    PairOut<T> po = pair_channels<T>(q, pt.s, pt.m, pt.Nq, pt.inv_m);
+    if constexpr (sizeof(T) == 4) {
+      if (po.group64) regroup64(po, A.snap64[r].m, A.snap64[jn_cur].m);
+    }
+    if constexpr (sizeof(T) == 8) { tot = __dadd_rn(tot, po.c0); tot = __dadd_rn(tot, po.c1); }
+    else { tot += po.c0; tot += po.c1; cert = cert && po.cert; }
+    T a, bb;
+    pair_moments<T>(po, j1, j2, a, bb);
+    la += a;
+    lb += bb;
+    if constexpr (sizeof(T) == 4) {
+      et = fmaf((float)po.derr, po.c0 + po.c1, et);
+      ea = fmaf((float)po.derr, a, ea);
+      eb = fmaf((float)po.derr, bb, eb);
+    }
+    if (A.chan_out) {
+      A.chan_out[(ci + k) * 2] = fx.pref * (double)po.c0;
+      A.chan_out[(ci + k) * 2 + 1] = fx.pref * (double)po.c1;
+    }
+  }
+  if constexpr (sizeof(T) == 8) {
+    lam = fx.pref * tot;
+    v[0] = fx.M;
+    v[1] = fx.M * (fx.pref * la);
+    v[2] = fx.M * (fx.pref * lb);
+    err = 0.0f;
+  } else {
+    const float rl = tot > 0.0f ? __fdividef(et, tot) : 0.0f;
+    const float ra = la > 0.0f ? __fdividef(ea, la) : 0.0f;
+    const float rb = lb > 0.0f ? __fdividef(eb, lb) : 0.0f;
+    err = fmaxf(rl, fmaxf(ra, rb)) * 1.0001f + (2.f * A.K + 16.f) * kU32;
+    const float lf = fx.prefT * tot;
+    lam = (lf > 1e-30f && lf < 1e30f) ? (double)lf : fx.pref * (double)tot;
+    const float Mf = A.gx[r].z;
+    v[0] = Mf;
+    v[1] = Mf * (fx.prefT * la);
+    v[2] = Mf * (fx.prefT * lb);
+  }
+  return cert;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128) k_rates(McArgs A, TileMap tm) {
   int b;
@@ -432,63 +559,45 @@ __global__ void __launch_bounds__(128) k_rates(McArgs A, TileMap tm) {
   tile_range(tm, blockIdx.x, b, lo, hi);
   const InstDev& P = A.P[b];
   for (long long r = lo + threadIdx.x; r < hi; r += blockDim.x) {
-    Fixed<T> fx;
-    Query<T> q;
-    T j1, j2;
-    int fbin;
-    if constexpr (sizeof(T) == 8) {
-      const Pos64 p = A.pos64[r];
-      const Snap64 sn = A.snap64[r];
-      Gas g = gas_of(P, p);
-      fx = make_fixed<double>(P, g, A.V[r], A.Mr[r], A.K);
-      frag_moments(sn.s, P.s_min, j1, j2);
-      q = live_query<T>(fx, sn.s, sn.m);
-      fbin = fine_bin(sn.s);
-    } else {
-      const float4 g4 = A.gx[r];
-      const float4 sn = A.snap32[r];
-      fx = make_fixed_f32(P, g4, A.pref32[r]);
-      frag_moments_f32(sn.x, fx.smin, j1, j2);
-      q = live_query_f32(fx, sn.x, sn.y);
-      fbin = __float_as_int(g4.w);
-    }
-    const int* row = A.nbr + r * A.K;
-    const long long ci = A.chan_out ? (long long)A.perm[r] * A.K : 0;
-    T tot = (T)0, la = (T)0, lb = (T)0;
-    // partners loaded one slot ahead of the pair being evaluated
-    int jn = __ldg(row);
-    Partner<T> pn = load_partner<T>(A, jn);
-    for (int k = 0; k < A.K; ++k) {
-      const Partner<T> pt = pn;
-      if (k + 1 < A.K) { jn = __ldg(row + k + 1); pn = load_partner<T>(A, jn); }
-      const PairOut<T> po = pair_channels<T>(q, pt.s, pt.m, pt.Nq, pt.inv_m);
-      if constexpr (sizeof(T) == 8) { tot = __dadd_rn(tot, po.c0); tot = __dadd_rn(tot, po.c1); }
-      else { tot += po.c0; tot += po.c1; }
-      T a, bb;
-      pair_moments<T>(po, j1, j2, a, bb);
-      la += a;
-      lb += bb;
-      if (A.chan_out) {
-        A.chan_out[(ci + k) * 2] = fx.pref * (double)po.c0;
-        A.chan_out[(ci + k) * 2 + 1] = fx.pref * (double)po.c1;
-      }
-    }
     double lam;
+    T v[3];
+    int fbin;
+    float err;
+    const bool cert = rate_particle<T>(A, P, r, lam, v, fbin, err);
     if constexpr (sizeof(T) == 8) {
-      lam = fx.pref * tot;
       Contrib64 c;
-      c.M = fx.M;
-      c.MA = fx.M * (fx.pref * la);
-      c.MB = fx.M * (fx.pref * lb);
-      c.fbin = fbin;
+      c.M = v[0]; c.MA = v[1]; c.MB = v[2]; c.fbin = fbin;
       static_cast<Contrib64*>(A.contrib)[r] = c;
     } else {
-      const float lf = fx.prefT * tot;
-      lam = (lf > 1e-30f && lf < 1e30f) ? (double)lf : fx.pref * (double)tot;
-      const float Mf = A.gx[r].z;
-      static_cast<float4*>(A.contrib)[r] =
-          make_float4(Mf, Mf * (fx.prefT * la), Mf * (fx.prefT * lb), __int_as_float(fbin));
+      static_cast<float4*>(A.contrib)[r] = make_float4(v[0], v[1], v[2], pack_ebin(err, fbin));
+      // a threshold decision the FP32 values cannot certify: the particle's rates are redone
+      // in FP64 (k_rates_redo)
+      if (!cert) {
+        A.redo[atomicAdd(A.redo_n, 1ull)] = (int)r;
+        atomicAdd((unsigned long long*)&A.st[b].rate_redo, 1ull);
+      }
     }
+    A.lam[r] = lam;
+    if (!isfinite(lam)) set_status(&A.st[b], GD_ST_NONFINITE);
+  }
+}
+
+// Mixed form: the particles k_rates could not certify, redone in FP64 (the FP64 form's
+// arithmetic), their lambda*_i and fine-bin contributions written over the FP32 ones.
+__global__ void __launch_bounds__(128) k_rates_redo(McArgs A) {
+  const long long total = (long long)*A.list_n;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long r = A.list[t];
+    const int b = inst_of(A.off, A.n_inst, r);
+    double lam;
+    double v[3];
+    int fbin;
+    float err;
+    rate_particle<double>(A, A.P[b], r, lam, v, fbin, err);
+    // FP64 values rounded to FP32: half a unit of their last place
+    static_cast<float4*>(A.contrib)[r] =
+        make_float4((float)v[0], (float)v[1], (float)v[2], pack_ebin(2.f * kU32, fbin));
     A.lam[r] = lam;
     if (!isfinite(lam)) set_status(&A.st[b], GD_ST_NONFINITE);
   }
@@ -506,9 +615,11 @@ __global__ void __launch_bounds__(128) k_bins_tile(TileMap tm, const int* __rest
   constexpr int NW = 4;
   __shared__ T acc[NW][3 * kNFine];
   __shared__ int cnt[NW][kNFine];
+  __shared__ unsigned emax[kNFine];   // bits of non-negative floats: their order as integers
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int t = threadIdx.x; t < NW * 3 * kNFine; t += blockDim.x) (&acc[0][0])[t] = (T)0;
   for (int t = threadIdx.x; t < NW * kNFine; t += blockDim.x) (&cnt[0][0])[t] = 0;
+  for (int t = threadIdx.x; t < kNFine; t += blockDim.x) emax[t] = 0u;
   __syncthreads();
   int b;
   long long lo, hi;
@@ -526,13 +637,15 @@ __global__ void __launch_bounds__(128) k_bins_tile(TileMap tm, const int* __rest
       } else {
         const float4 c = static_cast<const float4*>(contrib)[r];
         v[0] = c.x; v[1] = c.y; v[2] = c.z;
-        fb = __float_as_int(c.w);
+        fb = ebin_bin(c.w);
+        atomicMax(&emax[fb], __float_as_uint(ebin_err(c.w)));   // a maximum: any order
       }
     }
     warp_bin_add<T, 3>(&acc[w][0], &cnt[w][0], fb, v, lane);
   }
   __syncthreads();
   for (int f = threadIdx.x; f < kNFine; f += blockDim.x) {
+    part[(5LL * kNFine + f) * n_tiles + blockIdx.x] = (double)__uint_as_float(emax[f]);
     double c = 0.0, sM = 0.0, sA = 0.0, sB = 0.0;
     for (int ww = 0; ww < NW; ++ww) {
       c += (double)cnt[ww][f];
@@ -570,7 +683,7 @@ __global__ void __launch_bounds__(128) k_jbins(TileMap tm, const int* __restrict
       v[0] = MJ[i];
       if (v[0] != 0.0) {
         const int r = rank_of[i];
-        if (kMixed) fb = __float_as_int(static_cast<const float4*>(contrib)[r].w);
+        if (kMixed) fb = ebin_bin(static_cast<const float4*>(contrib)[r].w);
         else fb = (int)static_cast<const Contrib64*>(contrib)[r].fbin;
       }
     }
@@ -586,19 +699,27 @@ __global__ void __launch_bounds__(128) k_jbins(TileMap tm, const int* __restrict
 
 // Per-instance fine-bin sums from the tile partials, in a fixed order: one warp per
 // (quantity, bin); lane l adds the instance's tiles l, l + 32, ... in order, then the lanes'
-// sums meet in a fixed butterfly.  Quantities q0 .. q0 + nq - 1 of BinsDev (cnt, sM, sA, sB,
-// sJ) are overwritten.
+// sums meet in a fixed butterfly (quantity 5, an error bound, takes the maximum instead).
+// Quantities q0 .. q0 + nq - 1 of BinsDev (cnt, sM, sA, sB, sJ, sE) except skip_q are
+// overwritten.
 __global__ void k_bins_reduce(const long long* __restrict__ tile_off, const double* __restrict__ part,
-                              long long n_tiles, int q0, int nq, BinsDev* bins) {
+                              long long n_tiles, int q0, int nq, int skip_q, BinsDev* bins) {
   const int b = blockIdx.x;
   const int lane = threadIdx.x & 31;
   const int pair = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (pair >= nq * kNFine) return;
   const int q = q0 + pair / kNFine, f = pair % kNFine;
+  if (q == skip_q) return;
   const double* src = part + ((long long)q * kNFine + f) * n_tiles;
   double v = 0.0;
-  for (long long t = tile_off[b] + lane; t < tile_off[b + 1]; t += 32) v += src[t];
-  v = warp_sum(v);
+  if (q == 5) {
+    for (long long t = tile_off[b] + lane; t < tile_off[b + 1]; t += 32) v = fmax(v, src[t]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  } else {
+    for (long long t = tile_off[b] + lane; t < tile_off[b + 1]; t += 32) v += src[t];
+    v = warp_sum(v);
+  }
   if (lane == 0) (&bins[b].cnt[0])[q * kNFine + f] = v;
 }
 
@@ -606,18 +727,21 @@ __global__ void k_bins_reduce(const long long* __restrict__ tile_off, const doub
 // One block per instance: the fine bins are read into shared memory by all threads, then
 // one thread merges them into controller bins (>= max(K, 64) particles, ascending, a
 // remainder joins the previous bin), forms A_b and B_b in one ascending pass, and halves
-// dt_coll with the exact tick count of the time left.
+// dt_coll with the exact tick count of the time left.  A near tie of the interval choice is
+// a binding moment within 1e-10 (FP64 form) of a halving edge; in the mixed form within
+// 1.5 times the error bound of the binding bin's FP32 moments (their largest per-particle
+// bound plus 64 u of summation), at least 2e-5.
 __global__ void k_interval(const InstDev* __restrict__ P, StateDev* st, BinsDev* bins, int n_inst, int K,
-                           int no_audit, double tie) {
-  __shared__ double cnt[kNFine], sM[kNFine], sA[kNFine], sB[kNFine];
-  __shared__ double gM[kNFine], gA[kNFine], gB[kNFine];
+                           int no_audit, int mixed) {
+  __shared__ double cnt[kNFine], sM[kNFine], sA[kNFine], sB[kNFine], sE[kNFine];
+  __shared__ double gM[kNFine], gA[kNFine], gB[kNFine], gE[kNFine];
   __shared__ int gid[kNFine];
   const int b = blockIdx.x;
   if (b >= n_inst) return;
   BinsDev& Bn = bins[b];
   for (int f = threadIdx.x; f < kNFine; f += blockDim.x) {
-    cnt[f] = Bn.cnt[f]; sM[f] = Bn.sM[f]; sA[f] = Bn.sA[f]; sB[f] = Bn.sB[f];
-    gM[f] = 0.0; gA[f] = 0.0; gB[f] = 0.0;
+    cnt[f] = Bn.cnt[f]; sM[f] = Bn.sM[f]; sA[f] = Bn.sA[f]; sB[f] = Bn.sB[f]; sE[f] = Bn.sE[f];
+    gM[f] = 0.0; gA[f] = 0.0; gB[f] = 0.0; gE[f] = 0.0;
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
@@ -641,6 +765,7 @@ __global__ void k_interval(const InstDev* __restrict__ P, StateDev* st, BinsDev*
     const int g = gid[f];
     if (g < 0) continue;
     gM[g] += sM[f]; gA[g] += sA[f]; gB[g] += sB[f];
+    gE[g] = fmax(gE[g], sE[f]);
   }
   for (int f = 0; f < kNFine; ++f) Bn.gid[f] = gid[f];
   Bn.ngroups = ng;
@@ -655,15 +780,16 @@ __global__ void k_interval(const InstDev* __restrict__ P, StateDev* st, BinsDev*
   if (S.remain_ticks <= 0) S.remain_ticks = 1LL << 60;
   const double remain = ldexp((double)S.remain_ticks, -60) * dtc;
   const double dt_cap = remain < p.dt_fn_max ? remain : p.dt_fn_max;
-  double dt_ab = HUGE_VAL;
+  double dt_ab = HUGE_VAL, e_bind = 0.0;
   for (int g = 0; g < kNFine; ++g) { Bn.gA[g] = 0.0; Bn.gB[g] = 0.0; }
   for (int g = 0; g < ng; ++g) {
     const double A = gA[g] / gM[g], Bm = gB[g] / gM[g];
     Bn.gA[g] = A;
     Bn.gB[g] = Bm;
-    if (A > 0.0) { const double t = p.eps * C / A; if (t < dt_ab) dt_ab = t; }
-    if (Bm > 0.0) { const double t = p.eps * p.eps * C * C / Bm; if (t < dt_ab) dt_ab = t; }
+    if (A > 0.0) { const double t = p.eps * C / A; if (t < dt_ab) { dt_ab = t; e_bind = gE[g]; } }
+    if (Bm > 0.0) { const double t = p.eps * p.eps * C * C / Bm; if (t < dt_ab) { dt_ab = t; e_bind = gE[g]; } }
   }
+  const double tie = mixed ? fmax(2e-5, 1.5 * (e_bind + 64.0 * 0x1p-24)) : 1e-10;
   const double dt_req = dt_ab < dt_cap ? dt_ab : dt_cap;
   double dt = dtc;
   int k = 0;
@@ -684,24 +810,142 @@ __global__ void k_interval(const InstDev* __restrict__ P, StateDev* st, BinsDev*
 }
 
 // ---------------------------------------------------------------- sampler
+// Mixed form: one event decision settled with the FP64 form's arithmetic (warp-cooperative,
+// lane = slot; called by the whole warp): the FP64 gas disk at the particle, its channel
+// rates at the current state (s, m) against the frozen partners, their inclusive prefix and
+// lambda*_i; with choose, the channel the FP64 prefix selects for the draw (uw0, uw1) and its
+// partner, outcome, N_coll and psi.  Near ties are counted at the FP64 tolerance (1e-10).
+// Rare (only decisions the FP32 values cannot certify), so it is kept out of line.
+struct Fp64Pick {
+  int chosen, j, outcome, near;
+  double ncoll, psi, lam;
+};
+
+template <int S>
+__device__ __noinline__ Fp64Pick fp64_event(const McArgs& A, long long rp, int bp, double s, double m,
+                                            unsigned uw0, unsigned uw1, bool choose, int lane) {
+  const InstDev& P = A.P[bp];
+  Gas g = gas_of(P, A.pos64[rp]);
+  const Fixed<double> f = make_fixed<double>(P, g, A.V[rp], A.Mr[rp], A.K);
+  const Query<double> q = live_query<double>(f, s, m);
+  double c0[S], c1[S];
+  int jr[S];
+  PairOut<double> po[S];
+  const double v = lane_channels<double, S>(A, q, m, rp, lane, c0, c1, jr, po);
+  int near = 0;
+#pragma unroll
+  for (int t = 0; t < S; ++t)
+    if (jr[t] >= 0 && !po[t].cert) near++;
+  const double incl = warp_incl_scan(v, lane);
+  const double tot = __shfl_sync(FULLM, incl, 31);
+  Fp64Pick r;
+  r.lam = f.pref * tot;
+  r.chosen = -1; r.j = -1; r.outcome = 0; r.ncoll = 1.0; r.psi = 0.0;
+  if (choose) {
+    const double target = u01(uw0, uw1) * tot;
+    const double tie = 1e-10 * tot;
+    double cum = __shfl_up_sync(FULLM, incl, 1);
+    if (lane == 0) cum = 0.0;
+    int sel = INT_MAX, lastnz = -1;
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+      const int k = lane * S + t;
+      if (jr[t] < 0) continue;
+      cum = __dadd_rn(cum, c0[t]);
+      if (c0[t] > 0.0) {
+        lastnz = 2 * k;
+        if (fabs(target - cum) < tie) near++;
+        if (sel == INT_MAX && target < cum) sel = 2 * k;
+      }
+      cum = __dadd_rn(cum, c1[t]);
+      if (c1[t] > 0.0) {
+        lastnz = 2 * k + 1;
+        if (fabs(target - cum) < tie) near++;
+        if (sel == INT_MAX && target < cum) sel = 2 * k + 1;
+      }
+    }
+    int chosen = sel;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) chosen = min(chosen, __shfl_xor_sync(FULLM, chosen, o));
+    if (chosen == INT_MAX) {
+      int ln = lastnz;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) ln = max(ln, __shfl_xor_sync(FULLM, ln, o));
+      chosen = ln;
+      if (lane == 0) near++;
+    }
+    r.chosen = chosen;
+    if (chosen >= 0) {
+      const int slot = chosen >> 1, owner = slot / S, tsl = slot % S;
+      int jo = jr[0], oc = po[0].outcome;
+      double nco = po[0].ncoll, pso = po[0].psi;
+#pragma unroll
+      for (int t = 1; t < S; ++t)
+        if (t == tsl) { jo = jr[t]; oc = po[t].outcome; nco = po[t].ncoll; pso = po[t].psi; }
+      r.j = __shfl_sync(FULLM, jo, owner);
+      r.outcome = __shfl_sync(FULLM, oc, owner);
+      r.ncoll = __shfl_sync(FULLM, nco, owner);
+      r.psi = __shfl_sync(FULLM, pso, owner);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) near += __shfl_xor_sync(FULLM, near, o);
+  r.near = near;
+  return r;
+}
+
+// Chunks of 32 ranks are taken from a counter (lane = particle): event counts are
+// heavy-tailed, so a static assignment would leave warps idle behind the busiest chunks.
+// Each lane draws its particle's first waiting time from lambda*_i; the particles with an
+// event are then taken one at a time by the whole warp (lane = slot): the channel rates, the
+// partner channel from their inclusive prefix (warp scan), the outcome, the own rates
+// refreshed against the frozen partners, the next waiting time, until the waiting times
+// pass dt_exe.
+//
+// FP64 form: FP64 throughout.  A draw within 1e-10 of a channel boundary or of dt_exe, and a
+// pair within 1e-10 of an outcome, grouping or turbulence-regime threshold, is counted as a
+// near tie of the particle.  List mode (A.list): only the listed ranks, each lane's
+// lambda*_i formed afresh with the rate kernel's FP64 arithmetic -- the FP64 replay of the
+// particles a mixed context could not certify.
+//
+// Mixed form: FP32 channel rates, FP64 masses, fragment sizes and waiting-time sums.  Every
+// decision is certified to be the one the FP64 form takes, from error bounds:
+//  * each pair's thresholds (pair_channels), and its channel rates within their bound derr;
+//  * the FP32 prefix within eta = max derr + (2S + 7) u of the FP64 prefix (lambda*_i of the
+//    rate kernel within the bound it packed with the particle's fine bin), the FP32 target
+//    U_s lambda* within 1.5 u more: the channel is certified when the target lies more than
+//    1.5 (2 eta + 3 u) lambda* inside it;
+//  * each FP32 waiting time within eta + 8 u (the logarithm 4 u, the quotient 2 u, the
+//    prefactor's rounding) of the FP64 one: the running error bound of the time sum, and the
+//    decision against dt_exe certified when t + dt_w lies more than 1.5 times that bound
+//    (plus 1e-14 dt_exe) from dt_exe.
+// A particle with any uncertified decision is appended to A.redo and nothing of it is
+// written: the FP64 replay samples it.  The mixed form therefore reproduces the FP64 form's
+// event sequences except where the replay meets an FP64 near tie.
 template <typename T, int S>
 __global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
   const int lane = threadIdx.x & 31;
-  // chunks of 32 ranks are taken from a counter: event counts are heavy-tailed, so a
-  // static assignment would leave warps idle behind the busiest chunks
+  constexpr bool kMixed = sizeof(T) == 4;
+  const bool listed = A.list != nullptr;
+  const long long total = listed ? (long long)*A.list_n : A.N;
+  const float u = kU32;
+  // list mode (the FP64 replays): one listed particle per warp, so that the few replayed
+  // particles, often those with the most events, run side by side
+  const int per_chunk = listed ? 1 : 32;
   auto next_chunk = [&]() {
     unsigned long long c = 0;
     if (lane == 0) c = atomicAdd(A.work, 1ull);
-    return (long long)__shfl_sync(FULLM, c, 0) * 32;
+    return (long long)__shfl_sync(FULLM, c, 0) * per_chunk;
   };
-  for (long long base = next_chunk(); base < A.N; base = next_chunk()) {
-    const long long r = base + lane;
-    const bool valid = r < A.N;
+  for (long long base = next_chunk(); base < total; base = next_chunk()) {
+    const bool valid = lane < per_chunk && base + lane < total;
+    const long long r = !valid ? 0 : (listed ? (long long)A.list[base + lane] : base + lane);
     int b = 0;
     double lam = 0.0, dtw = 0.0, us = 0.0, dt_exe = 0.0;
     unsigned ival = 0, i_loc = 0, key0 = 0, key1 = 0, usw0 = 0, usw1 = 0;
-    bool ev = false;
+    bool ev = false, replay = false;
     int nn = 0;
+    float eta_lam = 0.0f;   // mixed form: error bound of the first waiting time
     if (valid) {
       b = inst_of(A.off, A.n_inst, r);
       const InstDev& P = A.P[b];
@@ -710,41 +954,48 @@ __global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
       key0 = P.key0;
       key1 = P.key1;
       i_loc = (unsigned)(A.perm[r] - P.off);
-      lam = A.lam[r];
+      if (listed) {
+        double v3[3];
+        int fb;
+        float e3;
+        rate_particle<double>(A, P, r, lam, v3, fb, e3);
+      } else {
+        lam = A.lam[r];
+      }
       U4 w = philox(i_loc, ival, 0u, 0u, key0, key1);
       usw0 = w.z;
       usw1 = w.w;
-      if constexpr (sizeof(T) == 8) us = u01(w.z, w.w);
+      if constexpr (!kMixed) us = u01(w.z, w.w);
       if (lam > 0.0 && isfinite(lam)) {
         dtw = waiting_time<T>(w.x, w.y, lam);
-        if (fabs(dtw - dt_exe) < tie_tol<T>() * dt_exe) nn++;
-        ev = !(dtw > dt_exe);
+        if constexpr (kMixed) {
+          // lambda*_i's bound from the rate kernel, the logarithm, quotient and roundings
+          eta_lam = ebin_err(reinterpret_cast<const float*>(A.contrib)[4 * r + 3]) + 8.f * u;
+          const float dd = (float)(dtw - dt_exe);
+          replay = !(fabsf(dd) > 1.5f * eta_lam * (float)dtw * 1.0001f + 1e-14f * (float)dt_exe);
+        } else {
+          if (fabs(dtw - dt_exe) < 1e-10 * dt_exe) nn++;
+        }
+        ev = !(dtw > dt_exe) && !replay;
       }
     }
     unsigned emask = __ballot_sync(FULLM, ev);
-    if (emask == 0) {
-      if (valid && nn) { atomicAdd((unsigned long long*)&A.st[b].near_draw, (unsigned long long)nn); }
-      if (valid) A.MJ[A.perm[r]] = 0.0;
-      if (valid && A.ev_count) {
-        int ci = A.perm[r];
-        A.ev_count[ci] = 0;
-        A.ev_hash[ci] = 0u;
-        A.near_out[ci] = nn;
-      }
-      continue;
-    }
     // per-lane fixed quantities of every particle of the chunk (lane = particle)
     Fixed<T> fx;
     double s_i = 1.0, m_i = 1.0;
-    if (valid) {
+    if (valid && ev) {
       const InstDev& P = A.P[b];
-      const Pos64 p = A.pos64[r];
       const Snap64 sn = A.snap64[r];
       s_i = sn.s;
       m_i = sn.m;
-      if constexpr (sizeof(T) == 8) {
-        Gas g = gas_of(P, p);
+      if constexpr (!kMixed) {
+        Gas g = gas_of(P, A.pos64[r]);
         fx = make_fixed<double>(P, g, A.V[r], A.Mr[r], A.K);
+      } else if (lam * dt_exe > 32.0) {
+        // many events expected: FP64-accurate gas constants keep every bound of the
+        // particle's many decisions near the FP32 rounding
+        Gas g = gas_of(P, A.pos64[r]);
+        fx = fixed_f32_of(make_fixed<double>(P, g, A.V[r], A.Mr[r], A.K), A.pref32[r]);
       } else {
         fx = make_fixed_f32(P, A.gx[r], A.pref32[r]);
       }
@@ -754,11 +1005,11 @@ __global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
     }
     int my_e = 0;
     unsigned my_h = 0u;
-    double my_MJ = 0.0;
+    double my_MJ = 0.0, my_s = s_i;
     while (emask) {
       const int p = __ffs(emask) - 1;
       emask &= emask - 1;
-      const long long rp = base + p;
+      const long long rp = __shfl_sync(FULLM, r, p);
       const Fixed<T> f = shfl_fixed<T>(fx, p);
       double s = __shfl_sync(FULLM, s_i, p), m = __shfl_sync(FULLM, m_i, p);
       double t = __shfl_sync(FULLM, dtw, p);
@@ -768,22 +1019,54 @@ __global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
       const unsigned iv = __shfl_sync(FULLM, ival, p), il = __shfl_sync(FULLM, i_loc, p);
       const unsigned k0 = __shfl_sync(FULLM, key0, p), k1 = __shfl_sync(FULLM, key1, p);
       const int bp = __shfl_sync(FULLM, b, p);
-      const double tie_dte = tie_tol<T>() * dte;
       // mixed form: FP32 copies of per-particle constants for the per-event FP32 steps
       const float k6f = (float)f.k6, preff = f.prefT;
       float sf = (float)s;      // mixed form: the FP32 diameter the pair rates use
       bool s_stale = false;     // mixed form: s lags m after a sticking or erosion event
-      int e = 0, near_ch = 0, near_u = 0;   // per-lane channel ties, warp-uniform ties
+      // mixed form: error bound of the time sum t (FP32; the sum itself is FP64)
+      float terr = (float)t * __shfl_sync(FULLM, eta_lam, p);
+      const float dtef = (float)dte;
+      bool unc = false;         // mixed form: an uncertified decision (warp-uniform)
+      int e = 0, near_ch = 0, near_u = 0;   // per-lane ties, warp-uniform ties
       unsigned h = 0u;
       T J = (T)0;
       T c0[S], c1[S];
       int jr[S];
       PairOut<T> po[S];
       Query<T> q = live_query<T>(f, s, m);
-      double v = lane_channels<T, S>(A, q, rp, lane, c0, c1, jr, po);
+      double v = lane_channels<T, S>(A, q, m, rp, lane, c0, c1, jr, po);
       double incl = 0.0, tot = 0.0;
-      float inclf = 0.0f, totf = 0.0f;
-      if constexpr (sizeof(T) == 8) {
+      float inclf = 0.0f, totf = 0.0f, eta = 0.0f;
+      bool bad64 = false;       // mixed form: a pair's decision is uncertified at this state
+      // certification (mixed) or near ties (FP64) of the pairs' threshold decisions
+      // mixed form: eta bounds the relative error of the FP32 prefix and of lambda*_i -- the
+      // pairs' absolute bounds derr c summed over the warp, over lambda*, plus the sums'
+      // rounding
+      auto pairs_checked = [&]() {
+        int bad = 0;
+        float de = 0.0f, cs = 0.0f;
+#pragma unroll
+        for (int t2 = 0; t2 < S; ++t2)
+          if (jr[t2] >= 0) {
+            bad += po[t2].cert ? 0 : 1;
+            if constexpr (kMixed) {
+              de = fmaf((float)po[t2].derr, (float)(c0[t2] + c1[t2]), de);
+              cs += (float)(c0[t2] + c1[t2]);
+            }
+          }
+        if constexpr (kMixed) {
+          bad64 = __any_sync(FULLM, bad != 0);
+          de = warp_sumf(de);
+          cs = warp_sumf(cs);
+          eta = (cs > 0.0f ? __fdividef(de, cs) * 1.0001f : 0.0f) + (2.f * S + 7.f) * u;
+        } else {
+          near_ch += bad;
+        }
+      };
+      // the particle's FP64 diameter (mixed form: formed from the FP64 mass when it lags)
+      auto s_exact = [&]() { return (kMixed && s_stale) ? diameter_of<T>(cube_of<T>(f, m)) : s; };
+      pairs_checked();
+      if constexpr (!kMixed) {
         incl = warp_incl_scan(v, lane);
         tot = __shfl_sync(FULLM, incl, 31);
       } else {
@@ -791,59 +1074,54 @@ __global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
         totf = __shfl_sync(FULLM, inclf, 31);
       }
       for (;;) {
+        if (unc) break;
         // partner channel: the first cumulative rate above U_s lambda*
-        int chosen = INT_MAX;
-        bool certified = false;
-        if constexpr (sizeof(T) == 4) {
-          // Mixed form: the choice of the FP64 prefix, found on the FP32 prefix.  Any FP32
-          // prefix of these FP32 rates is within (5 + 2S + 2) u lambda* of the exact one, so
-          // when the target lies more than 4e-6 lambda* inside the chosen channel both give
-          // that channel; otherwise the FP64 prefix below decides.
-          const float tf = fmaf((float)(uw0 >> 6), 0x1p26f, (float)(uw1 >> 6) + 0.5f) * 0x1p-52f * totf;
-          const float tie_f = 2e-5f * totf, mg = 4e-6f * totf;
-          float cumf = __shfl_up_sync(FULLM, inclf, 1);
-          if (lane == 0) cumf = 0.0f;
-          int sel = INT_MAX;
-          float blo = 0.0f, bhi = 0.0f;
+        int chosen = INT_MAX, j = -1, outcome = 0;
+        T ncoll_t = (T)1, psi_t = (T)0;
+        bool from_po = true;
+        if constexpr (kMixed) {
+          bool ok = false;
+          if (!bad64) {
+            const float tf = fmaf((float)(uw0 >> 6), 0x1p26f, (float)(uw1 >> 6) + 0.5f) * 0x1p-52f * totf;
+            const float mg = 1.5f * (2.f * eta + 3.f * u) * totf;
+            float cumf = __shfl_up_sync(FULLM, inclf, 1);
+            if (lane == 0) cumf = 0.0f;
+            int sel = INT_MAX;
+            float blo = 0.0f, bhi = 0.0f;
 #pragma unroll
-          for (int t2 = 0; t2 < S; ++t2) {
-            const int k = lane * S + t2;
-            if (jr[t2] < 0) continue;
-            const float b0 = cumf;
-            cumf += c0[t2];
-            if (c0[t2] > 0.0f) {
-              if (fabsf(tf - cumf) < tie_f) near_ch++;
-              if (sel == INT_MAX && tf < cumf) { sel = 2 * k; blo = b0; bhi = cumf; }
+            for (int t2 = 0; t2 < S; ++t2) {
+              const int k = lane * S + t2;
+              if (jr[t2] < 0) continue;
+              const float b0 = cumf;
+              cumf += c0[t2];
+              if (c0[t2] > 0.0f && sel == INT_MAX && tf < cumf) { sel = 2 * k; blo = b0; bhi = cumf; }
+              const float b1 = cumf;
+              cumf += c1[t2];
+              if (c1[t2] > 0.0f && sel == INT_MAX && tf < cumf) { sel = 2 * k + 1; blo = b1; bhi = cumf; }
             }
-            const float b1 = cumf;
-            cumf += c1[t2];
-            if (c1[t2] > 0.0f) {
-              if (fabsf(tf - cumf) < tie_f) near_ch++;
-              if (sel == INT_MAX && tf < cumf) { sel = 2 * k + 1; blo = b1; bhi = cumf; }
+            chosen = sel;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) chosen = min(chosen, __shfl_xor_sync(FULLM, chosen, o));
+            if (chosen != INT_MAX) {
+              const int own = (chosen >> 1) / S;
+              const bool in = (bhi - tf > mg) && (blo == 0.0f || tf - blo > mg);
+              ok = __shfl_sync(FULLM, in, own);
             }
           }
-          chosen = sel;
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) chosen = min(chosen, __shfl_xor_sync(FULLM, chosen, o));
-          if (chosen != INT_MAX) {
-            const int own = (chosen >> 1) / S;
-            const bool ok = (bhi - tf > mg) && (blo == 0.0f || tf - blo > mg);
-            certified = __shfl_sync(FULLM, ok, own);
+          if (!ok) {
+            // the FP32 values cannot certify this choice: the FP64 form's choice at this state
+            const Fp64Pick pk = fp64_event<S>(A, rp, bp, s_exact(), m, uw0, uw1, true, lane);
+            near_u += pk.near;
+            chosen = pk.chosen;
+            j = pk.j;
+            outcome = pk.outcome;
+            ncoll_t = (T)pk.ncoll;
+            psi_t = (T)pk.psi;
+            from_po = false;
           }
-          if (!certified) {
-            // the FP64 prefix of the same rates
-            v = 0.0;
-#pragma unroll
-            for (int t2 = 0; t2 < S; ++t2)
-              if (jr[t2] >= 0) { v = __dadd_rn(v, (double)c0[t2]); v = __dadd_rn(v, (double)c1[t2]); }
-            incl = warp_incl_scan(v, lane);
-            tot = __shfl_sync(FULLM, incl, 31);
-            u_s = u01(uw0, uw1);
-          }
-        }
-        if (!certified) {
+        } else {
           const double target = u_s * tot;
-          const double tie_ch = tie_tol<T>() * tot;
+          const double tie_ch = 1e-10 * tot;
           double cum = __shfl_up_sync(FULLM, incl, 1);
           if (lane == 0) cum = 0.0;
           int sel = INT_MAX, lastnz = -1;
@@ -851,17 +1129,16 @@ __global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
           for (int t2 = 0; t2 < S; ++t2) {
             int k = lane * S + t2;
             if (jr[t2] < 0) continue;
-            const double a = (double)c0[t2], bb = (double)c1[t2];
-            cum = __dadd_rn(cum, a);
+            cum = __dadd_rn(cum, (double)c0[t2]);
             if (c0[t2] > (T)0) {
               lastnz = 2 * k;
-              if (sizeof(T) == 8 && fabs(target - cum) < tie_ch) near_ch++;
+              if (fabs(target - cum) < tie_ch) near_ch++;
               if (sel == INT_MAX && target < cum) sel = 2 * k;
             }
-            cum = __dadd_rn(cum, bb);
+            cum = __dadd_rn(cum, (double)c1[t2]);
             if (c1[t2] > (T)0) {
               lastnz = 2 * k + 1;
-              if (sizeof(T) == 8 && fabs(target - cum) < tie_ch) near_ch++;
+              if (fabs(target - cum) < tie_ch) near_ch++;
               if (sel == INT_MAX && target < cum) sel = 2 * k + 1;
             }
           }
@@ -877,40 +1154,41 @@ __global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
           }
         }
         if (chosen < 0) break;
-        const int slot = chosen >> 1, ch = chosen & 1;
-        const int owner = slot / S, tsl = slot % S;
-        // partner data and outcome from the owning lane
-        int jo = jr[0], oc = po[0].outcome;
-        T nco = po[0].ncoll, pso = po[0].psi;
+        const int ch = chosen & 1;
+        if (from_po) {
+          // partner data and outcome from the owning lane
+          const int slot = chosen >> 1;
+          const int owner = slot / S, tsl = slot % S;
+          int jo = jr[0], oc = po[0].outcome;
+          T nco = po[0].ncoll, pso = po[0].psi;
 #pragma unroll
-        for (int t2 = 1; t2 < S; ++t2)
-          if (t2 == tsl) { jo = jr[t2]; oc = po[t2].outcome; nco = po[t2].ncoll; pso = po[t2].psi; }
-        const int j = __shfl_sync(FULLM, jo, owner);
-        const int outcome = __shfl_sync(FULLM, oc, owner);
-        const T ncoll_t = __shfl_sync(FULLM, nco, owner);
-        const T psi_t = __shfl_sync(FULLM, pso, owner);
+          for (int t2 = 1; t2 < S; ++t2)
+            if (t2 == tsl) { jo = jr[t2]; oc = po[t2].outcome; nco = po[t2].ncoll; pso = po[t2].psi; }
+          j = __shfl_sync(FULLM, jo, owner);
+          outcome = __shfl_sync(FULLM, oc, owner);
+          ncoll_t = __shfl_sync(FULLM, nco, owner);
+          psi_t = __shfl_sync(FULLM, pso, owner);
+        }
         const double ncoll = (double)ncoll_t;
         const Snap64 pj = A.snap64[j];
         double m_new, s_new = s;
         float Jf = 0.0f;   // mixed form: |ln s'/s| of the event from the pair's FP32 psi
         if (outcome == 0) {
-          if constexpr (sizeof(T) == 8) {
-            m_new = m + ncoll * pj.m;
+          if constexpr (!kMixed) m_new = m + ncoll * pj.m; else m_new = fma(ncoll, pj.m, m);
+          if constexpr (!kMixed) {
             s_new = diameter_of<T>(cube_of<T>(f, m_new));
           } else {
-            // mixed form: the mass in FP64; the pair rates only need the FP32 diameter, the
-            // FP64-accurate one is formed once when the particle's events are done
-            m_new = fma(ncoll, pj.m, m);
+            // the pair rates only need the FP32 diameter; the FP64-accurate one is formed
+            // when it is needed (a fragmentation, an FP64 decision, the particle's end)
             sf = cbrtf((float)m_new * k6f);
             s_stale = true;
             Jf = log1pf((float)ncoll_t * (float)psi_t) * (1.0f / 3.0f);
           }
         } else if (outcome == 1 && ch == 0) {
-          if constexpr (sizeof(T) == 8) {
-            m_new = m - ncoll * pj.m;
+          if constexpr (!kMixed) m_new = m - ncoll * pj.m; else m_new = fma(-ncoll, pj.m, m);
+          if constexpr (!kMixed) {
             s_new = diameter_of<T>(cube_of<T>(f, m_new));
           } else {
-            m_new = fma(-ncoll, pj.m, m);
             sf = cbrtf((float)m_new * k6f);
             s_stale = true;
             Jf = fabsf(log1pf(-(float)ncoll_t * (float)psi_t)) * (1.0f / 3.0f);
@@ -918,96 +1196,120 @@ __global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
         } else if (outcome == 1) {
           m_new = pj.m;
           s_new = pj.s;
-          if constexpr (sizeof(T) == 4) { sf = (float)s_new; s_stale = false; Jf = fabsf(logf((float)psi_t)) * (1.0f / 3.0f); }
+          if constexpr (kMixed) { sf = (float)s_new; s_stale = false; Jf = fabsf(logf((float)psi_t)) * (1.0f / 3.0f); }
         } else {
+          // fragmentation (Eq. frag): the size from the draw in FP64 in both forms
           U4 w2 = philox(il, iv, (unsigned)e, 1u, k0, k1);
-          if constexpr (sizeof(T) == 8) {
-            double U = u01(w2.x, w2.y);
-            double a = sqrt(f.s_min), bq = sqrt(s);
-            double xr = a + U * (bq - a);
-            s_new = xr * xr;
-            m_new = kPi * f.rho_s * s_new * s_new * s_new / 6.0;
-          } else {
-            // the fragment size is a draw: FP32 is enough; the mass follows it in FP64
-            const float U = fmaf((float)(w2.x >> 6), 0x1p26f, (float)(w2.y >> 6) + 0.5f) * 0x1p-52f;
-            const float a = sqrtf(f.smin), bq = sqrtf(sf);
-            const float xr = fmaf(U, bq - a, a);
-            sf = xr * xr;
-            s_new = (double)sf;
-            s_stale = false;
-            m_new = s_new * s_new * s_new / f.k6;
-            Jf = 2.0f * fabsf(logf(xr / bq));
+          if constexpr (kMixed) {
+            if (s_stale) { s = diameter_of<T>(cube_of<T>(f, m)); s_stale = false; }
           }
+          const double U = u01(w2.x, w2.y);
+          const double a = sqrt(f.s_min), bq = sqrt(s);
+          const double xr = a + U * (bq - a);
+          s_new = xr * xr;
+          if constexpr (!kMixed) m_new = kPi * f.rho_s * s_new * s_new * s_new / 6.0;
+          else m_new = f.mk * (s_new * s_new * s_new);
+          if constexpr (kMixed) { sf = (float)s_new; Jf = 2.0f * fabsf(logf((float)(xr / bq))); }
         }
-        if constexpr (sizeof(T) == 8) J += fabs(log(s_new / s));
+        if constexpr (!kMixed) J += fabs(log(s_new / s));
         else J += Jf;
         s = s_new;
         m = m_new;
         h = h * 31u + (unsigned)(chosen + 1);
         ++e;
         if (e >= A.max_events) { if (lane == 0) set_status(&A.st[bp], GD_ST_EVENT_CAP); break; }
-        if constexpr (sizeof(T) == 8) q = live_query<T>(f, s, m);
+        if constexpr (!kMixed) q = live_query<T>(f, s, m);
         else q = live_query_f(f, sf, (float)m);
-        v = lane_channels<T, S>(A, q, rp, lane, c0, c1, jr, po);
-        if constexpr (sizeof(T) == 8) {
+        v = lane_channels<T, S>(A, q, m, rp, lane, c0, c1, jr, po);
+        pairs_checked();
+        if constexpr (!kMixed) {
           incl = warp_incl_scan(v, lane);
           tot = __shfl_sync(FULLM, incl, 31);
         } else {
           inclf = warp_incl_scanf(lane_sumf<S>(c0, c1, jr), lane);
           totf = __shfl_sync(FULLM, inclf, 31);
         }
-        double lam_now = 0.0;   // FP64 form only
-        if constexpr (sizeof(T) == 8) {
+        double lam_now = 0.0;   // FP64 lambda*_i (FP64 form; mixed form at an uncertified state)
+        if constexpr (!kMixed) {
           lam_now = f.pref * tot;
+        } else if (bad64) {
+          const Fp64Pick pk = fp64_event<S>(A, rp, bp, s_exact(), m, 0u, 0u, false, lane);
+          near_u += pk.near;
+          lam_now = pk.lam;
+        }
+        if (!kMixed || bad64) {
           if (!(lam_now > 0.0) || !isfinite(lam_now)) {
             if (lane == 0 && !(lam_now == 0.0)) set_status(&A.st[bp], GD_ST_NONFINITE);
             break;
           }
-        } else {
-          if (!(totf > 0.0f) || !isfinite(totf)) {
-            if (lane == 0 && !(totf == 0.0f)) set_status(&A.st[bp], GD_ST_NONFINITE);
-            break;
-          }
+        } else if (!(totf > 0.0f) || !isfinite(totf)) {
+          if (totf == 0.0f) break;
+          unc = true;
+          break;
         }
         U4 w = philox(il, iv, (unsigned)e, 0u, k0, k1);
         uw0 = w.z;
         uw1 = w.w;
-        if constexpr (sizeof(T) == 8) u_s = u01(w.z, w.w);
+        if constexpr (!kMixed) u_s = u01(w.z, w.w);
         double dt2;
-        if constexpr (sizeof(T) == 8) {
+        if constexpr (!kMixed) {
           dt2 = waiting_time<T>(w.x, w.y, lam_now);
+          if (fabs((t + dt2) - dte) < 1e-10 * dte) near_u++;
         } else {
-          // lambda* = pref * totf in FP32 when it is in range (the FP32 wait is formed from
-          // it anyway), else in FP64
-          const float lf = preff * totf;
-          const float nl = neg_log_u01_f32(w.x, w.y);
-          dt2 = (lf > 1e-30f && lf < 1e30f) ? (double)__fdividef(nl, lf) : (double)nl / (f.pref * (double)totf);
+          if (bad64) {
+            dt2 = waiting_time<double>(w.x, w.y, lam_now);   // exact up to FP64 rounding
+          } else {
+            // lambda* = pref * totf in FP32 when it is in range (the FP32 wait is formed
+            // from it anyway), else in FP64
+            const float lf = preff * totf;
+            const float nl = neg_log_u01_f32(w.x, w.y);
+            float d2;
+            if (lf > 1e-30f && lf < 1e30f) { d2 = __fdividef(nl, lf); dt2 = (double)d2; }
+            else { dt2 = (double)nl / (f.pref * (double)totf); d2 = (float)dt2; }
+            terr = fmaf(d2, (eta + 8.f * u) * 1.0001f, terr);
+          }
+          // the time sum's decision: certified, or the particle is replayed in FP64 (one FP64
+          // difference, compared in FP32 with a margin far above its rounding)
+          const double tn = t + dt2;
+          const float dd = (float)(tn - dte);
+          if (!(fabsf(dd) > 1.5f * terr * 1.0001f + 1e-14f * dtef)) { unc = true; break; }
+          if (dd > 0.0f) break;
+          t = tn;
+          continue;
         }
-        if (fabs((t + dt2) - dte) < tie_dte) near_u++;
         if (t + dt2 > dte) break;
         t = t + dt2;
       }
-      if constexpr (sizeof(T) == 4) {
-        if (s_stale) s = diameter_of<T>(cube_of<T>(f, m));
+      if constexpr (kMixed) {
+        if (!unc && s_stale) s = diameter_of<T>(cube_of<T>(f, m));
       }
       int near_tot = near_ch;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) near_tot += __shfl_xor_sync(FULLM, near_tot, o);
       near_tot += near_u;
-      if (lane == p) { my_e = e; my_h = h; nn += near_tot; my_MJ = f.M * (double)J; }
-      if (lane == 0) {
-        int ci = A.perm[rp];
-        A.s_out[ci] = s;
-        atomicAdd((unsigned long long*)&A.st[bp].events, (unsigned long long)e);
+      if (lane == p) {
+        replay = unc;
+        my_e = e; my_h = h; nn += near_tot; my_MJ = f.M * (double)J; my_s = s;
       }
     }
-    if (valid) A.MJ[A.perm[r]] = my_MJ;
-    if (valid && nn) atomicAdd((unsigned long long*)&A.st[b].near_draw, (unsigned long long)nn);
-    if (valid && A.ev_count) {
-      int ci = A.perm[r];
-      A.ev_count[ci] = my_e;
-      A.ev_hash[ci] = my_h;
-      A.near_out[ci] = nn;
+    if (valid) {
+      if (replay) {
+        A.redo[atomicAdd(A.redo_n, 1ull)] = (int)r;   // the FP64 replay samples it
+        atomicAdd((unsigned long long*)&A.st[b].sample_redo, 1ull);
+      } else {
+        const int ci = A.perm[r];
+        if (my_e > 0) {
+          A.s_out[ci] = my_s;
+          atomicAdd((unsigned long long*)&A.st[b].events, (unsigned long long)my_e);
+        }
+        A.MJ[ci] = my_MJ;
+        if (nn) atomicAdd((unsigned long long*)&A.st[b].near_draw, (unsigned long long)nn);
+        if (A.ev_count) {
+          A.ev_count[ci] = my_e;
+          A.ev_hash[ci] = my_h;
+          A.near_out[ci] = nn;
+        }
+      }
     }
   }
 }
@@ -1116,6 +1418,10 @@ static McArgs mc_args(gd_ctx* c) {
   A.gx = c->d_gx;
   A.pref32 = c->d_pref32;
   A.contrib = c->d_contrib;
+  A.redo = c->d_redo;
+  A.redo_n = nullptr;
+  A.list = nullptr;
+  A.list_n = nullptr;
   A.MJ = c->d_MJ;
   A.part = c->d_part;
   A.n_tiles = c->n_tiles;
@@ -1123,9 +1429,9 @@ static McArgs mc_args(gd_ctx* c) {
 }
 
 // Per-instance sums of quantities q0 .. q0 + nq - 1 from the tile partials (8 warps a block).
-static void bins_reduce(gd_ctx* c, int q0, int nq) {
+static void bins_reduce(gd_ctx* c, int q0, int nq, int skip_q) {
   dim3 grid(c->n_inst, (nq * kNFine + 7) / 8);
-  k_bins_reduce<<<grid, 256, 0, c->stream>>>(c->d_tile_off, c->d_part, c->n_tiles, q0, nq, c->d_bins);
+  k_bins_reduce<<<grid, 256, 0, c->stream>>>(c->d_tile_off, c->d_part, c->n_tiles, q0, nq, skip_q, c->d_bins);
 }
 
 cudaError_t launch_rates(gd_ctx* c, double* chan_out) {
@@ -1134,15 +1440,23 @@ cudaError_t launch_rates(gd_ctx* c, double* chan_out) {
   time_begin(c, 2);
   // one block per tile, lane = particle: any K
   if (c->precision == GD_MIXED) {
+    // particles the FP32 rates cannot certify are listed (counter 5) and redone in FP64
+    A.redo_n = c->d_counters + 5;
+    cudaMemsetAsync(A.redo_n, 0, sizeof(unsigned long long), c->stream);
     k_rates<float><<<c->n_tiles, 128, 0, c->stream>>>(A, tile_map(c));
+    McArgs B = A;
+    B.list = c->d_redo;
+    B.list_n = A.redo_n;
+    k_rates_redo<<<c->num_sms * 2, 128, 0, c->stream>>>(B);
     k_bins_tile<float><<<c->n_tiles, 128, 0, c->stream>>>(tile_map(c), c->d_rank_of, c->d_contrib, c->d_part,
                                                           c->n_tiles);
+    c->launches += 1;
   } else {
     k_rates<double><<<c->n_tiles, 128, 0, c->stream>>>(A, tile_map(c));
     k_bins_tile<double><<<c->n_tiles, 128, 0, c->stream>>>(tile_map(c), c->d_rank_of, c->d_contrib, c->d_part,
                                                            c->n_tiles);
   }
-  bins_reduce(c, 0, 4);
+  bins_reduce(c, 0, 6, 4);     // count, M, M A, M B and the error bound; sJ after sampling
   time_end(c);
   c->launches += 3;
   return cudaGetLastError();
@@ -1152,7 +1466,7 @@ cudaError_t launch_interval(gd_ctx* c) {
   time_begin(c, 3);
   k_interval<<<c->n_inst, 128, 0, c->stream>>>(c->d_inst, c->d_state, c->d_bins, c->n_inst, c->K,
                                                (c->flags & GD_FLAG_NO_AUDIT) ? 1 : 0,
-                                               c->precision == GD_MIXED ? 2e-5 : 1e-10);
+                                               c->precision == GD_MIXED ? 1 : 0);
   time_end(c);
   c->launches += 1;
   return cudaGetLastError();
@@ -1169,12 +1483,26 @@ static void sample_launch(gd_ctx* c, const McArgs& A) {
   if (blocks > (chunks + 1) / 2) blocks = (chunks + 1) / 2;
   if (blocks < 1) blocks = 1;
   k_sample<T, S><<<(int)blocks, 64, 0, c->stream>>>(A);
+  if (sizeof(T) == 4) {
+    // the FP64 replay of the particles the mixed pass could not certify (counter 6 lists
+    // them, counter 7 hands out their chunks); its grid does not depend on their number
+    McArgs B = A;
+    B.list = c->d_redo;
+    B.list_n = c->d_counters + 6;
+    B.work = c->d_counters + 7;
+    k_sample<double, S><<<c->num_sms * 4, 64, 0, c->stream>>>(B);
+    c->launches += 1;
+  }
 }
 
 template <typename T>
 static void sample_t(gd_ctx* c, McArgs& A) {
   int S = (c->K + 31) / 32;
   A.work = c->d_counters;
+  if (sizeof(T) == 4) {
+    A.redo_n = c->d_counters + 6;
+    cudaMemsetAsync(c->d_counters + 6, 0, 2 * sizeof(unsigned long long), c->stream);
+  }
   cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long), c->stream);
   switch (S) {
     case 1: sample_launch<T, 1>(c, A); break;
@@ -1208,7 +1536,7 @@ cudaError_t launch_audit(gd_ctx* c) {
   else
     k_jbins<false><<<c->n_tiles, 128, 0, c->stream>>>(tile_map(c), c->d_rank_of, c->d_contrib, c->d_MJ, c->d_part,
                                                       c->n_tiles);
-  bins_reduce(c, 4, 1);
+  bins_reduce(c, 4, 1, -1);
   k_audit<<<c->n_inst, 128, 0, c->stream>>>(c->d_inst, c->d_state, c->d_bins, c->n_inst,
                                             (c->flags & GD_FLAG_NO_AUDIT) ? 1 : 0,
                                             c->precision == GD_MIXED ? 2e-5 : 1e-10);

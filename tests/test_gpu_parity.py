@@ -9,10 +9,11 @@ Bars (from the method's precision split):
   near tie (a draw within 1e-10 of a boundary) was flagged on either side;
 * diameters after sampling: within 1e-12 relative (FP64) where the sequences agree;
 * represented mass: never written (bitwise), sum N m = sum M within 1e-12;
-* mixed form: lists bit-exact; rates lambda*_i within 1e-4 relative; event sequences
-  identical except near ties at the mixed tolerance (2e-5 of a boundary, above the FP32
-  error of the rates) and at most a few grouping/outcome-threshold flips per thousand
-  event particles; diameters within 1e-5 relative where the sequences agree.
+* mixed form: lists bit-exact; lambda*_i and every channel rate within 1e-4 relative (the
+  largest pair-rate error the mixed form accepts without FP64); A_b, B_b within 2e-4; event
+  sequences identical to the FP64 ones except flagged near ties -- every FP32 decision is
+  certified against its error bound and the particles it cannot certify are replayed in
+  FP64 -- so the same bar as the FP64 form applies, with diameters within 1e-12.
 """
 import math
 
@@ -87,23 +88,17 @@ def test_patch_interval_parity(gd, oracle, precision):
             _check_bins(ref, got, st, 1e-12)
         else:
             assert rel.max() < 1e-4, rel.max()
-            _check_bins(ref, got, st, 1e-4)
+            _check_channels(ref, got, 1e-4)
+            _check_bins(ref, got, st, 2e-4)
         stats = sess.stats()
         inst = stats["instances"][0]
         s_gpu = sess.t["s"].cpu().numpy()
         if inst["dt_exe"] != st.dt_exe:
             # only a flagged near tie of the interval or audit rule may change the interval
             assert inst["near_dt"] + inst["near_audit"] + st.near_dt + st.near_audit > 0
-        elif precision == 0:
+        else:
             same = _compare_events(ref, got)
             assert np.abs(s_gpu[same] / s_or[same] - 1.0).max() < 1e-12
-        else:
-            same = (ref["ev_count"] == got["ev_count"]) & (ref["ev_hash"] == got["ev_hash"])
-            flagged = (ref["near"] > 0) | (got["near"] > 0)
-            n_ev = int((ref["ev_count"] > 0).sum())
-            bad = int((~same & ~flagged).sum())
-            assert bad <= max(2, 1e-3 * n_ev), (bad, n_ev)
-            assert np.abs(s_gpu[same] / s_or[same] - 1.0).max() < 1e-5
         # keep both sides on the same state for the next interval
         import torch
         sess.t["s"].copy_(torch.as_tensor(s_or, device=sess.device))
