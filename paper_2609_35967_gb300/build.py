@@ -19,7 +19,7 @@ SOURCES = ["gd_abi.cu", "k_cells.cu", "k_knn.cu", "k_mc.cu", "k_misc.cu", "gd_no
 PEAKS_LIB = os.path.join(HERE, "libgdpeaks.so")
 PEAKS_SRC = "pipe_peaks.cu"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC",
+FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
                 "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
 
 

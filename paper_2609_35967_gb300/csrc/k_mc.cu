@@ -553,7 +553,7 @@ __device__ __forceinline__ bool rate_particle(const McArgs& A, const InstDev& P,
 }
 
 template <typename T>
-__global__ void __launch_bounds__(128) k_rates(McArgs A, TileMap tm) {
+__global__ void __launch_bounds__(128, 8) k_rates(McArgs A, TileMap tm) {
   int b;
   long long lo, hi;
   tile_range(tm, blockIdx.x, b, lo, hi);
