@@ -190,6 +190,60 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def measure_form(gd, insts, dev, precision, steps, warmup, world, push=False, graph=False,
+                 cell_factor=0.0, cell_xsplit=0, timing=True):
+    """Times `steps` whole intervals of one form after `warmup` (CUDA events on the library's
+    stream, barrier and synchronize on both sides).  graph: the intervals are replayed as a
+    captured CUDA graph (gd_run_intervals), which per-kernel timing cannot see into."""
+    import torch
+    sess = gd.Session(insts, precision=precision, device=str(dev), velocities=push,
+                      flags=gd.GD_FLAG_TIMING if (timing and not graph) else 0, cell_factor=cell_factor,
+                      cell_xsplit=cell_xsplit)
+    cf, xs = (cell_factor, max(1, cell_xsplit)) if cell_factor > 0 else sess.autotune()
+    st = sess.stream
+
+    def step():
+        if graph:
+            sess.run_intervals(1, push)
+            return
+        sess.build_neighbors()
+        sess.collision_rates()
+        sess.sample_collisions()
+        if push:
+            sess.push_staggered(-1.0)
+
+    for _ in range(warmup):
+        step()
+    pre = sess.stats()
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    ck = clocks.stop()
+    post = sess.stats()
+    res = {"ms": ms, "clocks": ck, "launches": post["launches"] - pre["launches"],
+           "kernel_ms": {k: post["kernel_ms"][k] - pre["kernel_ms"][k] for k in post["kernel_ms"]},
+           "kernel_calls": {k: post["kernel_calls"][k] - pre["kernel_calls"][k]
+                            for k in post["kernel_calls"]},
+           "events": post["events"] - pre["events"], "status": post["status"], "cell_factor": cf,
+           "cell_xsplit": xs, "knn_redo": post["knn_redo"] - pre["knn_redo"],
+           "rate_redo": post["rate_redo"] - pre["rate_redo"],
+           "sample_redo": post["sample_redo"] - pre["sample_redo"],
+           "dt_exe": post["instances"][0]["dt_exe"]}
+    sess.close()
+    return res
+
+
 def run_gpu(args, rank, world):
     import torch
 
@@ -201,56 +255,16 @@ def run_gpu(args, rank, world):
     insts, cfg = make_workload(args.workload, rank)
     K = insts[0]["params"]["K"]
     push = args.workload == "disk24"
+    graph = args.workload == "patches256"
     N = int(sum(len(i["x"]) for i in insts))
     hbm, peak_kind = peaks()
 
-    def measure(precision, steps, warmup, timing):
-        sess = gd.Session(insts, precision=precision, device=str(dev), velocities=push,
-                          flags=gd.GD_FLAG_TIMING if timing else 0, cell_factor=args.cell_factor,
-                          cell_xsplit=args.cell_xsplit)
-        cf, xs = (args.cell_factor, max(1, args.cell_xsplit)) if args.cell_factor > 0 else sess.autotune()
-        st = sess.stream
-
-        def step():
-            sess.build_neighbors()
-            sess.collision_rates()
-            sess.sample_collisions()
-            if push:
-                sess.push_staggered(-1.0)
-
-        for _ in range(warmup):
-            step()
-        pre = sess.stats()
-        clocks = ClockSampler(dev.index)
-        clocks.start()
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        for _ in range(steps):
-            step()
-        e1.record(st)
-        torch.cuda.synchronize(dev)
-        if world > 1:
-            torch.distributed.barrier()
-        ms = e0.elapsed_time(e1)
-        ck = clocks.stop()
-        post = sess.stats()
-        res = {"ms": ms, "clocks": ck, "launches": post["launches"] - pre["launches"],
-               "kernel_ms": {k: post["kernel_ms"][k] - pre["kernel_ms"][k] for k in post["kernel_ms"]},
-               "kernel_calls": {k: post["kernel_calls"][k] - pre["kernel_calls"][k]
-                                for k in post["kernel_calls"]},
-               "events": post["events"] - pre["events"], "status": post["status"], "cell_factor": cf,
-               "cell_xsplit": xs,
-               "knn_redo": post["knn_redo"] - pre["knn_redo"]}
-        sess.close()
-        return res
-
-    mixed = measure(gd.GD_MIXED, args.steps, args.warmup, timing=True)
+    mixed = measure_form(gd, insts, dev, gd.GD_MIXED, args.steps, args.warmup, world, push=push,
+                         cell_factor=args.cell_factor, cell_xsplit=args.cell_xsplit)
     fp64 = None
     if not args.skip_fp64:
-        fp64 = measure(gd.GD_FP64, max(1, args.steps // 3), max(1, args.warmup // 3), timing=True)
+        fp64 = measure_form(gd, insts, dev, gd.GD_FP64, max(1, args.steps // 3), max(1, args.warmup // 3), world,
+                            push=push, cell_factor=args.cell_factor, cell_xsplit=args.cell_xsplit)
 
     # end to end through the C ABI with host buffers: H2D of the step's inputs from
     # pinned memory and D2H of the diameters inside the timed region, every step
@@ -287,10 +301,35 @@ def run_gpu(args, rank, world):
     torch.cuda.synchronize(dev)
     e2e_ms = max(e0.elapsed_time(e1), (time.perf_counter() - t0) * 1e3)
     sess.close()
+    del graph
+
+    # the other single-GPU workloads of the benchmark, each in both forms: the 2^24, K = 48
+    # disk with a push after every interval, and the 256-patch batch replayed as a graph
+    extras = {}
+    if not args.skip_extra and args.workload == "disk22":
+        for name, xsteps, xwarm in (("disk24", 3, 3), ("patches256", 10, 3)):
+            xinsts, xcfg = make_workload(name, rank)
+            xpush, xgraph = name == "disk24", name == "patches256"
+            m = measure_form(gd, xinsts, dev, gd.GD_MIXED, xsteps, xwarm, world, push=xpush, graph=xgraph)
+            # the graph's per-kernel split, from a short timed run of the same intervals
+            split = (measure_form(gd, xinsts, dev, gd.GD_MIXED, 2, 1, world, push=xpush,
+                                  cell_factor=m["cell_factor"], cell_xsplit=m["cell_xsplit"])
+                     if xgraph else m)
+            f = measure_form(gd, xinsts, dev, gd.GD_FP64, 1, 1, world, push=xpush, graph=xgraph,
+                             timing=False)
+            t = max_over_ranks([m["ms"], f["ms"]], world, dev)
+            extras[name] = dict(cfg=xcfg, N=int(sum(len(i["x"]) for i in xinsts)),
+                                K=xinsts[0]["params"]["K"], mixed=m, split=split, fp64=f,
+                                times=t, steps=xsteps, graph=xgraph, push=xpush)
 
     times = max_over_ranks([mixed["ms"], fp64["ms"] if fp64 else 0.0, e2e_ms], world, dev)
+    pp = None
+    try:
+        pp = pipe_peaks()
+    except Exception as e:          # reported, never fatal: the HBM roofline stands alone
+        pp = {"error": str(e)}
     return dict(N=N, K=K, cfg=cfg, mixed=mixed, fp64=fp64, times=times, hbm=hbm,
-                peak_kind=peak_kind, h2d=h2d, d2h=d2h, push=push)
+                peak_kind=peak_kind, h2d=h2d, d2h=d2h, push=push, extras=extras, pipe_peaks=pp)
 
 
 def max_over_ranks(times, world, dev):
@@ -304,24 +343,60 @@ def max_over_ranks(times, world, dev):
     return t.tolist()
 
 
-def cpu_oracle_rate(insts, budget_s=12.0, max_q=4096):
-    """Oracle (serial, FP64, brute-force K-NN) on a bounded sample of query particles."""
+def host_cpu():
+    """nproc and the CPU model of this host (from /proc/cpuinfo where it names one)."""
+    import platform
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read().splitlines()
+        for key in ("model name", "Model", "CPU part"):
+            for line in info:
+                if line.split(":")[0].strip() == key:
+                    model = f"{key}: {line.split(':', 1)[1].strip()}"
+                    break
+            if model:
+                break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu": model or platform.processor() or platform.machine(),
+            "machine": platform.machine()}
+
+
+def cpu_oracle_rate(insts, budget_s=12.0, max_q=4096, dt_exe=None, threads=1):
+    """The oracle (plain C, FP64, brute-force K-NN) on a bounded sample of query particles of
+    the largest instance: each query's K-NN, rates and sampling over one interval of length
+    dt_exe (the GPU's, when given).  threads > 1 spreads batches of queries over host threads
+    (the particles of an interval are independent and ctypes releases the GIL in the C calls);
+    the oracle's code is the same."""
+    import concurrent.futures as cf
+
     import numpy as np
 
     from oracle import gdo
     ins = max(insts, key=lambda i: len(i["x"]))
     P = gdo.params(ins["params"])
     n = len(ins["x"])
-    rng = np.random.default_rng(0)
-    done = 0
+    dt = dt_exe if dt_exe else P.dt_fn_max / 64.0
+    gdo.lib()
     t0 = time.perf_counter()
-    while done < max_q and time.perf_counter() - t0 < budget_s:
-        q = rng.choice(n, 8, replace=False)
-        nbr, d = gdo.knn(P, ins["x"], ins["y"], ins["z"], q)
-        gdo.rates_subset(P, ins["x"], ins["y"], ins["z"], ins["s"], ins["M"], q, nbr, d)
-        gdo.sample_subset(P, ins["x"], ins["y"], ins["z"], ins["s"], ins["M"], q, nbr, d,
-                          P.dt_fn_max / 64.0, 0)
-        done += len(q)
+
+    def work(seed):
+        rng = np.random.default_rng(seed)
+        done = 0
+        while done < max_q // threads and time.perf_counter() - t0 < budget_s:
+            q = rng.choice(n, 8, replace=False)
+            nbr, d = gdo.knn(P, ins["x"], ins["y"], ins["z"], q)
+            gdo.rates_subset(P, ins["x"], ins["y"], ins["z"], ins["s"], ins["M"], q, nbr, d)
+            gdo.sample_subset(P, ins["x"], ins["y"], ins["z"], ins["s"], ins["M"], q, nbr, d, dt, 0)
+            done += len(q)
+        return done
+
+    if threads > 1:
+        with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+            done = sum(ex.map(work, range(threads)))
+    else:
+        done = work(0)
     el = time.perf_counter() - t0
     return done / el, done, el, n
 
@@ -462,6 +537,8 @@ def main():
     ap.add_argument("--workload", default="disk22")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-extra", action="store_true",
+                    help="only the main workload (no disk24 / patches256 keys)")
     ap.add_argument("--cell-factor", type=float, default=0.0,
                     help="cell edge factor; 0 = pick it and the x division with gd_autotune")
     ap.add_argument("--cell-xsplit", type=int, default=0, choices=(0, 1, 2, 4),
@@ -482,24 +559,26 @@ def main():
         if rank != 0:
             return
         insts, cfg = make_workload(args.workload, 0)
-        vals = []
+        hc = host_cpu()
+        nth = max(1, hc["nproc"] or 1)
         for _ in range(args.warmup):
-            cpu_oracle_rate(insts, budget_s=2.0, max_q=64)
+            cpu_oracle_rate(insts, budget_s=1.0, max_q=64 * nth, threads=nth)
         total_q, total_t = 0, 0.0
         for _ in range(args.steps):
-            v, q, el, n = cpu_oracle_rate(insts, budget_s=6.0, max_q=512)
-            vals.append(v)
+            v, q, el, n = cpu_oracle_rate(insts, budget_s=5.0, max_q=1024 * nth, threads=nth)
             total_q += q
             total_t += el
         value = total_q / total_t
-        sample = (f"{total_q} query particles of the {n}-particle instance over {args.steps} steps: "
-                  "brute-force K-NN, FP64 rates and Philox sampling of each")
+        sample = (f"{total_q} query particles of the {n}-particle instance over {args.steps} steps on {nth} "
+                  "host threads: brute-force K-NN, FP64 rates and Philox sampling of each (serial C per "
+                  "particle, -O2)")
         print(json.dumps({
             "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": cfg,
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nth, "kind": "oracle", "sample": sample,
+                             "host": hc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return
 
@@ -526,14 +605,32 @@ def main():
         out = result_line(r, args, world)
         if world == 1 and not args.skip_cpu:
             insts, _ = make_workload(args.workload, 0)
-            v, q, el, n = cpu_oracle_rate(insts)
-            out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                   "sample": f"{q} query particles of the {n}-particle instance, {el:.1f} s: "
-                                             "brute-force K-NN, FP64 rates, sampling (serial C, -O2)"}
+            hc = host_cpu()
+            nth = max(1, hc["nproc"] or 1)
+            dt = r["mixed"]["dt_exe"]
+            v1, q1, el1, n = cpu_oracle_rate(insts, budget_s=8.0, max_q=1024, dt_exe=dt)
+            v, q, el, n = cpu_oracle_rate(insts, budget_s=12.0, max_q=65536, dt_exe=dt, threads=nth)
+            out["cpu_baseline"] = {
+                "value": v, "unit": UNIT, "cores": nth, "kind": "oracle", "host": hc,
+                "sample": f"{q} query particles of the {n}-particle instance in {el:.1f} s on {nth} host threads: "
+                          f"brute-force K-NN, FP64 rates and sampling over the GPU's interval ({dt:.4g} s) "
+                          "(serial C, -O2, the same calls spread over threads)",
+                "serial": {"value": v1, "cores": 1, "sample": f"{q1} query particles in {el1:.1f} s"}}
         print(json.dumps(out))
     if world > 1:
         import torch
         torch.distributed.destroy_process_group()
+
+
+def roofline_of(km, kc, K, N, hbm, peak_kind, workload):
+    """HBM roofline of the kernel with the largest share of the step: algorithmic bytes per
+    launch over its mean launch time (CUDA events on the library stream)."""
+    dom = max(("knn", "rates", "sample", "cells"), key=lambda k: km.get(k, 0.0))
+    avg_s = km[dom] / max(1, kc[dom]) * 1e-3
+    ach = algo_bytes(dom, K, True) * N / avg_s / 1e9
+    return {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "traffic": kernel_traffic(dom, workload, N), "peak_kind": peak_kind,
+            "algo_bytes_per_particle": algo_bytes(dom, K, True), "launch_ms": avg_s * 1e3}
 
 
 def result_line(r, args, world):
@@ -543,9 +640,6 @@ def result_line(r, args, world):
     value = world * N * args.steps / (ms_mixed * 1e-3)
     km = r["mixed"]["kernel_ms"]
     kc = r["mixed"]["kernel_calls"]
-    dom = max(("knn", "rates", "sample", "cells"), key=lambda k: km.get(k, 0.0))
-    avg_s = km[dom] / max(1, kc[dom]) * 1e-3
-    ach = algo_bytes(dom, K, True) * N / avg_s / 1e9
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_mixed / args.steps, "higher_is_better": True,
@@ -557,16 +651,17 @@ def result_line(r, args, world):
                        cell_xsplit=r["mixed"].get("cell_xsplit", 1)),
         "events_per_step": r["mixed"]["events"] / args.steps,
         "knn_fp64_redo_per_step": r["mixed"].get("knn_redo", 0) / args.steps,
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": r["hbm"], "unit": "GB/s",
-                     "frac": ach / r["hbm"], "traffic": kernel_traffic(dom, args.workload, N),
-                     "peak_kind": r["peak_kind"],
-                     "algo_bytes_per_particle": algo_bytes(dom, K, True)},
+        "mixed_fp64_settled_per_step": {"rates": r["mixed"]["rate_redo"] / args.steps,
+                                        "sampling": r["mixed"]["sample_redo"] / args.steps},
+        "roofline": roofline_of(km, kc, K, N, r["hbm"], r["peak_kind"], args.workload),
         "kernels_ms_per_step": {k: v / args.steps for k, v in km.items() if v > 0 and k != "stats"},
         "gpu_launches": r["mixed"]["launches"],
         "clocks": r["mixed"]["clocks"],
         "e2e": {"value": world * N * args.steps / (ms_e2e * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
     }
+    if r.get("pipe_peaks"):
+        out["pipe_peaks"] = r["pipe_peaks"]
     if r["fp64"]:
         st = max(1, args.steps // 3)
         out["fp64"] = {"value": world * N * st / (ms_fp64 * 1e-3), "ms_per_step": ms_fp64 / st,
@@ -574,6 +669,29 @@ def result_line(r, args, world):
                        "kernels_ms_per_step": {k: v / st for k, v in r["fp64"]["kernel_ms"].items()
                                                if v > 0 and k != "stats"}}
         out["mixed_over_fp64"] = out["value"] / out["fp64"]["value"]
+    for name, x in r.get("extras", {}).items():
+        xm, xf = x["times"]
+        sp = x["split"]
+        sst = 2 if x["graph"] else x["steps"]
+        v = world * x["N"] * x["steps"] / (xm * 1e-3)
+        vf = world * x["N"] / (xf * 1e-3)
+        out[name] = {
+            "value": v, "unit": UNIT, "ms_per_step": xm / x["steps"], "steps": x["steps"],
+            "config": dict(x["cfg"], n_particles=x["N"], K=x["K"], precision="mixed",
+                           timed="one CUDA graph replay per interval (gd_run_intervals)" if x["graph"]
+                           else "gd_build_neighbors, gd_collision_rates, gd_sample_collisions"
+                           + (", gd_push_staggered" if x["push"] else ""),
+                           cell_factor=x["mixed"]["cell_factor"], cell_xsplit=x["mixed"]["cell_xsplit"]),
+            "kernels_ms_per_step": {k: w / sst for k, w in sp["kernel_ms"].items() if w > 0 and k != "stats"},
+            "roofline": roofline_of(sp["kernel_ms"], sp["kernel_calls"], x["K"], x["N"], r["hbm"],
+                                    r["peak_kind"], name),
+            "events_per_step": x["mixed"]["events"] / x["steps"],
+            "mixed_fp64_settled_per_step": {"rates": x["mixed"]["rate_redo"] / x["steps"],
+                                            "sampling": x["mixed"]["sample_redo"] / x["steps"]},
+            "fp64": {"value": vf, "ms_per_step": xf},
+            "mixed_over_fp64": v / vf,
+            "status": x["mixed"]["status"],
+        }
     return out
 
 

@@ -198,6 +198,11 @@ typedef struct {
   int64_t near_draw, near_dt, near_audit;
   uint32_t status;             /* GD_ST_* bits of this instance                */
   int32_t n_groups;            /* controller bins of the last interval         */
+  double spectrum[96];         /* size spectrum: sum of M_i over the particles whose
+                                  diameter lies in fine log-size bin f, which covers
+                                  s in [2^((f - 75)/3), 2^((f - 74)/3)) cm (a third of an
+                                  octave, ~0.1 dex; the first and last bins also take
+                                  the sizes below and above); summed in a fixed order */
 } gd_instance_stats;
 
 /* Creates a context over caller-owned particle arrays (see gd_config).  Checks

@@ -63,7 +63,8 @@ class InstanceStats(C.Structure):
                 ("dt_remain", C.c_double), ("sum_M", C.c_double), ("sum_Mm", C.c_double),
                 ("sum_Ms", C.c_double), ("interval", C.c_int64), ("events", C.c_int64),
                 ("events_total", C.c_int64), ("near_draw", C.c_int64), ("near_dt", C.c_int64),
-                ("near_audit", C.c_int64), ("status", C.c_uint32), ("n_groups", C.c_int32)]
+                ("near_audit", C.c_int64), ("status", C.c_uint32), ("n_groups", C.c_int32),
+                ("spectrum", C.c_double * 96)]
 
 
 class DtRule(C.Structure):
@@ -357,5 +358,6 @@ class Session:
         out["kernel_ms"] = dict(zip(TIMING_SLOTS, list(st.kernel_ms)))
         out["kernel_calls"] = dict(zip(TIMING_SLOTS, list(st.kernel_calls)))
         out["code"] = code
-        out["instances"] = [{f: getattr(x, f) for f, _ in InstanceStats._fields_} for x in inst]
+        out["instances"] = [{f: (list(getattr(x, f)) if f == "spectrum" else getattr(x, f))
+                             for f, _ in InstanceStats._fields_} for x in inst]
         return out

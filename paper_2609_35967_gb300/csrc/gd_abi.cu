@@ -441,7 +441,12 @@ extern "C" gd_status gd_run_intervals(gd_ctx* c, int32_t n, int32_t push) {
 extern "C" gd_status gd_stats(gd_ctx* c, gd_stats_t* out, gd_instance_stats* inst_out) {
   if (!c || !out) return GD_ERR_ARG;
   if (launch_stats(c, c->d_sums) != cudaSuccess) return GD_ERR_CUDA;
+  if (inst_out && launch_spectrum(c) != cudaSuccess) return GD_ERR_CUDA;
   std::vector<StateDev> st(c->n_inst);
+  std::vector<BinsDev> bins(inst_out ? c->n_inst : 0);
+  if (inst_out && cudaMemcpyAsync(bins.data(), c->d_bins, sizeof(BinsDev) * c->n_inst, cudaMemcpyDeviceToHost,
+                                  c->stream) != cudaSuccess)
+    return GD_ERR_CUDA;
   std::vector<double> sums(3 * (size_t)c->n_inst);
   cudaError_t e = cudaMemcpyAsync(st.data(), c->d_state, sizeof(StateDev) * c->n_inst, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(sums.data(), c->d_sums, sizeof(double) * sums.size(), cudaMemcpyDeviceToHost, c->stream);
@@ -474,6 +479,7 @@ extern "C" gd_status gd_stats(gd_ctx* c, gd_stats_t* out, gd_instance_stats* ins
       o.near_draw = s.near_draw; o.near_dt = s.near_dt; o.near_audit = s.near_audit;
       o.status = s.status;
       o.n_groups = s.n_groups;
+      std::memcpy(o.spectrum, bins[b].spec, sizeof(o.spectrum));
     }
   }
   if (out->status & GD_ST_NONFINITE) return GD_ERR_NONFINITE;

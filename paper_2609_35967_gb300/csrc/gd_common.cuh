@@ -92,13 +92,14 @@ struct StateDev {
 };
 
 // Fine-bin sums of one instance (doubles; counts exact below 2^53), in this order (the
-// tile reduction addresses them as quantity q of the block cnt, sM, sA, sB, sJ, sE), and the
-// controller bins of the last interval choice: the fine bins' group ids and each group's
+// tile reduction addresses them as quantity q of the block cnt, sM, sA, sB, sJ, sE, spec), and
+// the controller bins of the last interval choice: the fine bins' group ids and each group's
 // A_b and B_b.  sE is not a sum: the largest relative error bound of the mixed form's FP32
-// moment contributions in the bin (0 in the FP64 form).
-constexpr int kBinQ = 6;          // cnt, sM, sA, sB, sJ, sE
+// moment contributions in the bin (0 in the FP64 form).  spec: the size spectrum of the last
+// gd_stats, sum of M_i over the particles whose current diameter lies in the bin.
+constexpr int kBinQ = 7;          // cnt, sM, sA, sB, sJ, sE, spec
 struct BinsDev {
-  double cnt[kNFine], sM[kNFine], sA[kNFine], sB[kNFine], sJ[kNFine], sE[kNFine];
+  double cnt[kNFine], sM[kNFine], sA[kNFine], sB[kNFine], sJ[kNFine], sE[kNFine], spec[kNFine];
   double gA[kNFine], gB[kNFine];
   int gid[kNFine];
   int ngroups;

@@ -111,6 +111,7 @@ cudaError_t launch_snapshot(gd_ctx* c);
 cudaError_t launch_step_begin(gd_ctx* c, double tau, int hold);
 cudaError_t launch_step_done(gd_ctx* c, int* d_flag);
 cudaError_t launch_stats(gd_ctx* c, double* d_sums);
+cudaError_t launch_spectrum(gd_ctx* c);
 cudaError_t launch_outputs_knn(gd_ctx* c, int* nbr_out, double* d_out);
 cudaError_t launch_outputs_lam(gd_ctx* c, double* lam_out);
 

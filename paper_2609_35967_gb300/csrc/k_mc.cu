@@ -697,6 +697,33 @@ __global__ void __launch_bounds__(128) k_jbins(TileMap tm, const int* __restrict
   }
 }
 
+// The size spectrum: sum of M_i per fine bin of the current diameter s_i, per tile of caller
+// indices in the fixed order of warp_bin_add; quantity 6 of the tile partials.
+__global__ void __launch_bounds__(128) k_spec_tile(TileMap tm, const double* __restrict__ s,
+                                                   const double* __restrict__ M, double* part, long long n_tiles) {
+  constexpr int NW = 4;
+  __shared__ double acc[NW][kNFine];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int t = threadIdx.x; t < NW * kNFine; t += blockDim.x) (&acc[0][0])[t] = 0.0;
+  __syncthreads();
+  int b;
+  long long lo, hi;
+  tile_range(tm, blockIdx.x, b, lo, hi);
+  for (long long base = lo; base < hi; base += blockDim.x) {
+    const long long i = base + threadIdx.x;
+    double v[1] = {0.0};
+    int fb = -1;
+    if (i < hi) { v[0] = M[i]; fb = fine_bin(s[i]); }
+    warp_bin_add<double, 1>(&acc[w][0], nullptr, fb, v, lane);
+  }
+  __syncthreads();
+  for (int f = threadIdx.x; f < kNFine; f += blockDim.x) {
+    double sp = 0.0;
+    for (int ww = 0; ww < NW; ++ww) sp += acc[ww][f];
+    part[(6LL * kNFine + f) * n_tiles + blockIdx.x] = sp;
+  }
+}
+
 // Per-instance fine-bin sums from the tile partials, in a fixed order: one warp per
 // (quantity, bin); lane l adds the instance's tiles l, l + 32, ... in order, then the lanes'
 // sums meet in a fixed butterfly (quantity 5, an error bound, takes the maximum instead).
@@ -1525,6 +1552,13 @@ cudaError_t launch_sample(gd_ctx* c, int* ev_count, unsigned* ev_hash, int* near
   if (c->precision == GD_MIXED) sample_t<float>(c, A); else sample_t<double>(c, A);
   time_end(c);
   c->launches += 1;
+  return cudaGetLastError();
+}
+
+// The size spectrum of every instance into BinsDev::spec (gd_stats).
+cudaError_t launch_spectrum(gd_ctx* c) {
+  k_spec_tile<<<c->n_tiles, 128, 0, c->stream>>>(tile_map(c), c->s, c->M, c->d_part, c->n_tiles);
+  bins_reduce(c, 6, 1, -1);
   return cudaGetLastError();
 }
 

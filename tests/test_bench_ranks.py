@@ -52,7 +52,8 @@ def _fake_rank_result(N=1000, K=32, ms=(20.0, 60.0, 25.0)):
     kernel_ms = {"cells": 1.0, "knn": 10.0, "rates": 3.0, "interval": 0.1, "sample": 5.0, "stats": 0.2}
     calls = {k: 10 for k in kernel_ms}
     mixed = {"ms": ms[0], "clocks": None, "launches": 170, "kernel_ms": kernel_ms, "kernel_calls": calls,
-             "events": 1234, "status": 0, "cell_factor": 0.8}
+             "events": 1234, "status": 0, "cell_factor": 0.8, "rate_redo": 3, "sample_redo": 1,
+             "dt_exe": 1.0}
     fp64 = dict(mixed, ms=ms[1])
     return dict(N=N, K=K, cfg={"workload": "test"}, mixed=mixed, fp64=fp64, times=list(ms),
                 hbm=6696.8, peak_kind="measured", h2d=40 * N, d2h=8 * N, push=False)

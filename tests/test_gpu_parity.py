@@ -146,8 +146,19 @@ def test_patch_hundred_intervals(gd, oracle):
     assert near_total <= 1e-6 * events, (near_total, events)
     inst = stats["instances"][0]
     assert inst["C"] == st.C
-    # represented mass is never written; sum N m = sum M
+    # the size spectrum of gd_stats: M summed per fine log-size bin of the current diameters,
+    # against the same sums formed here with the oracle's bins, and against the oracle's run
     s_gpu = sess.t["s"].cpu().numpy()
+    bins = np.array([oracle.fine_bin(v) for v in s_gpu])
+    want = np.bincount(bins, weights=ins["M"], minlength=96)
+    got = np.array(inst["spectrum"])
+    assert np.array_equal(got == 0.0, want == 0.0)
+    nz = want > 0
+    assert np.abs(got[nz] / want[nz] - 1.0).max() < 1e-13
+    assert got.sum() == pytest.approx(ins["M"].sum(), rel=1e-14)
+    bins_or = np.array([oracle.fine_bin(v) for v in s_or])
+    assert np.array_equal(np.bincount(bins_or, weights=ins["M"], minlength=96) > 0, got > 0)
+    # represented mass is never written; sum N m = sum M
     assert np.array_equal(sess.t["M"].cpu().numpy(), ins["M"])
     m = math.pi * P.rho_s * s_gpu ** 3 / 6.0
     assert abs((ins["M"] / m * m).sum() - ins["M"].sum()) <= 1e-12 * ins["M"].sum()
