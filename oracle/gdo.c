@@ -383,9 +383,12 @@ void gdo_choose_interval(const gdo_params* P, int64_t n, const double* s, const 
   gdo_choose_interval_ab(P, n, s, M, mA, mB, st, group_of, NULL, NULL);
 }
 
-void gdo_choose_interval_ab(const gdo_params* P, int64_t n, const double* s, const double* M,
-                            const double* mA, const double* mB, gdo_state* st,
-                            int32_t* group_of, double* A_b, double* B_b) {
+/* The request of one interval choice: controller bins, A_b and B_b, dt_req and the level k
+ * of repeated halving (dt_exe = dt_coll 2^-k) the rule above gives, capped by the time
+ * left.  Leaves st unchanged but for n_groups, near_dt and the floor status. */
+static int request_level(const gdo_params* P, int64_t n, const double* s, const double* M,
+                         const double* mA, const double* mB, gdo_state* st, int32_t* group_of,
+                         double* A_b, double* B_b, double* dt_req_out) {
   int64_t cnt[GDO_NFINE];
   int gid[GDO_NFINE];
   double sM[GDO_NFINE], sA[GDO_NFINE], sB[GDO_NFINE];
@@ -450,10 +453,24 @@ void gdo_choose_interval_ab(const gdo_params* P, int64_t n, const double* s, con
   if (dt_ab <= dt_cap * (1.0 + 1e-10) &&
       (fabs(dt - dt_ab) <= 1e-10 * dt_ab || fabs(2.0 * dt - dt_ab) <= 1e-10 * dt_ab))
     st->near_dt++;
-  st->dt_req = dt_req;
-  st->dt_exe = dt;
   st->n_groups = ng;
+  *dt_req_out = dt_req;
+  return k;
+}
+
+/* Executes the interval dt_coll 2^-k: the time left drops by its exact tick count. */
+static void commit_level(const gdo_params* P, gdo_state* st, int k, double dt_req) {
+  st->dt_req = dt_req;
+  st->dt_exe = ldexp(P->dt_coll, -k);
   st->remain_ticks -= (int64_t)1 << (60 - k);
+}
+
+void gdo_choose_interval_ab(const gdo_params* P, int64_t n, const double* s, const double* M,
+                            const double* mA, const double* mB, gdo_state* st,
+                            int32_t* group_of, double* A_b, double* B_b) {
+  double dt_req;
+  int k = request_level(P, n, s, M, mA, mB, st, group_of, A_b, B_b, &dt_req);
+  commit_level(P, st, k, dt_req);
   if (st->remain_ticks == 0) st->remain_ticks = (int64_t)1 << 60;
   st->dt_remain = ldexp((double)st->remain_ticks, -60) * P->dt_coll;
 }
@@ -731,6 +748,280 @@ int gdo_interval_step(const gdo_params* P, int64_t n, const double* x, const dou
   free(gas); free(nbr); free(d); free(V); free(s0); free(m0); free(N0);
   free(mA); free(mB); free(jsum); free(grp); free(ch); free(prs);
   return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Spatial groups, Sect. 2.5.3 (the domain split into groups that keep their own
+ * frozen-neighbour intervals; interacting groups' intervals at most 16 apart;
+ * scheduled intervals are kept, so a refinement may wait). */
+
+/* Group of a particle.  Reading: G equal-width groups, radial annuli of a disk over
+ * [R_in, R_out) with R = sqrt(x^2 + y^2), slabs of a patch over x in [-box_x/2,
+ * box_x/2); positions beyond the edges join the first or last group. */
+int32_t gdo_group_of(const gdo_params* P, int32_t G, double x, double y) {
+  double u;
+  if (P->geometry == GDO_DISK) {
+    double R = sqrt(x * x + y * y);
+    u = (R - P->R_in) / (P->R_out - P->R_in);
+  } else {
+    u = (x + 0.5 * P->box_x) / P->box_x;
+  }
+  double f = floor(u * (double)G);
+  if (!(f >= 0.0)) return 0;           /* also a NaN position */
+  if (f >= (double)G) return G - 1;
+  return (int32_t)f;
+}
+
+void gdo_groups_reset(const gdo_params* P, int32_t G, gdo_groups* S) {
+  memset(S, 0, sizeof(*S));
+  S->n_groups = G;
+  for (int g = 0; g < GDO_MAXG; ++g) {
+    S->level[g] = -1;
+    S->k_req[g] = -1;
+    S->st[g].C = 1.0;
+    S->st[g].dt_remain = P->dt_coll;
+    S->st[g].remain_ticks = 0;         /* no step begun */
+  }
+}
+
+void gdo_groups_assign(const gdo_params* P, int64_t n, const double* x, const double* y,
+                       const int32_t* nbr, int32_t* group_of, gdo_groups* S) {
+  const int G = S->n_groups;
+  for (int g = 0; g < GDO_MAXG; ++g) {
+    S->members[g] = 0;
+    S->inter[g] = 0;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    group_of[i] = gdo_group_of(P, G, x[i], y[i]);
+    S->members[group_of[i]]++;
+  }
+  /* g and h interact when a list of g holds a particle of h, or one of h a particle of g */
+  for (int64_t i = 0; i < n; ++i)
+    for (int k = 0; k < P->K; ++k) {
+      int32_t h = group_of[nbr[i * P->K + k]], g = group_of[i];
+      if (h != g) {
+        S->inter[g] |= (uint64_t)1 << h;
+        S->inter[h] |= (uint64_t)1 << g;
+      }
+    }
+}
+
+/* Levels of the active groups of one round.  Reading of the ratio-16 rule with
+ * scheduled intervals kept:
+ *  - an active group must end inside the collision step: at least its level k_fit;
+ *  - an inactive interacting group h is in the middle of its interval, which is kept:
+ *    the active group takes a level within 4 of level[h] (a coarser request is
+ *    refined to level[h] - 4, a finer one waits at level[h] + 4: a delayed
+ *    refinement), except that ending inside the step wins (counted as a break);
+ *  - among active interacting groups the finest-allowed levels follow the chains of
+ *    interactions (hi[g] <= hi[h] + 4), then each takes its request within [lo, hi]
+ *    and the coarser of two interacting groups is refined until they are within 4.
+ * Both passes are monotone iterations to their fixed points, so their order does not
+ * matter. */
+void gdo_schedule(int32_t G, const uint64_t* inter, const int64_t* members, const int32_t* active,
+                  const int32_t* k_req, const int32_t* k_fit, int32_t* level, int64_t* delayed,
+                  int64_t* breaks) {
+  int lo[GDO_MAXG], hi[GDO_MAXG], k[GDO_MAXG];
+  for (int g = 0; g < G; ++g) {
+    if (!active[g]) continue;
+    lo[g] = k_fit[g];
+    hi[g] = 60;
+    for (int h = 0; h < G; ++h) {
+      if (h == g || active[h] || members[h] == 0 || level[h] < 0) continue;
+      if (!((inter[g] >> h) & 1)) continue;
+      if (level[h] - 4 > lo[g]) lo[g] = level[h] - 4;
+      if (level[h] + 4 < hi[g]) hi[g] = level[h] + 4;
+    }
+    if (hi[g] < lo[g]) hi[g] = lo[g];
+  }
+  int changed = 1;
+  while (changed) {
+    changed = 0;
+    for (int g = 0; g < G; ++g) {
+      if (!active[g]) continue;
+      for (int h = 0; h < G; ++h) {
+        if (h == g || !active[h] || !((inter[g] >> h) & 1)) continue;
+        int cap = hi[h] + 4 > lo[g] ? hi[h] + 4 : lo[g];
+        if (cap < hi[g]) { hi[g] = cap; changed = 1; }
+      }
+    }
+  }
+  for (int g = 0; g < G; ++g) {
+    if (!active[g]) continue;
+    int kk = k_req[g] < hi[g] ? k_req[g] : hi[g];
+    k[g] = kk > lo[g] ? kk : lo[g];
+  }
+  changed = 1;
+  while (changed) {
+    changed = 0;
+    for (int g = 0; g < G; ++g) {
+      if (!active[g]) continue;
+      for (int h = 0; h < G; ++h) {
+        if (h == g || !active[h] || !((inter[g] >> h) & 1)) continue;
+        if (k[g] < k[h] - 4) { k[g] = k[h] - 4; changed = 1; }
+      }
+    }
+  }
+  for (int g = 0; g < G; ++g) {
+    if (!active[g]) continue;
+    if (k[g] < k_req[g]) (*delayed)++;
+    level[g] = k[g];
+  }
+  for (int g = 0; g < G; ++g)
+    for (int h = g + 1; h < G; ++h) {
+      if (!((inter[g] >> h) & 1) || level[g] < 0 || level[h] < 0) continue;
+      if (!active[g] && !active[h]) continue;
+      if (level[g] - level[h] > 4 || level[h] - level[g] > 4) (*breaks)++;
+    }
+}
+
+int gdo_group_round(const gdo_params* P, int64_t n, const int32_t* nbr, const double* V,
+                    const gdo_gas* gas, double* s, double* s0, const double* M,
+                    const int32_t* group_of, gdo_groups* S, gdo_outputs* out) {
+  const int G = S->n_groups;
+  const int K = P->K;
+  const int64_t full = (int64_t)1 << 60;
+  int new_step = 1;
+  for (int g = 0; g < G; ++g)
+    if (S->members[g] > 0 && S->st[g].remain_ticks > 0) new_step = 0;
+  if (new_step)
+    for (int g = 0; g < G; ++g) {
+      S->st[g].remain_ticks = full;
+      S->level[g] = -1;             /* a new step: no interval scheduled */
+    }
+  /* the clock of the round: the earliest end of a scheduled interval */
+  int64_t t = full;
+  for (int g = 0; g < G; ++g)
+    if (S->members[g] > 0 && S->st[g].remain_ticks > 0 && full - S->st[g].remain_ticks < t)
+      t = full - S->st[g].remain_ticks;
+  for (int g = 0; g < G; ++g)
+    S->active[g] = S->members[g] > 0 && S->st[g].remain_ticks > 0 &&
+                   full - S->st[g].remain_ticks == t;
+  S->t = t;
+  /* the active groups broadcast: their sizes enter the partner snapshot */
+  for (int64_t i = 0; i < n; ++i)
+    if (S->active[group_of[i]]) s0[i] = s[i];
+  double* m0 = (double*)malloc(sizeof(double) * n);
+  double* N0 = (double*)malloc(sizeof(double) * n);
+  for (int64_t j = 0; j < n; ++j) {
+    m0[j] = gdo_grain_mass(P, s0[j]);
+    N0[j] = M[j] / m0[j];
+  }
+  double* ch = (double*)malloc(sizeof(double) * 2 * K);
+  gdo_pair_t* prs = (gdo_pair_t*)malloc(sizeof(gdo_pair_t) * K);
+  double* gs = (double*)malloc(sizeof(double) * n);
+  double* gM = (double*)malloc(sizeof(double) * n);
+  double* gA = (double*)malloc(sizeof(double) * n);
+  double* gB = (double*)malloc(sizeof(double) * n);
+  double* gJ = (double*)malloc(sizeof(double) * n);
+  int32_t* gbin = (int32_t*)malloc(sizeof(int32_t) * n);
+  int32_t* cbin = (int32_t*)malloc(sizeof(int32_t) * n);   /* controller bin of each particle */
+  int64_t* idx = (int64_t*)malloc(sizeof(int64_t) * n);
+  int32_t k_fit[GDO_MAXG], k_req[GDO_MAXG];
+  double dt_req[GDO_MAXG];
+  /* rates, moments and the request of each active group (members in index order) */
+  for (int g = 0; g < G; ++g) {
+    k_fit[g] = 0;
+    k_req[g] = 0;
+    if (!S->active[g]) continue;
+    gdo_state* st = &S->st[g];
+    int64_t m = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      if (group_of[i] != g) continue;
+      double L = channels(P, &gas[i], nbr + i * K, V[i], s0[i], m0[i], s0, m0, N0, ch, prs);
+      double A = 0.0, B = 0.0;
+      for (int kk = 0; kk < K; ++kk)
+        for (int c = 0; c < 2; ++c) {
+          A = A + prs[kk].c[c] * prs[kk].J1[c];
+          B = B + prs[kk].c[c] * prs[kk].J2[c];
+        }
+      if (!isfinite(L)) st->status |= GDO_ST_NONFINITE;
+      if (out && out->lam) out->lam[i] = L;
+      idx[m] = i;
+      gs[m] = s0[i];
+      gM[m] = M[i];
+      gA[m] = A;
+      gB[m] = B;
+      ++m;
+    }
+    st->near_dt = 0;
+    st->near_audit = 0;
+    k_req[g] = request_level(P, m, gs, gM, gA, gB, st, gbin, NULL, NULL, &dt_req[g]);
+    for (int64_t t2 = 0; t2 < m; ++t2) cbin[idx[t2]] = gbin[t2];
+    while (k_fit[g] < 60 && ((int64_t)1 << (60 - k_fit[g])) > st->remain_ticks) k_fit[g]++;
+    S->k_req[g] = k_req[g];
+  }
+  gdo_schedule(G, S->inter, S->members, S->active, k_req, k_fit, S->level, &S->delayed,
+               &S->breaks);
+  /* each active group commits its interval, samples it and audits it */
+  for (int g = 0; g < G; ++g) {
+    if (!S->active[g]) continue;
+    gdo_state* st = &S->st[g];
+    commit_level(P, st, S->level[g], dt_req[g]);
+    st->dt_remain = ldexp((double)st->remain_ticks, -60) * P->dt_coll;
+    st->events = 0;
+    st->near_draw = 0;
+    int64_t m = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      if (group_of[i] != g) continue;
+      int32_t ec = 0, nn = 0;
+      uint32_t hh = 0;
+      double J = 0.0;
+      gdo_sample_one(P, &gas[i], i, nbr + i * K, V[i], s0, m0, N0, M[i], st->dt_exe,
+                     st->interval, &s[i], &ec, &hh, &nn, &J, &st->status);
+      st->events += ec;
+      st->near_draw += nn;
+      if (out && out->ev_count) out->ev_count[i] = ec;
+      if (out && out->ev_hash) out->ev_hash[i] = hh;
+      if (out && out->near) out->near[i] = nn;
+      if (out && out->jsum) out->jsum[i] = J;
+      gM[m] = M[i];
+      gJ[m] = J;
+      gbin[m] = cbin[i];     /* the controller bins of the interval's choice */
+      ++m;
+    }
+    gdo_audit(P, m, gM, gJ, gbin, st->n_groups, st);
+    st->interval++;
+    S->intervals[g]++;
+  }
+  S->rounds++;
+  free(m0); free(N0); free(ch); free(prs); free(gs); free(gM); free(gA); free(gB);
+  free(gJ); free(gbin); free(cbin); free(idx);
+  return new_step;
+}
+
+int gdo_collide_groups(const gdo_params* P, int64_t n, const double* x, const double* y,
+                       const double* z, double* s, const double* M, gdo_groups* S,
+                       int32_t max_rounds) {
+  int K = P->K;
+  if (n < K || K < 1) return -1;
+  gdo_gas* gas = (gdo_gas*)malloc(sizeof(gdo_gas) * n);
+  int32_t* nbr = (int32_t*)malloc(sizeof(int32_t) * n * K);
+  double* d = (double*)malloc(sizeof(double) * n);
+  double* V = (double*)malloc(sizeof(double) * n);
+  double* s0 = (double*)malloc(sizeof(double) * n);
+  int32_t* grp = (int32_t*)malloc(sizeof(int32_t) * n);
+  for (int64_t i = 0; i < n; ++i) {
+    gdo_gas_at(P, x[i], y[i], z[i], &gas[i]);
+    s0[i] = s[i];
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    gdo_knn_one(P, n, x, y, z, i, nbr + i * K, &d[i]);
+    V[i] = (P->kernel_mode == GDO_PHYSICAL) ? gdo_volume(P, d[i], gas[i].R) : 1.0;
+  }
+  /* members and interaction masks follow the positions and lists of this step; the
+   * groups' clocks, levels and C carry over */
+  gdo_groups_assign(P, n, x, y, nbr, grp, S);
+  int rc = -2;
+  for (int r = 0; r < max_rounds; ++r) {
+    gdo_group_round(P, n, nbr, V, gas, s, s0, M, grp, S, NULL);
+    int done = 1;
+    for (int g = 0; g < S->n_groups; ++g)
+      if (S->members[g] > 0 && S->st[g].remain_ticks > 0) done = 0;
+    if (done) { rc = r + 1; break; }
+  }
+  free(gas); free(nbr); free(d); free(V); free(s0); free(grp);
+  return rc;
 }
 
 /* ------------------------------------------------------------------ */

@@ -163,6 +163,53 @@ void   gdo_push_one(const gdo_params* P, int32_t drag, double dt, double* x, dou
                     double* z, double* vr, double* lth, double* lph, double s);
 void   gdo_push(const gdo_params* P, int32_t drag, double dt, int64_t n, double* x, double* y,
                 double* z, double* vr, double* lth, double* lph, const double* s);
+/* ---- Spatial groups, Sect. 2.5.3 ------------------------------------------------
+ * Reading: an instance is split into G spatial groups of equal width, radial annuli
+ * of a disk in R (R_in .. R_out) or slabs of a patch in x; each group has its own
+ * controller bins, safety factor C, interval level k (dt_coll 2^-k), clock and Philox
+ * interval counter.  Groups interact when a particle of one has a particle of the
+ * other in its neighbour list.  A round takes the groups whose scheduled interval ends
+ * earliest: they broadcast their particles' sizes into the partner snapshot, request a
+ * level, are scheduled (the ratio-16 rule, delayed refinements) and sample their new
+ * interval.  The step ends once every group reached dt_coll. */
+enum { GDO_MAXG = 64 };
+typedef struct {
+  int32_t n_groups;           /* G (1 .. GDO_MAXG) */
+  int32_t pad;
+  int64_t t;                  /* clock of the last round, ticks of dt_coll / 2^60 */
+  int64_t rounds;             /* rounds so far */
+  int64_t delayed;            /* requests held coarser by a scheduled interval (ratio 16) */
+  int64_t breaks;             /* interacting pairs left more than 16 apart (the step's end won) */
+  int32_t level[GDO_MAXG];    /* level of the group's scheduled (or last) interval; -1: none yet */
+  int32_t k_req[GDO_MAXG];    /* level the group requested in its last round */
+  int32_t active[GDO_MAXG];   /* 1: the group took part in the last round */
+  int32_t pad2;
+  int64_t members[GDO_MAXG];  /* particles of the group */
+  int64_t intervals[GDO_MAXG];/* intervals the group executed */
+  uint64_t inter[GDO_MAXG];   /* bit h of inter[g]: groups g and h interact (symmetric) */
+  gdo_state st[GDO_MAXG];     /* per-group interval state (C, clock via remain_ticks, ...) */
+} gdo_groups;
+
+int32_t gdo_group_of(const gdo_params* P, int32_t G, double x, double y);
+/* A fresh set of G groups (C = 1, no step begun). */
+void   gdo_groups_reset(const gdo_params* P, int32_t G, gdo_groups* S);
+/* Group of every particle, members and interaction masks from the neighbour lists. */
+void   gdo_groups_assign(const gdo_params* P, int64_t n, const double* x, const double* y,
+                         const int32_t* nbr, int32_t* group_of, gdo_groups* S);
+/* Levels of the active groups from their requests (see gdo.c). */
+void   gdo_schedule(int32_t G, const uint64_t* inter, const int64_t* members,
+                    const int32_t* active, const int32_t* k_req, const int32_t* k_fit,
+                    int32_t* level, int64_t* delayed, int64_t* breaks);
+/* One round (lists, V and gas of every particle given; s live sizes, s0 the partner
+ * snapshot, both updated).  Returns 1 if the round started a new collision step. */
+int    gdo_group_round(const gdo_params* P, int64_t n, const int32_t* nbr, const double* V,
+                       const gdo_gas* gas, double* s, double* s0, const double* M,
+                       const int32_t* group_of, gdo_groups* S, gdo_outputs* out);
+/* A whole collision step: lists once, then rounds until every group reached dt_coll. */
+int    gdo_collide_groups(const gdo_params* P, int64_t n, const double* x, const double* y,
+                          const double* z, double* s, const double* M, gdo_groups* S,
+                          int32_t max_rounds);
+
 /* The common transport timestep of Sect. 2.6 (reading; see gdo_local_dt). */
 typedef struct {
   double dt_max;        /* prescribed maximum timestep Delta t_max [s] */

@@ -62,6 +62,18 @@ class State(C.Structure):
                 ("status", C.c_int64), ("n_groups", C.c_int32), ("pad", C.c_int32)]
 
 
+MAXG = 64
+
+
+class Groups(C.Structure):
+    _fields_ = [("n_groups", C.c_int32), ("pad", C.c_int32), ("t", C.c_int64),
+                ("rounds", C.c_int64), ("delayed", C.c_int64), ("breaks", C.c_int64),
+                ("level", C.c_int32 * MAXG), ("k_req", C.c_int32 * MAXG),
+                ("active", C.c_int32 * MAXG), ("pad2", C.c_int32),
+                ("members", C.c_int64 * MAXG), ("intervals", C.c_int64 * MAXG),
+                ("inter", C.c_uint64 * MAXG), ("st", State * MAXG)]
+
+
 class Gas(C.Structure):
     _fields_ = [(k, C.c_double) for k in
                 ("R", "Z", "r", "Om", "T", "cs", "H", "h", "Sigma", "rho_g", "eta", "Re", "gst")]
@@ -125,6 +137,15 @@ def lib():
             L.gdo_local_dt.restype = dbl
             L.gdo_timestep.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
             L.gdo_timestep.restype = dbl
+            L.gdo_group_of.argtypes = [vp, C.c_int32, dbl, dbl]
+            L.gdo_group_of.restype = C.c_int32
+            L.gdo_groups_reset.argtypes = [vp, C.c_int32, vp]
+            L.gdo_groups_assign.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+            L.gdo_schedule.argtypes = [C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp]
+            L.gdo_group_round.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+            L.gdo_group_round.restype = C.c_int
+            L.gdo_collide_groups.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, C.c_int32]
+            L.gdo_collide_groups.restype = C.c_int
             _lib = L
     return _lib
 
@@ -354,3 +375,81 @@ def timestep(P: Params, rule: DtRule, x, y, z, s, vr=None, lth=None, lph=None):
     dt = lib().gdo_timestep(C.byref(P), C.byref(rule), len(dti), *[_p(a) for a in arrs],
                             *[None if a is None else _p(a) for a in vs], _p(dti))
     return dt, dti
+
+
+# ---------------------------------------------------------------- spatial groups
+def group_of(P: Params, G: int, x: float, y: float) -> int:
+    return lib().gdo_group_of(C.byref(P), G, x, y)
+
+
+def new_groups(P: Params, G: int) -> Groups:
+    assert 1 <= G <= MAXG
+    S = Groups()
+    lib().gdo_groups_reset(C.byref(P), G, C.byref(S))
+    return S
+
+
+def schedule(G, inter, members, active, k_req, k_fit, level):
+    """Levels of the active groups (gdo_schedule); level is updated in place and
+    (delayed, breaks) returned."""
+    inter = np.ascontiguousarray(inter, dtype=np.uint64)
+    members = np.ascontiguousarray(members, dtype=np.int64)
+    active, k_req, k_fit = (np.ascontiguousarray(a, dtype=np.int32) for a in (active, k_req, k_fit))
+    assert level.dtype == np.int32 and level.flags.c_contiguous
+    d = C.c_int64(0)
+    b = C.c_int64(0)
+    lib().gdo_schedule(G, _p(inter), _p(members), _p(active), _p(k_req), _p(k_fit), _p(level),
+                       C.byref(d), C.byref(b))
+    return d.value, b.value
+
+
+class GroupRun:
+    """Rounds of one instance split into spatial groups: lists, measures and gas once
+    (positions are frozen in a collision step), live sizes s and the partner snapshot s0."""
+
+    def __init__(self, P: Params, G: int, x, y, z, s, M, S: Groups | None = None):
+        self.P = P
+        self.x, self.y, self.z, self.M = (np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, z, M))
+        self.s = np.array(s, dtype=np.float64)
+        self.s0 = self.s.copy()
+        n, K = len(self.x), P.K
+        self.nbr, d = knn(P, self.x, self.y, self.z, np.arange(n))
+        self.nbr = np.ascontiguousarray(self.nbr, dtype=np.int32)
+        self.gas = (Gas * n)()
+        L = lib()
+        for i in range(n):
+            L.gdo_gas_at(C.byref(P), self.x[i], self.y[i], self.z[i], C.byref(self.gas[i]))
+        self.V = np.array([volume(P, d[i], self.gas[i].R) if P.kernel_mode == PHYSICAL else 1.0
+                           for i in range(n)])
+        self.S = S if S is not None else new_groups(P, G)
+        self.grp = np.zeros(n, dtype=np.int32)
+        L.gdo_groups_assign(C.byref(P), n, _p(self.x), _p(self.y), _p(self.nbr), _p(self.grp),
+                            C.byref(self.S))
+
+    def round(self, want=("ev_count", "ev_hash", "near")) -> dict:
+        n = len(self.x)
+        shapes = {"lam": (n, np.float64), "ev_count": (n, np.int32), "ev_hash": (n, np.uint32),
+                  "near": (n, np.int32), "jsum": (n, np.float64)}
+        res = {k: np.zeros(*shapes[k]) for k in want}
+        out = Outputs(**{k: _p(v) for k, v in res.items()})
+        res["new_step"] = lib().gdo_group_round(C.byref(self.P), n, _p(self.nbr), _p(self.V), self.gas,
+                                                _p(self.s), _p(self.s0), _p(self.M), _p(self.grp),
+                                                C.byref(self.S), C.byref(out))
+        return res
+
+    def done(self) -> bool:
+        S = self.S
+        return all(S.members[g] == 0 or S.st[g].remain_ticks == 0 for g in range(S.n_groups))
+
+
+def collide_groups(P: Params, G: int, x, y, z, s, M, S: Groups | None = None, max_rounds=1 << 20):
+    """A whole collision step of one instance in G spatial groups; s (float64) is updated
+    in place.  Returns (rounds, groups state)."""
+    x, y, z, M = (np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, z, M))
+    assert s.dtype == np.float64 and s.flags.c_contiguous
+    S = S if S is not None else new_groups(P, G)
+    rc = lib().gdo_collide_groups(C.byref(P), len(x), _p(x), _p(y), _p(z), _p(s), _p(M), C.byref(S),
+                                  max_rounds)
+    if rc < 0:
+        raise ValueError("oracle collision step failed (%d)" % rc)
+    return rc, S
