@@ -133,6 +133,13 @@ typedef struct {
   double Sc_R, Sc_Z, Sc_phi;  /* Schmidt numbers of the three directions
                                  (<= 0: 1)                                    */
   double D0;           /* ring test: D at R_0 [cm^2 s^-1]                     */
+  int32_t spatial_groups;  /* G, 0 or 1: one group; 2 .. 64: the instance is split
+                              into G spatial groups of equal width (Sect. 2.5.3),
+                              radial annuli of a disk over [R_in, R_out) by
+                              R = sqrt(x^2 + y^2), slabs of a patch over x in
+                              [-box_x/2, box_x/2) (beyond the edges: the first or
+                              last group); see gd_group_stats                    */
+  int32_t pad_sg;
 } gd_instance_params;
 
 typedef struct {
@@ -355,9 +362,66 @@ gd_status gd_stats(gd_ctx* ctx, gd_stats_t* out, gd_instance_stats* inst_out);
 gd_status gd_controller_bins(gd_ctx* ctx, int32_t instance, double* A_out, double* B_out,
                              int32_t* n_groups_out);
 
+/* Sect. 2.5.3, spatial groups (instances with spatial_groups = G > 1).  Each group
+ * keeps its own controller bins, safety factor C, interval level k (dt_exe =
+ * dt_coll 2^-k), clock and Philox interval counter.  Two groups interact when a
+ * neighbour list of one holds a particle of the other.  On such an instance one
+ * interval call (gd_collision_rates + gd_sample_collisions, one interval of
+ * gd_collide or gd_run_intervals) is one ROUND: the groups whose scheduled interval
+ * ends earliest broadcast their particles' sizes into the partner snapshot (the
+ * others' particles keep being read as they last broadcast them), request a level by
+ * the single-group rule, and are scheduled:
+ *   - a group ends inside the collision step (its remaining time bounds its level);
+ *   - against an interacting group in the middle of its interval (which is kept)
+ *     the level stays within 4 (a ratio of 16): a coarser request is refined, a
+ *     finer one waits at that group's level + 4 (a delayed refinement) -- the
+ *     collision step's end wins over the ratio (counted in breaks);
+ *   - interacting groups of the same round: finest-allowed levels propagate along
+ *     the interactions (+4 per step), each group takes its request within its
+ *     bounds, then the coarser of two interacting groups is refined until they are
+ *     within 4.
+ * Then the round's groups sample their intervals and audit them; the other groups'
+ * particles are idle (no events).  The step ends when every group reached its end;
+ * the next round starts the next step with every group.  Positions (and so groups
+ * and interactions) are taken at the neighbour build and stay frozen in the step.
+ * gd_push_staggered and gd_diffuse with dt < 0, and gd_run_intervals with push, take
+ * no grouped instance (GD_ERR_ARG).  gd_instance_stats of a grouped instance: C,
+ * dt_exe, dt_req, dt_remain and interval of group 0, events and ties summed over the
+ * groups, status OR-ed. */
+typedef struct {
+  double C;                    /* safety factor of the group                    */
+  double dt_exe;               /* its last executed interval [s] (0 when the
+                                  group was idle in the last round)             */
+  double dt_req;               /* its last requested interval [s]               */
+  int64_t clock;               /* its time in the step, ticks of dt_coll / 2^60:
+                                  the end of its scheduled interval            */
+  int64_t members;             /* particles of the group at the last build      */
+  int64_t intervals;           /* intervals the group executed                  */
+  int64_t events_total;        /* its events so far                             */
+  int64_t near_dt, near_draw;  /* its ties (interval choice; draws)             */
+  uint64_t interacts;          /* bit h: the group interacts with group h       */
+  int32_t level;               /* k of its scheduled (or last) interval; -1 none */
+  int32_t k_req;               /* k it requested in its last round              */
+  int32_t active;              /* 1: it took part in the last round             */
+  int32_t n_groups;            /* its controller bins                           */
+  uint32_t status;             /* its GD_ST_* bits                              */
+  int32_t pad;
+  /* per instance (the same in every group of it) */
+  int64_t rounds;              /* rounds so far                                 */
+  int64_t delayed;             /* requests held coarser by a scheduled interval */
+  int64_t breaks;              /* interacting pairs left more than 16 apart     */
+  int64_t round_clock;         /* clock of the last round (ticks)               */
+} gd_group_stats_t;
+
+/* The state of group `group` of instance `instance` (both 0-based; a one-group
+ * instance has group 0 only).  Synchronises the stream.  out: HOST, required.
+ * GD_ERR_ARG for an index out of range. */
+gd_status gd_group_stats(gd_ctx* ctx, int32_t instance, int32_t group, gd_group_stats_t* out);
+
 /* Runs n whole intervals (build, rates, sample and, if push != 0, push with
  * dt_exe) by replaying a CUDA graph of one interval captured on first use
- * (captures again if the arguments change).  Asynchronous. */
+ * (captures again if the arguments change); on instances with spatial groups an
+ * interval is a round.  Asynchronous. */
 gd_status gd_run_intervals(gd_ctx* ctx, int32_t n, int32_t push);
 
 /* Autotuner: times the cell binning and neighbour search (gd_build_neighbors'

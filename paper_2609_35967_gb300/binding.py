@@ -38,7 +38,8 @@ class InstanceParams(C.Structure):
                 ("box_x", C.c_double), ("box_y", C.c_double), ("t0", C.c_double),
                 ("m0", C.c_double), ("cell_size", C.c_double), ("seed", C.c_uint64),
                 ("diff_mode", C.c_int32), ("diff_chi", C.c_int32), ("Sc_R", C.c_double),
-                ("Sc_Z", C.c_double), ("Sc_phi", C.c_double), ("D0", C.c_double)]
+                ("Sc_Z", C.c_double), ("Sc_phi", C.c_double), ("D0", C.c_double),
+                ("spatial_groups", C.c_int32), ("pad_sg", C.c_int32)]
 
 
 class Config(C.Structure):
@@ -67,6 +68,17 @@ class InstanceStats(C.Structure):
                 ("spectrum", C.c_double * 96)]
 
 
+class GroupStats(C.Structure):
+    """gd_group_stats_t: one spatial group of one instance."""
+    _fields_ = [("C", C.c_double), ("dt_exe", C.c_double), ("dt_req", C.c_double),
+                ("clock", C.c_int64), ("members", C.c_int64), ("intervals", C.c_int64),
+                ("events_total", C.c_int64), ("near_dt", C.c_int64), ("near_draw", C.c_int64),
+                ("interacts", C.c_uint64), ("level", C.c_int32), ("k_req", C.c_int32),
+                ("active", C.c_int32), ("n_groups", C.c_int32), ("status", C.c_uint32),
+                ("pad", C.c_int32), ("rounds", C.c_int64), ("delayed", C.c_int64),
+                ("breaks", C.c_int64), ("round_clock", C.c_int64)]
+
+
 class DtRule(C.Structure):
     """gd_dt_rule: the common transport timestep's bounds and local limits."""
     _fields_ = [("dt_max", C.c_double), ("dt_out", C.c_double), ("f_orb", C.c_double),
@@ -90,6 +102,7 @@ SIGNATURES = {
     "gd_status_string": ([C.c_int], C.c_char_p),
     "gd_autotune": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "gd_controller_bins": ([C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "gd_group_stats": ([C.c_void_p, C.c_int32, C.c_int32, C.c_void_p], C.c_int),
     "gd_neighbors_fixed": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p,
                             C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
 }
@@ -207,6 +220,13 @@ def gd_controller_bins(ctx, instance):
     A, B, n = (C.c_double * 96)(), (C.c_double * 96)(), C.c_int32(0)
     _check("gd_controller_bins", load().gd_controller_bins(ctx, int(instance), A, B, C.byref(n)))
     return list(A)[:n.value], list(B)[:n.value]
+
+
+def gd_group_stats(ctx, instance, group):
+    """The state of one spatial group of one instance, as a dict."""
+    g = GroupStats()
+    _check("gd_group_stats", load().gd_group_stats(ctx, int(instance), int(group), C.byref(g)))
+    return {f: getattr(g, f) for f, _ in GroupStats._fields_ if not f.startswith("pad")}
 
 
 def gd_status_string(code):
@@ -349,6 +369,11 @@ class Session:
 
     def controller_bins(self, instance=0):
         return gd_controller_bins(self.ctx, instance)
+
+    def group_stats(self, instance=0):
+        """Every spatial group of one instance (one entry for a one-group instance)."""
+        G = max(1, int(self._params[instance].spatial_groups))
+        return [gd_group_stats(self.ctx, instance, g) for g in range(G)]
 
     def stats(self, check=True):
         code, st, inst = gd_stats(self.ctx, self.n_inst)

@@ -66,7 +66,8 @@ static void free_all(gd_ctx* c) {
                   c->d_cell_start, c->d_scan_tmp, c->d_cell_of, c->d_slot, c->d_perm, c->d_rank_of,
                   c->d_pos64, c->d_pos32, c->d_snap64, c->d_snap32, c->d_Mr, c->d_dist, c->d_V,
                   c->d_lam, c->d_nbr, c->d_counters, c->d_sums, c->d_dprev, c->d_redo, c->d_gx,
-                  c->d_pref32, c->d_contrib, c->d_MJ, c->d_part};
+                  c->d_pref32, c->d_contrib, c->d_MJ, c->d_part, c->d_unit_i, c->d_unit_r, c->d_gperm,
+                  c->d_uoff, c->d_utile_off, c->d_unit_inst, c->d_tcount, c->d_tbase, c->d_sb};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& e : c->ev_pool) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
@@ -105,6 +106,7 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
     if (p.diff_chi != 0 && p.diff_chi != 1) return GD_ERR_ARG;
     if (p.diff_mode == GD_DIFF_RING && !(p.D0 >= 0.0 && std::isfinite(p.D0) && p.r0 > 0.0)) return GD_ERR_ARG;
     if (p.kernel_mode != GD_KERNEL_PHYSICAL && (!finite_pos(p.t0) || !finite_pos(p.m0))) return GD_ERR_ARG;
+    if (p.spatial_groups < 0 || p.spatial_groups > kMaxSG) return GD_ERR_ARG;
   }
   const long long N = cfg->offsets[n];
   if (N >= (1LL << 31) - 1 || (long long)N * cfg->K >= (1LL << 40)) return GD_ERR_ARG;
@@ -133,6 +135,17 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
 
   std::vector<long long> tiles = tile_table(c->h_off);
   c->n_tiles = (int)tiles.back();
+  // units: one per spatial group of each instance
+  c->h_unit0.resize(n);
+  std::vector<int> unit_inst;
+  for (int b = 0; b < n; ++b) {
+    const int G = cfg->params[b].spatial_groups > 1 ? cfg->params[b].spatial_groups : 1;
+    c->h_unit0[b] = (int)unit_inst.size();
+    for (int g = 0; g < G; ++g) unit_inst.push_back(b);
+    if (G > 1) c->grouped = true;
+  }
+  c->U = (int)unit_inst.size();
+  c->n_btiles = c->grouped ? c->n_tiles + c->U : c->n_tiles;
   c->cell_cap = 16 * N + 64LL * n + 1024;
   long long nst = (c->cell_cap + 2048) / 2048 + 1;   // scan tiles of cells [0, cell_cap]
 
@@ -141,8 +154,8 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
   ok &= dalloc(&c->d_tile_off, n + 1) == cudaSuccess;
   ok &= dalloc(&c->d_inst, n) == cudaSuccess;
   ok &= dalloc(&c->d_grid, n) == cudaSuccess;
-  ok &= dalloc(&c->d_state, n) == cudaSuccess;
-  ok &= dalloc(&c->d_bins, n) == cudaSuccess;
+  ok &= dalloc(&c->d_state, c->U) == cudaSuccess;
+  ok &= dalloc(&c->d_bins, c->U) == cudaSuccess;
   ok &= dalloc(&c->d_cell_count, c->cell_cap + 1) == cudaSuccess;
   ok &= dalloc(&c->d_cell_start, c->cell_cap + 1) == cudaSuccess;
   ok &= dalloc(&c->d_scan_tmp, nst) == cudaSuccess;
@@ -167,7 +180,18 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
   }
   ok &= dalloc(reinterpret_cast<Contrib64**>(&c->d_contrib), N) == cudaSuccess;
   ok &= dalloc(&c->d_MJ, N) == cudaSuccess;
-  ok &= dalloc(&c->d_part, (size_t)kBinQ * kNFine * c->n_tiles) == cudaSuccess;
+  ok &= dalloc(&c->d_part, (size_t)kBinQ * kNFine * c->n_btiles) == cudaSuccess;
+  if (c->grouped) {
+    ok &= dalloc(&c->d_unit_i, N) == cudaSuccess;
+    ok &= dalloc(&c->d_unit_r, N) == cudaSuccess;
+    ok &= dalloc(&c->d_gperm, N) == cudaSuccess;
+    ok &= dalloc(&c->d_uoff, c->U + 1) == cudaSuccess;
+    ok &= dalloc(&c->d_utile_off, c->U + 1) == cudaSuccess;
+    ok &= dalloc(&c->d_unit_inst, c->U) == cudaSuccess;
+    ok &= dalloc(&c->d_tcount, (size_t)c->n_tiles * kMaxSG) == cudaSuccess;
+    ok &= dalloc(&c->d_tbase, (size_t)c->n_tiles * kMaxSG) == cudaSuccess;
+    ok &= dalloc(&c->d_sb, N) == cudaSuccess;
+  }
   ok &= dalloc(&c->d_counters, 16) == cudaSuccess;
   ok &= dalloc(&c->d_sums, 3 * ((size_t)n + c->n_tiles)) == cudaSuccess;
   if (!ok) {
@@ -178,7 +202,7 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
   }
 
   std::vector<InstDev> inst(n);
-  std::vector<StateDev> st(n);
+  std::vector<StateDev> st(c->U);
   for (int b = 0; b < n; ++b) {
     const gd_instance_params& p = c->h_params[b];
     InstDev& d = inst[b];
@@ -208,22 +232,34 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
     d.D0 = p.D0;
     d.off = c->h_off[b];
     d.n = c->h_off[b + 1] - c->h_off[b];
+    d.n_sg = p.spatial_groups > 1 ? p.spatial_groups : 1;
+    d.unit0 = c->h_unit0[b];
     if (p.geometry == GD_GEOM_DISK) c->any_disk = true;
     if (p.model == GD_MODEL_R) c->any_model_r = true;
-    StateDev& s = st[b];
-    std::memset(&s, 0, sizeof(s));
-    s.C = 1.0;
-    s.remain_ticks = 1LL << 60;
-    s.dt_remain = p.dt_coll;
-    for (int a = 0; a < 3; ++a) { s.bmin[a] = ~0ull; s.bmax[a] = 0ull; }
+    for (int g = 0; g < d.n_sg; ++g) {
+      StateDev& s = st[d.unit0 + g];
+      std::memset(&s, 0, sizeof(s));
+      s.C = 1.0;
+      s.remain_ticks = 1LL << 60;
+      s.dt_remain = p.dt_coll;
+      s.active = 1;
+      s.level = -1;
+      s.members = d.n_sg > 1 ? 0 : d.n;   // groups: counted at each build
+      for (int a = 0; a < 3; ++a) { s.bmin[a] = ~0ull; s.bmax[a] = 0ull; }
+    }
   }
   cudaStream_t str = c->stream;
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_off, c->h_off.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, str);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_tile_off, tiles.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, str);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_inst, inst.data(), sizeof(InstDev) * n, cudaMemcpyHostToDevice, str);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_state, st.data(), sizeof(StateDev) * n, cudaMemcpyHostToDevice, str);
-  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_bins, 0, sizeof(BinsDev) * n, str);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_state, st.data(), sizeof(StateDev) * c->U, cudaMemcpyHostToDevice, str);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_bins, 0, sizeof(BinsDev) * c->U, str);
+  if (c->grouped) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_unit_inst, unit_inst.data(), sizeof(int) * c->U, cudaMemcpyHostToDevice, str);
+    // nothing broadcast yet: the partners' sizes start as the caller's
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_sb, c->s, sizeof(double) * N, cudaMemcpyDeviceToDevice, str);
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * 16, str);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_dprev, 0, sizeof(double) * N, str);
   if (e == cudaSuccess) e = knn_prepare(c);
@@ -247,7 +283,9 @@ extern "C" gd_status gd_destroy(gd_ctx* c) {
 
 static gd_status do_build(gd_ctx* c, int32_t* nbr_out, double* d_out) {
   cudaError_t e = launch_cells(c);
+  if (e == cudaSuccess) e = launch_groups(c);
   if (e == cudaSuccess) e = launch_knn(c);
+  if (e == cudaSuccess) e = launch_group_inter(c);
   if (e == cudaSuccess) e = launch_outputs_knn(c, nbr_out, d_out);
   if (e != cudaSuccess) return GD_ERR_CUDA;
   c->phase = 1;
@@ -256,7 +294,9 @@ static gd_status do_build(gd_ctx* c, int32_t* nbr_out, double* d_out) {
 }
 
 static gd_status do_rates(gd_ctx* c, double* lam_out, double* chan_out) {
-  cudaError_t e = launch_rates(c, chan_out);
+  // spatial groups: the round's groups broadcast and the partner snapshot follows
+  cudaError_t e = launch_round_begin(c);
+  if (e == cudaSuccess) e = launch_rates(c, chan_out);
   if (e == cudaSuccess) e = launch_interval(c);
   if (e == cudaSuccess) e = launch_outputs_lam(c, lam_out);
   if (e != cudaSuccess) return GD_ERR_CUDA;
@@ -297,6 +337,7 @@ extern "C" gd_status gd_push_staggered(gd_ctx* c, double dt) {
   if (!c) return GD_ERR_ARG;
   if (!c->vr || !c->lth || !c->lph) return GD_ERR_ARG;
   if (!std::isfinite(dt)) return GD_ERR_ARG;
+  if (dt < 0.0 && c->grouped) return GD_ERR_ARG;   // groups have no common dt_exe
   c->lists_valid = false;           // positions move: gd_collide must build again
   return cuda_err(launch_push(c, dt));
 }
@@ -304,6 +345,7 @@ extern "C" gd_status gd_push_staggered(gd_ctx* c, double dt) {
 extern "C" gd_status gd_diffuse(gd_ctx* c, double dt) {
   if (!c) return GD_ERR_ARG;
   if (!std::isfinite(dt)) return GD_ERR_ARG;
+  if (dt < 0.0 && c->grouped) return GD_ERR_ARG;
   c->lists_valid = false;           // positions move: gd_collide must build again
   return cuda_err(launch_diffuse(c, dt));
 }
@@ -322,7 +364,8 @@ extern "C" gd_status gd_collide(gd_ctx* c, double tau, int32_t reuse_lists, int3
     if (n == 0 && !(reuse_lists && c->lists_valid)) {
       s = do_build(c, nullptr, nullptr);
     } else {
-      s = cuda_err(launch_snapshot(c));
+      // (with spatial groups do_rates refreshes the snapshot after the round's broadcast)
+      if (!c->grouped) s = cuda_err(launch_snapshot(c));
       c->phase = 1;
     }
     if (s == GD_OK) s = do_rates(c, nullptr, nullptr);
@@ -385,7 +428,7 @@ extern "C" gd_status gd_timestep(gd_ctx* c, const gd_dt_rule* r, double* dt_out_
 
 extern "C" gd_status gd_run_intervals(gd_ctx* c, int32_t n, int32_t push) {
   if (!c || n < 0) return GD_ERR_ARG;
-  if (push && (!c->vr || !c->lth || !c->lph)) return GD_ERR_ARG;
+  if (push && (!c->vr || !c->lth || !c->lph || c->grouped)) return GD_ERR_ARG;
   if (c->phase != 0) return GD_ERR_STATE;
   if (n == 0) return GD_OK;
   bool can_graph = c->stream != nullptr && !(c->flags & GD_FLAG_TIMING);
@@ -442,13 +485,13 @@ extern "C" gd_status gd_stats(gd_ctx* c, gd_stats_t* out, gd_instance_stats* ins
   if (!c || !out) return GD_ERR_ARG;
   if (launch_stats(c, c->d_sums) != cudaSuccess) return GD_ERR_CUDA;
   if (inst_out && launch_spectrum(c) != cudaSuccess) return GD_ERR_CUDA;
-  std::vector<StateDev> st(c->n_inst);
-  std::vector<BinsDev> bins(inst_out ? c->n_inst : 0);
-  if (inst_out && cudaMemcpyAsync(bins.data(), c->d_bins, sizeof(BinsDev) * c->n_inst, cudaMemcpyDeviceToHost,
+  std::vector<StateDev> st(c->U);
+  std::vector<BinsDev> bins(inst_out ? c->U : 0);
+  if (inst_out && cudaMemcpyAsync(bins.data(), c->d_bins, sizeof(BinsDev) * c->U, cudaMemcpyDeviceToHost,
                                   c->stream) != cudaSuccess)
     return GD_ERR_CUDA;
   std::vector<double> sums(3 * (size_t)c->n_inst);
-  cudaError_t e = cudaMemcpyAsync(st.data(), c->d_state, sizeof(StateDev) * c->n_inst, cudaMemcpyDeviceToHost, c->stream);
+  cudaError_t e = cudaMemcpyAsync(st.data(), c->d_state, sizeof(StateDev) * c->U, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(sums.data(), c->d_sums, sizeof(double) * sums.size(), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return GD_ERR_CUDA;
@@ -459,27 +502,41 @@ extern "C" gd_status gd_stats(gd_ctx* c, gd_stats_t* out, gd_instance_stats* ins
   out->n_instances = c->n_inst;
   for (int k = 0; k < gd_ctx::kSlots; ++k) { out->kernel_ms[k] = c->ms[k]; out->kernel_calls[k] = c->calls[k]; }
   for (int b = 0; b < c->n_inst; ++b) {
-    const StateDev& s = st[b];
-    out->events += s.events_total;
-    out->near_draw += s.near_draw;
-    out->near_dt += s.near_dt;
-    out->near_audit += s.near_audit;
-    out->knn_redo += s.knn_redo;
-    out->rate_redo += s.rate_redo;
-    out->sample_redo += s.sample_redo;
-    out->status |= s.status;
+    // an instance's units: one, or its spatial groups (C, dt and interval of group 0;
+    // events and ties summed; status OR-ed)
+    const int u0 = c->h_unit0[b], u1 = b + 1 < c->n_inst ? c->h_unit0[b + 1] : c->U;
+    const StateDev& s = st[u0];
+    long long events = 0, events_total = 0, near_draw = 0, near_dt = 0, near_audit = 0;
+    unsigned status = 0;
+    for (int u = u0; u < u1; ++u) {
+      const StateDev& g = st[u];
+      events += g.events;
+      events_total += g.events_total;
+      near_draw += g.near_draw;
+      near_dt += g.near_dt;
+      near_audit += g.near_audit;
+      status |= g.status;
+      out->knn_redo += g.knn_redo;
+      out->rate_redo += g.rate_redo;
+      out->sample_redo += g.sample_redo;
+    }
+    out->events += events_total;
+    out->near_draw += near_draw;
+    out->near_dt += near_dt;
+    out->near_audit += near_audit;
+    out->status |= status;
     if (inst_out) {
       gd_instance_stats& o = inst_out[b];
       std::memset(&o, 0, sizeof(o));
       o.C = s.C; o.dt_exe = s.dt_exe; o.dt_req = s.dt_req; o.dt_remain = s.dt_remain;
       o.sum_M = sums[3 * b]; o.sum_Mm = sums[3 * b + 1]; o.sum_Ms = sums[3 * b + 2];
       o.interval = s.interval_next;
-      o.events = s.events;
-      o.events_total = s.events_total;
-      o.near_draw = s.near_draw; o.near_dt = s.near_dt; o.near_audit = s.near_audit;
-      o.status = s.status;
+      o.events = events;
+      o.events_total = events_total;
+      o.near_draw = near_draw; o.near_dt = near_dt; o.near_audit = near_audit;
+      o.status = status;
       o.n_groups = s.n_groups;
-      std::memcpy(o.spectrum, bins[b].spec, sizeof(o.spectrum));
+      std::memcpy(o.spectrum, bins[u0].spec, sizeof(o.spectrum));
     }
   }
   if (out->status & GD_ST_NONFINITE) return GD_ERR_NONFINITE;
@@ -493,12 +550,47 @@ extern "C" gd_status gd_controller_bins(gd_ctx* c, int32_t instance, double* A_o
                                         int32_t* n_groups_out) {
   if (!c || instance < 0 || instance >= c->n_inst) return GD_ERR_ARG;
   BinsDev h;
-  cudaError_t e = cudaMemcpyAsync(&h, c->d_bins + instance, sizeof(BinsDev), cudaMemcpyDeviceToHost, c->stream);
+  cudaError_t e = cudaMemcpyAsync(&h, c->d_bins + c->h_unit0[instance], sizeof(BinsDev), cudaMemcpyDeviceToHost,
+                                  c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return GD_ERR_CUDA;
   if (A_out) std::memcpy(A_out, h.gA, sizeof(h.gA));
   if (B_out) std::memcpy(B_out, h.gB, sizeof(h.gB));
   if (n_groups_out) *n_groups_out = h.ngroups;
+  return GD_OK;
+}
+
+extern "C" gd_status gd_group_stats(gd_ctx* c, int32_t instance, int32_t group, gd_group_stats_t* out) {
+  if (!c || !out || instance < 0 || instance >= c->n_inst) return GD_ERR_ARG;
+  const int u0 = c->h_unit0[instance], u1 = instance + 1 < c->n_inst ? c->h_unit0[instance + 1] : c->U;
+  if (group < 0 || group >= u1 - u0) return GD_ERR_ARG;
+  StateDev h[2];
+  cudaError_t e = cudaMemcpyAsync(&h[0], c->d_state + u0, sizeof(StateDev), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&h[1], c->d_state + u0 + group, sizeof(StateDev), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return GD_ERR_CUDA;
+  const StateDev& g = h[1];
+  std::memset(out, 0, sizeof(*out));
+  out->C = g.C;
+  out->dt_exe = g.dt_exe;
+  out->dt_req = g.dt_req;
+  out->clock = (1LL << 60) - g.remain_ticks;
+  out->members = g.members;
+  out->intervals = g.intervals;
+  out->events_total = g.events_total;
+  out->near_dt = g.near_dt;
+  out->near_draw = g.near_draw;
+  out->interacts = g.inter;
+  out->level = g.level;
+  out->k_req = g.k_req;
+  out->active = g.active;
+  out->n_groups = g.n_groups;
+  out->status = g.status;
+  out->rounds = h[0].rounds;
+  out->delayed = h[0].delayed;
+  out->breaks = h[0].breaks;
+  out->round_clock = h[0].clock;
   return GD_OK;
 }
 
@@ -538,6 +630,7 @@ extern "C" gd_status gd_autotune(gd_ctx* c, double* factor_out, int32_t* xsplit_
   c->cell_factor = best;
   c->cell_xsplit = best_split;
   c->phase = 0;
+  c->lists_valid = false;      // the ranks changed: the next collision step builds again
   if (c->graph_exec) { cudaGraphExecDestroy(c->graph_exec); c->graph_exec = nullptr; c->graph_push = -1; }
   if (factor_out) *factor_out = best;
   if (xsplit_out) *xsplit_out = best_split;

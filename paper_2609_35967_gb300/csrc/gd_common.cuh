@@ -42,7 +42,12 @@ struct InstDev {
   // dust diffusion (Sect. 2.4)
   int diff_mode, diff_chi;
   double Sc_R, Sc_Z, Sc_phi, D0;
+  // spatial groups (Sect. 2.5.3): n_sg groups, whose states are units unit0 .. unit0 + n_sg - 1
+  // of the state and bin arrays (unit0 = b when no instance has more than one group)
+  int n_sg, unit0;
 };
+
+constexpr int kMaxSG = 64;               // spatial groups per instance (one 64-bit mask each)
 
 // Coordinates of the neighbour search in the instance's collision model (Sect. 2.5.1):
 // 3D positions, the meridional plane (R, Z, 0), the midplane (x, y, 0) or (R, 0, 0).  R is
@@ -54,6 +59,24 @@ __device__ __forceinline__ void model_pos(int model, double x, double y, double 
   X = __dsqrt_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)));
   Y = model == GD_MODEL_RZ ? z : 0.0;
   Z = 0.0;
+}
+
+// Spatial group of a position (Sect. 2.5.3): G equal-width radial annuli of a disk over
+// [R_in, R_out) by R = sqrt(x^2 + y^2), or slabs of a patch over x in [-box_x/2, box_x/2);
+// beyond the edges (and for a NaN) the first or last group.  Correctly rounded operations
+// without contraction, as the oracle forms them.
+__device__ __forceinline__ int group_of(const InstDev& p, double x, double y) {
+  double u;
+  if (p.geometry == GD_GEOM_DISK) {
+    const double R = __dsqrt_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)));
+    u = __ddiv_rn(__dadd_rn(R, -p.R_in), __dadd_rn(p.R_out, -p.R_in));
+  } else {
+    u = __ddiv_rn(__dadd_rn(x, __dmul_rn(0.5, p.box_x)), p.box_x);
+  }
+  const double f = floor(__dmul_rn(u, (double)p.n_sg));
+  if (!(f >= 0.0)) return 0;
+  if (f >= (double)p.n_sg) return p.n_sg - 1;
+  return (int)f;
 }
 
 // Uniform cell grid of one instance, rebuilt every interval from the data bounds.
@@ -86,7 +109,17 @@ struct StateDev {
   int hold;                 // 1: idle once the current collision step is used up (gd_collide)
   int pad_hold;
   unsigned int status;
-  int n_groups;
+  int n_groups;             // controller bins of the last interval choice
+  // spatial groups (Sect. 2.5.3); a unit is one group of one instance.  The per-instance
+  // round counters live in the instance's first unit.
+  int active;               // 1: the unit takes part in the current round (always 1 with one group)
+  int level;                // k of the scheduled (or last) interval, -1: none in this step
+  int k_req;                // level requested in the current round
+  int pad_sg;
+  long long members;        // particles of the unit
+  long long intervals;      // intervals the unit executed
+  unsigned long long inter; // bit h: the unit interacts with group h of its instance
+  long long rounds, delayed, breaks, clock;
   // bounds of the data (ordered-integer encodings of doubles), min then max, x y z
   unsigned long long bmin[3], bmax[3];
 };

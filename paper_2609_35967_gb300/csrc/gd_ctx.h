@@ -60,9 +60,27 @@ struct gd_ctx {
                                         // (FP64 form gd::Contrib64, mixed form float4)
   double* d_MJ = nullptr;               // [N] caller order: M_i times the interval's realised
                                         // sum of |ln s'/s|
-  double* d_part = nullptr;             // [kBinQ * kNFine * n_tiles] per-tile fine-bin partial sums
+  double* d_part = nullptr;             // [kBinQ * kNFine * n_btiles] per-tile fine-bin partial sums
   unsigned long long* d_counters = nullptr;  // [16] spare device counters
   double* d_sums = nullptr;             // [3 * (n_inst + n_tiles)] gd_stats sums, then per-tile partials
+
+  // spatial groups (Sect. 2.5.3).  Units: one state and bin entry per group of each
+  // instance, instance b's at unit0(b) ..; U = n_inst when no instance has more than one.
+  int U = 0;
+  bool grouped = false;                 // some instance has more than one group
+  std::vector<int> h_unit0;             // [n_inst]
+  int n_btiles = 0;                     // tiles of the fine-bin passes (n_tiles, or
+                                        // n_tiles + U over the units when grouped)
+  // grouped contexts only:
+  int* d_unit_i = nullptr;              // [N] caller order: unit of each particle
+  int* d_unit_r = nullptr;              // [N] rank order: unit of each particle
+  int* d_gperm = nullptr;               // [N] caller indices ordered by (unit, index)
+  long long* d_uoff = nullptr;          // [U + 1] first position of each unit in d_gperm
+  long long* d_utile_off = nullptr;     // [U + 1] first fine-bin tile of each unit
+  int* d_unit_inst = nullptr;           // [U] instance of each unit
+  int* d_tcount = nullptr;              // [n_tiles * kMaxSG] particles of each group per caller tile
+  long long* d_tbase = nullptr;         // [n_tiles * kMaxSG] their first position in d_gperm
+  double* d_sb = nullptr;               // [N] caller order: each particle's last broadcast size
 
   // sequencing: 0 nothing, 1 neighbours built, 2 rates done
   int phase = 0;
@@ -95,6 +113,17 @@ inline TileMap tile_map(const gd_ctx* c) {
   return tm;
 }
 
+// Tiles of the fine-bin passes: the instances' caller-index tiles, or (grouped) tiles of each
+// unit's caller indices in ascending order, read through d_gperm.
+inline TileMap bins_map(const gd_ctx* c) {
+  if (!c->grouped) return tile_map(c);
+  TileMap tm;
+  tm.off = c->d_uoff;
+  tm.n_inst = c->U;
+  tm.tile_off = c->d_utile_off;
+  return tm;
+}
+
 // launchers (each returns cudaGetLastError() of its launches)
 cudaError_t launch_cells(gd_ctx* c);
 cudaError_t launch_knn(gd_ctx* c);
@@ -108,6 +137,10 @@ cudaError_t launch_diffuse(gd_ctx* c, double dt);
 cudaError_t launch_timestep(gd_ctx* c, const gd_dt_rule& r, double* dti_out, unsigned long long* d_min,
                             unsigned long long* d_bad);
 cudaError_t launch_snapshot(gd_ctx* c);
+cudaError_t launch_groups(gd_ctx* c);          // units, their members and d_gperm (after the cells)
+cudaError_t launch_group_inter(gd_ctx* c);     // interaction masks (after the lists)
+cudaError_t launch_round_begin(gd_ctx* c);     // the round's groups, their broadcast and snapshot
+cudaError_t launch_schedule(gd_ctx* c);        // levels of the round's groups (after k_interval)
 cudaError_t launch_step_begin(gd_ctx* c, double tau, int hold);
 cudaError_t launch_step_done(gd_ctx* c, int* d_flag);
 cudaError_t launch_stats(gd_ctx* c, double* d_sums);

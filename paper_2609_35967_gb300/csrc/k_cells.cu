@@ -96,8 +96,8 @@ __global__ void k_bounds(TileMap tm, const InstDev* __restrict__ P, const double
     int a = threadIdx.x;
     unsigned long long m0 = ~0ull, m1 = 0;
     for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { m0 = min(m0, smn[a][k]); m1 = max(m1, smx[a][k]); }
-    atomicMin(&st[b].bmin[a], m0);
-    atomicMax(&st[b].bmax[a], m1);
+    atomicMin(&st[P[b].unit0].bmin[a], m0);
+    atomicMax(&st[P[b].unit0].bmax[a], m1);
   }
 }
 
@@ -202,7 +202,7 @@ __global__ void k_grid(const InstDev* __restrict__ P, StateDev* st, GridDev* gri
     long long mine = 0;
     for (int b = tid; b < n_inst; b += nthr) {
       GridDev g;
-      mine += grid_of(P[b], st[b], cell_factor, xsplit, grow, g);
+      mine += grid_of(P[b], st[P[b].unit0], cell_factor, xsplit, grow, g);
     }
     const long long total = block_sum64(mine, sh);
     if (total <= cell_cap) { fits = true; break; }
@@ -213,7 +213,7 @@ __global__ void k_grid(const InstDev* __restrict__ P, StateDev* st, GridDev* gri
     for (int base = 0; base < n_inst; base += nthr) {
       const int b = base + tid;
       GridDev g;
-      const long long cells = b < n_inst ? grid_of(P[b], st[b], cell_factor, xsplit, grow, g) : 0;
+      const long long cells = b < n_inst ? grid_of(P[b], st[P[b].unit0], cell_factor, xsplit, grow, g) : 0;
       // exclusive scan of the chunk's cell counts
       long long inc = cells;
       const int lane = tid & 31, w = tid >> 5, nw = nthr >> 5;
@@ -241,7 +241,7 @@ __global__ void k_grid(const InstDev* __restrict__ P, StateDev* st, GridDev* gri
     // stays exact, only slower) and the status reports it
     for (int b = tid; b < n_inst; b += nthr) {
       GridDev g;
-      grid_of(P[b], st[b], cell_factor, xsplit, grow, g);
+      grid_of(P[b], st[P[b].unit0], cell_factor, xsplit, grow, g);
       for (int a = 0; a < 3; ++a) {
         const double e = g.cs[a] * g.dim[a];
         g.dim[a] = 1;
@@ -251,13 +251,13 @@ __global__ void k_grid(const InstDev* __restrict__ P, StateDev* st, GridDev* gri
       grid_finish(g, P[b].geometry == GD_GEOM_PATCH);
       g.cell_off = b;
       grid[b] = g;
-      set_status(&st[b], GD_ST_CAPACITY);
+      set_status(&st[P[b].unit0], GD_ST_CAPACITY);
     }
     if (tid == 0) *used = (unsigned long long)n_inst;
   }
   __syncthreads();
   for (int b = tid; b < n_inst; b += nthr)
-    for (int a = 0; a < 3; ++a) { st[b].bmin[a] = ~0ull; st[b].bmax[a] = 0ull; }
+    for (int a = 0; a < 3; ++a) { st[P[b].unit0].bmin[a] = ~0ull; st[P[b].unit0].bmax[a] = 0ull; }
 }
 
 __global__ void k_cell_count(TileMap tm, const InstDev* __restrict__ P, const GridDev* __restrict__ grid,
@@ -481,15 +481,20 @@ std::vector<long long> tile_table(const std::vector<long long>& off) {
   return t;
 }
 
+// The sizes partners read: the live sizes, or with spatial groups each particle's size as its
+// group last broadcast it.
+static const double* partner_sizes(gd_ctx* c) { return c->grouped ? c->d_sb : c->s; }
+
 // Partner snapshot refresh at unchanged ranks (gd_collide's later intervals).
 cudaError_t launch_snapshot(gd_ctx* c) {
   time_begin(c, 0);
   const int nt = num_tiles(c);
+  const double* s = partner_sizes(c);
   if (c->precision == GD_MIXED)
-    k_snapshot<true><<<nt, 256, 0, c->stream>>>(tile_map(c), c->d_inst, c->s, c->M, c->d_rank_of, c->d_snap64,
+    k_snapshot<true><<<nt, 256, 0, c->stream>>>(tile_map(c), c->d_inst, s, c->M, c->d_rank_of, c->d_snap64,
                                                 c->d_snap32, c->d_Mr, c->d_gx);
   else
-    k_snapshot<false><<<nt, 256, 0, c->stream>>>(tile_map(c), c->d_inst, c->s, c->M, c->d_rank_of, c->d_snap64,
+    k_snapshot<false><<<nt, 256, 0, c->stream>>>(tile_map(c), c->d_inst, s, c->M, c->d_rank_of, c->d_snap64,
                                                  c->d_snap32, c->d_Mr, c->d_gx);
   time_end(c);
   c->launches += 1;
@@ -523,13 +528,14 @@ cudaError_t launch_cells(gd_ctx* c) {
   k_scan_reduce<<<nst, 256, 0, st>>>(c->d_cell_count, used, c->d_scan_tmp);
   k_scan_sums<<<1, 1024, 0, st>>>(c->d_scan_tmp, nst);
   k_scan_final<<<nst, 256, 0, st>>>(c->d_cell_count, used, c->d_scan_tmp, c->d_cell_start);
+  const double* s = partner_sizes(c);
   if (c->precision == GD_MIXED)
-    k_scatter<true><<<nt, 256, 0, st>>>(tm, c->d_inst, c->d_grid, c->x, c->y, c->z, c->s, c->M,
+    k_scatter<true><<<nt, 256, 0, st>>>(tm, c->d_inst, c->d_grid, c->x, c->y, c->z, s, c->M,
                                         c->d_cell_of, c->d_slot, c->d_cell_start, c->d_perm,
                                         c->d_rank_of, c->d_pos64, c->d_pos32, c->d_snap64,
                                         c->d_snap32, c->d_Mr, c->d_gx);
   else
-    k_scatter<false><<<nt, 256, 0, st>>>(tm, c->d_inst, c->d_grid, c->x, c->y, c->z, c->s, c->M,
+    k_scatter<false><<<nt, 256, 0, st>>>(tm, c->d_inst, c->d_grid, c->x, c->y, c->z, s, c->M,
                                          c->d_cell_of, c->d_slot, c->d_cell_start, c->d_perm,
                                          c->d_rank_of, c->d_pos64, c->d_pos32, c->d_snap64,
                                          c->d_snap32, c->d_Mr, c->d_gx);

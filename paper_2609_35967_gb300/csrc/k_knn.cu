@@ -686,7 +686,7 @@ __global__ void __launch_bounds__(128, CAP <= 40 ? 5 : 4) k_knn(KnnArgs A) {
       // the FP64 form redoes it
       const unsigned long long slot = atomicAdd(A.redo_n, 1ull);
       A.redo[slot] = (int)q;
-      atomicAdd((unsigned long long*)&A.st[b].knn_redo, 1ull);
+      atomicAdd((unsigned long long*)&A.st[A.P[b].unit0].knn_redo, 1ull);
     } else {
       // no acceptable radius: keep the row valid (the particle against itself) with an
       // infinite measure, so the particle gets no rate; the status reports it
@@ -695,7 +695,7 @@ __global__ void __launch_bounds__(128, CAP <= 40 ? 5 : 4) k_knn(KnnArgs A) {
       A.V[q] = __longlong_as_double(0x7FF0000000000000ll);
       if (A.pref32) A.pref32[q] = 0.0f;
       A.dprev[ci] = 0.0;
-      set_status(&A.st[b], GD_ST_KNN);
+      set_status(&A.st[A.P[b].unit0], GD_ST_KNN);
     }
   }
 }

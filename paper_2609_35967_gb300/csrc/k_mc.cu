@@ -49,6 +49,7 @@ struct McArgs {
   double* MJ;                 // caller order: M_i times the realised sum of |ln s'/s| (sampler)
   double* part;               // per-tile fine-bin partial sums [kBinQ][kNFine][n_tiles]
   long long n_tiles;
+  const int* unit_r;          // spatial groups: unit of each rank (nullptr: the unit is the instance)
 };
 
 // Per-particle quantities that do not depend on the live diameter.  The pair parameters
@@ -559,6 +560,11 @@ __global__ void __launch_bounds__(128, 8) k_rates(McArgs A, TileMap tm) {
   tile_range(tm, blockIdx.x, b, lo, hi);
   const InstDev& P = A.P[b];
   for (long long r = lo + threadIdx.x; r < hi; r += blockDim.x) {
+    int u = b;
+    if (A.unit_r) {
+      u = A.unit_r[r];
+      if (!A.st[u].active) continue;   // its group is in the middle of an interval
+    }
     double lam;
     T v[3];
     int fbin;
@@ -574,11 +580,11 @@ __global__ void __launch_bounds__(128, 8) k_rates(McArgs A, TileMap tm) {
       // in FP64 (k_rates_redo)
       if (!cert) {
         A.redo[atomicAdd(A.redo_n, 1ull)] = (int)r;
-        atomicAdd((unsigned long long*)&A.st[b].rate_redo, 1ull);
+        atomicAdd((unsigned long long*)&A.st[u].rate_redo, 1ull);
       }
     }
     A.lam[r] = lam;
-    if (!isfinite(lam)) set_status(&A.st[b], GD_ST_NONFINITE);
+    if (!isfinite(lam)) set_status(&A.st[u], GD_ST_NONFINITE);
   }
 }
 
@@ -599,7 +605,7 @@ __global__ void __launch_bounds__(128) k_rates_redo(McArgs A) {
     static_cast<float4*>(A.contrib)[r] =
         make_float4((float)v[0], (float)v[1], (float)v[2], pack_ebin(2.f * kU32, fbin));
     A.lam[r] = lam;
-    if (!isfinite(lam)) set_status(&A.st[b], GD_ST_NONFINITE);
+    if (!isfinite(lam)) set_status(&A.st[A.unit_r ? A.unit_r[r] : b], GD_ST_NONFINITE);
   }
 }
 
@@ -611,25 +617,28 @@ __global__ void __launch_bounds__(128) k_rates_redo(McArgs A) {
 template <typename T>
 __global__ void __launch_bounds__(128) k_bins_tile(TileMap tm, const int* __restrict__ rank_of,
                                                    const void* __restrict__ contrib, double* part,
-                                                   long long n_tiles) {
+                                                   long long n_tiles, const int* __restrict__ gperm,
+                                                   const StateDev* __restrict__ st) {
   constexpr int NW = 4;
   __shared__ T acc[NW][3 * kNFine];
   __shared__ int cnt[NW][kNFine];
   __shared__ unsigned emax[kNFine];   // bits of non-negative floats: their order as integers
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int b;
+  long long lo, hi;
+  // grouped: tiles of units (read through gperm), past the last tile or of an idle unit: none
+  if (!tile_range(tm, blockIdx.x, b, lo, hi)) return;
+  if (gperm && !st[b].active) return;
   for (int t = threadIdx.x; t < NW * 3 * kNFine; t += blockDim.x) (&acc[0][0])[t] = (T)0;
   for (int t = threadIdx.x; t < NW * kNFine; t += blockDim.x) (&cnt[0][0])[t] = 0;
   for (int t = threadIdx.x; t < kNFine; t += blockDim.x) emax[t] = 0u;
   __syncthreads();
-  int b;
-  long long lo, hi;
-  tile_range(tm, blockIdx.x, b, lo, hi);
   for (long long base = lo; base < hi; base += blockDim.x) {
     const long long i = base + threadIdx.x;
     int fb = -1;
     T v[3] = {(T)0, (T)0, (T)0};
     if (i < hi) {
-      const int r = rank_of[i];
+      const int r = rank_of[gperm ? gperm[i] : i];
       if constexpr (sizeof(T) == 8) {
         const Contrib64 c = static_cast<const Contrib64*>(contrib)[r];
         v[0] = c.M; v[1] = c.MA; v[2] = c.MB;
@@ -666,23 +675,26 @@ __global__ void __launch_bounds__(128) k_bins_tile(TileMap tm, const int* __rest
 template <bool kMixed>
 __global__ void __launch_bounds__(128) k_jbins(TileMap tm, const int* __restrict__ rank_of,
                                                const void* __restrict__ contrib, const double* __restrict__ MJ,
-                                               double* part, long long n_tiles) {
+                                               double* part, long long n_tiles, const int* __restrict__ gperm,
+                                               const StateDev* __restrict__ st) {
   constexpr int NW = 4;
   __shared__ double acc[NW][kNFine];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int t = threadIdx.x; t < NW * kNFine; t += blockDim.x) (&acc[0][0])[t] = 0.0;
-  __syncthreads();
   int b;
   long long lo, hi;
-  tile_range(tm, blockIdx.x, b, lo, hi);
+  if (!tile_range(tm, blockIdx.x, b, lo, hi)) return;
+  if (gperm && !st[b].active) return;
+  for (int t = threadIdx.x; t < NW * kNFine; t += blockDim.x) (&acc[0][0])[t] = 0.0;
+  __syncthreads();
   for (long long base = lo; base < hi; base += blockDim.x) {
     const long long i = base + threadIdx.x;
     double v[1] = {0.0};
     int fb = -1;
     if (i < hi) {
-      v[0] = MJ[i];
+      const long long ci = gperm ? gperm[i] : i;
+      v[0] = MJ[ci];
       if (v[0] != 0.0) {
-        const int r = rank_of[i];
+        const int r = rank_of[ci];
         if (kMixed) fb = ebin_bin(static_cast<const float4*>(contrib)[r].w);
         else fb = (int)static_cast<const Contrib64*>(contrib)[r].fbin;
       }
@@ -730,8 +742,12 @@ __global__ void __launch_bounds__(128) k_spec_tile(TileMap tm, const double* __r
 // Quantities q0 .. q0 + nq - 1 of BinsDev (cnt, sM, sA, sB, sJ, sE) except skip_q are
 // overwritten.
 __global__ void k_bins_reduce(const long long* __restrict__ tile_off, const double* __restrict__ part,
-                              long long n_tiles, int q0, int nq, int skip_q, BinsDev* bins) {
+                              long long n_tiles, int q0, int nq, int skip_q, BinsDev* bins,
+                              const InstDev* __restrict__ P, const StateDev* __restrict__ st) {
+  // blocks over units (st given: idle units are skipped), or over instances whose sums go to
+  // their first unit (P given)
   const int b = blockIdx.x;
+  if (st && !st[b].active) return;
   const int lane = threadIdx.x & 31;
   const int pair = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (pair >= nq * kNFine) return;
@@ -747,24 +763,31 @@ __global__ void k_bins_reduce(const long long* __restrict__ tile_off, const doub
     for (long long t = tile_off[b] + lane; t < tile_off[b + 1]; t += 32) v += src[t];
     v = warp_sum(v);
   }
-  if (lane == 0) (&bins[b].cnt[0])[q * kNFine + f] = v;
+  if (lane == 0) (&bins[P ? P[b].unit0 : b].cnt[0])[q * kNFine + f] = v;
 }
 
 // ---------------------------------------------------------------- interval choice
-// One block per instance: the fine bins are read into shared memory by all threads, then
-// one thread merges them into controller bins (>= max(K, 64) particles, ascending, a
+// One block per unit (an instance, or one spatial group of it): the fine bins are read into
+// shared memory by all threads, then one thread merges them into controller bins (>= max(K, 64) particles, ascending, a
 // remainder joins the previous bin), forms A_b and B_b in one ascending pass, and halves
 // dt_coll with the exact tick count of the time left.  A near tie of the interval choice is
 // a binding moment within 1e-10 (FP64 form) of a halving edge; in the mixed form within
 // 1.5 times the error bound of the binding bin's FP32 moments (their largest per-particle
 // bound plus 64 u of summation), at least 2e-5.
-__global__ void k_interval(const InstDev* __restrict__ P, StateDev* st, BinsDev* bins, int n_inst, int K,
-                           int no_audit, int mixed) {
+__global__ void k_interval(const InstDev* __restrict__ P, StateDev* st, BinsDev* bins, int n_units,
+                           const int* __restrict__ unit_inst, int K, int no_audit, int mixed) {
   __shared__ double cnt[kNFine], sM[kNFine], sA[kNFine], sB[kNFine], sE[kNFine];
   __shared__ double gM[kNFine], gA[kNFine], gB[kNFine], gE[kNFine];
   __shared__ int gid[kNFine];
-  const int b = blockIdx.x;
-  if (b >= n_inst) return;
+  const int b = blockIdx.x;    // the unit
+  if (b >= n_units) return;
+  const InstDev& p = P[unit_inst ? unit_inst[b] : b];
+  StateDev& S = st[b];
+  if (p.n_sg > 1 && !S.active) {
+    // a spatial group in the middle of its interval: idle in this round
+    if (threadIdx.x == 0) { S.dt_exe = 0.0; S.events = 0; }
+    return;
+  }
   BinsDev& Bn = bins[b];
   for (int f = threadIdx.x; f < kNFine; f += blockDim.x) {
     cnt[f] = Bn.cnt[f]; sM[f] = Bn.sM[f]; sA[f] = Bn.sA[f]; sB[f] = Bn.sB[f]; sE[f] = Bn.sE[f];
@@ -772,8 +795,6 @@ __global__ void k_interval(const InstDev* __restrict__ P, StateDev* st, BinsDev*
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
-  StateDev& S = st[b];
-  const InstDev& p = P[b];
   const double thr = K > 64 ? K : 64;
   int ng = 0;
   double acc = 0.0;
@@ -825,15 +846,22 @@ __global__ void k_interval(const InstDev* __restrict__ P, StateDev* st, BinsDev*
   if (dt_ab <= dt_cap * (1.0 + tie) &&
       (fabs(dt - dt_ab) <= tie * dt_ab || fabs(2.0 * dt - dt_ab) <= tie * dt_ab))
     S.near_dt++;
+  S.n_groups = ng;
+  if (p.n_sg > 1) {
+    // a spatial group: the level is its request, k_schedule decides and commits
+    S.dt_req = dt_req;
+    S.k_req = k;
+    return;
+  }
   S.dt_req = dt_req;
   S.dt_exe = dt;
-  S.n_groups = ng;
   S.remain_ticks -= 1LL << (60 - k);
   if (S.remain_ticks == 0 && !S.hold) S.remain_ticks = 1LL << 60;
   S.dt_remain = ldexp((double)S.remain_ticks, -60) * dtc;
   S.interval_cur = S.interval_next;
   S.interval_next = S.interval_next + 1;
   S.events = 0;
+  S.intervals++;
 }
 
 // ---------------------------------------------------------------- sampler
@@ -967,7 +995,7 @@ __global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
   for (long long base = next_chunk(); base < total; base = next_chunk()) {
     const bool valid = lane < per_chunk && base + lane < total;
     const long long r = !valid ? 0 : (listed ? (long long)A.list[base + lane] : base + lane);
-    int b = 0;
+    int b = 0, ub = 0;   // instance and unit (spatial group) of the particle
     double lam = 0.0, dtw = 0.0, us = 0.0, dt_exe = 0.0;
     unsigned ival = 0, i_loc = 0, key0 = 0, key1 = 0, usw0 = 0, usw1 = 0;
     bool ev = false, replay = false;
@@ -975,35 +1003,38 @@ __global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
     float eta_lam = 0.0f;   // mixed form: error bound of the first waiting time
     if (valid) {
       b = inst_of(A.off, A.n_inst, r);
+      ub = A.unit_r ? A.unit_r[r] : b;
       const InstDev& P = A.P[b];
-      dt_exe = A.st[b].dt_exe;
-      ival = (unsigned)A.st[b].interval_cur;
+      dt_exe = A.st[ub].dt_exe;     // 0 for a group idle in this round: no event
+      ival = (unsigned)A.st[ub].interval_cur;
       key0 = P.key0;
       key1 = P.key1;
       i_loc = (unsigned)(A.perm[r] - P.off);
-      if (listed) {
-        double v3[3];
-        int fb;
-        float e3;
-        rate_particle<double>(A, P, r, lam, v3, fb, e3);
-      } else {
-        lam = A.lam[r];
-      }
-      U4 w = philox(i_loc, ival, 0u, 0u, key0, key1);
-      usw0 = w.z;
-      usw1 = w.w;
-      if constexpr (!kMixed) us = u01(w.z, w.w);
-      if (lam > 0.0 && isfinite(lam)) {
-        dtw = waiting_time<T>(w.x, w.y, lam);
-        if constexpr (kMixed) {
-          // lambda*_i's bound from the rate kernel, the logarithm, quotient and roundings
-          eta_lam = ebin_err(reinterpret_cast<const float*>(A.contrib)[4 * r + 3]) + 8.f * u;
-          const float dd = (float)(dtw - dt_exe);
-          replay = !(fabsf(dd) > 1.5f * eta_lam * (float)dtw * 1.0001f + 1e-14f * (float)dt_exe);
+      if (dt_exe > 0.0) {   // else idle: a held instance or a spatial group between rounds
+        if (listed) {
+          double v3[3];
+          int fb;
+          float e3;
+          rate_particle<double>(A, P, r, lam, v3, fb, e3);
         } else {
-          if (fabs(dtw - dt_exe) < 1e-10 * dt_exe) nn++;
+          lam = A.lam[r];
         }
-        ev = !(dtw > dt_exe) && !replay;
+        U4 w = philox(i_loc, ival, 0u, 0u, key0, key1);
+        usw0 = w.z;
+        usw1 = w.w;
+        if constexpr (!kMixed) us = u01(w.z, w.w);
+        if (lam > 0.0 && isfinite(lam)) {
+          dtw = waiting_time<T>(w.x, w.y, lam);
+          if constexpr (kMixed) {
+            // lambda*_i's bound from the rate kernel, the logarithm, quotient and roundings
+            eta_lam = ebin_err(reinterpret_cast<const float*>(A.contrib)[4 * r + 3]) + 8.f * u;
+            const float dd = (float)(dtw - dt_exe);
+            replay = !(fabsf(dd) > 1.5f * eta_lam * (float)dtw * 1.0001f + 1e-14f * (float)dt_exe);
+          } else {
+            if (fabs(dtw - dt_exe) < 1e-10 * dt_exe) nn++;
+          }
+          ev = !(dtw > dt_exe) && !replay;
+        }
       }
     }
     unsigned emask = __ballot_sync(FULLM, ev);
@@ -1046,6 +1077,7 @@ __global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
       const unsigned iv = __shfl_sync(FULLM, ival, p), il = __shfl_sync(FULLM, i_loc, p);
       const unsigned k0 = __shfl_sync(FULLM, key0, p), k1 = __shfl_sync(FULLM, key1, p);
       const int bp = __shfl_sync(FULLM, b, p);
+      const int up = __shfl_sync(FULLM, ub, p);
       // mixed form: FP32 copies of per-particle constants for the per-event FP32 steps
       const float k6f = (float)f.k6, preff = f.prefT;
       float sf = (float)s;      // mixed form: the FP32 diameter the pair rates use
@@ -1244,7 +1276,7 @@ __global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
         m = m_new;
         h = h * 31u + (unsigned)(chosen + 1);
         ++e;
-        if (e >= A.max_events) { if (lane == 0) set_status(&A.st[bp], GD_ST_EVENT_CAP); break; }
+        if (e >= A.max_events) { if (lane == 0) set_status(&A.st[up], GD_ST_EVENT_CAP); break; }
         if constexpr (!kMixed) q = live_query<T>(f, s, m);
         else q = live_query_f(f, sf, (float)m);
         v = lane_channels<T, S>(A, q, m, rp, lane, c0, c1, jr, po);
@@ -1266,7 +1298,7 @@ __global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
         }
         if (!kMixed || bad64) {
           if (!(lam_now > 0.0) || !isfinite(lam_now)) {
-            if (lane == 0 && !(lam_now == 0.0)) set_status(&A.st[bp], GD_ST_NONFINITE);
+            if (lane == 0 && !(lam_now == 0.0)) set_status(&A.st[up], GD_ST_NONFINITE);
             break;
           }
         } else if (!(totf > 0.0f) || !isfinite(totf)) {
@@ -1322,15 +1354,15 @@ __global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
     if (valid) {
       if (replay) {
         A.redo[atomicAdd(A.redo_n, 1ull)] = (int)r;   // the FP64 replay samples it
-        atomicAdd((unsigned long long*)&A.st[b].sample_redo, 1ull);
+        atomicAdd((unsigned long long*)&A.st[ub].sample_redo, 1ull);
       } else {
         const int ci = A.perm[r];
         if (my_e > 0) {
           A.s_out[ci] = my_s;
-          atomicAdd((unsigned long long*)&A.st[b].events, (unsigned long long)my_e);
+          atomicAdd((unsigned long long*)&A.st[ub].events, (unsigned long long)my_e);
         }
         A.MJ[ci] = my_MJ;
-        if (nn) atomicAdd((unsigned long long*)&A.st[b].near_draw, (unsigned long long)nn);
+        if (nn) atomicAdd((unsigned long long*)&A.st[ub].near_draw, (unsigned long long)nn);
         if (A.ev_count) {
           A.ev_count[ci] = my_e;
           A.ev_hash[ci] = my_h;
@@ -1345,22 +1377,25 @@ __global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
 // gd_collide: every instance starts a collision step of length tau and idles once it is
 // used up, until the next call.
 // hold = 0 with tau = 0 returns the instances to collision steps of dt_coll.
-__global__ void k_step_begin(const InstDev* __restrict__ P, StateDev* st, int n_inst, double tau, int hold) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= n_inst) return;
+__global__ void k_step_begin(const InstDev* __restrict__ P, StateDev* st, int n_units, const int* __restrict__ unit_inst,
+                             double tau, int hold) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;   // the unit
+  if (b >= n_units) return;
   st[b].tau = tau;
   st[b].hold = hold;
   st[b].remain_ticks = 1LL << 60;
-  st[b].dt_remain = tau > 0.0 ? tau : P[b].dt_coll;
+  st[b].level = -1;
+  st[b].dt_remain = tau > 0.0 ? tau : P[unit_inst ? unit_inst[b] : b].dt_coll;
 }
 
-// *flag = 1 when every instance has used up its collision step.
-__global__ void k_step_done(const StateDev* st, int n_inst, int* flag) {
+// *flag = 1 when every unit (instance, or spatial group with members) has used up its
+// collision step.
+__global__ void k_step_done(const StateDev* st, int n_units, int* flag) {
   __shared__ int open;
   if (threadIdx.x == 0) open = 0;
   __syncthreads();
-  for (int b = threadIdx.x; b < n_inst; b += blockDim.x)
-    if (st[b].remain_ticks > 0) open = 1;
+  for (int b = threadIdx.x; b < n_units; b += blockDim.x)
+    if (st[b].remain_ticks > 0 && st[b].members > 0) open = 1;
   __syncthreads();
   if (threadIdx.x == 0) *flag = open ? 0 : 1;
 }
@@ -1369,12 +1404,13 @@ __global__ void k_step_done(const StateDev* st, int n_inst, int* flag) {
 // One block per instance: realised mass-weighted sum of |ln(s'/s)| per controller bin
 // against 2 eps C; C halves (>= 1/4) on excess, else grows by 1.25 (<= 1).  Clears the
 // fine bins for the next interval.
-__global__ void k_audit(const InstDev* __restrict__ P, StateDev* st, BinsDev* bins, int n_inst, int no_audit,
-                        double tie) {
+__global__ void k_audit(const InstDev* __restrict__ P, StateDev* st, BinsDev* bins, int n_units,
+                        const int* __restrict__ unit_inst, int no_audit, double tie) {
   __shared__ double sM[kNFine], sJ[kNFine], gM[kNFine], gJ[kNFine];
   __shared__ int gid[kNFine];
-  const int b = blockIdx.x;
-  if (b >= n_inst) return;
+  const int b = blockIdx.x;    // the unit
+  if (b >= n_units) return;
+  const InstDev& p = P[unit_inst ? unit_inst[b] : b];
   BinsDev& Bn = bins[b];
   for (int f = threadIdx.x; f < kNFine; f += blockDim.x) {
     sM[f] = Bn.sM[f]; sJ[f] = Bn.sJ[f]; gid[f] = Bn.gid[f];
@@ -1383,10 +1419,10 @@ __global__ void k_audit(const InstDev* __restrict__ P, StateDev* st, BinsDev* bi
   __syncthreads();
   if (threadIdx.x == 0 && st[b].dt_exe > 0.0) {   // an idle (held) interval leaves C alone
     StateDev& S = st[b];
-    if (P[b].audit && !no_audit) {
+    if (p.audit && !no_audit) {
       for (int f = 0; f < kNFine; ++f)
         if (gid[f] >= 0) { gM[gid[f]] += sM[f]; gJ[gid[f]] += sJ[f]; }
-      const double thr = 2.0 * P[b].eps * S.C;
+      const double thr = 2.0 * p.eps * S.C;
       bool exceed = false;
       for (int g = 0; g < Bn.ngroups; ++g) {
         const double Rg = gJ[g] / gM[g];
@@ -1407,13 +1443,13 @@ __global__ void k_audit(const InstDev* __restrict__ P, StateDev* st, BinsDev* bi
 
 // ---------------------------------------------------------------- launchers
 cudaError_t launch_step_begin(gd_ctx* c, double tau, int hold) {
-  k_step_begin<<<(c->n_inst + 127) / 128, 128, 0, c->stream>>>(c->d_inst, c->d_state, c->n_inst, tau, hold);
+  k_step_begin<<<(c->U + 127) / 128, 128, 0, c->stream>>>(c->d_inst, c->d_state, c->U, c->d_unit_inst, tau, hold);
   c->launches += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_step_done(gd_ctx* c, int* d_flag) {
-  k_step_done<<<1, 256, 0, c->stream>>>(c->d_state, c->n_inst, d_flag);
+  k_step_done<<<1, 256, 0, c->stream>>>(c->d_state, c->U, d_flag);
   c->launches += 1;
   return cudaGetLastError();
 }
@@ -1451,19 +1487,24 @@ static McArgs mc_args(gd_ctx* c) {
   A.list_n = nullptr;
   A.MJ = c->d_MJ;
   A.part = c->d_part;
-  A.n_tiles = c->n_tiles;
+  A.n_tiles = c->n_btiles;
+  A.unit_r = c->grouped ? c->d_unit_r : nullptr;
   return A;
 }
 
-// Per-instance sums of quantities q0 .. q0 + nq - 1 from the tile partials (8 warps a block).
+// Per-unit sums of quantities q0 .. q0 + nq - 1 from the fine-bin tile partials (8 warps a
+// block; idle spatial groups skipped).
 static void bins_reduce(gd_ctx* c, int q0, int nq, int skip_q) {
-  dim3 grid(c->n_inst, (nq * kNFine + 7) / 8);
-  k_bins_reduce<<<grid, 256, 0, c->stream>>>(c->d_tile_off, c->d_part, c->n_tiles, q0, nq, skip_q, c->d_bins);
+  dim3 grid(c->U, (nq * kNFine + 7) / 8);
+  k_bins_reduce<<<grid, 256, 0, c->stream>>>(c->grouped ? c->d_utile_off : c->d_tile_off, c->d_part, c->n_btiles,
+                                             q0, nq, skip_q, c->d_bins, nullptr,
+                                             c->grouped ? c->d_state : nullptr);
 }
 
 cudaError_t launch_rates(gd_ctx* c, double* chan_out) {
   McArgs A = mc_args(c);
   A.chan_out = chan_out;
+  const int* gperm = c->grouped ? c->d_gperm : nullptr;
   time_begin(c, 2);
   // one block per tile, lane = particle: any K
   if (c->precision == GD_MIXED) {
@@ -1475,13 +1516,13 @@ cudaError_t launch_rates(gd_ctx* c, double* chan_out) {
     B.list = c->d_redo;
     B.list_n = A.redo_n;
     k_rates_redo<<<c->num_sms * 2, 128, 0, c->stream>>>(B);
-    k_bins_tile<float><<<c->n_tiles, 128, 0, c->stream>>>(tile_map(c), c->d_rank_of, c->d_contrib, c->d_part,
-                                                          c->n_tiles);
+    k_bins_tile<float><<<c->n_btiles, 128, 0, c->stream>>>(bins_map(c), c->d_rank_of, c->d_contrib, c->d_part,
+                                                           c->n_btiles, gperm, c->d_state);
     c->launches += 1;
   } else {
     k_rates<double><<<c->n_tiles, 128, 0, c->stream>>>(A, tile_map(c));
-    k_bins_tile<double><<<c->n_tiles, 128, 0, c->stream>>>(tile_map(c), c->d_rank_of, c->d_contrib, c->d_part,
-                                                           c->n_tiles);
+    k_bins_tile<double><<<c->n_btiles, 128, 0, c->stream>>>(bins_map(c), c->d_rank_of, c->d_contrib, c->d_part,
+                                                            c->n_btiles, gperm, c->d_state);
   }
   bins_reduce(c, 0, 6, 4);     // count, M, M A, M B and the error bound; sJ after sampling
   time_end(c);
@@ -1491,12 +1532,14 @@ cudaError_t launch_rates(gd_ctx* c, double* chan_out) {
 
 cudaError_t launch_interval(gd_ctx* c) {
   time_begin(c, 3);
-  k_interval<<<c->n_inst, 128, 0, c->stream>>>(c->d_inst, c->d_state, c->d_bins, c->n_inst, c->K,
-                                               (c->flags & GD_FLAG_NO_AUDIT) ? 1 : 0,
-                                               c->precision == GD_MIXED ? 1 : 0);
-  time_end(c);
+  k_interval<<<c->U, 128, 0, c->stream>>>(c->d_inst, c->d_state, c->d_bins, c->U, c->d_unit_inst, c->K,
+                                          (c->flags & GD_FLAG_NO_AUDIT) ? 1 : 0,
+                                          c->precision == GD_MIXED ? 1 : 0);
   c->launches += 1;
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = launch_schedule(c);
+  time_end(c);
+  return e;
 }
 
 template <typename T, int S>
@@ -1557,23 +1600,27 @@ cudaError_t launch_sample(gd_ctx* c, int* ev_count, unsigned* ev_hash, int* near
 
 // The size spectrum of every instance into BinsDev::spec (gd_stats).
 cudaError_t launch_spectrum(gd_ctx* c) {
-  k_spec_tile<<<c->n_tiles, 128, 0, c->stream>>>(tile_map(c), c->s, c->M, c->d_part, c->n_tiles);
-  bins_reduce(c, 6, 1, -1);
+  k_spec_tile<<<c->n_tiles, 128, 0, c->stream>>>(tile_map(c), c->s, c->M, c->d_part, c->n_btiles);
+  // per instance, into its first unit
+  dim3 grid(c->n_inst, (kNFine + 7) / 8);
+  k_bins_reduce<<<grid, 256, 0, c->stream>>>(c->d_tile_off, c->d_part, c->n_btiles, 6, 1, -1, c->d_bins,
+                                             c->d_inst, nullptr);
   return cudaGetLastError();
 }
 
 cudaError_t launch_audit(gd_ctx* c) {
   time_begin(c, 3);
+  const int* gperm = c->grouped ? c->d_gperm : nullptr;
   if (c->precision == GD_MIXED)
-    k_jbins<true><<<c->n_tiles, 128, 0, c->stream>>>(tile_map(c), c->d_rank_of, c->d_contrib, c->d_MJ, c->d_part,
-                                                     c->n_tiles);
+    k_jbins<true><<<c->n_btiles, 128, 0, c->stream>>>(bins_map(c), c->d_rank_of, c->d_contrib, c->d_MJ, c->d_part,
+                                                      c->n_btiles, gperm, c->d_state);
   else
-    k_jbins<false><<<c->n_tiles, 128, 0, c->stream>>>(tile_map(c), c->d_rank_of, c->d_contrib, c->d_MJ, c->d_part,
-                                                      c->n_tiles);
+    k_jbins<false><<<c->n_btiles, 128, 0, c->stream>>>(bins_map(c), c->d_rank_of, c->d_contrib, c->d_MJ, c->d_part,
+                                                       c->n_btiles, gperm, c->d_state);
   bins_reduce(c, 4, 1, -1);
-  k_audit<<<c->n_inst, 128, 0, c->stream>>>(c->d_inst, c->d_state, c->d_bins, c->n_inst,
-                                            (c->flags & GD_FLAG_NO_AUDIT) ? 1 : 0,
-                                            c->precision == GD_MIXED ? 2e-5 : 1e-10);
+  k_audit<<<c->U, 128, 0, c->stream>>>(c->d_inst, c->d_state, c->d_bins, c->U, c->d_unit_inst,
+                                       (c->flags & GD_FLAG_NO_AUDIT) ? 1 : 0,
+                                       c->precision == GD_MIXED ? 2e-5 : 1e-10);
   time_end(c);
   c->launches += 3;
   return cudaGetLastError();

@@ -20,7 +20,7 @@ __global__ void k_push(long long N, int n_inst, const long long* __restrict__ of
   int b = inst_of(off, n_inst, i);
   const InstDev& p = P[b];
   if (p.geometry != GD_GEOM_DISK) return;
-  double dt = dt_in < 0.0 ? st[b].dt_exe : dt_in;
+  double dt = dt_in < 0.0 ? st[P[b].unit0].dt_exe : dt_in;
   double X = x[i], Y = y[i], Zc = z[i], VR = vr[i], LT = lth[i], LP = lph[i];
   double r = sqrt(X * X + Y * Y + Zc * Zc);
   double th = acos(Zc / r);
@@ -105,7 +105,7 @@ __global__ void k_push_f(long long N, int n_inst, const long long* __restrict__ 
   int b = inst_of(off, n_inst, i);
   const InstDev& p = P[b];
   if (p.geometry != GD_GEOM_DISK) return;
-  const double dt = dt_in < 0.0 ? st[b].dt_exe : dt_in;
+  const double dt = dt_in < 0.0 ? st[P[b].unit0].dt_exe : dt_in;
   const double h = 0.5 * dt;
   double X = x[i], Y = y[i], Zc = z[i], VR = vr[i], LT = lth[i], LP = lph[i];
   drift_f(h, X, Y, Zc, VR, LT, LP, true);
@@ -245,7 +245,7 @@ __global__ void k_diffuse_f(long long N, int n_inst, const long long* __restrict
   if (i >= N) return;
   const int b = inst_of(off, n_inst, i);
   const InstDev& p = P[b];
-  const float dt = (float)(dt_in < 0.0 ? st[b].dt_exe : dt_in);
+  const float dt = (float)(dt_in < 0.0 ? st[P[b].unit0].dt_exe : dt_in);
   const uint32_t il = (uint32_t)(i - p.off);
   float zR, zZ, zP, unused;
   normal_pair_f(p, il, (uint32_t)step, 0u, zR, zZ);
@@ -310,7 +310,7 @@ __global__ void k_diffuse(long long N, int n_inst, const long long* __restrict__
   if (i >= N) return;
   const int b = inst_of(off, n_inst, i);
   const InstDev& p = P[b];
-  const double dt = dt_in < 0.0 ? st[b].dt_exe : dt_in;
+  const double dt = dt_in < 0.0 ? st[P[b].unit0].dt_exe : dt_in;
   const uint32_t il = (uint32_t)(i - p.off);
   double zR, zZ, zP, unused;
   normal_pair(p, il, (uint32_t)step, 0u, zR, zZ);
