@@ -244,6 +244,44 @@ def measure_form(gd, insts, dev, precision, steps, warmup, world, push=False, gr
     return res
 
 
+def measure_collide(gd, insts, dev, G, steps, warmup, cell_factor, cell_xsplit):
+    """Whole collision steps (gd_collide over dt_coll, one neighbour build each) of the
+    workload split into G spatial groups per instance, mixed form: CUDA events on the library
+    stream around the timed steps (gd_collide synchronises after every round inside them)."""
+    import torch
+    xi = [dict(i, params=dict(i["params"], spatial_groups=G)) for i in insts]
+    sess = gd.Session(xi, precision=gd.GD_MIXED, device=str(dev), flags=gd.GD_FLAG_TIMING,
+                      cell_factor=cell_factor, cell_xsplit=cell_xsplit)
+    tau = insts[0]["params"]["dt_coll"]
+    for _ in range(warmup):
+        sess.collide(tau)
+    g0 = sess.group_stats(0)
+    pre = sess.stats()
+    st = sess.stream
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    rounds = 0
+    for _ in range(steps):
+        rounds += sess.collide(tau)
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    post = sess.stats()
+    g1 = sess.group_stats(0)
+    sess.close()
+    iv = [b["intervals"] - a["intervals"] for a, b in zip(g0, g1)]
+    upd = sum(b["members"] * d for b, d in zip(g1, iv))
+    return {"ms_per_step": ms / steps, "rounds_per_step": rounds / steps,
+            "intervals_per_step": [d / steps for d in iv], "members": [b["members"] for b in g1],
+            "updates_per_step": upd / steps, "updates_per_s": upd / (ms * 1e-3),
+            "delayed_per_step": (g1[0]["delayed"] - g0[0]["delayed"]) / steps,
+            "breaks": g1[0]["breaks"], "events_per_step": (post["events"] - pre["events"]) / steps,
+            "kernels_ms_per_step": {k: (post["kernel_ms"][k] - pre["kernel_ms"][k]) / steps
+                                    for k in post["kernel_ms"] if post["kernel_ms"][k] > pre["kernel_ms"][k]},
+            "status": post["status"]}
+
+
 def run_gpu(args, rank, world):
     import torch
 
@@ -322,6 +360,13 @@ def run_gpu(args, rank, world):
                                 K=xinsts[0]["params"]["K"], mixed=m, split=split, fp64=f,
                                 times=t, steps=xsteps, graph=xgraph, push=xpush)
 
+    # spatial groups (Sect. 2.5.3): whole collision steps of the bench disk in one group and
+    # in eight radial groups
+    groups = None
+    if not args.skip_extra and args.workload == "disk22":
+        groups = {f"G{G}": measure_collide(gd, insts, dev, G, 2, 1, mixed["cell_factor"], mixed["cell_xsplit"])
+                  for G in (1, 8)}
+
     times = max_over_ranks([mixed["ms"], fp64["ms"] if fp64 else 0.0, e2e_ms], world, dev)
     pp = None
     try:
@@ -329,7 +374,8 @@ def run_gpu(args, rank, world):
     except Exception as e:          # reported, never fatal: the HBM roofline stands alone
         pp = {"error": str(e)}
     return dict(N=N, K=K, cfg=cfg, mixed=mixed, fp64=fp64, times=times, hbm=hbm,
-                peak_kind=peak_kind, h2d=h2d, d2h=d2h, push=push, extras=extras, pipe_peaks=pp)
+                peak_kind=peak_kind, h2d=h2d, d2h=d2h, push=push, extras=extras, pipe_peaks=pp,
+                groups=groups)
 
 
 def max_over_ranks(times, world, dev):
@@ -669,6 +715,13 @@ def result_line(r, args, world):
                        "kernels_ms_per_step": {k: v / st for k, v in r["fp64"]["kernel_ms"].items()
                                                if v > 0 and k != "stats"}}
         out["mixed_over_fp64"] = out["value"] / out["fp64"]["value"]
+    if r.get("groups"):
+        g = r["groups"]
+        out["spatial_groups"] = {
+            "config": "the same disk, whole collision steps of dt_coll (gd_collide, one neighbour build "
+                      "each), mixed form, one group against eight equal-width radial groups",
+            **g, "step_time_8_over_1": g["G8"]["ms_per_step"] / g["G1"]["ms_per_step"],
+            "updates_8_over_1": g["G8"]["updates_per_step"] / g["G1"]["updates_per_step"]}
     for name, x in r.get("extras", {}).items():
         xm, xf = x["times"]
         sp = x["split"]

@@ -403,17 +403,20 @@ __device__ __forceinline__ void gas_coords(const InstDev& p, double X, double Y,
 }
 
 // The snapshot alone, at unchanged ranks (positions did not move since the last build); the
-// mixed form's FP32 (R, Z, M) stay, its fine bin follows the new size.
+// mixed form's FP32 (R, Z, M) stay, its fine bin follows the new size.  With spatial groups
+// (unit_i given) only the particles of the groups that broadcast in this round change.
 template <bool kMixed>
 __global__ void k_snapshot(TileMap tm, const InstDev* __restrict__ P, const double* __restrict__ s,
                            const double* __restrict__ M, const int* __restrict__ rank_of,
                            Snap64* __restrict__ snap64, float4* __restrict__ snap32, double* __restrict__ Mr,
-                           float4* __restrict__ gx) {
+                           float4* __restrict__ gx, const int* __restrict__ unit_i,
+                           const StateDev* __restrict__ st) {
   int b;
   long long lo, hi;
   if (!tile_range(tm, blockIdx.x, b, lo, hi)) return;
   const InstDev p = P[b];
   for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    if (unit_i && !st[unit_i[i]].active) continue;
     const int r = rank_of[i];
     put_snapshot<kMixed>(p, r, s[i], M[i], snap64, snap32, Mr);
     if (kMixed) reinterpret_cast<float*>(gx + r)[3] = __int_as_float(fine_bin(s[i]));
@@ -490,12 +493,13 @@ cudaError_t launch_snapshot(gd_ctx* c) {
   time_begin(c, 0);
   const int nt = num_tiles(c);
   const double* s = partner_sizes(c);
+  const int* unit_i = c->grouped ? c->d_unit_i : nullptr;
   if (c->precision == GD_MIXED)
     k_snapshot<true><<<nt, 256, 0, c->stream>>>(tile_map(c), c->d_inst, s, c->M, c->d_rank_of, c->d_snap64,
-                                                c->d_snap32, c->d_Mr, c->d_gx);
+                                                c->d_snap32, c->d_Mr, c->d_gx, unit_i, c->d_state);
   else
     k_snapshot<false><<<nt, 256, 0, c->stream>>>(tile_map(c), c->d_inst, s, c->M, c->d_rank_of, c->d_snap64,
-                                                 c->d_snap32, c->d_Mr, c->d_gx);
+                                                 c->d_snap32, c->d_Mr, c->d_gx, unit_i, c->d_state);
   time_end(c);
   c->launches += 1;
   return cudaGetLastError();
