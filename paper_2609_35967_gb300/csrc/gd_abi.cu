@@ -66,8 +66,8 @@ static void free_all(gd_ctx* c) {
                   c->d_cell_start, c->d_scan_tmp, c->d_cell_of, c->d_slot, c->d_perm, c->d_rank_of,
                   c->d_pos64, c->d_pos32, c->d_snap64, c->d_snap32, c->d_Mr, c->d_dist, c->d_V,
                   c->d_lam, c->d_nbr, c->d_counters, c->d_sums, c->d_dprev, c->d_redo, c->d_gx,
-                  c->d_pref32, c->d_contrib, c->d_MJ, c->d_part, c->d_unit_i, c->d_unit_r, c->d_gperm,
-                  c->d_uoff, c->d_utile_off, c->d_unit_inst, c->d_tcount, c->d_tbase, c->d_sb};
+                  c->d_pref32, c->d_contrib, c->d_MJ, c->d_part, c->d_heavy, c->d_unit_i, c->d_unit_r, c->d_gperm,
+                  c->d_uoff, c->d_utile_off, c->d_unit_inst, c->d_tcount, c->d_tbase, c->d_sb, c->d_rperm, c->d_act, c->d_aoff};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& e : c->ev_pool) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
@@ -171,6 +171,7 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
   ok &= dalloc(&c->d_dist, N) == cudaSuccess;
   ok &= dalloc(&c->d_dprev, N) == cudaSuccess;
   ok &= dalloc(&c->d_redo, N) == cudaSuccess;
+  ok &= dalloc(&c->d_heavy, N) == cudaSuccess;
   ok &= dalloc(&c->d_V, N) == cudaSuccess;
   ok &= dalloc(&c->d_lam, N) == cudaSuccess;
   ok &= dalloc(&c->d_nbr, (size_t)N * c->K) == cudaSuccess;
@@ -191,6 +192,9 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
     ok &= dalloc(&c->d_tcount, (size_t)c->n_tiles * kMaxSG) == cudaSuccess;
     ok &= dalloc(&c->d_tbase, (size_t)c->n_tiles * kMaxSG) == cudaSuccess;
     ok &= dalloc(&c->d_sb, N) == cudaSuccess;
+    ok &= dalloc(&c->d_rperm, N) == cudaSuccess;
+    ok &= dalloc(&c->d_act, N) == cudaSuccess;
+    ok &= dalloc(&c->d_aoff, c->U + 1) == cudaSuccess;
   }
   ok &= dalloc(&c->d_counters, 16) == cudaSuccess;
   ok &= dalloc(&c->d_sums, 3 * ((size_t)n + c->n_tiles)) == cudaSuccess;

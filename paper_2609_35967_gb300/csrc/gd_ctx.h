@@ -51,6 +51,7 @@ struct gd_ctx {
   double* d_dist = nullptr;             // [N] d_i, rank order
   double* d_dprev = nullptr;            // [N] d_i of the last build, caller order (0: none)
   int* d_redo = nullptr;                // [N] mixed K-NN: queries the FP64 form redoes
+  int* d_heavy = nullptr;               // [N] sampler: the particles sampled one per warp first
   double* d_V = nullptr;                // [N] V_i, rank order
   double* d_lam = nullptr;              // [N] lambda*_i, rank order
   int* d_nbr = nullptr;                 // [N*K] ranks
@@ -81,6 +82,9 @@ struct gd_ctx {
   int* d_tcount = nullptr;              // [n_tiles * kMaxSG] particles of each group per caller tile
   long long* d_tbase = nullptr;         // [n_tiles * kMaxSG] their first position in d_gperm
   double* d_sb = nullptr;               // [N] caller order: each particle's last broadcast size
+  int* d_rperm = nullptr;               // [N] ranks ordered by (unit, rank)
+  int* d_act = nullptr;                 // [N] the round's ranks (units taking part), unit by unit
+  long long* d_aoff = nullptr;          // [U + 1] each unit's first entry in d_act
 
   // sequencing: 0 nothing, 1 neighbours built, 2 rates done
   int phase = 0;
@@ -140,7 +144,8 @@ cudaError_t launch_snapshot(gd_ctx* c);
 cudaError_t launch_groups(gd_ctx* c);          // units, their members and d_gperm (after the cells)
 cudaError_t launch_group_inter(gd_ctx* c);     // interaction masks (after the lists)
 cudaError_t launch_round_begin(gd_ctx* c);     // the round's groups, their broadcast and snapshot
-cudaError_t launch_schedule(gd_ctx* c);        // levels of the round's groups (after k_interval)
+cudaError_t launch_schedule(gd_ctx* c);
+cudaError_t launch_broadcast_snapshot(gd_ctx* c);   // the round's broadcast and its snapshot entries        // levels of the round's groups (after k_interval)
 cudaError_t launch_step_begin(gd_ctx* c, double tau, int hold);
 cudaError_t launch_step_done(gd_ctx* c, int* d_flag);
 cudaError_t launch_stats(gd_ctx* c, double* d_sums);

@@ -403,23 +403,42 @@ __device__ __forceinline__ void gas_coords(const InstDev& p, double X, double Y,
 }
 
 // The snapshot alone, at unchanged ranks (positions did not move since the last build); the
-// mixed form's FP32 (R, Z, M) stay, its fine bin follows the new size.  With spatial groups
-// (unit_i given) only the particles of the groups that broadcast in this round change.
+// mixed form's FP32 (R, Z, M) stay, its fine bin follows the new size.
 template <bool kMixed>
 __global__ void k_snapshot(TileMap tm, const InstDev* __restrict__ P, const double* __restrict__ s,
                            const double* __restrict__ M, const int* __restrict__ rank_of,
                            Snap64* __restrict__ snap64, float4* __restrict__ snap32, double* __restrict__ Mr,
-                           float4* __restrict__ gx, const int* __restrict__ unit_i,
-                           const StateDev* __restrict__ st) {
+                           float4* __restrict__ gx) {
   int b;
   long long lo, hi;
   if (!tile_range(tm, blockIdx.x, b, lo, hi)) return;
   const InstDev p = P[b];
   for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    if (unit_i && !st[unit_i[i]].active) continue;
     const int r = rank_of[i];
     put_snapshot<kMixed>(p, r, s[i], M[i], snap64, snap32, Mr);
     if (kMixed) reinterpret_cast<float*>(gx + r)[3] = __int_as_float(fine_bin(s[i]));
+  }
+}
+
+// Spatial groups: the round's particles (the list act) broadcast -- their live sizes become
+// the sizes partners read (sb, caller order) -- and their snapshot entries follow; the other
+// particles' entries keep their last broadcast.
+template <bool kMixed>
+__global__ void k_broadcast_snapshot(const unsigned long long* __restrict__ total, const int* __restrict__ act,
+                                     const long long* __restrict__ off, int n_inst, const InstDev* __restrict__ P,
+                                     const int* __restrict__ perm, const double* __restrict__ s,
+                                     double* __restrict__ sb, const double* __restrict__ M,
+                                     Snap64* __restrict__ snap64, float4* __restrict__ snap32,
+                                     double* __restrict__ Mr, float4* __restrict__ gx) {
+  const long long n = (long long)*total;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int r = act[t];
+    const int ci = perm[r];
+    const double si = s[ci];
+    sb[ci] = si;
+    put_snapshot<kMixed>(P[inst_of(off, n_inst, r)], r, si, M[ci], snap64, snap32, Mr);
+    if (kMixed) reinterpret_cast<float*>(gx + r)[3] = __int_as_float(fine_bin(si));
   }
 }
 
@@ -493,13 +512,29 @@ cudaError_t launch_snapshot(gd_ctx* c) {
   time_begin(c, 0);
   const int nt = num_tiles(c);
   const double* s = partner_sizes(c);
-  const int* unit_i = c->grouped ? c->d_unit_i : nullptr;
   if (c->precision == GD_MIXED)
     k_snapshot<true><<<nt, 256, 0, c->stream>>>(tile_map(c), c->d_inst, s, c->M, c->d_rank_of, c->d_snap64,
-                                                c->d_snap32, c->d_Mr, c->d_gx, unit_i, c->d_state);
+                                                c->d_snap32, c->d_Mr, c->d_gx);
   else
     k_snapshot<false><<<nt, 256, 0, c->stream>>>(tile_map(c), c->d_inst, s, c->M, c->d_rank_of, c->d_snap64,
-                                                 c->d_snap32, c->d_Mr, c->d_gx, unit_i, c->d_state);
+                                                 c->d_snap32, c->d_Mr, c->d_gx);
+  time_end(c);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_broadcast_snapshot(gd_ctx* c) {
+  time_begin(c, 0);
+  const unsigned long long* total = c->d_counters + 10;
+  const int grid = c->num_sms * 8;
+  if (c->precision == GD_MIXED)
+    k_broadcast_snapshot<true><<<grid, 256, 0, c->stream>>>(total, c->d_act, c->d_off, c->n_inst, c->d_inst,
+                                                            c->d_perm, c->s, c->d_sb, c->M, c->d_snap64,
+                                                            c->d_snap32, c->d_Mr, c->d_gx);
+  else
+    k_broadcast_snapshot<false><<<grid, 256, 0, c->stream>>>(total, c->d_act, c->d_off, c->n_inst, c->d_inst,
+                                                             c->d_perm, c->s, c->d_sb, c->M, c->d_snap64,
+                                                             c->d_snap32, c->d_Mr, c->d_gx);
   time_end(c);
   c->launches += 1;
   return cudaGetLastError();

@@ -81,9 +81,26 @@ __global__ void k_group_scan(const InstDev* __restrict__ P, const long long* __r
   }
 }
 
-// Per caller tile: each particle's position in d_gperm (stable: ascending caller index inside
-// its unit) and its unit in rank order.  Chunks of blockDim particles; inside a warp equal
-// groups are ranked by __match_any_sync, the warps of a chunk in warp order.
+// Per rank tile: the tile's count of each group (the ranks of an instance are tiled like its
+// caller indices).
+__global__ void __launch_bounds__(256) k_unit_count(TileMap tm, const InstDev* __restrict__ P,
+                                                    const int* __restrict__ unit_r, int* __restrict__ tcount) {
+  __shared__ int cnt[kMaxSG];
+  int b;
+  long long lo, hi;
+  if (!tile_range(tm, blockIdx.x, b, lo, hi)) return;
+  const int u0 = P[b].unit0;
+  for (int g = threadIdx.x; g < kMaxSG; g += blockDim.x) cnt[g] = 0;
+  __syncthreads();
+  for (long long r = lo + threadIdx.x; r < hi; r += blockDim.x) atomicAdd(&cnt[unit_r[r] - u0], 1);
+  __syncthreads();
+  for (int g = threadIdx.x; g < kMaxSG; g += blockDim.x) tcount[(long long)blockIdx.x * kMaxSG + g] = cnt[g];
+}
+
+// Per tile of positions i (caller indices, or ranks): i's position in the unit-ordered
+// permutation perm (stable: ascending i inside its unit) and, with rank_of given, its unit in
+// rank order.  Chunks of blockDim particles; inside a warp equal groups are ranked by
+// __match_any_sync, the warps of a chunk in warp order.
 __global__ void __launch_bounds__(128) k_group_scatter(TileMap tm, const InstDev* __restrict__ P,
                                                        const int* __restrict__ unit_i,
                                                        const long long* __restrict__ tbase,
@@ -113,7 +130,7 @@ __global__ void __launch_bounds__(128) k_group_scatter(TileMap tm, const InstDev
       long long pos = run[g] + before;
       for (int ww = 0; ww < w; ++ww) pos += wcnt[ww][g];
       gperm[pos] = (int)i;
-      unit_r[rank_of[i]] = ui;
+      if (rank_of) unit_r[rank_of[i]] = ui;
     }
     __syncthreads();
     for (int gg = threadIdx.x; gg < kMaxSG; gg += blockDim.x) {
@@ -169,15 +186,6 @@ __global__ void k_round_begin(const InstDev* __restrict__ P, StateDev* st, int n
     S[g].active = (S[g].members > 0 && S[g].remain_ticks > 0 && full - S[g].remain_ticks == t) ? 1 : 0;
   S[0].clock = t;
   S[0].rounds++;
-}
-
-// The round's groups broadcast: their particles' live sizes become the sizes their partners
-// read (caller order).
-__global__ void k_broadcast(long long N, const int* __restrict__ unit_i, const StateDev* __restrict__ st,
-                            const double* __restrict__ s, double* __restrict__ sb) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  if (st[unit_i[i]].active) sb[i] = s[i];
 }
 
 // One thread per instance with groups: the levels of the round's groups from their requests
@@ -267,6 +275,56 @@ __global__ void k_schedule(const InstDev* __restrict__ P, StateDev* st, int n_in
   S[0].breaks += breaks;
 }
 
+// One block: the offsets of the round's particles in the compacted list, unit by unit (units
+// idle in the round take none), and their total in *total.
+__global__ void k_active_scan(const StateDev* __restrict__ st, int U, long long* __restrict__ aoff,
+                              unsigned long long* total) {
+  __shared__ long long wsum[32];
+  __shared__ long long carry;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < U; base += blockDim.x) {
+    const int u = base + threadIdx.x;
+    const long long v = (u < U && st[u].active) ? st[u].members : 0;
+    long long incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    long long before = carry;
+    for (int k = 0; k < w; ++k) before += wsum[k];
+    if (u < U) aoff[u] = before + incl - v;
+    __syncthreads();
+    if (threadIdx.x == 0) for (int k = 0; k < nw; ++k) carry += wsum[k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    aoff[U] = carry;
+    *total = (unsigned long long)carry;
+  }
+}
+
+// The round's particles as one list of ranks, unit by unit in rank order: position p of the
+// unit-ordered rank permutation goes to the list when its unit takes part in the round.
+__global__ void k_active_gather(long long N, int U, const long long* __restrict__ uoff,
+                                const long long* __restrict__ aoff, const StateDev* __restrict__ st,
+                                const int* __restrict__ rperm, int* __restrict__ act) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  int l = 0, h = U - 1;
+  while (l < h) {
+    const int mid = (l + h + 1) >> 1;
+    if (uoff[mid] <= p) l = mid; else h = mid - 1;
+  }
+  // l: the last unit starting at or before p (an empty unit shares its start with the next)
+  if (!st[l].active) return;
+  act[aoff[l] + (p - uoff[l])] = rperm[p];
+}
+
 // ---------------------------------------------------------------- launchers
 cudaError_t launch_groups(gd_ctx* c) {
   if (!c->grouped) return cudaSuccess;
@@ -276,8 +334,14 @@ cudaError_t launch_groups(gd_ctx* c) {
                                           c->d_uoff, c->d_utile_off, c->d_state, c->N);
   k_group_scatter<<<c->n_tiles, 128, 0, c->stream>>>(tile_map(c), c->d_inst, c->d_unit_i, c->d_tbase,
                                                      c->d_rank_of, c->d_gperm, c->d_unit_r);
+  // the ranks by unit, for the round lists
+  k_unit_count<<<c->n_tiles, 256, 0, c->stream>>>(tile_map(c), c->d_inst, c->d_unit_r, c->d_tcount);
+  k_group_scan<<<1, 1024, 0, c->stream>>>(c->d_inst, c->d_tile_off, c->d_unit_inst, c->U, c->d_tcount, c->d_tbase,
+                                          c->d_uoff, c->d_utile_off, c->d_state, c->N);
+  k_group_scatter<<<c->n_tiles, 128, 0, c->stream>>>(tile_map(c), c->d_inst, c->d_unit_r, c->d_tbase, nullptr,
+                                                     c->d_rperm, nullptr);
   time_end(c);
-  c->launches += 3;
+  c->launches += 6;
   return cudaGetLastError();
 }
 
@@ -295,11 +359,14 @@ cudaError_t launch_round_begin(gd_ctx* c) {
   if (!c->grouped) return cudaSuccess;
   time_begin(c, 3);
   k_round_begin<<<(c->n_inst + 127) / 128, 128, 0, c->stream>>>(c->d_inst, c->d_state, c->n_inst);
-  k_broadcast<<<(unsigned)((c->N + 255) / 256), 256, 0, c->stream>>>(c->N, c->d_unit_i, c->d_state, c->s, c->d_sb);
+  unsigned long long* total = c->d_counters + 10;
+  k_active_scan<<<1, 1024, 0, c->stream>>>(c->d_state, c->U, c->d_aoff, total);
+  k_active_gather<<<(unsigned)((c->N + 255) / 256), 256, 0, c->stream>>>(c->N, c->U, c->d_uoff, c->d_aoff,
+                                                                        c->d_state, c->d_rperm, c->d_act);
   time_end(c);
-  c->launches += 2;
+  c->launches += 3;
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = launch_snapshot(c);
+  if (e == cudaSuccess) e = launch_broadcast_snapshot(c);
   return e;
 }
 

@@ -50,7 +50,17 @@ struct McArgs {
   double* part;               // per-tile fine-bin partial sums [kBinQ][kNFine][n_tiles]
   long long n_tiles;
   const int* unit_r;          // spatial groups: unit of each rank (nullptr: the unit is the instance)
+  const int* act;             // spatial groups: the round's ranks (rate kernel and sampler take only
+  const unsigned long long* act_n;   //   these; nullptr: every rank)
+  const int* unit_inst;       // spatial groups: instance of each unit
+  const int* heavy;           // sampler: particles expecting more than kHeavy events, one warp each
+  const unsigned long long* heavy_n; //   first (their number; nullptr: no such list)
 };
+
+// Particles expecting more events than this in an interval (lambda*_i dt_exe) are sampled one
+// per warp ahead of the chunks of 32: their long serial event chains start first and never
+// share a warp with another chain.
+constexpr double kHeavy = 16.0;
 
 // Per-particle quantities that do not depend on the live diameter.  The pair parameters
 // are held in the pair precision T, so the mixed form converts them once per particle.
@@ -554,58 +564,99 @@ __device__ __forceinline__ bool rate_particle(const McArgs& A, const InstDev& P,
 }
 
 template <typename T>
+__device__ __forceinline__ void rates_one(const McArgs& A, const InstDev& P, long long r, int u) {
+  double lam;
+  T v[3];
+  int fbin;
+  float err;
+  const bool cert = rate_particle<T>(A, P, r, lam, v, fbin, err);
+  if constexpr (sizeof(T) == 8) {
+    Contrib64 c;
+    c.M = v[0]; c.MA = v[1]; c.MB = v[2]; c.fbin = fbin;
+    static_cast<Contrib64*>(A.contrib)[r] = c;
+  } else {
+    static_cast<float4*>(A.contrib)[r] = make_float4(v[0], v[1], v[2], pack_ebin(err, fbin));
+    // a threshold decision the FP32 values cannot certify: the particle's rates are redone
+    // in FP64 (k_rates_redo)
+    if (!cert) {
+      A.redo[atomicAdd(A.redo_n, 1ull)] = (int)r;
+      atomicAdd((unsigned long long*)&A.st[u].rate_redo, 1ull);
+    }
+  }
+  A.lam[r] = lam;
+  if (!isfinite(lam)) set_status(&A.st[u], GD_ST_NONFINITE);
+}
+
+// One block per tile of ranks; with spatial groups a grid-stride loop over the round's list.
+template <typename T>
 __global__ void __launch_bounds__(128, 8) k_rates(McArgs A, TileMap tm) {
+  if (A.act) {
+    const long long n = (long long)*A.act_n;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x) {
+      const long long r = A.act[t];
+      const int u = A.unit_r[r];
+      rates_one<T>(A, A.P[A.unit_inst[u]], r, u);
+    }
+    return;
+  }
   int b;
   long long lo, hi;
   tile_range(tm, blockIdx.x, b, lo, hi);
   const InstDev& P = A.P[b];
-  for (long long r = lo + threadIdx.x; r < hi; r += blockDim.x) {
-    int u = b;
-    if (A.unit_r) {
-      u = A.unit_r[r];
-      if (!A.st[u].active) continue;   // its group is in the middle of an interval
-    }
-    double lam;
-    T v[3];
-    int fbin;
-    float err;
-    const bool cert = rate_particle<T>(A, P, r, lam, v, fbin, err);
-    if constexpr (sizeof(T) == 8) {
-      Contrib64 c;
-      c.M = v[0]; c.MA = v[1]; c.MB = v[2]; c.fbin = fbin;
-      static_cast<Contrib64*>(A.contrib)[r] = c;
-    } else {
-      static_cast<float4*>(A.contrib)[r] = make_float4(v[0], v[1], v[2], pack_ebin(err, fbin));
-      // a threshold decision the FP32 values cannot certify: the particle's rates are redone
-      // in FP64 (k_rates_redo)
-      if (!cert) {
-        A.redo[atomicAdd(A.redo_n, 1ull)] = (int)r;
-        atomicAdd((unsigned long long*)&A.st[u].rate_redo, 1ull);
-      }
-    }
-    A.lam[r] = lam;
-    if (!isfinite(lam)) set_status(&A.st[u], GD_ST_NONFINITE);
-  }
+  for (long long r = lo + threadIdx.x; r < hi; r += blockDim.x) rates_one<T>(A, P, r, b);
 }
 
 // Mixed form: the particles k_rates could not certify, redone in FP64 (the FP64 form's
 // arithmetic), their lambda*_i and fine-bin contributions written over the FP32 ones.
 __global__ void __launch_bounds__(128) k_rates_redo(McArgs A) {
+  // a warp per listed particle, lane = slot: the serial FP64 pair loop of one thread would
+  // make the few listed particles the kernel's whole duration
+  const int lane = threadIdx.x & 31;
   const long long total = (long long)*A.list_n;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < total; t += nw) {
     const long long r = A.list[t];
     const int b = inst_of(A.off, A.n_inst, r);
-    double lam;
-    double v[3];
-    int fbin;
-    float err;
-    rate_particle<double>(A, A.P[b], r, lam, v, fbin, err);
-    // FP64 values rounded to FP32: half a unit of their last place
-    static_cast<float4*>(A.contrib)[r] =
-        make_float4((float)v[0], (float)v[1], (float)v[2], pack_ebin(2.f * kU32, fbin));
-    A.lam[r] = lam;
-    if (!isfinite(lam)) set_status(&A.st[A.unit_r ? A.unit_r[r] : b], GD_ST_NONFINITE);
+    const InstDev& P = A.P[b];
+    const Pos64 p = A.pos64[r];
+    const Snap64 sn = A.snap64[r];
+    Gas g = gas_of(P, p);
+    const Fixed<double> fx = make_fixed<double>(P, g, A.V[r], A.Mr[r], A.K);
+    double j1, j2;
+    frag_moments(sn.s, P.s_min, j1, j2);
+    const Query<double> q = live_query<double>(fx, sn.s, sn.m);
+    const int* row = A.nbr + r * A.K;
+    const long long ci = A.chan_out ? (long long)A.perm[r] * A.K : 0;
+    double tot = 0.0, la = 0.0, lb = 0.0;
+    for (int k = lane; k < A.K; k += 32) {
+      const Partner<double> pt = load_partner<double>(A, __ldg(row + k));
+      const PairOut<double> po = pair_channels<double>(q, pt.s, pt.m, pt.Nq, pt.inv_m);
+      tot += po.c0 + po.c1;
+      double a, bb;
+      pair_moments<double>(po, j1, j2, a, bb);
+      la += a;
+      lb += bb;
+      if (A.chan_out) {
+        A.chan_out[(ci + k) * 2] = fx.pref * po.c0;
+        A.chan_out[(ci + k) * 2 + 1] = fx.pref * po.c1;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      tot += __shfl_xor_sync(FULLM, tot, o);
+      la += __shfl_xor_sync(FULLM, la, o);
+      lb += __shfl_xor_sync(FULLM, lb, o);
+    }
+    if (lane == 0) {
+      const double lam = fx.pref * tot;
+      // FP64 values rounded to FP32: half a unit of their last place
+      static_cast<float4*>(A.contrib)[r] =
+          make_float4((float)fx.M, (float)(fx.M * (fx.pref * la)), (float)(fx.M * (fx.pref * lb)),
+                      pack_ebin(2.f * kU32, fine_bin(sn.s)));
+      A.lam[r] = lam;
+      if (!isfinite(lam)) set_status(&A.st[A.unit_r ? A.unit_r[r] : b], GD_ST_NONFINITE);
+    }
   }
 }
 
@@ -977,24 +1028,44 @@ __device__ __noinline__ Fp64Pick fp64_event(const McArgs& A, long long rp, int b
 // A particle with any uncertified decision is appended to A.redo and nothing of it is
 // written: the FP64 replay samples it.  The mixed form therefore reproduces the FP64 form's
 // event sequences except where the replay meets an FP64 near tie.
+// The heavy particles of the interval: lambda*_i dt_exe > kHeavy (the same product the
+// sampler's chunks test), listed in any order (each is sampled on its own).
+__global__ void k_heavy(McArgs A, int* __restrict__ heavy, unsigned long long* heavy_n) {
+  const long long total = A.act ? (long long)*A.act_n : A.N;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long r = A.act ? A.act[t] : t;
+    const int u = A.unit_r ? A.unit_r[r] : inst_of(A.off, A.n_inst, r);
+    if (A.lam[r] * A.st[u].dt_exe > kHeavy) heavy[atomicAdd(heavy_n, 1ull)] = (int)r;
+  }
+}
+
 template <typename T, int S>
 __global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
   const int lane = threadIdx.x & 31;
   constexpr bool kMixed = sizeof(T) == 4;
   const bool listed = A.list != nullptr;
-  const long long total = listed ? (long long)*A.list_n : A.N;
+  // spatial groups: the round's ranks only (A.act), 32 to a chunk like the full range
+  const long long total = listed ? (long long)*A.list_n : (A.act ? (long long)*A.act_n : A.N);
   const float u = kU32;
-  // list mode (the FP64 replays): one listed particle per warp, so that the few replayed
-  // particles, often those with the most events, run side by side
-  const int per_chunk = listed ? 1 : 32;
-  auto next_chunk = [&]() {
+  // work items from one counter: list mode (the FP64 replays) one listed particle per warp, so
+  // that the few replayed particles, often those with the most events, run side by side;
+  // otherwise first the heavy particles one per warp, then chunks of 32 ranks without them
+  const long long n_heavy = (!listed && A.heavy_n) ? (long long)*A.heavy_n : 0;
+  const long long n_items = listed ? total : n_heavy + (total + 31) / 32;
+  auto next_item = [&]() {
     unsigned long long c = 0;
     if (lane == 0) c = atomicAdd(A.work, 1ull);
-    return (long long)__shfl_sync(FULLM, c, 0) * per_chunk;
+    return (long long)__shfl_sync(FULLM, c, 0);
   };
-  for (long long base = next_chunk(); base < total; base = next_chunk()) {
-    const bool valid = lane < per_chunk && base + lane < total;
-    const long long r = !valid ? 0 : (listed ? (long long)A.list[base + lane] : base + lane);
+  for (long long item = next_item(); item < n_items; item = next_item()) {
+    const bool one = listed || item < n_heavy;   // one particle for the whole warp
+    const long long base = one ? 0 : (item - n_heavy) * 32;
+    bool valid = one ? lane == 0 : base + lane < total;
+    const long long r = !valid ? 0
+                        : listed ? (long long)A.list[item]
+                        : one ? (long long)A.heavy[item]
+                        : A.act ? (long long)A.act[base + lane] : base + lane;
     int b = 0, ub = 0;   // instance and unit (spatial group) of the particle
     double lam = 0.0, dtw = 0.0, us = 0.0, dt_exe = 0.0;
     unsigned ival = 0, i_loc = 0, key0 = 0, key1 = 0, usw0 = 0, usw1 = 0;
@@ -1004,8 +1075,12 @@ __global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
     if (valid) {
       b = inst_of(A.off, A.n_inst, r);
       ub = A.unit_r ? A.unit_r[r] : b;
-      const InstDev& P = A.P[b];
       dt_exe = A.st[ub].dt_exe;     // 0 for a group idle in this round: no event
+      // a heavy particle of a chunk is sampled by its own warp (the list of k_heavy)
+      if (!one && A.heavy_n && A.lam[r] * dt_exe > kHeavy) valid = false;
+    }
+    if (valid) {
+      const InstDev& P = A.P[b];
       ival = (unsigned)A.st[ub].interval_cur;
       key0 = P.key0;
       key1 = P.key1;
@@ -1489,6 +1564,11 @@ static McArgs mc_args(gd_ctx* c) {
   A.part = c->d_part;
   A.n_tiles = c->n_btiles;
   A.unit_r = c->grouped ? c->d_unit_r : nullptr;
+  A.act = c->grouped ? c->d_act : nullptr;
+  A.act_n = c->grouped ? c->d_counters + 10 : nullptr;
+  A.unit_inst = c->d_unit_inst;
+  A.heavy = nullptr;
+  A.heavy_n = nullptr;
   return A;
 }
 
@@ -1501,6 +1581,10 @@ static void bins_reduce(gd_ctx* c, int q0, int nq, int skip_q) {
                                              c->grouped ? c->d_state : nullptr);
 }
 
+// The rate kernel's grid: a block per tile of ranks, or (spatial groups) a grid-stride loop
+// over the round's list on every SM.
+static int rate_grid(const gd_ctx* c) { return c->grouped ? c->num_sms * 8 : c->n_tiles; }
+
 cudaError_t launch_rates(gd_ctx* c, double* chan_out) {
   McArgs A = mc_args(c);
   A.chan_out = chan_out;
@@ -1511,7 +1595,7 @@ cudaError_t launch_rates(gd_ctx* c, double* chan_out) {
     // particles the FP32 rates cannot certify are listed (counter 5) and redone in FP64
     A.redo_n = c->d_counters + 5;
     cudaMemsetAsync(A.redo_n, 0, sizeof(unsigned long long), c->stream);
-    k_rates<float><<<c->n_tiles, 128, 0, c->stream>>>(A, tile_map(c));
+    k_rates<float><<<rate_grid(c), 128, 0, c->stream>>>(A, tile_map(c));
     McArgs B = A;
     B.list = c->d_redo;
     B.list_n = A.redo_n;
@@ -1520,7 +1604,7 @@ cudaError_t launch_rates(gd_ctx* c, double* chan_out) {
                                                            c->n_btiles, gperm, c->d_state);
     c->launches += 1;
   } else {
-    k_rates<double><<<c->n_tiles, 128, 0, c->stream>>>(A, tile_map(c));
+    k_rates<double><<<rate_grid(c), 128, 0, c->stream>>>(A, tile_map(c));
     k_bins_tile<double><<<c->n_btiles, 128, 0, c->stream>>>(bins_map(c), c->d_rank_of, c->d_contrib, c->d_part,
                                                             c->n_btiles, gperm, c->d_state);
   }
@@ -1560,6 +1644,8 @@ static void sample_launch(gd_ctx* c, const McArgs& A) {
     B.list = c->d_redo;
     B.list_n = c->d_counters + 6;
     B.work = c->d_counters + 7;
+    B.heavy = nullptr;
+    B.heavy_n = nullptr;
     k_sample<double, S><<<c->num_sms * 4, 64, 0, c->stream>>>(B);
     c->launches += 1;
   }
@@ -1569,6 +1655,13 @@ template <typename T>
 static void sample_t(gd_ctx* c, McArgs& A) {
   int S = (c->K + 31) / 32;
   A.work = c->d_counters;
+  // the heavy particles first, one warp each (counter 11 counts them)
+  unsigned long long* hn = c->d_counters + 11;
+  cudaMemsetAsync(hn, 0, sizeof(unsigned long long), c->stream);
+  k_heavy<<<c->num_sms * 8, 256, 0, c->stream>>>(A, c->d_heavy, hn);
+  c->launches += 1;
+  A.heavy = c->d_heavy;
+  A.heavy_n = hn;
   if (sizeof(T) == 4) {
     A.redo_n = c->d_counters + 6;
     cudaMemsetAsync(c->d_counters + 6, 0, 2 * sizeof(unsigned long long), c->stream);
@@ -1592,6 +1685,12 @@ cudaError_t launch_sample(gd_ctx* c, int* ev_count, unsigned* ev_hash, int* near
     A.ev_count = nullptr;
   }
   time_begin(c, 4);
+  if (c->grouped && A.ev_count) {
+    // the sampler visits only the round's particles: the others report no event
+    cudaMemsetAsync(ev_count, 0, sizeof(int) * c->N, c->stream);
+    cudaMemsetAsync(ev_hash, 0, sizeof(unsigned) * c->N, c->stream);
+    cudaMemsetAsync(near, 0, sizeof(int) * c->N, c->stream);
+  }
   if (c->precision == GD_MIXED) sample_t<float>(c, A); else sample_t<double>(c, A);
   time_end(c);
   c->launches += 1;
