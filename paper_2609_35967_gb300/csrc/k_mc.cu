@@ -1000,7 +1000,8 @@ __device__ __noinline__ Fp64Pick fp64_event(const McArgs& A, long long rp, int b
   return r;
 }
 
-// Chunks of 32 ranks are taken from a counter (lane = particle): event counts are
+// Work items are taken from a counter: first the heavy particles (more than kHeavy events
+// expected), one per warp, then chunks of 32 ranks (lane = particle): event counts are
 // heavy-tailed, so a static assignment would leave warps idle behind the busiest chunks.
 // Each lane draws its particle's first waiting time from lambda*_i; the particles with an
 // event are then taken one at a time by the whole warp (lane = slot): the channel rates, the
@@ -1010,9 +1011,7 @@ __device__ __noinline__ Fp64Pick fp64_event(const McArgs& A, long long rp, int b
 //
 // FP64 form: FP64 throughout.  A draw within 1e-10 of a channel boundary or of dt_exe, and a
 // pair within 1e-10 of an outcome, grouping or turbulence-regime threshold, is counted as a
-// near tie of the particle.  List mode (A.list): only the listed ranks, each lane's
-// lambda*_i formed afresh with the rate kernel's FP64 arithmetic -- the FP64 replay of the
-// particles a mixed context could not certify.
+// near tie of the particle.
 //
 // Mixed form: FP32 channel rates, FP64 masses, fragment sizes and waiting-time sums.  Every
 // decision is certified to be the one the FP64 form takes, from error bounds:
@@ -1025,8 +1024,9 @@ __device__ __noinline__ Fp64Pick fp64_event(const McArgs& A, long long rp, int b
 //    prefactor's rounding) of the FP64 one: the running error bound of the time sum, and the
 //    decision against dt_exe certified when t + dt_w lies more than 1.5 times that bound
 //    (plus 1e-14 dt_exe) from dt_exe.
-// A particle with any uncertified decision is appended to A.redo and nothing of it is
-// written: the FP64 replay samples it.  The mixed form therefore reproduces the FP64 form's
+// A particle with any uncertified decision writes nothing: the same warp replays it at once
+// with the FP64 form's sampler (replay64, lambda*_i formed afresh with the rate kernel's FP64
+// arithmetic), which writes its results.  The mixed form therefore reproduces the FP64 form's
 // event sequences except where the replay meets an FP64 near tie.
 // The heavy particles of the interval: lambda*_i dt_exe > kHeavy (the same product the
 // sampler's chunks test), listed in any order (each is sampled on its own).
@@ -1040,165 +1040,307 @@ __global__ void k_heavy(McArgs A, int* __restrict__ heavy, unsigned long long* h
   }
 }
 
+// One work item of the sampler (a chunk of 32 particles, lane = particle, or one particle
+// for the whole warp): the first waiting times, then each event particle's chain with the
+// warp (lane = slot), then the results.  fresh: lambda*_i formed here in FP64 (the replay)
+// rather than read from the rate kernel.
+template <int S>
+__device__ __noinline__ void replay64(McArgs A, long long r, int lane);
+
 template <typename T, int S>
-__global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void sample_item(const McArgs& A, const int lane, const bool one, const bool fresh,
+                                            const long long r, bool valid) {
   constexpr bool kMixed = sizeof(T) == 4;
-  const bool listed = A.list != nullptr;
-  // spatial groups: the round's ranks only (A.act), 32 to a chunk like the full range
-  const long long total = listed ? (long long)*A.list_n : (A.act ? (long long)*A.act_n : A.N);
   const float u = kU32;
-  // work items from one counter: list mode (the FP64 replays) one listed particle per warp, so
-  // that the few replayed particles, often those with the most events, run side by side;
-  // otherwise first the heavy particles one per warp, then chunks of 32 ranks without them
-  const long long n_heavy = (!listed && A.heavy_n) ? (long long)*A.heavy_n : 0;
-  const long long n_items = listed ? total : n_heavy + (total + 31) / 32;
-  auto next_item = [&]() {
-    unsigned long long c = 0;
-    if (lane == 0) c = atomicAdd(A.work, 1ull);
-    return (long long)__shfl_sync(FULLM, c, 0);
-  };
-  for (long long item = next_item(); item < n_items; item = next_item()) {
-    const bool one = listed || item < n_heavy;   // one particle for the whole warp
-    const long long base = one ? 0 : (item - n_heavy) * 32;
-    bool valid = one ? lane == 0 : base + lane < total;
-    const long long r = !valid ? 0
-                        : listed ? (long long)A.list[item]
-                        : one ? (long long)A.heavy[item]
-                        : A.act ? (long long)A.act[base + lane] : base + lane;
-    int b = 0, ub = 0;   // instance and unit (spatial group) of the particle
-    double lam = 0.0, dtw = 0.0, us = 0.0, dt_exe = 0.0;
-    unsigned ival = 0, i_loc = 0, key0 = 0, key1 = 0, usw0 = 0, usw1 = 0;
-    bool ev = false, replay = false;
-    int nn = 0;
-    float eta_lam = 0.0f;   // mixed form: error bound of the first waiting time
-    if (valid) {
-      b = inst_of(A.off, A.n_inst, r);
-      ub = A.unit_r ? A.unit_r[r] : b;
-      dt_exe = A.st[ub].dt_exe;     // 0 for a group idle in this round: no event
-      // a heavy particle of a chunk is sampled by its own warp (the list of k_heavy)
-      if (!one && A.heavy_n && A.lam[r] * dt_exe > kHeavy) valid = false;
-    }
-    if (valid) {
-      const InstDev& P = A.P[b];
-      ival = (unsigned)A.st[ub].interval_cur;
-      key0 = P.key0;
-      key1 = P.key1;
-      i_loc = (unsigned)(A.perm[r] - P.off);
-      if (dt_exe > 0.0) {   // else idle: a held instance or a spatial group between rounds
-        if (listed) {
-          double v3[3];
-          int fb;
-          float e3;
-          rate_particle<double>(A, P, r, lam, v3, fb, e3);
-        } else {
-          lam = A.lam[r];
-        }
-        U4 w = philox(i_loc, ival, 0u, 0u, key0, key1);
-        usw0 = w.z;
-        usw1 = w.w;
-        if constexpr (!kMixed) us = u01(w.z, w.w);
-        if (lam > 0.0 && isfinite(lam)) {
-          dtw = waiting_time<T>(w.x, w.y, lam);
-          if constexpr (kMixed) {
-            // lambda*_i's bound from the rate kernel, the logarithm, quotient and roundings
-            eta_lam = ebin_err(reinterpret_cast<const float*>(A.contrib)[4 * r + 3]) + 8.f * u;
-            const float dd = (float)(dtw - dt_exe);
-            replay = !(fabsf(dd) > 1.5f * eta_lam * (float)dtw * 1.0001f + 1e-14f * (float)dt_exe);
-          } else {
-            if (fabs(dtw - dt_exe) < 1e-10 * dt_exe) nn++;
-          }
-          ev = !(dtw > dt_exe) && !replay;
-        }
-      }
-    }
-    unsigned emask = __ballot_sync(FULLM, ev);
-    // per-lane fixed quantities of every particle of the chunk (lane = particle)
-    Fixed<T> fx;
-    double s_i = 1.0, m_i = 1.0;
-    if (valid && ev) {
-      const InstDev& P = A.P[b];
-      const Snap64 sn = A.snap64[r];
-      s_i = sn.s;
-      m_i = sn.m;
-      if constexpr (!kMixed) {
-        Gas g = gas_of(P, A.pos64[r]);
-        fx = make_fixed<double>(P, g, A.V[r], A.Mr[r], A.K);
-      } else if (lam * dt_exe > 32.0) {
-        // many events expected: FP64-accurate gas constants keep every bound of the
-        // particle's many decisions near the FP32 rounding
-        Gas g = gas_of(P, A.pos64[r]);
-        fx = fixed_f32_of(make_fixed<double>(P, g, A.V[r], A.Mr[r], A.K), A.pref32[r]);
+  int b = 0, ub = 0;   // instance and unit (spatial group) of the particle
+  double lam = 0.0, dtw = 0.0, us = 0.0, dt_exe = 0.0;
+  unsigned ival = 0, i_loc = 0, key0 = 0, key1 = 0, usw0 = 0, usw1 = 0;
+  bool ev = false, replay = false;
+  int nn = 0;
+  float eta_lam = 0.0f;   // mixed form: error bound of the first waiting time
+  if (valid) {
+    b = inst_of(A.off, A.n_inst, r);
+    ub = A.unit_r ? A.unit_r[r] : b;
+    dt_exe = A.st[ub].dt_exe;     // 0 for a group idle in this round: no event
+    // a heavy particle of a chunk is sampled by its own warp (the list of k_heavy)
+    if (!one && A.heavy_n && A.lam[r] * dt_exe > kHeavy) valid = false;
+  }
+  if (valid) {
+    const InstDev& P = A.P[b];
+    ival = (unsigned)A.st[ub].interval_cur;
+    key0 = P.key0;
+    key1 = P.key1;
+    i_loc = (unsigned)(A.perm[r] - P.off);
+    if (dt_exe > 0.0) {   // else idle: a held instance or a spatial group between rounds
+      if (fresh) {
+        double v3[3];
+        int fb;
+        float e3;
+        rate_particle<double>(A, P, r, lam, v3, fb, e3);
       } else {
-        fx = make_fixed_f32(P, A.gx[r], A.pref32[r]);
+        lam = A.lam[r];
       }
-    } else {
-      fx = Fixed<T>{};
-      fx.mode = 0;
-    }
-    int my_e = 0;
-    unsigned my_h = 0u;
-    double my_MJ = 0.0, my_s = s_i;
-    while (emask) {
-      const int p = __ffs(emask) - 1;
-      emask &= emask - 1;
-      const long long rp = __shfl_sync(FULLM, r, p);
-      const Fixed<T> f = shfl_fixed<T>(fx, p);
-      double s = __shfl_sync(FULLM, s_i, p), m = __shfl_sync(FULLM, m_i, p);
-      double t = __shfl_sync(FULLM, dtw, p);
-      double u_s = __shfl_sync(FULLM, us, p);
-      unsigned uw0 = __shfl_sync(FULLM, usw0, p), uw1 = __shfl_sync(FULLM, usw1, p);   // words of U_s
-      const double dte = __shfl_sync(FULLM, dt_exe, p);
-      const unsigned iv = __shfl_sync(FULLM, ival, p), il = __shfl_sync(FULLM, i_loc, p);
-      const unsigned k0 = __shfl_sync(FULLM, key0, p), k1 = __shfl_sync(FULLM, key1, p);
-      const int bp = __shfl_sync(FULLM, b, p);
-      const int up = __shfl_sync(FULLM, ub, p);
-      // mixed form: FP32 copies of per-particle constants for the per-event FP32 steps
-      const float k6f = (float)f.k6, preff = f.prefT;
-      float sf = (float)s;      // mixed form: the FP32 diameter the pair rates use
-      bool s_stale = false;     // mixed form: s lags m after a sticking or erosion event
-      // mixed form: error bound of the time sum t (FP32; the sum itself is FP64)
-      float terr = (float)t * __shfl_sync(FULLM, eta_lam, p);
-      const float dtef = (float)dte;
-      bool unc = false;         // mixed form: an uncertified decision (warp-uniform)
-      int e = 0, near_ch = 0, near_u = 0;   // per-lane ties, warp-uniform ties
-      unsigned h = 0u;
-      T J = (T)0;
-      T c0[S], c1[S];
-      int jr[S];
-      PairOut<T> po[S];
-      Query<T> q = live_query<T>(f, s, m);
-      double v = lane_channels<T, S>(A, q, m, rp, lane, c0, c1, jr, po);
-      double incl = 0.0, tot = 0.0;
-      float inclf = 0.0f, totf = 0.0f, eta = 0.0f;
-      bool bad64 = false;       // mixed form: a pair's decision is uncertified at this state
-      // certification (mixed) or near ties (FP64) of the pairs' threshold decisions
-      // mixed form: eta bounds the relative error of the FP32 prefix and of lambda*_i -- the
-      // pairs' absolute bounds derr c summed over the warp, over lambda*, plus the sums'
-      // rounding
-      auto pairs_checked = [&]() {
-        int bad = 0;
-        float de = 0.0f, cs = 0.0f;
-#pragma unroll
-        for (int t2 = 0; t2 < S; ++t2)
-          if (jr[t2] >= 0) {
-            bad += po[t2].cert ? 0 : 1;
-            if constexpr (kMixed) {
-              de = fmaf((float)po[t2].derr, (float)(c0[t2] + c1[t2]), de);
-              cs += (float)(c0[t2] + c1[t2]);
-            }
-          }
+      U4 w = philox(i_loc, ival, 0u, 0u, key0, key1);
+      usw0 = w.z;
+      usw1 = w.w;
+      if constexpr (!kMixed) us = u01(w.z, w.w);
+      if (lam > 0.0 && isfinite(lam)) {
+        dtw = waiting_time<T>(w.x, w.y, lam);
         if constexpr (kMixed) {
-          bad64 = __any_sync(FULLM, bad != 0);
-          de = warp_sumf(de);
-          cs = warp_sumf(cs);
-          eta = (cs > 0.0f ? __fdividef(de, cs) * 1.0001f : 0.0f) + (2.f * S + 7.f) * u;
+          // lambda*_i's bound from the rate kernel, the logarithm, quotient and roundings
+          eta_lam = ebin_err(reinterpret_cast<const float*>(A.contrib)[4 * r + 3]) + 8.f * u;
+          const float dd = (float)(dtw - dt_exe);
+          replay = !(fabsf(dd) > 1.5f * eta_lam * (float)dtw * 1.0001f + 1e-14f * (float)dt_exe);
         } else {
-          near_ch += bad;
+          if (fabs(dtw - dt_exe) < 1e-10 * dt_exe) nn++;
         }
-      };
-      // the particle's FP64 diameter (mixed form: formed from the FP64 mass when it lags)
-      auto s_exact = [&]() { return (kMixed && s_stale) ? diameter_of<T>(cube_of<T>(f, m)) : s; };
+        ev = !(dtw > dt_exe) && !replay;
+      }
+    }
+  }
+  unsigned emask = __ballot_sync(FULLM, ev);
+  // per-lane fixed quantities of every particle of the chunk (lane = particle)
+  Fixed<T> fx;
+  double s_i = 1.0, m_i = 1.0;
+  if (valid && ev) {
+    const InstDev& P = A.P[b];
+    const Snap64 sn = A.snap64[r];
+    s_i = sn.s;
+    m_i = sn.m;
+    if constexpr (!kMixed) {
+      Gas g = gas_of(P, A.pos64[r]);
+      fx = make_fixed<double>(P, g, A.V[r], A.Mr[r], A.K);
+    } else if (lam * dt_exe > 32.0) {
+      // many events expected: FP64-accurate gas constants keep every bound of the
+      // particle's many decisions near the FP32 rounding
+      Gas g = gas_of(P, A.pos64[r]);
+      fx = fixed_f32_of(make_fixed<double>(P, g, A.V[r], A.Mr[r], A.K), A.pref32[r]);
+    } else {
+      fx = make_fixed_f32(P, A.gx[r], A.pref32[r]);
+    }
+  } else {
+    fx = Fixed<T>{};
+    fx.mode = 0;
+  }
+  int my_e = 0;
+  unsigned my_h = 0u;
+  double my_MJ = 0.0, my_s = s_i;
+  while (emask) {
+    const int p = __ffs(emask) - 1;
+    emask &= emask - 1;
+    const long long rp = __shfl_sync(FULLM, r, p);
+    const Fixed<T> f = shfl_fixed<T>(fx, p);
+    double s = __shfl_sync(FULLM, s_i, p), m = __shfl_sync(FULLM, m_i, p);
+    double t = __shfl_sync(FULLM, dtw, p);
+    double u_s = __shfl_sync(FULLM, us, p);
+    unsigned uw0 = __shfl_sync(FULLM, usw0, p), uw1 = __shfl_sync(FULLM, usw1, p);   // words of U_s
+    const double dte = __shfl_sync(FULLM, dt_exe, p);
+    const unsigned iv = __shfl_sync(FULLM, ival, p), il = __shfl_sync(FULLM, i_loc, p);
+    const unsigned k0 = __shfl_sync(FULLM, key0, p), k1 = __shfl_sync(FULLM, key1, p);
+    const int bp = __shfl_sync(FULLM, b, p);
+    const int up = __shfl_sync(FULLM, ub, p);
+    // mixed form: FP32 copies of per-particle constants for the per-event FP32 steps
+    const float k6f = (float)f.k6, preff = f.prefT;
+    float sf = (float)s;      // mixed form: the FP32 diameter the pair rates use
+    bool s_stale = false;     // mixed form: s lags m after a sticking or erosion event
+    // mixed form: error bound of the time sum t (FP32; the sum itself is FP64)
+    float terr = (float)t * __shfl_sync(FULLM, eta_lam, p);
+    const float dtef = (float)dte;
+    bool unc = false;         // mixed form: an uncertified decision (warp-uniform)
+    int e = 0, near_ch = 0, near_u = 0;   // per-lane ties, warp-uniform ties
+    unsigned h = 0u;
+    T J = (T)0;
+    T c0[S], c1[S];
+    int jr[S];
+    PairOut<T> po[S];
+    Query<T> q = live_query<T>(f, s, m);
+    double v = lane_channels<T, S>(A, q, m, rp, lane, c0, c1, jr, po);
+    double incl = 0.0, tot = 0.0;
+    float inclf = 0.0f, totf = 0.0f, eta = 0.0f;
+    bool bad64 = false;       // mixed form: a pair's decision is uncertified at this state
+    // certification (mixed) or near ties (FP64) of the pairs' threshold decisions
+    // mixed form: eta bounds the relative error of the FP32 prefix and of lambda*_i -- the
+    // pairs' absolute bounds derr c summed over the warp, over lambda*, plus the sums'
+    // rounding
+    auto pairs_checked = [&]() {
+      int bad = 0;
+      float de = 0.0f, cs = 0.0f;
+#pragma unroll
+      for (int t2 = 0; t2 < S; ++t2)
+        if (jr[t2] >= 0) {
+          bad += po[t2].cert ? 0 : 1;
+          if constexpr (kMixed) {
+            de = fmaf((float)po[t2].derr, (float)(c0[t2] + c1[t2]), de);
+            cs += (float)(c0[t2] + c1[t2]);
+          }
+        }
+      if constexpr (kMixed) {
+        bad64 = __any_sync(FULLM, bad != 0);
+        de = warp_sumf(de);
+        cs = warp_sumf(cs);
+        eta = (cs > 0.0f ? __fdividef(de, cs) * 1.0001f : 0.0f) + (2.f * S + 7.f) * u;
+      } else {
+        near_ch += bad;
+      }
+    };
+    // the particle's FP64 diameter (mixed form: formed from the FP64 mass when it lags)
+    auto s_exact = [&]() { return (kMixed && s_stale) ? diameter_of<T>(cube_of<T>(f, m)) : s; };
+    pairs_checked();
+    if constexpr (!kMixed) {
+      incl = warp_incl_scan(v, lane);
+      tot = __shfl_sync(FULLM, incl, 31);
+    } else {
+      inclf = warp_incl_scanf(lane_sumf<S>(c0, c1, jr), lane);
+      totf = __shfl_sync(FULLM, inclf, 31);
+    }
+    for (;;) {
+      if (unc) break;
+      // partner channel: the first cumulative rate above U_s lambda*
+      int chosen = INT_MAX, j = -1, outcome = 0;
+      T ncoll_t = (T)1, psi_t = (T)0;
+      bool from_po = true;
+      if constexpr (kMixed) {
+        bool ok = false;
+        if (!bad64) {
+          const float tf = fmaf((float)(uw0 >> 6), 0x1p26f, (float)(uw1 >> 6) + 0.5f) * 0x1p-52f * totf;
+          const float mg = 1.5f * (2.f * eta + 3.f * u) * totf;
+          float cumf = __shfl_up_sync(FULLM, inclf, 1);
+          if (lane == 0) cumf = 0.0f;
+          int sel = INT_MAX;
+          float blo = 0.0f, bhi = 0.0f;
+#pragma unroll
+          for (int t2 = 0; t2 < S; ++t2) {
+            const int k = lane * S + t2;
+            if (jr[t2] < 0) continue;
+            const float b0 = cumf;
+            cumf += c0[t2];
+            if (c0[t2] > 0.0f && sel == INT_MAX && tf < cumf) { sel = 2 * k; blo = b0; bhi = cumf; }
+            const float b1 = cumf;
+            cumf += c1[t2];
+            if (c1[t2] > 0.0f && sel == INT_MAX && tf < cumf) { sel = 2 * k + 1; blo = b1; bhi = cumf; }
+          }
+          chosen = sel;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) chosen = min(chosen, __shfl_xor_sync(FULLM, chosen, o));
+          if (chosen != INT_MAX) {
+            const int own = (chosen >> 1) / S;
+            const bool in = (bhi - tf > mg) && (blo == 0.0f || tf - blo > mg);
+            ok = __shfl_sync(FULLM, in, own);
+          }
+        }
+        if (!ok) {
+          // the FP32 values cannot certify this choice: the FP64 form's choice at this state
+          const Fp64Pick pk = fp64_event<S>(A, rp, bp, s_exact(), m, uw0, uw1, true, lane);
+          near_u += pk.near;
+          chosen = pk.chosen;
+          j = pk.j;
+          outcome = pk.outcome;
+          ncoll_t = (T)pk.ncoll;
+          psi_t = (T)pk.psi;
+          from_po = false;
+        }
+      } else {
+        const double target = u_s * tot;
+        const double tie_ch = 1e-10 * tot;
+        double cum = __shfl_up_sync(FULLM, incl, 1);
+        if (lane == 0) cum = 0.0;
+        int sel = INT_MAX, lastnz = -1;
+#pragma unroll
+        for (int t2 = 0; t2 < S; ++t2) {
+          int k = lane * S + t2;
+          if (jr[t2] < 0) continue;
+          cum = __dadd_rn(cum, (double)c0[t2]);
+          if (c0[t2] > (T)0) {
+            lastnz = 2 * k;
+            if (fabs(target - cum) < tie_ch) near_ch++;
+            if (sel == INT_MAX && target < cum) sel = 2 * k;
+          }
+          cum = __dadd_rn(cum, (double)c1[t2]);
+          if (c1[t2] > (T)0) {
+            lastnz = 2 * k + 1;
+            if (fabs(target - cum) < tie_ch) near_ch++;
+            if (sel == INT_MAX && target < cum) sel = 2 * k + 1;
+          }
+        }
+        chosen = sel;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) chosen = min(chosen, __shfl_xor_sync(FULLM, chosen, o));
+        if (chosen == INT_MAX) {
+          int ln = lastnz;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) ln = max(ln, __shfl_xor_sync(FULLM, ln, o));
+          chosen = ln;
+          near_u++;
+        }
+      }
+      if (chosen < 0) break;
+      const int ch = chosen & 1;
+      if (from_po) {
+        // partner data and outcome from the owning lane
+        const int slot = chosen >> 1;
+        const int owner = slot / S, tsl = slot % S;
+        int jo = jr[0], oc = po[0].outcome;
+        T nco = po[0].ncoll, pso = po[0].psi;
+#pragma unroll
+        for (int t2 = 1; t2 < S; ++t2)
+          if (t2 == tsl) { jo = jr[t2]; oc = po[t2].outcome; nco = po[t2].ncoll; pso = po[t2].psi; }
+        j = __shfl_sync(FULLM, jo, owner);
+        outcome = __shfl_sync(FULLM, oc, owner);
+        ncoll_t = __shfl_sync(FULLM, nco, owner);
+        psi_t = __shfl_sync(FULLM, pso, owner);
+      }
+      const double ncoll = (double)ncoll_t;
+      const Snap64 pj = A.snap64[j];
+      double m_new, s_new = s;
+      float Jf = 0.0f;   // mixed form: |ln s'/s| of the event from the pair's FP32 psi
+      if (outcome == 0) {
+        if constexpr (!kMixed) m_new = m + ncoll * pj.m; else m_new = fma(ncoll, pj.m, m);
+        if constexpr (!kMixed) {
+          s_new = diameter_of<T>(cube_of<T>(f, m_new));
+        } else {
+          // the pair rates only need the FP32 diameter; the FP64-accurate one is formed
+          // when it is needed (a fragmentation, an FP64 decision, the particle's end)
+          sf = cbrtf((float)m_new * k6f);
+          s_stale = true;
+          Jf = log1pf((float)ncoll_t * (float)psi_t) * (1.0f / 3.0f);
+        }
+      } else if (outcome == 1 && ch == 0) {
+        if constexpr (!kMixed) m_new = m - ncoll * pj.m; else m_new = fma(-ncoll, pj.m, m);
+        if constexpr (!kMixed) {
+          s_new = diameter_of<T>(cube_of<T>(f, m_new));
+        } else {
+          sf = cbrtf((float)m_new * k6f);
+          s_stale = true;
+          Jf = fabsf(log1pf(-(float)ncoll_t * (float)psi_t)) * (1.0f / 3.0f);
+        }
+      } else if (outcome == 1) {
+        m_new = pj.m;
+        s_new = pj.s;
+        if constexpr (kMixed) { sf = (float)s_new; s_stale = false; Jf = fabsf(logf((float)psi_t)) * (1.0f / 3.0f); }
+      } else {
+        // fragmentation (Eq. frag): the size from the draw in FP64 in both forms
+        U4 w2 = philox(il, iv, (unsigned)e, 1u, k0, k1);
+        if constexpr (kMixed) {
+          if (s_stale) { s = diameter_of<T>(cube_of<T>(f, m)); s_stale = false; }
+        }
+        const double U = u01(w2.x, w2.y);
+        const double a = sqrt(f.s_min), bq = sqrt(s);
+        const double xr = a + U * (bq - a);
+        s_new = xr * xr;
+        if constexpr (!kMixed) m_new = kPi * f.rho_s * s_new * s_new * s_new / 6.0;
+        else m_new = f.mk * (s_new * s_new * s_new);
+        if constexpr (kMixed) { sf = (float)s_new; Jf = 2.0f * fabsf(logf((float)(xr / bq))); }
+      }
+      if constexpr (!kMixed) J += fabs(log(s_new / s));
+      else J += Jf;
+      s = s_new;
+      m = m_new;
+      h = h * 31u + (unsigned)(chosen + 1);
+      ++e;
+      if (e >= A.max_events) { if (lane == 0) set_status(&A.st[up], GD_ST_EVENT_CAP); break; }
+      if constexpr (!kMixed) q = live_query<T>(f, s, m);
+      else q = live_query_f(f, sf, (float)m);
+      v = lane_channels<T, S>(A, q, m, rp, lane, c0, c1, jr, po);
       pairs_checked();
       if constexpr (!kMixed) {
         incl = warp_incl_scan(v, lane);
@@ -1207,244 +1349,129 @@ __global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
         inclf = warp_incl_scanf(lane_sumf<S>(c0, c1, jr), lane);
         totf = __shfl_sync(FULLM, inclf, 31);
       }
-      for (;;) {
-        if (unc) break;
-        // partner channel: the first cumulative rate above U_s lambda*
-        int chosen = INT_MAX, j = -1, outcome = 0;
-        T ncoll_t = (T)1, psi_t = (T)0;
-        bool from_po = true;
-        if constexpr (kMixed) {
-          bool ok = false;
-          if (!bad64) {
-            const float tf = fmaf((float)(uw0 >> 6), 0x1p26f, (float)(uw1 >> 6) + 0.5f) * 0x1p-52f * totf;
-            const float mg = 1.5f * (2.f * eta + 3.f * u) * totf;
-            float cumf = __shfl_up_sync(FULLM, inclf, 1);
-            if (lane == 0) cumf = 0.0f;
-            int sel = INT_MAX;
-            float blo = 0.0f, bhi = 0.0f;
-#pragma unroll
-            for (int t2 = 0; t2 < S; ++t2) {
-              const int k = lane * S + t2;
-              if (jr[t2] < 0) continue;
-              const float b0 = cumf;
-              cumf += c0[t2];
-              if (c0[t2] > 0.0f && sel == INT_MAX && tf < cumf) { sel = 2 * k; blo = b0; bhi = cumf; }
-              const float b1 = cumf;
-              cumf += c1[t2];
-              if (c1[t2] > 0.0f && sel == INT_MAX && tf < cumf) { sel = 2 * k + 1; blo = b1; bhi = cumf; }
-            }
-            chosen = sel;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) chosen = min(chosen, __shfl_xor_sync(FULLM, chosen, o));
-            if (chosen != INT_MAX) {
-              const int own = (chosen >> 1) / S;
-              const bool in = (bhi - tf > mg) && (blo == 0.0f || tf - blo > mg);
-              ok = __shfl_sync(FULLM, in, own);
-            }
-          }
-          if (!ok) {
-            // the FP32 values cannot certify this choice: the FP64 form's choice at this state
-            const Fp64Pick pk = fp64_event<S>(A, rp, bp, s_exact(), m, uw0, uw1, true, lane);
-            near_u += pk.near;
-            chosen = pk.chosen;
-            j = pk.j;
-            outcome = pk.outcome;
-            ncoll_t = (T)pk.ncoll;
-            psi_t = (T)pk.psi;
-            from_po = false;
-          }
-        } else {
-          const double target = u_s * tot;
-          const double tie_ch = 1e-10 * tot;
-          double cum = __shfl_up_sync(FULLM, incl, 1);
-          if (lane == 0) cum = 0.0;
-          int sel = INT_MAX, lastnz = -1;
-#pragma unroll
-          for (int t2 = 0; t2 < S; ++t2) {
-            int k = lane * S + t2;
-            if (jr[t2] < 0) continue;
-            cum = __dadd_rn(cum, (double)c0[t2]);
-            if (c0[t2] > (T)0) {
-              lastnz = 2 * k;
-              if (fabs(target - cum) < tie_ch) near_ch++;
-              if (sel == INT_MAX && target < cum) sel = 2 * k;
-            }
-            cum = __dadd_rn(cum, (double)c1[t2]);
-            if (c1[t2] > (T)0) {
-              lastnz = 2 * k + 1;
-              if (fabs(target - cum) < tie_ch) near_ch++;
-              if (sel == INT_MAX && target < cum) sel = 2 * k + 1;
-            }
-          }
-          chosen = sel;
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) chosen = min(chosen, __shfl_xor_sync(FULLM, chosen, o));
-          if (chosen == INT_MAX) {
-            int ln = lastnz;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) ln = max(ln, __shfl_xor_sync(FULLM, ln, o));
-            chosen = ln;
-            near_u++;
-          }
-        }
-        if (chosen < 0) break;
-        const int ch = chosen & 1;
-        if (from_po) {
-          // partner data and outcome from the owning lane
-          const int slot = chosen >> 1;
-          const int owner = slot / S, tsl = slot % S;
-          int jo = jr[0], oc = po[0].outcome;
-          T nco = po[0].ncoll, pso = po[0].psi;
-#pragma unroll
-          for (int t2 = 1; t2 < S; ++t2)
-            if (t2 == tsl) { jo = jr[t2]; oc = po[t2].outcome; nco = po[t2].ncoll; pso = po[t2].psi; }
-          j = __shfl_sync(FULLM, jo, owner);
-          outcome = __shfl_sync(FULLM, oc, owner);
-          ncoll_t = __shfl_sync(FULLM, nco, owner);
-          psi_t = __shfl_sync(FULLM, pso, owner);
-        }
-        const double ncoll = (double)ncoll_t;
-        const Snap64 pj = A.snap64[j];
-        double m_new, s_new = s;
-        float Jf = 0.0f;   // mixed form: |ln s'/s| of the event from the pair's FP32 psi
-        if (outcome == 0) {
-          if constexpr (!kMixed) m_new = m + ncoll * pj.m; else m_new = fma(ncoll, pj.m, m);
-          if constexpr (!kMixed) {
-            s_new = diameter_of<T>(cube_of<T>(f, m_new));
-          } else {
-            // the pair rates only need the FP32 diameter; the FP64-accurate one is formed
-            // when it is needed (a fragmentation, an FP64 decision, the particle's end)
-            sf = cbrtf((float)m_new * k6f);
-            s_stale = true;
-            Jf = log1pf((float)ncoll_t * (float)psi_t) * (1.0f / 3.0f);
-          }
-        } else if (outcome == 1 && ch == 0) {
-          if constexpr (!kMixed) m_new = m - ncoll * pj.m; else m_new = fma(-ncoll, pj.m, m);
-          if constexpr (!kMixed) {
-            s_new = diameter_of<T>(cube_of<T>(f, m_new));
-          } else {
-            sf = cbrtf((float)m_new * k6f);
-            s_stale = true;
-            Jf = fabsf(log1pf(-(float)ncoll_t * (float)psi_t)) * (1.0f / 3.0f);
-          }
-        } else if (outcome == 1) {
-          m_new = pj.m;
-          s_new = pj.s;
-          if constexpr (kMixed) { sf = (float)s_new; s_stale = false; Jf = fabsf(logf((float)psi_t)) * (1.0f / 3.0f); }
-        } else {
-          // fragmentation (Eq. frag): the size from the draw in FP64 in both forms
-          U4 w2 = philox(il, iv, (unsigned)e, 1u, k0, k1);
-          if constexpr (kMixed) {
-            if (s_stale) { s = diameter_of<T>(cube_of<T>(f, m)); s_stale = false; }
-          }
-          const double U = u01(w2.x, w2.y);
-          const double a = sqrt(f.s_min), bq = sqrt(s);
-          const double xr = a + U * (bq - a);
-          s_new = xr * xr;
-          if constexpr (!kMixed) m_new = kPi * f.rho_s * s_new * s_new * s_new / 6.0;
-          else m_new = f.mk * (s_new * s_new * s_new);
-          if constexpr (kMixed) { sf = (float)s_new; Jf = 2.0f * fabsf(logf((float)(xr / bq))); }
-        }
-        if constexpr (!kMixed) J += fabs(log(s_new / s));
-        else J += Jf;
-        s = s_new;
-        m = m_new;
-        h = h * 31u + (unsigned)(chosen + 1);
-        ++e;
-        if (e >= A.max_events) { if (lane == 0) set_status(&A.st[up], GD_ST_EVENT_CAP); break; }
-        if constexpr (!kMixed) q = live_query<T>(f, s, m);
-        else q = live_query_f(f, sf, (float)m);
-        v = lane_channels<T, S>(A, q, m, rp, lane, c0, c1, jr, po);
-        pairs_checked();
-        if constexpr (!kMixed) {
-          incl = warp_incl_scan(v, lane);
-          tot = __shfl_sync(FULLM, incl, 31);
-        } else {
-          inclf = warp_incl_scanf(lane_sumf<S>(c0, c1, jr), lane);
-          totf = __shfl_sync(FULLM, inclf, 31);
-        }
-        double lam_now = 0.0;   // FP64 lambda*_i (FP64 form; mixed form at an uncertified state)
-        if constexpr (!kMixed) {
-          lam_now = f.pref * tot;
-        } else if (bad64) {
-          const Fp64Pick pk = fp64_event<S>(A, rp, bp, s_exact(), m, 0u, 0u, false, lane);
-          near_u += pk.near;
-          lam_now = pk.lam;
-        }
-        if (!kMixed || bad64) {
-          if (!(lam_now > 0.0) || !isfinite(lam_now)) {
-            if (lane == 0 && !(lam_now == 0.0)) set_status(&A.st[up], GD_ST_NONFINITE);
-            break;
-          }
-        } else if (!(totf > 0.0f) || !isfinite(totf)) {
-          if (totf == 0.0f) break;
-          unc = true;
+      double lam_now = 0.0;   // FP64 lambda*_i (FP64 form; mixed form at an uncertified state)
+      if constexpr (!kMixed) {
+        lam_now = f.pref * tot;
+      } else if (bad64) {
+        const Fp64Pick pk = fp64_event<S>(A, rp, bp, s_exact(), m, 0u, 0u, false, lane);
+        near_u += pk.near;
+        lam_now = pk.lam;
+      }
+      if (!kMixed || bad64) {
+        if (!(lam_now > 0.0) || !isfinite(lam_now)) {
+          if (lane == 0 && !(lam_now == 0.0)) set_status(&A.st[up], GD_ST_NONFINITE);
           break;
         }
-        U4 w = philox(il, iv, (unsigned)e, 0u, k0, k1);
-        uw0 = w.z;
-        uw1 = w.w;
-        if constexpr (!kMixed) u_s = u01(w.z, w.w);
-        double dt2;
-        if constexpr (!kMixed) {
-          dt2 = waiting_time<T>(w.x, w.y, lam_now);
-          if (fabs((t + dt2) - dte) < 1e-10 * dte) near_u++;
-        } else {
-          if (bad64) {
-            dt2 = waiting_time<double>(w.x, w.y, lam_now);   // exact up to FP64 rounding
-          } else {
-            // lambda* = pref * totf in FP32 when it is in range (the FP32 wait is formed
-            // from it anyway), else in FP64
-            const float lf = preff * totf;
-            const float nl = neg_log_u01_f32(w.x, w.y);
-            float d2;
-            if (lf > 1e-30f && lf < 1e30f) { d2 = __fdividef(nl, lf); dt2 = (double)d2; }
-            else { dt2 = (double)nl / (f.pref * (double)totf); d2 = (float)dt2; }
-            terr = fmaf(d2, (eta + 8.f * u) * 1.0001f, terr);
-          }
-          // the time sum's decision: certified, or the particle is replayed in FP64 (one FP64
-          // difference, compared in FP32 with a margin far above its rounding)
-          const double tn = t + dt2;
-          const float dd = (float)(tn - dte);
-          if (!(fabsf(dd) > 1.5f * terr * 1.0001f + 1e-14f * dtef)) { unc = true; break; }
-          if (dd > 0.0f) break;
-          t = tn;
-          continue;
-        }
-        if (t + dt2 > dte) break;
-        t = t + dt2;
+      } else if (!(totf > 0.0f) || !isfinite(totf)) {
+        if (totf == 0.0f) break;
+        unc = true;
+        break;
       }
-      if constexpr (kMixed) {
-        if (!unc && s_stale) s = diameter_of<T>(cube_of<T>(f, m));
-      }
-      int near_tot = near_ch;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) near_tot += __shfl_xor_sync(FULLM, near_tot, o);
-      near_tot += near_u;
-      if (lane == p) {
-        replay = unc;
-        my_e = e; my_h = h; nn += near_tot; my_MJ = f.M * (double)J; my_s = s;
-      }
-    }
-    if (valid) {
-      if (replay) {
-        A.redo[atomicAdd(A.redo_n, 1ull)] = (int)r;   // the FP64 replay samples it
-        atomicAdd((unsigned long long*)&A.st[ub].sample_redo, 1ull);
+      U4 w = philox(il, iv, (unsigned)e, 0u, k0, k1);
+      uw0 = w.z;
+      uw1 = w.w;
+      if constexpr (!kMixed) u_s = u01(w.z, w.w);
+      double dt2;
+      if constexpr (!kMixed) {
+        dt2 = waiting_time<T>(w.x, w.y, lam_now);
+        if (fabs((t + dt2) - dte) < 1e-10 * dte) near_u++;
       } else {
-        const int ci = A.perm[r];
-        if (my_e > 0) {
-          A.s_out[ci] = my_s;
-          atomicAdd((unsigned long long*)&A.st[ub].events, (unsigned long long)my_e);
+        if (bad64) {
+          dt2 = waiting_time<double>(w.x, w.y, lam_now);   // exact up to FP64 rounding
+        } else {
+          // lambda* = pref * totf in FP32 when it is in range (the FP32 wait is formed
+          // from it anyway), else in FP64
+          const float lf = preff * totf;
+          const float nl = neg_log_u01_f32(w.x, w.y);
+          float d2;
+          if (lf > 1e-30f && lf < 1e30f) { d2 = __fdividef(nl, lf); dt2 = (double)d2; }
+          else { dt2 = (double)nl / (f.pref * (double)totf); d2 = (float)dt2; }
+          terr = fmaf(d2, (eta + 8.f * u) * 1.0001f, terr);
         }
-        A.MJ[ci] = my_MJ;
-        if (nn) atomicAdd((unsigned long long*)&A.st[ub].near_draw, (unsigned long long)nn);
-        if (A.ev_count) {
-          A.ev_count[ci] = my_e;
-          A.ev_hash[ci] = my_h;
-          A.near_out[ci] = nn;
-        }
+        // the time sum's decision: certified, or the particle is replayed in FP64 (one FP64
+        // difference, compared in FP32 with a margin far above its rounding)
+        const double tn = t + dt2;
+        const float dd = (float)(tn - dte);
+        if (!(fabsf(dd) > 1.5f * terr * 1.0001f + 1e-14f * dtef)) { unc = true; break; }
+        if (dd > 0.0f) break;
+        t = tn;
+        continue;
+      }
+      if (t + dt2 > dte) break;
+      t = t + dt2;
+    }
+    if constexpr (kMixed) {
+      if (!unc && s_stale) s = diameter_of<T>(cube_of<T>(f, m));
+    }
+    int near_tot = near_ch;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) near_tot += __shfl_xor_sync(FULLM, near_tot, o);
+    near_tot += near_u;
+    if (lane == p) {
+      replay = unc;
+      my_e = e; my_h = h; nn += near_tot; my_MJ = f.M * (double)J; my_s = s;
+    }
+  }
+  if constexpr (kMixed) {
+    // the particles with an uncertified decision: replayed at once by the FP64 form (the
+    // whole warp, one particle after another), which writes their results
+    unsigned rep = __ballot_sync(FULLM, valid && replay);
+    if (valid && replay) atomicAdd((unsigned long long*)&A.st[ub].sample_redo, 1ull);
+    while (rep) {
+      const int p = __ffs(rep) - 1;
+      rep &= rep - 1u;
+      replay64<S>(A, __shfl_sync(FULLM, r, p), lane);
+    }
+  }
+  if (valid) {
+    if (replay) {
+    } else {
+      const int ci = A.perm[r];
+      if (my_e > 0) {
+        A.s_out[ci] = my_s;
+        atomicAdd((unsigned long long*)&A.st[ub].events, (unsigned long long)my_e);
+      }
+      A.MJ[ci] = my_MJ;
+      if (nn) atomicAdd((unsigned long long*)&A.st[ub].near_draw, (unsigned long long)nn);
+      if (A.ev_count) {
+        A.ev_count[ci] = my_e;
+        A.ev_hash[ci] = my_h;
+        A.near_out[ci] = nn;
       }
     }
+  }
+}
+
+// The FP64 replay of one particle the mixed pass could not certify: the FP64 form's sampler
+// for that particle alone (its lambda*_i in FP64, every decision in FP64), run by the whole
+// warp.  Kept out of line: rare, and its registers stay apart from the mixed pass's.
+template <int S>
+__device__ __noinline__ void replay64(McArgs A, long long r, int lane) {
+  sample_item<double, S>(A, lane, true, true, r, lane == 0);
+}
+
+template <typename T, int S>
+__global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
+  const int lane = threadIdx.x & 31;
+  // spatial groups: the round's ranks only (A.act), 32 to a chunk like the full range
+  const long long total = A.act ? (long long)*A.act_n : A.N;
+  // work items from one counter: first the heavy particles one per warp, then chunks of 32
+  // ranks without them
+  const long long n_heavy = A.heavy_n ? (long long)*A.heavy_n : 0;
+  const long long n_items = n_heavy + (total + 31) / 32;
+  auto next_item = [&]() {
+    unsigned long long c = 0;
+    if (lane == 0) c = atomicAdd(A.work, 1ull);
+    return (long long)__shfl_sync(FULLM, c, 0);
+  };
+  for (long long item = next_item(); item < n_items; item = next_item()) {
+    const bool one = item < n_heavy;   // one particle for the whole warp
+    const long long base = one ? 0 : (item - n_heavy) * 32;
+    const bool valid = one ? lane == 0 : base + lane < total;
+    const long long r = !valid ? 0
+                        : one ? (long long)A.heavy[item]
+                        : A.act ? (long long)A.act[base + lane] : base + lane;
+    sample_item<T, S>(A, lane, one, false, r, valid);
   }
 }
 
@@ -1637,18 +1664,6 @@ static void sample_launch(gd_ctx* c, const McArgs& A) {
   if (blocks > (chunks + 1) / 2) blocks = (chunks + 1) / 2;
   if (blocks < 1) blocks = 1;
   k_sample<T, S><<<(int)blocks, 64, 0, c->stream>>>(A);
-  if (sizeof(T) == 4) {
-    // the FP64 replay of the particles the mixed pass could not certify (counter 6 lists
-    // them, counter 7 hands out their chunks); its grid does not depend on their number
-    McArgs B = A;
-    B.list = c->d_redo;
-    B.list_n = c->d_counters + 6;
-    B.work = c->d_counters + 7;
-    B.heavy = nullptr;
-    B.heavy_n = nullptr;
-    k_sample<double, S><<<c->num_sms * 4, 64, 0, c->stream>>>(B);
-    c->launches += 1;
-  }
 }
 
 template <typename T>
@@ -1662,10 +1677,6 @@ static void sample_t(gd_ctx* c, McArgs& A) {
   c->launches += 1;
   A.heavy = c->d_heavy;
   A.heavy_n = hn;
-  if (sizeof(T) == 4) {
-    A.redo_n = c->d_counters + 6;
-    cudaMemsetAsync(c->d_counters + 6, 0, 2 * sizeof(unsigned long long), c->stream);
-  }
   cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long), c->stream);
   switch (S) {
     case 1: sample_launch<T, 1>(c, A); break;
