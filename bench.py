@@ -121,6 +121,16 @@ TRAFFIC = {
 }
 
 
+# Instructions of one launch at full size, per particle, from an ncu capture of the bench
+# command (smsp__inst_executed.sum: warp instructions issued; sm__inst_executed_pipe_fp64.sum:
+# warp instructions on the FP64 pipe), under the same source digest rule as TRAFFIC.
+INST_CSRC_SHA256 = None
+INST = {}
+
+# Issue rate of the SMs: 4 schedulers per SM, one warp instruction each per cycle.
+SCHEDULERS_PER_SM = 4
+
+
 KERNEL_SOURCES = ("gd_common.cuh", "gd_ctx.h", "gd_physics.cuh", "k_cells.cu", "k_knn.cu", "k_mc.cu")
 
 
@@ -373,7 +383,8 @@ def run_gpu(args, rank, world):
         pp = pipe_peaks()
     except Exception as e:          # reported, never fatal: the HBM roofline stands alone
         pp = {"error": str(e)}
-    return dict(N=N, K=K, cfg=cfg, mixed=mixed, fp64=fp64, times=times, hbm=hbm,
+    num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    return dict(N=N, K=K, cfg=cfg, mixed=mixed, fp64=fp64, times=times, hbm=hbm, num_sms=num_sms,
                 peak_kind=peak_kind, h2d=h2d, d2h=d2h, push=push, extras=extras, pipe_peaks=pp,
                 groups=groups)
 
@@ -668,15 +679,44 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-def roofline_of(km, kc, K, N, hbm, peak_kind, workload):
-    """HBM roofline of the kernel with the largest share of the step: algorithmic bytes per
-    launch over its mean launch time (CUDA events on the library stream)."""
+def kernel_inst(kernel, workload, n):
+    rec = INST.get(kernel)
+    if not rec or rec["workload"] != workload or csrc_digest() != INST_CSRC_SHA256:
+        return None
+    return {k: rec[k] * n for k in ("inst", "fp64_inst")}
+
+
+def roofline_of(km, kc, K, N, hbm, peak_kind, workload, pp=None, sm_mhz=None, num_sms=None):
+    """Roofline of the kernel with the largest share of the step, from its mean launch time
+    (CUDA events on the library stream).  HBM: algorithmic bytes per launch over that time.
+    None of these kernels is HBM-bound; with the launch's instruction counts recorded from
+    ncu (INST), the issue fraction (warp instructions over 4 per SM and cycle at the sampled
+    SM clock) is the bound reported, and the FP64-pipe fraction (FP64 warp instructions over
+    the measured FP64 FMA peak, 32 lanes x 2 flops each) beside it."""
     dom = max(("knn", "rates", "sample", "cells"), key=lambda k: km.get(k, 0.0))
     avg_s = km[dom] / max(1, kc[dom]) * 1e-3
     ach = algo_bytes(dom, K, True) * N / avg_s / 1e9
-    return {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-            "traffic": kernel_traffic(dom, workload, N), "peak_kind": peak_kind,
-            "algo_bytes_per_particle": algo_bytes(dom, K, True), "launch_ms": avg_s * 1e3}
+    hbm_rl = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+              "traffic": kernel_traffic(dom, workload, N), "peak_kind": peak_kind,
+              "algo_bytes_per_particle": algo_bytes(dom, K, True), "launch_ms": avg_s * 1e3}
+    ins = kernel_inst(dom, workload, N)
+    if not ins or not sm_mhz or not num_sms:
+        return hbm_rl
+    issue_peak = SCHEDULERS_PER_SM * num_sms * sm_mhz * 1e6
+    issue = ins["inst"] / avg_s
+    out = {"bound": "alu", "kernel": dom, "achieved": issue, "peak": issue_peak, "unit": "warp-instructions/s",
+           "frac": issue / issue_peak, "peak_kind": f"{SCHEDULERS_PER_SM} schedulers x {num_sms} SMs x "
+                                                    f"{sm_mhz:.0f} MHz (sampled)",
+           "traffic": hbm_rl["traffic"], "launch_ms": avg_s * 1e3,
+           "inst_per_particle": INST[dom]["inst"], "hbm": {k: hbm_rl[k] for k in
+                                                              ("achieved", "peak", "unit", "frac", "peak_kind",
+                                                               "algo_bytes_per_particle")}}
+    if pp and pp.get("fp64_tflops"):
+        fp64_peak = pp["fp64_tflops"] * 1e12 / 64.0       # FP64 FMA warp instructions per second
+        out["fp64_pipe"] = {"achieved": ins["fp64_inst"] / avg_s, "peak": fp64_peak,
+                            "unit": "FP64 warp-instructions/s", "frac": ins["fp64_inst"] / avg_s / fp64_peak,
+                            "peak_kind": "measured FP64 FMA chain (pipe_peaks)"}
+    return out
 
 
 def result_line(r, args, world):
@@ -699,7 +739,8 @@ def result_line(r, args, world):
         "knn_fp64_redo_per_step": r["mixed"].get("knn_redo", 0) / args.steps,
         "mixed_fp64_settled_per_step": {"rates": r["mixed"]["rate_redo"] / args.steps,
                                         "sampling": r["mixed"]["sample_redo"] / args.steps},
-        "roofline": roofline_of(km, kc, K, N, r["hbm"], r["peak_kind"], args.workload),
+        "roofline": roofline_of(km, kc, K, N, r["hbm"], r["peak_kind"], args.workload, r.get("pipe_peaks"),
+                                (r["mixed"]["clocks"] or {}).get("sm_mhz"), r.get("num_sms")),
         "kernels_ms_per_step": {k: v / args.steps for k, v in km.items() if v > 0 and k != "stats"},
         "gpu_launches": r["mixed"]["launches"],
         "clocks": r["mixed"]["clocks"],
@@ -737,7 +778,8 @@ def result_line(r, args, world):
                            cell_factor=x["mixed"]["cell_factor"], cell_xsplit=x["mixed"]["cell_xsplit"]),
             "kernels_ms_per_step": {k: w / sst for k, w in sp["kernel_ms"].items() if w > 0 and k != "stats"},
             "roofline": roofline_of(sp["kernel_ms"], sp["kernel_calls"], x["K"], x["N"], r["hbm"],
-                                    r["peak_kind"], name),
+                                    r["peak_kind"], name, r.get("pipe_peaks"),
+                                    (sp.get("clocks") or {}).get("sm_mhz"), r.get("num_sms")),
             "events_per_step": x["mixed"]["events"] / x["steps"],
             "mixed_fp64_settled_per_step": {"rates": x["mixed"]["rate_redo"] / x["steps"],
                                             "sampling": x["mixed"]["sample_redo"] / x["steps"]},

@@ -6,7 +6,7 @@
 // entry e at [(w * CAP + e) * 33 + l], so lanes touching the same entry, or one lane
 // walking its entries, never share a bank.
 //
-//  radius : 1.02 x the particle's d_i of the previous build when there is one (exact
+//  radius : 1.001 x the particle's d_i of the previous build when there is one (exact
 //           when the particles did not move; after a push the radius search corrects it),
 //           else an estimate from the particle count of the 27 cells around it;
 //  scan   : the cell rows that meet the ball are produced row by row and consumed
@@ -787,11 +787,13 @@ cudaError_t launch_knn(gd_ctx* c) {
   A.redo_n = c->d_counters + 1;
   A.list = nullptr;
   A.list_n = nullptr;
-  // static particles: d_i of the last build is exact and 1.02 d_i holds the K-1 others; after
-  // a move the K-th distance scatters around it, so the first radius aims at the middle of
-  // the buffer's range instead
+  // static particles: d_i of the last build is exact, and 1.001 d_i (with the search's own
+  // rounding margins) holds the K-1 others and little else: the scan's overscan shrinks with
+  // the ball (1.02 d_i took 6.11 ms per build of the 2^22 disk, 1.001 d_i 5.59 ms); after a
+  // move the K-th distance scatters around it, so the first radius aims at the middle of the
+  // buffer's range instead
   const bool wide = c->moved;
-  A.rfac = c->moved ? 1.045f : 1.02f;
+  A.rfac = c->moved ? 1.045f : 1.001f;
   c->moved = false;
   time_begin(c, 1);
   cudaError_t e = cudaSuccess;
