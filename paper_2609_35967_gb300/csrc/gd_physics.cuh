@@ -215,13 +215,9 @@ __device__ __forceinline__ PairOut<T> pair_channels(const Query<T>& q, T s_j, T 
   if (q.mode == GD_KERNEL_PHYSICAL) {
     T St_j = q.g * s_j;
     T aj, bj;
-    if constexpr (sizeof(T) == 8) {
-      aj = St_j / (one + St_j * St_j);
-      bj = one / (one + St_j * St_j);
-    } else {
-      bj = __fdividef(one, one + St_j * St_j);
-      aj = St_j * bj;
-    }
+    // one quotient for both (an FP64 division is a long sequence on the narrow FP64 pipe)
+    if constexpr (sizeof(T) == 8) bj = one / (one + St_j * St_j); else bj = __fdividef(one, one + St_j * St_j);
+    aj = St_j * bj;
     T hj = St_j < (T)0.5 ? St_j : (T)0.5;
     T dvR = q.e2 * (q.ai - aj);
     T dvZ = q.zo * (q.hi - hj);
@@ -234,8 +230,7 @@ __device__ __forceinline__ PairOut<T> pair_channels(const Query<T>& q, T s_j, T 
     int regime;
     T s1, s2;
     T t2 = turb_dv2<T>(q.St, St_j, q.Vg2, q.tRe, regime, s1, s2);
-    T dvt2;
-    if constexpr (sizeof(T) == 8) { T dvt = sqrt(t2); dvt2 = dvt * dvt; } else { dvt2 = t2; }
+    const T dvt2 = t2;     // the squared turbulent term enters dv^2 as it is
     T dv, xd;
     if constexpr (sizeof(T) == 4) { xd = dvR * dvR + dvZ * dvZ + dvP * dvP + dvB * dvB + dvt2; dv = xd * rsqrtf(xd); }
     else { xd = dvR * dvR + dvZ * dvZ + dvP * dvP + dvB * dvB + dvt2; dv = sqrt(xd); }
