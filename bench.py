@@ -112,20 +112,23 @@ def algo_bytes(kernel, K, mixed):
 # bench command (dram__bytes_read.sum + dram__bytes_write.sum), per particle.  The records
 # hold only while the sources the measured kernels compile from (their files and the shared
 # headers) have the content they had at the capture.
-TRAFFIC_CSRC_SHA256 = "4fcd75968df81bea2d8c6b7a641da2c66715ed9e07873d5bb6d5912d07416acc"
+TRAFFIC_CSRC_SHA256 = "0621719fe9bfd124c5613e8678f10bdd18bb4fdbcccba098df338266b9b9d4db"
 TRAFFIC = {
-    "knn": {"workload": "disk22", "bytes_per_particle": 427.318},
-    "rates": {"workload": "disk22", "bytes_per_particle": 297.257},
-    "sample": {"workload": "disk22", "bytes_per_particle": 108.494},
-    "cells": {"workload": "disk22", "bytes_per_particle": 399.111},
+    "knn": {"workload": "disk22", "bytes_per_particle": 435.35},
+    "rates": {"workload": "disk22", "bytes_per_particle": 251.44},
+    "sample": {"workload": "disk22", "bytes_per_particle": 149.15},
 }
 
 
 # Instructions of one launch at full size, per particle, from an ncu capture of the bench
 # command (smsp__inst_executed.sum: warp instructions issued; sm__inst_executed_pipe_fp64.sum:
 # warp instructions on the FP64 pipe), under the same source digest rule as TRAFFIC.
-INST_CSRC_SHA256 = None
-INST = {}
+INST_CSRC_SHA256 = TRAFFIC_CSRC_SHA256
+INST = {
+    "knn": {"workload": "disk22", "inst": 642.61, "fp64_inst": 2.2876},
+    "rates": {"workload": "disk22", "inst": 352.37, "fp64_inst": 4.1884},
+    "sample": {"workload": "disk22", "inst": 286.59, "fp64_inst": 6.9174},
+}
 
 # Issue rate of the SMs: 4 schedulers per SM, one warp instruction each per cycle.
 SCHEDULERS_PER_SM = 4
