@@ -192,8 +192,9 @@ constexpr float kU32 = 5.9604645e-8f;     // unit roundoff of FP32, 2^-24
 // and dv^2 by E2 = 2 (2 sum |dv_k| err_k + err_t + 5u dv^2) (a factor 2 of margin).  The
 // decision dv < v_frag is certified when |dv^2 - v_frag^2| > E2 + 4u v_frag^2; psi = m_j/m_i
 // (relative error <= 6u) against 0.1 and 1e-6 with a margin of 16u; N_coll = floor(1e-4/psi)
-// when 1e-4/psi (8.5u) lies more than 20u of itself from an integer below 2^23, else the
-// caller forms it from the FP64 masses (group64, regroup64); the regime of St1 against
+// when 1e-4 m_i/m_j (an IEEE quotient, within 5u) lies more than 10u of itself from an
+// integer below 2^23, else the caller forms it from the FP64 masses (group64, regroup64); the
+// regime of St1 against
 // Re^-1/2 and 1 with a margin of 2 (eps + 2u).  The channel rates are then within
 // derr = E2 / (2 dv^2) + 8u of the FP64 ones.
 template <typename T>
@@ -205,7 +206,9 @@ __device__ __forceinline__ PairOut<T> pair_channels(const Query<T>& q, T s_j, T 
   T ncoll = one;
   T vg = (T)0;      // 1e-4 / psi when grouped
   if (psi <= (T)1e-6) {
-    if constexpr (sizeof(T) == 4) vg = __fdividef(1e-4f, psi); else vg = (T)1e-4 / psi;
+    // mixed form: 1e-4 m_i / m_j with an IEEE quotient -- within 5u of the FP64 form's
+    // 1e-4 / psi (the roundings of m_i, m_j, 1e-4, the product and the quotient)
+    if constexpr (sizeof(T) == 4) vg = __fdiv_rn(1e-4f * q.m, m_j); else vg = (T)1e-4 / psi;
     ncoll = floor(vg);
   }
   T rate;
@@ -274,7 +277,7 @@ __device__ __forceinline__ PairOut<T> pair_channels(const Query<T>& q, T s_j, T 
   if constexpr (sizeof(T) == 4) {
     const float u = kU32;
     cert = cert && fabsf(psi - 1e-6f) > 16.f * u * 1e-6f;
-    if (psi <= 1e-6f && !(vg < 8388608.f && vg - ncoll > 20.f * u * vg && ncoll + 1.f - vg > 20.f * u * vg))
+    if (psi <= 1e-6f && !(vg < 8388608.f && vg - ncoll > 10.f * u * vg && ncoll + 1.f - vg > 10.f * u * vg))
       group64 = 1;
   } else {
     const double tie = 1e-10;
@@ -303,13 +306,13 @@ __device__ __forceinline__ PairOut<T> pair_channels(const Query<T>& q, T s_j, T 
   return o;
 }
 
-// Mixed form: N_coll of a grouped pair from the FP64 masses m_i and m_j with the FP64 form's
-// operations (psi = m_j / m_i, floor(1e-4 / psi)), the channel rates recomputed with it in
-// FP32 (N_coll rounded to FP32, half a unit more of error).  A count within 1e-10 of an
-// integer boundary stays uncertified.
+// Mixed form: N_coll of a grouped pair from the FP64 masses m_i and m_j, the channel rates
+// recomputed with it in FP32 (N_coll rounded to FP32, half a unit more of error).  The FP64
+// form forms floor(1e-4 / (m_j / m_i)); here one FP64 quotient (1e-4 m_i) / m_j, within 4
+// units of the last place of that value, so the two floors differ only within 4e-16 of an
+// integer.  A count within 1e-10 of an integer boundary stays uncertified, which covers that.
 __device__ __forceinline__ void regroup64(PairOut<float>& o, double m_i, double m_j) {
-  const double psi = m_j / m_i;
-  const double vg = 1e-4 / psi;
+  const double vg = (1e-4 * m_i) / m_j;
   const double n = floor(vg);
   if (vg - n <= 1e-10 * vg || n + 1.0 - vg <= 1e-10 * vg) o.cert = 0;
   const float nf = (float)n;

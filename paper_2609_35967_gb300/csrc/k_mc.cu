@@ -474,7 +474,7 @@ __device__ __forceinline__ void warp_bin_add(Acc* acc, int* cnt, int fbin, const
 }
 
 // ---------------------------------------------------------------- rate kernel
-// Block = one tile of up to kTile ranks of one instance; lane = particle: each thread walks
+// Lane = particle (consecutive threads take consecutive ranks): each thread walks
 // its own neighbour row (the row stays in L1 across the walk), evaluates the K pairs in slot
 // order and sums lambda*_i and the moments sum lambda* <J>, sum lambda* <J^2> in registers
 // (FP64 form: the channel rates in the oracle's order, slot by slot, remnant before debris).
@@ -587,24 +587,22 @@ __device__ __forceinline__ void rates_one(const McArgs& A, const InstDev& P, lon
   if (!isfinite(lam)) set_status(&A.st[u], GD_ST_NONFINITE);
 }
 
-// One block per tile of ranks; with spatial groups a grid-stride loop over the round's list.
+// A grid-stride loop over the ranks (consecutive threads, consecutive ranks), filling every
+// SM whatever the number of particles; with spatial groups over the round's list only.
 template <typename T>
-__global__ void __launch_bounds__(128, 8) k_rates(McArgs A, TileMap tm) {
-  if (A.act) {
-    const long long n = (long long)*A.act_n;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-         t += (long long)gridDim.x * blockDim.x) {
+__global__ void __launch_bounds__(128, 8) k_rates(McArgs A) {
+  const long long n = A.act ? (long long)*A.act_n : A.N;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    if (A.act) {
       const long long r = A.act[t];
       const int u = A.unit_r[r];
       rates_one<T>(A, A.P[A.unit_inst[u]], r, u);
+    } else {
+      const int b = inst_of(A.off, A.n_inst, t);
+      rates_one<T>(A, A.P[b], t, b);
     }
-    return;
   }
-  int b;
-  long long lo, hi;
-  tile_range(tm, blockIdx.x, b, lo, hi);
-  const InstDev& P = A.P[b];
-  for (long long r = lo + threadIdx.x; r < hi; r += blockDim.x) rates_one<T>(A, P, r, b);
 }
 
 // Mixed form: the particles k_rates could not certify, redone in FP64 (the FP64 form's
@@ -1608,9 +1606,8 @@ static void bins_reduce(gd_ctx* c, int q0, int nq, int skip_q) {
                                              c->grouped ? c->d_state : nullptr);
 }
 
-// The rate kernel's grid: a block per tile of ranks, or (spatial groups) a grid-stride loop
-// over the round's list on every SM.
-static int rate_grid(const gd_ctx* c) { return c->grouped ? c->num_sms * 8 : c->n_tiles; }
+// The rate kernel's grid: 8 blocks of 128 threads on every SM (its register budget's limit).
+static int rate_grid(const gd_ctx* c) { return c->num_sms * 8; }
 
 cudaError_t launch_rates(gd_ctx* c, double* chan_out) {
   McArgs A = mc_args(c);
@@ -1622,7 +1619,7 @@ cudaError_t launch_rates(gd_ctx* c, double* chan_out) {
     // particles the FP32 rates cannot certify are listed (counter 5) and redone in FP64
     A.redo_n = c->d_counters + 5;
     cudaMemsetAsync(A.redo_n, 0, sizeof(unsigned long long), c->stream);
-    k_rates<float><<<rate_grid(c), 128, 0, c->stream>>>(A, tile_map(c));
+    k_rates<float><<<rate_grid(c), 128, 0, c->stream>>>(A);
     McArgs B = A;
     B.list = c->d_redo;
     B.list_n = A.redo_n;
@@ -1631,7 +1628,7 @@ cudaError_t launch_rates(gd_ctx* c, double* chan_out) {
                                                            c->n_btiles, gperm, c->d_state);
     c->launches += 1;
   } else {
-    k_rates<double><<<rate_grid(c), 128, 0, c->stream>>>(A, tile_map(c));
+    k_rates<double><<<rate_grid(c), 128, 0, c->stream>>>(A);
     k_bins_tile<double><<<c->n_btiles, 128, 0, c->stream>>>(bins_map(c), c->d_rank_of, c->d_contrib, c->d_part,
                                                             c->n_btiles, gperm, c->d_state);
   }
