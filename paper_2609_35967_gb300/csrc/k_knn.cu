@@ -539,7 +539,7 @@ template <int CAP> struct KnnShape {
 // kRow1: a context of 1D radial instances (their one-row grids pack the x cell in all the
 // bits of w; the 1D model cannot share a context with the others).
 template <int CAP, bool kMixed, bool kRow1>
-__global__ void __launch_bounds__(128, CAP <= 40 ? 5 : 4) k_knn(KnnArgs A) {
+__global__ void __launch_bounds__(128, CAP <= 40 ? 6 : 4) k_knn(KnnArgs A) {
   extern __shared__ uint32_t smem[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   LaneBuf<CAP, kMixed> buf;
@@ -730,7 +730,7 @@ static cudaError_t prepare_t() {
 
 template <bool kMixed>
 static cudaError_t prepare_cap(int K) {
-  if (K <= 32) return prepare_t<40, kMixed>();
+  if (K <= 32) return prepare_t<34, kMixed>();
   if (K <= 48) return prepare_t<64, kMixed>();
   if (K <= 80) return prepare_t<96, kMixed>();
   if (K <= 128) return prepare_t<144, kMixed>();
@@ -755,9 +755,12 @@ static cudaError_t launch_both(gd_ctx* c, const KnnArgs& A) {
 
 template <bool kMixed>
 static cudaError_t launch_cap(gd_ctx* c, const KnnArgs& A, bool wide) {
-  // buffer capacity: the K-1 members plus room for the radius margin; after particles
-  // moved, the K-th distance is uncertain and K <= 32 takes the 64-entry buffer
-  if (c->K <= 32) return wide ? launch_both<64, kMixed>(c, A) : launch_both<40, kMixed>(c, A);
+  // buffer capacity: the K-1 members plus room for the radius margin.  Static builds start
+  // at 1.001 d_i, so for K <= 32 a 34-entry buffer holds the ball, and its 36 KB per block
+  // with at most 80 registers lets 6 blocks share an SM (a 40-entry buffer allowed 5: 5.53
+  // against 5.18 ms per build of the 2^22 disk); after particles moved, the K-th distance
+  // is uncertain and K <= 32 takes the 64-entry buffer
+  if (c->K <= 32) return wide ? launch_both<64, kMixed>(c, A) : launch_both<34, kMixed>(c, A);
   if (c->K <= 48) return launch_both<64, kMixed>(c, A);
   if (c->K <= 80) return launch_both<96, kMixed>(c, A);
   if (c->K <= 128) return launch_both<144, kMixed>(c, A);
