@@ -904,6 +904,8 @@ __global__ void k_interval(const InstDev* __restrict__ P, StateDev* st, BinsDev*
   }
   S.dt_req = dt_req;
   S.dt_exe = dt;
+  S.level = k;
+  S.k_req = k;
   S.remain_ticks -= 1LL << (60 - k);
   if (S.remain_ticks == 0 && !S.hold) S.remain_ticks = 1LL << 60;
   S.dt_remain = ldexp((double)S.remain_ticks, -60) * dtc;

@@ -147,3 +147,43 @@ def test_disk22_eight_groups_fewer_updates(gd):
           "delayed %d, breaks %d" % (res[1][0], res[1][2], res[8][0], res[8][1], res[8][2], res[8][3], res[8][4]))
     assert res[8][2] < res[1][2]
     assert max(res[8][1]) >= res[1][1][0] // 2
+
+
+def test_batched_grouped_and_plain_instances(gd, oracle):
+    """One context with a three-group disk, a plain patch and a two-slab patch: each instance
+    advances by its own rounds (the plain one by intervals) and matches its own oracle run;
+    the units of the later instances sit behind the first instance's groups."""
+    disk = dense_inner_disk(2000, seed=34, G=3)
+    plain = W.patch_instance(900, K=16, seed=35)
+    slabs = W.patch_instance(1200, K=16, seed=36)
+    slabs["params"] = dict(slabs["params"], spatial_groups=2)
+    insts = [disk, plain, slabs]
+    Gs = [3, 1, 2]
+    runs = [oracle.GroupRun(oracle.params(i["params"]), G, i["x"], i["y"], i["z"], i["s"], i["M"])
+            for i, G in zip(insts, Gs)]
+    offs = W.concat(insts)["offsets"]
+    sess = gd.Session(insts, K=16, precision=gd.GD_FP64)
+    compared = 0
+    for r in range(60):
+        sess.build_neighbors()
+        sess.collision_rates()
+        ec, eh, nn = sess.sample_collisions(want=True)
+        ec, eh, nn = ec.cpu().numpy(), eh.cpu().numpy().view(np.uint32), nn.cpu().numpy()
+        s_gpu = sess.t["s"].cpu().numpy()
+        outs = [run.round(want=("ev_count", "ev_hash", "near")) for run in runs]
+        if (nn > 0).any() or any((o["near"] > 0).any() for o in outs):
+            break
+        for b, (run, o, G) in enumerate(zip(runs, outs, Gs)):
+            lo, hi = offs[b], offs[b + 1]
+            assert np.array_equal(ec[lo:hi], o["ev_count"]), (r, b)
+            assert np.array_equal(eh[lo:hi], o["ev_hash"]), (r, b)
+            assert np.abs(s_gpu[lo:hi] / run.s - 1.0).max() < 1e-12, (r, b)
+            gs = sess.group_stats(b)
+            assert len(gs) == G
+            for g in range(G):
+                assert gs[g]["level"] == run.S.level[g] and gs[g]["C"] == run.S.st[g].C, (r, b, g)
+                assert gs[g]["clock"] == FULL - run.S.st[g].remain_ticks or G == 1, (r, b, g)
+        compared += 1
+    assert compared >= 40, compared
+    assert sess.stats()["status"] == 0
+    sess.close()
