@@ -112,11 +112,11 @@ def algo_bytes(kernel, K, mixed):
 # bench command (dram__bytes_read.sum + dram__bytes_write.sum), per particle.  The records
 # hold only while the sources the measured kernels compile from (their files and the shared
 # headers) have the content they had at the capture.
-TRAFFIC_CSRC_SHA256 = "0621719fe9bfd124c5613e8678f10bdd18bb4fdbcccba098df338266b9b9d4db"
+TRAFFIC_CSRC_SHA256 = "ba6ac4cd6b208057b8e6c5fa4fb3e397fb49d417aa8920ecccdb6006ecd42d16"
 TRAFFIC = {
-    "knn": {"workload": "disk22", "bytes_per_particle": 435.35},
-    "rates": {"workload": "disk22", "bytes_per_particle": 251.44},
-    "sample": {"workload": "disk22", "bytes_per_particle": 149.15},
+    "knn": {"workload": "disk22", "bytes_per_particle": 545.77},
+    "rates": {"workload": "disk22", "bytes_per_particle": 204.63},
+    "sample": {"workload": "disk22", "bytes_per_particle": 149.03},
 }
 
 
@@ -125,9 +125,9 @@ TRAFFIC = {
 # warp instructions on the FP64 pipe), under the same source digest rule as TRAFFIC.
 INST_CSRC_SHA256 = TRAFFIC_CSRC_SHA256
 INST = {
-    "knn": {"workload": "disk22", "inst": 642.61, "fp64_inst": 2.2876},
-    "rates": {"workload": "disk22", "inst": 352.37, "fp64_inst": 4.1884},
-    "sample": {"workload": "disk22", "inst": 286.59, "fp64_inst": 6.9174},
+    "knn": {"workload": "disk22", "inst": 645.00, "fp64_inst": 2.0289},
+    "rates": {"workload": "disk22", "inst": 332.78, "fp64_inst": 0.18779},
+    "sample": {"workload": "disk22", "inst": 284.31, "fp64_inst": 6.9086},
 }
 
 # Issue rate of the SMs: 4 schedulers per SM, one warp instruction each per cycle.
