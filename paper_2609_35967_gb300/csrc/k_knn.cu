@@ -539,7 +539,7 @@ template <int CAP> struct KnnShape {
 // kRow1: a context of 1D radial instances (their one-row grids pack the x cell in all the
 // bits of w; the 1D model cannot share a context with the others).
 template <int CAP, bool kMixed, bool kRow1>
-__global__ void __launch_bounds__(128, CAP <= 40 ? 6 : 4) k_knn(KnnArgs A) {
+__global__ void __launch_bounds__(128, CAP <= 40 && kMixed ? 6 : 4) k_knn(KnnArgs A) {
   extern __shared__ uint32_t smem[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   LaneBuf<CAP, kMixed> buf;

@@ -590,7 +590,7 @@ __device__ __forceinline__ void rates_one(const McArgs& A, const InstDev& P, lon
 // A grid-stride loop over the ranks (consecutive threads, consecutive ranks), filling every
 // SM whatever the number of particles; with spatial groups over the round's list only.
 template <typename T>
-__global__ void __launch_bounds__(128, 8) k_rates(McArgs A) {
+__global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 8) k_rates(McArgs A) {
   const long long n = A.act ? (long long)*A.act_n : A.N;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x) {
@@ -1451,7 +1451,7 @@ __device__ __noinline__ void replay64(McArgs A, long long r, int lane) {
 }
 
 template <typename T, int S>
-__global__ void __launch_bounds__(64, 7) k_sample(McArgs A) {
+__global__ void __launch_bounds__(64, sizeof(T) == 8 ? 4 : 7) k_sample(McArgs A) {
   const int lane = threadIdx.x & 31;
   // spatial groups: the round's ranks only (A.act), 32 to a chunk like the full range
   const long long total = A.act ? (long long)*A.act_n : A.N;
