@@ -63,7 +63,16 @@ def pipe_peaks():
     return out
 
 
-def make_workload(name, rank=0):
+def shard(n_items, rank, world):
+    """Instances of a batch a rank takes when the batch is split across ranks: rank r takes
+    r, r + world, r + 2 world, ... (disjoint, all covered, sizes within one)."""
+    return list(range(rank, n_items, world))
+
+
+def make_workload(name, rank=0, world=1):
+    """The workload and its config.  Every workload runs as one replica per rank (its own
+    seed: weak scaling), except the 256-patch batch, whose instances are split across the
+    ranks (the same batch on any number of ranks: strong scaling, no exchange)."""
     from paper_2609_35967_gb300 import workloads as W
     if name == "disk22":
         return W.config2(seed=1 + rank), dict(workload="global disk 5-100 au, 2^22 particles, "
@@ -72,8 +81,13 @@ def make_workload(name, rank=0):
         return W.config1(seed=1 + rank), dict(workload="global disk 5-100 au, 2^20 particles, "
                                                "a = 1 um, K=32")
     if name == "patches256":
-        return W.config3(seed0=1000 + 1000 * rank), dict(workload="256 local patches, N_b log-uniform "
-                                                          "2^10-2^16, K=32")
+        insts = W.config3(seed0=1000)
+        cfg = dict(workload="256 local patches, N_b log-uniform 2^10-2^16, K=32")
+        if world > 1:
+            cfg["sharding"] = f"instances r, r + {world}, ... on rank r (the same 256 patches split across ranks)"
+            cfg["n_particles_total"] = int(sum(len(i["x"]) for i in insts))
+            insts = [insts[b] for b in shard(len(insts), rank, world)]
+        return insts, cfg
     if name == "disk24":
         return W.config4(seed=1 + rank), dict(workload="global disk, 2^24 particles, log-normal a "
                                                "(median 1 um, sigma_ln 0.5), K=48, with push")
@@ -303,7 +317,7 @@ def run_gpu(args, rank, world):
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.set_device(dev)
-    insts, cfg = make_workload(args.workload, rank)
+    insts, cfg = make_workload(args.workload, rank, world)
     K = insts[0]["params"]["K"]
     push = args.workload == "disk24"
     graph = args.workload == "patches256"
@@ -726,16 +740,21 @@ def result_line(r, args, world):
     """The JSON line of the GPU arm from one rank's results with max-over-ranks times."""
     N, K = r["N"], r["K"]
     ms_mixed, ms_fp64, ms_e2e = r["times"]
-    value = world * N * args.steps / (ms_mixed * 1e-3)
+    # the units all ranks processed: N each (replicas), or the whole batch split across them
+    n_job = r["cfg"].get("n_particles_total", world * N)
+    value = n_job * args.steps / (ms_mixed * 1e-3)
     km = r["mixed"]["kernel_ms"]
     kc = r["mixed"]["kernel_calls"]
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_mixed / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
+        "scaling": "strong" if "sharding" in r["cfg"] else "weak", "vs_baseline": None,
+        "dtype": "f32+f64 (mixed)", "data": "synthetic",
         "config": dict(r["cfg"], n_particles=N, K=K, precision="mixed",
                        l2="no flush: working set > 129 MB L2 (lists alone 4K B/particle)",
-                       parallelism=f"{world} independent replicas" if world > 1 else "1 GPU",
+                       parallelism=("1 GPU" if world == 1 else
+                                    f"instances split across {world} ranks" if "sharding" in r["cfg"] else
+                                    f"{world} independent replicas"),
                        cell_factor=r["mixed"]["cell_factor"],
                        cell_xsplit=r["mixed"].get("cell_xsplit", 1)),
         "events_per_step": r["mixed"]["events"] / args.steps,
@@ -747,14 +766,14 @@ def result_line(r, args, world):
         "kernels_ms_per_step": {k: v / args.steps for k, v in km.items() if v > 0 and k != "stats"},
         "gpu_launches": r["mixed"]["launches"],
         "clocks": r["mixed"]["clocks"],
-        "e2e": {"value": world * N * args.steps / (ms_e2e * 1e-3), "unit": UNIT,
+        "e2e": {"value": n_job * args.steps / (ms_e2e * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
     }
     if r.get("pipe_peaks"):
         out["pipe_peaks"] = r["pipe_peaks"]
     if r["fp64"]:
         st = max(1, args.steps // 3)
-        out["fp64"] = {"value": world * N * st / (ms_fp64 * 1e-3), "ms_per_step": ms_fp64 / st,
+        out["fp64"] = {"value": n_job * st / (ms_fp64 * 1e-3), "ms_per_step": ms_fp64 / st,
                        "cell_factor": r["fp64"]["cell_factor"],
                        "kernels_ms_per_step": {k: v / st for k, v in r["fp64"]["kernel_ms"].items()
                                                if v > 0 and k != "stats"}}

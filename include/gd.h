@@ -212,13 +212,17 @@ typedef struct {
                                   the sizes below and above); summed in a fixed order */
 } gd_instance_stats;
 
-/* Creates a context over caller-owned particle arrays (see gd_config).  Checks
- * every argument (each instance must hold at least K particles), copies the
- * parameter tables to the device and allocates the library's scratch.
+/* Creates a context over caller-owned particle arrays (see gd_config): the
+ * representative particles of Sect. 2 (position, diameter s_i, particle mass M_i)
+ * of one or more instances, each with the gas disk of Sect. 2.2 and the
+ * collision-model parameters of Sect. 2.5.  Checks every argument (each instance
+ * must hold at least K = N_K particles, Sect. 2.5.1), copies the parameter tables
+ * to the device and allocates the library's scratch.
  * Returns GD_ERR_ARG, GD_ERR_OOM or GD_ERR_CUDA on failure (*out = NULL). */
 gd_status gd_create(gd_ctx** out, const gd_config* cfg);
 
-/* Waits for the context's stream, frees everything the library allocated. */
+/* Waits for the context's stream, frees everything the library allocated (a
+ * service of the library; the paper has no counterpart). */
 gd_status gd_destroy(gd_ctx* ctx);
 
 /* Sect. 2.5.1: bins every particle into a per-instance uniform cell grid
@@ -347,7 +351,10 @@ typedef struct {
 } gd_dt_rule;
 gd_status gd_timestep(gd_ctx* ctx, const gd_dt_rule* rule, double* dt_out_host, double* dti_out);
 
-/* Synchronises the stream, reduces per-instance sums and copies counters.
+/* Synchronises the stream, reduces per-instance sums and copies counters: the
+ * mass bookkeeping of Sect. 2.5.2 (sum M_i, which no call writes, and sum M_i m_i,
+ * sum M_i s_i with N_i = M_i / m_i), the size spectrum, the interval state of
+ * Sect. 2.5.3 (C, dt_exe, dt_req, time left) and the event and near-tie counts.
  * out: HOST, required.  inst_out: HOST [n_instances] or NULL.
  * Returns the first device error as a gd_status (GD_OK if none). */
 gd_status gd_stats(gd_ctx* ctx, gd_stats_t* out, gd_instance_stats* inst_out);

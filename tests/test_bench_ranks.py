@@ -89,3 +89,19 @@ def test_reference_arm_prints_on_rank0_only():
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_batch_sharding_splits_instances():
+    """The 256-patch batch on N ranks: disjoint shards that cover every instance, sizes within
+    one; the whole-job value counts the whole batch once (strong scaling)."""
+    for world in (1, 2, 3, 4, 8):
+        parts = [bench.shard(256, r, world) for r in range(world)]
+        flat = sorted(b for p in parts for b in p)
+        assert flat == list(range(256))
+        assert max(map(len, parts)) - min(map(len, parts)) <= 1
+    args = types.SimpleNamespace(steps=10, warmup=3, workload="patches256")
+    r = _fake_rank_result(N=500)
+    r["cfg"] = {"workload": "test", "sharding": "r::2", "n_particles_total": 1000}
+    out = bench.result_line(r, args, 2)
+    assert out["scaling"] == "strong"
+    assert out["value"] == 1000 * args.steps / (r["times"][0] * 1e-3)
