@@ -1154,7 +1154,12 @@ __device__ __forceinline__ void sample_item(const McArgs& A, const int lane, con
     int jr[S];
     PairOut<T> po[S];
     Query<T> q = live_query<T>(f, s, m);
-    double v = lane_channels<T, S>(A, q, m, rp, lane, c0, c1, jr, po);
+    // the row and the frozen partners are the same for every event of the particle: loaded
+    // once, so that an event's pair refresh waits on no dependent pair of loads
+    Partner<T> pt[S];
+    load_row_slots<S>(A, rp, lane, jr);
+    load_partners<T, S>(A, jr, pt);
+    double v = channels_of<T, S>(A, q, m, jr, pt, c0, c1, po);
     double incl = 0.0, tot = 0.0;
     float inclf = 0.0f, totf = 0.0f, eta = 0.0f;
     bool bad64 = false;       // mixed form: a pair's decision is uncertified at this state
@@ -1340,7 +1345,7 @@ __device__ __forceinline__ void sample_item(const McArgs& A, const int lane, con
       if (e >= A.max_events) { if (lane == 0) set_status(&A.st[up], GD_ST_EVENT_CAP); break; }
       if constexpr (!kMixed) q = live_query<T>(f, s, m);
       else q = live_query_f(f, sf, (float)m);
-      v = lane_channels<T, S>(A, q, m, rp, lane, c0, c1, jr, po);
+      v = channels_of<T, S>(A, q, m, jr, pt, c0, c1, po);
       pairs_checked();
       if constexpr (!kMixed) {
         incl = warp_incl_scan(v, lane);
