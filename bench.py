@@ -126,11 +126,11 @@ def algo_bytes(kernel, K, mixed):
 # bench command (dram__bytes_read.sum + dram__bytes_write.sum), per particle.  The records
 # hold only while the sources the measured kernels compile from (their files and the shared
 # headers) have the content they had at the capture.
-TRAFFIC_CSRC_SHA256 = "481e08c3602dde58e44b1befff5b7db0a40e50b166f4c4fde1d07738c4ff8db5"
+TRAFFIC_CSRC_SHA256 = "7a3dac2b2419e591b2f85ea3d4f11242b23f983dbe0048c26cebb89193af4c36"
 TRAFFIC = {
-    "knn": {"workload": "disk22", "bytes_per_particle": 546.43},
-    "rates": {"workload": "disk22", "bytes_per_particle": 204.68},
-    "sample": {"workload": "disk22", "bytes_per_particle": 148.87},
+    "knn": {"workload": "disk22", "bytes_per_particle": 389.38},
+    "rates": {"workload": "disk22", "bytes_per_particle": 204.53},
+    "sample": {"workload": "disk22", "bytes_per_particle": 145.26},
 }
 
 
@@ -139,9 +139,9 @@ TRAFFIC = {
 # warp instructions on the FP64 pipe), under the same source digest rule as TRAFFIC.
 INST_CSRC_SHA256 = TRAFFIC_CSRC_SHA256
 INST = {
-    "knn": {"workload": "disk22", "inst": 644.97, "fp64_inst": 2.0289},
+    "knn": {"workload": "disk22", "inst": 654.56, "fp64_inst": 2.0289},
     "rates": {"workload": "disk22", "inst": 332.78, "fp64_inst": 0.18779},
-    "sample": {"workload": "disk22", "inst": 284.31, "fp64_inst": 6.9086},
+    "sample": {"workload": "disk22", "inst": 276.84, "fp64_inst": 6.9077},
 }
 
 # Issue rate of the SMs: 4 schedulers per SM, one warp instruction each per cycle.
