@@ -1343,6 +1343,9 @@ __device__ __forceinline__ void sample_item(const McArgs& A, const int lane, con
       h = h * 31u + (unsigned)(chosen + 1);
       ++e;
       if (e >= A.max_events) { if (lane == 0) set_status(&A.st[up], GD_ST_EVENT_CAP); break; }
+      // the next event's draws depend only on its counter: formed before the pair refresh, so
+      // that their integer work fills the refresh's latencies
+      U4 w = philox(il, iv, (unsigned)e, 0u, k0, k1);
       if constexpr (!kMixed) q = live_query<T>(f, s, m);
       else q = live_query_f(f, sf, (float)m);
       v = channels_of<T, S>(A, q, m, jr, pt, c0, c1, po);
@@ -1372,7 +1375,6 @@ __device__ __forceinline__ void sample_item(const McArgs& A, const int lane, con
         unc = true;
         break;
       }
-      U4 w = philox(il, iv, (unsigned)e, 0u, k0, k1);
       uw0 = w.z;
       uw1 = w.w;
       if constexpr (!kMixed) u_s = u01(w.z, w.w);
