@@ -179,3 +179,56 @@ def test_interacting_groups_schedule(oracle):
     # the next call starts a new step at clock 0 with every group active
     run.round()
     assert S.t == 0 and all(S.active[g] for g in range(G))
+
+
+def test_schedule_invariants_random(oracle):
+    """The scheduling rule on 3000 random cases (up to 10 groups, random interactions, active
+    sets, scheduled levels within 4 of each other where they interact, requests and step-end
+    floors): every active group ends inside the step (level >= floor); every interacting pair
+    with an active member ends within 4 levels unless a break is counted; a group is coarser
+    than its request only when a scheduled neighbour holds it (a delay is counted) and finer
+    only for a floor or a neighbour; and the result does not depend on the groups' order."""
+    rng = np.random.default_rng(77)
+    for case in range(3000):
+        G = int(rng.integers(2, 11))
+        inter = np.zeros((G, G), dtype=bool)
+        for g in range(G):
+            for h in range(g + 1, G):
+                if rng.random() < 0.4:
+                    inter[g, h] = inter[h, g] = True
+        active = rng.random(G) < 0.5
+        # scheduled levels of the inactive groups: a consistent state (interacting ones within 4)
+        level = np.full(G, -1, dtype=np.int32)
+        base = int(rng.integers(0, 30))
+        for g in range(G):
+            if not active[g]:
+                level[g] = base + int(rng.integers(0, 3))
+        k_req = rng.integers(0, 45, G).astype(np.int32)
+        k_fit = np.minimum(rng.integers(0, 6, G), k_req).astype(np.int32)
+        masks = [sum(1 << h for h in range(G) if inter[g, h]) for g in range(G)]
+        lv = level.copy()
+        d, b = _sched_raw(oracle, G, masks, active, k_req, k_fit, lv)
+        for g in range(G):
+            if not active[g]:
+                assert lv[g] == level[g]
+                continue
+            assert lv[g] >= k_fit[g]
+            if lv[g] < k_req[g]:
+                # held back by an inactive interacting group within 4 levels of it, or by a chain
+                assert any(inter[g, h] for h in range(G)), case
+        n_far = sum(1 for g in range(G) for h in range(g + 1, G)
+                    if inter[g, h] and (active[g] or active[h]) and abs(int(lv[g]) - int(lv[h])) > 4)
+        assert n_far == b, (case, n_far, b)
+        assert d == sum(1 for g in range(G) if active[g] and lv[g] < k_req[g])
+        # the same case with the groups in reverse order gives the reversed levels
+        rev = list(range(G))[::-1]
+        masks_r = [sum(1 << rev.index(h) for h in range(G) if inter[g, h]) for g in rev]
+        lv_r = level[rev].copy()
+        _sched_raw(oracle, G, masks_r, active[rev], k_req[rev], k_fit[rev], lv_r)
+        assert np.array_equal(lv_r[::-1], lv), case
+
+
+def _sched_raw(oracle, G, masks, active, k_req, k_fit, level):
+    from oracle import gdo
+    inter = np.array(masks, dtype=np.uint64)
+    return gdo.schedule(G, inter, np.ones(G), np.asarray(active, dtype=np.int32), k_req, k_fit, level)
