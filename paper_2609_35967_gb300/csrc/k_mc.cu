@@ -1616,7 +1616,7 @@ static void bins_reduce(gd_ctx* c, int q0, int nq, int skip_q) {
 }
 
 // The rate kernel's grid: 6 blocks of 128 threads on every SM (its register budget's limit;
-// 85 registers without spills ran 1.60 ms on the 2^22 disk against 1.64 with 64 and 8 blocks).
+// 80 registers without spills ran 1.60 ms on the 2^22 disk against 1.64 with 64 and 8 blocks).
 static int rate_grid(const gd_ctx* c) { return c->num_sms * 6; }
 
 cudaError_t launch_rates(gd_ctx* c, double* chan_out) {
