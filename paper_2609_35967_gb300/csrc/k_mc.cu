@@ -1615,9 +1615,11 @@ static void bins_reduce(gd_ctx* c, int q0, int nq, int skip_q) {
                                              c->grouped ? c->d_state : nullptr);
 }
 
-// The rate kernel's grid: 6 blocks of 128 threads on every SM (its register budget's limit;
-// 80 registers without spills ran 1.60 ms on the 2^22 disk against 1.64 with 64 and 8 blocks).
-static int rate_grid(const gd_ctx* c) { return c->num_sms * 6; }
+// The rate kernel's grid: one wave of the blocks its register budget lets an SM hold -- 6 of
+// 128 threads in the mixed form (80 registers without spills ran 1.60 ms on the 2^22 disk
+// against 1.64 with 64 and 8 blocks), 4 in the FP64 form (a second, partial wave of the
+// grid-stride loop made the FP64 rates a third slower).
+static int rate_grid(const gd_ctx* c) { return c->num_sms * (c->precision == GD_MIXED ? 6 : 4); }
 
 cudaError_t launch_rates(gd_ctx* c, double* chan_out) {
   McArgs A = mc_args(c);
