@@ -126,11 +126,11 @@ def algo_bytes(kernel, K, mixed):
 # bench command (dram__bytes_read.sum + dram__bytes_write.sum), per particle.  The records
 # hold only while the sources the measured kernels compile from (their files and the shared
 # headers) have the content they had at the capture.
-TRAFFIC_CSRC_SHA256 = "7a3dac2b2419e591b2f85ea3d4f11242b23f983dbe0048c26cebb89193af4c36"
+TRAFFIC_CSRC_SHA256 = "17d595a4bcf0f88302a06d379c1a3d97427a3edfdcb4c98fd4c0c5d62443baef"
 TRAFFIC = {
-    "knn": {"workload": "disk22", "bytes_per_particle": 389.38},
-    "rates": {"workload": "disk22", "bytes_per_particle": 204.53},
-    "sample": {"workload": "disk22", "bytes_per_particle": 145.26},
+    "knn": {"workload": "disk22", "bytes_per_particle": 389.18},
+    "rates": {"workload": "disk22", "bytes_per_particle": 196.03},
+    "sample": {"workload": "disk22", "bytes_per_particle": 149.69},
 }
 
 
@@ -139,9 +139,9 @@ TRAFFIC = {
 # warp instructions on the FP64 pipe), under the same source digest rule as TRAFFIC.
 INST_CSRC_SHA256 = TRAFFIC_CSRC_SHA256
 INST = {
-    "knn": {"workload": "disk22", "inst": 654.56, "fp64_inst": 2.0289},
-    "rates": {"workload": "disk22", "inst": 332.78, "fp64_inst": 0.18779},
-    "sample": {"workload": "disk22", "inst": 276.84, "fp64_inst": 6.9077},
+    "knn": {"workload": "disk22", "inst": 654.56, "fp64_inst": 2.0288},
+    "rates": {"workload": "disk22", "inst": 321.52, "fp64_inst": 0.18779},
+    "sample": {"workload": "disk22", "inst": 279.76, "fp64_inst": 6.9077},
 }
 
 # Issue rate of the SMs: 4 schedulers per SM, one warp instruction each per cycle.
