@@ -1080,6 +1080,267 @@ void gdo_push(const gdo_params* P, int32_t drag, double dt, int64_t n, double* x
 }
 
 /* ------------------------------------------------------------------ */
+/* Radiation forces, Sect. 2.3.2.  beta(s) and kappa(s) scale as (s/s_0)^-1
+ * (Eqs. beta, kappa); beta0 and kappa0 are set independently (the paper allows it),
+ * s_0 is a diameter like every s here. */
+#define GDO_C_LIGHT 2.99792458e10   /* speed of light [cm s^-1] */
+
+/* sizeof(gdo_params), for the Python mirror's layout check */
+int64_t gdo_params_size(void) { return (int64_t)sizeof(gdo_params); }
+
+double gdo_rad_beta(const gdo_params* P, double s) { return P->beta0 * (P->rad_s0 / s); }
+
+double gdo_rad_kappa(const gdo_params* P, double s) { return P->kappa0 * (P->rad_s0 / s); }
+
+/* Sect. 2.3.2: the taper xi^2 (3 - 2 xi), xi = min(max(t / t_beta, 0), 1); no taper
+ * (factor 1) when t_beta <= 0 (reading). */
+double gdo_rad_taper(const gdo_params* P, double t) {
+  if (!(P->t_beta > 0.0)) return 1.0;
+  double xi = t / P->t_beta;
+  if (xi < 0.0) xi = 0.0;
+  if (xi > 1.0) xi = 1.0;
+  return xi * xi * (3.0 - 2.0 * xi);
+}
+
+/* The optical depth grid (Sect. 2.3.2, Eqs. tau_3d and tau_2d).  Readings, the paper
+ * naming neither the grid nor the deposit:
+ *  - 3D form: cells uniform in r over [tau_rmin, tau_rmax), in mu = cos theta over
+ *    [-tau_mu, tau_mu) and in phi over [-pi, pi); 2D form: uniform in R and phi, one
+ *    polar cell.  A column is one (mu, phi) cell, j * nphi + k.
+ *  - Each particle adds kappa(s_i) M_i to the cell that holds it (nearest grid point);
+ *    particles outside the grid add nothing.  The cell's kappa rho_d is that sum over the
+ *    cell volume, (r_hi^3 - r_lo^3)/3 dmu dphi, or in the 2D form kappa Sigma_d /
+ *    (sqrt(2 pi) H_g) with Sigma_d over the area (R_hi^2 - R_lo^2)/2 dphi and H_g at the
+ *    cell's mid radius.
+ *  - tau is the integral from the grid's inner edge (no interior extinction): T at
+ *    the radial faces of each column, T_0 = 0, T_{i+1} = T_i + (kappa rho_d)_i dr, stored
+ *    as T[column * (nr + 1) + i].
+ *  - At a point, tau is linear in r between the faces of its column (the exact integral
+ *    of the binned density) and bilinear between the centres of the four nearest
+ *    columns (clamped at the polar edges, periodic in phi); zero inside tau_rmin, the
+ *    outer face beyond tau_rmax. */
+static int tau_nmu(const gdo_params* P) { return P->tau_geom == GDO_TAU_2D ? 1 : P->tau_nmu; }
+
+int64_t gdo_tau_size(const gdo_params* P) {
+  if (P->tau_nr <= 0) return 0;
+  return (int64_t)tau_nmu(P) * P->tau_nphi * (P->tau_nr + 1);
+}
+
+/* phi folded into [-pi, pi) */
+static double fold_phi(double ph) { return ph - 2.0 * GDO_PI * floor((ph + GDO_PI) / (2.0 * GDO_PI)); }
+
+/* cell of a point given by its grid radius (r or R), mu and phi; -1 outside */
+static int64_t tau_cell(const gdo_params* P, double rad, double mu, double phi) {
+  int nr = P->tau_nr, nm = tau_nmu(P), np = P->tau_nphi;
+  double dr = (P->tau_rmax - P->tau_rmin) / nr;
+  double u = (rad - P->tau_rmin) / dr;
+  if (!(u >= 0.0) || !(u < (double)nr)) return -1;
+  int64_t i = (int64_t)floor(u);
+  int64_t j = 0;
+  if (P->tau_geom != GDO_TAU_2D) {
+    double dmu = 2.0 * P->tau_mu / nm;
+    double w = (mu + P->tau_mu) / dmu;
+    if (!(w >= 0.0) || !(w < (double)nm)) return -1;
+    j = (int64_t)floor(w);
+  }
+  double dphi = 2.0 * GDO_PI / np;
+  int64_t k = (int64_t)floor((phi + GDO_PI) / dphi);
+  if (k >= np) k = np - 1;
+  if (k < 0) k = 0;
+  return (j * np + k) * (nr + 1) + i;   /* index of the cell's inner face */
+}
+
+/* builds T from the points (rad, mu, phi) of n particles, their sizes and masses */
+static void tau_build(const gdo_params* P, int64_t n, const double* rad, const double* mu,
+                      const double* phi, const double* s, const double* M, double* T) {
+  int nr = P->tau_nr, nm = tau_nmu(P), np = P->tau_nphi;
+  int64_t size = gdo_tau_size(P);
+  for (int64_t c = 0; c < size; ++c) T[c] = 0.0;
+  /* the sums of kappa M, each kept at its cell's inner face slot for now */
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t c = tau_cell(P, rad[i], mu[i], phi[i]);
+    if (c >= 0) T[c] += gdo_rad_kappa(P, s[i]) * M[i];
+  }
+  double dr = (P->tau_rmax - P->tau_rmin) / nr;
+  double dmu = 2.0 * P->tau_mu / nm;
+  double dphi = 2.0 * GDO_PI / np;
+  for (int64_t col = 0; col < (int64_t)nm * np; ++col) {
+    double* Tc = T + col * (nr + 1);
+    double acc = 0.0;
+    for (int i = 0; i < nr; ++i) {
+      double r_lo = P->tau_rmin + i * dr, r_hi = P->tau_rmin + (i + 1) * dr;
+      double V;
+      if (P->tau_geom == GDO_TAU_2D) {
+        gdo_gas g;
+        gas_RZ(P, P->tau_rmin + (i + 0.5) * dr, 0.0, &g);
+        V = (r_hi * r_hi - r_lo * r_lo) / 2.0 * dphi * (sqrt(2.0 * GDO_PI) * g.H);
+      } else {
+        V = (r_hi * r_hi * r_hi - r_lo * r_lo * r_lo) / 3.0 * dmu * dphi;
+      }
+      double kr = Tc[i] / V;
+      Tc[i] = acc;
+      acc = acc + kr * dr;
+    }
+    Tc[nr] = acc;
+  }
+}
+
+/* tau at a point given by its grid radius, mu and phi */
+static double tau_interp(const gdo_params* P, const double* T, double rad, double mu, double phi) {
+  int nr = P->tau_nr, nm = tau_nmu(P), np = P->tau_nphi;
+  if (nr <= 0) return 0.0;
+  double dr = (P->tau_rmax - P->tau_rmin) / nr;
+  double u = (rad - P->tau_rmin) / dr;
+  if (!(u > 0.0)) return 0.0;
+  int64_t i = 0;
+  double fr = 0.0;
+  if (u >= (double)nr) {
+    i = nr;
+  } else {
+    i = (int64_t)floor(u);
+    fr = u - (double)i;
+  }
+  int64_t j0 = 0, j1 = 0;
+  double fm = 0.0;
+  if (nm > 1) {
+    double dmu = 2.0 * P->tau_mu / nm;
+    double w = (mu + P->tau_mu) / dmu - 0.5;
+    if (w <= 0.0) {
+      j0 = j1 = 0;
+    } else if (w >= (double)(nm - 1)) {
+      j0 = j1 = nm - 1;
+    } else {
+      j0 = (int64_t)floor(w);
+      j1 = j0 + 1;
+      fm = w - (double)j0;
+    }
+  }
+  double dphi = 2.0 * GDO_PI / np;
+  double v = (phi + GDO_PI) / dphi - 0.5;
+  double kf = floor(v);
+  double fp = v - kf;
+  int64_t k0 = ((int64_t)kf % np + np) % np, k1 = (k0 + 1) % np;
+  int64_t cols[4] = {j0 * np + k0, j0 * np + k1, j1 * np + k0, j1 * np + k1};
+  double w4[4] = {(1.0 - fm) * (1.0 - fp), (1.0 - fm) * fp, fm * (1.0 - fp), fm * fp};
+  double tau = 0.0;
+  for (int c = 0; c < 4; ++c) {
+    const double* Tc = T + cols[c] * (nr + 1);
+    double tc = (i >= nr) ? Tc[nr] : Tc[i] + fr * (Tc[i + 1] - Tc[i]);
+    tau = tau + w4[c] * tc;
+  }
+  return tau;
+}
+
+/* grid coordinates of a Cartesian point: (r, z/r, phi) in 3D, (R, 0, phi) in 2D */
+static void tau_coords(const gdo_params* P, double x, double y, double z, double* rad, double* mu,
+                       double* phi) {
+  if (P->tau_geom == GDO_TAU_2D) {
+    *rad = sqrt(x * x + y * y);
+    *mu = 0.0;
+  } else {
+    *rad = sqrt(x * x + y * y + z * z);
+    *mu = z / *rad;
+  }
+  *phi = atan2(y, x);
+}
+
+/* T from the particles at their positions (x, y, z). */
+void gdo_tau_grid(const gdo_params* P, int64_t n, const double* x, const double* y,
+                  const double* z, const double* s, const double* M, double* T) {
+  if (P->tau_nr <= 0) return;
+  double* c = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+  for (int64_t i = 0; i < n; ++i) tau_coords(P, x[i], y[i], z[i], &c[i], &c[n + i], &c[2 * n + i]);
+  tau_build(P, n, c, c + n, c + 2 * n, s, M, T);
+  free(c);
+}
+
+double gdo_tau_at(const gdo_params* P, const double* T, double x, double y, double z) {
+  double rad, mu, phi;
+  tau_coords(P, x, y, z, &rad, &mu, &phi);
+  return tau_interp(P, T, rad, mu, phi);
+}
+
+/* The staggered step of gdo_push_one with radiation forces (Sect. 2.3.2-2.3.3):
+ *  f_r = -(1 - beta e^-tau) GM/r^2 + l_theta^2/r^3 + l_phi^2/(r^3 sin^2 theta),
+ *  gamma_PR = beta e^-tau GM/(c r^2), gamma_r = 1/t_s + 2 gamma_PR,
+ *  gamma_theta = gamma_phi = 1/t_s + gamma_PR, and each component of
+ *  dy/dt = -gamma y + y_g/t_s + f advanced exactly for fixed coefficients:
+ *  y += k (f + y_g/t_s - gamma y), k = (1 - e^{-gamma dt})/gamma.
+ * beta e^-tau carries the taper at the kick's time t + dt/2.  Readings: tau is built
+ * from every particle at the midpoint of the first drift (the positions the kick sees)
+ * and interpolated at each particle's own midpoint; mid holds (r, theta, phi) of all n
+ * particles between the two passes, T the grid (gdo_tau_size doubles). */
+void gdo_push_rad(const gdo_params* P, int32_t drag, double dt, double t, int64_t n, double* x,
+                  double* y, double* z, double* vr, double* lth, double* lph, const double* s,
+                  const double* M, double* T, double* mid) {
+  double h = 0.5 * dt;
+  double* mr = mid;
+  double* mth = mid + n;
+  double* mph = mid + 2 * n;
+  for (int64_t i = 0; i < n; ++i) {
+    double r = sqrt(x[i] * x[i] + y[i] * y[i] + z[i] * z[i]);
+    double th = acos(z[i] / r);
+    double ph = atan2(y[i], x[i]);
+    double st = sin(th);
+    ph = ph + h * lph[i] / (r * r * st * st);
+    th = th + h * lth[i] / (r * r);
+    r = r + h * vr[i];
+    mr[i] = r;
+    mth[i] = th;
+    mph[i] = ph;
+  }
+  int grid = P->tau_nr > 0 && P->kappa0 > 0.0;
+  if (grid) {
+    double* c = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) {
+      double st = sin(mth[i]);
+      c[i] = (P->tau_geom == GDO_TAU_2D) ? mr[i] * st : mr[i];
+      c[n + i] = (P->tau_geom == GDO_TAU_2D) ? 0.0 : cos(mth[i]);
+      c[2 * n + i] = fold_phi(mph[i]);
+    }
+    tau_build(P, n, c, c + n, c + 2 * n, s, M, T);
+    free(c);
+  }
+  double GM = GDO_G * P->M_star;
+  double taper = gdo_rad_taper(P, t + h);
+  for (int64_t i = 0; i < n; ++i) {
+    double r = mr[i], th = mth[i], ph = mph[i];
+    double st = sin(th);
+    double ct = cos(th);
+    double tau = 0.0;
+    if (grid)
+      tau = tau_interp(P, T, (P->tau_geom == GDO_TAU_2D) ? r * st : r, (P->tau_geom == GDO_TAU_2D) ? 0.0 : ct,
+                       fold_phi(ph));
+    double be = taper * gdo_rad_beta(P, s[i]) * exp(-tau);
+    double fr = -(1.0 - be) * GM / (r * r) + lth[i] * lth[i] / (r * r * r) +
+                lph[i] * lph[i] / (r * r * r * st * st);
+    double fth = lph[i] * lph[i] * ct / (r * r * st * st * st);
+    double gpr = P->rad_pr ? be * GM / (GDO_C_LIGHT * r * r) : 0.0;
+    double gam = 0.0, ygph = 0.0;
+    if (drag) {
+      gdo_gas g;
+      gas_RZ(P, r * st, r * ct, &g);
+      double ts = g.gst * s[i] / g.Om;
+      gam = 1.0 / ts;
+      ygph = sqrt(1.0 - 2.0 * g.eta) * g.Om * g.R * g.R;
+    }
+    double g_r = gam + 2.0 * gpr, g_t = gam + gpr;
+    double k_r = (g_r > 0.0) ? -expm1(-dt * g_r) / g_r : dt;
+    double k_t = (g_t > 0.0) ? -expm1(-dt * g_t) / g_t : dt;
+    vr[i] = vr[i] + k_r * (fr - g_r * vr[i]);
+    lth[i] = lth[i] + k_t * (fth - g_t * lth[i]);
+    lph[i] = lph[i] + k_t * (gam * ygph - g_t * lph[i]);
+    r = r + h * vr[i];
+    th = th + h * lth[i] / (r * r);
+    st = sin(th);
+    ph = ph + h * lph[i] / (r * r * st * st);
+    x[i] = r * st * cos(ph);
+    y[i] = r * st * sin(ph);
+    z[i] = r * cos(th);
+  }
+}
+
+/* ------------------------------------------------------------------ */
 /* Dust diffusion, Sect. 2.4.  The diffusion tensor is diagonal in the local
  * cylindrical basis, D_a = nu / (Sc_a (1 + St^2)) with nu = alpha c_s H_g at R
  * (Sect. 2.2), and one Euler-Maruyama step displaces a particle by

@@ -31,6 +31,9 @@ enum { GDO_DIFF_PHYSICAL = 0, GDO_DIFF_RING = 1 };  /* dust diffusion models (Se
  * (meridional plane); 2D radial-azimuthal, vertically integrated; 1D radial */
 enum { GDO_MODEL_3D = 0, GDO_MODEL_RZ = 1, GDO_MODEL_RPHI = 2, GDO_MODEL_R = 3 };
 enum { GDO_NFINE = 96, GDO_TMIN = -72 };          /* fine controller bins */
+/* optical depth forms of Sect. 2.3.2: from the 3D dust density along rays of r; in the
+ * midplane of a vertically integrated model, along R */
+enum { GDO_TAU_3D = 0, GDO_TAU_2D = 1 };
 
 /* status bits (sticky) */
 enum {
@@ -71,6 +74,17 @@ typedef struct {
   int32_t model;        /* GDO_MODEL_*: which dimensions the neighbour search and the
                            sampling measure resolve (RZ and R: global disks only) */
   int32_t pad_model;
+  /* radiation forces and the optical depth (Sect. 2.3.2; global disks) */
+  double beta0;         /* beta at the reference diameter rad_s0; 0: no radiation forces */
+  double kappa0;        /* opacity at rad_s0 for the optical depth [cm^2 g^-1]; 0: tau = 0 */
+  double rad_s0;        /* reference diameter s_0 of beta(s) and kappa(s) [cm] */
+  double t_beta;        /* taper time scale [s]; <= 0: no taper */
+  int32_t rad_pr;       /* 1: Poynting-Robertson drag */
+  int32_t tau_geom;     /* GDO_TAU_3D or GDO_TAU_2D */
+  int32_t tau_nr, tau_nmu, tau_nphi, pad_tau;  /* grid cells: radial, polar (in cos theta),
+                                                  azimuthal; tau_nr = 0: tau = 0 */
+  double tau_rmin, tau_rmax;  /* radial extent of the grid [cm] (r in 3D, R in 2D) */
+  double tau_mu;        /* 3D grid: cos theta in [-tau_mu, tau_mu] */
 } gdo_params;
 
 typedef struct {
@@ -163,6 +177,18 @@ void   gdo_push_one(const gdo_params* P, int32_t drag, double dt, double* x, dou
                     double* z, double* vr, double* lth, double* lph, double s);
 void   gdo_push(const gdo_params* P, int32_t drag, double dt, int64_t n, double* x, double* y,
                 double* z, double* vr, double* lth, double* lph, const double* s);
+/* ---- Radiation forces and the optical depth, Sect. 2.3.2 ------------------------ */
+int64_t gdo_params_size(void);
+double gdo_rad_beta(const gdo_params* P, double s);
+double gdo_rad_kappa(const gdo_params* P, double s);
+double gdo_rad_taper(const gdo_params* P, double t);
+int64_t gdo_tau_size(const gdo_params* P);
+void   gdo_tau_grid(const gdo_params* P, int64_t n, const double* x, const double* y,
+                    const double* z, const double* s, const double* M, double* T);
+double gdo_tau_at(const gdo_params* P, const double* T, double x, double y, double z);
+void   gdo_push_rad(const gdo_params* P, int32_t drag, double dt, double t, int64_t n, double* x,
+                    double* y, double* z, double* vr, double* lth, double* lph, const double* s,
+                    const double* M, double* T, double* mid);
 /* ---- Spatial groups, Sect. 2.5.3 ------------------------------------------------
  * Reading: an instance is split into G spatial groups of equal width, radial annuli
  * of a disk in R (R_in .. R_out) or slabs of a patch in x; each group has its own

@@ -52,7 +52,12 @@ class Params(C.Structure):
                 ("m0", C.c_double), ("seed", C.c_uint64), ("max_events", C.c_int64),
                 ("diff_mode", C.c_int32), ("diff_chi", C.c_int32), ("Sc_R", C.c_double),
                 ("Sc_Z", C.c_double), ("Sc_phi", C.c_double), ("D0", C.c_double),
-                ("model", C.c_int32), ("pad_model", C.c_int32)]
+                ("model", C.c_int32), ("pad_model", C.c_int32),
+                ("beta0", C.c_double), ("kappa0", C.c_double), ("rad_s0", C.c_double),
+                ("t_beta", C.c_double), ("rad_pr", C.c_int32), ("tau_geom", C.c_int32),
+                ("tau_nr", C.c_int32), ("tau_nmu", C.c_int32), ("tau_nphi", C.c_int32),
+                ("pad_tau", C.c_int32), ("tau_rmin", C.c_double), ("tau_rmax", C.c_double),
+                ("tau_mu", C.c_double)]
 
 
 class State(C.Structure):
@@ -131,6 +136,22 @@ def lib():
                                             dbl, i64, vp, vp, vp, vp, vp, vp]
             L.gdo_push_one.argtypes = [vp, C.c_int32, dbl, vp, vp, vp, vp, vp, vp, dbl]
             L.gdo_push.argtypes = [vp, C.c_int32, dbl, i64, vp, vp, vp, vp, vp, vp, vp]
+            L.gdo_params_size.argtypes = []
+            L.gdo_params_size.restype = i64
+            assert L.gdo_params_size() == C.sizeof(Params), "gdo_params layout differs"
+            L.gdo_rad_beta.argtypes = [vp, dbl]
+            L.gdo_rad_beta.restype = dbl
+            L.gdo_rad_kappa.argtypes = [vp, dbl]
+            L.gdo_rad_kappa.restype = dbl
+            L.gdo_rad_taper.argtypes = [vp, dbl]
+            L.gdo_rad_taper.restype = dbl
+            L.gdo_tau_size.argtypes = [vp]
+            L.gdo_tau_size.restype = i64
+            L.gdo_tau_grid.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
+            L.gdo_tau_at.argtypes = [vp, vp, dbl, dbl, dbl]
+            L.gdo_tau_at.restype = dbl
+            L.gdo_push_rad.argtypes = [vp, C.c_int32, dbl, dbl, i64, vp, vp, vp, vp, vp, vp, vp, vp,
+                                       vp, vp]
             L.gdo_diff_coeffs.argtypes = [vp, dbl, dbl, dbl, vp]
             L.gdo_diffuse.argtypes = [vp, dbl, i64, i64, vp, vp, vp, vp, vp, vp, vp]
             L.gdo_local_dt.argtypes = [vp, vp, dbl, dbl, dbl, dbl, vp]
@@ -333,6 +354,53 @@ def push(P: Params, x, y, z, vr, lth, lph, s, dt, drag=True):
     s = np.ascontiguousarray(s, dtype=np.float64)
     lib().gdo_push(C.byref(P), 1 if drag else 0, dt, len(x), _p(x), _p(y), _p(z), _p(vr),
                    _p(lth), _p(lph), _p(s))
+
+
+def rad_beta(P: Params, s: float) -> float:
+    """beta(s) of Sect. 2.3.2."""
+    return lib().gdo_rad_beta(C.byref(P), s)
+
+
+def rad_kappa(P: Params, s: float) -> float:
+    """kappa(s) of Sect. 2.3.2."""
+    return lib().gdo_rad_kappa(C.byref(P), s)
+
+
+def rad_taper(P: Params, t: float) -> float:
+    """The taper xi^2 (3 - 2 xi) of the radiation forces at time t."""
+    return lib().gdo_rad_taper(C.byref(P), t)
+
+
+def tau_grid(P: Params, x, y, z, s, M) -> np.ndarray:
+    """Optical depth at the radial faces of every grid column, T[column, face]
+    (column = j * nphi + k), from the particles at (x, y, z)."""
+    n = len(x)
+    size = lib().gdo_tau_size(C.byref(P))
+    T = np.zeros(max(size, 1))
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, z, s, M)]
+    lib().gdo_tau_grid(C.byref(P), n, *[_p(a) for a in arrs], _p(T))
+    return T[:size]
+
+
+def tau_at(P: Params, T, x: float, y: float, z: float) -> float:
+    """tau at one point, interpolated from the face grid T."""
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    return lib().gdo_tau_at(C.byref(P), _p(T), x, y, z)
+
+
+def push_rad(P: Params, x, y, z, vr, lth, lph, s, M, dt, t, drag=True):
+    """One staggered step with radiation forces, in place; returns the grid T built at
+    the first drift's midpoints and those midpoints (r, theta, phi) as a [3, n] array."""
+    for arr in (x, y, z, vr, lth, lph):
+        assert arr.dtype == np.float64 and arr.flags.c_contiguous
+    n = len(x)
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    T = np.zeros(max(lib().gdo_tau_size(C.byref(P)), 1))
+    mid = np.zeros(3 * max(n, 1))
+    lib().gdo_push_rad(C.byref(P), 1 if drag else 0, dt, t, n, _p(x), _p(y), _p(z), _p(vr),
+                       _p(lth), _p(lph), _p(s), _p(M), _p(T), _p(mid))
+    return T[:lib().gdo_tau_size(C.byref(P))], mid[:3 * n].reshape(3, n)
 
 
 def diff_coeffs(P: Params, R: float, Z: float, s: float) -> np.ndarray:
