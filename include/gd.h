@@ -12,7 +12,10 @@
  *                                                        (Sect. 2.5.1-2.5.3)
  *   gd_sample_collisions  Gillespie sampling of events against the frozen
  *                         neighbourhood, mass/weight updates      (Sect. 2.5.3)
- *   gd_push_staggered     staggered semi-analytic trajectory step (Sect. 2.3.3)
+ *   gd_push_staggered     staggered semi-analytic trajectory step (Sect. 2.3.3),
+ *                         with radiation forces                   (Sect. 2.3.2)
+ *   gd_optical_depth      the optical depth grid of the radiation forces
+ *                                                                 (Sect. 2.3.2)
  *   gd_stats              reductions and counters (the only call that
  *                         synchronises the stream)
  *
@@ -78,6 +81,9 @@ enum { GD_DIFF_PHYSICAL = 0, GD_DIFF_RING = 1 };   /* gd_diffuse models */
  * speeds in the midplane.  gd_push_staggered, gd_diffuse and gd_timestep move
  * and limit the 3D positions whatever the model. */
 enum { GD_MODEL_3D = 0, GD_MODEL_RZ = 1, GD_MODEL_RPHI = 2, GD_MODEL_R = 3 };
+/* Optical depth forms of Sect. 2.3.2: along r from the 3D dust density (Eq. tau_3d);
+ * along R in the midplane from the surface density over sqrt(2 pi) H_g (Eq. tau_2d). */
+enum { GD_TAU_3D = 0, GD_TAU_2D = 1 };
 enum { GD_KERNEL_PHYSICAL = 0, GD_KERNEL_CONSTANT = 1, GD_KERNEL_LINEAR = 2,
        GD_KERNEL_PRODUCT = 3 };
 
@@ -140,6 +146,26 @@ typedef struct {
                               [-box_x/2, box_x/2) (beyond the edges: the first or
                               last group); see gd_group_stats                    */
   int32_t pad_sg;
+  /* Radiation forces (Sect. 2.3.2; global disks, gd_push_staggered) and the optical
+   * depth grid (gd_push_staggered, gd_optical_depth).  beta(s) = beta0 s0/s and
+   * kappa(s) = kappa0 s0/s with s0 = rad_s0; beta0 = 0: the push has no radiation
+   * forces; kappa0 = 0 or tau_nr = 0: tau = 0.                                  */
+  double beta0;        /* radiation pressure over gravity at diameter rad_s0     */
+  double kappa0;       /* opacity at rad_s0 for the optical depth [cm^2 g^-1]     */
+  double rad_s0;       /* reference diameter s0 [cm] (> 0 when beta0 or kappa0 is) */
+  double t_beta;       /* taper time scale [s]: forces times xi^2 (3 - 2 xi),
+                          xi = min(max(t / t_beta, 0), 1) at the kick's time;
+                          <= 0: no taper                                         */
+  int32_t rad_pr;      /* 1: Poynting-Robertson drag                             */
+  int32_t tau_geom;    /* GD_TAU_3D or GD_TAU_2D                                 */
+  int32_t tau_nr;      /* grid cells in r (3D) or R (2D); 0: no grid             */
+  int32_t tau_nmu;     /* 3D: cells in mu = cos theta over [-tau_mu, tau_mu)     */
+  int32_t tau_nphi;    /* cells in phi over [-pi, pi)                            */
+  int32_t pad_tau;
+  double tau_rmin, tau_rmax;  /* radial extent of the grid [cm]                  */
+  double tau_mu;       /* 3D: polar extent, 0 < tau_mu <= 1                      */
+  double t_start;      /* the taper's clock at gd_create [s]; every push of a
+                          context with radiation forces advances it by its dt    */
 } gd_instance_params;
 
 typedef struct {
@@ -210,6 +236,8 @@ typedef struct {
                                   s in [2^((f - 75)/3), 2^((f - 74)/3)) cm (a third of an
                                   octave, ~0.1 dex; the first and last bins also take
                                   the sizes below and above); summed in a fixed order */
+  double t_rad;                /* the radiation taper's clock [s] (t_start plus the
+                                  pushes' dt in a context with radiation forces) */
 } gd_instance_stats;
 
 /* Creates a context over caller-owned particle arrays (see gd_config): the
@@ -274,6 +302,44 @@ gd_status gd_sample_collisions(gd_ctx* ctx, int32_t* ev_count_out, uint32_t* ev_
  * h l_phi / R^2, in the meridional plane by h l_theta / r^2) and scale it by
  * 1 + h v_r / r; the forces are FP64, the gas disk and the drag factor FP32. */
 gd_status gd_push_staggered(gd_ctx* ctx, double dt);
+/*
+ * With radiation forces (an instance with beta0 > 0; Sect. 2.3.2) the same step adds
+ *   f_RP = beta e^-tau GM/r^2 r_hat to the kick's radial force, and with rad_pr the
+ *   Poynting-Robertson damping gamma_PR = beta e^-tau GM/(c r^2) to the drag rates:
+ *   gamma_r = 1/t_s + 2 gamma_PR, gamma_theta = gamma_phi = 1/t_s + gamma_PR, each
+ *   component advanced exactly for fixed rates, y += k (f + y_g/t_s - gamma y),
+ *   k = (1 - e^{-gamma dt})/gamma;
+ * beta e^-tau carries the taper at the instance clock + dt/2.  tau is rebuilt every
+ * push from all particles at the midpoint of the first drift (the grid of
+ * gd_optical_depth) and interpolated at each particle's midpoint.  Such a push is
+ * four kernels (first drift with the deposit, column sums, kick with the second
+ * drift, clock); instances without beta0 take the plain step.  GD_MIXED: the cell of
+ * the deposit is decided in FP32 where certified (FP64 near a cell edge), tau is
+ * interpolated in FP32, the radiation factors are FP32 and the forces FP64.
+ */
+
+/* Sect. 2.3.2: the optical depth of every instance with a grid (tau_nr > 0 and
+ * kappa0 > 0) from the particles at their current positions.  Readings of the paper,
+ * which names neither grid nor deposit:
+ *  - cells uniform in r over [tau_rmin, tau_rmax), in mu = z/r over
+ *    [-tau_mu, tau_mu) and in phi = atan2(y, x) over [-pi, pi) (3D); in R and phi
+ *    with one polar cell (2D); a column is one (mu, phi) cell, j * tau_nphi + k;
+ *  - each particle adds kappa(s) M to the cell holding it (none outside the grid);
+ *    the cell's kappa rho_d is that sum over the cell volume (r_hi^3 - r_lo^3)/3
+ *    dmu dphi, or kappa Sigma_d / (sqrt(2 pi) H_g) over the area
+ *    (R_hi^2 - R_lo^2)/2 dphi with H_g at the cell's mid radius (2D);
+ *  - tau at the radial faces: T_0 = 0, T_{i+1} = T_i + (kappa rho_d)_i dr (no
+ *    extinction inside tau_rmin);
+ *  - at a point: linear in r between its column's faces, bilinear between the
+ *    centres of the four nearest columns (clamped at the polar edges, periodic in
+ *    phi), 0 inside tau_rmin and the outer face beyond tau_rmax.
+ * The cell sums are exact (128-bit fixed point with the scale of the instance's
+ * largest kappa M, 2^-60 of it) and independent of scheduling.
+ * tau_out: DEVICE [N] or NULL: tau at each particle (0 for instances without a grid).
+ * grid_out: DEVICE or NULL: T of the instances with a grid, in instance order, each
+ *   as [column][face] = tau_nmu' * tau_nphi * (tau_nr + 1) doubles (tau_nmu' = 1 in 2D).
+ * Returns GD_ERR_ARG if no instance has a grid.  Asynchronous. */
+gd_status gd_optical_depth(gd_ctx* ctx, double* tau_out, double* grid_out);
 
 /* Sect. 2.4: one Euler-Maruyama dust diffusion step of length dt (dt < 0: each
  * instance's last dt_exe) for every particle.  The tensor is diagonal in the

@@ -24,6 +24,7 @@ GD_ERR_NONFINITE, GD_ERR_EVENT_CAP, GD_ERR_TIMEOUT, GD_ERR_STATE = -5, -6, -7, -
 GD_FP64, GD_MIXED = 0, 1
 GD_GEOM_PATCH, GD_GEOM_DISK = 0, 1
 GD_FLAG_TIMING, GD_FLAG_NO_AUDIT = 1, 2
+GD_TAU_3D, GD_TAU_2D = 0, 1
 ST_EVENT_CAP, ST_DT_FLOOR, ST_NONFINITE, ST_KNN, ST_CAPACITY, ST_TIMEOUT = 1, 2, 4, 8, 16, 32
 TIMING_SLOTS = ("cells", "knn", "rates", "interval", "sample", "push", "stats", "diffuse")
 
@@ -39,7 +40,12 @@ class InstanceParams(C.Structure):
                 ("m0", C.c_double), ("cell_size", C.c_double), ("seed", C.c_uint64),
                 ("diff_mode", C.c_int32), ("diff_chi", C.c_int32), ("Sc_R", C.c_double),
                 ("Sc_Z", C.c_double), ("Sc_phi", C.c_double), ("D0", C.c_double),
-                ("spatial_groups", C.c_int32), ("pad_sg", C.c_int32)]
+                ("spatial_groups", C.c_int32), ("pad_sg", C.c_int32),
+                ("beta0", C.c_double), ("kappa0", C.c_double), ("rad_s0", C.c_double),
+                ("t_beta", C.c_double), ("rad_pr", C.c_int32), ("tau_geom", C.c_int32),
+                ("tau_nr", C.c_int32), ("tau_nmu", C.c_int32), ("tau_nphi", C.c_int32),
+                ("pad_tau", C.c_int32), ("tau_rmin", C.c_double), ("tau_rmax", C.c_double),
+                ("tau_mu", C.c_double), ("t_start", C.c_double)]
 
 
 class Config(C.Structure):
@@ -65,7 +71,7 @@ class InstanceStats(C.Structure):
                 ("sum_Ms", C.c_double), ("interval", C.c_int64), ("events", C.c_int64),
                 ("events_total", C.c_int64), ("near_draw", C.c_int64), ("near_dt", C.c_int64),
                 ("near_audit", C.c_int64), ("status", C.c_uint32), ("n_groups", C.c_int32),
-                ("spectrum", C.c_double * 96)]
+                ("spectrum", C.c_double * 96), ("t_rad", C.c_double)]
 
 
 class GroupStats(C.Structure):
@@ -94,6 +100,7 @@ SIGNATURES = {
     "gd_sample_collisions": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "gd_push_staggered": ([C.c_void_p, C.c_double], C.c_int),
     "gd_diffuse": ([C.c_void_p, C.c_double], C.c_int),
+    "gd_optical_depth": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "gd_collide": ([C.c_void_p, C.c_double, C.c_int32, C.c_int32, C.c_void_p], C.c_int),
     "gd_step": ([C.c_void_p, C.c_double, C.c_int32, C.c_void_p], C.c_int),
     "gd_timestep": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
@@ -173,6 +180,10 @@ def gd_push_staggered(ctx, dt):
 
 def gd_diffuse(ctx, dt):
     return _check("gd_diffuse", load().gd_diffuse(ctx, float(dt)))
+
+
+def gd_optical_depth(ctx, tau_out=0, grid_out=0):
+    return _check("gd_optical_depth", load().gd_optical_depth(ctx, tau_out or None, grid_out or None))
 
 
 def gd_collide(ctx, tau, reuse_lists=False, max_intervals=1 << 20):
@@ -346,6 +357,24 @@ class Session:
 
     def diffuse(self, dt=-1.0):
         gd_diffuse(self.ctx, dt)
+
+    def optical_depth(self, want_grid=False):
+        """tau at every particle (float64 [N]) and, with want_grid, the face grids of the
+        instances with a grid, concatenated ([column][face] each)."""
+        import torch
+        tau = torch.empty(self.N, dtype=torch.float64, device=self.device)
+        grid = None
+        if want_grid:
+            n = 0
+            for p in self._params:
+                if p.tau_nr > 0 and p.kappa0 > 0.0:
+                    nm = 1 if p.tau_geom == GD_TAU_2D else p.tau_nmu
+                    n += nm * p.tau_nphi * (p.tau_nr + 1)
+            grid = torch.empty(max(n, 1), dtype=torch.float64, device=self.device)
+        torch.cuda.synchronize(self.device)
+        gd_optical_depth(self.ctx, tau.data_ptr(), grid.data_ptr() if grid is not None else 0)
+        self.stream.synchronize()
+        return (tau, grid[:n]) if want_grid else tau
 
     def collide(self, tau, reuse_lists=False, max_intervals=1 << 20):
         return gd_collide(self.ctx, tau, reuse_lists, max_intervals)

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libgd.so")
-SOURCES = ["gd_abi.cu", "k_cells.cu", "k_knn.cu", "k_mc.cu", "k_misc.cu", "k_groups.cu", "gd_noalloc.cu"]
+SOURCES = ["gd_abi.cu", "k_cells.cu", "k_knn.cu", "k_mc.cu", "k_misc.cu", "k_groups.cu", "k_rad.cu", "gd_noalloc.cu"]
 # FMA-chain microbenchmarks of the FP32 / FP64 pipes (the bench's pipe roofline denominators)
 PEAKS_LIB = os.path.join(HERE, "libgdpeaks.so")
 PEAKS_SRC = "pipe_peaks.cu"

@@ -67,7 +67,9 @@ static void free_all(gd_ctx* c) {
                   c->d_pos64, c->d_pos32, c->d_snap64, c->d_snap32, c->d_Mr, c->d_dist, c->d_V,
                   c->d_lam, c->d_nbr, c->d_counters, c->d_sums, c->d_dprev, c->d_redo, c->d_gx,
                   c->d_pref32, c->d_contrib, c->d_MJ, c->d_part, c->d_heavy, c->d_unit_i, c->d_unit_r, c->d_gperm,
-                  c->d_uoff, c->d_utile_off, c->d_unit_inst, c->d_tcount, c->d_tbase, c->d_sb, c->d_rperm, c->d_act, c->d_aoff};
+                  c->d_uoff, c->d_utile_off, c->d_unit_inst, c->d_tcount, c->d_tbase, c->d_sb, c->d_rperm, c->d_act, c->d_aoff,
+                  c->d_col_off, c->d_tau_acc, c->d_tau_T, c->d_tau_max, c->d_tau_ci, c->d_tau_q, c->d_mid,
+                  c->d_trad, c->d_face_off};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& e : c->ev_pool) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
@@ -77,6 +79,60 @@ static void free_all(gd_ctx* c) {
 }
 
 static bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+// The instance's radiation parameters as the kernels read them, with the error bounds (in
+// cells, four times the sum of the rounding errors' bounds) of the mixed form's FP32 grid
+// coordinates: u = (r - r_min)/dr from sqrtf of the FP64 r^2, w = (z/r + mu_max)/dmu,
+// v = (atan2f(y, x) + pi)/dphi (atan2f within 3 ulp).
+static void fill_rad(InstDev& d, const gd_instance_params& p, long long cell0, long long face0) {
+  d.rad = p.geometry == GD_GEOM_DISK && p.beta0 > 0.0;
+  d.tau_on = p.tau_nr > 0 && p.kappa0 > 0.0;
+  d.rad_pr = p.rad_pr;
+  d.tau_geom = p.tau_geom;
+  d.tau_nr = d.tau_on ? p.tau_nr : 0;
+  d.tau_nm = d.tau_on ? (p.tau_geom == GD_TAU_2D ? 1 : p.tau_nmu) : 1;
+  d.tau_np = d.tau_on ? p.tau_nphi : 1;
+  d.beta0 = p.beta0; d.kappa0 = p.kappa0; d.rad_s0 = p.rad_s0; d.t_beta = p.t_beta;
+  d.tau_rmin = p.tau_rmin; d.tau_rmax = p.tau_rmax; d.tau_mu = p.tau_mu;
+  d.tau_cell0 = cell0;
+  d.tau_face0 = face0;
+  d.f_beta0 = (float)p.beta0;
+  d.f_rad_s0 = (float)p.rad_s0;
+  if (!d.tau_on) return;
+  const double dr = (p.tau_rmax - p.tau_rmin) / d.tau_nr;
+  const double dmu = p.tau_geom == GD_TAU_2D ? 1.0 : 2.0 * p.tau_mu / d.tau_nm;
+  const double dphi = 2.0 * kPi / d.tau_np;
+  d.f_tau_rmin = (float)p.tau_rmin;
+  d.f_tau_dr = (float)dr;
+  d.f_tau_mu = (float)p.tau_mu;
+  d.f_tau_dmu = (float)dmu;
+  d.f_tau_dphi = (float)dphi;
+  d.f_eu = (float)(4.0 * ((1.8e-7 * p.tau_rmax + 6e-8 * p.tau_rmin) / dr + 1.2e-7 * d.tau_nr) + 1e-5);
+  d.f_ew = (float)(4.0 * (4.2e-7 / dmu + 1.2e-7 * d.tau_nm) + 1e-5);
+  d.f_ev = (float)(4.0 * (1.2e-6 / dphi + 1.2e-7 * d.tau_np) + 1e-5);
+}
+
+// Radiation forces and the optical depth grid (Sect. 2.3.2): global disks only; a grid of
+// at most 2^28 cells per instance.
+static bool rad_params_ok(const gd_instance_params& p) {
+  const bool any = p.beta0 != 0.0 || p.kappa0 != 0.0 || p.rad_pr != 0 || p.tau_nr != 0;
+  if (!any) return true;
+  if (p.geometry != GD_GEOM_DISK) return false;
+  if (!(p.beta0 >= 0.0) || !std::isfinite(p.beta0) || !(p.kappa0 >= 0.0) || !std::isfinite(p.kappa0)) return false;
+  if ((p.beta0 > 0.0 || p.kappa0 > 0.0) && !finite_pos(p.rad_s0)) return false;
+  if (p.rad_pr != 0 && p.rad_pr != 1) return false;
+  if (!std::isfinite(p.t_beta) || !std::isfinite(p.t_start)) return false;
+  if (p.tau_nr < 0) return false;
+  if (p.tau_nr > 0) {
+    if (p.tau_geom != GD_TAU_3D && p.tau_geom != GD_TAU_2D) return false;
+    const long long nm = p.tau_geom == GD_TAU_2D ? 1 : p.tau_nmu;
+    if (nm < 1 || p.tau_nphi < 1) return false;
+    if ((long long)p.tau_nr * nm * p.tau_nphi > (1LL << 28)) return false;
+    if (!(p.tau_rmin >= 0.0) || !(p.tau_rmax > p.tau_rmin) || !std::isfinite(p.tau_rmax)) return false;
+    if (p.tau_geom == GD_TAU_3D && !(p.tau_mu > 0.0 && p.tau_mu <= 1.0)) return false;
+  }
+  return true;
+}
 
 extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
   if (!out) return GD_ERR_ARG;
@@ -107,6 +163,7 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
     if (p.diff_mode == GD_DIFF_RING && !(p.D0 >= 0.0 && std::isfinite(p.D0) && p.r0 > 0.0)) return GD_ERR_ARG;
     if (p.kernel_mode != GD_KERNEL_PHYSICAL && (!finite_pos(p.t0) || !finite_pos(p.m0))) return GD_ERR_ARG;
     if (p.spatial_groups < 0 || p.spatial_groups > kMaxSG) return GD_ERR_ARG;
+    if (!rad_params_ok(p)) return GD_ERR_ARG;
   }
   const long long N = cfg->offsets[n];
   if (N >= (1LL << 31) - 1 || (long long)N * cfg->K >= (1LL << 40)) return GD_ERR_ARG;
@@ -198,6 +255,38 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
   }
   ok &= dalloc(&c->d_counters, 16) == cudaSuccess;
   ok &= dalloc(&c->d_sums, 3 * ((size_t)n + c->n_tiles)) == cudaSuccess;
+  // radiation forces and the optical depth grid
+  std::vector<long long> col_off(n + 1, 0), face_off(n + 1, 0), cell0(n, 0), face0(n, 0);
+  for (int b = 0; b < n; ++b) {
+    const gd_instance_params& p = cfg->params[b];
+    const bool tau_on = p.tau_nr > 0 && p.kappa0 > 0.0;
+    const long long nm = p.tau_geom == GD_TAU_2D ? 1 : p.tau_nmu;
+    const long long ncol = tau_on ? nm * p.tau_nphi : 0;
+    if (p.beta0 > 0.0) c->any_rad = true;
+    if (tau_on) c->any_tau = true;
+    cell0[b] = c->tau_cells;
+    face0[b] = c->tau_faces;
+    col_off[b + 1] = col_off[b] + ncol;
+    face_off[b + 1] = face_off[b] + ncol * (tau_on ? p.tau_nr + 1 : 0);
+    c->tau_cells += ncol * (tau_on ? p.tau_nr : 0);
+    c->tau_faces += ncol * (tau_on ? p.tau_nr + 1 : 0);
+  }
+  c->tau_cols = col_off[n];
+  c->tau_out_faces = face_off[n];
+  c->any_plain_push = !c->any_rad;
+  for (int b = 0; b < n; ++b)
+    if (cfg->params[b].geometry == GD_GEOM_DISK && !(cfg->params[b].beta0 > 0.0)) c->any_plain_push = true;
+  if (c->any_rad || c->any_tau) {
+    ok &= dalloc(&c->d_tau_max, n) == cudaSuccess;
+    ok &= dalloc(&c->d_tau_ci, N) == cudaSuccess;
+    ok &= dalloc(&c->d_tau_q, N) == cudaSuccess;
+    ok &= dalloc(&c->d_trad, n) == cudaSuccess;
+    ok &= dalloc(&c->d_col_off, n + 1) == cudaSuccess;
+    ok &= dalloc(&c->d_face_off, n + 1) == cudaSuccess;
+    ok &= dalloc(&c->d_tau_acc, 2 * (size_t)c->tau_cells) == cudaSuccess;
+    ok &= dalloc(&c->d_tau_T, c->tau_faces) == cudaSuccess;
+  }
+  if (c->any_rad) ok &= dalloc(&c->d_mid, 3 * (size_t)N) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     free_all(c);
@@ -238,6 +327,7 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
     d.n = c->h_off[b + 1] - c->h_off[b];
     d.n_sg = p.spatial_groups > 1 ? p.spatial_groups : 1;
     d.unit0 = c->h_unit0[b];
+    fill_rad(d, p, cell0[b], face0[b]);
     if (p.geometry == GD_GEOM_DISK) c->any_disk = true;
     if (p.model == GD_MODEL_R) c->any_model_r = true;
     for (int g = 0; g < d.n_sg; ++g) {
@@ -263,6 +353,16 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_unit_inst, unit_inst.data(), sizeof(int) * c->U, cudaMemcpyHostToDevice, str);
     // nothing broadcast yet: the partners' sizes start as the caller's
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_sb, c->s, sizeof(double) * N, cudaMemcpyDeviceToDevice, str);
+  }
+  if (c->any_rad || c->any_tau) {
+    std::vector<double> t0(n);
+    for (int b = 0; b < n; ++b) t0[b] = c->h_params[b].t_start;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_trad, t0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, str);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_col_off, col_off.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, str);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_face_off, face_off.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, str);
+    if (e == cudaSuccess && c->tau_cells > 0)
+      e = cudaMemsetAsync(c->d_tau_acc, 0, sizeof(unsigned long long) * 2 * c->tau_cells, str);
+    if (e == cudaSuccess && c->tau_faces > 0) e = cudaMemsetAsync(c->d_tau_T, 0, sizeof(double) * c->tau_faces, str);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * 16, str);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_dprev, 0, sizeof(double) * N, str);
@@ -352,6 +452,12 @@ extern "C" gd_status gd_diffuse(gd_ctx* c, double dt) {
   if (dt < 0.0 && c->grouped) return GD_ERR_ARG;
   c->lists_valid = false;           // positions move: gd_collide must build again
   return cuda_err(launch_diffuse(c, dt));
+}
+
+extern "C" gd_status gd_optical_depth(gd_ctx* c, double* tau_out, double* grid_out) {
+  if (!c) return GD_ERR_ARG;
+  if (!c->any_tau) return GD_ERR_ARG;
+  return cuda_err(launch_optical_depth(c, tau_out, grid_out));
 }
 
 extern "C" gd_status gd_collide(gd_ctx* c, double tau, int32_t reuse_lists, int32_t max_intervals,
@@ -495,6 +601,12 @@ extern "C" gd_status gd_stats(gd_ctx* c, gd_stats_t* out, gd_instance_stats* ins
                                   c->stream) != cudaSuccess)
     return GD_ERR_CUDA;
   std::vector<double> sums(3 * (size_t)c->n_inst);
+  std::vector<double> trad(c->n_inst, 0.0);
+  if (inst_out && c->d_trad &&
+      cudaMemcpyAsync(trad.data(), c->d_trad, sizeof(double) * c->n_inst, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+    return GD_ERR_CUDA;
+  if (inst_out && !c->d_trad)
+    for (int b = 0; b < c->n_inst; ++b) trad[b] = c->h_params[b].t_start;
   cudaError_t e = cudaMemcpyAsync(st.data(), c->d_state, sizeof(StateDev) * c->U, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(sums.data(), c->d_sums, sizeof(double) * sums.size(), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -541,6 +653,7 @@ extern "C" gd_status gd_stats(gd_ctx* c, gd_stats_t* out, gd_instance_stats* ins
       o.status = status;
       o.n_groups = s.n_groups;
       std::memcpy(o.spectrum, bins[u0].spec, sizeof(o.spectrum));
+      o.t_rad = trad[b];
     }
   }
   if (out->status & GD_ST_NONFINITE) return GD_ERR_NONFINITE;

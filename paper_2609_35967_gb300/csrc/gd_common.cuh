@@ -45,6 +45,16 @@ struct InstDev {
   // spatial groups (Sect. 2.5.3): n_sg groups, whose states are units unit0 .. unit0 + n_sg - 1
   // of the state and bin arrays (unit0 = b when no instance has more than one group)
   int n_sg, unit0;
+  // radiation forces and the optical depth grid (Sect. 2.3.2)
+  int rad;             // 1: beta0 > 0 (the push takes the radiation step)
+  int tau_on;          // 1: the instance has a grid (tau_nr > 0, kappa0 > 0)
+  int rad_pr, tau_geom, tau_nr, tau_nm, tau_np, pad_rad;   // tau_nm = 1 in the 2D form
+  double beta0, kappa0, rad_s0, t_beta, tau_rmin, tau_rmax, tau_mu;
+  long long tau_cell0, tau_face0;   // the instance's first cell / face in the concatenated arrays
+  // FP32 copies for the mixed form, and the error bounds (in cells) of its FP32 grid
+  // coordinates u (radial), w (polar) and v (azimuthal)
+  float f_beta0, f_rad_s0, f_tau_rmin, f_tau_dr, f_tau_mu, f_tau_dmu, f_tau_dphi;
+  float f_eu, f_ew, f_ev;
 };
 
 constexpr int kMaxSG = 64;               // spatial groups per instance (one 64-bit mask each)

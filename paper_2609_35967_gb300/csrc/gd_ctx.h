@@ -86,6 +86,26 @@ struct gd_ctx {
   int* d_act = nullptr;                 // [N] the round's ranks (units taking part), unit by unit
   long long* d_aoff = nullptr;          // [U + 1] each unit's first entry in d_act
 
+  // radiation forces and the optical depth grid (Sect. 2.3.2)
+  bool any_rad = false;                 // some instance has beta0 > 0
+  bool any_plain_push = false;          // some disk instance has none (the plain step)
+  bool any_tau = false;                 // some instance has a grid
+  long long tau_cols = 0;               // grid columns of all instances
+  long long tau_cells = 0;              // grid cells of all instances
+  long long tau_faces = 0;              // radial faces times columns, all instances
+  long long* d_col_off = nullptr;       // [n_inst + 1] first column of each instance
+  unsigned long long* d_tau_acc = nullptr;   // [2 * tau_cells] 128-bit fixed-point cell sums
+                                        // (low, high word), [radial cell][column] per instance
+  double* d_tau_T = nullptr;            // [tau_faces] tau at the faces, [face][column]
+  unsigned long long* d_tau_max = nullptr;   // [n_inst] largest kappa M (bits) of the deposit
+  int* d_tau_ci = nullptr;              // [N] cell of each particle's deposit (-1: none)
+  double* d_tau_q = nullptr;            // [N] its kappa M
+  double* d_mid = nullptr;              // [3 N] the first drift's midpoints of the radiation
+                                        // step ((r, theta, phi) FP64 form, (x, y, z) mixed)
+  double* d_trad = nullptr;             // [n_inst] the taper's clock
+  long long tau_out_faces = 0;          // faces of gd_optical_depth's grid output
+  long long* d_face_off = nullptr;      // [n_inst + 1] each instance's first output face
+
   // sequencing: 0 nothing, 1 neighbours built, 2 rates done
   int phase = 0;
   long long intervals = 0;
@@ -137,6 +157,8 @@ cudaError_t launch_interval(gd_ctx* c);
 cudaError_t launch_sample(gd_ctx* c, int* ev_count, unsigned* ev_hash, int* near);
 cudaError_t launch_audit(gd_ctx* c);
 cudaError_t launch_push(gd_ctx* c, double dt);
+cudaError_t launch_push_rad(gd_ctx* c, double dt);     // instances with radiation forces
+cudaError_t launch_optical_depth(gd_ctx* c, double* tau_out, double* grid_out);
 cudaError_t launch_diffuse(gd_ctx* c, double dt);
 cudaError_t launch_timestep(gd_ctx* c, const gd_dt_rule& r, double* dti_out, unsigned long long* d_min,
                             unsigned long long* d_bad);

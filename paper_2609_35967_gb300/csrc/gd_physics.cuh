@@ -350,4 +350,44 @@ __device__ __forceinline__ void pair_moments(const PairOut<T>& o, T fj1, T fj2, 
   }
 }
 
+// Drift of the mixed staggered step (Sect. 2.3.3), half a step of length h: the FP64
+// position rotated by FP32 angle increments, dphi = h l_phi / R^2 about the z axis and
+// dtheta = h l_theta / r^2 in the meridional plane (cos a - 1 = -2 sin^2(a/2) and sin a in
+// FP32), then scaled by 1 + h v_r / r.  The first half takes phi, theta (both at the old
+// radius), radius; the second half the mirrored order.
+__device__ __forceinline__ void drift_f(double h, double& X, double& Y, double& Z, double VR, double LT,
+                                        double LP, bool first_half) {
+  auto phi = [&]() {
+    const double R2 = X * X + Y * Y;
+    const float dph = (float)(h * LP) / (float)R2;
+    const float s2 = sinf(0.5f * dph);
+    const double c1 = (double)(-2.0f * s2 * s2), s1 = (double)sinf(dph);
+    const double Xr = X + (c1 * X - s1 * Y), Yr = Y + (c1 * Y + s1 * X);
+    X = Xr;
+    Y = Yr;
+  };
+  auto theta = [&]() {
+    const double R = sqrt(X * X + Y * Y), r2 = R * R + Z * Z;
+    const float dth = (float)(h * LT) / (float)r2;
+    const float t2 = sinf(0.5f * dth);
+    const double ct = (double)(-2.0f * t2 * t2), st = (double)sinf(dth);
+    // theta from +z: R' = R cos + Z sin, Z' = Z cos - R sin
+    const double dR = ct * R + st * Z, dZ = ct * Z - st * R;
+    const double f = 1.0 + dR / R;
+    X *= f;
+    Y *= f;
+    Z += dZ;
+  };
+  auto radius = [&]() {
+    const double r = sqrt(X * X + Y * Y + Z * Z);
+    const double f = 1.0 + h * VR / r;
+    X *= f;
+    Y *= f;
+    Z *= f;
+  };
+  // first half: phi, theta (both at the old radius), radius; second half mirrored
+  if (first_half) { phi(); theta(); radius(); }
+  else { radius(); theta(); phi(); }
+}
+
 }  // namespace gd

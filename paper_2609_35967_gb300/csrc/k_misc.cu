@@ -19,7 +19,7 @@ __global__ void k_push(long long N, int n_inst, const long long* __restrict__ of
   if (i >= N) return;
   int b = inst_of(off, n_inst, i);
   const InstDev& p = P[b];
-  if (p.geometry != GD_GEOM_DISK) return;
+  if (p.geometry != GD_GEOM_DISK || p.rad) return;   // radiation: k_rad.cu
   double dt = dt_in < 0.0 ? st[P[b].unit0].dt_exe : dt_in;
   double X = x[i], Y = y[i], Zc = z[i], VR = vr[i], LT = lth[i], LP = lph[i];
   double r = sqrt(X * X + Y * Y + Zc * Zc);
@@ -61,41 +61,6 @@ __global__ void k_push(long long N, int n_inst, const long long* __restrict__ of
 // kick takes the forces in FP64 from direction cosines (algebraic), the gas disk, t_s and
 // the relaxation factor k in FP32, and the gas angular momentum sqrt(1 - 2 eta) sqrt(GM R)
 // in FP64 so that l_phi,g - l_phi keeps its accuracy.
-__device__ __forceinline__ void drift_f(double h, double& X, double& Y, double& Z, double VR, double LT,
-                                        double LP, bool first_half) {
-  auto phi = [&]() {
-    const double R2 = X * X + Y * Y;
-    const float dph = (float)(h * LP) / (float)R2;
-    const float s2 = sinf(0.5f * dph);
-    const double c1 = (double)(-2.0f * s2 * s2), s1 = (double)sinf(dph);
-    const double Xr = X + (c1 * X - s1 * Y), Yr = Y + (c1 * Y + s1 * X);
-    X = Xr;
-    Y = Yr;
-  };
-  auto theta = [&]() {
-    const double R = sqrt(X * X + Y * Y), r2 = R * R + Z * Z;
-    const float dth = (float)(h * LT) / (float)r2;
-    const float t2 = sinf(0.5f * dth);
-    const double ct = (double)(-2.0f * t2 * t2), st = (double)sinf(dth);
-    // theta from +z: R' = R cos + Z sin, Z' = Z cos - R sin
-    const double dR = ct * R + st * Z, dZ = ct * Z - st * R;
-    const double f = 1.0 + dR / R;
-    X *= f;
-    Y *= f;
-    Z += dZ;
-  };
-  auto radius = [&]() {
-    const double r = sqrt(X * X + Y * Y + Z * Z);
-    const double f = 1.0 + h * VR / r;
-    X *= f;
-    Y *= f;
-    Z *= f;
-  };
-  // first half: phi, theta (both at the old radius), radius; second half mirrored
-  if (first_half) { phi(); theta(); radius(); }
-  else { radius(); theta(); phi(); }
-}
-
 __global__ void k_push_f(long long N, int n_inst, const long long* __restrict__ off,
                          const InstDev* __restrict__ P, const StateDev* __restrict__ st, double dt_in,
                          double* x, double* y, double* z, double* vr, double* lth, double* lph,
@@ -104,7 +69,7 @@ __global__ void k_push_f(long long N, int n_inst, const long long* __restrict__ 
   if (i >= N) return;
   int b = inst_of(off, n_inst, i);
   const InstDev& p = P[b];
-  if (p.geometry != GD_GEOM_DISK) return;
+  if (p.geometry != GD_GEOM_DISK || p.rad) return;   // radiation: k_rad.cu
   const double dt = dt_in < 0.0 ? st[P[b].unit0].dt_exe : dt_in;
   const double h = 0.5 * dt;
   double X = x[i], Y = y[i], Zc = z[i], VR = vr[i], LT = lth[i], LP = lph[i];
@@ -518,6 +483,14 @@ __global__ void k_out_lam(long long N, const int* __restrict__ rank_of, const do
 }
 
 cudaError_t launch_push(gd_ctx* c, double dt) {
+  if (c->any_rad) {
+    cudaError_t e = launch_push_rad(c, dt);
+    if (e != cudaSuccess) return e;
+  }
+  if (!c->any_plain_push) {
+    c->moved = true;
+    return cudaSuccess;
+  }
   time_begin(c, 5);
   int blocks = (int)((c->N + 255) / 256);
   if (c->precision == GD_MIXED)

@@ -55,3 +55,31 @@ def test_create_rejects_bad_arguments_without_gpu():
     assert L.gd_create(ctypes.byref(h), ctypes.byref(cfg)) == binding.GD_ERR_ARG
     assert L.gd_build_neighbors(None, None, None) == binding.GD_ERR_ARG
     assert L.gd_stats(None, None, None) == binding.GD_ERR_ARG
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors of the header's structs have the C sizes and field offsets
+    (a C program built with gcc prints them; no GPU)."""
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    import subprocess
+    from paper_2609_35967_gb300 import binding
+    structs = {"gd_instance_params": binding.InstanceParams, "gd_config": binding.Config,
+               "gd_stats_t": binding.Stats, "gd_instance_stats": binding.InstanceStats,
+               "gd_group_stats_t": binding.GroupStats, "gd_dt_rule": binding.DtRule}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gd.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = dict(line.rsplit(" ", 1) for line in out if line)
+    for cname, py in structs.items():
+        assert int(got[cname]) == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(got[f"{cname}.{f}"]) == getattr(py, f).offset, (cname, f)
