@@ -523,6 +523,73 @@ def split_step_line(args):
             "kernels_ms_per_step": {k: v for k, v in split.items() if v > 0.0}, "status": status}
 
 
+def push_line(args):
+    """The staggered step (Sect. 2.3.3) on the 2^22 disk with velocities, plain and with the
+    radiation forces of Sect. 2.3.2 (beta0 = 0.05 at s0 = 2 um, P-R drag, a 3D optical depth
+    grid of 256 x 16 x 256 cells over 5-100 au and |z/r| < 0.2; kappa0 = 3 cm^2/g at 2 um
+    gives an outer tau of about 2 at the median column, 40 in the midplane), both forms;
+    CUDA events on the library stream.  Algorithmic bytes: the state read (x, y, z, s, v_r,
+    l_theta, l_phi; M too with radiation) and written (six FP64), and with radiation the
+    grid's accumulators read and cleared and its faces written."""
+    import torch
+    from paper_2609_35967_gb300 import binding as gd
+    from paper_2609_35967_gb300 import workloads as W
+    ins = W.disk_instance(1 << 22, seed=1, K=32, sizes=("lognormal", 10.0, 1.0), velocities=True)
+    N = len(ins["x"])
+    dt = 0.05 * ins["params"]["dt_coll"]
+    nr, nm, nph = 256, 16, 256
+    rad = dict(ins["params"], beta0=0.05, kappa0=3.0, rad_s0=2e-4, rad_pr=1, tau_geom=0, tau_nr=nr,
+               tau_nmu=nm, tau_nphi=nph, tau_rmin=5 * W.AU, tau_rmax=100 * W.AU, tau_mu=0.2)
+    hbm, peak_kind = peaks()
+
+    def timed(params, precision):
+        sess = gd.Session([dict(ins, params=params)], precision=precision, velocities=True,
+                          flags=gd.GD_FLAG_TIMING)
+        for _ in range(args.warmup):
+            sess.push_staggered(dt)
+        pre = sess.stats()["kernel_ms"]["push"]
+        st = sess.stream
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.steps):
+            sess.push_staggered(dt)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        kms = (sess.stats()["kernel_ms"]["push"] - pre) / args.steps
+        tau_max = 0.0
+        if params.get("tau_nr"):
+            tau_max = float(sess.optical_depth().max())
+        sess.close()
+        return ms, kms, tau_max
+
+    out = {"metric": "particle push steps/s (Sect. 2.3.3, with the radiation forces of Sect. 2.3.2)",
+           "unit": "particle-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "higher_is_better": True, "data": "synthetic",
+           "config": {"workload": "global disk 5-100 au, 2^22 particles with velocities, dt = dt_coll/20",
+                      "n_particles": N, "tau_grid": [nr, nm, nph]}, "forms": {}}
+    plain_b = 7 * 8 + 6 * 8
+    rad_b = 8 * 8 + 6 * 8
+    cells = nr * nm * nph
+    grid_b = cells * (16 + 16) + (nr + 1) * nm * nph * 8
+    for name, prec in (("mixed", gd.GD_MIXED), ("fp64", gd.GD_FP64)):
+        ms0, k0, _ = timed(ins["params"], prec)
+        ms1, k1, tmax = timed(rad, prec)
+        out["forms"][name] = {
+            "plain": {"ms": ms0, "value": N / (ms0 * 1e-3),
+                      "roofline": {"bound": "hbm", "achieved": plain_b * N / (k0 * 1e-3) / 1e9, "peak": hbm,
+                                   "frac": plain_b * N / (k0 * 1e-3) / 1e9 / hbm, "algo_bytes_per_particle": plain_b}},
+            "radiation": {"ms": ms1, "value": N / (ms1 * 1e-3), "tau_max": tmax,
+                          "roofline": {"bound": "hbm", "achieved": (rad_b * N + grid_b) / (k1 * 1e-3) / 1e9,
+                                       "peak": hbm, "frac": (rad_b * N + grid_b) / (k1 * 1e-3) / 1e9 / hbm,
+                                       "algo_bytes": rad_b * N + grid_b}}}
+    out["value"] = out["forms"]["mixed"]["radiation"]["value"]
+    out["ms_per_step"] = out["forms"]["mixed"]["radiation"]["ms"]
+    out["peak_kind"] = peak_kind
+    return out
+
+
 def diffusion_line(args):
     """The dust diffusion step (Sect. 2.4) alone on the 2^22 disk: positions only in the
     mixed form (FP32 draws and coefficients, FP64 positions), and with velocities (the
@@ -621,6 +688,8 @@ def main():
                     help="time the dust diffusion step alone (one JSON line, 1 GPU)")
     ap.add_argument("--split-step", action="store_true",
                     help="time whole split timesteps with gd_timestep (one JSON line, 1 GPU)")
+    ap.add_argument("--push", action="store_true",
+                    help="time the staggered step, plain and with radiation forces (one JSON line, 1 GPU)")
     ap.add_argument("--peaks", action="store_true",
                     help="measure the FP32 / FP64 FMA-pipe peaks alone (one JSON line, 1 GPU)")
     args = ap.parse_args()
@@ -669,6 +738,10 @@ def main():
     if args.split_step:
         if rank == 0:
             print(json.dumps(split_step_line(args)))
+        return
+    if args.push:
+        if rank == 0:
+            print(json.dumps(push_line(args)))
         return
 
     if world > 1:

@@ -69,7 +69,7 @@ static void free_all(gd_ctx* c) {
                   c->d_pref32, c->d_contrib, c->d_MJ, c->d_part, c->d_heavy, c->d_unit_i, c->d_unit_r, c->d_gperm,
                   c->d_uoff, c->d_utile_off, c->d_unit_inst, c->d_tcount, c->d_tbase, c->d_sb, c->d_rperm, c->d_act, c->d_aoff,
                   c->d_col_off, c->d_tau_acc, c->d_tau_T, c->d_tau_max, c->d_tau_ci, c->d_tau_q, c->d_mid,
-                  c->d_trad, c->d_face_off};
+                  c->d_trad, c->d_face_off, c->d_cell_off};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& e : c->ev_pool) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
@@ -283,6 +283,7 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
     ok &= dalloc(&c->d_trad, n) == cudaSuccess;
     ok &= dalloc(&c->d_col_off, n + 1) == cudaSuccess;
     ok &= dalloc(&c->d_face_off, n + 1) == cudaSuccess;
+    ok &= dalloc(&c->d_cell_off, n + 1) == cudaSuccess;
     ok &= dalloc(&c->d_tau_acc, 2 * (size_t)c->tau_cells) == cudaSuccess;
     ok &= dalloc(&c->d_tau_T, c->tau_faces) == cudaSuccess;
   }
@@ -354,12 +355,16 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
     // nothing broadcast yet: the partners' sizes start as the caller's
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_sb, c->s, sizeof(double) * N, cudaMemcpyDeviceToDevice, str);
   }
+  // host tables of the radiation grid (kept until the stream synchronises below)
+  std::vector<double> t0(n);
+  std::vector<long long> cell_off(cell0.begin(), cell0.end());
+  cell_off.push_back(c->tau_cells);
   if (c->any_rad || c->any_tau) {
-    std::vector<double> t0(n);
     for (int b = 0; b < n; ++b) t0[b] = c->h_params[b].t_start;
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_trad, t0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, str);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_col_off, col_off.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, str);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_face_off, face_off.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, str);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_cell_off, cell_off.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, str);
     if (e == cudaSuccess && c->tau_cells > 0)
       e = cudaMemsetAsync(c->d_tau_acc, 0, sizeof(unsigned long long) * 2 * c->tau_cells, str);
     if (e == cudaSuccess && c->tau_faces > 0) e = cudaMemsetAsync(c->d_tau_T, 0, sizeof(double) * c->tau_faces, str);

@@ -94,6 +94,7 @@ struct gd_ctx {
   long long tau_cells = 0;              // grid cells of all instances
   long long tau_faces = 0;              // radial faces times columns, all instances
   long long* d_col_off = nullptr;       // [n_inst + 1] first column of each instance
+  long long* d_cell_off = nullptr;      // [n_inst + 1] first cell of each instance
   unsigned long long* d_tau_acc = nullptr;   // [2 * tau_cells] 128-bit fixed-point cell sums
                                         // (low, high word), [radial cell][column] per instance
   double* d_tau_T = nullptr;            // [tau_faces] tau at the faces, [face][column]

@@ -1,7 +1,7 @@
 // k_rad.cu -- radiation pressure and Poynting-Robertson drag (Sect. 2.3.2) in the staggered
 // semi-analytic step (Sect. 2.3.3), and the optical depth grid they see.
 //
-// One radiation step is four kernels:
+// One radiation step is five kernels:
 //   k_rad_drift   first half drift of every particle of an instance with beta0 > 0; the
 //                 midpoint goes to d_mid and, for instances with a grid, the particle's cell
 //                 and kappa(s) M to d_tau_ci / d_tau_q, with the instance's largest kappa M
@@ -9,8 +9,9 @@
 //   k_tau_deposit each particle's kappa M in 128-bit fixed point, scaled by 2^(60 - e) for
 //                 the instance's largest value < 2^e, added to its cell (two 64-bit words,
 //                 the carry counted in the high word): exact, so independent of order;
-//   k_tau_columns one thread per column: cell sums over the cell volumes, the radial prefix
-//                 of the faces (kappa rho_d dr), and the accumulators cleared for the next use;
+//   k_tau_cells   one thread per cell: its sum over its volume times dr (the accumulators
+//                 cleared for the next use);
+//   k_tau_columns one thread per column: the radial prefix of those increments at the faces;
 //   k_rad_kick    tau interpolated at the midpoint, the kick with the radiation force and the
 //                 P-R damping, the second half drift;
 // then k_rad_clock advances each instance's taper clock by its dt.
@@ -186,14 +187,39 @@ __device__ __forceinline__ double rad_taper(const InstDev& p, double t) {
   return xi * xi * (3.0 - 2.0 * xi);
 }
 
-__device__ __forceinline__ void deposit_note(const InstDev& p, int b, long long i, int cell, double s, double M,
-                                             int* __restrict__ ci, double* __restrict__ q,
-                                             unsigned long long* __restrict__ qmax) {
+// Records a particle's deposit (its cell, -1 for none, and kappa(s) M); returns the bits of
+// kappa M (0: none) for the instance maximum.
+__device__ __forceinline__ unsigned long long deposit_note(const InstDev& p, long long i, int cell, double s,
+                                                           double M, int* __restrict__ ci,
+                                                           double* __restrict__ q) {
   ci[i] = cell;
-  if (cell < 0) return;
+  if (cell < 0) return 0ull;
   const double v = p.kappa0 * (p.rad_s0 / s) * M;
   q[i] = v;
-  atomicMax(&qmax[b], (unsigned long long)__double_as_longlong(v));
+  return (unsigned long long)__double_as_longlong(v);
+}
+
+// The instance maximum of the deposits' bits (positive doubles order as integers).  Every
+// thread of the 256-thread block calls it: a block inside one instance reduces over warps
+// and shared memory to one atomicMax; a block across an instance boundary takes one per lane.
+__device__ __forceinline__ void block_max(long long N, int n_inst, const long long* __restrict__ off, int b,
+                                          unsigned long long v, unsigned long long* __restrict__ qmax) {
+  __shared__ unsigned long long sm[8];
+  const long long i0 = (long long)blockIdx.x * blockDim.x;
+  const int b_lo = inst_of(off, n_inst, i0);
+  const int b_hi = inst_of(off, n_inst, min(N - 1, i0 + (long long)blockDim.x - 1));
+  if (b_lo != b_hi) {
+    if (v) atomicMax(&qmax[b], v);
+    return;
+  }
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long m = 0ull;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, sm[w]);
+    if (m) atomicMax(&qmax[b_lo], m);
+  }
 }
 
 // ---------------------------------------------------------------- kernels
@@ -211,39 +237,42 @@ __global__ void __launch_bounds__(256) k_rad_drift(long long N, int n_inst, cons
                                                    int* __restrict__ ci, double* __restrict__ q,
                                                    unsigned long long* __restrict__ qmax) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const int b = inst_of(off, n_inst, i);
+  const int b = inst_of(off, n_inst, min(i, N - 1));
   const InstDev& p = P[b];
-  if (!p.rad || p.geometry != GD_GEOM_DISK) { ci[i] = -1; return; }
-  const double dt = dt_in < 0.0 ? st[p.unit0].dt_exe : dt_in;
-  const double h = 0.5 * dt;
-  double X = x[i], Y = y[i], Zc = z[i];
-  const double VR = vr[i], LT = lth[i], LP = lph[i];
-  int cell = -1;
-  if (kMixed) {
-    drift_f(h, X, Y, Zc, VR, LT, LP, true);
-    mid[i] = X;
-    mid[N + i] = Y;
-    mid[2 * N + i] = Zc;
-    if (p.tau_on) cell = tau_cell_mixed(p, X, Y, Zc);
-  } else {
-    double r = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(X, X), __dmul_rn(Y, Y)), __dmul_rn(Zc, Zc)));
-    double th = acos(Zc / r);
-    double ph = atan2(Y, X);
-    const double sth = sin(th);
-    ph = __dadd_rn(ph, __ddiv_rn(__dmul_rn(h, LP), __dmul_rn(__dmul_rn(__dmul_rn(r, r), sth), sth)));
-    th = __dadd_rn(th, __ddiv_rn(__dmul_rn(h, LT), __dmul_rn(r, r)));
-    r = __dadd_rn(r, __dmul_rn(h, VR));
-    mid[i] = r;
-    mid[N + i] = th;
-    mid[2 * N + i] = ph;
-    if (p.tau_on) {
-      const double rad = p.tau_geom == GD_TAU_2D ? __dmul_rn(r, sin(th)) : r;
-      const double mu = p.tau_geom == GD_TAU_2D ? 0.0 : cos(th);
-      cell = tau_cell64(p, rad, mu, fold_phi(ph));
+  unsigned long long v = 0ull;
+  if (i < N && !(p.rad && p.geometry == GD_GEOM_DISK)) ci[i] = -1;
+  if (i < N && p.rad && p.geometry == GD_GEOM_DISK) {
+    const double dt = dt_in < 0.0 ? st[p.unit0].dt_exe : dt_in;
+    const double h = 0.5 * dt;
+    double X = x[i], Y = y[i], Zc = z[i];
+    const double VR = vr[i], LT = lth[i], LP = lph[i];
+    int cell = -1;
+    if (kMixed) {
+      drift_f(h, X, Y, Zc, VR, LT, LP, true);
+      mid[i] = X;
+      mid[N + i] = Y;
+      mid[2 * N + i] = Zc;
+      if (p.tau_on) cell = tau_cell_mixed(p, X, Y, Zc);
+    } else {
+      double r = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(X, X), __dmul_rn(Y, Y)), __dmul_rn(Zc, Zc)));
+      double th = acos(Zc / r);
+      double ph = atan2(Y, X);
+      const double sth = sin(th);
+      ph = __dadd_rn(ph, __ddiv_rn(__dmul_rn(h, LP), __dmul_rn(__dmul_rn(__dmul_rn(r, r), sth), sth)));
+      th = __dadd_rn(th, __ddiv_rn(__dmul_rn(h, LT), __dmul_rn(r, r)));
+      r = __dadd_rn(r, __dmul_rn(h, VR));
+      mid[i] = r;
+      mid[N + i] = th;
+      mid[2 * N + i] = ph;
+      if (p.tau_on) {
+        const double rad = p.tau_geom == GD_TAU_2D ? __dmul_rn(r, sin(th)) : r;
+        const double mu = p.tau_geom == GD_TAU_2D ? 0.0 : cos(th);
+        cell = tau_cell64(p, rad, mu, fold_phi(ph));
+      }
     }
+    v = deposit_note(p, i, cell, s[i], M[i], ci, q);
   }
-  deposit_note(p, b, i, cell, s[i], M[i], ci, q, qmax);
+  block_max(N, n_inst, off, b, v, qmax);
 }
 
 // Cells of the particles at their current positions (gd_optical_depth), FP64 coordinates.
@@ -254,21 +283,24 @@ __global__ void __launch_bounds__(256) k_tau_bin(long long N, int n_inst, const 
                                                  int* __restrict__ ci, double* __restrict__ q,
                                                  unsigned long long* __restrict__ qmax) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const int b = inst_of(off, n_inst, i);
+  const int b = inst_of(off, n_inst, min(i, N - 1));
   const InstDev& p = P[b];
-  int cell = -1;
-  if (p.tau_on) {
-    const double X = x[i], Y = y[i], Zc = z[i];
-    const double R2 = __dadd_rn(__dmul_rn(X, X), __dmul_rn(Y, Y));
-    if (p.tau_geom == GD_TAU_2D) {
-      cell = tau_cell64(p, __dsqrt_rn(R2), 0.0, atan2(Y, X));
-    } else {
-      const double r = __dsqrt_rn(__dadd_rn(R2, __dmul_rn(Zc, Zc)));
-      cell = tau_cell64(p, r, __ddiv_rn(Zc, r), atan2(Y, X));
+  unsigned long long v = 0ull;
+  if (i < N) {
+    int cell = -1;
+    if (p.tau_on) {
+      const double X = x[i], Y = y[i], Zc = z[i];
+      const double R2 = __dadd_rn(__dmul_rn(X, X), __dmul_rn(Y, Y));
+      if (p.tau_geom == GD_TAU_2D) {
+        cell = tau_cell64(p, __dsqrt_rn(R2), 0.0, atan2(Y, X));
+      } else {
+        const double r = __dsqrt_rn(__dadd_rn(R2, __dmul_rn(Zc, Zc)));
+        cell = tau_cell64(p, r, __ddiv_rn(Zc, r), atan2(Y, X));
+      }
     }
+    v = deposit_note(p, i, cell, s[i], M[i], ci, q);
   }
-  deposit_note(p, b, i, cell, s[i], M[i], ci, q, qmax);
+  block_max(N, n_inst, off, b, v, qmax);
 }
 
 // Each particle's kappa M into its cell: 128-bit fixed point, q 2^(60 - e) rounded to an
@@ -292,49 +324,71 @@ __global__ void __launch_bounds__(256) k_tau_deposit(long long N, int n_inst, co
   if (old + v < old) atomicAdd(&a[1], 1ull);
 }
 
-// One thread per column: (kappa rho_d)_i = sum_i / V_i, T_0 = 0, T_{i+1} = T_i + (kappa rho_d)_i dr,
-// with the oracle's correctly rounded steps for the volumes and the prefix; clears the
-// column's accumulators.
+// One thread per cell: its increment (kappa rho_d)_i dr = (sum_i / V_i) dr into the slot of
+// its outer face, with the oracle's correctly rounded steps for the volume; the cell's
+// accumulators cleared for the next use.
+__global__ void __launch_bounds__(256) k_tau_cells(long long n_cells, int n_inst,
+                                                   const long long* __restrict__ cell_off,
+                                                   const InstDev* __restrict__ P,
+                                                   const unsigned long long* __restrict__ qmax,
+                                                   unsigned long long* __restrict__ acc, double* __restrict__ T) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n_cells) return;
+  const int b = inst_of(cell_off, n_inst, g);
+  const InstDev& p = P[b];
+  const long long l = g - cell_off[b];
+  const int ncol = p.tau_nm * p.tau_np;
+  const int i = (int)(l / ncol), col = (int)(l % ncol);
+  int e;
+  frexp(__longlong_as_double((long long)qmax[b]), &e);
+  unsigned long long* a = acc + 2 * (p.tau_cell0 + l);
+  const unsigned long long lo = a[0], hi = a[1];
+  a[0] = 0ull;
+  a[1] = 0ull;
+  const double A = ldexp(__dadd_rn(__dmul_rn((double)hi, 18446744073709551616.0), (double)lo), e - 60);
+  const double dr = __ddiv_rn(__dsub_rn(p.tau_rmax, p.tau_rmin), (double)p.tau_nr);
+  const double dphi = __ddiv_rn(kTwoPi, (double)p.tau_np);
+  const double r_lo = __dadd_rn(p.tau_rmin, __dmul_rn((double)i, dr));
+  const double r_hi = __dadd_rn(p.tau_rmin, __dmul_rn((double)(i + 1), dr));
+  double V;
+  if (p.tau_geom == GD_TAU_2D) {
+    const Gas gs = gas_RZ(p, __dadd_rn(p.tau_rmin, __dmul_rn((double)i + 0.5, dr)), 0.0);
+    V = __dmul_rn(__dmul_rn(__ddiv_rn(__dsub_rn(__dmul_rn(r_hi, r_hi), __dmul_rn(r_lo, r_lo)), 2.0), dphi),
+                  __dmul_rn(sqrt(2.0 * kPi), gs.H));
+  } else {
+    const double dmu = __ddiv_rn(2.0 * p.tau_mu, (double)p.tau_nm);
+    const double c3 = __dsub_rn(__dmul_rn(__dmul_rn(r_hi, r_hi), r_hi), __dmul_rn(__dmul_rn(r_lo, r_lo), r_lo));
+    V = __dmul_rn(__dmul_rn(__ddiv_rn(c3, 3.0), dmu), dphi);
+  }
+  T[p.tau_face0 + (long long)(i + 1) * ncol + col] = __dmul_rn(__ddiv_rn(A, V), dr);
+}
+
+// One thread per column: T_0 = 0, T_{i+1} = T_i + increment_i, in the oracle's order; the
+// increments are read eight at a time ahead of their adds.
 __global__ void __launch_bounds__(128) k_tau_columns(long long n_cols, int n_inst,
                                                      const long long* __restrict__ col_off,
-                                                     const InstDev* __restrict__ P,
-                                                     const unsigned long long* __restrict__ qmax,
-                                                     unsigned long long* __restrict__ acc, double* __restrict__ T) {
+                                                     const InstDev* __restrict__ P, double* __restrict__ T) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n_cols) return;
   const int b = inst_of(col_off, n_inst, g);
   const InstDev& p = P[b];
   const int col = (int)(g - col_off[b]);
   const int nr = p.tau_nr, ncol = p.tau_nm * p.tau_np;
-  int e;
-  frexp(__longlong_as_double((long long)qmax[b]), &e);
-  const double dr = __ddiv_rn(__dsub_rn(p.tau_rmax, p.tau_rmin), (double)nr);
-  const double dmu = __ddiv_rn(2.0 * p.tau_mu, (double)p.tau_nm);
-  const double dphi = __ddiv_rn(kTwoPi, (double)p.tau_np);
-  unsigned long long* a = acc + 2 * (p.tau_cell0 + col);
   double* Tc = T + p.tau_face0 + col;
+  Tc[0] = 0.0;
   double sum = 0.0;
-  for (int i = 0; i < nr; ++i) {
-    const long long o = 2LL * i * ncol;
-    const unsigned long long lo = a[o], hi = a[o + 1];
-    a[o] = 0ull;
-    a[o + 1] = 0ull;
-    const double A = ldexp(__dadd_rn(__dmul_rn((double)hi, 18446744073709551616.0), (double)lo), e - 60);
-    const double r_lo = __dadd_rn(p.tau_rmin, __dmul_rn((double)i, dr));
-    const double r_hi = __dadd_rn(p.tau_rmin, __dmul_rn((double)(i + 1), dr));
-    double V;
-    if (p.tau_geom == GD_TAU_2D) {
-      const Gas gs = gas_RZ(p, __dadd_rn(p.tau_rmin, __dmul_rn((double)i + 0.5, dr)), 0.0);
-      V = __dmul_rn(__dmul_rn(__ddiv_rn(__dsub_rn(__dmul_rn(r_hi, r_hi), __dmul_rn(r_lo, r_lo)), 2.0), dphi),
-                    __dmul_rn(sqrt(2.0 * kPi), gs.H));
-    } else {
-      const double c3 = __dsub_rn(__dmul_rn(__dmul_rn(r_hi, r_hi), r_hi), __dmul_rn(__dmul_rn(r_lo, r_lo), r_lo));
-      V = __dmul_rn(__dmul_rn(__ddiv_rn(c3, 3.0), dmu), dphi);
+  for (int i0 = 1; i0 <= nr; i0 += 8) {
+    double inc[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) inc[u] = i0 + u <= nr ? Tc[(long long)(i0 + u) * ncol] : 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (i0 + u <= nr) {
+        sum = __dadd_rn(sum, inc[u]);
+        Tc[(long long)(i0 + u) * ncol] = sum;
+      }
     }
-    Tc[(long long)i * ncol] = sum;
-    sum = __dadd_rn(sum, __dmul_rn(__ddiv_rn(A, V), dr));
   }
-  Tc[(long long)nr * ncol] = sum;
 }
 
 // The kick at the midpoint with the radiation force and the P-R damping, and the second
@@ -475,9 +529,11 @@ static cudaError_t tau_sums(gd_ctx* c) {
   const int blocks = (int)((c->N + 255) / 256);
   k_tau_deposit<<<blocks, 256, 0, c->stream>>>(c->N, c->n_inst, c->d_off, c->d_inst, c->d_tau_ci, c->d_tau_q,
                                                c->d_tau_max, c->d_tau_acc);
-  k_tau_columns<<<(int)((c->tau_cols + 127) / 128), 128, 0, c->stream>>>(
-      c->tau_cols, c->n_inst, c->d_col_off, c->d_inst, c->d_tau_max, c->d_tau_acc, c->d_tau_T);
-  c->launches += 2;
+  k_tau_cells<<<(int)((c->tau_cells + 255) / 256), 256, 0, c->stream>>>(
+      c->tau_cells, c->n_inst, c->d_cell_off, c->d_inst, c->d_tau_max, c->d_tau_acc, c->d_tau_T);
+  k_tau_columns<<<(int)((c->tau_cols + 127) / 128), 128, 0, c->stream>>>(c->tau_cols, c->n_inst, c->d_col_off,
+                                                                        c->d_inst, c->d_tau_T);
+  c->launches += 3;
   return cudaGetLastError();
 }
 
