@@ -266,6 +266,7 @@ def measure_form(gd, insts, dev, precision, steps, warmup, world, push=False, gr
            "cell_xsplit": xs, "knn_redo": post["knn_redo"] - pre["knn_redo"],
            "rate_redo": post["rate_redo"] - pre["rate_redo"],
            "sample_redo": post["sample_redo"] - pre["sample_redo"],
+           "sample_deferred": post["sample_deferred"] - pre["sample_deferred"],
            "dt_exe": post["instances"][0]["dt_exe"]}
     sess.close()
     return res
@@ -833,7 +834,8 @@ def result_line(r, args, world):
         "events_per_step": r["mixed"]["events"] / args.steps,
         "knn_fp64_redo_per_step": r["mixed"].get("knn_redo", 0) / args.steps,
         "mixed_fp64_settled_per_step": {"rates": r["mixed"]["rate_redo"] / args.steps,
-                                        "sampling": r["mixed"]["sample_redo"] / args.steps},
+                                        "sampling": r["mixed"]["sample_redo"] / args.steps,
+                                        "sampling_deferred": r["mixed"]["sample_deferred"] / args.steps},
         "roofline": roofline_of(km, kc, K, N, r["hbm"], r["peak_kind"], args.workload, r.get("pipe_peaks"),
                                 (r["mixed"]["clocks"] or {}).get("sm_mhz"), r.get("num_sms")),
         "kernels_ms_per_step": {k: v / args.steps for k, v in km.items() if v > 0 and k != "stats"},

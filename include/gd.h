@@ -214,6 +214,9 @@ typedef struct {
                                   error bounds could not certify, redone in FP64 */
   int64_t sample_redo;         /* mixed form: particles with an uncertified sampling
                                   decision, replayed in FP64 (all intervals) */
+  int64_t sample_deferred;     /* of those, heavy particles whose open time decision
+                                  the deferred FP64 pass settled from their logged
+                                  events (all intervals) */
 } gd_stats_t;
 
 /* Per-instance state and reductions (gd_stats). */

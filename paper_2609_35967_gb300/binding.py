@@ -62,7 +62,7 @@ class Stats(C.Structure):
                 ("near_dt", C.c_int64), ("near_audit", C.c_int64), ("launches", C.c_int64),
                 ("status", C.c_uint32), ("n_instances", C.c_int32),
                 ("kernel_ms", C.c_double * 8), ("kernel_calls", C.c_int64 * 8), ("knn_redo", C.c_int64),
-                ("rate_redo", C.c_int64), ("sample_redo", C.c_int64)]
+                ("rate_redo", C.c_int64), ("sample_redo", C.c_int64), ("sample_deferred", C.c_int64)]
 
 
 class InstanceStats(C.Structure):

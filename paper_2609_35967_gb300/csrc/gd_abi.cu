@@ -1,5 +1,6 @@
 // gd_abi.cu -- the C ABI of include/gd.h: argument checks, the library-owned memory
 // plan, call sequencing, per-kernel event timing, CUDA-graph replay and gd_stats.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -69,7 +70,7 @@ static void free_all(gd_ctx* c) {
                   c->d_pref32, c->d_contrib, c->d_MJ, c->d_part, c->d_heavy, c->d_unit_i, c->d_unit_r, c->d_gperm,
                   c->d_uoff, c->d_utile_off, c->d_unit_inst, c->d_tcount, c->d_tbase, c->d_sb, c->d_rperm, c->d_act, c->d_aoff,
                   c->d_col_off, c->d_tau_acc, c->d_tau_T, c->d_tau_max, c->d_tau_ci, c->d_tau_q, c->d_mid,
-                  c->d_trad, c->d_face_off, c->d_cell_off};
+                  c->d_trad, c->d_face_off, c->d_cell_off, c->d_dlog, c->d_defer, c->d_dstate};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& e : c->ev_pool) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
@@ -235,6 +236,14 @@ extern "C" gd_status gd_create(gd_ctx** out, const gd_config* cfg) {
   if (c->precision == GD_MIXED) {
     ok &= dalloc(&c->d_gx, N) == cudaSuccess;
     ok &= dalloc(&c->d_pref32, N) == cudaSuccess;
+    // the heavy particles' event logs (about 2 lambda*_i dt_exe + 64 entries each) and
+    // the deferred FP64 settlement's records and states
+    c->dlog_cap = std::min(std::max(1LL << 20, N), 1LL << 23);
+    c->defer_cap = 256;
+    c->dstate_cap = 1LL << 18;
+    ok &= dalloc(&c->d_dlog, c->dlog_cap) == cudaSuccess;
+    ok &= dalloc(&c->d_defer, c->defer_cap) == cudaSuccess;
+    ok &= dalloc(&c->d_dstate, c->dstate_cap) == cudaSuccess;
   }
   ok &= dalloc(reinterpret_cast<Contrib64**>(&c->d_contrib), N) == cudaSuccess;
   ok &= dalloc(&c->d_MJ, N) == cudaSuccess;
@@ -640,6 +649,7 @@ extern "C" gd_status gd_stats(gd_ctx* c, gd_stats_t* out, gd_instance_stats* ins
       out->knn_redo += g.knn_redo;
       out->rate_redo += g.rate_redo;
       out->sample_redo += g.sample_redo;
+      out->sample_deferred += g.sample_deferred;
     }
     out->events += events_total;
     out->near_draw += near_draw;

@@ -59,6 +59,26 @@ struct InstDev {
 
 constexpr int kMaxSG = 64;               // spatial groups per instance (one 64-bit mask each)
 
+// Mixed-form sampler: a heavy particle whose time decision the FP32 bounds leave open is
+// settled by a deferred FP64 pass from its logged events, its states spread over the SMs.
+struct DeferRec {
+  long long r;       // rank
+  long long lbase;   // first entry of its event log
+  long long sbase;   // first entry of its states
+  int n;             // logged events (states 0 .. n)
+  int ok;            // 0: no room for its states (the particle is replayed in line)
+};
+struct DState {
+  double s, m;       // diameter and mass after k events (the FP64 form's arithmetic)
+  double lam, dt;    // lambda*_i at the state and the waiting time drawn from it
+  double J, ncoll;   // |ln s'/s| of the event leaving the state; the chosen pair's N_coll
+  int sset;          // 1: s is set, 0: s = cbrt(6 m / (pi rho_o)) (formed by the state pass)
+  int chosen, j, outcome;   // the FP64 choice at the state
+  int np, nc;        // near ties of the pairs' thresholds and of the channel choice
+  int bad;           // the logged choice differs from the FP64 one
+  int pad;
+};
+
 // Coordinates of the neighbour search in the instance's collision model (Sect. 2.5.1):
 // 3D positions, the meridional plane (R, Z, 0), the midplane (x, y, 0) or (R, 0, 0).  R is
 // the correctly rounded sqrt(x*x + y*y) without contraction, as the oracle forms it.
@@ -115,6 +135,7 @@ struct StateDev {
   long long knn_redo;       // mixed K-NN queries redone in FP64
   long long rate_redo;      // mixed rates redone in FP64
   long long sample_redo;    // mixed sampling replayed in FP64
+  long long sample_deferred;  // of those, settled by the deferred FP64 pass
   double tau;               // length of the current collision step (0: dt_coll)
   int hold;                 // 1: idle once the current collision step is used up (gd_collide)
   int pad_hold;

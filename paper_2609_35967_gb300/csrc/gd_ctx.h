@@ -63,6 +63,13 @@ struct gd_ctx {
                                         // sum of |ln s'/s|
   double* d_part = nullptr;             // [kBinQ * kNFine * n_btiles] per-tile fine-bin partial sums
   unsigned long long* d_counters = nullptr;  // [16] spare device counters
+  // mixed form: the heavy particles' event logs and the deferred FP64 settlement
+  int4* d_dlog = nullptr;               // [dlog_cap] (chosen, j, outcome, N_coll) per event
+  long long dlog_cap = 0;
+  gd::DeferRec* d_defer = nullptr;      // [defer_cap]
+  int defer_cap = 0;
+  gd::DState* d_dstate = nullptr;       // [dstate_cap]
+  long long dstate_cap = 0;
   double* d_sums = nullptr;             // [3 * (n_inst + n_tiles)] gd_stats sums, then per-tile partials
 
   // spatial groups (Sect. 2.5.3).  Units: one state and bin entry per group of each

@@ -55,6 +55,14 @@ struct McArgs {
   const int* unit_inst;       // spatial groups: instance of each unit
   const int* heavy;           // sampler: particles expecting more than kHeavy events, one warp each
   const unsigned long long* heavy_n; //   first (their number; nullptr: no such list)
+  // mixed form: the heavy particles' event logs and the deferred FP64 settlement (nullptr: none)
+  int4* dlog;
+  long long dlog_cap;
+  unsigned long long* dctr;   // [3]: log entries reserved, particles deferred, state entries reserved
+  DeferRec* defer;
+  int defer_cap;
+  DState* dstate;
+  long long dstate_cap;
 };
 
 // Particles expecting more events than this in an interval (lambda*_i dt_exe) are sampled one
@@ -922,8 +930,39 @@ __global__ void k_interval(const InstDev* __restrict__ P, StateDev* st, BinsDev*
 // lambda*_i; with choose, the channel the FP64 prefix selects for the draw (uw0, uw1) and its
 // partner, outcome, N_coll and psi.  Near ties are counted at the FP64 tolerance (1e-10).
 // Rare (only decisions the FP32 values cannot certify), so it is kept out of line.
+// lambda*_i of rank r at its snapshot state as the FP64 rate kernel forms it -- its pair
+// terms summed in slot order -- with the pairs evaluated by the whole warp (lane = slot) and
+// the sum taken in that order through shuffles (every lane returns it).
+template <int S>
+__device__ __forceinline__ double lam0_fp64(const McArgs& A, long long r, int lane) {
+  const int b = inst_of(A.off, A.n_inst, r);
+  const InstDev& P = A.P[b];
+  const Snap64 sn = A.snap64[r];
+  const Gas g = gas_of(P, A.pos64[r]);
+  const Fixed<double> f = make_fixed<double>(P, g, A.V[r], A.Mr[r], A.K);
+  const Query<double> q = live_query<double>(f, sn.s, sn.m);
+  double c0[S], c1[S];
+  int jr[S];
+  PairOut<double> po[S];
+  lane_channels<double, S>(A, q, sn.m, r, lane, c0, c1, jr, po);
+  double tot = 0.0;
+  for (int src = 0; src < 32; ++src) {
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+      const double a = __shfl_sync(FULLM, c0[t], src);
+      const double bb = __shfl_sync(FULLM, c1[t], src);
+      if (src * S + t < A.K) {
+        tot = __dadd_rn(tot, a);
+        tot = __dadd_rn(tot, bb);
+      }
+    }
+  }
+  return f.pref * tot;
+}
+
 struct Fp64Pick {
   int chosen, j, outcome, near;
+  int near_pair;      // the near ties of the pairs' thresholds alone (part of near)
   double ncoll, psi, lam;
 };
 
@@ -942,6 +981,7 @@ __device__ __noinline__ Fp64Pick fp64_event(const McArgs& A, long long rp, int b
 #pragma unroll
   for (int t = 0; t < S; ++t)
     if (jr[t] >= 0 && !po[t].cert) near++;
+  int near_pair = near;
   const double incl = warp_incl_scan(v, lane);
   const double tot = __shfl_sync(FULLM, incl, 31);
   Fp64Pick r;
@@ -995,10 +1035,47 @@ __device__ __noinline__ Fp64Pick fp64_event(const McArgs& A, long long rp, int b
     }
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) near += __shfl_xor_sync(FULLM, near, o);
+  for (int o = 16; o > 0; o >>= 1) {
+    near += __shfl_xor_sync(FULLM, near, o);
+    near_pair += __shfl_xor_sync(FULLM, near_pair, o);
+  }
   r.near = near;
+  r.near_pair = near_pair;
   return r;
 }
+
+// The FP64 form's update of (s, m) by one event of outcome `outcome` on channel ch with the
+// frozen partner pj (Sect. 2.5.2, Eq. frag); sset = 0: s is left to s_of_m64 (s must be set
+// for a fragmentation).  Shared by the FP64 sampler and the deferred settlement so that both
+// form the same states.
+__device__ __forceinline__ double s_of_m64(double rho_s, double m) { return cbrt(6.0 * m / (kPi * rho_s)); }
+
+__device__ __forceinline__ void event64(double rho_s, double s_min, unsigned k0, unsigned k1, const Snap64& pj,
+                                        int ch, int outcome, double ncoll, unsigned il, unsigned iv, unsigned e,
+                                        double& s, double& m, int& sset) {
+  if (outcome == 0) {
+    m = __fma_rn(ncoll, pj.m, m);
+    sset = 0;
+  } else if (outcome == 1 && ch == 0) {
+    m = __fma_rn(-ncoll, pj.m, m);
+    sset = 0;
+  } else if (outcome == 1) {
+    m = pj.m;
+    s = pj.s;
+    sset = 1;
+  } else {
+    const U4 w2 = philox(il, iv, e, 1u, k0, k1);
+    const double U = u01(w2.x, w2.y);
+    const double a = sqrt(s_min), bq = sqrt(s);
+    const double xr = __fma_rn(U, bq - a, a);
+    s = xr * xr;
+    m = kPi * rho_s * s * s * s / 6.0;
+    sset = 1;
+  }
+}
+
+// Heavy particles with fewer logged events than this keep the in-line FP64 replay.
+constexpr int kDeferMin = 32;
 
 // Work items are taken from a counter: first the heavy particles (more than kHeavy events
 // expected), one per warp, then chunks of 32 ranks (lane = particle): event counts are
@@ -1042,20 +1119,20 @@ __global__ void k_heavy(McArgs A, int* __restrict__ heavy, unsigned long long* h
 
 // One work item of the sampler (a chunk of 32 particles, lane = particle, or one particle
 // for the whole warp): the first waiting times, then each event particle's chain with the
-// warp (lane = slot), then the results.  fresh: lambda*_i formed here in FP64 (the replay)
-// rather than read from the rate kernel.
+// warp (lane = slot), then the results.  fresh: lambda*_i is lam_fresh, formed in FP64 by
+// the caller (the replay), rather than read from the rate kernel.
 template <int S>
 __device__ __noinline__ void replay64(McArgs A, long long r, int lane);
 
 template <typename T, int S>
 __device__ __forceinline__ void sample_item(const McArgs& A, const int lane, const bool one, const bool fresh,
-                                            const long long r, bool valid) {
+                                            const long long r, bool valid, const double lam_fresh = 0.0) {
   constexpr bool kMixed = sizeof(T) == 4;
   const float u = kU32;
   int b = 0, ub = 0;   // instance and unit (spatial group) of the particle
   double lam = 0.0, dtw = 0.0, us = 0.0, dt_exe = 0.0;
   unsigned ival = 0, i_loc = 0, key0 = 0, key1 = 0, usw0 = 0, usw1 = 0;
-  bool ev = false, replay = false;
+  bool ev = false, replay = false, deferred = false;
   int nn = 0;
   float eta_lam = 0.0f;   // mixed form: error bound of the first waiting time
   if (valid) {
@@ -1072,14 +1149,7 @@ __device__ __forceinline__ void sample_item(const McArgs& A, const int lane, con
     key1 = P.key1;
     i_loc = (unsigned)(A.perm[r] - P.off);
     if (dt_exe > 0.0) {   // else idle: a held instance or a spatial group between rounds
-      if (fresh) {
-        double v3[3];
-        int fb;
-        float e3;
-        rate_particle<double>(A, P, r, lam, v3, fb, e3);
-      } else {
-        lam = A.lam[r];
-      }
+      lam = fresh ? lam_fresh : A.lam[r];
       U4 w = philox(i_loc, ival, 0u, 0u, key0, key1);
       usw0 = w.z;
       usw1 = w.w;
@@ -1139,6 +1209,23 @@ __device__ __forceinline__ void sample_item(const McArgs& A, const int lane, con
     const unsigned k0 = __shfl_sync(FULLM, key0, p), k1 = __shfl_sync(FULLM, key1, p);
     const int bp = __shfl_sync(FULLM, b, p);
     const int up = __shfl_sync(FULLM, ub, p);
+    // mixed form, a heavy particle: its events are logged so that a time decision the FP32
+    // bounds leave open can be settled by the deferred FP64 pass instead of a serial replay
+    long long lbase = 0;
+    int lcap = 0;
+    if constexpr (kMixed) {
+      if (one && A.dlog) {
+        long long bl = 0;
+        int cl = 0;
+        if (lane == 0) {
+          cl = (int)fmin(fmin((double)A.max_events, 2.0 * ceil(lam * dte) + 64.0), 1073741824.0);
+          bl = (long long)atomicAdd(&A.dctr[0], (unsigned long long)cl);
+          if (bl + cl > A.dlog_cap) cl = 0;
+        }
+        lbase = __shfl_sync(FULLM, bl, 0);
+        lcap = __shfl_sync(FULLM, cl, 0);
+      }
+    }
     // mixed form: FP32 copies of per-particle constants for the per-event FP32 steps
     const float k6f = (float)f.k6, preff = f.prefT;
     float sf = (float)s;      // mixed form: the FP32 diameter the pair rates use
@@ -1147,6 +1234,7 @@ __device__ __forceinline__ void sample_item(const McArgs& A, const int lane, con
     float terr = (float)t * __shfl_sync(FULLM, eta_lam, p);
     const float dtef = (float)dte;
     bool unc = false;         // mixed form: an uncertified decision (warp-uniform)
+    bool tunc = false;        // mixed form: that decision is the time sum's against dt_exe
     int e = 0, near_ch = 0, near_u = 0;   // per-lane ties, warp-uniform ties
     unsigned h = 0u;
     T J = (T)0;
@@ -1294,47 +1382,47 @@ __device__ __forceinline__ void sample_item(const McArgs& A, const int lane, con
         ncoll_t = __shfl_sync(FULLM, nco, owner);
         psi_t = __shfl_sync(FULLM, pso, owner);
       }
+      if constexpr (kMixed) {
+        if (e < lcap && lane == 0) A.dlog[lbase + e] = make_int4(chosen, j, outcome, (int)ncoll_t);
+      }
       const double ncoll = (double)ncoll_t;
       const Snap64 pj = A.snap64[j];
       double m_new, s_new = s;
       float Jf = 0.0f;   // mixed form: |ln s'/s| of the event from the pair's FP32 psi
-      if (outcome == 0) {
-        if constexpr (!kMixed) m_new = m + ncoll * pj.m; else m_new = fma(ncoll, pj.m, m);
-        if constexpr (!kMixed) {
-          s_new = diameter_of<T>(cube_of<T>(f, m_new));
-        } else {
-          // the pair rates only need the FP32 diameter; the FP64-accurate one is formed
-          // when it is needed (a fragmentation, an FP64 decision, the particle's end)
-          sf = cbrtf((float)m_new * k6f);
-          s_stale = true;
-          Jf = log1pf((float)ncoll_t * (float)psi_t) * (1.0f / 3.0f);
-        }
+      if constexpr (!kMixed) {
+        int sset;
+        m_new = m;
+        event64(f.rho_s, f.s_min, k0, k1, pj, ch, outcome, ncoll, il, iv, (unsigned)e, s_new, m_new, sset);
+        if (!sset) s_new = s_of_m64(f.rho_s, m_new);
+      } else if (outcome == 0) {
+        // mixed form: the pair rates only need the FP32 diameter; the FP64-accurate one is
+        // formed when it is needed (a fragmentation, an FP64 decision, the particle's end)
+        m_new = fma(ncoll, pj.m, m);
+        sf = cbrtf((float)m_new * k6f);
+        s_stale = true;
+        Jf = log1pf((float)ncoll_t * (float)psi_t) * (1.0f / 3.0f);
       } else if (outcome == 1 && ch == 0) {
-        if constexpr (!kMixed) m_new = m - ncoll * pj.m; else m_new = fma(-ncoll, pj.m, m);
-        if constexpr (!kMixed) {
-          s_new = diameter_of<T>(cube_of<T>(f, m_new));
-        } else {
-          sf = cbrtf((float)m_new * k6f);
-          s_stale = true;
-          Jf = fabsf(log1pf(-(float)ncoll_t * (float)psi_t)) * (1.0f / 3.0f);
-        }
+        m_new = fma(-ncoll, pj.m, m);
+        sf = cbrtf((float)m_new * k6f);
+        s_stale = true;
+        Jf = fabsf(log1pf(-(float)ncoll_t * (float)psi_t)) * (1.0f / 3.0f);
       } else if (outcome == 1) {
         m_new = pj.m;
         s_new = pj.s;
-        if constexpr (kMixed) { sf = (float)s_new; s_stale = false; Jf = fabsf(logf((float)psi_t)) * (1.0f / 3.0f); }
+        sf = (float)s_new;
+        s_stale = false;
+        Jf = fabsf(logf((float)psi_t)) * (1.0f / 3.0f);
       } else {
         // fragmentation (Eq. frag): the size from the draw in FP64 in both forms
         U4 w2 = philox(il, iv, (unsigned)e, 1u, k0, k1);
-        if constexpr (kMixed) {
-          if (s_stale) { s = diameter_of<T>(cube_of<T>(f, m)); s_stale = false; }
-        }
+        if (s_stale) { s = diameter_of<T>(cube_of<T>(f, m)); s_stale = false; }
         const double U = u01(w2.x, w2.y);
         const double a = sqrt(f.s_min), bq = sqrt(s);
         const double xr = a + U * (bq - a);
         s_new = xr * xr;
-        if constexpr (!kMixed) m_new = kPi * f.rho_s * s_new * s_new * s_new / 6.0;
-        else m_new = f.mk * (s_new * s_new * s_new);
-        if constexpr (kMixed) { sf = (float)s_new; Jf = 2.0f * fabsf(logf((float)(xr / bq))); }
+        m_new = f.mk * (s_new * s_new * s_new);
+        sf = (float)s_new;
+        Jf = 2.0f * fabsf(logf((float)(xr / bq)));
       }
       if constexpr (!kMixed) J += fabs(log(s_new / s));
       else J += Jf;
@@ -1399,7 +1487,7 @@ __device__ __forceinline__ void sample_item(const McArgs& A, const int lane, con
         // difference, compared in FP32 with a margin far above its rounding)
         const double tn = t + dt2;
         const float dd = (float)(tn - dte);
-        if (!(fabsf(dd) > 1.5f * terr * 1.0001f + 1e-14f * dtef)) { unc = true; break; }
+        if (!(fabsf(dd) > 1.5f * terr * 1.0001f + 1e-14f * dtef)) { unc = true; tunc = true; break; }
         if (dd > 0.0f) break;
         t = tn;
         continue;
@@ -1410,12 +1498,36 @@ __device__ __forceinline__ void sample_item(const McArgs& A, const int lane, con
     if constexpr (kMixed) {
       if (!unc && s_stale) s = diameter_of<T>(cube_of<T>(f, m));
     }
+    // mixed form: a heavy particle whose time decision stayed open with all its events
+    // logged goes to the deferred FP64 pass (its states then need e + 1 state entries)
+    bool dfr = false;
+    if constexpr (kMixed) {
+      if (tunc && one && e >= kDeferMin && e <= lcap && A.defer) {
+        int okd = 0;
+        if (lane == 0) {
+          const unsigned long long d = atomicAdd(&A.dctr[1], 1ull);
+          if (d < (unsigned long long)A.defer_cap) {
+            const unsigned long long sb = atomicAdd(&A.dctr[2], (unsigned long long)(e + 1));
+            DeferRec rec;
+            rec.r = rp;
+            rec.lbase = lbase;
+            rec.sbase = (long long)sb;
+            rec.n = e;
+            rec.ok = sb + (unsigned long long)(e + 1) <= (unsigned long long)A.dstate_cap ? 1 : 0;
+            A.defer[d] = rec;
+            okd = rec.ok;
+          }
+        }
+        dfr = __shfl_sync(FULLM, okd, 0) != 0;
+      }
+    }
     int near_tot = near_ch;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) near_tot += __shfl_xor_sync(FULLM, near_tot, o);
     near_tot += near_u;
     if (lane == p) {
-      replay = unc;
+      replay = unc && !dfr;
+      deferred = dfr;
       my_e = e; my_h = h; nn += near_tot; my_MJ = f.M * (double)J; my_s = s;
     }
   }
@@ -1423,7 +1535,7 @@ __device__ __forceinline__ void sample_item(const McArgs& A, const int lane, con
     // the particles with an uncertified decision: replayed at once by the FP64 form (the
     // whole warp, one particle after another), which writes their results
     unsigned rep = __ballot_sync(FULLM, valid && replay);
-    if (valid && replay) atomicAdd((unsigned long long*)&A.st[ub].sample_redo, 1ull);
+    if (valid && (replay || deferred)) atomicAdd((unsigned long long*)&A.st[ub].sample_redo, 1ull);
     while (rep) {
       const int p = __ffs(rep) - 1;
       rep &= rep - 1u;
@@ -1431,7 +1543,8 @@ __device__ __forceinline__ void sample_item(const McArgs& A, const int lane, con
     }
   }
   if (valid) {
-    if (replay) {
+    if (replay || deferred) {
+      // written by the FP64 replay or the deferred pass
     } else {
       const int ci = A.perm[r];
       if (my_e > 0) {
@@ -1454,7 +1567,270 @@ __device__ __forceinline__ void sample_item(const McArgs& A, const int lane, con
 // warp.  Kept out of line: rare, and its registers stay apart from the mixed pass's.
 template <int S>
 __device__ __noinline__ void replay64(McArgs A, long long r, int lane) {
-  sample_item<double, S>(A, lane, true, true, r, lane == 0);
+  const double lam0 = lam0_fp64<S>(A, r, lane);
+  sample_item<double, S>(A, lane, true, true, r, lane == 0, lam0);
+}
+
+// ---------------------------------------------------------------- deferred FP64 settlement
+// Mixed form.  A heavy particle whose time decision the FP32 bounds left open has had every
+// channel decision certified or settled in FP64, so its states (s, m after k events) follow
+// from its logged choices with the FP64 form's arithmetic, and the FP64 waiting times of all
+// its states can be formed at once, a warp per state spread over the SMs, where the in-line
+// replay takes them one after another on one SM:
+//   k_defer_chain   the mass chain of each deferred particle (a warp each, the log read
+//                   32 entries at a time);
+//   k_defer_states  each state's lambda*_i (state 0: the rate kernel's FP64 arithmetic),
+//                   waiting time, FP64 choice, near ties and |ln s'/s| (a warp per state);
+//   k_defer_finish  the FP64 form's time sum in order, the chain continued in FP64 past the
+//                   logged events where the FP64 times say so, the particle's results (a
+//                   warp per particle; a choice that differs from the log falls back to the
+//                   in-line replay).
+// The results are the FP64 replay's: the same states, quantities and sums in the same order.
+__device__ __forceinline__ int defer_count(const McArgs& A) {
+  const unsigned long long n = A.dctr[1];
+  return n < (unsigned long long)A.defer_cap ? (int)n : A.defer_cap;
+}
+
+// A warp per deferred particle: each lane loads one event's log entry and partner, the
+// chain then runs through the chunk by shuffles (every lane the same values), lane i
+// storing the state after event i of the chunk.
+__global__ void __launch_bounds__(32) k_defer_chain(McArgs A) {
+  const int lane = threadIdx.x;
+  const int d = blockIdx.x;
+  if (d >= defer_count(A)) return;
+  const DeferRec rec = A.defer[d];
+  if (!rec.ok) return;
+  const long long r = rec.r;
+  const int b = inst_of(A.off, A.n_inst, r);
+  const InstDev& P = A.P[b];
+  const int ub = A.unit_r ? A.unit_r[r] : b;
+  const unsigned il = (unsigned)(A.perm[r] - P.off), iv = (unsigned)A.st[ub].interval_cur;
+  const Snap64 sn = A.snap64[r];
+  double s = sn.s, m = sn.m;
+  int sset = 1;
+  DState* St = A.dstate + rec.sbase;
+  if (lane == 0) {
+    St[0].s = s;
+    St[0].m = m;
+    St[0].sset = 1;
+  }
+  for (int base = 0; base < rec.n; base += 32) {
+    const int k = base + lane;
+    int4 L = make_int4(0, 0, 0, 0);
+    double pm = 0.0, ps = 0.0;
+    if (k < rec.n) {
+      L = A.dlog[rec.lbase + k];
+      const Snap64 pj = A.snap64[L.y];
+      pm = pj.m;
+      ps = pj.s;
+    }
+    const int cnt = min(32, rec.n - base);
+    for (int i = 0; i < cnt; ++i) {
+      const int ch = __shfl_sync(FULLM, L.x, i) & 1;
+      const int oc = __shfl_sync(FULLM, L.z, i);
+      const double nc = (double)__shfl_sync(FULLM, L.w, i);
+      Snap64 pj;
+      pj.m = __shfl_sync(FULLM, pm, i);
+      pj.s = __shfl_sync(FULLM, ps, i);
+      pj.N = 0.0;
+      pj.inv_m = 0.0;
+      if (oc == 2 && !sset) {   // a fragmentation starts from the FP64 diameter
+        s = s_of_m64(P.rho_s, m);
+        sset = 1;
+      }
+      event64(P.rho_s, P.s_min, P.key0, P.key1, pj, ch, oc, nc, il, iv, (unsigned)(base + i), s, m, sset);
+      if (lane == i) {
+        St[base + i + 1].s = s;
+        St[base + i + 1].m = m;
+        St[base + i + 1].sset = sset;
+      }
+    }
+  }
+}
+
+template <int S>
+__global__ void __launch_bounds__(256) k_defer_states(McArgs A) {
+  const int lane = threadIdx.x & 31;
+  const int d = blockIdx.y;
+  if (d >= defer_count(A)) return;
+  const DeferRec rec = A.defer[d];
+  if (!rec.ok) return;
+  const long long r = rec.r;
+  const int b = inst_of(A.off, A.n_inst, r);
+  const InstDev& P = A.P[b];
+  const int ub = A.unit_r ? A.unit_r[r] : b;
+  const unsigned il = (unsigned)(A.perm[r] - P.off), iv = (unsigned)A.st[ub].interval_cur;
+  const int wpb = blockDim.x >> 5;
+  for (int k = blockIdx.x * wpb + (threadIdx.x >> 5); k <= rec.n; k += gridDim.x * wpb) {
+    DState* Sk = A.dstate + rec.sbase + k;
+    const double m = Sk->m;
+    const double s = Sk->sset ? Sk->s : s_of_m64(P.rho_s, m);
+    const U4 w = philox(il, iv, (unsigned)k, 0u, P.key0, P.key1);
+    const Fp64Pick pk = fp64_event<S>(A, r, b, s, m, w.z, w.w, true, lane);
+    double lam = pk.lam;
+    // the first waiting time takes lambda*_i as the rate kernel forms it
+    if (k == 0) lam = lam0_fp64<S>(A, r, lane);
+    double dt = 0.0;
+    if (lam > 0.0 && isfinite(lam)) dt = waiting_time<double>(w.x, w.y, lam);
+    double J = 0.0;
+    int bad = 0;
+    if (k < rec.n) {
+      const int4 L = A.dlog[rec.lbase + k];
+      bad = L.x != pk.chosen ? 1 : 0;
+      const DState& Sn = A.dstate[rec.sbase + k + 1];
+      const double s1 = Sn.sset ? Sn.s : s_of_m64(P.rho_s, Sn.m);
+      J = fabs(log(s1 / s));
+    }
+    if (lane == 0) {
+      Sk->lam = lam;
+      Sk->dt = dt;
+      Sk->J = J;
+      Sk->ncoll = pk.ncoll;
+      Sk->chosen = pk.chosen;
+      Sk->j = pk.j;
+      Sk->outcome = pk.outcome;
+      Sk->np = pk.near_pair;
+      Sk->nc = pk.near - pk.near_pair;
+      Sk->bad = bad;
+    }
+  }
+}
+
+template <int S>
+__global__ void __launch_bounds__(32) k_defer_finish(McArgs A) {
+  const int lane = threadIdx.x;
+  const int d = blockIdx.x;
+  if (d >= defer_count(A)) return;
+  const DeferRec rec = A.defer[d];
+  if (!rec.ok) return;
+  const long long r = rec.r;
+  const DState* St = A.dstate + rec.sbase;
+  int bad = 0;
+  for (int k = lane; k < rec.n; k += 32) bad |= St[k].bad;
+  if (__any_sync(FULLM, bad != 0)) {
+    replay64<S>(A, r, lane);
+    return;
+  }
+  const int b = inst_of(A.off, A.n_inst, r);
+  const InstDev& P = A.P[b];
+  const int ub = A.unit_r ? A.unit_r[r] : b;
+  const unsigned il = (unsigned)(A.perm[r] - P.off), iv = (unsigned)A.st[ub].interval_cur;
+  const double dte = A.st[ub].dt_exe;
+  // the records of the logged states, 32 at a time: lane i holds state cb + i, and every lane
+  // takes state k's fields by shuffles, so the walk below is uniform over the warp
+  int cb = -1;
+  double c_lam = 0.0, c_dt = 0.0, c_J = 0.0;
+  int c_np = 0, c_nc = 0, c_ch = -1;
+  double lam, dt, Jk;
+  int np, nc, ch;
+  auto rec_of = [&](int k) {
+    const int base = k & ~31;
+    if (base != cb) {
+      cb = base;
+      const int q = base + lane;
+      if (q <= rec.n) {
+        const DState& x = St[q];
+        c_lam = x.lam; c_dt = x.dt; c_J = x.J; c_np = x.np; c_nc = x.nc; c_ch = x.chosen;
+      }
+    }
+    const int src = k - base;
+    lam = __shfl_sync(FULLM, c_lam, src);
+    dt = __shfl_sync(FULLM, c_dt, src);
+    Jk = __shfl_sync(FULLM, c_J, src);
+    np = __shfl_sync(FULLM, c_np, src);
+    nc = __shfl_sync(FULLM, c_nc, src);
+    ch = __shfl_sync(FULLM, c_ch, src);
+  };
+  int nn = 0, e = 0;
+  unsigned h = 0u;
+  double J = 0.0;
+  rec_of(0);
+  double t = dt;
+  bool any = false;
+  if (lam > 0.0 && isfinite(lam)) {
+    if (fabs(t - dte) < 1e-10 * dte) nn++;
+    any = !(t > dte);
+  }
+  // past the logged events: the state's (s, m) and its choice's partner, outcome and N_coll
+  double s = 0.0, m = 0.0, cn = 1.0;
+  int cj = -1, co = 0;
+  bool past = false;
+  if (any) {
+    nn += np;
+    for (;;) {
+      // the event at the current state (its FP64 choice)
+      nn += nc;
+      if (ch < 0) break;
+      h = h * 31u + (unsigned)(ch + 1);
+      if (e < rec.n) {
+        J += Jk;
+      } else {
+        if (!past) {
+          const DState& x = St[rec.n];
+          m = x.m;
+          s = x.sset ? x.s : s_of_m64(P.rho_s, x.m);
+          cj = x.j;
+          co = x.outcome;
+          cn = x.ncoll;
+          past = true;
+        }
+        double s1 = s, m1 = m;
+        int ss1 = 1;
+        event64(P.rho_s, P.s_min, P.key0, P.key1, A.snap64[cj], ch & 1, co, cn, il, iv, (unsigned)e, s1, m1, ss1);
+        if (!ss1) s1 = s_of_m64(P.rho_s, m1);
+        J += fabs(log(s1 / s));
+        s = s1;
+        m = m1;
+      }
+      ++e;
+      if (e >= A.max_events) {
+        if (lane == 0) set_status(&A.st[ub], GD_ST_EVENT_CAP);
+        break;
+      }
+      // the new state: from the state pass, or formed here past the logged events
+      if (e <= rec.n) {
+        rec_of(e);
+      } else {
+        const U4 w = philox(il, iv, (unsigned)e, 0u, P.key0, P.key1);
+        const Fp64Pick pk = fp64_event<S>(A, r, b, s, m, w.z, w.w, true, lane);
+        lam = pk.lam;
+        dt = (pk.lam > 0.0 && isfinite(pk.lam)) ? waiting_time<double>(w.x, w.y, pk.lam) : 0.0;
+        np = pk.near_pair;
+        nc = pk.near - pk.near_pair;
+        ch = pk.chosen;
+        cj = pk.j;
+        co = pk.outcome;
+        cn = pk.ncoll;
+      }
+      nn += np;
+      if (!(lam > 0.0) || !isfinite(lam)) {
+        if (lane == 0 && !(lam == 0.0)) set_status(&A.st[ub], GD_ST_NONFINITE);
+        break;
+      }
+      if (fabs((t + dt) - dte) < 1e-10 * dte) nn++;
+      if (t + dt > dte) break;
+      t = t + dt;
+    }
+  }
+  if (!past) {   // the final diameter: that of the state reached
+    const DState& x = St[e];
+    s = x.sset ? x.s : s_of_m64(P.rho_s, x.m);
+  }
+  if (lane == 0) {
+    const int ci = A.perm[r];
+    atomicAdd((unsigned long long*)&A.st[ub].sample_deferred, 1ull);
+    if (e > 0) {
+      A.s_out[ci] = s;
+      atomicAdd((unsigned long long*)&A.st[ub].events, (unsigned long long)e);
+    }
+    A.MJ[ci] = A.Mr[r] * J;
+    if (nn) atomicAdd((unsigned long long*)&A.st[ub].near_draw, (unsigned long long)nn);
+    if (A.ev_count) {
+      A.ev_count[ci] = e;
+      A.ev_hash[ci] = h;
+      A.near_out[ci] = nn;
+    }
+  }
 }
 
 template <typename T, int S>
@@ -1603,6 +1979,13 @@ static McArgs mc_args(gd_ctx* c) {
   A.unit_inst = c->d_unit_inst;
   A.heavy = nullptr;
   A.heavy_n = nullptr;
+  A.dlog = c->d_dlog;
+  A.dlog_cap = c->dlog_cap;
+  A.dctr = c->d_counters + 12;
+  A.defer = c->d_defer;
+  A.defer_cap = c->defer_cap;
+  A.dstate = c->d_dstate;
+  A.dstate_cap = c->dstate_cap;
   return A;
 }
 
@@ -1675,6 +2058,16 @@ static void sample_launch(gd_ctx* c, const McArgs& A) {
   k_sample<T, S><<<(int)blocks, 64, 0, c->stream>>>(A);
 }
 
+// The deferred FP64 settlement after the mixed sampler: 32 blocks of 8 warps per deferred
+// particle for its states (each warp a state at a time), then a warp per particle.
+template <int S>
+static void defer_launch(gd_ctx* c, const McArgs& A) {
+  k_defer_chain<<<c->defer_cap, 32, 0, c->stream>>>(A);
+  k_defer_states<S><<<dim3(32, c->defer_cap), 256, 0, c->stream>>>(A);
+  k_defer_finish<S><<<c->defer_cap, 32, 0, c->stream>>>(A);
+  c->launches += 3;
+}
+
 template <typename T>
 static void sample_t(gd_ctx* c, McArgs& A) {
   int S = (c->K + 31) / 32;
@@ -1687,12 +2080,22 @@ static void sample_t(gd_ctx* c, McArgs& A) {
   A.heavy = c->d_heavy;
   A.heavy_n = hn;
   cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long), c->stream);
+  if (sizeof(T) == 4 && A.dlog) cudaMemsetAsync(A.dctr, 0, 3 * sizeof(unsigned long long), c->stream);
   switch (S) {
     case 1: sample_launch<T, 1>(c, A); break;
     case 2: sample_launch<T, 2>(c, A); break;
     case 3: sample_launch<T, 3>(c, A); break;
     case 4: sample_launch<T, 4>(c, A); break;
     default: sample_launch<T, 8>(c, A); break;
+  }
+  if (sizeof(T) == 4 && A.dlog) {
+    switch (S) {
+      case 1: defer_launch<1>(c, A); break;
+      case 2: defer_launch<2>(c, A); break;
+      case 3: defer_launch<3>(c, A); break;
+      case 4: defer_launch<4>(c, A); break;
+      default: defer_launch<8>(c, A); break;
+    }
   }
 }
 

@@ -104,7 +104,9 @@ def test_config2_mixed_reproduces_fp64(gd):
     particles has the same event count and channel sequence in the mixed form as in the FP64
     form unless a near tie was flagged (the mixed form certifies each FP32 decision against
     its error bound and replays the rest in FP64), the flagged particles stay below 1e-6 of
-    the events, and the diameters agree to 1e-12 where the sequences do."""
+    the events, and the diameters agree to 1e-12 where the sequences do.  Among them are the
+    heavy particles whose open time decisions the deferred FP64 pass settled from their
+    logged events (some every interval on this workload)."""
     ins = W.config2()[0]
     res = {}
     for prec in (0, 1):
@@ -119,8 +121,10 @@ def test_config2_mixed_reproduces_fp64(gd):
     (e64, h64, n64, s64, st64), (e32, h32, n32, s32, st32) = res[0], res[1]
     i64, i32 = st64["instances"][0], st32["instances"][0]
     print(f"events {st64['events']} / {st32['events']}; near ties {st64['near_draw']} / {st32['near_draw']}; "
-          f"mixed FP64 redo: rates {st32['rate_redo']}, sampling {st32['sample_redo']}")
+          f"mixed FP64 redo: rates {st32['rate_redo']}, sampling {st32['sample_redo']} "
+          f"(deferred {st32['sample_deferred']})")
     assert st64["status"] == 0 and st32["status"] == 0
+    assert st32["sample_deferred"] >= 1 and st64["sample_deferred"] == 0
     assert i64["dt_exe"] == i32["dt_exe"] or i32["near_dt"] + i64["near_dt"] > 0
     if i64["dt_exe"] == i32["dt_exe"]:
         same = (e64 == e32) & (h64 == h32)
