@@ -835,7 +835,7 @@ def result_line(r, args, world):
         "knn_fp64_redo_per_step": r["mixed"].get("knn_redo", 0) / args.steps,
         "mixed_fp64_settled_per_step": {"rates": r["mixed"]["rate_redo"] / args.steps,
                                         "sampling": r["mixed"]["sample_redo"] / args.steps,
-                                        "sampling_deferred": r["mixed"]["sample_deferred"] / args.steps},
+                                        "sampling_deferred": r["mixed"].get("sample_deferred", 0) / args.steps},
         "roofline": roofline_of(km, kc, K, N, r["hbm"], r["peak_kind"], args.workload, r.get("pipe_peaks"),
                                 (r["mixed"]["clocks"] or {}).get("sm_mhz"), r.get("num_sms")),
         "kernels_ms_per_step": {k: v / args.steps for k, v in km.items() if v > 0 and k != "stats"},

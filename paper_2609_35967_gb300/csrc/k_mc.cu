@@ -1651,47 +1651,48 @@ __global__ void __launch_bounds__(32) k_defer_chain(McArgs A) {
 template <int S>
 __global__ void __launch_bounds__(256) k_defer_states(McArgs A) {
   const int lane = threadIdx.x & 31;
-  const int d = blockIdx.y;
-  if (d >= defer_count(A)) return;
-  const DeferRec rec = A.defer[d];
-  if (!rec.ok) return;
-  const long long r = rec.r;
-  const int b = inst_of(A.off, A.n_inst, r);
-  const InstDev& P = A.P[b];
-  const int ub = A.unit_r ? A.unit_r[r] : b;
-  const unsigned il = (unsigned)(A.perm[r] - P.off), iv = (unsigned)A.st[ub].interval_cur;
-  const int wpb = blockDim.x >> 5;
-  for (int k = blockIdx.x * wpb + (threadIdx.x >> 5); k <= rec.n; k += gridDim.x * wpb) {
-    DState* Sk = A.dstate + rec.sbase + k;
-    const double m = Sk->m;
-    const double s = Sk->sset ? Sk->s : s_of_m64(P.rho_s, m);
-    const U4 w = philox(il, iv, (unsigned)k, 0u, P.key0, P.key1);
-    const Fp64Pick pk = fp64_event<S>(A, r, b, s, m, w.z, w.w, true, lane);
-    double lam = pk.lam;
-    // the first waiting time takes lambda*_i as the rate kernel forms it
-    if (k == 0) lam = lam0_fp64<S>(A, r, lane);
-    double dt = 0.0;
-    if (lam > 0.0 && isfinite(lam)) dt = waiting_time<double>(w.x, w.y, lam);
-    double J = 0.0;
-    int bad = 0;
-    if (k < rec.n) {
-      const int4 L = A.dlog[rec.lbase + k];
-      bad = L.x != pk.chosen ? 1 : 0;
-      const DState& Sn = A.dstate[rec.sbase + k + 1];
-      const double s1 = Sn.sset ? Sn.s : s_of_m64(P.rho_s, Sn.m);
-      J = fabs(log(s1 / s));
-    }
-    if (lane == 0) {
-      Sk->lam = lam;
-      Sk->dt = dt;
-      Sk->J = J;
-      Sk->ncoll = pk.ncoll;
-      Sk->chosen = pk.chosen;
-      Sk->j = pk.j;
-      Sk->outcome = pk.outcome;
-      Sk->np = pk.near_pair;
-      Sk->nc = pk.near - pk.near_pair;
-      Sk->bad = bad;
+  const int nd = defer_count(A);
+  for (int d = blockIdx.y; d < nd; d += gridDim.y) {
+    const DeferRec rec = A.defer[d];
+    if (!rec.ok) continue;
+    const long long r = rec.r;
+    const int b = inst_of(A.off, A.n_inst, r);
+    const InstDev& P = A.P[b];
+    const int ub = A.unit_r ? A.unit_r[r] : b;
+    const unsigned il = (unsigned)(A.perm[r] - P.off), iv = (unsigned)A.st[ub].interval_cur;
+    const int wpb = blockDim.x >> 5;
+    for (int k = blockIdx.x * wpb + (threadIdx.x >> 5); k <= rec.n; k += gridDim.x * wpb) {
+      DState* Sk = A.dstate + rec.sbase + k;
+      const double m = Sk->m;
+      const double s = Sk->sset ? Sk->s : s_of_m64(P.rho_s, m);
+      const U4 w = philox(il, iv, (unsigned)k, 0u, P.key0, P.key1);
+      const Fp64Pick pk = fp64_event<S>(A, r, b, s, m, w.z, w.w, true, lane);
+      double lam = pk.lam;
+      // the first waiting time takes lambda*_i as the rate kernel forms it
+      if (k == 0) lam = lam0_fp64<S>(A, r, lane);
+      double dt = 0.0;
+      if (lam > 0.0 && isfinite(lam)) dt = waiting_time<double>(w.x, w.y, lam);
+      double J = 0.0;
+      int bad = 0;
+      if (k < rec.n) {
+        const int4 L = A.dlog[rec.lbase + k];
+        bad = L.x != pk.chosen ? 1 : 0;
+        const DState& Sn = A.dstate[rec.sbase + k + 1];
+        const double s1 = Sn.sset ? Sn.s : s_of_m64(P.rho_s, Sn.m);
+        J = fabs(log(s1 / s));
+      }
+      if (lane == 0) {
+        Sk->lam = lam;
+        Sk->dt = dt;
+        Sk->J = J;
+        Sk->ncoll = pk.ncoll;
+        Sk->chosen = pk.chosen;
+        Sk->j = pk.j;
+        Sk->outcome = pk.outcome;
+        Sk->np = pk.near_pair;
+        Sk->nc = pk.near - pk.near_pair;
+        Sk->bad = bad;
+      }
     }
   }
 }
@@ -2059,11 +2060,12 @@ static void sample_launch(gd_ctx* c, const McArgs& A) {
 }
 
 // The deferred FP64 settlement after the mixed sampler: 32 blocks of 8 warps per deferred
-// particle for its states (each warp a state at a time), then a warp per particle.
+// particle for its states (each warp a state at a time; 32 particles at once, the grid
+// striding over more), then a warp per particle.
 template <int S>
 static void defer_launch(gd_ctx* c, const McArgs& A) {
   k_defer_chain<<<c->defer_cap, 32, 0, c->stream>>>(A);
-  k_defer_states<S><<<dim3(32, c->defer_cap), 256, 0, c->stream>>>(A);
+  k_defer_states<S><<<dim3(32, 32), 256, 0, c->stream>>>(A);
   k_defer_finish<S><<<c->defer_cap, 32, 0, c->stream>>>(A);
   c->launches += 3;
 }
