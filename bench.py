@@ -126,11 +126,11 @@ def algo_bytes(kernel, K, mixed):
 # bench command (dram__bytes_read.sum + dram__bytes_write.sum), per particle.  The records
 # hold only while the sources the measured kernels compile from (their files and the shared
 # headers) have the content they had at the capture.
-TRAFFIC_CSRC_SHA256 = "17d595a4bcf0f88302a06d379c1a3d97427a3edfdcb4c98fd4c0c5d62443baef"
+TRAFFIC_CSRC_SHA256 = "1cee01f75e8560e8e8e3c027c926c2417346d94da4c0722d7aa176479ea4aa51"
 TRAFFIC = {
-    "knn": {"workload": "disk22", "bytes_per_particle": 389.18},
-    "rates": {"workload": "disk22", "bytes_per_particle": 196.03},
-    "sample": {"workload": "disk22", "bytes_per_particle": 149.69},
+    "knn": {"workload": "disk22", "bytes_per_particle": 392.34},
+    "rates": {"workload": "disk22", "bytes_per_particle": 196.20},
+    "sample": {"workload": "disk22", "bytes_per_particle": 161.97},
 }
 
 
@@ -139,9 +139,9 @@ TRAFFIC = {
 # warp instructions on the FP64 pipe), under the same source digest rule as TRAFFIC.
 INST_CSRC_SHA256 = TRAFFIC_CSRC_SHA256
 INST = {
-    "knn": {"workload": "disk22", "inst": 654.56, "fp64_inst": 2.0288},
+    "knn": {"workload": "disk22", "inst": 654.53, "fp64_inst": 2.0289},
     "rates": {"workload": "disk22", "inst": 321.52, "fp64_inst": 0.18779},
-    "sample": {"workload": "disk22", "inst": 279.76, "fp64_inst": 6.9077},
+    "sample": {"workload": "disk22", "inst": 291.51, "fp64_inst": 6.8512},
 }
 
 # Issue rate of the SMs: 4 schedulers per SM, one warp instruction each per cycle.
