@@ -542,7 +542,10 @@ cudaError_t launch_push_rad(gd_ctx* c, double dt) {
   const int blocks = (int)((c->N + 255) / 256);
   cudaError_t e = cudaSuccess;
   if (c->any_tau) e = cudaMemsetAsync(c->d_tau_max, 0, sizeof(unsigned long long) * c->n_inst, c->stream);
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess) {
+    time_end(c);
+    return e;
+  }
   if (c->precision == GD_MIXED)
     k_rad_drift<true><<<blocks, 256, 0, c->stream>>>(c->N, c->n_inst, c->d_off, c->d_inst, c->d_state, dt, c->x,
                                                      c->y, c->z, c->vr, c->lth, c->lph, c->s, c->M, c->d_mid,
@@ -554,7 +557,10 @@ cudaError_t launch_push_rad(gd_ctx* c, double dt) {
   c->launches += 1;
   if (c->any_tau) {
     e = tau_sums(c);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) {
+      time_end(c);
+      return e;
+    }
   }
   if (c->precision == GD_MIXED)
     k_rad_kick<true><<<blocks, 256, 0, c->stream>>>(c->N, c->n_inst, c->d_off, c->d_inst, c->d_state, dt, c->d_mid,
