@@ -105,3 +105,20 @@ def test_batch_sharding_splits_instances():
     out = bench.result_line(r, args, 2)
     assert out["scaling"] == "strong"
     assert out["value"] == 1000 * args.steps / (r["times"][0] * 1e-3)
+
+
+def test_counter_records_match_the_kernel_sources():
+    """The instruction and DRAM records the bench's roofline uses were taken on the kernel
+    sources as committed: their digest matches, and the bench-workload roofline of the K-NN
+    comes out as the issue bound with its traffic."""
+    import bench
+    assert bench.csrc_digest() == bench.TRAFFIC_CSRC_SHA256 == bench.INST_CSRC_SHA256
+    N = 1 << 22
+    km = {"knn": 49.7, "rates": 16.1, "sample": 38.6, "cells": 13.7}
+    kc = {k: 10 for k in km}
+    rl = bench.roofline_of(km, kc, 32, N, 6790.0, "measured", "disk22", {"fp64_tflops": 1.05}, 2070.0, 152)
+    assert rl["bound"] == "alu" and rl["kernel"] == "knn"
+    issue = bench.INST["knn"]["inst"] * N / 4.97e-3
+    assert abs(rl["frac"] - issue / (4 * 152 * 2070e6)) < 1e-9
+    assert abs(rl["traffic"] - bench.TRAFFIC["knn"]["bytes_per_particle"] * N) < 1.0
+    assert 0.0 < rl["fp64_pipe"]["frac"] < 1.0 and 0.0 < rl["hbm"]["frac"] < 1.0
